@@ -1,0 +1,414 @@
+/*
+ * lbm_oracle.c -- plain, slow, FP64 CPU oracle for the lattice Boltzmann hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or calls this
+ * file; only the test suite, the smoke check and the CPU-baseline leg of the benchmark load
+ * it.  It shares no code, header or table with the CUDA path.
+ *
+ * What it computes (waLBerla paper, Sec. 4.1 "Lattice Boltzmann method"):
+ *   - Eq. 1: density and momentum density are the zeroth and first moments of the PDFs.
+ *   - Eq. 2: f_i(x + c_i, t + 1) = f_i(x, t) + Omega_i(f(x, t)): collide, then push each
+ *     post-collision PDF to the neighbour it points at.
+ *   - Eq. 3 with the special relaxation matrices named right after it: SRT (one rate) and
+ *     TRT (one rate for the even part, one for the odd part of each direction pair).
+ *   - Sec. 4.1 body-force paragraph: a constant body force drives periodic set-ups; the
+ *     force model is Guo et al. (the paper cites it), split into even/odd parts under TRT.
+ *   - Sec. 4.1 boundary paragraph: no-slip, velocity and pressure boundaries.  The paper
+ *     cites Ginzburg 2008 for them; the oracle takes halfway bounce-back (no-slip),
+ *     bounce-back with a wall-velocity term (velocity) and anti-bounce-back (pressure).
+ *   - Sec. 3.5: boundary handling driven by a per-cell flag field (the "straightforward
+ *     way" of the paper).  The CUDA path uses the per-kind link lists instead.
+ * The paper fixes none of the constants of these operators; the reading adopted for each
+ * one is stated next to the code below.
+ *
+ * State convention: the oracle's state is the post-collision field f*(x, t) at fluid cells
+ * (the right-hand side of Eq. 2).  Arrays are f[i][z][y][x] with no ghost layer; the global
+ * domain has nx*ny*nz cells and knows nothing about blocks.
+ *
+ * Floating point: every operation is IEEE double, evaluated in source order (the build
+ * passes -ffp-contract=off so x86-64 and aarch64 give the same bits).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* cell / face kinds (flag field values) */
+#define ORC_FLUID 0
+#define ORC_NOSLIP 1
+#define ORC_VELOCITY 2
+#define ORC_PRESSURE 3
+#define ORC_PERIODIC 4 /* face kind only */
+
+#define ORC_SRT 0
+#define ORC_TRT 1
+
+#define QMAX 27
+
+typedef struct {
+    int32_t q;            /* 19 or 27 */
+    int32_t collision;    /* ORC_SRT or ORC_TRT */
+    int32_t nx, ny, nz;   /* global domain size in cells */
+    int32_t periodic[3];  /* non-zero: axis is periodic */
+    int32_t face_kind[6]; /* kind of the region outside face (axis, side) = index 2*axis+side */
+    double omega;         /* SRT: omega = 1/tau; TRT: omega_plus */
+    double magic_lambda;  /* TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2) */
+    double force[3];      /* constant body force per cell, lattice units */
+    double face_u[6][3];  /* wall velocity of a velocity face */
+    double face_rho[6];   /* wall density of a velocity face / pressure of a pressure face */
+} orc_params;
+
+/* ---------------------------------------------------------------------------------------
+ * Lattice.  The paper names D3Q19 and D3Q27 (Sec. 4.1) but prints no table.  The oracle
+ * enumerates the velocity set from its definition: all c in {-1,0,1}^3 with |c|^2 <= 2
+ * (D3Q19) or <= 3 (D3Q27), ordered by |c|^2 first; within |c|^2 = 1 the order is
+ * +x,-x,+y,-y,+z,-z; within |c|^2 = 2 and 3 it is lexicographic in (cx,cy,cz).  Weights are
+ * the standard ones that make the lattice isotropic to fourth order with c_s^2 = 1/3:
+ * D3Q19 1/3, 1/18, 1/36 and D3Q27 8/27, 2/27, 1/54, 1/216 by |c|^2 = 0,1,2,3.
+ * ------------------------------------------------------------------------------------- */
+int orc_lattice(int q, int *c, double *w, int *opp)
+{
+    if (q != 19 && q != 27) return -1;
+    int maxsq = (q == 19) ? 2 : 3;
+    int n = 0;
+    /* |c|^2 = 0 */
+    c[0] = c[1] = c[2] = 0;
+    n = 1;
+    /* |c|^2 = 1: one axis at a time, positive before negative */
+    for (int a = 0; a < 3; ++a) {
+        for (int s = 0; s < 2; ++s) {
+            c[3 * n + 0] = c[3 * n + 1] = c[3 * n + 2] = 0;
+            c[3 * n + a] = s == 0 ? 1 : -1;
+            ++n;
+        }
+    }
+    /* |c|^2 = 2, then 3: lexicographic */
+    for (int sq = 2; sq <= maxsq; ++sq) {
+        for (int cx = -1; cx <= 1; ++cx)
+            for (int cy = -1; cy <= 1; ++cy)
+                for (int cz = -1; cz <= 1; ++cz) {
+                    if (cx * cx + cy * cy + cz * cz != sq) continue;
+                    c[3 * n + 0] = cx;
+                    c[3 * n + 1] = cy;
+                    c[3 * n + 2] = cz;
+                    ++n;
+                }
+    }
+    if (n != q) return -2;
+    for (int i = 0; i < q; ++i) {
+        int sq = c[3 * i] * c[3 * i] + c[3 * i + 1] * c[3 * i + 1] + c[3 * i + 2] * c[3 * i + 2];
+        if (q == 19)
+            w[i] = sq == 0 ? 1.0 / 3.0 : (sq == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
+        else
+            w[i] = sq == 0 ? 8.0 / 27.0 : (sq == 1 ? 2.0 / 27.0 : (sq == 2 ? 1.0 / 54.0 : 1.0 / 216.0));
+        opp[i] = -1;
+        for (int j = 0; j < q; ++j)
+            if (c[3 * j] == -c[3 * i] && c[3 * j + 1] == -c[3 * i + 1] && c[3 * j + 2] == -c[3 * i + 2])
+                opp[i] = j;
+        if (opp[i] < 0) return -3;
+    }
+    return 0;
+}
+
+typedef struct {
+    int q;
+    int c[3 * QMAX];
+    double w[QMAX];
+    int opp[QMAX];
+} lattice_t;
+
+static int get_lattice(int q, lattice_t *L)
+{
+    L->q = q;
+    return orc_lattice(q, L->c, L->w, L->opp);
+}
+
+/* TRT: the second rate follows from the "magic" parameter
+ *   Lambda = (1/omega+ - 1/2) (1/omega- - 1/2)        (Ginzburg 2008, cited for TRT). */
+double orc_omega_minus(double omega_plus, double magic_lambda)
+{
+    double lp = 1.0 / omega_plus - 0.5;
+    return 1.0 / (magic_lambda / lp + 0.5);
+}
+
+/* Second-order polynomial equilibrium, compressible form (rho multiplies every term):
+ *   f_eq_i = w_i rho [1 + 3 c_i.u + 9/2 (c_i.u)^2 - 3/2 u.u].
+ * Same form for D3Q19 and D3Q27 (the paper does not fix it; this is the standard choice). */
+static void equilibrium(const lattice_t *L, double rho, const double u[3], double *feq)
+{
+    double usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < L->q; ++i) {
+        double cu = L->c[3 * i] * u[0] + L->c[3 * i + 1] * u[1] + L->c[3 * i + 2] * u[2];
+        feq[i] = L->w[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+    }
+}
+
+void orc_equilibrium(int q, double rho, const double *u, double *feq)
+{
+    lattice_t L;
+    if (get_lattice(q, &L) != 0) return;
+    equilibrium(&L, rho, u, feq);
+}
+
+/* Eq. 1 plus the Guo half-force shift:  rho = sum f,  rho u = sum c f + F/2. */
+static void moments_pre(const lattice_t *L, const double *f, const double F[3], double *rho, double u[3])
+{
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < L->q; ++i) {
+        r += f[i];
+        j[0] += L->c[3 * i] * f[i];
+        j[1] += L->c[3 * i + 1] * f[i];
+        j[2] += L->c[3 * i + 2] * f[i];
+    }
+    *rho = r;
+    for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * F[a]) / r;
+}
+
+/* Moments of a post-collision state: the collision adds F to sum c f, so the physical
+ * velocity of the same time level is (sum c f* - F/2) / rho.  Used for output and for the
+ * pressure boundary's u_b. */
+static void moments_post(const lattice_t *L, const double *f, const double F[3], double *rho, double u[3])
+{
+    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < L->q; ++i) {
+        r += f[i];
+        j[0] += L->c[3 * i] * f[i];
+        j[1] += L->c[3 * i + 1] * f[i];
+        j[2] += L->c[3 * i + 2] * f[i];
+    }
+    *rho = r;
+    for (int a = 0; a < 3; ++a) u[a] = (j[a] - 0.5 * F[a]) / r;
+}
+
+/* Collision operator Omega of Eq. 2, SRT or TRT (Eq. 3 with special S), with Guo forcing:
+ *   S_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F
+ *   SRT: f*_i = f_i - w (f_i - feq_i) + (1 - w/2) S_i
+ *   TRT: g+- = (g_i +- g_opp(i)) / 2 for g in {f, feq, S};
+ *        f*_i = f_i - w+ (f+ - feq+) - w- (f- - feq-) + (1 - w+/2) S+ + (1 - w-/2) S-.     */
+static void collide(const lattice_t *L, const orc_params *p, const double *f, double *fout)
+{
+    const double *F = p->force;
+    double rho, u[3];
+    moments_pre(L, f, F, &rho, u);
+    double feq[QMAX], S[QMAX];
+    equilibrium(L, rho, u, feq);
+    for (int i = 0; i < L->q; ++i) {
+        double cx = L->c[3 * i], cy = L->c[3 * i + 1], cz = L->c[3 * i + 2];
+        double cu = cx * u[0] + cy * u[1] + cz * u[2];
+        double ax = 3.0 * (cx - u[0]) + 9.0 * cu * cx;
+        double ay = 3.0 * (cy - u[1]) + 9.0 * cu * cy;
+        double az = 3.0 * (cz - u[2]) + 9.0 * cu * cz;
+        S[i] = L->w[i] * (ax * F[0] + ay * F[1] + az * F[2]);
+    }
+    if (p->collision == ORC_SRT) {
+        double w = p->omega;
+        for (int i = 0; i < L->q; ++i) fout[i] = f[i] - w * (f[i] - feq[i]) + (1.0 - 0.5 * w) * S[i];
+    } else {
+        double wp = p->omega;
+        double wm = orc_omega_minus(wp, p->magic_lambda);
+        for (int i = 0; i < L->q; ++i) {
+            int o = L->opp[i];
+            double fp = 0.5 * (f[i] + f[o]), fm = 0.5 * (f[i] - f[o]);
+            double ep = 0.5 * (feq[i] + feq[o]), em = 0.5 * (feq[i] - feq[o]);
+            double sp = 0.5 * (S[i] + S[o]), sm = 0.5 * (S[i] - S[o]);
+            fout[i] = f[i] - wp * (fp - ep) - wm * (fm - em) + (1.0 - 0.5 * wp) * sp + (1.0 - 0.5 * wm) * sm;
+        }
+    }
+}
+
+void orc_collide(const orc_params *p, const double *f, double *fout)
+{
+    lattice_t L;
+    if (get_lattice(p->q, &L) != 0) return;
+    collide(&L, p, f, fout);
+}
+
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Initial state.  Reading: the pre-collision populations at t = 0 are the equilibrium at
+ * rho0 and u0 - F/(2 rho0), so that the half-force-corrected velocity of Eq. 1 equals the
+ * requested u0; the stored state is their post-collision image f*(x, 0).
+ * rho, u: N and 3N (SoA: u[a*N + cell]) arrays, cell = x + nx (y + ny z).
+ * Non-fluid cells get all-zero PDFs.
+ * ------------------------------------------------------------------------------------- */
+int orc_init(const orc_params *p, const uint8_t *flags, const double *rho, const double *u, double *f)
+{
+    lattice_t L;
+    if (get_lattice(p->q, &L) != 0) return -1;
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    const int q = L.q;
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        if (flags[n] != ORC_FLUID) {
+            for (int i = 0; i < q; ++i) f[i * N + n] = 0.0;
+            continue;
+        }
+        double r = rho[n];
+        double uu[3];
+        for (int a = 0; a < 3; ++a) uu[a] = u[a * N + n] - 0.5 * p->force[a] / r;
+        double feq[QMAX], fs[QMAX];
+        equilibrium(&L, r, uu, feq);
+        collide(&L, p, feq, fs);
+        for (int i = 0; i < q; ++i) f[i * N + n] = fs[i];
+    }
+    return 0;
+}
+
+/* Kind of the cell at (x, y, z), which may lie outside the domain by one cell.
+ * Periodic axes wrap.  A coordinate outside a non-periodic axis takes the kind of that
+ * face; when it is outside on several non-periodic axes, the first of x, y, z decides
+ * (reading: the paper does not treat domain corners).  *cell receives the wrapped linear
+ * index for in-domain cells, *face the face index (2*axis+side) for outside cells. */
+static int resolve(const orc_params *p, const uint8_t *flags, int x, int y, int z, int64_t *cell, int *face)
+{
+    int xyz[3] = {x, y, z};
+    const int n[3] = {p->nx, p->ny, p->nz};
+    for (int a = 0; a < 3; ++a) {
+        if (xyz[a] >= 0 && xyz[a] < n[a]) continue;
+        if (p->periodic[a]) {
+            xyz[a] = (xyz[a] + n[a]) % n[a];
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        if (xyz[a] < 0 || xyz[a] >= n[a]) {
+            *face = 2 * a + (xyz[a] < 0 ? 0 : 1);
+            return p->face_kind[*face];
+        }
+    }
+    *cell = (int64_t)xyz[0] + (int64_t)n[0] * ((int64_t)xyz[1] + (int64_t)n[1] * xyz[2]);
+    *face = -1;
+    return flags[*cell];
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Time stepping in the push form of Eq. 2.
+ *   f   : in/out, post-collision state f*(t) -> f*(t + nsteps)
+ *   work: scratch array of the same size (pre-collision field of the next step)
+ *   cell_u (3N, SoA) / cell_rho (N): wall velocity / density of interior VELOCITY and
+ *   PRESSURE cells; may be NULL when the flag field has no such cells.
+ * For each fluid x and direction i, with y = x + c_i:
+ *   y fluid    : f_i(y, t+1)    = f*_i(x)
+ *   y no-slip  : f_opp(x, t+1)  = f*_i(x)                                   (bounce-back)
+ *   y velocity : f_opp(x, t+1)  = f*_i(x) - 6 w_i rho_w (c_i . u_w)       (moving wall)
+ *   y pressure : f_opp(x, t+1)  = -f*_i(x) + 2 w_i rho_w [1 + 9/2 (c_i.u_b)^2 - 3/2 u_b^2]
+ *                with u_b the velocity of x at time t (anti-bounce-back, no extrapolation)
+ * The wall lies halfway between x and y.  Then every fluid cell collides.
+ * ------------------------------------------------------------------------------------- */
+int orc_run(const orc_params *p, const uint8_t *flags, const double *cell_u, const double *cell_rho, double *f,
+            double *work, int64_t nsteps)
+{
+    lattice_t L;
+    if (get_lattice(p->q, &L) != 0) return -1;
+    const int nx = p->nx, ny = p->ny, nz = p->nz, q = L.q;
+    const int64_t N = (int64_t)nx * ny * nz;
+    int bad = 0;
+    for (int a = 0; a < 6; ++a) {
+        if (p->periodic[a / 2]) continue;
+        int k = p->face_kind[a];
+        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE) bad = 1;
+    }
+    if (bad) return -2;
+
+    for (int64_t step = 0; step < nsteps; ++step) {
+#pragma omp parallel for schedule(static) reduction(| : bad)
+        for (int z = 0; z < nz; ++z) {
+            for (int y = 0; y < ny; ++y) {
+                for (int x = 0; x < nx; ++x) {
+                    int64_t n = (int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z);
+                    if (flags[n] != ORC_FLUID) continue;
+                    double fs[QMAX];
+                    for (int i = 0; i < q; ++i) fs[i] = f[i * N + n];
+                    double rb = 0.0, ub[3] = {0.0, 0.0, 0.0};
+                    int have_ub = 0;
+                    for (int i = 0; i < q; ++i) {
+                        int64_t m;
+                        int face;
+                        int kind = resolve(p, flags, x + L.c[3 * i], y + L.c[3 * i + 1], z + L.c[3 * i + 2], &m, &face);
+                        int o = L.opp[i];
+                        if (kind == ORC_FLUID) {
+                            work[i * N + m] = fs[i];
+                        } else if (kind == ORC_NOSLIP) {
+                            work[o * N + n] = fs[i];
+                        } else if (kind == ORC_VELOCITY) {
+                            double uw[3], rw;
+                            if (face >= 0) {
+                                for (int a = 0; a < 3; ++a) uw[a] = p->face_u[face][a];
+                                rw = p->face_rho[face];
+                            } else {
+                                for (int a = 0; a < 3; ++a) uw[a] = cell_u[a * N + m];
+                                rw = cell_rho[m];
+                            }
+                            double cu = L.c[3 * i] * uw[0] + L.c[3 * i + 1] * uw[1] + L.c[3 * i + 2] * uw[2];
+                            work[o * N + n] = fs[i] - 6.0 * L.w[i] * rw * cu;
+                        } else if (kind == ORC_PRESSURE) {
+                            double rw = face >= 0 ? p->face_rho[face] : cell_rho[m];
+                            if (!have_ub) {
+                                moments_post(&L, fs, p->force, &rb, ub);
+                                have_ub = 1;
+                            }
+                            double cu = L.c[3 * i] * ub[0] + L.c[3 * i + 1] * ub[1] + L.c[3 * i + 2] * ub[2];
+                            double usq = ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2];
+                            work[o * N + n] = -fs[i] + 2.0 * L.w[i] * rw * (1.0 + 4.5 * cu * cu - 1.5 * usq);
+                        } else {
+                            bad = 1;
+                        }
+                    }
+                    (void)rb;
+                }
+            }
+        }
+        if (bad) return -3;
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < N; ++n) {
+            if (flags[n] != ORC_FLUID) continue;
+            double fin[QMAX], fout[QMAX];
+            for (int i = 0; i < q; ++i) fin[i] = work[i * N + n];
+            collide(&L, p, fin, fout);
+            for (int i = 0; i < q; ++i) f[i * N + n] = fout[i];
+        }
+    }
+    return 0;
+}
+
+/* Output moments of the stored state (Eq. 1, with the Guo shift for a post-collision
+ * state): rho = sum f*, u = (sum c f* - F/2) / rho.  Non-fluid cells give rho = u = 0. */
+int orc_macroscopic(const orc_params *p, const uint8_t *flags, const double *f, double *rho, double *u)
+{
+    lattice_t L;
+    if (get_lattice(p->q, &L) != 0) return -1;
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(static)
+    for (int64_t n = 0; n < N; ++n) {
+        if (flags[n] != ORC_FLUID) {
+            rho[n] = 0.0;
+            u[n] = u[N + n] = u[2 * N + n] = 0.0;
+            continue;
+        }
+        double fs[QMAX], r, uu[3];
+        for (int i = 0; i < L.q; ++i) fs[i] = f[i * N + n];
+        moments_post(&L, fs, p->force, &r, uu);
+        rho[n] = r;
+        for (int a = 0; a < 3; ++a) u[a * N + n] = uu[a];
+    }
+    return 0;
+}
