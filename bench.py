@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of the LBM hot path on GB300: MLUPS and fraction of the HBM roofline.
+
+Workload (one "step" = one lbm_step: boundary/ghost fill + fused stream-collide sweep):
+  D3Q19 TRT (Lambda = 3/16, tau = 1), 256^3 channel, no-slip bounce-back walls in y
+  (halfway, solid ghost layers), periodic x and z, body force (1e-6, 0, 0), rest start.
+  Headline variant: FP32 storage (two-grid unless --variant says otherwise); the other
+  variants (FP64 / FP32 x two-grid / AA) are reported under "variants".
+
+Timing: W untimed warm-up steps, then K steps bracketed by a barrier and a device
+synchronisation, measured with CUDA events on the library's stream; max over ranks.  The
+state (2 x 2.6 GB for FP32 two-grid) is far larger than L2 (129 MB), so no L2 flush is
+needed between steps.  Per-kernel device times come from the library's own event tracing
+(lbm_enable_timing / lbm_read_timing) on the same stream.
+
+--impl reference times the CPU oracle (the plain FP64 C program the parity tests use) on
+a bounded sample of the same workload: each step is one oracle time step of a
+256 x 256 x 8 slab of the channel (periodic in z, identical per-cell work).
+
+Multi-GPU: every rank runs an independent replica of the workload on its own GPU (the
+path is not sharded in this build); value = total lattice updates of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (256, 256, 256)
+FORCE = (1e-6, 0.0, 0.0)
+OMEGA = 1.0
+LAMBDA = 3.0 / 16.0
+METRIC = "MLUPS (lattice updates per second) of the fused stream-collide step and % of HBM roofline"
+WORKLOAD = "D3Q19 TRT (Lambda=3/16, tau=1) channel 256^3, no-slip walls in y, periodic x/z, body force 1e-6"
+VARIANTS = {
+    "fp32-twogrid": ("FP32", "TWO_GRID"),
+    "fp32-aa": ("FP32", "AA"),
+    "fp64-twogrid": ("FP64", "TWO_GRID"),
+    "fp64-aa": ("FP64", "AA"),
+}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas)
+# ---------------------------------------------------------------------------------------
+def dist_setup(backend=None):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max of a float over ranks (timing: the slowest rank defines the step time)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(units_per_rank: float, seconds_per_rank: float, world: int):
+    """Whole-job throughput: units of all ranks / max time over ranks."""
+    tmax = reduce_max(seconds_per_rank, world)
+    return units_per_rank * world / tmax, tmax
+
+
+# ---------------------------------------------------------------------------------------
+# measurement helpers
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.gpu = gpu_index
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except (ValueError, IndexError):
+                continue
+            for k, n in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1909_13772_gb300", "csrc")
+    for name in ("sweep.cu", "kernels.cuh", "lattice.cuh", "select.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(variant: str):
+    """DRAM bytes per sweep launch from a committed ncu summary, if it was taken on the
+    current sweep source (a line 'TRAFFIC variant=<v> bytes_per_launch=<n> source=<hash>')."""
+    cur = sweep_source_hash()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")) + glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
+        with open(path) as fh:
+            for line in fh:
+                m = re.search(r"TRAFFIC variant=(\S+) bytes_per_launch=([0-9.eE+]+) source=([0-9a-f]+)", line)
+                if m and m.group(1) == variant and m.group(3) == cur:
+                    return float(m.group(2))
+    return None
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def make_sim(lbm, storage, pattern, stream, tile=None):
+    p = lbm.make_params(stencil=lbm.D3Q19, collision=lbm.TRT, storage=getattr(lbm, storage),
+                        pattern=getattr(lbm, pattern), omega=OMEGA, magic_lambda=LAMBDA, force=FORCE,
+                        periodic=(1, 0, 1))
+    sim = lbm.Simulation(p, [((0, 0, 0), SHAPE)], stream=stream)
+    if tile:
+        sim.set_tile(*tile)
+    # y faces default to no-slip: walls at y = -1/2 and y = 255.5
+    return sim
+
+
+def time_variant(lbm, variant, steps, warmup, world, tile=None):
+    import torch
+    storage, pattern = VARIANTS[variant]
+    stream = torch.cuda.Stream()
+    sim = make_sim(lbm, storage, pattern, stream.cuda_stream, tile)
+    from paper_1909_13772_gb300 import inputs
+    rho, u = inputs.rest(SHAPE)
+    sim.init(0, rho, u)
+    info = sim.info()
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = sim.launches()
+    lbm.lbm_read_timing(sim.ctx, reset=True)
+    lbm.lbm_enable_timing(sim.ctx, True)
+    sampler = ClockSampler(torch.cuda.current_device())
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(steps):
+        sim.step(1)
+    end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(world)
+    lbm.lbm_enable_timing(sim.ctx, False)
+    kt = lbm.lbm_read_timing(sim.ctx, reset=True)
+    launches = sim.launches() - launches0
+    ms = start.elapsed_time(end)
+    diag = sim.reduce()
+    sim.close()
+    del stream
+    cells = info["cells"]
+    bpp = info["bytes_per_pdf"]
+    lups_per_s, tmax = aggregate(cells * steps, ms / 1e3, world)
+    sweep_ms = kt["sweep"][0] / max(1, kt["sweep"][1])
+    fill_ms = kt["fill"][0] / max(1, kt["fill"][1])
+    alg_bytes = 2 * 19 * bpp * info["fluid_cells"]  # per sweep launch
+    return {
+        "mlups": lups_per_s / 1e6, "ms_per_step": tmax * 1e3 / steps, "sweep_ms": sweep_ms, "fill_ms": fill_ms,
+        "sweep_share": kt["sweep"][0] / max(1e-9, kt["sweep"][0] + kt["fill"][0]),
+        "sweep_gbs": alg_bytes / (sweep_ms / 1e3) / 1e9, "alg_bytes_per_sweep": alg_bytes, "launches": launches,
+        "clocks": clocks, "info": info, "finite": diag["nonfinite"] == 0, "mass": diag["mass"],
+    }
+
+
+def time_e2e(lbm, variant, steps, world):
+    """Same metric through the C ABI with host buffers: host->device upload of the initial
+    macroscopic fields, K x (lbm_step + lbm_reduce read-back), device->host download of the
+    final fields, all inside the timed region."""
+    import torch
+    from paper_1909_13772_gb300 import inputs
+    storage, pattern = VARIANTS[variant]
+    stream = torch.cuda.Stream()
+    sim = make_sim(lbm, storage, pattern, stream.cuda_stream)
+    rho, u = inputs.rest(SHAPE)
+    rho_h = torch.from_numpy(rho).pin_memory().numpy()
+    u_h = torch.from_numpy(u).pin_memory().numpy()
+    rho_o = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
+    u_o = torch.empty(u.shape, dtype=torch.float64).pin_memory().numpy()
+    sim.init(0, rho_h, u_h)  # allocates and builds lists outside the timed region
+    sim.step(2)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    lbm.lbm_init_macroscopic(sim.ctx, 0, rho_h, u_h)
+    for _ in range(steps):
+        lbm.lbm_step(sim.ctx, 1)
+        lbm.lbm_reduce(sim.ctx)
+    lbm.lbm_get_macroscopic(sim.ctx, 0, rho_o, u_o)
+    dt = time.perf_counter() - t0
+    barrier(world)
+    cells = sim.info()["cells"]
+    sim.close()
+    lups, _ = aggregate(cells * steps, dt, world)
+    n = rho.size
+    return {"value": lups / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(4 * n * 8 / steps),
+            "d2h_bytes_per_step": int((4 * n * 8) / steps + 64)}
+
+
+def cpu_baseline(min_seconds=10.0, max_steps=200):
+    """The oracle as it stands, on the host cores, on a 256 x 256 x 8 slab of the channel."""
+    import oracle
+    from paper_1909_13772_gb300 import inputs
+    shape = (SHAPE[0], SHAPE[1], 8)
+    p = oracle.OracleParams(shape=shape, q=19, collision=oracle.TRT, omega=OMEGA, magic_lambda=LAMBDA, force=FORCE,
+                            periodic=(1, 0, 1), face_kind=(1, 1, 1, 1, 1, 1))
+    rho, u = inputs.rest(shape)
+    f = oracle.init(p, rho, u)
+    f = oracle.run(p, f, 1)
+    steps, t = 0, 0.0
+    while t < min_seconds and steps < max_steps:
+        t0 = time.perf_counter()
+        f = oracle.run(p, f, 1)
+        t += time.perf_counter() - t0
+        steps += 1
+    cells = shape[0] * shape[1] * shape[2]
+    return {"value": cells * steps / t / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "%d oracle steps of a 256x256x8 slab of the channel (FP64, D3Q19 TRT, walls in y)" % steps}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_setup()
+    from paper_1909_13772_gb300 import lbm
+    lbm.load_library()
+    head = args.variant
+    res = time_variant(lbm, head, args.steps, args.warmup, world)
+    variants = {}
+    if not args.headline_only:
+        for v in VARIANTS:
+            if v == head:
+                variants[v] = res
+                continue
+            k = max(10, min(args.steps, 200 if v.startswith("fp64") else args.steps))
+            variants[v] = time_variant(lbm, v, k, args.warmup, world)
+    e2e = time_e2e(lbm, head, args.steps, world)
+    cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    peak, peak_kind = measured_peaks()
+    traffic = recorded_traffic(head)
+    roof = {"bound": "hbm", "achieved": round(res["sweep_gbs"], 1), "peak": peak, "unit": "GB/s",
+            "frac": round(res["sweep_gbs"] / peak, 4), "traffic": traffic,
+            "kernel": "k_sweep (fused stream-collide, %s)" % head,
+            "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else "fallback",
+            "alg_bytes_per_launch": res["alg_bytes_per_sweep"], "sweep_ms": round(res["sweep_ms"], 4),
+            "sweep_share_of_step": round(res["sweep_share"], 4)}
+    out = {
+        "metric": METRIC, "value": round(res["mlups"], 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(res["ms_per_step"], 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if head.startswith("fp32") else "f64",
+        "data": "synthetic (rest state, body-force driven; no dataset)",
+        "config": {"workload": WORKLOAD, "variant": head, "shape": list(SHAPE), "stencil": "D3Q19",
+                   "collision": "TRT", "magic_lambda": LAMBDA, "omega": OMEGA,
+                   "cells_per_gpu": res["info"]["cells"], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "no flush: state of %.1f GB per array >> 129 MB L2" % (
+                       res["info"]["cells"] * 19 * res["info"]["bytes_per_pdf"] / 1e9)},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "variants": {k: {"mlups": round(v["mlups"], 1), "sweep_gbs": round(v["sweep_gbs"], 1),
+                         "frac_hbm": round(v["sweep_gbs"] / peak, 4), "ms_per_step": round(v["ms_per_step"], 4),
+                         "sweep_ms": round(v["sweep_ms"], 4), "fill_ms": round(v["fill_ms"], 4)}
+                     for k, v in variants.items()},
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_1909_13772_gb300 import inputs
+    shape = (SHAPE[0], SHAPE[1], 8)
+    p = oracle.OracleParams(shape=shape, q=19, collision=oracle.TRT, omega=OMEGA, magic_lambda=LAMBDA, force=FORCE,
+                            periodic=(1, 0, 1), face_kind=(1, 1, 1, 1, 1, 1))
+    rho, u = inputs.rest(shape)
+    f = oracle.init(p, rho, u)
+    f = oracle.run(p, f, args.warmup)
+    t0 = time.perf_counter()
+    f = oracle.run(p, f, args.steps)
+    dt = time.perf_counter() - t0
+    cells = shape[0] * shape[1] * shape[2]
+    v = cells * args.steps / dt / 1e6
+    sample = "each step: one oracle time step of a 256x256x8 slab of the channel (FP64, D3Q19 TRT)"
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (rest state, body-force driven; no dataset)",
+           "config": {"workload": WORKLOAD, "variant": args.variant, "shape": list(SHAPE), "sample_shape": list(shape)},
+           "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--variant", choices=list(VARIANTS), default="fp32-twogrid")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other variants")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann library (liblbm.so).
+ *
+ * The library runs the hot path of the block-structured lattice Boltzmann method described
+ * in the waLBerla paper (arXiv:1909.13772) on one GPU:
+ *   - the fused stream-collide sweep (Sec. 4.1, Eq. 1-2; Sec. 4.1.2 "stream and collision
+ *     step is fused"), D3Q19 or D3Q27, SRT or TRT collision (Eq. 3 with special S), Guo
+ *     body force (Sec. 4.1 body-force paragraph);
+ *   - structure-of-arrays PDF fields with one ghost layer per block (Sec. 3.1 "Structured
+ *     grids", Sec. 3.2 "Fields and sweeps": SoA layout, padded aligned rows);
+ *   - boundary sweeps driven by per-kind boundary link lists built from flag fields
+ *     (Sec. 3.5: "a separate list ... for each boundary condition", no-slip, velocity,
+ *     pressure; Sec. 4.1 boundary paragraph), plus periodic domain faces;
+ *   - the ghost-layer copy between blocks held on the same GPU (Sec. 2.3 PackInfo "local
+ *     transfer without intermediate buffers"; Sec. 3.2 "ghost layer exchange before or after
+ *     the kernel call");
+ *   - device compute with host mirrors only for set-up and output (Sec. 3.3 GPU support).
+ * The paper states its kernels are callable through a C ABI (Sec. 5.1 code generation);
+ * this header is that interface for this library.
+ *
+ * Conventions
+ *   - Every function returns lbm_status and never aborts.  On error, lbm_last_error(ctx)
+ *     gives a message.  CUDA errors are caught after each launch sequence (LBM_ERR_CUDA).
+ *   - Host buffers are owned by the caller and only touched during the call.
+ *   - Device memory is owned by the context (cudaMalloc) or, for the PDF arrays, by the
+ *     caller through lbm_bind_device_memory (e.g. a PyTorch tensor).
+ *   - A context is not thread-safe; it issues all work on one CUDA stream (given at
+ *     creation).  lbm_step returns without synchronising the host; lbm_get_* and
+ *     lbm_set_* synchronise the stream.
+ *   - Cell arrays on the host are per block, interior cells only, x fastest:
+ *     index = x + nx (y + ny z).  Vector fields are SoA: u[a*N + index], a = x, y, z.
+ *     PDF arrays are f[i*N + index] in the canonical direction order below.
+ *   - Canonical direction order (D3Q19): 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = the 12
+ *     vectors with |c|^2 = 2 in lexicographic order of (cx,cy,cz).  D3Q27 appends the 8
+ *     corner vectors in lexicographic order as 19..26.  Weights: D3Q19 1/3, 1/18, 1/36;
+ *     D3Q27 8/27, 2/27, 1/54, 1/216; c_s^2 = 1/3.
+ *   - The stored state is the post-collision field f*(x, t) (the right-hand side of Eq. 2);
+ *     lbm_get_macroscopic returns rho = sum f*, u = (sum c f* - F/2) / rho.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx; /* opaque; owned by the library */
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,         /* invalid argument */
+    LBM_ERR_STATE = 2,       /* call not valid in the context's current state */
+    LBM_ERR_CUDA = 3,        /* a CUDA call or kernel launch failed */
+    LBM_ERR_OOM = 4,         /* device or host allocation failed / bound buffer too small */
+    LBM_ERR_DIVERGED = 5,    /* diagnostics found non-finite values */
+    LBM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    LBM_ERR_UNSUPPORTED = 7  /* valid request this build does not support */
+} lbm_status;
+
+enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 };
+enum { LBM_SRT = 0, LBM_TRT = 1 };
+/* PDF storage: FP64 and FP32 store f_i; the *_DEV forms store f_i - w_i rho0 in 16 bits and
+ * collide in FP32. */
+enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16_DEV = 2, LBM_FP16_DEV = 3 };
+/* Two-grid: source and destination arrays swapped every step.  AA: one array updated in
+ * place with alternating even/odd access patterns. */
+enum { LBM_TWO_GRID = 0, LBM_AA = 1 };
+/* Cell kinds of a flag field, and kinds of a domain face. */
+enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_VELOCITY = 2, LBM_PRESSURE = 3, LBM_PERIODIC = 4 };
+
+typedef struct {
+    int32_t stencil;       /* LBM_D3Q19 or LBM_D3Q27 */
+    int32_t collision;     /* LBM_SRT or LBM_TRT */
+    int32_t storage;       /* LBM_FP64 ... */
+    int32_t pattern;       /* LBM_TWO_GRID or LBM_AA */
+    double omega;          /* SRT: omega = 1/tau; TRT: omega+ (sets the viscosity) */
+    double magic_lambda;   /* TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2); 3/16 typical */
+    double force[3];       /* constant body force per cell (lattice units), Guo scheme */
+    double rho0;           /* reference density (1.0); base of the *_DEV storages */
+    int32_t periodic[3];   /* non-zero: the domain is periodic along that axis */
+    int32_t diag_interval; /* >0: lbm_step checks the diagnostics every that many steps */
+} lbm_params;
+
+/* One block: global cell coordinates of its first interior cell and its interior size.
+ * Blocks must not overlap.  The domain is the bounding box of all blocks; cells of the
+ * bounding box not covered by any block are treated as no-slip solid. */
+typedef struct {
+    int64_t origin[3];
+    int32_t size[3];
+} lbm_block_desc;
+
+/* Domain totals over fluid cells (FP64, deterministic order). */
+typedef struct {
+    double mass;           /* sum rho */
+    double momentum[3];    /* sum rho u (physical velocity, half-force corrected) */
+    double kinetic_energy; /* sum rho |u|^2 / 2 */
+    double max_speed;      /* max |u| */
+    int64_t nonfinite;     /* number of fluid cells with a non-finite PDF */
+    int64_t fluid_cells;   /* number of fluid cells */
+} lbm_diagnostics;
+
+/* Sizes of the work one lbm_step performs, from the built boundary and ghost lists. */
+typedef struct {
+    int64_t cells;          /* interior cells of all blocks */
+    int64_t fluid_cells;    /* interior fluid cells */
+    int64_t links[4];       /* boundary links by kind (index LBM_NOSLIP..LBM_PRESSURE) */
+    int64_t ghost_slots;    /* PDF values copied by the ghost exchange per step */
+    int64_t ghost_runs;     /* copy runs in the ghost exchange list */
+    int64_t tiles;          /* sweep tiles (CTAs) per step */
+    int64_t bytes_per_pdf;  /* bytes of one stored PDF value */
+    int64_t device_bytes;   /* device memory held by the context */
+} lbm_info;
+
+/* Create a context for `nblocks` blocks.  `cuda_stream` is a cudaStream_t (or NULL for the
+ * default stream) on which all work of the context is issued.  Uses the current CUDA
+ * device.  No device memory is allocated yet (see lbm_bind_device_memory).
+ * Errors: LBM_ERR_ARG for invalid parameters or overlapping blocks. */
+lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks,
+                             void *cuda_stream, lbm_ctx **out);
+
+/* Bytes of device memory the PDF arrays need (two arrays for two-grid, one for AA),
+ * including 256-byte alignment slack. */
+size_t lbm_required_bytes(const lbm_ctx *ctx);
+
+/* Optional: place the PDF arrays in caller-owned device memory `dev_ptr` of `bytes` bytes
+ * (at least lbm_required_bytes).  Must be called before any call that touches PDFs.  The
+ * caller keeps the buffer alive until lbm_destroy.  Without it the library cudaMallocs.
+ * Boundary lists, masks and reduction scratch are always allocated by the library.
+ * Errors: LBM_ERR_OOM if too small, LBM_ERR_STATE if the arrays already exist. */
+lbm_status lbm_bind_device_memory(lbm_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* Kind of the region outside a domain face (axis 0..2, side 0 = low, 1 = high):
+ * LBM_NOSLIP, LBM_VELOCITY (wall velocity u_wall, density rho_wall) or LBM_PRESSURE
+ * (density rho_wall).  Faces of periodic axes are ignored.  Default: LBM_NOSLIP. */
+lbm_status lbm_set_face(lbm_ctx *ctx, int32_t axis, int32_t side, int32_t kind, const double u_wall[3],
+                        double rho_wall);
+
+/* Flag field of one block: uint8 per interior cell (LBM_FLUID, LBM_NOSLIP, LBM_VELOCITY,
+ * LBM_PRESSURE).  Velocity and pressure cells of this block use (u_wall, rho_wall).  NULL
+ * flags = all fluid.  Boundary link lists and ghost-copy lists are (re)built on the host
+ * before the next step.  Set flags before lbm_init_macroscopic: a cell that becomes fluid
+ * later has no valid PDFs. */
+lbm_status lbm_set_boundary(lbm_ctx *ctx, int32_t block, const uint8_t *flags, const double u_wall[3],
+                            double rho_wall);
+
+/* Initial state of one block from density rho[N] and velocity u[3N] (host, FP64): the
+ * populations are the equilibrium at (rho, u - F/(2 rho)), so the half-force-corrected
+ * velocity equals u; the stored state is their post-collision image, written in the
+ * context's current storage layout (two-grid source array or the current AA parity).
+ * Non-fluid cells are left untouched. */
+lbm_status lbm_init_macroscopic(lbm_ctx *ctx, int32_t block, const double *rho, const double *u);
+
+/* Advance all blocks by n time steps (asynchronous on the context's stream).  Each step:
+ * ghost-layer copy and boundary links, then the fused stream-collide sweep.  With
+ * diag_interval > 0 the host reads the diagnostics every diag_interval steps and returns
+ * LBM_ERR_DIVERGED when a value is non-finite. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Density rho[N] and velocity u[3N] of one block's stored state (host FP64 buffers).
+ * Non-fluid cells give 0.  Synchronises the stream. */
+lbm_status lbm_get_macroscopic(lbm_ctx *ctx, int32_t block, double *rho, double *u);
+
+/* Canonical post-collision PDFs f[Q*N] of one block (host FP64), whatever the pattern and
+ * AA parity.  Non-fluid cells give 0.  Synchronises the stream. */
+lbm_status lbm_get_pdfs(lbm_ctx *ctx, int32_t block, double *f);
+
+/* Overwrite one block's state with canonical post-collision PDFs f[Q*N] (host FP64),
+ * converted to the storage format.  Checkpoint restart: get_pdfs of every block, then
+ * set_pdfs of every block continues the run exactly.  Synchronises the stream. */
+lbm_status lbm_set_pdfs(lbm_ctx *ctx, int32_t block, const double *f);
+
+/* Domain totals of the stored state over all fluid cells (FP64, deterministic: fixed
+ * per-CTA partial sums reduced in a fixed order).  Synchronises the stream. */
+lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
+
+/* Work sizes of one step (builds the boundary lists if needed). */
+lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
+
+/* Sweep tile shape (cells per CTA along x, y, z; threads = tx * ty).  tx must be a
+ * multiple of 32, tx*ty <= 1024.  Takes effect at the next list build.  Default 64 x 4 x 4. */
+lbm_status lbm_set_tile(lbm_ctx *ctx, int32_t tx, int32_t ty, int32_t tz);
+
+/* Per-kernel device timing of lbm_step (tracing): when enabled, lbm_step records CUDA events
+ * around its fill and sweep launches on the context's stream.  lbm_read_timing synchronises
+ * the stream and returns, since the last reset, the summed device milliseconds and launch
+ * counts of the two kernels: ms[0]/count[0] = boundary-and-ghost fill, ms[1]/count[1] =
+ * stream-collide sweep.  enable = 0 stops recording; lbm_read_timing(ctx, ..., 1) resets. */
+lbm_status lbm_enable_timing(lbm_ctx *ctx, int32_t enable);
+lbm_status lbm_read_timing(lbm_ctx *ctx, double ms[2], int64_t count[2], int32_t reset);
+
+/* Number of kernels lbm_step launched since the context was created. */
+int64_t lbm_kernel_launches(const lbm_ctx *ctx);
+
+/* Canonical velocity set of a stencil (host only, no GPU needed): c[3*q] (cx, cy, cz per
+ * direction), w[q], opp[q].  Returns LBM_ERR_ARG for an unknown q. */
+lbm_status lbm_stencil_table(int32_t q, int32_t *c, double *w, int32_t *opp);
+
+/* Host-side view of the built lists, for inspection and tests (no GPU needed; builds the
+ * lists if needed).  Links: uint64 words, bits 0-4 direction q (pointing from the fluid
+ * cell into the boundary), 5-6 kind, 7-15 wall-parameter index, 16-31 block, 32-63 cell
+ * index in the block's padded layout.  Runs of `pattern` (LBM_TWO_GRID or LBM_AA): five
+ * int64 per run (src, dst, len, src stride, dst stride), offsets in elements from the base
+ * of a PDF array.  With out == NULL only the count is returned in *n. */
+lbm_status lbm_plan_links(lbm_ctx *ctx, uint64_t *out, int64_t cap, int64_t *n);
+lbm_status lbm_plan_runs(lbm_ctx *ctx, int32_t pattern, int64_t *out, int64_t cap, int64_t *n);
+/* Padded layout of a block: out[0..7] = xo, pitch, plane, slab, offset (elements), and the
+ * interior size nx, ny, nz.  Cell (x, y, z), each in [-1, n], has index
+ * (z+1) plane + (y+1) pitch + xo + x; direction i of it lives at offset + i slab + index.
+ * Also gives the arena size in elements as out[8]. */
+lbm_status lbm_plan_layout(lbm_ctx *ctx, int32_t block, int64_t out[9]);
+/* Wall-parameter table of the built lists: (ux, uy, uz, rho) per index. */
+lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
+
+/* Last error message of the context (never NULL). */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Free the context and all device memory it owns (not memory bound by the caller). */
+void lbm_destroy(lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,93 @@
+"""Build liblbm.so (the C-ABI library) in-tree with nvcc for sm_103a.
+
+Translation units: api.cu (C ABI, scheduler), plan.cpp (host list builder, OpenMP), and
+sweep.cu / aux.cu compiled once per (stencil, storage) variant.  Objects are compiled in
+parallel; the library lands in ``paper_1909_13772_gb300/_build/liblbm.so``.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(BUILD, "liblbm.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", "-I", INCLUDE, "-I", CSRC,
+           "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
+VARIANTS = [(q, st) for q in (19, 27) for st in (0, 1, 2, 3)]
+
+
+def _nvcc() -> str:
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build liblbm.so")
+
+
+def _sources():
+    return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))] + [os.path.join(INCLUDE, "lbm.h")]
+
+
+def _jobs(nvcc, extra):
+    jobs = []
+    for name in ("api.cu", "plan.cpp"):
+        src = os.path.join(CSRC, name)
+        obj = os.path.join(BUILD, name.replace(".", "_") + ".o")
+        lang = [] if name.endswith(".cu") else ["-x", "cu"]
+        jobs.append([nvcc] + ARCH + NVFLAGS + extra + lang + ["-c", src, "-o", obj])
+    for q, st in VARIANTS:
+        for name in ("sweep.cu", "aux.cu"):
+            src = os.path.join(CSRC, name)
+            obj = os.path.join(BUILD, "%s_%d_%d.o" % (name[:-3], q, st))
+            jobs.append([nvcc] + ARCH + NVFLAGS + extra + ["-DLBM_Q=%d" % q, "-DLBM_ST=%d" % st, "-c", src, "-o", obj])
+    return jobs
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
+    """Compile (if stale) and return the path of liblbm.so."""
+    srcs = _sources()
+    if (not force and not extra_flags and os.path.exists(LIB)
+            and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in srcs)):
+        return LIB
+    nvcc = _nvcc()
+    os.makedirs(BUILD, exist_ok=True)
+    extra = list(extra_flags or [])
+    jobs = _jobs(nvcc, extra)
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        return cmd, r
+
+    workers = max(1, min(len(jobs), os.cpu_count() or 4))
+    with cf.ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(run, jobs))
+    errors = [(c, r) for c, r in results if r.returncode != 0]
+    for c, r in results:
+        if verbose and (r.stdout or r.stderr):
+            sys.stderr.write(r.stdout + r.stderr)
+    if errors:
+        c, r = errors[0]
+        raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(c), r.stdout, r.stderr))
+    objs = [j[j.index("-o") + 1] for j in jobs]
+    tmp = LIB + ".%d.tmp" % os.getpid()
+    link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp", "-lgomp"]
+    r = subprocess.run(link, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("link failed:\n%s\n%s%s" % (" ".join(link), r.stdout, r.stderr))
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    import time
+    t = time.time()
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print("%.1f s" % (time.time() - t))

@@ -1,0 +1,804 @@
+// api.cu -- the C ABI (include/lbm.h): context, device memory, list upload and the step
+// scheduler.  Every step runs on the context's stream as two launches:
+//   two-grid:  fill(links + ghost runs into src) -> pull sweep src -> dst, swap
+//   AA:        fill(E) -> neighbour sweep  |  fill(O) -> local sweep   (alternating)
+// (Sec. 3.2: "a ghost layer exchange before or after the kernel call"; Sec. 3.5 boundary
+// lists handled by their own kernel; Sec. 4.1.2 fused stream-collide sweep.)
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "launch.hpp"
+#include "plan.hpp"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params p{};
+    int q = 19, storage = 1, pattern = 0, bpp = 4;
+    bool force = false;
+    std::vector<BlockLayout> blocks;
+    std::vector<std::vector<uint8_t>> flags;
+    std::vector<WallParam> block_param;
+    int face_kind[6];
+    WallParam face_param[6];
+    int tile[3] = {64, 4, 4};
+    int64_t arena_elems = 0;
+    cudaStream_t stream = nullptr;
+
+    // device state
+    bool dev_ready = false;
+    void *arena_raw = nullptr;
+    bool arena_owned = false;
+    size_t arena_bytes = 0;
+    void *arr[2] = {nullptr, nullptr};
+    int cur = 0;                 // two-grid: index of the array holding the state
+    int aa_layout = LAYOUT_AA_E;  // AA: layout of the stored state
+
+    Plan plan;
+    bool plan_built = false, plan_uploaded = false;
+    DevBlock *d_blocks = nullptr;
+    uint64_t *d_links = nullptr;
+    DevRun *d_runs_pull = nullptr, *d_runs_aa = nullptr;
+    DevTile *d_tiles = nullptr;
+    double *d_params = nullptr;
+    uint8_t *d_masks = nullptr;
+    std::vector<const uint8_t *> mask_ptr;
+    double *d_partials = nullptr;
+    int64_t partials_cap = 0;
+    double *d_out = nullptr;
+    double *d_scratch = nullptr;
+    int64_t scratch_cap = 0;
+    size_t list_bytes = 0;
+
+    Coll<double> cd{};
+    Coll<float> cf{};
+    double base[27] = {0};
+
+    int64_t launches = 0;
+    int64_t steps_done = 0;
+    std::string err;
+
+    // tracing: events around fill and sweep launches (pairs of [start, end])
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_marks[2];  // per kernel kind: (start idx, end idx)
+    size_t ev_used = 0;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *what)
+{
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+template <class T>
+void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+// ---- dispatch to the per-(stencil, storage) objects --------------------------------------
+#define LBM_SWITCH(q, st, NAME, ...)                              \
+    do {                                                          \
+        if (q == 19) {                                            \
+            switch (st) {                                         \
+                case 0: return NAME##19_0(__VA_ARGS__);           \
+                case 1: return NAME##19_1(__VA_ARGS__);           \
+                case 2: return NAME##19_2(__VA_ARGS__);           \
+                case 3: return NAME##19_3(__VA_ARGS__);           \
+            }                                                     \
+        } else {                                                  \
+            switch (st) {                                         \
+                case 0: return NAME##27_0(__VA_ARGS__);           \
+                case 1: return NAME##27_1(__VA_ARGS__);           \
+                case 2: return NAME##27_2(__VA_ARGS__);           \
+                case 3: return NAME##27_3(__VA_ARGS__);           \
+            }                                                     \
+        }                                                         \
+        return cudaErrorInvalidValue;                             \
+    } while (0)
+
+cudaError_t do_sweep(int q, int st, const SweepArgs &s) { LBM_SWITCH(q, st, launch_sweep_, s); }
+cudaError_t do_fill(int q, int st, const FillArgs &s) { LBM_SWITCH(q, st, launch_fill_, s); }
+cudaError_t do_cells(int q, int st, int op, int force, const CellArgs &s) { LBM_SWITCH(q, st, launch_cells_, op, force, s); }
+cudaError_t do_reduce(int q, int st, const ReduceArgs &s) { LBM_SWITCH(q, st, launch_reduce_, s); }
+
+int bytes_of(int storage) { return storage == LBM_FP64 ? 8 : (storage == LBM_FP32 ? 4 : 2); }
+
+lbm_status build_lists(lbm_ctx *c)
+{
+    if (c->plan_built) return LBM_OK;
+    PlanInput in;
+    in.q = c->q;
+    in.bytes_per_pdf = c->bpp;
+    for (int a = 0; a < 3; ++a) in.periodic[a] = c->p.periodic[a] != 0;
+    for (int f = 0; f < 6; ++f) {
+        in.face_kind[f] = c->face_kind[f];
+        in.face_param[f] = c->face_param[f];
+    }
+    for (int a = 0; a < 3; ++a) in.tile[a] = c->tile[a];
+    in.blocks = &c->blocks;
+    in.flags = &c->flags;
+    in.block_param = &c->block_param;
+    std::string e = build_plan(in, c->plan);
+    if (!e.empty()) return fail(c, LBM_ERR_UNSUPPORTED, "%s", e.c_str());
+    if ((int64_t)c->plan.tiles.size() > 0x7fffffffLL) return fail(c, LBM_ERR_UNSUPPORTED, "too many tiles");
+    c->plan_built = true;
+    c->plan_uploaded = false;
+    return LBM_OK;
+}
+
+template <class T>
+lbm_status upload(lbm_ctx *c, T *&dst, const std::vector<T> &v, const char *what)
+{
+    dfree(dst);
+    if (v.empty()) return LBM_OK;
+    CK(cudaMalloc((void **)&dst, v.size() * sizeof(T)), what);
+    CK(cudaMemcpy(dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), what);
+    c->list_bytes += v.size() * sizeof(T);
+    return LBM_OK;
+}
+
+lbm_status ensure_arena(lbm_ctx *c)
+{
+    if (c->dev_ready) return LBM_OK;
+    const int narr = c->pattern == LBM_TWO_GRID ? 2 : 1;
+    const size_t bytes1 = (size_t)c->arena_elems * c->bpp;
+    const size_t need = lbm_required_bytes(c);
+    if (!c->arena_raw) {
+        CK(cudaMalloc(&c->arena_raw, need), "cudaMalloc(PDF arrays)");
+        c->arena_owned = true;
+        c->arena_bytes = need;
+    }
+    uintptr_t b = ((uintptr_t)c->arena_raw + 255) & ~(uintptr_t)255;
+    c->arr[0] = (void *)b;
+    c->arr[1] = narr == 2 ? (void *)((b + bytes1 + 255) & ~(uintptr_t)255) : nullptr;
+    CK(cudaMemsetAsync(c->arr[0], 0, bytes1, c->stream), "clear PDF array");
+    if (narr == 2) CK(cudaMemsetAsync(c->arr[1], 0, bytes1, c->stream), "clear PDF array");
+    CK(cudaMalloc((void **)&c->d_out, 8 * sizeof(double)), "cudaMalloc(reduction output)");
+    c->dev_ready = true;
+    return LBM_OK;
+}
+
+lbm_status ensure_lists(lbm_ctx *c)
+{
+    lbm_status s = build_lists(c);
+    if (s != LBM_OK) return s;
+    if (c->plan_uploaded) return LBM_OK;
+    CK(cudaStreamSynchronize(c->stream), "synchronise before list upload");
+    c->list_bytes = 0;
+    const Plan &P = c->plan;
+    // masks: one buffer, per-block offsets
+    dfree(c->d_masks);
+    size_t mbytes = 0;
+    for (const auto &m : P.masks) mbytes += (m.size() + 255) / 256 * 256;
+    c->mask_ptr.assign(c->blocks.size(), nullptr);
+    if (mbytes) {
+        CK(cudaMalloc((void **)&c->d_masks, mbytes), "cudaMalloc(masks)");
+        c->list_bytes += mbytes;
+        size_t off = 0;
+        for (size_t b = 0; b < P.masks.size(); ++b) {
+            if (P.masks[b].empty()) continue;
+            CK(cudaMemcpy(c->d_masks + off, P.masks[b].data(), P.masks[b].size(), cudaMemcpyHostToDevice), "upload mask");
+            c->mask_ptr[b] = c->d_masks + off;
+            off += (P.masks[b].size() + 255) / 256 * 256;
+        }
+    }
+    std::vector<DevBlock> db(c->blocks.size());
+    for (size_t b = 0; b < db.size(); ++b) {
+        const BlockLayout &L = c->blocks[b];
+        db[b] = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[b], L.xo, 0};
+    }
+    lbm_status s2;
+    if ((s2 = upload(c, c->d_blocks, db, "upload blocks")) != LBM_OK) return s2;
+    if ((s2 = upload(c, c->d_links, P.links, "upload links")) != LBM_OK) return s2;
+    static_assert(sizeof(GhostRun) == sizeof(DevRun), "run layout");
+    static_assert(sizeof(Tile) == sizeof(DevTile), "tile layout");
+    std::vector<DevRun> rp(P.runs_pull.size()), ra(P.runs_aa.size());
+    if (!rp.empty()) memcpy(rp.data(), P.runs_pull.data(), rp.size() * sizeof(DevRun));
+    if (!ra.empty()) memcpy(ra.data(), P.runs_aa.data(), ra.size() * sizeof(DevRun));
+    if ((s2 = upload(c, c->d_runs_pull, rp, "upload runs")) != LBM_OK) return s2;
+    if ((s2 = upload(c, c->d_runs_aa, ra, "upload runs")) != LBM_OK) return s2;
+    std::vector<DevTile> dt(P.tiles.size());
+    if (!dt.empty()) memcpy(dt.data(), P.tiles.data(), dt.size() * sizeof(DevTile));
+    if ((s2 = upload(c, c->d_tiles, dt, "upload tiles")) != LBM_OK) return s2;
+    std::vector<double> par;
+    for (const auto &w : P.params) {
+        par.push_back(w.u[0]);
+        par.push_back(w.u[1]);
+        par.push_back(w.u[2]);
+        par.push_back(w.rho);
+    }
+    if ((s2 = upload(c, c->d_params, par, "upload params")) != LBM_OK) return s2;
+    const int64_t need = std::max<int64_t>(1, (int64_t)P.tiles.size()) * 8;
+    if (need > c->partials_cap) {
+        dfree(c->d_partials);
+        CK(cudaMalloc((void **)&c->d_partials, need * sizeof(double)), "cudaMalloc(reduction partials)");
+        c->partials_cap = need;
+    }
+    c->plan_uploaded = true;
+    return LBM_OK;
+}
+
+lbm_status ensure_scratch(lbm_ctx *c, int64_t doubles)
+{
+    if (doubles <= c->scratch_cap) return LBM_OK;
+    dfree(c->d_scratch);
+    CK(cudaMalloc((void **)&c->d_scratch, doubles * sizeof(double)), "cudaMalloc(transfer buffer)");
+    c->scratch_cap = doubles;
+    return LBM_OK;
+}
+
+int state_layout(const lbm_ctx *c) { return c->pattern == LBM_TWO_GRID ? LAYOUT_PULL : c->aa_layout; }
+
+CellArgs cell_args(lbm_ctx *c, int block)
+{
+    CellArgs a{};
+    const BlockLayout &L = c->blocks[block];
+    a.a = c->pattern == LBM_TWO_GRID ? c->arr[c->cur] : c->arr[0];
+    a.blk = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[block], L.xo, 0};
+    a.layout = state_layout(c);
+    a.mask = c->mask_ptr[block];
+    for (int k = 0; k < 3; ++k) a.F[k] = c->p.force[k];
+    for (int i = 0; i < 27; ++i) a.base[i] = c->base[i];
+    a.cd = c->cd;
+    a.cf = c->cf;
+    a.stream = c->stream;
+    return a;
+}
+
+lbm_status prepare(lbm_ctx *c)
+{
+    lbm_status s = ensure_arena(c);
+    if (s != LBM_OK) return s;
+    return ensure_lists(c);
+}
+
+// Next free event of the tracing pool (created on demand).
+lbm_status next_event(lbm_ctx *c, int *idx)
+{
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e), "cudaEventCreate");
+        c->ev_pool.push_back(e);
+    }
+    *idx = (int)c->ev_used++;
+    return LBM_OK;
+}
+
+lbm_status mark(lbm_ctx *c, int *idx)
+{
+    lbm_status s = next_event(c, idx);
+    if (s != LBM_OK) return s;
+    CK(cudaEventRecord(c->ev_pool[*idx], c->stream), "cudaEventRecord");
+    return LBM_OK;
+}
+
+lbm_status check_block(lbm_ctx *c, int32_t block)
+{
+    if (block < 0 || block >= (int32_t)c->blocks.size()) return fail(c, LBM_ERR_ARG, "block index %d out of range", block);
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks,
+                             void *cuda_stream, lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!params || !blocks || nblocks <= 0) return LBM_ERR_ARG;
+    const lbm_params &p = *params;
+    if (p.stencil != LBM_D3Q19 && p.stencil != LBM_D3Q27) return LBM_ERR_ARG;
+    if (p.collision != LBM_SRT && p.collision != LBM_TRT) return LBM_ERR_ARG;
+    if (p.storage < LBM_FP64 || p.storage > LBM_FP16_DEV) return LBM_ERR_ARG;
+    if (p.pattern != LBM_TWO_GRID && p.pattern != LBM_AA) return LBM_ERR_ARG;
+    if (!(p.omega >= 0.0 && p.omega < 2.0)) return LBM_ERR_ARG;
+    if (p.collision == LBM_TRT && !(p.magic_lambda > 0.0) && p.omega > 0.0) return LBM_ERR_ARG;
+    if (!(p.rho0 > 0.0) || p.diag_interval < 0) return LBM_ERR_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(p.force[a])) return LBM_ERR_ARG;
+    lbm_ctx *c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_ERR_OOM;
+    c->p = p;
+    c->q = p.stencil;
+    c->storage = p.storage;
+    c->pattern = p.pattern;
+    c->bpp = bytes_of(p.storage);
+    c->force = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->blocks.resize(nblocks);
+    for (int b = 0; b < nblocks; ++b) {
+        for (int a = 0; a < 3; ++a) {
+            c->blocks[b].origin[a] = blocks[b].origin[a];
+            c->blocks[b].n[a] = blocks[b].size[a];
+        }
+    }
+    int64_t elems = 0;
+    layout_blocks(c->blocks, c->bpp, c->q, 128, &elems);
+    std::string e = check_blocks(c->blocks);
+    if (!e.empty()) {
+        delete c;
+        return LBM_ERR_ARG;
+    }
+    c->arena_elems = elems;
+    c->flags.assign(nblocks, {});
+    c->block_param.assign(nblocks, WallParam{{0, 0, 0}, 1.0});
+    for (int f = 0; f < 6; ++f) {
+        c->face_kind[f] = LBM_NOSLIP;
+        c->face_param[f] = WallParam{{0, 0, 0}, 1.0};
+    }
+    // collision constants
+    const double wp = p.omega;
+    double wm = wp;
+    // TRT: Lambda = (1/w+ - 1/2)(1/w- - 1/2); at w+ = 0 (no relaxation of the even part) the
+    // IEEE evaluation gives the limit w- = 2.
+    if (p.collision == LBM_TRT) wm = 1.0 / (p.magic_lambda / (1.0 / wp - 0.5) + 0.5);
+    c->cd.omega_p = wp;
+    c->cd.omega_m = wm;
+    c->cd.a_p = 1.0 - 0.5 * wp;
+    c->cd.a_m = 1.0 - 0.5 * wm;
+    for (int a = 0; a < 3; ++a) c->cd.F[a] = p.force[a];
+    const LatticeView L = lattice_view(c->q);
+    for (int i = 0; i < 27; ++i) c->base[i] = (c->storage >= LBM_BF16_DEV && i < L.q) ? L.w[i] * p.rho0 : 0.0;
+    for (int i = 0; i < 27; ++i) c->cd.base[i] = c->base[i];
+    c->cf.omega_p = (float)wp;
+    c->cf.omega_m = (float)wm;
+    c->cf.a_p = (float)c->cd.a_p;
+    c->cf.a_m = (float)c->cd.a_m;
+    for (int a = 0; a < 3; ++a) c->cf.F[a] = (float)p.force[a];
+    for (int i = 0; i < 27; ++i) c->cf.base[i] = (float)c->base[i];
+    *out = c;
+    return LBM_OK;
+}
+
+size_t lbm_required_bytes(const lbm_ctx *c)
+{
+    if (!c) return 0;
+    const int narr = c->pattern == LBM_TWO_GRID ? 2 : 1;
+    const size_t bytes1 = ((size_t)c->arena_elems * c->bpp + 255) / 256 * 256;
+    return narr * bytes1 + 256;
+}
+
+lbm_status lbm_bind_device_memory(lbm_ctx *c, void *dev_ptr, size_t bytes)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (!dev_ptr) return fail(c, LBM_ERR_ARG, "null device pointer");
+    if (c->dev_ready || c->arena_raw) return fail(c, LBM_ERR_STATE, "PDF arrays already allocated");
+    if (bytes < lbm_required_bytes(c))
+        return fail(c, LBM_ERR_OOM, "bound buffer has %zu bytes, need %zu", bytes, lbm_required_bytes(c));
+    c->arena_raw = dev_ptr;
+    c->arena_owned = false;
+    c->arena_bytes = bytes;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_face(lbm_ctx *c, int32_t axis, int32_t side, int32_t kind, const double u_wall[3], double rho_wall)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (axis < 0 || axis > 2 || side < 0 || side > 1) return fail(c, LBM_ERR_ARG, "bad face");
+    if (kind != LBM_NOSLIP && kind != LBM_VELOCITY && kind != LBM_PRESSURE && kind != LBM_PERIODIC)
+        return fail(c, LBM_ERR_ARG, "bad face kind %d", kind);
+    if (kind == LBM_PERIODIC) {
+        if (!c->p.periodic[axis]) return fail(c, LBM_ERR_ARG, "axis %d is not periodic in the parameters", axis);
+        return LBM_OK;
+    }
+    if (!std::isfinite(rho_wall) || rho_wall <= 0.0) return fail(c, LBM_ERR_ARG, "bad wall density");
+    const int f = 2 * axis + side;
+    c->face_kind[f] = kind;
+    for (int a = 0; a < 3; ++a) c->face_param[f].u[a] = u_wall ? u_wall[a] : 0.0;
+    c->face_param[f].rho = rho_wall;
+    c->plan_built = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_boundary(lbm_ctx *c, int32_t block, const uint8_t *flags, const double u_wall[3], double rho_wall)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    const BlockLayout &L = c->blocks[block];
+    const size_t N = (size_t)L.n[0] * L.n[1] * L.n[2];
+    if (!std::isfinite(rho_wall) || rho_wall <= 0.0) return fail(c, LBM_ERR_ARG, "bad wall density");
+    if (!flags) {
+        c->flags[block].clear();
+    } else {
+        for (size_t n = 0; n < N; ++n)
+            if (flags[n] > LBM_PRESSURE) return fail(c, LBM_ERR_ARG, "flag value %d at cell %zu", flags[n], n);
+        c->flags[block].assign(flags, flags + N);
+    }
+    for (int a = 0; a < 3; ++a) c->block_param[block].u[a] = u_wall ? u_wall[a] : 0.0;
+    c->block_param[block].rho = rho_wall;
+    c->plan_built = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_macroscopic(lbm_ctx *c, int32_t block, const double *rho, const double *u)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if (!rho || !u) return fail(c, LBM_ERR_ARG, "null rho or u");
+    if ((s = prepare(c)) != LBM_OK) return s;
+    const BlockLayout &L = c->blocks[block];
+    const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
+    if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
+    CK(cudaMemcpyAsync(c->d_scratch, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy rho");
+    CK(cudaMemcpyAsync(c->d_scratch + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy u");
+    CellArgs a = cell_args(c, block);
+    a.f64 = c->d_scratch;
+    CK(do_cells(c->q, c->storage, CELL_INIT, c->force ? 1 : 0, a), "init kernel");
+    CK(cudaStreamSynchronize(c->stream), "init");
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *c, int64_t n)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (n < 0) return fail(c, LBM_ERR_ARG, "negative step count");
+    lbm_status s = prepare(c);
+    if (s != LBM_OK) return s;
+    const Plan &P = c->plan;
+    SweepArgs sw{};
+    sw.blocks = c->d_blocks;
+    sw.tiles = c->d_tiles;
+    sw.ntiles = (int64_t)P.tiles.size();
+    sw.tx = c->tile[0];
+    sw.ty = c->tile[1];
+    sw.tz = c->tile[2];
+    sw.force = c->force ? 1 : 0;
+    sw.cd = c->cd;
+    sw.cf = c->cf;
+    sw.stream = c->stream;
+    FillArgs fa{};
+    fa.blocks = c->d_blocks;
+    fa.links = c->d_links;
+    fa.nlinks = (int64_t)P.links.size();
+    fa.params = c->d_params;
+    for (int a = 0; a < 3; ++a) fa.F[a] = c->p.force[a];
+    for (int i = 0; i < 27; ++i) fa.base[i] = c->base[i];
+    fa.stream = c->stream;
+    for (int64_t t = 0; t < n; ++t) {
+        if (c->pattern == LBM_TWO_GRID) {
+            fa.a = c->arr[c->cur];
+            fa.mode = FILL_PULL;
+            fa.runs = c->d_runs_pull;
+            fa.nruns = (int64_t)P.runs_pull.size();
+            sw.a = c->arr[c->cur];
+            sw.b = c->arr[1 - c->cur];
+            sw.kind = SWEEP_PULL;
+        } else {
+            const bool even = c->aa_layout == LAYOUT_AA_E;
+            fa.a = c->arr[0];
+            fa.mode = even ? FILL_AA_E : FILL_AA_O;
+            fa.runs = c->d_runs_aa;
+            fa.nruns = (int64_t)P.runs_aa.size();
+            sw.a = c->arr[0];
+            sw.b = nullptr;
+            sw.kind = even ? SWEEP_AA_NBR : SWEEP_AA_LOCAL;
+        }
+        int e0 = -1, e1 = -1, e2 = -1;
+        if (c->timing && (s = mark(c, &e0)) != LBM_OK) return s;
+        if (fa.nlinks + fa.nruns > 0) {
+            CK(do_fill(c->q, c->storage, fa), "boundary/ghost fill launch");
+            c->launches++;
+        }
+        if (c->timing && (s = mark(c, &e1)) != LBM_OK) return s;
+        if (sw.ntiles > 0) {
+            CK(do_sweep(c->q, c->storage, sw), "sweep launch");
+            c->launches++;
+        }
+        if (c->timing) {
+            if ((s = mark(c, &e2)) != LBM_OK) return s;
+            if (fa.nlinks + fa.nruns > 0) c->ev_marks[0].push_back({e0, e1});
+            if (sw.ntiles > 0) c->ev_marks[1].push_back({e1, e2});
+        }
+        if (c->pattern == LBM_TWO_GRID)
+            c->cur = 1 - c->cur;
+        else
+            c->aa_layout = c->aa_layout == LAYOUT_AA_E ? LAYOUT_AA_O : LAYOUT_AA_E;
+        c->steps_done++;
+        if (c->p.diag_interval > 0 && c->steps_done % c->p.diag_interval == 0) {
+            lbm_diagnostics d;
+            lbm_status r = lbm_reduce(c, &d);
+            if (r != LBM_OK) return r;
+            if (d.nonfinite > 0 || !std::isfinite(d.mass))
+                return fail(c, LBM_ERR_DIVERGED, "non-finite state after step %lld (%lld cells)", (long long)c->steps_done,
+                            (long long)d.nonfinite);
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if (!rho || !u) return fail(c, LBM_ERR_ARG, "null output");
+    if ((s = prepare(c)) != LBM_OK) return s;
+    const BlockLayout &L = c->blocks[block];
+    const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
+    if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
+    CellArgs a = cell_args(c, block);
+    a.rho = c->d_scratch;
+    a.u = c->d_scratch + N;
+    CK(do_cells(c->q, c->storage, CELL_MACRO, 0, a), "macroscopic kernel");
+    CK(cudaMemcpyAsync(rho, c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy rho");
+    CK(cudaMemcpyAsync(u, c->d_scratch + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy u");
+    CK(cudaStreamSynchronize(c->stream), "get_macroscopic");
+    return LBM_OK;
+}
+
+lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(c, LBM_ERR_ARG, "null output");
+    if ((s = prepare(c)) != LBM_OK) return s;
+    const BlockLayout &L = c->blocks[block];
+    const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
+    if ((s = ensure_scratch(c, (int64_t)c->q * N)) != LBM_OK) return s;
+    CellArgs a = cell_args(c, block);
+    a.f64 = c->d_scratch;
+    CK(do_cells(c->q, c->storage, CELL_GET, 0, a), "get_pdfs kernel");
+    CK(cudaMemcpyAsync(f, c->d_scratch, (size_t)c->q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "copy pdfs");
+    CK(cudaStreamSynchronize(c->stream), "get_pdfs");
+    return LBM_OK;
+}
+
+lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if (!f) return fail(c, LBM_ERR_ARG, "null input");
+    if ((s = prepare(c)) != LBM_OK) return s;
+    const BlockLayout &L = c->blocks[block];
+    const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
+    if ((s = ensure_scratch(c, (int64_t)c->q * N)) != LBM_OK) return s;
+    CK(cudaMemcpyAsync(c->d_scratch, f, (size_t)c->q * N * sizeof(double), cudaMemcpyHostToDevice, c->stream),
+       "copy pdfs");
+    CellArgs a = cell_args(c, block);
+    a.f64 = c->d_scratch;
+    CK(do_cells(c->q, c->storage, CELL_SET, 0, a), "set_pdfs kernel");
+    CK(cudaStreamSynchronize(c->stream), "set_pdfs");
+    return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_ctx *c, lbm_diagnostics *out)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    lbm_status s = prepare(c);
+    if (s != LBM_OK) return s;
+    double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (!c->plan.tiles.empty()) {
+        ReduceArgs r{};
+        r.a = c->pattern == LBM_TWO_GRID ? c->arr[c->cur] : c->arr[0];
+        r.blocks = c->d_blocks;
+        r.tiles = c->d_tiles;
+        r.ntiles = (int64_t)c->plan.tiles.size();
+        r.tx = c->tile[0];
+        r.ty = c->tile[1];
+        r.tz = c->tile[2];
+        r.layout = state_layout(c);
+        for (int a = 0; a < 3; ++a) r.F[a] = c->p.force[a];
+        for (int i = 0; i < 27; ++i) r.base[i] = c->base[i];
+        r.partials = c->d_partials;
+        r.out = c->d_out;
+        r.stream = c->stream;
+        CK(do_reduce(c->q, c->storage, r), "reduction kernels");
+        CK(cudaMemcpyAsync(h, c->d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
+        CK(cudaStreamSynchronize(c->stream), "reduce");
+    }
+    out->mass = h[0];
+    out->momentum[0] = h[1];
+    out->momentum[1] = h[2];
+    out->momentum[2] = h[3];
+    out->kinetic_energy = h[4];
+    out->max_speed = h[5];
+    out->nonfinite = (int64_t)h[6];
+    out->fluid_cells = (int64_t)h[7];
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_ctx *c, lbm_info *out)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    lbm_status s = build_lists(c);
+    if (s != LBM_OK) return s;
+    const Plan &P = c->plan;
+    out->cells = P.cells;
+    out->fluid_cells = P.fluid_cells;
+    for (int k = 0; k < 4; ++k) out->links[k] = P.link_count[k];
+    const bool tg = c->pattern == LBM_TWO_GRID;
+    out->ghost_slots = tg ? P.ghost_slots_pull : P.ghost_slots_aa;
+    out->ghost_runs = (int64_t)(tg ? P.runs_pull.size() : P.runs_aa.size());
+    out->tiles = (int64_t)P.tiles.size();
+    out->bytes_per_pdf = c->bpp;
+    out->device_bytes = (int64_t)(c->arena_owned ? c->arena_bytes : 0) + (int64_t)c->list_bytes +
+                        c->partials_cap * 8 + c->scratch_cap * 8;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_tile(lbm_ctx *c, int32_t tx, int32_t ty, int32_t tz)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (tx <= 0 || ty <= 0 || tz <= 0 || tx % 32 != 0 || tx * ty > 256 || tx > 32000 || ty > 32000 || tz > 32000)
+        return fail(c, LBM_ERR_ARG, "bad tile %d x %d x %d (tx multiple of 32, tx*ty <= 256)", tx, ty, tz);
+    c->tile[0] = tx;
+    c->tile[1] = ty;
+    c->tile[2] = tz;
+    c->plan_built = false;
+    return LBM_OK;
+}
+
+lbm_status lbm_enable_timing(lbm_ctx *c, int32_t enable)
+{
+    if (!c) return LBM_ERR_ARG;
+    c->timing = enable != 0;
+    return LBM_OK;
+}
+
+lbm_status lbm_read_timing(lbm_ctx *c, double ms[2], int64_t count[2], int32_t reset)
+{
+    if (!c || !ms || !count) return LBM_ERR_ARG;
+    for (int k = 0; k < 2; ++k) {
+        ms[k] = 0.0;
+        count[k] = (int64_t)c->ev_marks[k].size();
+    }
+    if (!c->ev_marks[0].empty() || !c->ev_marks[1].empty()) {
+        CK(cudaStreamSynchronize(c->stream), "synchronise for timing");
+        for (int k = 0; k < 2; ++k)
+            for (const auto &m : c->ev_marks[k]) {
+                float t = 0.f;
+                CK(cudaEventElapsedTime(&t, c->ev_pool[m.first], c->ev_pool[m.second]), "cudaEventElapsedTime");
+                ms[k] += t;
+            }
+    }
+    if (reset) {
+        c->ev_marks[0].clear();
+        c->ev_marks[1].clear();
+        c->ev_used = 0;
+    }
+    return LBM_OK;
+}
+
+int64_t lbm_kernel_launches(const lbm_ctx *c) { return c ? c->launches : 0; }
+
+lbm_status lbm_stencil_table(int32_t q, int32_t *cv, double *w, int32_t *opp)
+{
+    if (q != 19 && q != 27) return LBM_ERR_ARG;
+    const LatticeView L = lattice_view(q);
+    for (int i = 0; i < q; ++i) {
+        if (cv) {
+            cv[3 * i] = L.cx[i];
+            cv[3 * i + 1] = L.cy[i];
+            cv[3 * i + 2] = L.cz[i];
+        }
+        if (w) w[i] = L.w[i];
+        if (opp) opp[i] = L.opp[i];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_links(lbm_ctx *c, uint64_t *out, int64_t cap, int64_t *n)
+{
+    if (!c || !n) return LBM_ERR_ARG;
+    lbm_status s = build_lists(c);
+    if (s != LBM_OK) return s;
+    *n = (int64_t)c->plan.links.size();
+    if (!out) return LBM_OK;
+    if (cap < *n) return fail(c, LBM_ERR_ARG, "buffer too small");
+    memcpy(out, c->plan.links.data(), (size_t)*n * sizeof(uint64_t));
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_runs(lbm_ctx *c, int32_t pattern, int64_t *out, int64_t cap, int64_t *n)
+{
+    if (!c || !n) return LBM_ERR_ARG;
+    lbm_status s = build_lists(c);
+    if (s != LBM_OK) return s;
+    const std::vector<GhostRun> &R = pattern == LBM_TWO_GRID ? c->plan.runs_pull : c->plan.runs_aa;
+    *n = (int64_t)R.size();
+    if (!out) return LBM_OK;
+    if (cap < 5 * *n) return fail(c, LBM_ERR_ARG, "buffer too small");
+    for (size_t r = 0; r < R.size(); ++r) {
+        out[5 * r] = R[r].src;
+        out[5 * r + 1] = R[r].dst;
+        out[5 * r + 2] = R[r].len;
+        out[5 * r + 3] = R[r].sstride;
+        out[5 * r + 4] = R[r].dstride;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_layout(lbm_ctx *c, int32_t block, int64_t out[9])
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    const BlockLayout &L = c->blocks[block];
+    out[0] = L.xo;
+    out[1] = L.pitch;
+    out[2] = L.plane;
+    out[3] = L.slab;
+    out[4] = L.offset;
+    out[5] = L.n[0];
+    out[6] = L.n[1];
+    out[7] = L.n[2];
+    out[8] = c->arena_elems;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_params(lbm_ctx *c, double *out, int64_t cap, int64_t *n)
+{
+    if (!c || !n) return LBM_ERR_ARG;
+    lbm_status s = build_lists(c);
+    if (s != LBM_OK) return s;
+    *n = (int64_t)c->plan.params.size();
+    if (!out) return LBM_OK;
+    if (cap < 4 * *n) return fail(c, LBM_ERR_ARG, "buffer too small");
+    for (size_t k = 0; k < c->plan.params.size(); ++k) {
+        for (int a = 0; a < 3; ++a) out[4 * k + a] = c->plan.params[k].u[a];
+        out[4 * k + 3] = c->plan.params[k].rho;
+    }
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    if (c->dev_ready || c->arena_owned) cudaStreamSynchronize(c->stream);
+    if (c->arena_owned) cudaFree(c->arena_raw);
+    dfree(c->d_blocks);
+    dfree(c->d_links);
+    dfree(c->d_runs_pull);
+    dfree(c->d_runs_aa);
+    dfree(c->d_tiles);
+    dfree(c->d_params);
+    dfree(c->d_masks);
+    dfree(c->d_partials);
+    dfree(c->d_out);
+    dfree(c->d_scratch);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

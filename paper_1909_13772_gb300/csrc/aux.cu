@@ -1,0 +1,388 @@
+// aux.cu -- boundary/ghost fill, initialisation, state import/export, macroscopic output and
+// deterministic reductions.  Compiled once per (stencil, storage) pair like sweep.cu.
+//
+// Storage layouts of the post-collision state f*_i(x) (x a fluid interior cell):
+//   LAYOUT_PULL (two-grid source array):  a[i][x]
+//   LAYOUT_AA_E (after an AA local sweep): a[opp i][x]
+//   LAYOUT_AA_O (after an AA neighbour sweep): a[i][x + c_i]
+#include "select.cuh"
+
+namespace lbm {
+namespace {
+
+constexpr int kQ = LBM_Q;
+using S = Storage<StoreT>;
+using R = typename S::R;
+using Lq = Lattice<kQ>;
+
+__device__ __forceinline__ int64_t slot(int layout, int i, int64_t cell, const DevBlock &B)
+{
+    if (layout == LAYOUT_PULL) return (int64_t)i * B.slab + cell;
+    if (layout == LAYOUT_AA_E) return (int64_t)Lq::opp(i) * B.slab + cell;
+    return (int64_t)i * B.slab + cell + dir_offset<kQ>(i, B.pitch, B.plane);
+}
+
+// ---------------------------------------------------------------------------------------
+// Boundary links and ghost copies (one launch; Sec. 3.5 boundary lists, Sec. 2.3 local
+// ghost transfer).  For a link (x, q) the outgoing post-collision PDF v = f*_q(x) hits the
+// boundary halfway to x + c_q and comes back as the incoming f_opp(q)(x, t+1):
+//   no-slip  : v
+//   velocity : v - 6 w_q rho_w (c_q . u_w)
+//   pressure : -v + 2 w_q rho_w [1 + 4.5 (c_q . u_b)^2 - 1.5 u_b^2],  u_b = u(x, t)
+// The result goes where the next sweep reads direction opp(q) of x:
+//   pull: a[opp q][x + c_q];  AA (before neighbour sweep): a[q][x + c_q];
+//   AA (before local sweep): a[opp q][x].
+// Ghost runs copy the slots the next sweep reads (pull, AA forward) from the interior
+// image cell to the ghost, or (AA reverse) the slots the neighbour sweep wrote into a ghost
+// back to the image cell.
+// ---------------------------------------------------------------------------------------
+struct FillConst {
+    R F[3];
+    R base[27];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevBlock *__restrict__ blocks,
+                                              const uint64_t *__restrict__ links, int64_t nlinks,
+                                              const DevRun *__restrict__ runs, int64_t nruns, int64_t link_ctas,
+                                              const double *__restrict__ params, FillConst k)
+{
+    if ((int64_t)blockIdx.x < link_ctas) {
+        const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (l >= nlinks) return;
+        const uint64_t w = links[l];
+        const int q = (int)(w & 31u);
+        const int kind = (int)((w >> 5) & 3u);
+        const int par = (int)((w >> 7) & 511u);
+        const int blk = (int)((w >> 16) & 0xffffu);
+        const int64_t cell = (int64_t)(w >> 32);
+        const DevBlock &B = blocks[blk];
+        StoreT *a = A + B.offset;
+        const int o = Lq::opp(q);
+        const int64_t offq = dir_offset<kQ>(q, B.pitch, B.plane);
+        int64_t src, dst;
+        int layout;
+        if (MODE == FILL_PULL) {
+            src = (int64_t)q * B.slab + cell;
+            dst = (int64_t)o * B.slab + cell + offq;
+            layout = LAYOUT_PULL;
+        } else if (MODE == FILL_AA_E) {
+            src = (int64_t)o * B.slab + cell;
+            dst = (int64_t)q * B.slab + cell + offq;
+            layout = LAYOUT_AA_E;
+        } else {
+            src = (int64_t)q * B.slab + cell + offq;
+            dst = (int64_t)o * B.slab + cell;
+            layout = LAYOUT_AA_O;
+        }
+        const R v = S::ld_rw(a + src, k.base[q]);
+        const R wq = R(Lq::w(q));
+        const R cx = R(Lq::cx(q)), cy = R(Lq::cy(q)), cz = R(Lq::cz(q));
+        R out;
+        if (kind == 1) {
+            out = v;
+        } else if (kind == 2) {
+            const double *p = params + 4 * par;
+            const R cu = cx * R(p[0]) + cy * R(p[1]) + cz * R(p[2]);
+            out = v - R(6) * wq * R(p[3]) * cu;
+        } else {
+            const double *p = params + 4 * par;
+            R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                const R fi = S::ld_rw(a + slot(layout, i, cell, B), k.base[i]);
+                rho += fi;
+                jx += R(Lq::cx(i)) * fi;
+                jy += R(Lq::cy(i)) * fi;
+                jz += R(Lq::cz(i)) * fi;
+            }
+            const R inv = R(1) / rho;
+            const R ux = (jx - R(0.5) * k.F[0]) * inv, uy = (jy - R(0.5) * k.F[1]) * inv,
+                    uz = (jz - R(0.5) * k.F[2]) * inv;
+            const R cu = cx * ux + cy * uy + cz * uz;
+            const R usq = ux * ux + uy * uy + uz * uz;
+            out = -v + R(2) * wq * R(p[3]) * (R(1) + R(4.5) * cu * cu - R(1.5) * usq);
+        }
+        S::st_plain(a + dst, out, k.base[o]);
+    } else {
+        const int64_t gt = ((int64_t)blockIdx.x - link_ctas) * blockDim.x + threadIdx.x;
+        const int64_t r = gt >> 5;
+        const int lane = threadIdx.x & 31;
+        if (r >= nruns) return;
+        const DevRun run = runs[r];
+        for (int e = lane; e < run.len; e += 32) {
+            const int64_t s = run.src + (int64_t)e * run.sstride;
+            const int64_t d = run.dst + (int64_t)e * run.dstride;
+            if (MODE == FILL_AA_O)
+                A[s] = A[d];
+            else
+                A[d] = A[s];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-cell kernels over one block's interior (thread per cell, n = x + nx (y + ny z)).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ int64_t cell_of(int64_t n, const DevBlock &B)
+{
+    const int x = (int)(n % B.nx);
+    const int64_t t = n / B.nx;
+    const int y = (int)(t % B.ny);
+    const int z = (int)(t / B.ny);
+    return (int64_t)(z + 1) * B.plane + (int64_t)(y + 1) * B.pitch + B.xo + x;
+}
+
+// Initial state: populations = equilibrium at (rho, u - F/(2 rho)), then one collision
+// (the stored state is post-collision).  Equilibrium: w rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u).
+template <bool FORCE>
+__global__ void k_init(StoreT *__restrict__ A, DevBlock B, int layout, const double *__restrict__ in,
+                       const uint8_t *__restrict__ mask, Coll<R> k)
+{
+    const int64_t N = (int64_t)B.nx * B.ny * B.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int64_t cell = cell_of(n, B);
+    StoreT *a = A + B.offset;
+    if (mask && mask[cell] != 0) return;  // non-fluid cells hold no state
+    const R rho = R(in[n]);
+    R ux = R(in[N + n]), uy = R(in[2 * N + n]), uz = R(in[3 * N + n]);
+    if (FORCE) {
+        ux -= R(0.5) * k.F[0] / rho;
+        uy -= R(0.5) * k.F[1] / rho;
+        uz -= R(0.5) * k.F[2] / rho;
+    }
+    const R usq = ux * ux + uy * uy + uz * uz;
+    R f[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const R cu = R(Lq::cx(i)) * ux + R(Lq::cy(i)) * uy + R(Lq::cz(i)) * uz;
+        f[i] = R(Lq::w(i)) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
+    }
+    collide<kQ, FORCE, R>(f, k);
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B), f[i], k.base[i]);
+}
+
+__global__ void k_get(const StoreT *__restrict__ A, DevBlock B, int layout, double *__restrict__ out,
+                      const uint8_t *__restrict__ mask, FillConst k)
+{
+    const int64_t N = (int64_t)B.nx * B.ny * B.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int64_t cell = cell_of(n, B);
+    const StoreT *a = A + B.offset;
+    const bool fluid = !(mask && mask[cell] != 0);
+    for (int i = 0; i < kQ; ++i)
+        out[(int64_t)i * N + n] = fluid ? (double)S::ld_rw(a + slot(layout, i, cell, B), k.base[i]) : 0.0;
+}
+
+__global__ void k_set(StoreT *__restrict__ A, DevBlock B, int layout, const double *__restrict__ in,
+                      const uint8_t *__restrict__ mask, FillConst k)
+{
+    const int64_t N = (int64_t)B.nx * B.ny * B.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int64_t cell = cell_of(n, B);
+    if (mask && mask[cell] != 0) return;
+    StoreT *a = A + B.offset;
+    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B), R(in[(int64_t)i * N + n]), k.base[i]);
+}
+
+// Output moments in FP64: rho = sum f*, u = (sum c f* - F/2) / rho.
+__global__ void k_macro(const StoreT *__restrict__ A, DevBlock B, int layout, double *__restrict__ rho_out,
+                        double *__restrict__ u_out, const uint8_t *__restrict__ mask, FillConst k, double Fx,
+                        double Fy, double Fz)
+{
+    const int64_t N = (int64_t)B.nx * B.ny * B.nz;
+    const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int64_t cell = cell_of(n, B);
+    if (mask && mask[cell] != 0) {
+        rho_out[n] = 0.0;
+        u_out[n] = u_out[N + n] = u_out[2 * N + n] = 0.0;
+        return;
+    }
+    const StoreT *a = A + B.offset;
+    double f[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B), k.base[i]);
+    const double F[3] = {Fx, Fy, Fz};
+    double rho, j[3];
+    moments_post<kQ>(f, F, rho, j);
+    rho_out[n] = rho;
+    u_out[n] = j[0] / rho;
+    u_out[N + n] = j[1] / rho;
+    u_out[2 * N + n] = j[2] / rho;
+}
+
+// ---------------------------------------------------------------------------------------
+// Deterministic FP64 reduction over all fluid cells: per tile (CTA) partial sums reduced by
+// warp shuffles, then one CTA sums the partials in a fixed order.
+// Partial record: mass, j_x, j_y, j_z, kinetic energy, max |u|, non-finite cells, fluid cells.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_reduce_tiles(const StoreT *__restrict__ A, const DevBlock *__restrict__ blocks,
+                                                      const DevTile *__restrict__ tiles, int tx, int tz, int layout,
+                                                      FillConst k, double Fx, double Fy, double Fz,
+                                                      double *__restrict__ partials)
+{
+    const DevTile t = tiles[blockIdx.x];
+    const DevBlock B = blocks[t.block];
+    const int lx = threadIdx.x % tx, ly = threadIdx.x / tx;
+    const int x = t.x0 + lx, y = t.y0 + ly;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const double F[3] = {Fx, Fy, Fz};
+    if (x < B.nx && y < B.ny) {
+        const int zend = min((int)t.z0 + tz, B.nz);
+        const StoreT *a = A + B.offset;
+        for (int z = t.z0; z < zend; ++z) {
+            const int64_t cell = (int64_t)(z + 1) * B.plane + (int64_t)(y + 1) * B.pitch + B.xo + x;
+            if (B.mask && B.mask[cell] != 0) continue;
+            double f[kQ];
+            bool finite = true;
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B), k.base[i]);
+                finite = finite && isfinite(f[i]);
+            }
+            double rho, j[3];
+            moments_post<kQ>(f, F, rho, j);
+            const double j2 = j[0] * j[0] + j[1] * j[1] + j[2] * j[2];
+            acc[0] += rho;
+            acc[1] += j[0];
+            acc[2] += j[1];
+            acc[3] += j[2];
+            acc[4] += 0.5 * j2 / rho;
+            acc[5] = fmax(acc[5], sqrt(j2) / rho);
+            acc[6] += finite ? 0.0 : 1.0;
+            acc[7] += 1.0;
+        }
+    }
+    __shared__ double sh[8][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const double v = c == 5 ? warp_max(acc[c]) : warp_sum(acc[c]);
+        if (lane == 0) sh[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int c = threadIdx.x;
+        double v = 0.0;
+        for (int w2 = 0; w2 < nwarps; ++w2) v = c == 5 ? fmax(v, sh[w2][c]) : v + sh[w2][c];
+        partials[(int64_t)blockIdx.x * 8 + c] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__ partials, int64_t n,
+                                                      double *__restrict__ out)
+{
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t p = threadIdx.x; p < n; p += blockDim.x)
+        for (int c = 0; c < 8; ++c) acc[c] = c == 5 ? fmax(acc[c], partials[p * 8 + c]) : acc[c] + partials[p * 8 + c];
+    __shared__ double sh[8][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const double v = c == 5 ? warp_max(acc[c]) : warp_sum(acc[c]);
+        if (lane == 0) sh[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int c = threadIdx.x;
+        double v = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v = c == 5 ? fmax(v, sh[w2][c]) : v + sh[w2][c];
+        out[c] = v;
+    }
+}
+
+FillConst fill_const(const double F[3], const double base[27])
+{
+    FillConst k;
+    for (int a = 0; a < 3; ++a) k.F[a] = (R)F[a];
+    for (int i = 0; i < 27; ++i) k.base[i] = (R)base[i];
+    return k;
+}
+
+template <int MODE>
+cudaError_t go_fill(const FillArgs &s)
+{
+    const int threads = 256;
+    const int64_t link_ctas = (s.nlinks + threads - 1) / threads;
+    const int64_t run_ctas = (s.nruns * 32 + threads - 1) / threads;
+    const int64_t ctas = link_ctas + run_ctas;
+    if (ctas == 0) return cudaSuccess;
+    if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_fill<MODE><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.links, s.nlinks, s.runs, s.nruns,
+                                                         link_ctas, s.params, fill_const(s.F, s.base));
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t LBM_CAT(launch_fill_, LBM_Q, LBM_ST)(const FillArgs &s)
+{
+    switch (s.mode) {
+        case FILL_PULL: return go_fill<FILL_PULL>(s);
+        case FILL_AA_E: return go_fill<FILL_AA_E>(s);
+        case FILL_AA_O: return go_fill<FILL_AA_O>(s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t LBM_CAT(launch_cells_, LBM_Q, LBM_ST)(int op, int force, const CellArgs &s)
+{
+    const int64_t N = (int64_t)s.blk.nx * s.blk.ny * s.blk.nz;
+    if (N == 0) return cudaSuccess;
+    const int threads = 256;
+    const int64_t ctas = (N + threads - 1) / threads;
+    if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const FillConst fk = fill_const(s.F, s.base);
+    const Coll<R> &k = coll_of(s.cd, s.cf, (R *)nullptr);
+    switch (op) {
+        case CELL_INIT:
+            if (force)
+                k_init<true><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, k);
+            else
+                k_init<false><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, k);
+            break;
+        case CELL_GET:
+            k_get<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, fk);
+            break;
+        case CELL_SET:
+            k_set<<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, fk);
+            break;
+        case CELL_MACRO:
+            k_macro<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blk, s.layout, s.rho, s.u, s.mask,
+                                                              fk, s.F[0], s.F[1], s.F[2]);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t LBM_CAT(launch_reduce_, LBM_Q, LBM_ST)(const ReduceArgs &s)
+{
+    if (s.ntiles <= 0 || s.ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (s.tx * s.ty > 256) return cudaErrorInvalidConfiguration;
+    const FillConst fk = fill_const(s.F, s.base);
+    k_reduce_tiles<<<(unsigned)s.ntiles, s.tx * s.ty, 0, s.stream>>>((const StoreT *)s.a, s.blocks, s.tiles, s.tx, s.tz,
+                                                                    s.layout, fk, s.F[0], s.F[1], s.F[2], s.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_reduce_final<<<1, 256, 0, s.stream>>>(s.partials, s.ntiles, s.out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,198 @@
+// kernels.cuh -- device-side data structures and the collision operator of the CUDA path.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+// Device view of one block (mirrors BlockLayout plus the device mask pointer).
+struct DevBlock {
+    int32_t nx, ny, nz, pitch;
+    int64_t plane, slab;
+    int64_t offset;       // element offset of this block in the PDF arena arrays
+    const uint8_t *mask;  // padded-layout cell kinds (0 = fluid) or nullptr
+    int32_t xo, pad;
+};
+
+struct DevTile {
+    int32_t block;
+    int16_t x0, y0, z0;
+    uint16_t flags;
+};
+
+struct DevRun {
+    int64_t src, dst;
+    int32_t len, sstride, dstride, pad;
+};
+
+// Collision constants, in the arithmetic type R of the sweep.
+template <class R>
+struct Coll {
+    R omega_p, omega_m;  // TRT rates (SRT: equal)
+    R a_p, a_m;          // 1 - omega/2 factors of the Guo source
+    R F[3];              // body force
+    R base[27];          // storage offset per direction (w_i rho0 for *_DEV storages, else 0)
+};
+
+// ---------------------------------------------------------------------------------------
+// Storage formats.  T is the stored type, R the arithmetic type.  The *_DEV formats store
+// the deviation f_i - w_i rho0 (base[i]) in 16 bits.
+// ---------------------------------------------------------------------------------------
+template <class T>
+struct Storage;
+
+template <>
+struct Storage<double> {
+    using T = double;
+    using R = double;
+    static __device__ __forceinline__ R ld(const T *p, R) { return __ldg(p); }
+    static __device__ __forceinline__ R ld_rw(const T *p, R) { return *p; }
+    static __device__ __forceinline__ void st(T *p, R v, R) { __stcs(p, v); }
+    static __device__ __forceinline__ void st_plain(T *p, R v, R) { *p = v; }
+};
+
+template <>
+struct Storage<float> {
+    using T = float;
+    using R = float;
+    static __device__ __forceinline__ R ld(const T *p, R) { return __ldg(p); }
+    static __device__ __forceinline__ R ld_rw(const T *p, R) { return *p; }
+    static __device__ __forceinline__ void st(T *p, R v, R) { __stcs(p, v); }
+    static __device__ __forceinline__ void st_plain(T *p, R v, R) { *p = v; }
+};
+
+template <>
+struct Storage<__nv_bfloat16> {
+    using T = __nv_bfloat16;
+    using R = float;
+    static __device__ __forceinline__ R ld(const T *p, R base) { return base + __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ R ld_rw(const T *p, R base) { return base + __bfloat162float(*p); }
+    static __device__ __forceinline__ void st(T *p, R v, R base) { __stcs(p, __float2bfloat16_rn(v - base)); }
+    static __device__ __forceinline__ void st_plain(T *p, R v, R base) { *p = __float2bfloat16_rn(v - base); }
+};
+
+template <>
+struct Storage<__half> {
+    using T = __half;
+    using R = float;
+    static __device__ __forceinline__ R ld(const T *p, R base) { return base + __half2float(__ldg(p)); }
+    static __device__ __forceinline__ R ld_rw(const T *p, R base) { return base + __half2float(*p); }
+    static __device__ __forceinline__ void st(T *p, R v, R base) { __stcs(p, __float2half_rn(v - base)); }
+    static __device__ __forceinline__ void st_plain(T *p, R v, R base) { *p = __float2half_rn(v - base); }
+};
+
+// ---------------------------------------------------------------------------------------
+// Collision operator (Eq. 2-3 of the paper with SRT/TRT relaxation and Guo forcing), fused
+// over opposite direction pairs.  For each pair (i, o = opp(i)):
+//   s = f_i + f_o, d = f_i - f_o                     (even / odd parts, times 2)
+//   rho = f_0 + sum s,  rho u = sum c_i d + F/2
+//   feq+ = w rho (1 + 4.5 (c.u)^2 - 1.5 u.u),  feq- = 3 w rho c.u
+//   S+ = w (9 (c.u)(c.F) - 3 u.F),  S- = 3 w c.F
+//   f*_i = f_i - w+ (s/2 - feq+) - w- (d/2 - feq-) + a+ S+ + a- S-
+//   f*_o = f_o - w+ (s/2 - feq+) + w- (d/2 - feq-) + a+ S+ - a- S-
+// which is the TRT operator written per pair; SRT is the case w- = w+.
+// ---------------------------------------------------------------------------------------
+template <int Q, bool FORCE, class R>
+__device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
+{
+    using L = Lattice<Q>;
+    R rho = f[0], jx = R(0), jy = R(0), jz = R(0);
+    R s[Q], d[Q];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const int o = L::opp(i);
+        s[i] = f[i] + f[o];
+        d[i] = f[i] - f[o];
+        rho += s[i];
+        if (L::cx(i) > 0) jx += d[i];
+        if (L::cx(i) < 0) jx -= d[i];
+        if (L::cy(i) > 0) jy += d[i];
+        if (L::cy(i) < 0) jy -= d[i];
+        if (L::cz(i) > 0) jz += d[i];
+        if (L::cz(i) < 0) jz -= d[i];
+    }
+    R ux, uy, uz;
+    const R inv = R(1) / rho;
+    if (FORCE) {
+        ux = (jx + R(0.5) * k.F[0]) * inv;
+        uy = (jy + R(0.5) * k.F[1]) * inv;
+        uz = (jz + R(0.5) * k.F[2]) * inv;
+    } else {
+        ux = jx * inv;
+        uy = jy * inv;
+        uz = jz * inv;
+    }
+    const R usq = ux * ux + uy * uy + uz * uz;
+    const R rb = rho * (R(1) - R(1.5) * usq);  // rho (1 - 1.5 u.u)
+    const R uF = FORCE ? ux * k.F[0] + uy * k.F[1] + uz * k.F[2] : R(0);
+    {
+        const R w0 = R(L::w(0));
+        R fs = f[0] - k.omega_p * (f[0] - w0 * rb);
+        if (FORCE) fs += k.a_p * (w0 * R(-3) * uF);
+        f[0] = fs;
+    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        if (L::opp(i) < i) continue;
+        const int o = L::opp(i);
+        const R w = R(L::w(i));
+        R cu = R(0);
+        if (L::cx(i) > 0) cu += ux;
+        if (L::cx(i) < 0) cu -= ux;
+        if (L::cy(i) > 0) cu += uy;
+        if (L::cy(i) < 0) cu -= uy;
+        if (L::cz(i) > 0) cu += uz;
+        if (L::cz(i) < 0) cu -= uz;
+        const R feqp = w * (rb + R(4.5) * rho * cu * cu);
+        const R feqm = w * R(3) * rho * cu;
+        const R ep = k.omega_p * (R(0.5) * s[i] - feqp);
+        const R em = k.omega_m * (R(0.5) * d[i] - feqm);
+        R fi = f[i] - ep - em;
+        R fo = f[o] - ep + em;
+        if (FORCE) {
+            R cF = R(0);
+            if (L::cx(i) > 0) cF += k.F[0];
+            if (L::cx(i) < 0) cF -= k.F[0];
+            if (L::cy(i) > 0) cF += k.F[1];
+            if (L::cy(i) < 0) cF -= k.F[1];
+            if (L::cz(i) > 0) cF += k.F[2];
+            if (L::cz(i) < 0) cF -= k.F[2];
+            const R sp = k.a_p * (w * (R(9) * cu * cF - R(3) * uF));
+            const R sm = k.a_m * (w * R(3) * cF);
+            fi += sp + sm;
+            fo += sp - sm;
+        }
+        f[i] = fi;
+        f[o] = fo;
+    }
+}
+
+// Moments of a stored post-collision state, in FP64: rho = sum f*, j = sum c f* - F/2.
+template <int Q>
+__device__ __forceinline__ void moments_post(const double (&f)[Q], const double F[3], double &rho, double j[3])
+{
+    using L = Lattice<Q>;
+    rho = 0.0;
+    j[0] = j[1] = j[2] = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        rho += f[i];
+        j[0] += L::cx(i) * f[i];
+        j[1] += L::cy(i) * f[i];
+        j[2] += L::cz(i) * f[i];
+    }
+    for (int a = 0; a < 3; ++a) j[a] -= 0.5 * F[a];
+}
+
+template <int Q>
+__host__ __device__ constexpr int64_t dir_offset(int i, int64_t pitch, int64_t plane)
+{
+    return (int64_t)Lattice<Q>::cx(i) + (int64_t)Lattice<Q>::cy(i) * pitch + (int64_t)Lattice<Q>::cz(i) * plane;
+}
+
+}  // namespace lbm

@@ -1,0 +1,96 @@
+// launch.hpp -- host-side launch interface between the C ABI layer and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "kernels.cuh"
+
+namespace lbm {
+
+enum SweepKind { SWEEP_PULL = 0, SWEEP_AA_LOCAL = 1, SWEEP_AA_NBR = 2 };
+enum FillMode { FILL_PULL = 0, FILL_AA_E = 1, FILL_AA_O = 2 };
+enum Layout { LAYOUT_PULL = 0, LAYOUT_AA_E = 1, LAYOUT_AA_O = 2 };
+
+struct SweepArgs {
+    void *a;  // two-grid source / AA array
+    void *b;  // two-grid destination (unused for AA)
+    const DevBlock *blocks;
+    const DevTile *tiles;
+    int64_t ntiles;
+    int tx, ty, tz;
+    int kind;   // SweepKind
+    int force;  // body force non-zero
+    Coll<double> cd;
+    Coll<float> cf;
+    cudaStream_t stream;
+};
+
+struct FillArgs {
+    void *a;  // array holding the state the next sweep reads
+    const DevBlock *blocks;
+    const uint64_t *links;
+    int64_t nlinks;
+    const DevRun *runs;
+    int64_t nruns;
+    const double *params;  // wall table: (ux, uy, uz, rho) per entry
+    int mode;              // FillMode
+    double F[3];
+    double base[27];
+    cudaStream_t stream;
+};
+
+// Per-cell kernels over the interior cells of one block (get/set/macroscopic/init).
+struct CellArgs {
+    void *a;
+    DevBlock blk;
+    int layout;  // Layout of the stored state
+    double *f64;        // get: out f[Q*N]; set: in; init: rho[N] then u[3N]
+    double *rho, *u;    // macroscopic out
+    const uint8_t *mask;
+    double F[3];
+    double base[27];
+    Coll<double> cd;
+    Coll<float> cf;
+    cudaStream_t stream;
+};
+
+struct ReduceArgs {
+    const void *a;
+    const DevBlock *blocks;
+    const DevTile *tiles;
+    int64_t ntiles;
+    int tx, ty, tz;
+    int layout;
+    double F[3];
+    double base[27];
+    double *partials;  // ntiles * 8 doubles
+    double *out;       // 8 doubles (device)
+    cudaStream_t stream;
+};
+
+inline const Coll<double> &coll_of(const Coll<double> &d, const Coll<float> &, double *) { return d; }
+inline const Coll<float> &coll_of(const Coll<double> &, const Coll<float> &f, float *) { return f; }
+
+// Cell-kernel operations of launch_cells.
+enum CellOp { CELL_INIT = 0, CELL_GET = 1, CELL_SET = 2, CELL_MACRO = 3 };
+
+// Entry points of the per-(stencil, storage) objects; storage 0 fp64, 1 fp32, 2 bf16-dev,
+// 3 fp16-dev.  sweep.cu defines launch_sweep_<Q>_<ST>; aux.cu the other three.
+#define LBM_DECLARE(Q, ST)                                                  \
+    cudaError_t launch_sweep_##Q##_##ST(const SweepArgs &s);                \
+    cudaError_t launch_fill_##Q##_##ST(const FillArgs &s);                  \
+    cudaError_t launch_cells_##Q##_##ST(int op, int force, const CellArgs &s); \
+    cudaError_t launch_reduce_##Q##_##ST(const ReduceArgs &s);
+LBM_DECLARE(19, 0)
+LBM_DECLARE(19, 1)
+LBM_DECLARE(19, 2)
+LBM_DECLARE(19, 3)
+LBM_DECLARE(27, 0)
+LBM_DECLARE(27, 1)
+LBM_DECLARE(27, 2)
+LBM_DECLARE(27, 3)
+#undef LBM_DECLARE
+
+}  // namespace lbm

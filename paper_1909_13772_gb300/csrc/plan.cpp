@@ -1,0 +1,352 @@
+// plan.cpp -- host-side list builder (see plan.hpp).
+#include "plan.hpp"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <tuple>
+
+#include "lattice.cuh"
+
+namespace lbm {
+
+void layout_blocks(std::vector<BlockLayout> &blocks, int bytes_per_pdf, int q, int align_bytes, int64_t *total_elems)
+{
+    int a = std::max(1, align_bytes / bytes_per_pdf);
+    int64_t off = 0;
+    for (auto &b : blocks) {
+        b.xo = a;
+        int need = a + b.n[0] + 1;
+        b.pitch = (need + a - 1) / a * a;
+        b.plane = (int64_t)b.pitch * (b.n[1] + 2);
+        b.slab = b.plane * (b.n[2] + 2);
+        b.offset = off;
+        off += (int64_t)q * b.slab;
+    }
+    *total_elems = off;
+}
+
+std::string check_blocks(const std::vector<BlockLayout> &blocks)
+{
+    if (blocks.empty()) return "no blocks";
+    if ((int64_t)blocks.size() > kMaxBlocks) return "too many blocks (max 65536)";
+    for (size_t i = 0; i < blocks.size(); ++i) {
+        const auto &b = blocks[i];
+        for (int a = 0; a < 3; ++a)
+            if (b.n[a] < 1 || b.n[a] > 32000) return "block size out of range [1, 32000]";
+        if (b.slab >= ((int64_t)1 << 32)) return "block too large (padded cells >= 2^32)";
+    }
+    // pairwise overlap test, sorted by x origin so the inner loop stops early
+    std::vector<int> order(blocks.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::sort(order.begin(), order.end(), [&](int p, int r) { return blocks[p].origin[0] < blocks[r].origin[0]; });
+    for (size_t ii = 0; ii < order.size(); ++ii) {
+        const auto &A = blocks[order[ii]];
+        for (size_t jj = ii + 1; jj < order.size(); ++jj) {
+            const auto &B = blocks[order[jj]];
+            if (B.origin[0] >= A.origin[0] + A.n[0]) break;
+            bool ov = true;
+            for (int a = 0; a < 3; ++a)
+                ov = ov && A.origin[a] < B.origin[a] + B.n[a] && B.origin[a] < A.origin[a] + A.n[a];
+            if (ov) return "blocks overlap";
+        }
+    }
+    return "";
+}
+
+namespace {
+
+struct Candidate {
+    int block;
+    int64_t shift[3];  // global offset added to the candidate's coordinates
+};
+
+struct Elem {
+    int64_t src, dst;
+};
+
+// Append one element copy to a run list, extending the last run when the element continues
+// it: along x (strides 1, 1) or along y (strides = the two blocks' row pitches).
+void append_run(std::vector<GhostRun> &runs, int64_t src, int64_t dst, int32_t spitch, int32_t dpitch)
+{
+    if (!runs.empty()) {
+        GhostRun &r = runs.back();
+        if (r.len == 1) {
+            int64_t ds = src - r.src, dd = dst - r.dst;
+            if ((ds == 1 && dd == 1) || (ds == spitch && dd == dpitch)) {
+                r.sstride = (int32_t)ds;
+                r.dstride = (int32_t)dd;
+                r.len = 2;
+                return;
+            }
+        } else if (src == r.src + (int64_t)r.len * r.sstride && dst == r.dst + (int64_t)r.len * r.dstride &&
+                   r.len < (1 << 30)) {
+            r.len += 1;
+            return;
+        }
+    }
+    runs.push_back(GhostRun{src, dst, 1, 1, 1, 0});
+}
+
+struct BlockOut {
+    std::vector<uint64_t> links[4];
+    std::vector<GhostRun> runs_pull, runs_aa;
+    int64_t slots_pull = 0, slots_aa = 0;
+    std::vector<Tile> tiles;
+    std::vector<uint8_t> mask;
+    int64_t cells = 0, fluid = 0;
+};
+
+}  // namespace
+
+std::string build_plan(const PlanInput &in, Plan &out)
+{
+    const auto &blocks = *in.blocks;
+    const auto &flags = *in.flags;
+    const int nb = (int)blocks.size();
+    const LatticeView L = lattice_view(in.q);
+
+    // domain bounding box
+    int64_t lo[3], hi[3], ext[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = blocks[0].origin[a];
+        hi[a] = blocks[0].origin[a] + blocks[0].n[a];
+        for (const auto &b : blocks) {
+            lo[a] = std::min(lo[a], b.origin[a]);
+            hi[a] = std::max(hi[a], b.origin[a] + (int64_t)b.n[a]);
+        }
+        ext[a] = hi[a] - lo[a];
+    }
+
+    // wall parameter table: faces first, then the distinct block parameter sets
+    out.params.assign(in.face_param, in.face_param + 6);
+    std::vector<int> bparam(nb, 0);
+    {
+        std::map<std::tuple<double, double, double, double>, int> seen;
+        for (int b = 0; b < nb; ++b) {
+            const WallParam &p = (*in.block_param)[b];
+            auto key = std::make_tuple(p.u[0], p.u[1], p.u[2], p.rho);
+            auto it = seen.find(key);
+            if (it == seen.end()) {
+                if ((int)out.params.size() >= kMaxParams) return "too many distinct wall parameter sets (max 506)";
+                it = seen.emplace(key, (int)out.params.size()).first;
+                out.params.push_back(p);
+            }
+            bparam[b] = it->second;
+        }
+    }
+
+    // neighbour candidates: blocks (possibly periodic images) overlapping the dilated box
+    std::vector<std::vector<Candidate>> cand(nb);
+    std::vector<int> order(nb);
+    for (int i = 0; i < nb; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int p, int r) { return blocks[p].origin[0] < blocks[r].origin[0]; });
+    std::vector<int64_t> ox(nb);
+    for (int i = 0; i < nb; ++i) ox[i] = blocks[order[i]].origin[0];
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < nb; ++b) {
+        const auto &B = blocks[b];
+        int64_t dlo[3], dhi[3];
+        for (int a = 0; a < 3; ++a) {
+            dlo[a] = B.origin[a] - 1;
+            dhi[a] = B.origin[a] + B.n[a] + 1;
+        }
+        int srange[3][2];
+        for (int a = 0; a < 3; ++a) {
+            srange[a][0] = (in.periodic[a] && dlo[a] < lo[a]) ? -1 : 0;
+            srange[a][1] = (in.periodic[a] && dhi[a] > hi[a]) ? 1 : 0;
+        }
+        for (int sz = srange[2][0]; sz <= srange[2][1]; ++sz)
+            for (int sy = srange[1][0]; sy <= srange[1][1]; ++sy)
+                for (int sx = srange[0][0]; sx <= srange[0][1]; ++sx) {
+                    int64_t sh[3] = {sx * ext[0], sy * ext[1], sz * ext[2]};
+                    // candidates need origin_x + sh_x < dhi_x and origin_x + n_x + sh_x > dlo_x
+                    for (int k = 0; k < nb; ++k) {
+                        if (ox[k] + sh[0] >= dhi[0]) break;
+                        int c = order[k];
+                        const auto &C = blocks[c];
+                        if (c == b && sx == 0 && sy == 0 && sz == 0) continue;
+                        bool ov = true;
+                        for (int a = 0; a < 3; ++a)
+                            ov = ov && C.origin[a] + sh[a] < dhi[a] && C.origin[a] + C.n[a] + sh[a] > dlo[a];
+                        if (ov) cand[b].push_back(Candidate{c, {sh[0], sh[1], sh[2]}});
+                    }
+                }
+    }
+
+    std::vector<BlockOut> bo(nb);
+    std::string err;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < nb; ++b) {
+        const auto &B = blocks[b];
+        const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+        const int px = nx + 2, py = ny + 2, pz = nz + 2;
+        const int64_t np = (int64_t)px * py * pz;
+        // local padded index p(x,y,z) = (x+1) + px ((y+1) + py (z+1))
+        auto pidx = [&](int x, int y, int z) { return (int64_t)(x + 1) + px * ((int64_t)(y + 1) + (int64_t)py * (z + 1)); };
+        std::vector<uint8_t> kind(np, 255);
+        std::vector<uint16_t> param(np, 0);
+        std::vector<int32_t> sblock(np, -1);
+        std::vector<int64_t> scell(np, 0);
+        const std::vector<uint8_t> &fl = flags[b];
+        BlockOut &o = bo[b];
+        bool has_solid = false;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    uint8_t k = fl.empty() ? (uint8_t)K_FLUID : fl[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)];
+                    int64_t p = pidx(x, y, z);
+                    kind[p] = k;
+                    param[p] = (uint16_t)bparam[b];
+                    if (k != K_FLUID) has_solid = true;
+                }
+        // shell cells covered by a (periodic image of a) block
+        for (const Candidate &cd : cand[b]) {
+            const auto &C = blocks[cd.block];
+            int64_t ilo[3], ihi[3];
+            bool empty = false;
+            for (int a = 0; a < 3; ++a) {
+                ilo[a] = std::max(B.origin[a] - 1, C.origin[a] + cd.shift[a]);
+                ihi[a] = std::min(B.origin[a] + B.n[a] + 1, C.origin[a] + C.n[a] + cd.shift[a]);
+                if (ilo[a] >= ihi[a]) empty = true;
+            }
+            if (empty) continue;
+            const std::vector<uint8_t> &cf = flags[cd.block];
+            for (int64_t gz = ilo[2]; gz < ihi[2]; ++gz)
+                for (int64_t gy = ilo[1]; gy < ihi[1]; ++gy)
+                    for (int64_t gx = ilo[0]; gx < ihi[0]; ++gx) {
+                        int lx = (int)(gx - B.origin[0]), ly = (int)(gy - B.origin[1]), lz = (int)(gz - B.origin[2]);
+                        if (lx >= 0 && lx < nx && ly >= 0 && ly < ny && lz >= 0 && lz < nz) continue;  // interior
+                        int cx = (int)(gx - cd.shift[0] - C.origin[0]);
+                        int cy = (int)(gy - cd.shift[1] - C.origin[1]);
+                        int cz = (int)(gz - cd.shift[2] - C.origin[2]);
+                        uint8_t k = cf.empty() ? (uint8_t)K_FLUID
+                                               : cf[(size_t)cx + (size_t)C.n[0] * ((size_t)cy + (size_t)C.n[1] * cz)];
+                        int64_t p = pidx(lx, ly, lz);
+                        if (k == K_FLUID) {
+                            kind[p] = K_MIRROR;
+                            sblock[p] = cd.block;
+                            scell[p] = C.cell(cx, cy, cz);
+                        } else {
+                            kind[p] = k;
+                            param[p] = (uint16_t)bparam[cd.block];
+                        }
+                    }
+        }
+        // remaining shell cells: outside the domain (face kind) or uncovered (no-slip)
+        for (int z = -1; z <= nz; ++z)
+            for (int y = -1; y <= ny; ++y)
+                for (int x = -1; x <= nx; ++x) {
+                    int64_t p = pidx(x, y, z);
+                    if (kind[p] != 255) continue;
+                    int64_t g[3] = {B.origin[0] + x, B.origin[1] + y, B.origin[2] + z};
+                    int face = -1;
+                    for (int a = 0; a < 3 && face < 0; ++a) {
+                        if (g[a] >= lo[a] && g[a] < hi[a]) continue;
+                        if (in.periodic[a]) continue;
+                        face = 2 * a + (g[a] < lo[a] ? 0 : 1);
+                    }
+                    if (face >= 0) {
+                        kind[p] = (uint8_t)in.face_kind[face];
+                        param[p] = (uint16_t)face;
+                    } else {
+                        kind[p] = K_NOSLIP;
+                        param[p] = 0;
+                    }
+                }
+        // links: fluid interior cell x, direction q with a boundary neighbour
+        for (int qd = 1; qd < L.q; ++qd) {
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) {
+                        if (kind[pidx(x, y, z)] != K_FLUID) continue;
+                        int64_t pn = pidx(x + L.cx[qd], y + L.cy[qd], z + L.cz[qd]);
+                        uint8_t k = kind[pn];
+                        if (k == K_NOSLIP || k == K_VELOCITY || k == K_PRESSURE)
+                            o.links[k].push_back(pack_link(qd, k, param[pn], b, B.cell(x, y, z)));
+                    }
+        }
+        // ghost runs: for each direction, shell cells mirroring a fluid cell, in (z, y, x) order
+        const int64_t base = B.offset;
+        for (int j = 0; j < L.q; ++j) {
+            for (int z = -1; z <= nz; ++z)
+                for (int y = -1; y <= ny; ++y)
+                    for (int x = -1; x <= nx; ++x) {
+                        bool shell = x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz;
+                        if (!shell) continue;
+                        int64_t p = pidx(x, y, z);
+                        if (kind[p] != K_MIRROR) continue;
+                        const auto &S = blocks[sblock[p]];
+                        int64_t src = S.offset + (int64_t)j * S.slab + scell[p];
+                        int64_t dst = base + (int64_t)j * B.slab + B.cell(x, y, z);
+                        // two-grid pull: interior fluid cell g + c_j reads slot j of g
+                        int ax = x + L.cx[j], ay = y + L.cy[j], az = z + L.cz[j];
+                        if (ax >= 0 && ax < nx && ay >= 0 && ay < ny && az >= 0 && az < nz &&
+                            kind[pidx(ax, ay, az)] == K_FLUID) {
+                            append_run(o.runs_pull, src, dst, S.pitch, B.pitch);
+                            o.slots_pull++;
+                        }
+                        // AA: interior fluid cell g - c_j reads (odd step) / writes (odd step) slot j of g
+                        int bx = x - L.cx[j], by = y - L.cy[j], bz = z - L.cz[j];
+                        if (bx >= 0 && bx < nx && by >= 0 && by < ny && bz >= 0 && bz < nz &&
+                            kind[pidx(bx, by, bz)] == K_FLUID) {
+                            append_run(o.runs_aa, src, dst, S.pitch, B.pitch);
+                            o.slots_aa++;
+                        }
+                    }
+        }
+        // mask and tiles
+        if (has_solid) {
+            o.mask.assign((size_t)B.slab, (uint8_t)255);
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) o.mask[(size_t)B.cell(x, y, z)] = kind[pidx(x, y, z)];
+        }
+        const int tx = in.tile[0], ty = in.tile[1], tz = in.tile[2];
+        for (int z0 = 0; z0 < nz; z0 += tz)
+            for (int y0 = 0; y0 < ny; y0 += ty)
+                for (int x0 = 0; x0 < nx; x0 += tx) {
+                    int64_t nfl = 0, ntot = 0;
+                    for (int z = z0; z < std::min(nz, z0 + tz); ++z)
+                        for (int y = y0; y < std::min(ny, y0 + ty); ++y)
+                            for (int x = x0; x < std::min(nx, x0 + tx); ++x) {
+                                ++ntot;
+                                nfl += kind[pidx(x, y, z)] == K_FLUID;
+                            }
+                    if (nfl == 0) continue;
+                    o.tiles.push_back(Tile{b, (int16_t)x0, (int16_t)y0, (int16_t)z0, (uint16_t)(nfl < ntot ? 1 : 0)});
+                }
+        o.cells = (int64_t)nx * ny * nz;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) o.fluid += kind[pidx(x, y, z)] == K_FLUID;
+    }
+    if (!err.empty()) return err;
+
+    out.links.clear();
+    out.runs_pull.clear();
+    out.runs_aa.clear();
+    out.tiles.clear();
+    out.masks.assign(nb, {});
+    out.cells = out.fluid_cells = 0;
+    out.ghost_slots_pull = out.ghost_slots_aa = 0;
+    for (int k = 0; k < 4; ++k) out.link_count[k] = 0;
+    for (int k = 1; k < 4; ++k)
+        for (int b = 0; b < nb; ++b) {
+            out.links.insert(out.links.end(), bo[b].links[k].begin(), bo[b].links[k].end());
+            out.link_count[k] += (int64_t)bo[b].links[k].size();
+        }
+    for (int b = 0; b < nb; ++b) {
+        out.runs_pull.insert(out.runs_pull.end(), bo[b].runs_pull.begin(), bo[b].runs_pull.end());
+        out.runs_aa.insert(out.runs_aa.end(), bo[b].runs_aa.begin(), bo[b].runs_aa.end());
+        out.ghost_slots_pull += bo[b].slots_pull;
+        out.ghost_slots_aa += bo[b].slots_aa;
+        out.tiles.insert(out.tiles.end(), bo[b].tiles.begin(), bo[b].tiles.end());
+        out.masks[b].swap(bo[b].mask);
+        out.cells += bo[b].cells;
+        out.fluid_cells += bo[b].fluid;
+    }
+    return "";
+}
+
+}  // namespace lbm

@@ -1,0 +1,103 @@
+// plan.hpp -- host-side block layout and the per-step work lists of the LBM sweep.
+//
+// Everything here is plain C++ on the host (no CUDA calls): it turns the block layout and the
+// flag fields into
+//   * the padded SoA layout of each block's PDF array (one ghost layer, aligned rows;
+//     Sec. 3.2 "Fields and sweeps": SoA layout, padding so that every line is aligned),
+//   * the boundary link lists, one entry per (fluid cell, direction) whose neighbour is a
+//     boundary cell, tagged with the boundary kind (Sec. 3.5: "a separate list ... for each
+//     boundary condition", handled by their own kernel),
+//   * the ghost-copy run lists between blocks on the same GPU and across periodic faces
+//     (Sec. 2.3 PackInfo local transfer; only the PDFs that cross into the block are copied),
+//   * the sweep tile list (which CTA sweeps which cells of which block).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace lbm {
+
+enum CellKind : uint8_t { K_FLUID = 0, K_NOSLIP = 1, K_VELOCITY = 2, K_PRESSURE = 3, K_PERIODIC = 4, K_MIRROR = 5 };
+
+struct WallParam {
+    double u[3];
+    double rho;
+};
+
+struct BlockLayout {
+    int64_t origin[3];
+    int32_t n[3];    // interior cells
+    int32_t xo;      // row index of interior x = 0 (ghost x = -1 sits at xo - 1)
+    int32_t pitch;   // elements per row
+    int64_t plane;   // pitch * (n[1] + 2)
+    int64_t slab;    // plane * (n[2] + 2): elements of one direction
+    int64_t offset;  // element offset of this block's array in the PDF arena
+    // cell index of interior/ghost coordinate (x, y, z), each in [-1, n]
+    int64_t cell(int x, int y, int z) const { return (int64_t)(z + 1) * plane + (int64_t)(y + 1) * pitch + xo + x; }
+};
+
+// One ghost-copy run: len elements, element k copied from arena[src + k*sstride] to
+// arena[dst + k*dstride] (offsets are relative to the base of the current PDF array).
+struct GhostRun {
+    int64_t src;
+    int64_t dst;
+    int32_t len;
+    int32_t sstride;
+    int32_t dstride;
+    int32_t pad;
+};
+
+// Sweep tile: x0, y0, z0 of a TX x TY x TZ box of one block; flags bit 0: tile has
+// non-fluid cells (the kernel reads the mask).
+struct Tile {
+    int32_t block;
+    int16_t x0, y0, z0;
+    uint16_t flags;
+};
+
+// Link word: bits 0-4 direction q (the link points from fluid cell x along c_q into a
+// boundary cell), 5-6 kind, 7-15 wall-parameter index, 16-31 block, 32-63 cell index of x
+// in the block's padded layout.
+inline uint64_t pack_link(int q, int kind, int param, int block, int64_t cell)
+{
+    return (uint64_t)q | ((uint64_t)kind << 5) | ((uint64_t)param << 7) | ((uint64_t)block << 16) |
+           ((uint64_t)cell << 32);
+}
+constexpr int kMaxParams = 512;
+constexpr int kMaxBlocks = 65536;
+
+struct PlanInput {
+    int q;
+    int bytes_per_pdf;
+    int periodic[3];
+    int face_kind[6];
+    WallParam face_param[6];
+    int tile[3];
+    std::vector<BlockLayout> const *blocks;
+    std::vector<std::vector<uint8_t>> const *flags;  // per block, interior, may be empty (all fluid)
+    std::vector<WallParam> const *block_param;       // per block
+};
+
+struct Plan {
+    std::vector<uint64_t> links;           // sorted by (kind, block, q, cell)
+    int64_t link_count[4] = {0, 0, 0, 0};  // by kind
+    std::vector<WallParam> params;         // wall parameter table (faces first)
+    std::vector<GhostRun> runs_pull;       // two-grid: slots j of ghost g with g + c_j fluid interior
+    std::vector<GhostRun> runs_aa;         // AA: slots j of ghost g with g - c_j fluid interior
+    int64_t ghost_slots_pull = 0, ghost_slots_aa = 0;
+    std::vector<Tile> tiles;
+    std::vector<std::vector<uint8_t>> masks;  // per block: padded-layout mask (0 fluid) or empty
+    int64_t cells = 0, fluid_cells = 0;
+};
+
+// Compute the padded layout of each block (alignment in bytes for rows).
+void layout_blocks(std::vector<BlockLayout> &blocks, int bytes_per_pdf, int q, int align_bytes, int64_t *total_elems);
+
+// Validate the layout (non-overlapping blocks); returns an empty string or an error.
+std::string check_blocks(const std::vector<BlockLayout> &blocks);
+
+// Build all lists.  Returns an empty string or an error.
+std::string build_plan(const PlanInput &in, Plan &out);
+
+}  // namespace lbm

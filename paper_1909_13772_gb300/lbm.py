@@ -1,0 +1,359 @@
+"""Python binding of liblbm.so (include/lbm.h): argument marshalling only.
+
+Every function of the C ABI is exposed under the same name; each raises ``LbmError`` on a
+non-zero status.  ``Simulation`` bundles a context with NumPy-friendly calls.  All compute
+runs in the library's CUDA kernels; there is no CPU fallback -- if the library cannot be
+built or loaded, importing the functions fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+D3Q19, D3Q27 = 19, 27
+SRT, TRT = 0, 1
+FP64, FP32, BF16_DEV, FP16_DEV = 0, 1, 2, 3
+TWO_GRID, AA = 0, 1
+FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
+
+STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_STATE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
+          5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_UNSUPPORTED"}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status, message=""):
+        self.status = status
+        super().__init__("%s: %s" % (STATUS.get(status, status), message))
+
+
+class lbm_params(ctypes.Structure):
+    _fields_ = [("stencil", ctypes.c_int32), ("collision", ctypes.c_int32), ("storage", ctypes.c_int32),
+                ("pattern", ctypes.c_int32), ("omega", ctypes.c_double), ("magic_lambda", ctypes.c_double),
+                ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("periodic", ctypes.c_int32 * 3),
+                ("diag_interval", ctypes.c_int32)]
+
+
+class lbm_block_desc(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_int64 * 3), ("size", ctypes.c_int32 * 3)]
+
+
+class lbm_diagnostics(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("momentum", ctypes.c_double * 3), ("kinetic_energy", ctypes.c_double),
+                ("max_speed", ctypes.c_double), ("nonfinite", ctypes.c_int64), ("fluid_cells", ctypes.c_int64)]
+
+
+class lbm_info(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("fluid_cells", ctypes.c_int64), ("links", ctypes.c_int64 * 4),
+                ("ghost_slots", ctypes.c_int64), ("ghost_runs", ctypes.c_int64), ("tiles", ctypes.c_int64),
+                ("bytes_per_pdf", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_P = ctypes.POINTER
+_vp, _dp, _u8p, _i32p, _i64p, _u64p = (ctypes.c_void_p, _P(ctypes.c_double), _P(ctypes.c_uint8),
+                                       _P(ctypes.c_int32), _P(ctypes.c_int64), _P(ctypes.c_uint64))
+_SIGS = {
+    "lbm_create_blocks": ([_P(lbm_params), _P(lbm_block_desc), ctypes.c_int32, _vp, _P(_vp)], ctypes.c_int),
+    "lbm_required_bytes": ([_vp], ctypes.c_size_t),
+    "lbm_bind_device_memory": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
+    "lbm_set_face": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dp, ctypes.c_double], ctypes.c_int),
+    "lbm_set_boundary": ([_vp, ctypes.c_int32, _u8p, _dp, ctypes.c_double], ctypes.c_int),
+    "lbm_init_macroscopic": ([_vp, ctypes.c_int32, _dp, _dp], ctypes.c_int),
+    "lbm_step": ([_vp, ctypes.c_int64], ctypes.c_int),
+    "lbm_get_macroscopic": ([_vp, ctypes.c_int32, _dp, _dp], ctypes.c_int),
+    "lbm_get_pdfs": ([_vp, ctypes.c_int32, _dp], ctypes.c_int),
+    "lbm_set_pdfs": ([_vp, ctypes.c_int32, _dp], ctypes.c_int),
+    "lbm_reduce": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
+    "lbm_get_info": ([_vp, _P(lbm_info)], ctypes.c_int),
+    "lbm_set_tile": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "lbm_kernel_launches": ([_vp], ctypes.c_int64),
+    "lbm_enable_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "lbm_read_timing": ([_vp, _dp, _i64p, ctypes.c_int32], ctypes.c_int),
+    "lbm_stencil_table": ([ctypes.c_int32, _i32p, _dp, _i32p], ctypes.c_int),
+    "lbm_plan_links": ([_vp, _u64p, ctypes.c_int64, _i64p], ctypes.c_int),
+    "lbm_plan_runs": ([_vp, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p], ctypes.c_int),
+    "lbm_plan_layout": ([_vp, ctypes.c_int32, _i64p], ctypes.c_int),
+    "lbm_plan_params": ([_vp, _dp, ctypes.c_int64, _i64p], ctypes.c_int),
+    "lbm_last_error": ([_vp], ctypes.c_char_p),
+    "lbm_destroy": ([_vp], None),
+}
+
+
+def library_path() -> str:
+    from . import build as _build
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load liblbm.so (building it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    path = _build.build() if build_if_missing else _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("liblbm.so not found at %s; run paper_1909_13772_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(_P(ctype)) if a is not None else None
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = load_library().lbm_last_error(ctx).decode() if ctx else ""
+        raise LbmError(status, msg)
+
+
+# ---- the C ABI under its own names ------------------------------------------------------
+
+def lbm_create_blocks(params: lbm_params, blocks, stream=None):
+    """blocks: sequence of (origin(3), size(3)).  Returns an opaque context handle."""
+    L = load_library()
+    arr = (lbm_block_desc * len(blocks))()
+    for k, (o, s) in enumerate(blocks):
+        for a in range(3):
+            arr[k].origin[a] = int(o[a])
+            arr[k].size[a] = int(s[a])
+    out = ctypes.c_void_p()
+    st = L.lbm_create_blocks(ctypes.byref(params), arr, len(blocks), ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    if st != 0:
+        raise LbmError(st, "lbm_create_blocks rejected the parameters or block layout")
+    return out
+
+
+def lbm_required_bytes(ctx) -> int:
+    return int(load_library().lbm_required_bytes(ctx))
+
+
+def lbm_bind_device_memory(ctx, dev_ptr: int, nbytes: int):
+    _check(ctx, load_library().lbm_bind_device_memory(ctx, ctypes.c_void_p(dev_ptr), nbytes))
+
+
+def lbm_set_face(ctx, axis, side, kind, u_wall=(0.0, 0.0, 0.0), rho_wall=1.0):
+    u = _arr(u_wall, np.float64)
+    _check(ctx, load_library().lbm_set_face(ctx, axis, side, kind, _ptr(u, ctypes.c_double), float(rho_wall)))
+
+
+def lbm_set_boundary(ctx, block, flags, u_wall=(0.0, 0.0, 0.0), rho_wall=1.0):
+    f = None if flags is None else _arr(flags, np.uint8)
+    u = _arr(u_wall, np.float64)
+    _check(ctx, load_library().lbm_set_boundary(ctx, block, _ptr(f, ctypes.c_uint8), _ptr(u, ctypes.c_double),
+                                                float(rho_wall)))
+
+
+def lbm_init_macroscopic(ctx, block, rho, u):
+    r = _arr(rho, np.float64)
+    v = _arr(u, np.float64)
+    _check(ctx, load_library().lbm_init_macroscopic(ctx, block, _ptr(r, ctypes.c_double), _ptr(v, ctypes.c_double)))
+
+
+def lbm_step(ctx, n: int = 1):
+    _check(ctx, load_library().lbm_step(ctx, int(n)))
+
+
+def lbm_get_macroscopic(ctx, block, rho_out, u_out):
+    _check(ctx, load_library().lbm_get_macroscopic(ctx, block, _ptr(rho_out, ctypes.c_double),
+                                                   _ptr(u_out, ctypes.c_double)))
+
+
+def lbm_get_pdfs(ctx, block, f_out):
+    _check(ctx, load_library().lbm_get_pdfs(ctx, block, _ptr(f_out, ctypes.c_double)))
+
+
+def lbm_set_pdfs(ctx, block, f):
+    a = _arr(f, np.float64)
+    _check(ctx, load_library().lbm_set_pdfs(ctx, block, _ptr(a, ctypes.c_double)))
+
+
+def lbm_reduce(ctx) -> dict:
+    d = lbm_diagnostics()
+    _check(ctx, load_library().lbm_reduce(ctx, ctypes.byref(d)))
+    return {"mass": d.mass, "momentum": tuple(d.momentum), "kinetic_energy": d.kinetic_energy,
+            "max_speed": d.max_speed, "nonfinite": d.nonfinite, "fluid_cells": d.fluid_cells}
+
+
+def lbm_get_info(ctx) -> dict:
+    i = lbm_info()
+    _check(ctx, load_library().lbm_get_info(ctx, ctypes.byref(i)))
+    return {"cells": i.cells, "fluid_cells": i.fluid_cells, "links": tuple(i.links), "ghost_slots": i.ghost_slots,
+            "ghost_runs": i.ghost_runs, "tiles": i.tiles, "bytes_per_pdf": i.bytes_per_pdf,
+            "device_bytes": i.device_bytes}
+
+
+def lbm_set_tile(ctx, tx, ty, tz):
+    _check(ctx, load_library().lbm_set_tile(ctx, tx, ty, tz))
+
+
+def lbm_kernel_launches(ctx) -> int:
+    return int(load_library().lbm_kernel_launches(ctx))
+
+
+def lbm_enable_timing(ctx, enable=True):
+    _check(ctx, load_library().lbm_enable_timing(ctx, 1 if enable else 0))
+
+
+def lbm_read_timing(ctx, reset=True) -> dict:
+    """{'fill': (ms, launches), 'sweep': (ms, launches)} summed since the last reset."""
+    ms = np.zeros(2, dtype=np.float64)
+    cnt = np.zeros(2, dtype=np.int64)
+    _check(ctx, load_library().lbm_read_timing(ctx, _ptr(ms, ctypes.c_double), _ptr(cnt, ctypes.c_int64),
+                                               1 if reset else 0))
+    return {"fill": (float(ms[0]), int(cnt[0])), "sweep": (float(ms[1]), int(cnt[1]))}
+
+
+def lbm_stencil_table(q: int):
+    c = np.zeros(3 * q, dtype=np.int32)
+    w = np.zeros(q, dtype=np.float64)
+    opp = np.zeros(q, dtype=np.int32)
+    st = load_library().lbm_stencil_table(q, _ptr(c, ctypes.c_int32), _ptr(w, ctypes.c_double),
+                                          _ptr(opp, ctypes.c_int32))
+    if st != 0:
+        raise LbmError(st, "unknown stencil %d" % q)
+    return c.reshape(q, 3), w, opp
+
+
+def lbm_plan_links(ctx) -> np.ndarray:
+    L = load_library()
+    n = ctypes.c_int64()
+    _check(ctx, L.lbm_plan_links(ctx, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.uint64)
+    _check(ctx, L.lbm_plan_links(ctx, _ptr(out, ctypes.c_uint64), n.value, ctypes.byref(n)))
+    return out
+
+
+def lbm_plan_runs(ctx, pattern) -> np.ndarray:
+    L = load_library()
+    n = ctypes.c_int64()
+    _check(ctx, L.lbm_plan_runs(ctx, pattern, None, 0, ctypes.byref(n)))
+    out = np.zeros(5 * n.value, dtype=np.int64)
+    _check(ctx, L.lbm_plan_runs(ctx, pattern, _ptr(out, ctypes.c_int64), 5 * n.value, ctypes.byref(n)))
+    return out.reshape(n.value, 5)
+
+
+def lbm_plan_layout(ctx, block) -> dict:
+    out = np.zeros(9, dtype=np.int64)
+    _check(ctx, load_library().lbm_plan_layout(ctx, block, _ptr(out, ctypes.c_int64)))
+    keys = ("xo", "pitch", "plane", "slab", "offset", "nx", "ny", "nz", "arena_elems")
+    return {k: int(v) for k, v in zip(keys, out)}
+
+
+def lbm_plan_params(ctx) -> np.ndarray:
+    L = load_library()
+    n = ctypes.c_int64()
+    _check(ctx, L.lbm_plan_params(ctx, None, 0, ctypes.byref(n)))
+    out = np.zeros(4 * n.value, dtype=np.float64)
+    _check(ctx, L.lbm_plan_params(ctx, _ptr(out, ctypes.c_double), 4 * n.value, ctypes.byref(n)))
+    return out.reshape(n.value, 4)
+
+
+def lbm_last_error(ctx) -> str:
+    return load_library().lbm_last_error(ctx).decode()
+
+
+def lbm_destroy(ctx):
+    load_library().lbm_destroy(ctx)
+
+
+# ---- convenience wrapper ----------------------------------------------------------------
+
+def make_params(stencil=D3Q19, collision=TRT, storage=FP32, pattern=TWO_GRID, omega=1.0, magic_lambda=3.0 / 16.0,
+                force=(0.0, 0.0, 0.0), rho0=1.0, periodic=(1, 1, 1), diag_interval=0) -> lbm_params:
+    p = lbm_params()
+    p.stencil, p.collision, p.storage, p.pattern = stencil, collision, storage, pattern
+    p.omega, p.magic_lambda, p.rho0 = float(omega), float(magic_lambda), float(rho0)
+    for a in range(3):
+        p.force[a] = float(force[a])
+        p.periodic[a] = int(bool(periodic[a]))
+    p.diag_interval = int(diag_interval)
+    return p
+
+
+class Simulation:
+    """A context plus NumPy marshalling.  Per-block host arrays are [z, y, x] (scalars),
+    [3, z, y, x] (velocity) and [q, z, y, x] (PDFs)."""
+
+    def __init__(self, params: lbm_params, blocks, stream=None, device_buffer=None):
+        self.params = params
+        self.q = params.stencil
+        self.blocks = [(tuple(int(v) for v in o), tuple(int(v) for v in s)) for o, s in blocks]
+        self.ctx = lbm_create_blocks(params, self.blocks, stream)
+        self._buffer = device_buffer
+        if device_buffer is not None:
+            lbm_bind_device_memory(self.ctx, device_buffer.data_ptr(), device_buffer.numel() * device_buffer.element_size())
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def shape(self, b):
+        nx, ny, nz = self.blocks[b][1]
+        return nz, ny, nx
+
+    def set_face(self, axis, side, kind, u_wall=(0.0, 0.0, 0.0), rho_wall=1.0):
+        lbm_set_face(self.ctx, axis, side, kind, u_wall, rho_wall)
+
+    def set_boundary(self, b, flags, u_wall=(0.0, 0.0, 0.0), rho_wall=1.0):
+        if flags is not None and np.asarray(flags).shape != self.shape(b):
+            raise ValueError("flags of block %d must have shape %s" % (b, self.shape(b)))
+        lbm_set_boundary(self.ctx, b, flags, u_wall, rho_wall)
+
+    def init(self, b, rho, u):
+        nz, ny, nx = self.shape(b)
+        lbm_init_macroscopic(self.ctx, b, np.broadcast_to(rho, (nz, ny, nx)),
+                             np.broadcast_to(u, (3, nz, ny, nx)))
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def macroscopic(self, b):
+        nz, ny, nx = self.shape(b)
+        rho = np.zeros((nz, ny, nx))
+        u = np.zeros((3, nz, ny, nx))
+        lbm_get_macroscopic(self.ctx, b, rho, u)
+        return rho, u
+
+    def pdfs(self, b):
+        nz, ny, nx = self.shape(b)
+        f = np.zeros((self.q, nz, ny, nx))
+        lbm_get_pdfs(self.ctx, b, f)
+        return f
+
+    def set_pdfs(self, b, f):
+        lbm_set_pdfs(self.ctx, b, f)
+
+    def reduce(self):
+        return lbm_reduce(self.ctx)
+
+    def info(self):
+        return lbm_get_info(self.ctx)
+
+    def set_tile(self, tx, ty, tz):
+        lbm_set_tile(self.ctx, tx, ty, tz)
+
+    def launches(self):
+        return lbm_kernel_launches(self.ctx)

@@ -1,0 +1,244 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.  Gate: normwise max relative PDF error <= 1e-12 (FP64 storage) and <= 1e-5 (FP32
+storage), max_x,i |gpu - oracle| / max_x,i |oracle| over fluid cells.  Sizes span several
+sweep tiles plus a ragged tail in every axis."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import TOL, Case, gather_macro, gather_pdfs, init_sim, normwise, oracle_run
+from paper_1909_13772_gb300 import inputs, lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm.load_library()
+
+
+def _compare(case, rho, u, steps, tol=None):
+    sim = case.make_sim()
+    init_sim(sim, rho, u)
+    sim.step(steps)
+    got = gather_pdfs(sim, case)
+    _, want = oracle_run(case, rho, u, steps)
+    fl = case.global_flags() == 0
+    err = normwise(got, want, fl)
+    sim.close()
+    assert err <= (tol or TOL[case.storage]), err
+    return got, want, err
+
+
+# ---- C1: Taylor-Green vortex, D3Q19 SRT, 32^3, FP64, 100 steps ---------------------------
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+def test_taylor_green_fp64_matches_oracle_and_decay(pattern):
+    n, tau, steps = 32, 0.6, 100
+    case = Case(shape=(n, n, n), q=19, collision=lbm.SRT, storage=lbm.FP64, pattern=pattern, omega=1 / tau)
+    rho, u = inputs.taylor_green(n, u0=0.01)
+    sim = case.make_sim()
+    init_sim(sim, rho, u)
+    sim.step(20)
+    v20 = gather_macro(sim, case)[1]
+    sim.step(steps - 20)
+    got = gather_pdfs(sim, case)
+    v100 = gather_macro(sim, case)[1]
+    sim.close()
+    _, want = oracle_run(case, rho, u, steps)
+    assert normwise(got, want) <= 1e-12
+    k = 2 * math.pi / n
+    X, Y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    mode = np.cos(k * X) * np.sin(k * Y)
+    amp = lambda v: (v[0] * mode[None]).sum() / (mode * mode).sum() / n  # noqa: E731
+    rate = -math.log(amp(v100) / amp(v20)) / (steps - 20)
+    nu = (tau - 0.5) / 3
+    assert abs(rate / (2 * nu * k * k) - 1) < 5e-3
+
+
+# ---- channel with walls and body force (C2 family), several tiles + ragged tails -----------
+@pytest.mark.parametrize("storage", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+@pytest.mark.parametrize("q", [19, 27])
+def test_channel_trt_force(storage, pattern, q):
+    shape = (70, 37, 11)
+    case = Case(shape=shape, q=q, collision=lbm.TRT, storage=storage, pattern=pattern, omega=1.0,
+                force=(1e-5, 0.0, 0.0), periodic=(1, 0, 1), faces=(1, 1, lbm.NOSLIP, lbm.NOSLIP, 1, 1))
+    rho, u = inputs.random_state(shape, seed=21, rho_amp=0.02, u_amp=0.03)
+    _compare(case, rho, u, 40)
+
+
+@pytest.mark.parametrize("storage", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("collision", [lbm.SRT, lbm.TRT])
+def test_periodic_random_state(storage, collision):
+    shape = (45, 19, 13)
+    case = Case(shape=shape, q=27, collision=collision, storage=storage, omega=1.7, magic_lambda=0.25,
+                force=(2e-6, -1e-6, 3e-6))
+    rho, u = inputs.random_state(shape, seed=5)
+    _compare(case, rho, u, 30)
+
+
+def _porous_case(storage, pattern, q=19):
+    """Uneven multi-block layout, spheres, velocity inlet at x-, pressure outlet at x+."""
+    blocks, shape, _ = inputs.rectilinear_blocks(nb=(3, 2, 2), lo=9, hi=21, seed=4)
+    flags = inputs.sphere_packing(shape, radius=3.0, porosity=0.6, seed=7, buffer=4.0)
+    return Case(shape=shape, blocks=blocks, q=q, collision=lbm.TRT, storage=storage, pattern=pattern, omega=1 / 0.8,
+                periodic=(0, 1, 1), faces=(lbm.VELOCITY, lbm.PRESSURE, 1, 1, 1, 1),
+                face_u=((0.02, 0.0, 0.0),) + ((0.0, 0.0, 0.0),) * 5, face_rho=(1.0,) * 6, flags=flags)
+
+
+@pytest.mark.parametrize("storage", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+def test_porous_multiblock(storage, pattern):
+    case = _porous_case(storage, pattern)
+    rho, u = inputs.rest(case.shape)
+    _compare(case, rho, u, 60)
+
+
+def test_porous_multiblock_d3q27():
+    case = _porous_case(lbm.FP64, lbm.AA, q=27)
+    rho, u = inputs.rest(case.shape)
+    _compare(case, rho, u, 25)
+
+
+# ---- pure streaming: omega = 0 and F = 0 make lbm_step a permutation -- bitwise ----------
+@pytest.mark.parametrize("storage", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+@pytest.mark.parametrize("q", [19, 27])
+def test_pure_streaming_bitwise(storage, pattern, q):
+    case = _porous_case(storage, pattern, q=q)
+    case.collision = lbm.SRT
+    case.omega = 0.0
+    case.faces = (lbm.NOSLIP, lbm.NOSLIP, 1, 1, 1, 1)
+    nx, ny, nz = case.shape
+    fl = case.global_flags() == 0
+    rng = np.random.default_rng(3)
+    f0 = rng.random((q, nz, ny, nx))
+    if storage == lbm.FP32:
+        f0 = f0.astype(np.float32).astype(np.float64)
+    f0[:, ~fl] = 0.0
+    sim = case.make_sim()
+    for b, (o, s) in enumerate(sim.blocks):
+        sim.set_pdfs(b, f0[:, o[2]:o[2] + s[2], o[1]:o[1] + s[1], o[0]:o[0] + s[0]])
+    sim.step(3)
+    got = gather_pdfs(sim, case)
+    sim.close()
+    want = oracle.run(case.oracle_params(), f0, 3, flags=case.global_flags())
+    np.testing.assert_array_equal(got[:, fl], want[:, fl])
+
+
+# ---- checkpoint / restart and determinism ------------------------------------------------
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+@pytest.mark.parametrize("split_at", [4, 5])
+def test_checkpoint_restart_bitwise(pattern, split_at):
+    case = _porous_case(lbm.FP32, pattern)
+    rho, u = inputs.random_state(case.shape, seed=9, rho_amp=0.01, u_amp=0.01)
+    a = case.make_sim()
+    init_sim(a, rho, u)
+    a.step(10)
+    want = gather_pdfs(a, case)
+    a.close()
+    b = case.make_sim()
+    init_sim(b, rho, u)
+    b.step(split_at)
+    saved = [b.pdfs(k) for k in range(len(b.blocks))]
+    b.close()
+    c = case.make_sim()
+    for k, f in enumerate(saved):
+        c.set_pdfs(k, f)
+    c.step(10 - split_at)
+    got = gather_pdfs(c, case)
+    c.close()
+    np.testing.assert_array_equal(got, want)
+
+
+def test_aa_equals_two_grid():
+    base = _porous_case(lbm.FP64, lbm.TWO_GRID)
+    rho, u = inputs.rest(base.shape)
+    out = []
+    for pattern in (lbm.TWO_GRID, lbm.AA):
+        base.pattern = pattern
+        s = base.make_sim()
+        init_sim(s, rho, u)
+        s.step(7)
+        out.append(gather_pdfs(s, base))
+        s.close()
+    assert normwise(out[1], out[0], base.global_flags() == 0) <= 1e-14
+
+
+def test_tile_shape_does_not_change_results():
+    case = Case(shape=(70, 21, 9), q=19, storage=lbm.FP32, force=(1e-5, 0, 0), periodic=(1, 0, 1),
+                faces=(1, 1, lbm.NOSLIP, lbm.NOSLIP, 1, 1))
+    rho, u = inputs.random_state(case.shape, seed=2, rho_amp=0.01, u_amp=0.02)
+    res = []
+    for tile in ((32, 1, 1), (64, 4, 4), (128, 2, 3), (256, 1, 8)):
+        case.tile = tile
+        s = case.make_sim()
+        init_sim(s, rho, u)
+        s.step(12)
+        res.append(gather_pdfs(s, case))
+        s.close()
+    for r in res[1:]:
+        np.testing.assert_array_equal(r, res[0])
+
+
+# ---- reductions and failure detection ----------------------------------------------------
+def test_reduction_matches_oracle_and_is_deterministic():
+    case = _porous_case(lbm.FP64, lbm.TWO_GRID)
+    rho, u = inputs.random_state(case.shape, seed=12, rho_amp=0.02, u_amp=0.02)
+    s = case.make_sim()
+    init_sim(s, rho, u)
+    s.step(5)
+    d1, d2 = s.reduce(), s.reduce()
+    s.close()
+    assert d1 == d2
+    _, f = oracle_run(case, rho, u, 5)
+    want = oracle.diagnostics(case.oracle_params(), f, case.global_flags())
+    assert abs(d1["mass"] / want["mass"] - 1) < 1e-13
+    np.testing.assert_allclose(d1["momentum"], want["momentum"], rtol=1e-10, atol=1e-14)
+    assert abs(d1["kinetic_energy"] / want["kinetic_energy"] - 1) < 1e-10
+    assert abs(d1["max_speed"] / want["max_speed"] - 1) < 1e-10
+    assert d1["nonfinite"] == 0
+    assert d1["fluid_cells"] == int((case.global_flags() == 0).sum())
+
+
+def test_divergence_is_reported():
+    case = Case(shape=(40, 9, 6), storage=lbm.FP32)
+    p = lbm.make_params(stencil=19, storage=lbm.FP32, omega=1.2, diag_interval=2)
+    sim = lbm.Simulation(p, case.block_list())
+    rho, u = inputs.rest(case.shape)
+    sim.init(0, rho, u)
+    sim.step(2)
+    f = sim.pdfs(0)
+    f[3, 2, 4, 7] = np.nan
+    sim.set_pdfs(0, f)
+    with pytest.raises(lbm.LbmError) as e:
+        sim.step(4)
+    assert e.value.status == 5
+    assert sim.reduce()["nonfinite"] >= 1
+    sim.close()
+
+
+def test_bound_torch_buffer_and_stream():
+    import torch
+    case = Case(shape=(33, 10, 7), storage=lbm.FP32, pattern=lbm.AA)
+    p = lbm.make_params(stencil=19, storage=lbm.FP32, pattern=lbm.AA, omega=1.3)
+    stream = torch.cuda.Stream()
+    probe = lbm.Simulation(p, case.block_list())
+    need = lbm.lbm_required_bytes(probe.ctx)
+    probe.close()
+    buf = torch.empty(need, dtype=torch.uint8, device="cuda")
+    sim = lbm.Simulation(p, case.block_list(), stream=stream.cuda_stream, device_buffer=buf)
+    rho, u = inputs.random_state(case.shape, seed=4, rho_amp=0.01, u_amp=0.01)
+    sim.init(0, rho, u)
+    sim.step(6)
+    got = sim.pdfs(0)
+    assert sim.launches() == 12
+    sim.close()
+    case.omega = 1.3
+    _, want = oracle_run(case, rho, u, 6)
+    assert normwise(got, want) <= 1e-5
