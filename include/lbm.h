@@ -3,19 +3,19 @@
  *
  * The library runs the hot path of the block-structured lattice Boltzmann method described
  * in the waLBerla paper (arXiv:1909.13772) on one GPU:
- *   - the fused stream-collide sweep (Sec. 4.1, Eq. 1-2; Sec. 4.1.2 "stream and collision
- *     step is fused"), D3Q19 or D3Q27, SRT or TRT collision (Eq. 3 with special S), Guo
- *     body force (Sec. 4.1 body-force paragraph);
- *   - structure-of-arrays PDF fields with one ghost layer per block (Sec. 3.1 "Structured
- *     grids", Sec. 3.2 "Fields and sweeps": SoA layout, padded aligned rows);
+ *   - the fused stream-collide sweep (Sec. 5.1.1, Eq. 1-2; Sec. 5.1.2: streaming and
+ *     collision fused in one kernel), D3Q19 or D3Q27, SRT or TRT collision (Eq. 3 with
+ *     special S), Guo body force (Sec. 5.1.1, body-force paragraph);
+ *   - structure-of-arrays PDF fields with one ghost layer per block (Sec. 4.1 structured
+ *     grids; Sec. 4.2 fields: SoA layout, padded aligned rows);
  *   - boundary sweeps driven by per-kind boundary link lists built from flag fields
- *     (Sec. 3.5: "a separate list ... for each boundary condition", no-slip, velocity,
- *     pressure; Sec. 4.1 boundary paragraph), plus periodic domain faces;
- *   - the ghost-layer copy between blocks held on the same GPU (Sec. 2.3 PackInfo "local
- *     transfer without intermediate buffers"; Sec. 3.2 "ghost layer exchange before or after
- *     the kernel call");
- *   - device compute with host mirrors only for set-up and output (Sec. 3.3 GPU support).
- * The paper states its kernels are callable through a C ABI (Sec. 5.1 code generation);
+ *     (Sec. 4.4: one index list per boundary condition, each with its own kernel; no-slip,
+ *     velocity and pressure kinds from Sec. 5.1.1), plus periodic domain faces;
+ *   - the ghost-layer copy between blocks held on the same GPU (Sec. 3.3: PackInfo copies
+ *     directly between blocks of one process, without buffers; Sec. 4.2: ghost layers are
+ *     exchanged between sweeps);
+ *   - device compute with host mirrors only for set-up and output (Sec. 4.3).
+ * The paper states its kernels are callable through a C ABI (Sec. 6.1 on code generation);
  * this header is that interface for this library.
  *
  * Conventions

@@ -5,19 +5,20 @@
  * file; only the test suite, the smoke check and the CPU-baseline leg of the benchmark load
  * it.  It shares no code, header or table with the CUDA path.
  *
- * What it computes (waLBerla paper, Sec. 4.1 "Lattice Boltzmann method"):
+ * What it computes (waLBerla paper, Sec. 5.1, lattice Boltzmann method):
  *   - Eq. 1: density and momentum density are the zeroth and first moments of the PDFs.
  *   - Eq. 2: f_i(x + c_i, t + 1) = f_i(x, t) + Omega_i(f(x, t)): collide, then push each
  *     post-collision PDF to the neighbour it points at.
  *   - Eq. 3 with the special relaxation matrices named right after it: SRT (one rate) and
  *     TRT (one rate for the even part, one for the odd part of each direction pair).
- *   - Sec. 4.1 body-force paragraph: a constant body force drives periodic set-ups; the
+ *   - Sec. 5.1.1, body-force paragraph: a constant body force drives periodic set-ups; the
  *     force model is Guo et al. (the paper cites it), split into even/odd parts under TRT.
- *   - Sec. 4.1 boundary paragraph: no-slip, velocity and pressure boundaries.  The paper
+ *   - Sec. 5.1.1, boundary paragraph: no-slip, velocity and pressure boundaries.  The paper
  *     cites Ginzburg 2008 for them; the oracle takes halfway bounce-back (no-slip),
  *     bounce-back with a wall-velocity term (velocity) and anti-bounce-back (pressure).
- *   - Sec. 3.5: boundary handling driven by a per-cell flag field (the "straightforward
- *     way" of the paper).  The CUDA path uses the per-kind link lists instead.
+ *   - Sec. 4.4: boundary handling by iterating over all cells and reading a per-cell flag
+ *     field, the simple method the paper describes first.  The CUDA path uses the
+ *     per-kind link lists instead.
  * The paper fixes none of the constants of these operators; the reading adopted for each
  * one is stated next to the code below.
  *
@@ -62,7 +63,7 @@ typedef struct {
 } orc_params;
 
 /* ---------------------------------------------------------------------------------------
- * Lattice.  The paper names D3Q19 and D3Q27 (Sec. 4.1) but prints no table.  The oracle
+ * Lattice.  The paper names D3Q19 and D3Q27 (Sec. 5.1.1) but prints no table.  The oracle
  * enumerates the velocity set from its definition: all c in {-1,0,1}^3 with |c|^2 <= 2
  * (D3Q19) or <= 3 (D3Q27), ordered by |c|^2 first; within |c|^2 = 1 the order is
  * +x,-x,+y,-y,+z,-z; within |c|^2 = 2 and 3 it is lexicographic in (cx,cy,cz).  Weights are

@@ -4,7 +4,7 @@ Written separately from ``lbm_oracle.c`` (vectorised NumPy, lattice built with i
 moment sums as matrix products) so that a slip in either one (a dropped term, a wrong sign,
 a transposed operand) shows up when the two are compared on random cells.
 
-Formulas (waLBerla paper, Sec. 4.1, Eq. 1-3; constants as read in the oracle):
+Formulas (waLBerla paper, Sec. 5.1, Eq. 1-3; constants as read in the oracle):
   rho = sum f,  u = (sum c f + F/2) / rho
   feq = w rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 |u|^2)
   S   = w (3 (c - u) + 9 (c.u) c) . F

@@ -2,8 +2,8 @@
 // scheduler.  Every step runs on the context's stream as two launches:
 //   two-grid:  fill(links + ghost runs into src) -> pull sweep src -> dst, swap
 //   AA:        fill(E) -> neighbour sweep  |  fill(O) -> local sweep   (alternating)
-// (Sec. 3.2: "a ghost layer exchange before or after the kernel call"; Sec. 3.5 boundary
-// lists handled by their own kernel; Sec. 4.1.2 fused stream-collide sweep.)
+// (Sec. 4.2: "a ghost layer exchange before or after the kernel call"; Sec. 4.4 boundary
+// lists handled by their own kernel; Sec. 5.1.2 fused stream-collide sweep.)
 #include <cuda_runtime.h>
 
 #include <cmath>

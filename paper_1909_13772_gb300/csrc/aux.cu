@@ -23,7 +23,7 @@ __device__ __forceinline__ int64_t slot(int layout, int i, int64_t cell, const D
 }
 
 // ---------------------------------------------------------------------------------------
-// Boundary links and ghost copies (one launch; Sec. 3.5 boundary lists, Sec. 2.3 local
+// Boundary links and ghost copies (one launch; Sec. 4.4 boundary lists, Sec. 3.3 local
 // ghost transfer).  For a link (x, q) the outgoing post-collision PDF v = f*_q(x) hits the
 // boundary halfway to x + c_q and comes back as the incoming f_opp(q)(x, t+1):
 //   no-slip  : v

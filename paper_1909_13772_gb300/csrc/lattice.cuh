@@ -1,6 +1,6 @@
 // lattice.cuh -- D3Q19 / D3Q27 velocity sets for the CUDA path (host and device).
 //
-// The paper names both stencils (Sec. 4.1, "Overview") without printing a table.  These are
+// The paper names both stencils (Sec. 5.1.1) without printing a table.  These are
 // the standard tables (c_s^2 = 1/3) in the library's canonical order: rest; +x -x +y -y +z -z;
 // the 12 |c|^2 = 2 vectors in lexicographic (cx, cy, cz) order; for D3Q27 the 8 corners in
 // lexicographic order.  Opposite pairs: (1,2) (3,4) (5,6), edges i <-> 25 - i, corners

@@ -3,12 +3,12 @@
 // Everything here is plain C++ on the host (no CUDA calls): it turns the block layout and the
 // flag fields into
 //   * the padded SoA layout of each block's PDF array (one ghost layer, aligned rows;
-//     Sec. 3.2 "Fields and sweeps": SoA layout, padding so that every line is aligned),
+//     Sec. 4.2: SoA layout, each line padded so the next one starts aligned),
 //   * the boundary link lists, one entry per (fluid cell, direction) whose neighbour is a
-//     boundary cell, tagged with the boundary kind (Sec. 3.5: "a separate list ... for each
-//     boundary condition", handled by their own kernel),
+//     boundary cell, tagged with the boundary kind (Sec. 4.4: one index list per boundary
+//     condition, each treated by its own kernel),
 //   * the ghost-copy run lists between blocks on the same GPU and across periodic faces
-//     (Sec. 2.3 PackInfo local transfer; only the PDFs that cross into the block are copied),
+//     (Sec. 3.3 PackInfo local transfer; only the PDFs that cross into the block are copied),
 //   * the sweep tile list (which CTA sweeps which cells of which block).
 #pragma once
 

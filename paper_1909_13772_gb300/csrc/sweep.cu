@@ -4,7 +4,7 @@
 // bf16-deviation, fp16-deviation).  Each object defines launch_sweep_<Q>_<ST>.
 //
 // Method: Eq. 2 of the paper with the stream and collision steps fused into one pass over
-// the cells (Sec. 4.1.2), pull form: each cell gathers the PDFs streaming into it, collides
+// the cells (Sec. 5.1.2), pull form: each cell gathers the PDFs streaming into it, collides
 // them (SRT/TRT with Guo force, kernels.cuh) and writes its post-collision PDFs.
 //   two-grid pull : f_i <- src[x - c_i][i];  collide;  dst[x][i] <- f*_i
 //   AA local      : f_i <- A[x][i];          collide;  A[x][opp i] <- f*_i

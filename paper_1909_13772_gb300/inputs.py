@@ -5,7 +5,7 @@ velocity fields, flag fields and block layouts that both the CUDA path and the o
 as input.  Every generator is deterministic in its arguments (NumPy ``default_rng(seed)``).
 
 Workloads (the paper's own geometries -- artery tree, vocal fold, crystal filter and the
-porous beds of Sec. 4.1.3 -- are not available; these stand in for them):
+porous beds of Sec. 5.1.3 -- are not available; these stand in for them):
   * ``taylor_green``   2-D Taylor-Green vortex extruded in z (decays as exp(-2 nu k^2 t)).
   * ``rest``           uniform density, zero velocity (body-force-driven channel start).
   * ``turbulence``     random-phase solenoidal field with E(k) ~ k^(-5/3).

@@ -1,6 +1,6 @@
 """Pins for the oracle's single-cell collision (CPU only).
 
-What the method fixes (Sec. 4.1, Eq. 1-3, SRT/TRT as special cases of Eq. 3, Guo forcing):
+What the method fixes (Sec. 5.1, Eq. 1-3, SRT/TRT as special cases of Eq. 3, Guo forcing):
   * the equilibrium is a fixed point of the collision without force;
   * the collision conserves mass exactly and adds exactly F to the momentum;
   * TRT with omega- = omega+ is SRT;

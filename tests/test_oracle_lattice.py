@@ -1,7 +1,7 @@
 """Pins for the oracle's lattice and equilibrium (CPU only).
 
 The lattice must satisfy the exact isotropy identities that make the method recover the
-Navier-Stokes equations with c_s^2 = 1/3 (Sec. 4.1 names the stencils; the identities are
+Navier-Stokes equations with c_s^2 = 1/3 (Sec. 5.1 names the stencils; the identities are
 the mathematics), and must equal the hand-typed canonical tables in tests/golden/.
 """
 from fractions import Fraction
