@@ -214,6 +214,31 @@ lbm_status lbm_plan_layout(lbm_ctx *ctx, int32_t block, int64_t out[9]);
 /* Wall-parameter table of the built lists: (ux, uy, uz, rho) per index. */
 lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
 
+/* Allocation-free diagnostics of a caller-owned PDF field.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- code that takes all
+ * device memory from its own pool or fixed arena, or that runs where an allocation is not
+ * allowed because cudaMalloc/cudaFree can synchronise the device or fail mid-run.
+ *   f_dev   : device pointer to a dense canonical field f[i*ncells + n] (i in canonical
+ *             direction order, n any cell order), LBM_FP64 (double) or LBM_FP32 (float);
+ *             every cell counts as fluid.  Owned by the caller, only read.
+ *   force   : body force used for the half-force momentum shift (NULL = zero).
+ *   out_dev : device pointer to 8 doubles, written asynchronously on cuda_stream: mass,
+ *             momentum x, y, z, kinetic energy, max speed, non-finite cells, cells (the
+ *             fields of lbm_diagnostics as lbm_reduce computes them).
+ * No memory is allocated: the per-CTA partial sums use a fixed device array of
+ * LBM_REDUCE_NOALLOC_MAX_CELLS / 4096 records (2 MiB), which every GPU that loads the
+ * library holds until the process exits.  Fields with more than LBM_REDUCE_NOALLOC_MAX_CELLS
+ * cells are rejected with LBM_ERR_UNSUPPORTED; BF16/FP16 storages too.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) with the device current;
+ * make that first call before any stream capture.  All calls share the array: each call
+ * writes every record it reads, so nothing needs clearing, but calls whose kernels overlap
+ * on the GPU (different streams, no ordering between them) race on it.
+ * Errors: LBM_ERR_ARG (null pointer, bad stencil, ncells <= 0), LBM_ERR_UNSUPPORTED (storage
+ * or size), LBM_ERR_CUDA (launch or address lookup failed). */
+#define LBM_REDUCE_NOALLOC_MAX_CELLS 134217728LL
+lbm_status lbm_reduce_noalloc(const void *f_dev, int32_t stencil, int32_t storage, int64_t ncells,
+                              const double force[3], double *out_dev, void *cuda_stream);
+
 /* Last error message of the context (never NULL). */
 const char *lbm_last_error(const lbm_ctx *ctx);
 

@@ -38,7 +38,7 @@ def _sources():
 
 def _jobs(nvcc, extra):
     jobs = []
-    for name in ("api.cu", "plan.cpp"):
+    for name in ("api.cu", "plan.cpp", "reduce_static.cu"):
         src = os.path.join(CSRC, name)
         obj = os.path.join(BUILD, name.replace(".", "_") + ".o")
         lang = [] if name.endswith(".cu") else ["-x", "cu"]

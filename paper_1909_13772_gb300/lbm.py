@@ -76,6 +76,7 @@ _SIGS = {
     "lbm_plan_runs": ([_vp, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_plan_layout": ([_vp, ctypes.c_int32, _i64p], ctypes.c_int),
     "lbm_plan_params": ([_vp, _dp, ctypes.c_int64, _i64p], ctypes.c_int),
+    "lbm_reduce_noalloc": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _dp, _vp, _vp], ctypes.c_int),
     "lbm_last_error": ([_vp], ctypes.c_char_p),
     "lbm_destroy": ([_vp], None),
 }
@@ -262,6 +263,23 @@ def lbm_plan_params(ctx) -> np.ndarray:
     out = np.zeros(4 * n.value, dtype=np.float64)
     _check(ctx, L.lbm_plan_params(ctx, _ptr(out, ctypes.c_double), 4 * n.value, ctypes.byref(n)))
     return out.reshape(n.value, 4)
+
+
+REDUCE_NOALLOC_MAX_CELLS = 134217728
+
+
+def lbm_reduce_noalloc(f_dev_ptr: int, stencil: int, storage: int, ncells: int, force, out_dev_ptr: int, stream=None):
+    """Allocation-free diagnostics of a caller-owned dense device field (see include/lbm.h);
+    writes 8 doubles to out_dev_ptr asynchronously on ``stream``."""
+    F = _arr(force if force is not None else (0.0, 0.0, 0.0), np.float64)
+    st = load_library().lbm_reduce_noalloc(ctypes.c_void_p(f_dev_ptr), stencil, storage, int(ncells),
+                                           _ptr(F, ctypes.c_double), ctypes.c_void_p(out_dev_ptr),
+                                           ctypes.c_void_p(stream or 0))
+    if st != 0:
+        why = {1: "null pointer, unknown stencil or ncells <= 0",
+               7: "storage must be FP64 or FP32 and ncells <= %d" % REDUCE_NOALLOC_MAX_CELLS,
+               3: "CUDA launch or scratch address lookup failed"}.get(st, "")
+        raise LbmError(st, "lbm_reduce_noalloc: " + why)
 
 
 def lbm_last_error(ctx) -> str:
