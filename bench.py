@@ -15,7 +15,8 @@ needed between steps.  Per-kernel device times come from the library's own event
 
 --impl reference times the CPU oracle (the plain FP64 C program the parity tests use) on
 a bounded sample of the same workload: each step is one oracle time step of a
-256 x 256 x 8 slab of the channel (periodic in z, identical per-cell work).
+256 x 256 x d slab of the channel (periodic in z, identical per-cell work), d <= 8 chosen so
+that the run takes about a minute.
 
 Multi-GPU: every rank runs an independent replica of the workload on its own GPU (the
 path is not sharded in this build); value = total lattice updates of all ranks / max time.
@@ -210,8 +211,7 @@ def time_variant(lbm, variant, steps, warmup, world, tile=None):
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     start.record(stream)
-    for _ in range(steps):
-        sim.step(1)
+    sim.step(steps)
     end.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -239,8 +239,9 @@ def time_variant(lbm, variant, steps, warmup, world, tile=None):
 
 def time_e2e(lbm, variant, steps, world):
     """Same metric through the C ABI with host buffers: host->device upload of the initial
-    macroscopic fields, K x (lbm_step + lbm_reduce read-back), device->host download of the
-    final fields, all inside the timed region."""
+    macroscopic fields, K x (lbm_step + read-back of the step's diagnostics -- mass, momentum,
+    energy, max speed), device->host download of the final fields, all inside the timed
+    region."""
     import torch
     from paper_1909_13772_gb300 import inputs
     storage, pattern = VARIANTS[variant]
@@ -259,7 +260,7 @@ def time_e2e(lbm, variant, steps, world):
     lbm.lbm_init_macroscopic(sim.ctx, 0, rho_h, u_h)
     for _ in range(steps):
         lbm.lbm_step(sim.ctx, 1)
-        lbm.lbm_reduce(sim.ctx)
+        lbm.lbm_step_diagnostics(sim.ctx)
     lbm.lbm_get_macroscopic(sim.ctx, 0, rho_o, u_o)
     dt = time.perf_counter() - t0
     barrier(world)
@@ -351,7 +352,9 @@ def run_reference(args):
         return
     import oracle
     from paper_1909_13772_gb300 import inputs
-    shape = (SHAPE[0], SHAPE[1], 8)
+    # slab depth: about a minute of oracle work at ~17 MLUPS for the requested steps
+    depth = int(max(1, min(8, round(60.0 * 17e6 / (max(1, args.steps) * SHAPE[0] * SHAPE[1])))))
+    shape = (SHAPE[0], SHAPE[1], depth)
     p = oracle.OracleParams(shape=shape, q=19, collision=oracle.TRT, omega=OMEGA, magic_lambda=LAMBDA, force=FORCE,
                             periodic=(1, 0, 1), face_kind=(1, 1, 1, 1, 1, 1))
     rho, u = inputs.rest(shape)
@@ -362,7 +365,8 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     cells = shape[0] * shape[1] * shape[2]
     v = cells * args.steps / dt / 1e6
-    sample = "each step: one oracle time step of a 256x256x8 slab of the channel (FP64, D3Q19 TRT)"
+    sample = ("each step: one oracle time step of a 256x256x%d slab of the channel (FP64, D3Q19 TRT); "
+              "slab depth sized so that the whole run stays near a minute" % shape[2])
     out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3 / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -377,7 +381,7 @@ def run_reference(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--variant", choices=list(VARIANTS), default="fp32-twogrid")

@@ -155,8 +155,8 @@ lbm_status lbm_init_macroscopic(lbm_ctx *ctx, int32_t block, const double *rho, 
 
 /* Advance all blocks by n time steps (asynchronous on the context's stream).  Each step:
  * ghost-layer copy and boundary links, then the fused stream-collide sweep.  With
- * diag_interval > 0 the host reads the diagnostics every diag_interval steps and returns
- * LBM_ERR_DIVERGED when a value is non-finite. */
+ * diag_interval > 0 the host reads the step diagnostics (lbm_step_diagnostics) every
+ * diag_interval steps and returns LBM_ERR_DIVERGED when a value is non-finite. */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
 
 /* Density rho[N] and velocity u[3N] of one block's stored state (host FP64 buffers).
@@ -176,11 +176,21 @@ lbm_status lbm_set_pdfs(lbm_ctx *ctx, int32_t block, const double *f);
  * per-CTA partial sums reduced in a fixed order).  Synchronises the stream. */
 lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
 
+/* Diagnostics of the state produced by the most recent lbm_step, computed inside that
+ * step's last sweep from the values it was writing (no extra pass over the state): per-cell
+ * and per-warp sums in the sweep's arithmetic type (FP32 for FP32 and 16-bit storage, FP64 for
+ * FP64), FP64 across warps and tiles, fixed order.  Cheap enough to read after every step;
+ * lbm_reduce is the full-FP64 pass over the stored values.  Synchronises the stream.
+ * Errors: LBM_ERR_STATE when the state was set (init, set_pdfs) after the last step. */
+lbm_status lbm_step_diagnostics(lbm_ctx *ctx, lbm_diagnostics *out);
+
 /* Work sizes of one step (builds the boundary lists if needed). */
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 
 /* Sweep tile shape (cells per CTA along x, y, z; threads = tx * ty).  tx must be a
- * multiple of 32, tx*ty <= 1024.  Takes effect at the next list build.  Default 64 x 4 x 4. */
+ * multiple of 32, tx*ty <= 256.  A block narrower than tx gets tiles of its width rounded
+ * up to 32 and proportionally more rows.  Takes effect at the next list build.
+ * Default 256 x 1 x 4. */
 lbm_status lbm_set_tile(lbm_ctx *ctx, int32_t tx, int32_t ty, int32_t tz);
 
 /* Per-kernel device timing of lbm_step (tracing): when enabled, lbm_step records CUDA events
@@ -200,8 +210,9 @@ lbm_status lbm_stencil_table(int32_t q, int32_t *c, double *w, int32_t *opp);
 
 /* Host-side view of the built lists, for inspection and tests (no GPU needed; builds the
  * lists if needed).  Links: uint64 words, bits 0-4 direction q (pointing from the fluid
- * cell into the boundary), 5-6 kind, 7-15 wall-parameter index, 16-31 block, 32-63 cell
- * index in the block's padded layout.  Runs of `pattern` (LBM_TWO_GRID or LBM_AA): five
+ * cell into the boundary), 5-6 kind, 7-9 wrap bits (the boundary cell lies across a face of
+ * an axis the block wraps on), 10-17 wall-parameter index, 18-31 block, 32-63 cell index in
+ * the block's padded layout.  Runs of `pattern` (LBM_TWO_GRID or LBM_AA): five
  * int64 per run (src, dst, len, src stride, dst stride), offsets in elements from the base
  * of a PDF array.  With out == NULL only the count is returned in *n. */
 lbm_status lbm_plan_links(lbm_ctx *ctx, uint64_t *out, int64_t cap, int64_t *n);
@@ -209,8 +220,9 @@ lbm_status lbm_plan_runs(lbm_ctx *ctx, int32_t pattern, int64_t *out, int64_t ca
 /* Padded layout of a block: out[0..7] = xo, pitch, plane, slab, offset (elements), and the
  * interior size nx, ny, nz.  Cell (x, y, z), each in [-1, n], has index
  * (z+1) plane + (y+1) pitch + xo + x; direction i of it lives at offset + i slab + index.
- * Also gives the arena size in elements as out[8]. */
-lbm_status lbm_plan_layout(lbm_ctx *ctx, int32_t block, int64_t out[9]);
+ * out[8] = arena size in elements; out[9] = wrap bits (bit a: the block spans periodic axis a
+ * alone and the kernels wrap neighbour indices along a instead of using its ghost layer). */
+lbm_status lbm_plan_layout(lbm_ctx *ctx, int32_t block, int64_t out[10]);
 /* Wall-parameter table of the built lists: (ux, uy, uz, rho) per index. */
 lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
 

@@ -36,31 +36,34 @@ def _sources():
     return [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))] + [os.path.join(INCLUDE, "lbm.h")]
 
 
-def _jobs(nvcc, extra):
+def _jobs(nvcc, extra, build_dir):
     jobs = []
-    for name in ("api.cu", "plan.cpp", "reduce_static.cu"):
+    for name in ("api.cu", "plan.cpp", "diag.cu", "reduce_static.cu"):
         src = os.path.join(CSRC, name)
-        obj = os.path.join(BUILD, name.replace(".", "_") + ".o")
+        obj = os.path.join(build_dir, name.replace(".", "_") + ".o")
         lang = [] if name.endswith(".cu") else ["-x", "cu"]
         jobs.append([nvcc] + ARCH + NVFLAGS + extra + lang + ["-c", src, "-o", obj])
     for q, st in VARIANTS:
         for name in ("sweep.cu", "aux.cu"):
             src = os.path.join(CSRC, name)
-            obj = os.path.join(BUILD, "%s_%d_%d.o" % (name[:-3], q, st))
+            obj = os.path.join(build_dir, "%s_%d_%d.o" % (name[:-3], q, st))
             jobs.append([nvcc] + ARCH + NVFLAGS + extra + ["-DLBM_Q=%d" % q, "-DLBM_ST=%d" % st, "-c", src, "-o", obj])
     return jobs
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
-    """Compile (if stale) and return the path of liblbm.so."""
+def build(force: bool = False, verbose: bool = False, extra_flags=None, build_dir=None) -> str:
+    """Compile (if stale) and return the path of liblbm.so.  ``extra_flags`` (e.g. -D knobs)
+    and ``build_dir`` build a separate copy of the library elsewhere."""
     srcs = _sources()
-    if (not force and not extra_flags and os.path.exists(LIB)
-            and os.path.getmtime(LIB) >= max(os.path.getmtime(s) for s in srcs)):
-        return LIB
+    bdir = build_dir or BUILD
+    lib = os.path.join(bdir, "liblbm.so")
+    if (not force and os.path.exists(lib)
+            and os.path.getmtime(lib) >= max(os.path.getmtime(s) for s in srcs)):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(bdir, exist_ok=True)
     extra = list(extra_flags or [])
-    jobs = _jobs(nvcc, extra)
+    jobs = _jobs(nvcc, extra, bdir)
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -77,13 +80,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         c, r = errors[0]
         raise RuntimeError("nvcc failed:\n%s\n%s%s" % (" ".join(c), r.stdout, r.stderr))
     objs = [j[j.index("-o") + 1] for j in jobs]
-    tmp = LIB + ".%d.tmp" % os.getpid()
+    tmp = lib + ".%d.tmp" % os.getpid()
     link = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-Xcompiler", "-fopenmp", "-lgomp"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s%s" % (" ".join(link), r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

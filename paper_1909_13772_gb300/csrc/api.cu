@@ -28,7 +28,7 @@ struct lbm_ctx {
     std::vector<WallParam> block_param;
     int face_kind[6];
     WallParam face_param[6];
-    int tile[3] = {64, 4, 4};
+    int tile[3] = {256, 1, 4};
     int64_t arena_elems = 0;
     cudaStream_t stream = nullptr;
 
@@ -52,6 +52,8 @@ struct lbm_ctx {
     std::vector<const uint8_t *> mask_ptr;
     double *d_partials = nullptr;
     int64_t partials_cap = 0;
+    double *d_step_partials = nullptr;  // per-tile diagnostics written by the last sweep
+    bool step_diag_valid = false;       // d_step_partials describe the stored state
     double *d_out = nullptr;
     double *d_scratch = nullptr;
     int64_t scratch_cap = 0;
@@ -213,7 +215,7 @@ lbm_status ensure_lists(lbm_ctx *c)
     std::vector<DevBlock> db(c->blocks.size());
     for (size_t b = 0; b < db.size(); ++b) {
         const BlockLayout &L = c->blocks[b];
-        db[b] = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[b], L.xo, 0};
+        db[b] = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[b], L.xo, P.wrap[b]};
     }
     lbm_status s2;
     if ((s2 = upload(c, c->d_blocks, db, "upload blocks")) != LBM_OK) return s2;
@@ -239,9 +241,12 @@ lbm_status ensure_lists(lbm_ctx *c)
     const int64_t need = std::max<int64_t>(1, (int64_t)P.tiles.size()) * 8;
     if (need > c->partials_cap) {
         dfree(c->d_partials);
+        dfree(c->d_step_partials);
         CK(cudaMalloc((void **)&c->d_partials, need * sizeof(double)), "cudaMalloc(reduction partials)");
+        CK(cudaMalloc((void **)&c->d_step_partials, need * sizeof(double)), "cudaMalloc(step diagnostics)");
         c->partials_cap = need;
     }
+    c->step_diag_valid = false;
     c->plan_uploaded = true;
     return LBM_OK;
 }
@@ -262,7 +267,8 @@ CellArgs cell_args(lbm_ctx *c, int block)
     CellArgs a{};
     const BlockLayout &L = c->blocks[block];
     a.a = c->pattern == LBM_TWO_GRID ? c->arr[c->cur] : c->arr[0];
-    a.blk = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[block], L.xo, 0};
+    a.blk = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[block], L.xo,
+                     c->plan.wrap[block]};
     a.layout = state_layout(c);
     a.mask = c->mask_ptr[block];
     for (int k = 0; k < 3; ++k) a.F[k] = c->p.force[k];
@@ -456,6 +462,7 @@ lbm_status lbm_init_macroscopic(lbm_ctx *c, int32_t block, const double *rho, co
     CellArgs a = cell_args(c, block);
     a.f64 = c->d_scratch;
     CK(do_cells(c->q, c->storage, CELL_INIT, c->force ? 1 : 0, a), "init kernel");
+    c->step_diag_valid = false;
     CK(cudaStreamSynchronize(c->stream), "init");
     return LBM_OK;
 }
@@ -475,6 +482,8 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
     sw.ty = c->tile[1];
     sw.tz = c->tile[2];
     sw.force = c->force ? 1 : 0;
+    sw.wrap = 0;
+    for (int w : P.wrap) sw.wrap |= w;
     sw.cd = c->cd;
     sw.cf = c->cf;
     sw.stream = c->stream;
@@ -512,10 +521,13 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
             c->launches++;
         }
         if (c->timing && (s = mark(c, &e1)) != LBM_OK) return s;
+        const bool diag_due = c->p.diag_interval > 0 && (c->steps_done + 1) % c->p.diag_interval == 0;
+        sw.partials = (t == n - 1 || diag_due) ? c->d_step_partials : nullptr;
         if (sw.ntiles > 0) {
             CK(do_sweep(c->q, c->storage, sw), "sweep launch");
             c->launches++;
         }
+        c->step_diag_valid = sw.partials != nullptr;
         if (c->timing) {
             if ((s = mark(c, &e2)) != LBM_OK) return s;
             if (fa.nlinks + fa.nruns > 0) c->ev_marks[0].push_back({e0, e1});
@@ -528,7 +540,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
         c->steps_done++;
         if (c->p.diag_interval > 0 && c->steps_done % c->p.diag_interval == 0) {
             lbm_diagnostics d;
-            lbm_status r = lbm_reduce(c, &d);
+            lbm_status r = lbm_step_diagnostics(c, &d);
             if (r != LBM_OK) return r;
             if (d.nonfinite > 0 || !std::isfinite(d.mass))
                 return fail(c, LBM_ERR_DIVERGED, "non-finite state after step %lld (%lld cells)", (long long)c->steps_done,
@@ -592,6 +604,7 @@ lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
     CellArgs a = cell_args(c, block);
     a.f64 = c->d_scratch;
     CK(do_cells(c->q, c->storage, CELL_SET, 0, a), "set_pdfs kernel");
+    c->step_diag_valid = false;
     CK(cudaStreamSynchronize(c->stream), "set_pdfs");
     return LBM_OK;
 }
@@ -620,6 +633,28 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_diagnostics *out)
         CK(do_reduce(c->q, c->storage, r), "reduction kernels");
         CK(cudaMemcpyAsync(h, c->d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
         CK(cudaStreamSynchronize(c->stream), "reduce");
+    }
+    out->mass = h[0];
+    out->momentum[0] = h[1];
+    out->momentum[1] = h[2];
+    out->momentum[2] = h[3];
+    out->kinetic_energy = h[4];
+    out->max_speed = h[5];
+    out->nonfinite = (int64_t)h[6];
+    out->fluid_cells = (int64_t)h[7];
+    return LBM_OK;
+}
+
+lbm_status lbm_step_diagnostics(lbm_ctx *c, lbm_diagnostics *out)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    if (!c->step_diag_valid) return fail(c, LBM_ERR_STATE, "no step has run since the state was last set");
+    double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (!c->plan.tiles.empty()) {
+        CK(launch_reduce_final(c->d_step_partials, (int64_t)c->plan.tiles.size(), c->d_out, c->stream),
+           "diagnostics kernel");
+        CK(cudaMemcpyAsync(h, c->d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
+        CK(cudaStreamSynchronize(c->stream), "step diagnostics");
     }
     out->mass = h[0];
     out->momentum[0] = h[1];
@@ -743,11 +778,12 @@ lbm_status lbm_plan_runs(lbm_ctx *c, int32_t pattern, int64_t *out, int64_t cap,
     return LBM_OK;
 }
 
-lbm_status lbm_plan_layout(lbm_ctx *c, int32_t block, int64_t out[9])
+lbm_status lbm_plan_layout(lbm_ctx *c, int32_t block, int64_t out[10])
 {
     if (!c || !out) return LBM_ERR_ARG;
     lbm_status s = check_block(c, block);
     if (s != LBM_OK) return s;
+    if ((s = build_lists(c)) != LBM_OK) return s;
     const BlockLayout &L = c->blocks[block];
     out[0] = L.xo;
     out[1] = L.pitch;
@@ -758,6 +794,7 @@ lbm_status lbm_plan_layout(lbm_ctx *c, int32_t block, int64_t out[9])
     out[6] = L.n[1];
     out[7] = L.n[2];
     out[8] = c->arena_elems;
+    out[9] = c->plan.wrap[block];
     return LBM_OK;
 }
 
@@ -795,6 +832,7 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_params);
     dfree(c->d_masks);
     dfree(c->d_partials);
+    dfree(c->d_step_partials);
     dfree(c->d_out);
     dfree(c->d_scratch);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);

@@ -15,11 +15,21 @@ using S = Storage<StoreT>;
 using R = typename S::R;
 using Lq = Lattice<kQ>;
 
-__device__ __forceinline__ int64_t slot(int layout, int i, int64_t cell, const DevBlock &B)
+__device__ __forceinline__ int64_t slot(int layout, int i, int64_t cell, const DevBlock &B, int x, int y, int z)
 {
     if (layout == LAYOUT_PULL) return (int64_t)i * B.slab + cell;
     if (layout == LAYOUT_AA_E) return (int64_t)Lq::opp(i) * B.slab + cell;
-    return (int64_t)i * B.slab + cell + dir_offset<kQ>(i, B.pitch, B.plane);
+    return (int64_t)i * B.slab + cell + dir_offset<kQ>(i, B.pitch, B.plane) +
+           wrap_shift(B, x, y, z, Lq::cx(i), Lq::cy(i), Lq::cz(i));
+}
+
+// Interior coordinates of a cell index of the padded layout.
+__device__ __forceinline__ void coords_of(int64_t cell, const DevBlock &B, int &x, int &y, int &z)
+{
+    z = (int)(cell / B.plane) - 1;
+    const int64_t r = cell - (int64_t)(z + 1) * B.plane;
+    y = (int)(r / B.pitch) - 1;
+    x = (int)(r - (int64_t)(y + 1) * B.pitch) - B.xo;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -53,13 +63,15 @@ __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevB
         const uint64_t w = links[l];
         const int q = (int)(w & 31u);
         const int kind = (int)((w >> 5) & 3u);
-        const int par = (int)((w >> 7) & 511u);
-        const int blk = (int)((w >> 16) & 0xffffu);
+        const int bits = (int)((w >> 7) & 7u);
+        const int par = (int)((w >> 10) & 255u);
+        const int blk = (int)((w >> 18) & 0x3fffu);
         const int64_t cell = (int64_t)(w >> 32);
         const DevBlock &B = blocks[blk];
         StoreT *a = A + B.offset;
         const int o = Lq::opp(q);
-        const int64_t offq = dir_offset<kQ>(q, B.pitch, B.plane);
+        // offset of the boundary cell x + c_q (wrapped back along self-periodic axes)
+        const int64_t offq = dir_offset<kQ>(q, B.pitch, B.plane) + wrap_shift_bits(B, bits, Lq::cx(q), Lq::cy(q), Lq::cz(q));
         int64_t src, dst;
         int layout;
         if (MODE == FILL_PULL) {
@@ -87,10 +99,12 @@ __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevB
             out = v - R(6) * wq * R(p[3]) * cu;
         } else {
             const double *p = params + 4 * par;
+            int cx0, cy0, cz0;
+            coords_of(cell, B, cx0, cy0, cz0);
             R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                const R fi = S::ld_rw(a + slot(layout, i, cell, B), k.base[i]);
+                const R fi = S::ld_rw(a + slot(layout, i, cell, B, cx0, cy0, cz0), k.base[i]);
                 rho += fi;
                 jx += R(Lq::cx(i)) * fi;
                 jy += R(Lq::cy(i)) * fi;
@@ -124,12 +138,12 @@ __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevB
 // ---------------------------------------------------------------------------------------
 // Per-cell kernels over one block's interior (thread per cell, n = x + nx (y + ny z)).
 // ---------------------------------------------------------------------------------------
-__device__ __forceinline__ int64_t cell_of(int64_t n, const DevBlock &B)
+__device__ __forceinline__ int64_t cell_of(int64_t n, const DevBlock &B, int &x, int &y, int &z)
 {
-    const int x = (int)(n % B.nx);
+    x = (int)(n % B.nx);
     const int64_t t = n / B.nx;
-    const int y = (int)(t % B.ny);
-    const int z = (int)(t / B.ny);
+    y = (int)(t % B.ny);
+    z = (int)(t / B.ny);
     return (int64_t)(z + 1) * B.plane + (int64_t)(y + 1) * B.pitch + B.xo + x;
 }
 
@@ -142,7 +156,8 @@ __global__ void k_init(StoreT *__restrict__ A, DevBlock B, int layout, const dou
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int64_t cell = cell_of(n, B);
+    int x, y, z;
+    const int64_t cell = cell_of(n, B, x, y, z);
     StoreT *a = A + B.offset;
     if (mask && mask[cell] != 0) return;  // non-fluid cells hold no state
     const R rho = R(in[n]);
@@ -161,7 +176,7 @@ __global__ void k_init(StoreT *__restrict__ A, DevBlock B, int layout, const dou
     }
     collide<kQ, FORCE, R>(f, k);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B), f[i], k.base[i]);
+    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B, x, y, z), f[i], k.base[i]);
 }
 
 __global__ void k_get(const StoreT *__restrict__ A, DevBlock B, int layout, double *__restrict__ out,
@@ -170,11 +185,12 @@ __global__ void k_get(const StoreT *__restrict__ A, DevBlock B, int layout, doub
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int64_t cell = cell_of(n, B);
+    int x, y, z;
+    const int64_t cell = cell_of(n, B, x, y, z);
     const StoreT *a = A + B.offset;
     const bool fluid = !(mask && mask[cell] != 0);
     for (int i = 0; i < kQ; ++i)
-        out[(int64_t)i * N + n] = fluid ? (double)S::ld_rw(a + slot(layout, i, cell, B), k.base[i]) : 0.0;
+        out[(int64_t)i * N + n] = fluid ? (double)S::ld_rw(a + slot(layout, i, cell, B, x, y, z), k.base[i]) : 0.0;
 }
 
 __global__ void k_set(StoreT *__restrict__ A, DevBlock B, int layout, const double *__restrict__ in,
@@ -183,10 +199,11 @@ __global__ void k_set(StoreT *__restrict__ A, DevBlock B, int layout, const doub
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int64_t cell = cell_of(n, B);
+    int x, y, z;
+    const int64_t cell = cell_of(n, B, x, y, z);
     if (mask && mask[cell] != 0) return;
     StoreT *a = A + B.offset;
-    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B), R(in[(int64_t)i * N + n]), k.base[i]);
+    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B, x, y, z), R(in[(int64_t)i * N + n]), k.base[i]);
 }
 
 // Output moments in FP64: rho = sum f*, u = (sum c f* - F/2) / rho.
@@ -197,7 +214,8 @@ __global__ void k_macro(const StoreT *__restrict__ A, DevBlock B, int layout, do
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    const int64_t cell = cell_of(n, B);
+    int x, y, z;
+    const int64_t cell = cell_of(n, B, x, y, z);
     if (mask && mask[cell] != 0) {
         rho_out[n] = 0.0;
         u_out[n] = u_out[N + n] = u_out[2 * N + n] = 0.0;
@@ -206,7 +224,7 @@ __global__ void k_macro(const StoreT *__restrict__ A, DevBlock B, int layout, do
     const StoreT *a = A + B.offset;
     double f[kQ];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B), k.base[i]);
+    for (int i = 0; i < kQ; ++i) f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B, x, y, z), k.base[i]);
     const double F[3] = {Fx, Fy, Fz};
     double rho, j[3];
     moments_post<kQ>(f, F, rho, j);
@@ -239,11 +257,13 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const StoreT *__restrict__
 {
     const DevTile t = tiles[blockIdx.x];
     const DevBlock B = blocks[t.block];
-    const int lx = threadIdx.x % tx, ly = threadIdx.x / tx;
+    const int ttx = 32 * t.tx32;
+    const int rows = blockDim.x / ttx;  // the tile's height; leftover threads stay idle
+    const int lx = threadIdx.x % ttx, ly = threadIdx.x / ttx;
     const int x = t.x0 + lx, y = t.y0 + ly;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const double F[3] = {Fx, Fy, Fz};
-    if (x < B.nx && y < B.ny) {
+    if (ly < rows && x < B.nx && y < B.ny) {
         const int zend = min((int)t.z0 + tz, B.nz);
         const StoreT *a = A + B.offset;
         for (int z = t.z0; z < zend; ++z) {
@@ -253,7 +273,7 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const StoreT *__restrict__
             bool finite = true;
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B), k.base[i]);
+                f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B, x, y, z), k.base[i]);
                 finite = finite && isfinite(f[i]);
             }
             double rho, j[3];

@@ -1,0 +1,50 @@
+// diag.cu -- second pass of the step diagnostics: the sweep writes one record of 8 partial
+// sums per CTA (tile); one CTA adds them up in a fixed order, so the result is the same from
+// run to run.  Record: mass, momentum x/y/z, kinetic energy, max |u| (max, not sum),
+// non-finite cells, fluid cells.
+#include "launch.hpp"
+
+namespace lbm {
+namespace {
+
+__device__ __forceinline__ double dsum(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double dmax(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partials, int64_t n, double *__restrict__ out)
+{
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int64_t p = threadIdx.x; p < n; p += blockDim.x)
+        for (int c = 0; c < 8; ++c) acc[c] = c == 5 ? fmax(acc[c], partials[p * 8 + c]) : acc[c] + partials[p * 8 + c];
+    __shared__ double sh[8][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const double v = c == 5 ? dmax(acc[c]) : dsum(acc[c]);
+        if (lane == 0) sh[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int c = threadIdx.x;
+        double v = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = c == 5 ? fmax(v, sh[w][c]) : v + sh[w][c];
+        out[c] = v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, cudaStream_t s)
+{
+    k_diag_final<<<1, 256, 0, s>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -15,13 +15,47 @@ struct DevBlock {
     int64_t plane, slab;
     int64_t offset;       // element offset of this block in the PDF arena arrays
     const uint8_t *mask;  // padded-layout cell kinds (0 = fluid) or nullptr
-    int32_t xo, pad;
+    int32_t xo;
+    int32_t wrap;         // bit a: the block is its own periodic neighbour along axis a
 };
+
+// Index shift that maps a neighbour of cell (x, y, z) one step outside the block back
+// inside, along the axes the block wraps on.  (dx, dy, dz) is the neighbour's offset in
+// {-1, 0, 1}^3 (compile-time in the sweeps); the result is added to the plain neighbour
+// offset.  Written as coordinate arithmetic so that nothing extra stays live across a sweep.
+__host__ __device__ __forceinline__ int64_t wrap_shift(const DevBlock &B, int x, int y, int z, int dx, int dy, int dz)
+{
+    int sx = 0, sy = 0, sz = 0;
+    if (dx != 0 && (B.wrap & 1)) {
+        const int xx = x + dx;
+        sx = xx < 0 ? 1 : (xx >= B.nx ? -1 : 0);
+    }
+    if (dy != 0 && (B.wrap & 2)) {
+        const int yy = y + dy;
+        sy = yy < 0 ? 1 : (yy >= B.ny ? -1 : 0);
+    }
+    if (dz != 0 && (B.wrap & 4)) {
+        const int zz = z + dz;
+        sz = zz < 0 ? 1 : (zz >= B.nz ? -1 : 0);
+    }
+    return (int64_t)(sx * B.nx + sy * B.ny * B.pitch) + (int64_t)sz * B.nz * B.plane;
+}
+
+// The same shift for a neighbour known (from a link's wrap bits) to lie across wrapped faces.
+__host__ __device__ __forceinline__ int64_t wrap_shift_bits(const DevBlock &B, int bits, int dx, int dy, int dz)
+{
+    int64_t s = 0;
+    if (bits & 1) s -= dx * (int64_t)B.nx;
+    if (bits & 2) s -= dy * (int64_t)B.ny * B.pitch;
+    if (bits & 4) s -= dz * (int64_t)B.nz * B.plane;
+    return s;
+}
 
 struct DevTile {
     int32_t block;
     int16_t x0, y0, z0;
-    uint16_t flags;
+    uint8_t flags;  // bit 0: tile has non-fluid cells
+    uint8_t tx32;   // tile width in cells / 32 (threads per CTA / width = tile height)
 };
 
 struct DevRun {
@@ -42,6 +76,22 @@ struct Coll {
 // Storage formats.  T is the stored type, R the arithmetic type.  The *_DEV formats store
 // the deviation f_i - w_i rho0 (base[i]) in 16 bits.
 // ---------------------------------------------------------------------------------------
+// Load path of the two-grid source array (read-only during the sweep): 0 = read-only data
+// path (ld.global.nc), 1 = evict-first streaming load (ld.global.cs).
+#ifndef LBM_PULL_LOAD
+#define LBM_PULL_LOAD 0
+#endif
+
+template <class T>
+__device__ __forceinline__ T ld_src(const T *p)
+{
+#if LBM_PULL_LOAD == 1
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
+}
+
 template <class T>
 struct Storage;
 
@@ -49,7 +99,7 @@ template <>
 struct Storage<double> {
     using T = double;
     using R = double;
-    static __device__ __forceinline__ R ld(const T *p, R) { return __ldg(p); }
+    static __device__ __forceinline__ R ld(const T *p, R) { return ld_src(p); }
     static __device__ __forceinline__ R ld_rw(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { __stcs(p, v); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R) { *p = v; }
@@ -59,7 +109,7 @@ template <>
 struct Storage<float> {
     using T = float;
     using R = float;
-    static __device__ __forceinline__ R ld(const T *p, R) { return __ldg(p); }
+    static __device__ __forceinline__ R ld(const T *p, R) { return ld_src(p); }
     static __device__ __forceinline__ R ld_rw(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { __stcs(p, v); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R) { *p = v; }
@@ -69,7 +119,7 @@ template <>
 struct Storage<__nv_bfloat16> {
     using T = __nv_bfloat16;
     using R = float;
-    static __device__ __forceinline__ R ld(const T *p, R base) { return base + __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ R ld(const T *p, R base) { return base + __bfloat162float(ld_src(p)); }
     static __device__ __forceinline__ R ld_rw(const T *p, R base) { return base + __bfloat162float(*p); }
     static __device__ __forceinline__ void st(T *p, R v, R base) { __stcs(p, __float2bfloat16_rn(v - base)); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R base) { *p = __float2bfloat16_rn(v - base); }
@@ -79,7 +129,7 @@ template <>
 struct Storage<__half> {
     using T = __half;
     using R = float;
-    static __device__ __forceinline__ R ld(const T *p, R base) { return base + __half2float(__ldg(p)); }
+    static __device__ __forceinline__ R ld(const T *p, R base) { return base + __half2float(ld_src(p)); }
     static __device__ __forceinline__ R ld_rw(const T *p, R base) { return base + __half2float(*p); }
     static __device__ __forceinline__ void st(T *p, R v, R base) { __stcs(p, __float2half_rn(v - base)); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R base) { *p = __float2half_rn(v - base); }
@@ -97,24 +147,25 @@ struct Storage<__half> {
 // which is the TRT operator written per pair; SRT is the case w- = w+.
 // ---------------------------------------------------------------------------------------
 template <int Q, bool FORCE, class R>
-__device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
+__device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, R &rho_out, R &ux_out, R &uy_out, R &uz_out)
 {
     using L = Lattice<Q>;
+    // pass 1: moments from the pair sums / differences (not kept: pass 2 recomputes them,
+    // which costs two adds per pair but keeps only the Q populations live)
     R rho = f[0], jx = R(0), jy = R(0), jz = R(0);
-    R s[Q], d[Q];
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
-        s[i] = f[i] + f[o];
-        d[i] = f[i] - f[o];
-        rho += s[i];
-        if (L::cx(i) > 0) jx += d[i];
-        if (L::cx(i) < 0) jx -= d[i];
-        if (L::cy(i) > 0) jy += d[i];
-        if (L::cy(i) < 0) jy -= d[i];
-        if (L::cz(i) > 0) jz += d[i];
-        if (L::cz(i) < 0) jz -= d[i];
+        const R si = f[i] + f[o];
+        const R di = f[i] - f[o];
+        rho += si;
+        if (L::cx(i) > 0) jx += di;
+        if (L::cx(i) < 0) jx -= di;
+        if (L::cy(i) > 0) jy += di;
+        if (L::cy(i) < 0) jy -= di;
+        if (L::cz(i) > 0) jz += di;
+        if (L::cz(i) < 0) jz -= di;
     }
     R ux, uy, uz;
     const R inv = R(1) / rho;
@@ -127,6 +178,10 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
         uy = jy * inv;
         uz = jz * inv;
     }
+    rho_out = rho;
+    ux_out = ux;
+    uy_out = uy;
+    uz_out = uz;
     const R usq = ux * ux + uy * uy + uz * uz;
     const R rb = rho * (R(1) - R(1.5) * usq);  // rho (1 - 1.5 u.u)
     const R uF = FORCE ? ux * k.F[0] + uy * k.F[1] + uz * k.F[2] : R(0);
@@ -148,10 +203,12 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
         if (L::cy(i) < 0) cu -= uy;
         if (L::cz(i) > 0) cu += uz;
         if (L::cz(i) < 0) cu -= uz;
+        const R si = f[i] + f[o];
+        const R di = f[i] - f[o];
         const R feqp = w * (rb + R(4.5) * rho * cu * cu);
         const R feqm = w * R(3) * rho * cu;
-        const R ep = k.omega_p * (R(0.5) * s[i] - feqp);
-        const R em = k.omega_m * (R(0.5) * d[i] - feqm);
+        const R ep = k.omega_p * (R(0.5) * si - feqp);
+        const R em = k.omega_m * (R(0.5) * di - feqm);
         R fi = f[i] - ep - em;
         R fo = f[o] - ep + em;
         if (FORCE) {
@@ -170,6 +227,13 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
         f[i] = fi;
         f[o] = fo;
     }
+}
+
+template <int Q, bool FORCE, class R>
+__device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
+{
+    R rho, ux, uy, uz;
+    collide<Q, FORCE, R>(f, k, rho, ux, uy, uz);
 }
 
 // Moments of a stored post-collision state, in FP64: rho = sum f*, j = sum c f* - F/2.

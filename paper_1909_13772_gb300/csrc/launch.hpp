@@ -22,6 +22,8 @@ struct SweepArgs {
     int tx, ty, tz;
     int kind;   // SweepKind
     int force;  // body force non-zero
+    double *partials;  // non-null: write per-CTA diagnostics records (8 doubles per tile)
+    int wrap;          // some block wraps onto itself along a periodic axis
     Coll<double> cd;
     Coll<float> cf;
     cudaStream_t stream;
@@ -78,6 +80,9 @@ enum CellOp { CELL_INIT = 0, CELL_GET = 1, CELL_SET = 2, CELL_MACRO = 3 };
 
 // Entry points of the per-(stencil, storage) objects; storage 0 fp64, 1 fp32, 2 bf16-dev,
 // 3 fp16-dev.  sweep.cu defines launch_sweep_<Q>_<ST>; aux.cu the other three.
+// Second pass of the diagnostics: fixed-order sum of n per-CTA records into out[8].
+cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, cudaStream_t s);
+
 #define LBM_DECLARE(Q, ST)                                                  \
     cudaError_t launch_sweep_##Q##_##ST(const SweepArgs &s);                \
     cudaError_t launch_fill_##Q##_##ST(const FillArgs &s);                  \

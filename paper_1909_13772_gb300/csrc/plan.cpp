@@ -29,7 +29,7 @@ void layout_blocks(std::vector<BlockLayout> &blocks, int bytes_per_pdf, int q, i
 std::string check_blocks(const std::vector<BlockLayout> &blocks)
 {
     if (blocks.empty()) return "no blocks";
-    if ((int64_t)blocks.size() > kMaxBlocks) return "too many blocks (max 65536)";
+    if ((int64_t)blocks.size() > kMaxBlocks) return "too many blocks (max 16384)";
     for (size_t i = 0; i < blocks.size(); ++i) {
         const auto &b = blocks[i];
         for (int a = 0; a < 3; ++a)
@@ -128,7 +128,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
             auto key = std::make_tuple(p.u[0], p.u[1], p.u[2], p.rho);
             auto it = seen.find(key);
             if (it == seen.end()) {
-                if ((int)out.params.size() >= kMaxParams) return "too many distinct wall parameter sets (max 506)";
+                if ((int)out.params.size() >= kMaxParams) return "too many distinct wall parameter sets (max 250)";
                 it = seen.emplace(key, (int)out.params.size()).first;
                 out.params.push_back(p);
             }
@@ -174,6 +174,11 @@ std::string build_plan(const PlanInput &in, Plan &out)
                 }
     }
 
+    std::vector<int> wrapb(nb, 0);
+    for (int b = 0; b < nb; ++b)
+        for (int a = 0; a < 3; ++a)
+            if (in.periodic[a] && blocks[b].origin[a] == lo[a] && blocks[b].n[a] == ext[a]) wrapb[b] |= 1 << a;
+
     std::vector<BlockOut> bo(nb);
     std::string err;
 #pragma omp parallel for schedule(dynamic, 1)
@@ -184,6 +189,21 @@ std::string build_plan(const PlanInput &in, Plan &out)
         const int64_t np = (int64_t)px * py * pz;
         // local padded index p(x,y,z) = (x+1) + px ((y+1) + py (z+1))
         auto pidx = [&](int x, int y, int z) { return (int64_t)(x + 1) + px * ((int64_t)(y + 1) + (int64_t)py * (z + 1)); };
+        // wrap a coordinate (at most one cell outside) along the axes the block wraps on;
+        // returns the bits of the axes that were wrapped
+        const int W = wrapb[b];
+        auto wrapc = [&](int &x, int &y, int &z) {
+            int bits = 0;
+            if ((W & 1) && (x < 0 || x >= nx)) { x = x < 0 ? x + nx : x - nx; bits |= 1; }
+            if ((W & 2) && (y < 0 || y >= ny)) { y = y < 0 ? y + ny : y - ny; bits |= 2; }
+            if ((W & 4) && (z < 0 || z >= nz)) { z = z < 0 ? z + nz : z - nz; bits |= 4; }
+            return bits;
+        };
+        auto inside = [&](int x, int y, int z) { return x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz; };
+        // ghost cells outside the block along a wrapped axis are never read or written
+        auto wrapped_away = [&](int x, int y, int z) {
+            return ((W & 1) && (x < 0 || x >= nx)) || ((W & 2) && (y < 0 || y >= ny)) || ((W & 4) && (z < 0 || z >= nz));
+        };
         std::vector<uint8_t> kind(np, 255);
         std::vector<uint16_t> param(np, 0);
         std::vector<int32_t> sblock(np, -1);
@@ -260,10 +280,12 @@ std::string build_plan(const PlanInput &in, Plan &out)
                 for (int y = 0; y < ny; ++y)
                     for (int x = 0; x < nx; ++x) {
                         if (kind[pidx(x, y, z)] != K_FLUID) continue;
-                        int64_t pn = pidx(x + L.cx[qd], y + L.cy[qd], z + L.cz[qd]);
+                        int tx = x + L.cx[qd], ty = y + L.cy[qd], tz = z + L.cz[qd];
+                        const int bits = wrapc(tx, ty, tz);
+                        int64_t pn = pidx(tx, ty, tz);
                         uint8_t k = kind[pn];
                         if (k == K_NOSLIP || k == K_VELOCITY || k == K_PRESSURE)
-                            o.links[k].push_back(pack_link(qd, k, param[pn], b, B.cell(x, y, z)));
+                            o.links[k].push_back(pack_link(qd, k, bits, param[pn], b, B.cell(x, y, z)));
                     }
         }
         // ghost runs: for each direction, shell cells mirroring a fluid cell, in (z, y, x) order
@@ -273,23 +295,23 @@ std::string build_plan(const PlanInput &in, Plan &out)
                 for (int y = -1; y <= ny; ++y)
                     for (int x = -1; x <= nx; ++x) {
                         bool shell = x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz;
-                        if (!shell) continue;
+                        if (!shell || wrapped_away(x, y, z)) continue;
                         int64_t p = pidx(x, y, z);
                         if (kind[p] != K_MIRROR) continue;
                         const auto &S = blocks[sblock[p]];
                         int64_t src = S.offset + (int64_t)j * S.slab + scell[p];
                         int64_t dst = base + (int64_t)j * B.slab + B.cell(x, y, z);
-                        // two-grid pull: interior fluid cell g + c_j reads slot j of g
+                        // two-grid pull: interior fluid cell wrap(g + c_j) reads slot j of g
                         int ax = x + L.cx[j], ay = y + L.cy[j], az = z + L.cz[j];
-                        if (ax >= 0 && ax < nx && ay >= 0 && ay < ny && az >= 0 && az < nz &&
-                            kind[pidx(ax, ay, az)] == K_FLUID) {
+                        wrapc(ax, ay, az);
+                        if (inside(ax, ay, az) && kind[pidx(ax, ay, az)] == K_FLUID) {
                             append_run(o.runs_pull, src, dst, S.pitch, B.pitch);
                             o.slots_pull++;
                         }
-                        // AA: interior fluid cell g - c_j reads (odd step) / writes (odd step) slot j of g
+                        // AA: interior fluid cell wrap(g - c_j) reads and writes slot j of g
                         int bx = x - L.cx[j], by = y - L.cy[j], bz = z - L.cz[j];
-                        if (bx >= 0 && bx < nx && by >= 0 && by < ny && bz >= 0 && bz < nz &&
-                            kind[pidx(bx, by, bz)] == K_FLUID) {
+                        wrapc(bx, by, bz);
+                        if (inside(bx, by, bz) && kind[pidx(bx, by, bz)] == K_FLUID) {
                             append_run(o.runs_aa, src, dst, S.pitch, B.pitch);
                             o.slots_aa++;
                         }
@@ -302,7 +324,8 @@ std::string build_plan(const PlanInput &in, Plan &out)
                 for (int y = 0; y < ny; ++y)
                     for (int x = 0; x < nx; ++x) o.mask[(size_t)B.cell(x, y, z)] = kind[pidx(x, y, z)];
         }
-        const int tx = in.tile[0], ty = in.tile[1], tz = in.tile[2];
+        const int threads = in.tile[0] * in.tile[1], tz = in.tile[2];
+        const int tx = std::min(in.tile[0], (nx + 31) / 32 * 32), ty = threads / tx;
         for (int z0 = 0; z0 < nz; z0 += tz)
             for (int y0 = 0; y0 < ny; y0 += ty)
                 for (int x0 = 0; x0 < nx; x0 += tx) {
@@ -314,7 +337,8 @@ std::string build_plan(const PlanInput &in, Plan &out)
                                 nfl += kind[pidx(x, y, z)] == K_FLUID;
                             }
                     if (nfl == 0) continue;
-                    o.tiles.push_back(Tile{b, (int16_t)x0, (int16_t)y0, (int16_t)z0, (uint16_t)(nfl < ntot ? 1 : 0)});
+                    o.tiles.push_back(Tile{b, (int16_t)x0, (int16_t)y0, (int16_t)z0, (uint8_t)(nfl < ntot ? 1 : 0),
+                                           (uint8_t)(tx / 32)});
                 }
         o.cells = (int64_t)nx * ny * nz;
         for (int z = 0; z < nz; ++z)
@@ -328,6 +352,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
     out.runs_aa.clear();
     out.tiles.clear();
     out.masks.assign(nb, {});
+    out.wrap = wrapb;
     out.cells = out.fluid_cells = 0;
     out.ghost_slots_pull = out.ghost_slots_aa = 0;
     for (int k = 0; k < 4; ++k) out.link_count[k] = 0;

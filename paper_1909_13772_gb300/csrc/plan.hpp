@@ -48,24 +48,28 @@ struct GhostRun {
     int32_t pad;
 };
 
-// Sweep tile: x0, y0, z0 of a TX x TY x TZ box of one block; flags bit 0: tile has
-// non-fluid cells (the kernel reads the mask).
+// Sweep tile: x0, y0, z0 of a box of one block, tx32 * 32 cells wide, (threads / width)
+// rows high and TZ planes deep; flags bit 0: tile has non-fluid cells (the kernel reads the
+// mask).  The width adapts to the block: min(TX, nx rounded up to 32), the height takes the
+// remaining threads, so narrow blocks do not leave most lanes idle.
 struct Tile {
     int32_t block;
     int16_t x0, y0, z0;
-    uint16_t flags;
+    uint8_t flags;
+    uint8_t tx32;
 };
 
 // Link word: bits 0-4 direction q (the link points from fluid cell x along c_q into a
-// boundary cell), 5-6 kind, 7-15 wall-parameter index, 16-31 block, 32-63 cell index of x
-// in the block's padded layout.
-inline uint64_t pack_link(int q, int kind, int param, int block, int64_t cell)
+// boundary cell), 5-6 kind, 7-9 wrap bits (x, y, z: the boundary cell x + c_q lies across a
+// face along which the block wraps onto itself, so its slot sits at the wrapped position),
+// 10-17 wall-parameter index, 18-31 block, 32-63 cell index of x in the block's padded layout.
+inline uint64_t pack_link(int q, int kind, int wrapbits, int param, int block, int64_t cell)
 {
-    return (uint64_t)q | ((uint64_t)kind << 5) | ((uint64_t)param << 7) | ((uint64_t)block << 16) |
-           ((uint64_t)cell << 32);
+    return (uint64_t)q | ((uint64_t)kind << 5) | ((uint64_t)wrapbits << 7) | ((uint64_t)param << 10) |
+           ((uint64_t)block << 18) | ((uint64_t)cell << 32);
 }
-constexpr int kMaxParams = 512;
-constexpr int kMaxBlocks = 65536;
+constexpr int kMaxParams = 256;
+constexpr int kMaxBlocks = 16384;
 
 struct PlanInput {
     int q;
@@ -88,6 +92,10 @@ struct Plan {
     int64_t ghost_slots_pull = 0, ghost_slots_aa = 0;
     std::vector<Tile> tiles;
     std::vector<std::vector<uint8_t>> masks;  // per block: padded-layout mask (0 fluid) or empty
+    // per block: bit a set when the block spans a periodic axis a alone, so it is its own
+    // neighbour across both faces of that axis; kernels then wrap neighbour indices along a
+    // and no ghost copy is made there
+    std::vector<int> wrap;
     int64_t cells = 0, fluid_cells = 0;
 };
 

@@ -66,6 +66,7 @@ _SIGS = {
     "lbm_get_pdfs": ([_vp, ctypes.c_int32, _dp], ctypes.c_int),
     "lbm_set_pdfs": ([_vp, ctypes.c_int32, _dp], ctypes.c_int),
     "lbm_reduce": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
+    "lbm_step_diagnostics": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
     "lbm_get_info": ([_vp, _P(lbm_info)], ctypes.c_int),
     "lbm_set_tile": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "lbm_kernel_launches": ([_vp], ctypes.c_int64),
@@ -93,7 +94,11 @@ def load_library(build_if_missing: bool = True):
     if _lib is not None:
         return _lib
     from . import build as _build
-    path = _build.build() if build_if_missing else _build.LIB
+    override = os.environ.get("LBM_LIBRARY")
+    if override:
+        path = override
+    else:
+        path = _build.build() if build_if_missing else _build.LIB
     if not os.path.exists(path):
         raise ImportError("liblbm.so not found at %s; run paper_1909_13772_gb300.build.build()" % path)
     lib = ctypes.CDLL(path)
@@ -191,6 +196,13 @@ def lbm_reduce(ctx) -> dict:
             "max_speed": d.max_speed, "nonfinite": d.nonfinite, "fluid_cells": d.fluid_cells}
 
 
+def lbm_step_diagnostics(ctx) -> dict:
+    d = lbm_diagnostics()
+    _check(ctx, load_library().lbm_step_diagnostics(ctx, ctypes.byref(d)))
+    return {"mass": d.mass, "momentum": tuple(d.momentum), "kinetic_energy": d.kinetic_energy,
+            "max_speed": d.max_speed, "nonfinite": d.nonfinite, "fluid_cells": d.fluid_cells}
+
+
 def lbm_get_info(ctx) -> dict:
     i = lbm_info()
     _check(ctx, load_library().lbm_get_info(ctx, ctypes.byref(i)))
@@ -250,9 +262,9 @@ def lbm_plan_runs(ctx, pattern) -> np.ndarray:
 
 
 def lbm_plan_layout(ctx, block) -> dict:
-    out = np.zeros(9, dtype=np.int64)
+    out = np.zeros(10, dtype=np.int64)
     _check(ctx, load_library().lbm_plan_layout(ctx, block, _ptr(out, ctypes.c_int64)))
-    keys = ("xo", "pitch", "plane", "slab", "offset", "nx", "ny", "nz", "arena_elems")
+    keys = ("xo", "pitch", "plane", "slab", "offset", "nx", "ny", "nz", "arena_elems", "wrap")
     return {k: int(v) for k, v in zip(keys, out)}
 
 
@@ -366,6 +378,9 @@ class Simulation:
 
     def reduce(self):
         return lbm_reduce(self.ctx)
+
+    def step_diagnostics(self):
+        return lbm_step_diagnostics(self.ctx)
 
     def info(self):
         return lbm_get_info(self.ctx)

@@ -88,26 +88,41 @@ class Replay:
         L = self.lay[b]
         return self.c[i, 0] + self.c[i, 1] * L["pitch"] + self.c[i, 2] * L["plane"]
 
+    def wrap(self, b, x, y, z, d):
+        """Index shift for neighbour x + d of interior cells (arrays) along self-periodic axes."""
+        L = self.lay[b]
+        W = L["wrap"]
+        s = np.zeros_like(x, dtype=np.int64)
+        for a, (pos, n, stride) in enumerate(((x, L["nx"], 1), (y, L["ny"], L["pitch"]), (z, L["nz"], L["plane"]))):
+            if not (W >> a) & 1:
+                continue
+            if d[a] > 0:
+                s = s - np.where(pos == n - 1, n * stride, 0)
+            elif d[a] < 0:
+                s = s + np.where(pos == 0, n * stride, 0)
+        return s
+
     def interior(self, b):
         (ox, oy, oz), (nx, ny, nz) = self.sim.blocks[b]
         z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         return x.ravel(), y.ravel(), z.ravel(), ox, oy, oz
 
-    def slot(self, layout, b, i, cells):
+    def slot(self, layout, b, i, cells, xyz):
         L = self.lay[b]
         if layout == "pull":
             return L["offset"] + i * L["slab"] + cells
         if layout == "E":
             return L["offset"] + self.opp[i] * L["slab"] + cells
-        return L["offset"] + i * L["slab"] + cells + self.doff(b, i)
+        return L["offset"] + i * L["slab"] + cells + self.doff(b, i) + self.wrap(b, *xyz, self.c[i])
 
     def put(self, f, fluid, layout):
         for b in range(len(self.sim.blocks)):
             x, y, z, ox, oy, oz = self.interior(b)
             keep = fluid[z + oz, y + oy, x + ox]
             cells = self.cell(b, x, y, z)[keep]
+            xyz = (x[keep], y[keep], z[keep])
             for i in range(self.q):
-                self.A[self.slot(layout, b, i, cells)] = f[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]]
+                self.A[self.slot(layout, b, i, cells, xyz)] = f[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]]
 
     def get(self, fluid, layout):
         out = np.zeros((self.q,) + fluid.shape)
@@ -115,8 +130,9 @@ class Replay:
             x, y, z, ox, oy, oz = self.interior(b)
             keep = fluid[z + oz, y + oy, x + ox]
             cells = self.cell(b, x, y, z)[keep]
+            xyz = (x[keep], y[keep], z[keep])
             for i in range(self.q):
-                out[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]] = self.A[self.slot(layout, b, i, cells)]
+                out[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]] = self.A[self.slot(layout, b, i, cells, xyz)]
         return out
 
     def runs(self, pattern, reverse=False):
@@ -132,12 +148,18 @@ class Replay:
         w = self.links
         q = (w & 31).astype(int)
         kind = ((w >> 5) & 3).astype(int)
-        par = ((w >> 7) & 511).astype(int)
-        blk = ((w >> 16) & 0xFFFF).astype(int)
+        bits = ((w >> 7) & 7).astype(int)
+        par = ((w >> 10) & 255).astype(int)
+        blk = ((w >> 18) & 0x3FFF).astype(int)
         cell = (w >> 32).astype(np.int64)
         base = np.array([self.lay[b]["offset"] for b in blk], dtype=np.int64)
         slab = np.array([self.lay[b]["slab"] for b in blk], dtype=np.int64)
         off = np.array([self.doff(b, qq) for b, qq in zip(blk, q)], dtype=np.int64)
+        for k in range(len(w)):  # wrap the boundary cell back along self-periodic axes
+            L = self.lay[blk[k]]
+            for a, (n, stride) in enumerate(((L["nx"], 1), (L["ny"], L["pitch"]), (L["nz"], L["plane"]))):
+                if (bits[k] >> a) & 1:
+                    off[k] -= self.c[q[k], a] * n * stride
         o = self.opp[q]
         if mode == "pull":
             src, dst = base + q * slab + cell, base + o * slab + cell + off
@@ -159,9 +181,10 @@ class Replay:
             keep = fluid[z + oz, y + oy, x + ox]
             cells = self.cell(b, x, y, z)[keep]
             L = self.lay[b]
+            xyz = (x[keep], y[keep], z[keep])
             for i in range(self.q):
                 out[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]] = \
-                    self.A[L["offset"] + i * L["slab"] + cells - self.doff(b, i)]
+                    self.A[L["offset"] + i * L["slab"] + cells - self.doff(b, i) + self.wrap(b, *xyz, -self.c[i])]
         return out
 
 
@@ -177,9 +200,10 @@ def _replay_aa_step(R, fluid, phase):
             keep = fluid[z + oz, y + oy, x + ox]
             cells = R.cell(b, x, y, z)[keep]
             L = R.lay[b]
+            xyz = (x[keep], y[keep], z[keep])
             for i in range(R.q):
                 f[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]] = \
-                    R.A[L["offset"] + R.opp[i] * L["slab"] + cells - R.doff(b, i)]
+                    R.A[L["offset"] + R.opp[i] * L["slab"] + cells - R.doff(b, i) + R.wrap(b, *xyz, -R.c[i])]
         R.put(f, fluid, "O")
         return f
     R.fill_links("O")
@@ -265,25 +289,30 @@ def test_replayed_lists_stream_like_oracle(q, layout, walls):
 
 
 def test_channel_link_and_ghost_counts():
-    """C2-shaped channel (walls in y, periodic x/z): 5 wall links per wall cell and per wall
-    (D3Q19), 5 crossing slots per periodic face cell plus 1 per edge cell."""
+    """Channel (walls in y, periodic x/z), D3Q19: 5 wall links per wall cell and wall.  One
+    block spanning x and z wraps onto itself: no ghost copies.  Split into two blocks along x,
+    each still spans z alone (wraps in z) and copies, per x-face ghost cell, the directions
+    that enter the neighbour (wrapping z)."""
     nx, ny, nz = 16, 12, 8
     p = lbm.make_params(stencil=19, periodic=(1, 0, 1))
     sim = lbm.Simulation(p, [((0, 0, 0), (nx, ny, nz))])
     info = sim.info()
     assert info["links"][lbm.NOSLIP] == 2 * 5 * nx * nz
     assert info["cells"] == info["fluid_cells"] == nx * ny * nz
-    # pull slots: x faces (2 * ny * nz cells, 5 dirs minus those leaving the y range),
-    # z faces, and x-z edges; counted directly from the geometry
+    assert info["ghost_slots"] == 0 and info["ghost_runs"] == 0
+    assert lbm.lbm_plan_layout(sim.ctx, 0)["wrap"] == 0b101
+    sim.close()
+    half = nx // 2
+    sim = lbm.Simulation(p, [((0, 0, 0), (half, ny, nz)), ((half, 0, 0), (half, ny, nz))])
+    info = sim.info()
+    assert info["links"][lbm.NOSLIP] == 2 * 5 * nx * nz
     c, _, _ = lbm.lbm_stencil_table(19)
     slots = 0
-    for z in range(-1, nz + 1):
-        for y in range(0, ny):
-            for x in range(-1, nx + 1):
-                if 0 <= x < nx and 0 <= z < nz:
-                    continue
+    for gx in (-1, half):
+        for y in range(ny):
+            for z in range(nz):
                 for i in range(19):
-                    ax, ay, az = x + c[i, 0], y + c[i, 1], z + c[i, 2]
-                    slots += (0 <= ax < nx) and (0 <= ay < ny) and (0 <= az < nz)
-    assert info["ghost_slots"] == slots
+                    ax, ay, az = gx + c[i, 0], y + c[i, 1], (z + c[i, 2]) % nz
+                    slots += (0 <= ax < half) and (0 <= ay < ny)
+    assert info["ghost_slots"] == 2 * slots
     sim.close()

@@ -225,8 +225,9 @@ def test_divergence_is_reported():
 
 def test_bound_torch_buffer_and_stream():
     import torch
-    case = Case(shape=(33, 10, 7), storage=lbm.FP32, pattern=lbm.AA)
-    p = lbm.make_params(stencil=19, storage=lbm.FP32, pattern=lbm.AA, omega=1.3)
+    case = Case(shape=(33, 10, 7), storage=lbm.FP32, pattern=lbm.AA, periodic=(1, 0, 1),
+                faces=(1, 1, lbm.NOSLIP, lbm.NOSLIP, 1, 1))
+    p = lbm.make_params(stencil=19, storage=lbm.FP32, pattern=lbm.AA, omega=1.3, periodic=(1, 0, 1))
     stream = torch.cuda.Stream()
     probe = lbm.Simulation(p, case.block_list())
     need = lbm.lbm_required_bytes(probe.ctx)
@@ -242,3 +243,52 @@ def test_bound_torch_buffer_and_stream():
     case.omega = 1.3
     _, want = oracle_run(case, rho, u, 6)
     assert normwise(got, want) <= 1e-5
+
+
+@pytest.mark.parametrize("storage,pattern", [(lbm.FP64, lbm.TWO_GRID), (lbm.FP64, lbm.AA), (lbm.FP32, lbm.TWO_GRID),
+                                             (lbm.FP32, lbm.AA)])
+def test_step_diagnostics_match_full_reduction(storage, pattern):
+    """The diagnostics fused into the last sweep of lbm_step agree with the full FP64 pass
+    over the stored state (to rounding of the sweep's arithmetic type)."""
+    case = _porous_case(storage, pattern)
+    rho, u = inputs.random_state(case.shape, seed=14, rho_amp=0.02, u_amp=0.02)
+    s = case.make_sim()
+    init_sim(s, rho, u)
+    with pytest.raises(lbm.LbmError):
+        s.step_diagnostics()  # state was set, no step yet
+    s.step(3)
+    fused, full = s.step_diagnostics(), s.reduce()
+    s.close()
+    tol = 1e-13 if storage == lbm.FP64 else 2e-6
+    assert abs(fused["mass"] / full["mass"] - 1) < tol
+    scale = max(abs(v) for v in full["momentum"]) + 1e-300
+    assert max(abs(a - b) for a, b in zip(fused["momentum"], full["momentum"])) / scale < (1e-10 if storage == lbm.FP64 else 2e-3)
+    assert abs(fused["kinetic_energy"] / full["kinetic_energy"] - 1) < (1e-10 if storage == lbm.FP64 else 1e-4)
+    assert abs(fused["max_speed"] / full["max_speed"] - 1) < (1e-10 if storage == lbm.FP64 else 1e-5)
+    assert fused["nonfinite"] == 0 and fused["fluid_cells"] == full["fluid_cells"]
+
+
+def test_full_size_channel_equals_column_oracle():
+    """256^3 channel (the benchmark workload and launch configuration, FP32 and FP64): the
+    flow is x- and z-invariant, so every column must equal the oracle's 1 x 256 x 1 run."""
+    n, steps = 256, 20
+    force = (1e-6, 0.0, 0.0)
+    col = Case(shape=(1, n, 1), q=19, collision=lbm.TRT, storage=lbm.FP64, omega=1.0, force=force,
+               periodic=(1, 0, 1), faces=(1, 1, lbm.NOSLIP, lbm.NOSLIP, 1, 1))
+    rho1, u1 = inputs.rest(col.shape)
+    _, want = oracle_run(col, rho1, u1, steps)
+    for storage in (lbm.FP32, lbm.FP64):
+        case = Case(shape=(n, n, n), q=19, collision=lbm.TRT, storage=storage, omega=1.0, force=force,
+                    periodic=(1, 0, 1), faces=(1, 1, lbm.NOSLIP, lbm.NOSLIP, 1, 1))
+        s = case.make_sim()
+        rho, u = inputs.rest(case.shape)
+        s.init(0, rho, u)
+        s.step(steps)
+        f = s.pdfs(0)
+        s.close()
+        rng = np.random.default_rng(0)
+        for _ in range(8):
+            x, z = rng.integers(0, n, 2)
+            assert normwise(f[:, z, :, x], want[:, 0, :, 0]) <= TOL[storage]
+        # x/z invariance of the whole field
+        assert np.abs(f - f[:, :1, :, :1]).max() <= TOL[storage] * np.abs(f).max()
