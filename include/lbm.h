@@ -102,7 +102,9 @@ typedef struct {
     int64_t fluid_cells;   /* number of fluid cells */
 } lbm_diagnostics;
 
-/* Sizes of the work one lbm_step performs, from the built boundary and ghost lists. */
+/* Sizes of the work one lbm_step performs, from the built boundary and ghost lists.  No-slip
+ * links (links[LBM_NOSLIP]) are applied inside the sweep from cell masks; velocity and
+ * pressure links go through the fill kernel's link list. */
 typedef struct {
     int64_t cells;          /* interior cells of all blocks */
     int64_t fluid_cells;    /* interior fluid cells */
@@ -210,9 +212,8 @@ lbm_status lbm_stencil_table(int32_t q, int32_t *c, double *w, int32_t *opp);
 
 /* Host-side view of the built lists, for inspection and tests (no GPU needed; builds the
  * lists if needed).  Links: uint64 words, bits 0-4 direction q (pointing from the fluid
- * cell into the boundary), 5-6 kind, 7-9 wrap bits (the boundary cell lies across a face of
- * an axis the block wraps on), 10-17 wall-parameter index, 18-31 block, 32-63 cell index in
- * the block's padded layout.  Runs of `pattern` (LBM_TWO_GRID or LBM_AA): five
+ * cell into the boundary), 5-6 kind, 7-9 reserved, 10-17 wall-parameter index, 18-31 block,
+ * 32-63 cell index in the block's padded layout.  Runs of `pattern` (LBM_TWO_GRID or LBM_AA): five
  * int64 per run (src, dst, len, src stride, dst stride), offsets in elements from the base
  * of a PDF array.  With out == NULL only the count is returned in *n. */
 lbm_status lbm_plan_links(lbm_ctx *ctx, uint64_t *out, int64_t cap, int64_t *n);
@@ -220,9 +221,22 @@ lbm_status lbm_plan_runs(lbm_ctx *ctx, int32_t pattern, int64_t *out, int64_t ca
 /* Padded layout of a block: out[0..7] = xo, pitch, plane, slab, offset (elements), and the
  * interior size nx, ny, nz.  Cell (x, y, z), each in [-1, n], has index
  * (z+1) plane + (y+1) pitch + xo + x; direction i of it lives at offset + i slab + index.
- * out[8] = arena size in elements; out[9] = wrap bits (bit a: the block spans periodic axis a
- * alone and the kernels wrap neighbour indices along a instead of using its ghost layer). */
+ * out[8] = arena size in elements; out[9] = 1 when the block reads and writes its neighbour
+ * cells in place (every region of its ghost shell is covered by exactly one block with a
+ * matching face, or lies outside the domain), 0 when it keeps ghost copies. */
 lbm_status lbm_plan_layout(lbm_ctx *ctx, int32_t block, int64_t out[10]);
+/* Neighbour table of a block: out[r], r = (rx+1) + 3 (ry+1) + 9 (rz+1) for the ghost-shell
+ * region on side r_a in {-1, 0, 1} of each axis, is the block covering that region exactly
+ * (the block itself across a periodic axis it spans alone), or -1 (outside the domain,
+ * uncovered, or no exact match).  The cell of a neighbour read in place is the first (+) or
+ * last (-) layer of that block along the crossed axes, the same coordinate along the others. */
+lbm_status lbm_plan_neighbors(lbm_ctx *ctx, int32_t block, int32_t out[27]);
+/* Cell masks of a block in its padded layout (uint32 per cell; *n = 0 when the block needs
+ * none): bit 31 = the cell is not fluid; bit i = the pull source x - c_i of direction i is a
+ * no-slip cell, so the sweep applies halfway bounce-back for it (Sec. 4.4 boundary handling;
+ * no-slip needs no link list). */
+lbm_status lbm_plan_mask(lbm_ctx *ctx, int32_t block, uint32_t *out, int64_t cap, int64_t *n);
+
 /* Wall-parameter table of the built lists: (ux, uy, uz, rho) per index. */
 lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
 

@@ -48,8 +48,8 @@ struct lbm_ctx {
     DevRun *d_runs_pull = nullptr, *d_runs_aa = nullptr;
     DevTile *d_tiles = nullptr;
     double *d_params = nullptr;
-    uint8_t *d_masks = nullptr;
-    std::vector<const uint8_t *> mask_ptr;
+    uint32_t *d_masks = nullptr;
+    std::vector<const uint32_t *> mask_ptr;
     double *d_partials = nullptr;
     int64_t partials_cap = 0;
     double *d_step_partials = nullptr;  // per-tile diagnostics written by the last sweep
@@ -188,6 +188,30 @@ lbm_status ensure_arena(lbm_ctx *c)
     return LBM_OK;
 }
 
+DevBlock dev_block(const lbm_ctx *c, int b)
+{
+    const BlockLayout &L = c->blocks[b];
+    DevBlock d{};
+    d.nx = L.n[0];
+    d.ny = L.n[1];
+    d.nz = L.n[2];
+    d.pitch = L.pitch;
+    d.plane = L.plane;
+    d.slab = L.slab;
+    d.offset = L.offset;
+    d.mask = c->mask_ptr.empty() ? nullptr : c->mask_ptr[b];
+    d.xo = L.xo;
+    d.through = c->plan.through.empty() ? 0 : c->plan.through[b];
+    for (int r = 0; r < 27; ++r) d.nbr[r] = c->plan.nbr.empty() ? -1 : c->plan.nbr[b][r];
+    d.wrap = 0;
+    if (d.through)
+        for (int a = 0; a < 3; ++a) {
+            const int lo = a == 0 ? 12 : (a == 1 ? 10 : 4), hi = a == 0 ? 14 : (a == 1 ? 16 : 22);
+            if (d.nbr[lo] == b && d.nbr[hi] == b) d.wrap |= 1 << a;
+        }
+    return d;
+}
+
 lbm_status ensure_lists(lbm_ctx *c)
 {
     lbm_status s = build_lists(c);
@@ -199,24 +223,24 @@ lbm_status ensure_lists(lbm_ctx *c)
     // masks: one buffer, per-block offsets
     dfree(c->d_masks);
     size_t mbytes = 0;
-    for (const auto &m : P.masks) mbytes += (m.size() + 255) / 256 * 256;
+    // element counts rounded to 64 (256 bytes) so each block's mask starts aligned
+    for (const auto &m : P.masks) mbytes += (m.size() + 63) / 64 * 64;
     c->mask_ptr.assign(c->blocks.size(), nullptr);
     if (mbytes) {
-        CK(cudaMalloc((void **)&c->d_masks, mbytes), "cudaMalloc(masks)");
-        c->list_bytes += mbytes;
+        CK(cudaMalloc((void **)&c->d_masks, mbytes * sizeof(uint32_t)), "cudaMalloc(masks)");
+        c->list_bytes += mbytes * sizeof(uint32_t);
         size_t off = 0;
         for (size_t b = 0; b < P.masks.size(); ++b) {
             if (P.masks[b].empty()) continue;
-            CK(cudaMemcpy(c->d_masks + off, P.masks[b].data(), P.masks[b].size(), cudaMemcpyHostToDevice), "upload mask");
+            CK(cudaMemcpy(c->d_masks + off, P.masks[b].data(), P.masks[b].size() * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice),
+               "upload mask");
             c->mask_ptr[b] = c->d_masks + off;
-            off += (P.masks[b].size() + 255) / 256 * 256;
+            off += (P.masks[b].size() + 63) / 64 * 64;
         }
     }
     std::vector<DevBlock> db(c->blocks.size());
-    for (size_t b = 0; b < db.size(); ++b) {
-        const BlockLayout &L = c->blocks[b];
-        db[b] = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[b], L.xo, P.wrap[b]};
-    }
+    for (size_t b = 0; b < db.size(); ++b) db[b] = dev_block(c, (int)b);
     lbm_status s2;
     if ((s2 = upload(c, c->d_blocks, db, "upload blocks")) != LBM_OK) return s2;
     if ((s2 = upload(c, c->d_links, P.links, "upload links")) != LBM_OK) return s2;
@@ -267,8 +291,9 @@ CellArgs cell_args(lbm_ctx *c, int block)
     CellArgs a{};
     const BlockLayout &L = c->blocks[block];
     a.a = c->pattern == LBM_TWO_GRID ? c->arr[c->cur] : c->arr[0];
-    a.blk = DevBlock{L.n[0], L.n[1], L.n[2], L.pitch, L.plane, L.slab, L.offset, c->mask_ptr[block], L.xo,
-                     c->plan.wrap[block]};
+    a.blocks = c->d_blocks;
+    a.block = block;
+    a.blk = dev_block(c, block);
     a.layout = state_layout(c);
     a.mask = c->mask_ptr[block];
     for (int k = 0; k < 3; ++k) a.F[k] = c->p.force[k];
@@ -482,8 +507,15 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
     sw.ty = c->tile[1];
     sw.tz = c->tile[2];
     sw.force = c->force ? 1 : 0;
-    sw.wrap = 0;
-    for (int w : P.wrap) sw.wrap |= w;
+    // neighbour mode of the launch: 0 none in place, 1 every in-place neighbour is the block
+    // itself (wrap arithmetic), 2 general neighbour table
+    sw.through = 0;
+    for (size_t b = 0; b < c->blocks.size(); ++b) {
+        if (!P.through[b]) continue;
+        sw.through = std::max(sw.through, 1);
+        for (int r = 0; r < 27; ++r)
+            if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) sw.through = 2;
+    }
     sw.cd = c->cd;
     sw.cf = c->cf;
     sw.stream = c->stream;
@@ -794,7 +826,31 @@ lbm_status lbm_plan_layout(lbm_ctx *c, int32_t block, int64_t out[10])
     out[6] = L.n[1];
     out[7] = L.n[2];
     out[8] = c->arena_elems;
-    out[9] = c->plan.wrap[block];
+    out[9] = c->plan.through[block];
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_neighbors(lbm_ctx *c, int32_t block, int32_t out[27])
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if ((s = build_lists(c)) != LBM_OK) return s;
+    for (int r = 0; r < 27; ++r) out[r] = c->plan.nbr[block][r];
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_mask(lbm_ctx *c, int32_t block, uint32_t *out, int64_t cap, int64_t *n)
+{
+    if (!c || !n) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if ((s = build_lists(c)) != LBM_OK) return s;
+    const std::vector<uint32_t> &m = c->plan.masks[block];
+    *n = (int64_t)m.size();
+    if (!out) return LBM_OK;
+    if (cap < *n) return fail(c, LBM_ERR_ARG, "buffer too small");
+    if (*n) memcpy(out, m.data(), (size_t)*n * sizeof(uint32_t));
     return LBM_OK;
 }
 

@@ -15,13 +15,21 @@ using S = Storage<StoreT>;
 using R = typename S::R;
 using Lq = Lattice<kQ>;
 
-__device__ __forceinline__ int64_t slot(int layout, int i, int64_t cell, const DevBlock &B, int x, int y, int z)
+// Arena offset (from the base of the PDF array) of the slot holding f*_i of cell (x, y, z)
+// of block Bp in each layout.  In the AA O layout the value sits at the cell x + c_i, which
+// may lie in a neighbour block read in place (resolve); a value whose target x + c_i is
+// no-slip sits in the cell's own slot opp(i) (the neighbour sweep's bounce-back; m = the
+// cell's mask).
+__device__ __forceinline__ int64_t slot(int layout, int i, int64_t cell, const DevBlock *__restrict__ blocks,
+                                        const DevBlock *Bp, int x, int y, int z, uint32_t m)
 {
-    if (layout == LAYOUT_PULL) return (int64_t)i * B.slab + cell;
-    if (layout == LAYOUT_AA_E) return (int64_t)Lq::opp(i) * B.slab + cell;
-    return (int64_t)i * B.slab + cell + dir_offset<kQ>(i, B.pitch, B.plane) +
-           wrap_shift(B, x, y, z, Lq::cx(i), Lq::cy(i), Lq::cz(i));
+    if (layout == LAYOUT_PULL) return Bp->offset + (int64_t)i * Bp->slab + cell;
+    if (layout == LAYOUT_AA_E) return Bp->offset + (int64_t)Lq::opp(i) * Bp->slab + cell;
+    if (i > 0 && ((m >> Lq::opp(i)) & 1u)) return Bp->offset + (int64_t)Lq::opp(i) * Bp->slab + cell;
+    return resolve(blocks, Bp, x, y, z, Lq::cx(i), Lq::cy(i), Lq::cz(i), i);
 }
+
+__device__ __forceinline__ uint32_t mask_of(const DevBlock &B, int64_t cell) { return B.mask ? B.mask[cell] : 0u; }
 
 // Interior coordinates of a cell index of the padded layout.
 __device__ __forceinline__ void coords_of(int64_t cell, const DevBlock &B, int &x, int &y, int &z)
@@ -67,27 +75,28 @@ __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevB
         const int par = (int)((w >> 10) & 255u);
         const int blk = (int)((w >> 18) & 0x3fffu);
         const int64_t cell = (int64_t)(w >> 32);
-        const DevBlock &B = blocks[blk];
-        StoreT *a = A + B.offset;
+        const DevBlock *Bp = blocks + blk;
+        const DevBlock &B = *Bp;
         const int o = Lq::opp(q);
-        // offset of the boundary cell x + c_q (wrapped back along self-periodic axes)
-        const int64_t offq = dir_offset<kQ>(q, B.pitch, B.plane) + wrap_shift_bits(B, bits, Lq::cx(q), Lq::cy(q), Lq::cz(q));
+        int cx0, cy0, cz0;
+        coords_of(cell, B, cx0, cy0, cz0);
+        // slots of the boundary cell x + c_q: own ghost / solid cell, or a neighbour block's cell
         int64_t src, dst;
         int layout;
         if (MODE == FILL_PULL) {
-            src = (int64_t)q * B.slab + cell;
-            dst = (int64_t)o * B.slab + cell + offq;
+            src = B.offset + (int64_t)q * B.slab + cell;
+            dst = resolve(blocks, Bp, cx0, cy0, cz0, Lq::cx(q), Lq::cy(q), Lq::cz(q), o);
             layout = LAYOUT_PULL;
         } else if (MODE == FILL_AA_E) {
-            src = (int64_t)o * B.slab + cell;
-            dst = (int64_t)q * B.slab + cell + offq;
+            src = B.offset + (int64_t)o * B.slab + cell;
+            dst = resolve(blocks, Bp, cx0, cy0, cz0, Lq::cx(q), Lq::cy(q), Lq::cz(q), q);
             layout = LAYOUT_AA_E;
         } else {
-            src = (int64_t)q * B.slab + cell + offq;
-            dst = (int64_t)o * B.slab + cell;
+            src = resolve(blocks, Bp, cx0, cy0, cz0, Lq::cx(q), Lq::cy(q), Lq::cz(q), q);
+            dst = B.offset + (int64_t)o * B.slab + cell;
             layout = LAYOUT_AA_O;
         }
-        const R v = S::ld_rw(a + src, k.base[q]);
+        const R v = S::ld_rw(A + src, k.base[q]);
         const R wq = R(Lq::w(q));
         const R cx = R(Lq::cx(q)), cy = R(Lq::cy(q)), cz = R(Lq::cz(q));
         R out;
@@ -99,12 +108,11 @@ __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevB
             out = v - R(6) * wq * R(p[3]) * cu;
         } else {
             const double *p = params + 4 * par;
-            int cx0, cy0, cz0;
-            coords_of(cell, B, cx0, cy0, cz0);
+            const uint32_t m0 = mask_of(B, cell);
             R rho = R(0), jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                const R fi = S::ld_rw(a + slot(layout, i, cell, B, cx0, cy0, cz0), k.base[i]);
+                const R fi = S::ld_rw(A + slot(layout, i, cell, blocks, Bp, cx0, cy0, cz0, m0), k.base[i]);
                 rho += fi;
                 jx += R(Lq::cx(i)) * fi;
                 jy += R(Lq::cy(i)) * fi;
@@ -117,7 +125,7 @@ __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevB
             const R usq = ux * ux + uy * uy + uz * uz;
             out = -v + R(2) * wq * R(p[3]) * (R(1) + R(4.5) * cu * cu - R(1.5) * usq);
         }
-        S::st_plain(a + dst, out, k.base[o]);
+        S::st_plain(A + dst, out, k.base[o]);
     } else {
         const int64_t gt = ((int64_t)blockIdx.x - link_ctas) * blockDim.x + threadIdx.x;
         const int64_t r = gt >> 5;
@@ -150,16 +158,20 @@ __device__ __forceinline__ int64_t cell_of(int64_t n, const DevBlock &B, int &x,
 // Initial state: populations = equilibrium at (rho, u - F/(2 rho)), then one collision
 // (the stored state is post-collision).  Equilibrium: w rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u).
 template <bool FORCE>
-__global__ void k_init(StoreT *__restrict__ A, DevBlock B, int layout, const double *__restrict__ in,
-                       const uint8_t *__restrict__ mask, Coll<R> k)
+__global__ void k_init(StoreT *__restrict__ A, const DevBlock *__restrict__ blocks, int blk, int layout,
+                       const double *__restrict__ in,
+                       const uint32_t *__restrict__ mask, Coll<R> k)
 {
+    const DevBlock *Bp = blocks + blk;
+    const DevBlock &B = *Bp;
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     int x, y, z;
     const int64_t cell = cell_of(n, B, x, y, z);
     StoreT *a = A + B.offset;
-    if (mask && mask[cell] != 0) return;  // non-fluid cells hold no state
+    const uint32_t m = mask ? mask[cell] : 0u;
+    if (m & kMaskSolid) return;  // non-fluid cells hold no state
     const R rho = R(in[n]);
     R ux = R(in[N + n]), uy = R(in[2 * N + n]), uz = R(in[3 * N + n]);
     if (FORCE) {
@@ -176,47 +188,60 @@ __global__ void k_init(StoreT *__restrict__ A, DevBlock B, int layout, const dou
     }
     collide<kQ, FORCE, R>(f, k);
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B, x, y, z), f[i], k.base[i]);
+    for (int i = 0; i < kQ; ++i) S::st_plain(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), f[i], k.base[i]);
 }
 
-__global__ void k_get(const StoreT *__restrict__ A, DevBlock B, int layout, double *__restrict__ out,
-                      const uint8_t *__restrict__ mask, FillConst k)
+__global__ void k_get(const StoreT *__restrict__ A, const DevBlock *__restrict__ blocks, int blk, int layout,
+                      double *__restrict__ out,
+                      const uint32_t *__restrict__ mask, FillConst k)
 {
+    const DevBlock *Bp = blocks + blk;
+    const DevBlock &B = *Bp;
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     int x, y, z;
     const int64_t cell = cell_of(n, B, x, y, z);
     const StoreT *a = A + B.offset;
-    const bool fluid = !(mask && mask[cell] != 0);
+    const uint32_t m = mask ? mask[cell] : 0u;
+    const bool fluid = !(m & kMaskSolid);
     for (int i = 0; i < kQ; ++i)
-        out[(int64_t)i * N + n] = fluid ? (double)S::ld_rw(a + slot(layout, i, cell, B, x, y, z), k.base[i]) : 0.0;
+        out[(int64_t)i * N + n] = fluid ? (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]) : 0.0;
 }
 
-__global__ void k_set(StoreT *__restrict__ A, DevBlock B, int layout, const double *__restrict__ in,
-                      const uint8_t *__restrict__ mask, FillConst k)
+__global__ void k_set(StoreT *__restrict__ A, const DevBlock *__restrict__ blocks, int blk, int layout,
+                      const double *__restrict__ in,
+                      const uint32_t *__restrict__ mask, FillConst k)
 {
+    const DevBlock *Bp = blocks + blk;
+    const DevBlock &B = *Bp;
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     int x, y, z;
     const int64_t cell = cell_of(n, B, x, y, z);
-    if (mask && mask[cell] != 0) return;
+    const uint32_t m = mask ? mask[cell] : 0u;
+    if (m & kMaskSolid) return;
     StoreT *a = A + B.offset;
-    for (int i = 0; i < kQ; ++i) S::st_plain(a + slot(layout, i, cell, B, x, y, z), R(in[(int64_t)i * N + n]), k.base[i]);
+    for (int i = 0; i < kQ; ++i)
+        S::st_plain(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), R(in[(int64_t)i * N + n]), k.base[i]);
 }
 
 // Output moments in FP64: rho = sum f*, u = (sum c f* - F/2) / rho.
-__global__ void k_macro(const StoreT *__restrict__ A, DevBlock B, int layout, double *__restrict__ rho_out,
-                        double *__restrict__ u_out, const uint8_t *__restrict__ mask, FillConst k, double Fx,
+__global__ void k_macro(const StoreT *__restrict__ A, const DevBlock *__restrict__ blocks, int blk, int layout,
+                        double *__restrict__ rho_out,
+                        double *__restrict__ u_out, const uint32_t *__restrict__ mask, FillConst k, double Fx,
                         double Fy, double Fz)
 {
+    const DevBlock *Bp = blocks + blk;
+    const DevBlock &B = *Bp;
     const int64_t N = (int64_t)B.nx * B.ny * B.nz;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
     int x, y, z;
     const int64_t cell = cell_of(n, B, x, y, z);
-    if (mask && mask[cell] != 0) {
+    const uint32_t m = mask ? mask[cell] : 0u;
+    if (m & kMaskSolid) {
         rho_out[n] = 0.0;
         u_out[n] = u_out[N + n] = u_out[2 * N + n] = 0.0;
         return;
@@ -224,7 +249,7 @@ __global__ void k_macro(const StoreT *__restrict__ A, DevBlock B, int layout, do
     const StoreT *a = A + B.offset;
     double f[kQ];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B, x, y, z), k.base[i]);
+    for (int i = 0; i < kQ; ++i) f[i] = (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]);
     const double F[3] = {Fx, Fy, Fz};
     double rho, j[3];
     moments_post<kQ>(f, F, rho, j);
@@ -256,8 +281,9 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const StoreT *__restrict__
                                                       double *__restrict__ partials)
 {
     const DevTile t = tiles[blockIdx.x];
-    const DevBlock B = blocks[t.block];
-    const int ttx = 32 * t.tx32;
+    const DevBlock *Bp = blocks + t.block;
+    const DevBlock &B = *Bp;
+    const int ttx = (int)t.width_m1 + 1;
     const int rows = blockDim.x / ttx;  // the tile's height; leftover threads stay idle
     const int lx = threadIdx.x % ttx, ly = threadIdx.x / ttx;
     const int x = t.x0 + lx, y = t.y0 + ly;
@@ -268,12 +294,13 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const StoreT *__restrict__
         const StoreT *a = A + B.offset;
         for (int z = t.z0; z < zend; ++z) {
             const int64_t cell = (int64_t)(z + 1) * B.plane + (int64_t)(y + 1) * B.pitch + B.xo + x;
-            if (B.mask && B.mask[cell] != 0) continue;
+            const uint32_t m = mask_of(B, cell);
+            if (m & kMaskSolid) continue;
             double f[kQ];
             bool finite = true;
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                f[i] = (double)S::ld_rw(a + slot(layout, i, cell, B, x, y, z), k.base[i]);
+                f[i] = (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]);
                 finite = finite && isfinite(f[i]);
             }
             double rho, j[3];
@@ -373,18 +400,18 @@ cudaError_t LBM_CAT(launch_cells_, LBM_Q, LBM_ST)(int op, int force, const CellA
     switch (op) {
         case CELL_INIT:
             if (force)
-                k_init<true><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, k);
+                k_init<true><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, k);
             else
-                k_init<false><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, k);
+                k_init<false><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, k);
             break;
         case CELL_GET:
-            k_get<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, fk);
+            k_get<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, fk);
             break;
         case CELL_SET:
-            k_set<<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blk, s.layout, s.f64, s.mask, fk);
+            k_set<<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, fk);
             break;
         case CELL_MACRO:
-            k_macro<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blk, s.layout, s.rho, s.u, s.mask,
+            k_macro<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blocks, s.block, s.layout, s.rho, s.u, s.mask,
                                                               fk, s.F[0], s.F[1], s.F[2]);
             break;
         default: return cudaErrorInvalidValue;

@@ -13,49 +13,60 @@ namespace lbm {
 struct DevBlock {
     int32_t nx, ny, nz, pitch;
     int64_t plane, slab;
-    int64_t offset;       // element offset of this block in the PDF arena arrays
-    const uint8_t *mask;  // padded-layout cell kinds (0 = fluid) or nullptr
+    int64_t offset;        // element offset of this block in the PDF arena arrays
+    const uint32_t *mask;  // padded-layout cell masks (bit 31 non-fluid, bit i bounce-back) or nullptr
     int32_t xo;
-    int32_t wrap;         // bit a: the block is its own periodic neighbour along axis a
+    int32_t through;       // neighbours are read and written in place (see nbr)
+    int32_t nbr[27];       // block covering each ghost-shell region, -1 = boundary / none
+    int32_t wrap;          // bit a: across axis a the block is its own neighbour (nbr = itself)
+    __host__ __device__ int64_t cell(int x, int y, int z) const
+    {
+        return (int64_t)(z + 1) * plane + (int64_t)(y + 1) * pitch + xo + x;
+    }
 };
 
-// Index shift that maps a neighbour of cell (x, y, z) one step outside the block back
-// inside, along the axes the block wraps on.  (dx, dy, dz) is the neighbour's offset in
-// {-1, 0, 1}^3 (compile-time in the sweeps); the result is added to the plain neighbour
-// offset.  Written as coordinate arithmetic so that nothing extra stays live across a sweep.
-__host__ __device__ __forceinline__ int64_t wrap_shift(const DevBlock &B, int x, int y, int z, int dx, int dy, int dz)
+constexpr uint32_t kMaskSolid = 1u << 31;
+
+// Arena offset (elements from the base of the PDF array) of slot `q` of cell
+// (x, y, z) + (dx, dy, dz) of block *Bp.  Inside the block, or outside with no neighbour in
+// place (boundary region, or a block that keeps ghost copies): the own (ghost) cell.
+// Outside with a neighbour in place: the neighbour block's cell -- along a crossed axis its
+// first (+) or last (-) layer, along the other axes the same coordinate (faces of such
+// neighbours match exactly); a block spanning a periodic axis alone is its own neighbour,
+// which wraps the index.
+// Index shift that brings the neighbour (x, y, z) + (dx, dy, dz) back into a block that is
+// its own neighbour across the crossed faces (wrap bits): -n or +n times the axis stride.
+__device__ __forceinline__ int64_t wrap_shift(const DevBlock &B, int x, int y, int z, int dx, int dy, int dz)
 {
     int sx = 0, sy = 0, sz = 0;
-    if (dx != 0 && (B.wrap & 1)) {
-        const int xx = x + dx;
-        sx = xx < 0 ? 1 : (xx >= B.nx ? -1 : 0);
-    }
-    if (dy != 0 && (B.wrap & 2)) {
-        const int yy = y + dy;
-        sy = yy < 0 ? 1 : (yy >= B.ny ? -1 : 0);
-    }
-    if (dz != 0 && (B.wrap & 4)) {
-        const int zz = z + dz;
-        sz = zz < 0 ? 1 : (zz >= B.nz ? -1 : 0);
-    }
+    if (dx != 0 && (B.wrap & 1)) sx = (x + dx < 0) ? 1 : (x + dx >= B.nx ? -1 : 0);
+    if (dy != 0 && (B.wrap & 2)) sy = (y + dy < 0) ? 1 : (y + dy >= B.ny ? -1 : 0);
+    if (dz != 0 && (B.wrap & 4)) sz = (z + dz < 0) ? 1 : (z + dz >= B.nz ? -1 : 0);
     return (int64_t)(sx * B.nx + sy * B.ny * B.pitch) + (int64_t)sz * B.nz * B.plane;
 }
 
-// The same shift for a neighbour known (from a link's wrap bits) to lie across wrapped faces.
-__host__ __device__ __forceinline__ int64_t wrap_shift_bits(const DevBlock &B, int bits, int dx, int dy, int dz)
+__device__ __forceinline__ int64_t resolve(const DevBlock *__restrict__ blocks, const DevBlock *Bp, int x, int y,
+                                           int z, int dx, int dy, int dz, int q)
 {
-    int64_t s = 0;
-    if (bits & 1) s -= dx * (int64_t)B.nx;
-    if (bits & 2) s -= dy * (int64_t)B.ny * B.pitch;
-    if (bits & 4) s -= dz * (int64_t)B.nz * B.plane;
-    return s;
+    int sx = x + dx, sy = y + dy, sz = z + dz;
+    const int rx = sx < 0 ? -1 : (sx >= Bp->nx ? 1 : 0);
+    const int ry = sy < 0 ? -1 : (sy >= Bp->ny ? 1 : 0);
+    const int rz = sz < 0 ? -1 : (sz >= Bp->nz ? 1 : 0);
+    int nb = -1;
+    if ((rx | ry | rz) != 0 && Bp->through) nb = Bp->nbr[(rx + 1) + 3 * (ry + 1) + 9 * (rz + 1)];
+    if (nb < 0) return Bp->offset + (int64_t)q * Bp->slab + Bp->cell(sx, sy, sz);
+    const DevBlock *N = blocks + nb;
+    if (rx) sx = rx > 0 ? 0 : N->nx - 1;
+    if (ry) sy = ry > 0 ? 0 : N->ny - 1;
+    if (rz) sz = rz > 0 ? 0 : N->nz - 1;
+    return N->offset + (int64_t)q * N->slab + N->cell(sx, sy, sz);
 }
 
 struct DevTile {
     int32_t block;
     int16_t x0, y0, z0;
-    uint8_t flags;  // bit 0: tile has non-fluid cells
-    uint8_t tx32;   // tile width in cells / 32 (threads per CTA / width = tile height)
+    uint8_t flags;     // bit 0: some cell of the tile has a non-zero mask
+    uint8_t width_m1;  // tile width in cells - 1 (threads per CTA / width = tile height)
 };
 
 struct DevRun {

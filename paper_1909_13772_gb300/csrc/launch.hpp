@@ -23,7 +23,7 @@ struct SweepArgs {
     int kind;   // SweepKind
     int force;  // body force non-zero
     double *partials;  // non-null: write per-CTA diagnostics records (8 doubles per tile)
-    int wrap;          // some block wraps onto itself along a periodic axis
+    int through;       // in-place neighbours: 0 none, 1 only the block itself (wrap), 2 other blocks
     Coll<double> cd;
     Coll<float> cf;
     cudaStream_t stream;
@@ -46,11 +46,13 @@ struct FillArgs {
 // Per-cell kernels over the interior cells of one block (get/set/macroscopic/init).
 struct CellArgs {
     void *a;
+    const DevBlock *blocks;  // device block table
+    int block;               // this block's index in it
     DevBlock blk;
     int layout;  // Layout of the stored state
     double *f64;        // get: out f[Q*N]; set: in; init: rho[N] then u[3N]
     double *rho, *u;    // macroscopic out
-    const uint8_t *mask;
+    const uint32_t *mask;
     double F[3];
     double base[27];
     Coll<double> cd;

@@ -93,8 +93,8 @@ struct BlockOut {
     std::vector<GhostRun> runs_pull, runs_aa;
     int64_t slots_pull = 0, slots_aa = 0;
     std::vector<Tile> tiles;
-    std::vector<uint8_t> mask;
-    int64_t cells = 0, fluid = 0;
+    std::vector<uint32_t> mask;
+    int64_t cells = 0, fluid = 0, bounce = 0;
 };
 
 }  // namespace
@@ -174,10 +174,45 @@ std::string build_plan(const PlanInput &in, Plan &out)
                 }
     }
 
-    std::vector<int> wrapb(nb, 0);
-    for (int b = 0; b < nb; ++b)
-        for (int a = 0; a < 3; ++a)
-            if (in.periodic[a] && blocks[b].origin[a] == lo[a] && blocks[b].n[a] == ext[a]) wrapb[b] |= 1 << a;
+    // neighbour tables: for each region of the ghost shell, the candidate that covers it
+    // exactly (same extent along the axes the region does not cross, adjacent along the
+    // crossed ones), or -1 when no block covers any of it
+    std::vector<std::array<int32_t, 27>> nbrt(nb);
+    std::vector<uint8_t> through(nb, 1);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int b = 0; b < nb; ++b) {
+        const auto &B = blocks[b];
+        for (int r = 0; r < 27; ++r) {
+            nbrt[b][r] = -1;
+            const int rr[3] = {r % 3 - 1, (r / 3) % 3 - 1, r / 9 - 1};
+            if (r == 13) continue;
+            int64_t glo[3], ghi[3];  // region box
+            for (int a = 0; a < 3; ++a) {
+                glo[a] = rr[a] < 0 ? B.origin[a] - 1 : (rr[a] > 0 ? B.origin[a] + B.n[a] : B.origin[a]);
+                ghi[a] = rr[a] < 0 ? B.origin[a] : (rr[a] > 0 ? B.origin[a] + B.n[a] + 1 : B.origin[a] + B.n[a]);
+            }
+            bool exact = false, touched = false;
+            for (const Candidate &cd : cand[b]) {
+                const auto &C = blocks[cd.block];
+                bool ov = true, ex = true;
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t clo = C.origin[a] + cd.shift[a], chi = clo + C.n[a];
+                    ov = ov && clo < ghi[a] && chi > glo[a];
+                    if (rr[a] == 0) ex = ex && clo == B.origin[a] && C.n[a] == B.n[a];
+                    if (rr[a] > 0) ex = ex && clo == B.origin[a] + B.n[a];
+                    if (rr[a] < 0) ex = ex && chi == B.origin[a];
+                }
+                if (!ov) continue;
+                touched = true;
+                if (ex) {
+                    nbrt[b][r] = cd.block;
+                    exact = true;
+                    break;
+                }
+            }
+            if (touched && !exact) through[b] = 0;
+        }
+    }
 
     std::vector<BlockOut> bo(nb);
     std::string err;
@@ -189,21 +224,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
         const int64_t np = (int64_t)px * py * pz;
         // local padded index p(x,y,z) = (x+1) + px ((y+1) + py (z+1))
         auto pidx = [&](int x, int y, int z) { return (int64_t)(x + 1) + px * ((int64_t)(y + 1) + (int64_t)py * (z + 1)); };
-        // wrap a coordinate (at most one cell outside) along the axes the block wraps on;
-        // returns the bits of the axes that were wrapped
-        const int W = wrapb[b];
-        auto wrapc = [&](int &x, int &y, int &z) {
-            int bits = 0;
-            if ((W & 1) && (x < 0 || x >= nx)) { x = x < 0 ? x + nx : x - nx; bits |= 1; }
-            if ((W & 2) && (y < 0 || y >= ny)) { y = y < 0 ? y + ny : y - ny; bits |= 2; }
-            if ((W & 4) && (z < 0 || z >= nz)) { z = z < 0 ? z + nz : z - nz; bits |= 4; }
-            return bits;
-        };
         auto inside = [&](int x, int y, int z) { return x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz; };
-        // ghost cells outside the block along a wrapped axis are never read or written
-        auto wrapped_away = [&](int x, int y, int z) {
-            return ((W & 1) && (x < 0 || x >= nx)) || ((W & 2) && (y < 0 || y >= ny)) || ((W & 4) && (z < 0 || z >= nz));
-        };
         std::vector<uint8_t> kind(np, 255);
         std::vector<uint16_t> param(np, 0);
         std::vector<int32_t> sblock(np, -1);
@@ -280,65 +301,85 @@ std::string build_plan(const PlanInput &in, Plan &out)
                 for (int y = 0; y < ny; ++y)
                     for (int x = 0; x < nx; ++x) {
                         if (kind[pidx(x, y, z)] != K_FLUID) continue;
-                        int tx = x + L.cx[qd], ty = y + L.cy[qd], tz = z + L.cz[qd];
-                        const int bits = wrapc(tx, ty, tz);
-                        int64_t pn = pidx(tx, ty, tz);
+                        int64_t pn = pidx(x + L.cx[qd], y + L.cy[qd], z + L.cz[qd]);
                         uint8_t k = kind[pn];
-                        if (k == K_NOSLIP || k == K_VELOCITY || k == K_PRESSURE)
-                            o.links[k].push_back(pack_link(qd, k, bits, param[pn], b, B.cell(x, y, z)));
+                        // no-slip is applied by the sweep from the cell mask (bounce bits)
+                        if (k == K_VELOCITY || k == K_PRESSURE)
+                            o.links[k].push_back(pack_link(qd, k, param[pn], b, B.cell(x, y, z)));
                     }
         }
-        // ghost runs: for each direction, shell cells mirroring a fluid cell, in (z, y, x) order
+        // ghost runs (only for blocks that cannot read their neighbours in place): for each
+        // direction, shell cells mirroring a fluid cell, in (z, y, x) order
         const int64_t base = B.offset;
-        for (int j = 0; j < L.q; ++j) {
+        for (int j = 0; j < L.q && !through[b]; ++j) {
             for (int z = -1; z <= nz; ++z)
                 for (int y = -1; y <= ny; ++y)
                     for (int x = -1; x <= nx; ++x) {
                         bool shell = x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz;
-                        if (!shell || wrapped_away(x, y, z)) continue;
+                        if (!shell) continue;
                         int64_t p = pidx(x, y, z);
                         if (kind[p] != K_MIRROR) continue;
                         const auto &S = blocks[sblock[p]];
                         int64_t src = S.offset + (int64_t)j * S.slab + scell[p];
                         int64_t dst = base + (int64_t)j * B.slab + B.cell(x, y, z);
-                        // two-grid pull: interior fluid cell wrap(g + c_j) reads slot j of g
+                        // two-grid pull: interior fluid cell g + c_j reads slot j of g
                         int ax = x + L.cx[j], ay = y + L.cy[j], az = z + L.cz[j];
-                        wrapc(ax, ay, az);
                         if (inside(ax, ay, az) && kind[pidx(ax, ay, az)] == K_FLUID) {
                             append_run(o.runs_pull, src, dst, S.pitch, B.pitch);
                             o.slots_pull++;
                         }
-                        // AA: interior fluid cell wrap(g - c_j) reads and writes slot j of g
+                        // AA: interior fluid cell g - c_j reads and writes slot j of g
                         int bx = x - L.cx[j], by = y - L.cy[j], bz = z - L.cz[j];
-                        wrapc(bx, by, bz);
                         if (inside(bx, by, bz) && kind[pidx(bx, by, bz)] == K_FLUID) {
                             append_run(o.runs_aa, src, dst, S.pitch, B.pitch);
                             o.slots_aa++;
                         }
                     }
         }
-        // mask and tiles
-        if (has_solid) {
-            o.mask.assign((size_t)B.slab, (uint8_t)255);
+        // cell masks: non-fluid bit and bounce-back bits (source x - c_i is no-slip)
+        std::vector<uint32_t> cm((size_t)nx * ny * nz, 0u);
+        bool any_mask = has_solid;
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    uint32_t m = 0;
+                    if (kind[pidx(x, y, z)] != K_FLUID) {
+                        m = kCellNotFluid;
+                    } else {
+                        for (int i = 1; i < L.q; ++i) {
+                            // the shell's kinds are those of the cells the ghosts stand for
+                            if (kind[pidx(x - L.cx[i], y - L.cy[i], z - L.cz[i])] == K_NOSLIP) {
+                                m |= 1u << i;
+                                o.bounce++;
+                            }
+                        }
+                    }
+                    any_mask = any_mask || m != 0;
+                    cm[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)] = m;
+                }
+        if (any_mask) {
+            o.mask.assign((size_t)B.slab, kCellNotFluid);
             for (int z = 0; z < nz; ++z)
                 for (int y = 0; y < ny; ++y)
-                    for (int x = 0; x < nx; ++x) o.mask[(size_t)B.cell(x, y, z)] = kind[pidx(x, y, z)];
+                    for (int x = 0; x < nx; ++x)
+                        o.mask[(size_t)B.cell(x, y, z)] = cm[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)];
         }
         const int threads = in.tile[0] * in.tile[1], tz = in.tile[2];
-        const int tx = std::min(in.tile[0], (nx + 31) / 32 * 32), ty = threads / tx;
+        const int tx = nx < threads ? std::min(nx, threads) : in.tile[0], ty = threads / tx;
         for (int z0 = 0; z0 < nz; z0 += tz)
             for (int y0 = 0; y0 < ny; y0 += ty)
                 for (int x0 = 0; x0 < nx; x0 += tx) {
-                    int64_t nfl = 0, ntot = 0;
+                    int64_t nfl = 0;
+                    bool masked = false;
                     for (int z = z0; z < std::min(nz, z0 + tz); ++z)
                         for (int y = y0; y < std::min(ny, y0 + ty); ++y)
                             for (int x = x0; x < std::min(nx, x0 + tx); ++x) {
-                                ++ntot;
                                 nfl += kind[pidx(x, y, z)] == K_FLUID;
+                                masked = masked || cm[(size_t)x + (size_t)nx * ((size_t)y + (size_t)ny * z)] != 0;
                             }
                     if (nfl == 0) continue;
-                    o.tiles.push_back(Tile{b, (int16_t)x0, (int16_t)y0, (int16_t)z0, (uint8_t)(nfl < ntot ? 1 : 0),
-                                           (uint8_t)(tx / 32)});
+                    o.tiles.push_back(Tile{b, (int16_t)x0, (int16_t)y0, (int16_t)z0, (uint8_t)(masked ? 1 : 0),
+                                           (uint8_t)(tx - 1)});
                 }
         o.cells = (int64_t)nx * ny * nz;
         for (int z = 0; z < nz; ++z)
@@ -352,7 +393,8 @@ std::string build_plan(const PlanInput &in, Plan &out)
     out.runs_aa.clear();
     out.tiles.clear();
     out.masks.assign(nb, {});
-    out.wrap = wrapb;
+    out.nbr = nbrt;
+    out.through = through;
     out.cells = out.fluid_cells = 0;
     out.ghost_slots_pull = out.ghost_slots_aa = 0;
     for (int k = 0; k < 4; ++k) out.link_count[k] = 0;
@@ -361,6 +403,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
             out.links.insert(out.links.end(), bo[b].links[k].begin(), bo[b].links[k].end());
             out.link_count[k] += (int64_t)bo[b].links[k].size();
         }
+    for (int b = 0; b < nb; ++b) out.link_count[K_NOSLIP] += bo[b].bounce;
     for (int b = 0; b < nb; ++b) {
         out.runs_pull.insert(out.runs_pull.end(), bo[b].runs_pull.begin(), bo[b].runs_pull.end());
         out.runs_aa.insert(out.runs_aa.end(), bo[b].runs_aa.begin(), bo[b].runs_aa.end());

@@ -12,6 +12,7 @@
 //   * the sweep tile list (which CTA sweeps which cells of which block).
 #pragma once
 
+#include <array>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -48,26 +49,28 @@ struct GhostRun {
     int32_t pad;
 };
 
-// Sweep tile: x0, y0, z0 of a box of one block, tx32 * 32 cells wide, (threads / width)
-// rows high and TZ planes deep; flags bit 0: tile has non-fluid cells (the kernel reads the
-// mask).  The width adapts to the block: min(TX, nx rounded up to 32), the height takes the
-// remaining threads, so narrow blocks do not leave most lanes idle.
+// Sweep tile: x0, y0, z0 of a box of one block, `width` cells wide, (threads / width) rows
+// high and TZ planes deep; flags bit 0: some cell of the tile has a non-zero mask (the kernel
+// reads the mask).  The width adapts to the block: a block narrower than the CTA gets tiles
+// exactly as wide as the block, whose rows follow each other inside a warp, so narrow blocks
+// keep almost every lane busy; wider blocks get tiles TX wide.
 struct Tile {
     int32_t block;
     int16_t x0, y0, z0;
     uint8_t flags;
-    uint8_t tx32;
+    uint8_t width_m1;  // width - 1 (1..256)
 };
 
 // Link word: bits 0-4 direction q (the link points from fluid cell x along c_q into a
-// boundary cell), 5-6 kind, 7-9 wrap bits (x, y, z: the boundary cell x + c_q lies across a
-// face along which the block wraps onto itself, so its slot sits at the wrapped position),
-// 10-17 wall-parameter index, 18-31 block, 32-63 cell index of x in the block's padded layout.
-inline uint64_t pack_link(int q, int kind, int wrapbits, int param, int block, int64_t cell)
+// boundary cell), 5-6 kind, 7-9 reserved (0), 10-17 wall-parameter index, 18-31 block,
+// 32-63 cell index of x in the block's padded layout.  The boundary cell's slot is found at
+// run time like the sweep finds it (own ghost layer, or a neighbour block's cell).
+inline uint64_t pack_link(int q, int kind, int param, int block, int64_t cell)
 {
-    return (uint64_t)q | ((uint64_t)kind << 5) | ((uint64_t)wrapbits << 7) | ((uint64_t)param << 10) |
-           ((uint64_t)block << 18) | ((uint64_t)cell << 32);
+    return (uint64_t)q | ((uint64_t)kind << 5) | ((uint64_t)param << 10) | ((uint64_t)block << 18) |
+           ((uint64_t)cell << 32);
 }
+constexpr uint32_t kCellNotFluid = 1u << 31;  // mask bit 31 (the device side calls it kMaskSolid)
 constexpr int kMaxParams = 256;
 constexpr int kMaxBlocks = 16384;
 
@@ -84,18 +87,26 @@ struct PlanInput {
 };
 
 struct Plan {
-    std::vector<uint64_t> links;           // sorted by (kind, block, q, cell)
-    int64_t link_count[4] = {0, 0, 0, 0};  // by kind
+    std::vector<uint64_t> links;           // velocity and pressure links, sorted by (kind, block, q, cell)
+    int64_t link_count[4] = {0, 0, 0, 0};  // by kind; no-slip ones are the mask bits the sweep applies
     std::vector<WallParam> params;         // wall parameter table (faces first)
     std::vector<GhostRun> runs_pull;       // two-grid: slots j of ghost g with g + c_j fluid interior
     std::vector<GhostRun> runs_aa;         // AA: slots j of ghost g with g - c_j fluid interior
     int64_t ghost_slots_pull = 0, ghost_slots_aa = 0;
     std::vector<Tile> tiles;
-    std::vector<std::vector<uint8_t>> masks;  // per block: padded-layout mask (0 fluid) or empty
-    // per block: bit a set when the block spans a periodic axis a alone, so it is its own
-    // neighbour across both faces of that axis; kernels then wrap neighbour indices along a
-    // and no ghost copy is made there
-    std::vector<int> wrap;
+    // per block: padded-layout cell masks or empty (block with no solid cell and no no-slip
+    // neighbour).  Bit 31: the cell is not fluid.  Bit i (1 <= i < Q): the pull source of
+    // direction i, x - c_i, is a no-slip cell, so the sweep applies halfway bounce-back
+    // itself (f_i(x, t+1) = f*_opp(i)(x, t)) instead of going through a link list.
+    std::vector<std::vector<uint32_t>> masks;
+    // Per block: the block that exactly covers each of the 26 neighbour regions of its
+    // ghost shell (region index (rx+1) + 3 (ry+1) + 9 (rz+1), r = -1/0/+1 per axis; itself
+    // across a periodic axis it spans alone), -1 where the region is outside the domain or
+    // uncovered.  through[b] = 1 when every region is of one of those two kinds: the kernels
+    // then read and write neighbour cells in place (no ghost copies for that block).
+    // Otherwise (faces that do not match one block exactly) the block keeps ghost copies.
+    std::vector<std::array<int32_t, 27>> nbr;
+    std::vector<uint8_t> through;
     int64_t cells = 0, fluid_cells = 0;
 };
 

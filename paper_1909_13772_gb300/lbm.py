@@ -76,7 +76,9 @@ _SIGS = {
     "lbm_plan_links": ([_vp, _u64p, ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_plan_runs": ([_vp, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_plan_layout": ([_vp, ctypes.c_int32, _i64p], ctypes.c_int),
+    "lbm_plan_neighbors": ([_vp, ctypes.c_int32, _i32p], ctypes.c_int),
     "lbm_plan_params": ([_vp, _dp, ctypes.c_int64, _i64p], ctypes.c_int),
+    "lbm_plan_mask": ([_vp, ctypes.c_int32, _P(ctypes.c_uint32), ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_reduce_noalloc": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _dp, _vp, _vp], ctypes.c_int),
     "lbm_last_error": ([_vp], ctypes.c_char_p),
     "lbm_destroy": ([_vp], None),
@@ -264,8 +266,24 @@ def lbm_plan_runs(ctx, pattern) -> np.ndarray:
 def lbm_plan_layout(ctx, block) -> dict:
     out = np.zeros(10, dtype=np.int64)
     _check(ctx, load_library().lbm_plan_layout(ctx, block, _ptr(out, ctypes.c_int64)))
-    keys = ("xo", "pitch", "plane", "slab", "offset", "nx", "ny", "nz", "arena_elems", "wrap")
+    keys = ("xo", "pitch", "plane", "slab", "offset", "nx", "ny", "nz", "arena_elems", "through")
     return {k: int(v) for k, v in zip(keys, out)}
+
+
+def lbm_plan_mask(ctx, block) -> np.ndarray:
+    L = load_library()
+    n = ctypes.c_int64()
+    _check(ctx, L.lbm_plan_mask(ctx, block, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.uint32)
+    if n.value:
+        _check(ctx, L.lbm_plan_mask(ctx, block, _ptr(out, ctypes.c_uint32), n.value, ctypes.byref(n)))
+    return out
+
+
+def lbm_plan_neighbors(ctx, block) -> np.ndarray:
+    out = np.zeros(27, dtype=np.int32)
+    _check(ctx, load_library().lbm_plan_neighbors(ctx, block, _ptr(out, ctypes.c_int32)))
+    return out
 
 
 def lbm_plan_params(ctx) -> np.ndarray:

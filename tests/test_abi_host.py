@@ -79,6 +79,16 @@ class Replay:
         self.A = np.full(self.lay[0]["arena_elems"], np.nan)
         self.links = lbm.lbm_plan_links(sim.ctx)
         self.params = lbm.lbm_plan_params(sim.ctx)
+        self.masks = [lbm.lbm_plan_mask(sim.ctx, b) for b in range(len(sim.blocks))]
+        self.nbr = [lbm.lbm_plan_neighbors(sim.ctx, b) for b in range(len(sim.blocks))]
+
+    def bits(self, b, cells):
+        """Cell masks (bounce-back bits; bit 31 non-fluid) of interior cells, 0 if none."""
+        m = self.masks[b]
+        return m[cells].astype(np.int64) if m.size else np.zeros_like(cells, dtype=np.int64)
+
+    def bounce(self, b, cells, i):
+        return ((self.bits(b, cells) >> i) & 1).astype(bool) if i > 0 else np.zeros(cells.shape, bool)
 
     def cell(self, b, x, y, z):
         L = self.lay[b]
@@ -88,19 +98,37 @@ class Replay:
         L = self.lay[b]
         return self.c[i, 0] + self.c[i, 1] * L["pitch"] + self.c[i, 2] * L["plane"]
 
-    def wrap(self, b, x, y, z, d):
-        """Index shift for neighbour x + d of interior cells (arrays) along self-periodic axes."""
+    def resolve(self, b, x, y, z, d):
+        """(base, slab, cell) of cells (x, y, z) + d of block b: own (ghost) cell, or the
+        neighbour block's cell read in place (first/last layer along crossed axes)."""
         L = self.lay[b]
-        W = L["wrap"]
-        s = np.zeros_like(x, dtype=np.int64)
-        for a, (pos, n, stride) in enumerate(((x, L["nx"], 1), (y, L["ny"], L["pitch"]), (z, L["nz"], L["plane"]))):
-            if not (W >> a) & 1:
-                continue
-            if d[a] > 0:
-                s = s - np.where(pos == n - 1, n * stride, 0)
-            elif d[a] < 0:
-                s = s + np.where(pos == 0, n * stride, 0)
-        return s
+        sx, sy, sz = x + d[0], y + d[1], z + d[2]
+        rx = np.where(sx < 0, -1, np.where(sx >= L["nx"], 1, 0))
+        ry = np.where(sy < 0, -1, np.where(sy >= L["ny"], 1, 0))
+        rz = np.where(sz < 0, -1, np.where(sz >= L["nz"], 1, 0))
+        r = (rx + 1) + 3 * (ry + 1) + 9 * (rz + 1)
+        nb = np.where((r != 13) & bool(L["through"]), self.nbr[b][r], -1)
+        base = np.full(np.shape(sx), L["offset"], dtype=np.int64)
+        slab = np.full(np.shape(sx), L["slab"], dtype=np.int64)
+        cell = self.cell(b, sx, sy, sz)
+        for k in np.unique(nb[nb >= 0]):
+            sel = nb == k
+            N = self.lay[k]
+            xx = np.where(rx[sel] > 0, 0, np.where(rx[sel] < 0, N["nx"] - 1, sx[sel]))
+            yy = np.where(ry[sel] > 0, 0, np.where(ry[sel] < 0, N["ny"] - 1, sy[sel]))
+            zz = np.where(rz[sel] > 0, 0, np.where(rz[sel] < 0, N["nz"] - 1, sz[sel]))
+            base[sel] = N["offset"]
+            slab[sel] = N["slab"]
+            cell[sel] = self.cell(k, xx, yy, zz)
+        return base, slab, cell
+
+    def coords(self, b, cells):
+        L = self.lay[b]
+        z = cells // L["plane"] - 1
+        r = cells - (z + 1) * L["plane"]
+        y = r // L["pitch"] - 1
+        x = r - (y + 1) * L["pitch"] - L["xo"]
+        return x, y, z
 
     def interior(self, b):
         (ox, oy, oz), (nx, ny, nz) = self.sim.blocks[b]
@@ -113,7 +141,10 @@ class Replay:
             return L["offset"] + i * L["slab"] + cells
         if layout == "E":
             return L["offset"] + self.opp[i] * L["slab"] + cells
-        return L["offset"] + i * L["slab"] + cells + self.doff(b, i) + self.wrap(b, *xyz, self.c[i])
+        o = self.opp[i]
+        moved = L["offset"] + o * L["slab"] + cells  # target x + c_i is no-slip: own slot opp(i)
+        base, slab, cell = self.resolve(b, *xyz, self.c[i])
+        return np.where(self.bounce(b, cells, o), moved, base + i * slab + cell)
 
     def put(self, f, fluid, layout):
         for b in range(len(self.sim.blocks)):
@@ -148,31 +179,31 @@ class Replay:
         w = self.links
         q = (w & 31).astype(int)
         kind = ((w >> 5) & 3).astype(int)
-        bits = ((w >> 7) & 7).astype(int)
         par = ((w >> 10) & 255).astype(int)
         blk = ((w >> 18) & 0x3FFF).astype(int)
         cell = (w >> 32).astype(np.int64)
         base = np.array([self.lay[b]["offset"] for b in blk], dtype=np.int64)
         slab = np.array([self.lay[b]["slab"] for b in blk], dtype=np.int64)
-        off = np.array([self.doff(b, qq) for b, qq in zip(blk, q)], dtype=np.int64)
-        for k in range(len(w)):  # wrap the boundary cell back along self-periodic axes
-            L = self.lay[blk[k]]
-            for a, (n, stride) in enumerate(((L["nx"], 1), (L["ny"], L["pitch"]), (L["nz"], L["plane"]))):
-                if (bits[k] >> a) & 1:
-                    off[k] -= self.c[q[k], a] * n * stride
+        # the boundary cell x + c_q, resolved like the kernels do
+        lb_base = np.zeros(len(w), np.int64)
+        lb_slab = np.zeros(len(w), np.int64)
+        lb_cell = np.zeros(len(w), np.int64)
+        for k in range(len(w)):
+            xyz = self.coords(blk[k], np.array([cell[k]]))
+            bb, ss, cc = self.resolve(blk[k], *xyz, self.c[q[k]])
+            lb_base[k], lb_slab[k], lb_cell[k] = bb[0], ss[0], cc[0]
         o = self.opp[q]
         if mode == "pull":
-            src, dst = base + q * slab + cell, base + o * slab + cell + off
+            src, dst = base + q * slab + cell, lb_base + o * lb_slab + lb_cell
         elif mode == "E":
-            src, dst = base + o * slab + cell, base + q * slab + cell + off
+            src, dst = base + o * slab + cell, lb_base + q * lb_slab + lb_cell
         else:
-            src, dst = base + q * slab + cell + off, base + o * slab + cell
+            src, dst = lb_base + q * lb_slab + lb_cell, base + o * slab + cell
         v = self.A[src]
         p = self.params[par]
         cu_w = (self.c[q] * p[:, :3]).sum(axis=1)
-        out = np.where(kind == 1, v, v - 6 * self.w[q] * p[:, 3] * cu_w)
-        assert not (kind == 3).any(), "pressure links are replayed on the GPU tests only"
-        self.A[dst] = out
+        assert (kind == 2).all(), "no-slip is applied in the sweep; pressure links are replayed on the GPU only"
+        self.A[dst] = v - 6 * self.w[q] * p[:, 3] * cu_w
 
     def pull_sweep(self, fluid):
         out = np.zeros((self.q,) + fluid.shape)
@@ -183,8 +214,11 @@ class Replay:
             L = self.lay[b]
             xyz = (x[keep], y[keep], z[keep])
             for i in range(self.q):
+                bb, ss, cc = self.resolve(b, *xyz, -self.c[i])
+                normal = bb + i * ss + cc
+                bounced = L["offset"] + self.opp[i] * L["slab"] + cells
                 out[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]] = \
-                    self.A[L["offset"] + i * L["slab"] + cells - self.doff(b, i) + self.wrap(b, *xyz, -self.c[i])]
+                    self.A[np.where(self.bounce(b, cells, i), bounced, normal)]
         return out
 
 
@@ -202,8 +236,10 @@ def _replay_aa_step(R, fluid, phase):
             L = R.lay[b]
             xyz = (x[keep], y[keep], z[keep])
             for i in range(R.q):
-                f[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]] = \
-                    R.A[L["offset"] + R.opp[i] * L["slab"] + cells - R.doff(b, i) + R.wrap(b, *xyz, -R.c[i])]
+                bb, ss, cc = R.resolve(b, *xyz, -R.c[i])
+                normal = bb + R.opp[i] * ss + cc
+                bounced = L["offset"] + i * L["slab"] + cells  # E layout keeps f*_opp(i)(x) there
+                f[i, (z + oz)[keep], (y + oy)[keep], (x + ox)[keep]] = R.A[np.where(R.bounce(b, cells, i), bounced, normal)]
         R.put(f, fluid, "O")
         return f
     R.fill_links("O")
@@ -288,11 +324,45 @@ def test_replayed_lists_stream_like_oracle(q, layout, walls):
     sim.close()
 
 
+@pytest.mark.parametrize("q", [19, 27])
+def test_replayed_lists_mixed_in_place_and_ghost_blocks(q):
+    """Block 0 matches its neighbours exactly and reads them in place; blocks 1-3 meet
+    faces that match no single block and keep ghost copies.  x has a no-slip and a moving
+    wall, y and z are periodic."""
+    blocks = [((0, 0, 0), (3, 4, 4)), ((3, 0, 0), (3, 4, 4)), ((6, 0, 0), (4, 4, 2)), ((6, 0, 2), (4, 4, 2))]
+    shape = (10, 4, 4)
+    periodic = (0, 1, 1)
+    faces = (lbm.NOSLIP, lbm.VELOCITY, 1, 1, 1, 1)
+    uw = (0.0, 0.02, -0.01)
+    nx, ny, nz = shape
+    flags = np.zeros((nz, ny, nx), np.uint8)
+    flags[1, 2, 4] = lbm.NOSLIP
+    fluid = flags == 0
+    f0 = np.random.default_rng(5).random((q, nz, ny, nx))
+    f0[:, ~fluid] = 0.0
+    op = _oracle_params(q, shape, periodic, faces, uw)
+    want1 = oracle.run(op, f0, 1, flags=flags)
+    want2 = oracle.run(op, want1, 1, flags=flags)
+    for pattern in (lbm.TWO_GRID, lbm.AA):
+        sim = _setup(q, blocks, shape, periodic, faces, flags, pattern, uw)
+        assert [lbm.lbm_plan_layout(sim.ctx, b)["through"] for b in range(4)] == [1, 0, 0, 0]
+        R = Replay(sim, q, shape)
+        if pattern == lbm.TWO_GRID:
+            R.put(f0, fluid, "pull")
+            R.fill_links("pull")
+            R.runs(lbm.TWO_GRID)
+            np.testing.assert_array_equal(R.pull_sweep(fluid)[:, fluid], want1[:, fluid])
+        else:
+            R.put(f0, fluid, "E")
+            np.testing.assert_array_equal(_replay_aa_step(R, fluid, "E")[:, fluid], want1[:, fluid])
+            np.testing.assert_array_equal(_replay_aa_step(R, fluid, "O")[:, fluid], want2[:, fluid])
+        sim.close()
+
+
 def test_channel_link_and_ghost_counts():
-    """Channel (walls in y, periodic x/z), D3Q19: 5 wall links per wall cell and wall.  One
-    block spanning x and z wraps onto itself: no ghost copies.  Split into two blocks along x,
-    each still spans z alone (wraps in z) and copies, per x-face ghost cell, the directions
-    that enter the neighbour (wrapping z)."""
+    """Channel (walls in y, periodic x/z), D3Q19: 5 wall links per wall cell and wall (applied
+    in the sweep).  One block spanning x and z is its own neighbour: no ghost copies; split
+    into two halves along x, each reads the other in place."""
     nx, ny, nz = 16, 12, 8
     p = lbm.make_params(stencil=19, periodic=(1, 0, 1))
     sim = lbm.Simulation(p, [((0, 0, 0), (nx, ny, nz))])
@@ -300,19 +370,30 @@ def test_channel_link_and_ghost_counts():
     assert info["links"][lbm.NOSLIP] == 2 * 5 * nx * nz
     assert info["cells"] == info["fluid_cells"] == nx * ny * nz
     assert info["ghost_slots"] == 0 and info["ghost_runs"] == 0
-    assert lbm.lbm_plan_layout(sim.ctx, 0)["wrap"] == 0b101
+    assert lbm.lbm_plan_layout(sim.ctx, 0)["through"] == 1
+    nbr = lbm.lbm_plan_neighbors(sim.ctx, 0)
+    for r in range(27):
+        rx, ry, rz = r % 3 - 1, (r // 3) % 3 - 1, r // 9 - 1
+        assert nbr[r] == (-1 if (ry != 0 or r == 13) else 0)
+    assert lbm.lbm_plan_links(sim.ctx).size == 0  # no-slip is applied in the sweep
+    m = lbm.lbm_plan_mask(sim.ctx, 0)
+    L = lbm.lbm_plan_layout(sim.ctx, 0)
+    c, _, _ = lbm.lbm_stencil_table(19)
+    bottom = m[(0 + 1) * L["plane"] + (0 + 1) * L["pitch"] + L["xo"] + 3]
+    want = sum(1 << i for i in range(1, 19) if c[i, 1] == 1)  # sources at y = -1
+    assert bottom == want
     sim.close()
     half = nx // 2
     sim = lbm.Simulation(p, [((0, 0, 0), (half, ny, nz)), ((half, 0, 0), (half, ny, nz))])
     info = sim.info()
     assert info["links"][lbm.NOSLIP] == 2 * 5 * nx * nz
-    c, _, _ = lbm.lbm_stencil_table(19)
-    slots = 0
-    for gx in (-1, half):
-        for y in range(ny):
-            for z in range(nz):
-                for i in range(19):
-                    ax, ay, az = gx + c[i, 0], y + c[i, 1], (z + c[i, 2]) % nz
-                    slots += (0 <= ax < half) and (0 <= ay < ny)
-    assert info["ghost_slots"] == 2 * slots
+    # the halves meet exactly (and wrap around x onto each other): both read in place
+    assert info["ghost_slots"] == 0
+    for b in (0, 1):
+        assert lbm.lbm_plan_layout(sim.ctx, b)["through"] == 1
+        nbr = lbm.lbm_plan_neighbors(sim.ctx, b)
+        region = lambda rx, ry, rz: (rx + 1) + 3 * (ry + 1) + 9 * (rz + 1)  # noqa: E731
+        assert nbr[region(-1, 0, 0)] == 1 - b and nbr[region(1, 0, 0)] == 1 - b
+        assert nbr[region(0, 0, -1)] == b and nbr[region(0, 0, 1)] == b  # itself (periodic)
+        assert nbr[region(0, 1, 0)] == -1 and nbr[region(1, -1, 0)] == -1  # walls
     sim.close()

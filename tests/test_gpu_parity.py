@@ -238,7 +238,7 @@ def test_bound_torch_buffer_and_stream():
     sim.init(0, rho, u)
     sim.step(6)
     got = sim.pdfs(0)
-    assert sim.launches() == 12
+    assert sim.launches() == 6  # one sweep per step: no-slip walls need no fill launch
     sim.close()
     case.omega = 1.3
     _, want = oracle_run(case, rho, u, 6)
