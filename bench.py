@@ -381,11 +381,24 @@ def run_porous(args):
         rho, u = inputs.rest(sz)
         sim.init(b, rho, u)
     t_init = time.perf_counter() - t0
+    if args.per_block:
+        lbm.lbm_set_batching(sim.ctx, False)
+    tuned = None
+    if args.autotune:
+        tuned = lbm.lbm_autotune(sim.ctx, 10)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     barrier(world)
+    # per-kernel times from the library's tracing (plain launches)
     lbm.lbm_read_timing(sim.ctx, reset=True)
     lbm.lbm_enable_timing(sim.ctx, True)
+    sim.step(min(args.steps, 50))
+    lbm.lbm_enable_timing(sim.ctx, False)
+    kt = lbm.lbm_read_timing(sim.ctx, reset=True)
+    if args.graph:
+        lbm.lbm_set_graph(sim.ctx, True)
+        sim.step(3)  # capture
+    torch.cuda.synchronize()
     sampler = ClockSampler(torch.cuda.current_device())
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     start.record(stream)
@@ -393,8 +406,6 @@ def run_porous(args):
     end.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    lbm.lbm_enable_timing(sim.ctx, False)
-    kt = lbm.lbm_read_timing(sim.ctx, reset=True)
     ms = start.elapsed_time(end)
     diag = sim.step_diagnostics()
     sim.close()
@@ -420,7 +431,102 @@ def run_porous(args):
                         "unit": "GB/s", "frac": round(alg / (sweep_ms / 1e3) / 1e9 / peak, 4), "traffic": None,
                         "kernel": "k_sweep (fluid cells only)", "sweep_ms": round(sweep_ms, 4),
                         "fill_ms": round(fill_ms, 4)},
-           "clocks": clocks, "finite": diag["nonfinite"] == 0, "max_speed": diag["max_speed"]}
+           "clocks": clocks, "finite": diag["nonfinite"] == 0, "max_speed": diag["max_speed"],
+           "graph": bool(args.graph), "autotuned_tile": list(tuned[0]) if tuned else None,
+           "launch": "one sweep launch per block" if args.per_block else "one batched sweep launch"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def _spectrum(u):
+    """Shell-averaged kinetic-energy spectrum E(k), k = 1..n/2, of a periodic u[3, z, y, x]."""
+    n = u.shape[-1]
+    uh = np.stack([np.fft.rfftn(u[a]) for a in range(3)]) / n ** 3
+    e = 0.5 * (np.abs(uh) ** 2).sum(axis=0)
+    e[..., 1:] *= 2.0  # half spectrum along x: count the conjugate modes
+    kf = np.fft.fftfreq(n, d=1.0 / n)
+    kr = np.fft.rfftfreq(n, d=1.0 / n)
+    KZ, KY, KX = np.meshgrid(kf, kf, kr, indexing="ij")
+    shell = np.rint(np.sqrt(KX * KX + KY * KY + KZ * KZ)).astype(int)
+    return np.bincount(shell.ravel(), weights=e.ravel(), minlength=n)[1:n // 2 + 1]
+
+
+def run_turbulence(args):
+    """Decaying turbulence, D3Q27 TRT (Lambda = 3/16), tau = 0.52, periodic box, random-phase
+    solenoidal k^(-5/3) start (default_rng(1909), shells 1..32, max|u| = 0.05), rho = 1.
+    Throughput: 512^3 for each storage variant.  Error: the same run at 256^3 for the
+    configured steps in every storage variant, compared field by field with the GPU FP64 run."""
+    import torch
+    rank, world, local = dist_setup()
+    from paper_1909_13772_gb300 import inputs, lbm
+    lbm.load_library()
+    variants = [("FP64", "f64"), ("FP32", "f32"), ("FP16_DEV", "f16-dev"), ("BF16_DEV", "bf16-dev")]
+    stream = torch.cuda.Stream()
+
+    def make(n, storage):
+        p = lbm.make_params(stencil=lbm.D3Q27, collision=lbm.TRT, storage=getattr(lbm, storage), pattern=lbm.AA,
+                            omega=1 / 0.52, magic_lambda=LAMBDA, periodic=(1, 1, 1))
+        return lbm.Simulation(p, [((0, 0, 0), (n, n, n))], stream=stream.cuda_stream)
+
+    # throughput at 512^3
+    n_perf, perf_steps = args.turb_size, min(args.steps, 200)
+    t0 = time.perf_counter()
+    rho, u = inputs.turbulence(n_perf, seed=1909, kmax=32, umax=0.05)
+    t_gen = time.perf_counter() - t0
+    perf = {}
+    for storage, name in variants:
+        if storage == "FP64" and not args.turb_fp64_perf:
+            continue
+        sim = make(n_perf, storage)
+        sim.init(0, rho, u)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        sim.step(perf_steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        ms = start.elapsed_time(end) / perf_steps
+        info = sim.info()
+        sim.close()
+        alg = 2 * 27 * info["bytes_per_pdf"] * info["cells"]
+        perf[name] = {"mlups": round(info["cells"] / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
+                      "gbs": round(alg / (ms / 1e3) / 1e9, 1)}
+    del rho, u
+    # per-field error at the error-study size
+    n = args.turb_err_size
+    rho, u = inputs.turbulence(n, seed=1909, kmax=32, umax=0.05)
+    fields = {}
+    for storage, name in variants:
+        sim = make(n, storage)
+        sim.init(0, rho, u)
+        d0 = sim.reduce()
+        sim.step(args.steps)
+        r, v = sim.macroscopic(0)
+        d1 = sim.reduce()
+        sim.close()
+        fields[name] = (r, v, d0, d1)
+    r64, v64, d064, d164 = fields["f64"]
+    e64 = _spectrum(v64)
+    err = {}
+    for name, (r, v, d0, d1) in fields.items():
+        e = _spectrum(v)
+        err[name] = {
+            "rho": float(np.abs(r - r64).max() / np.abs(r64 - 1.0).max()),
+            "u": float(np.abs(v - v64).max() / np.abs(v64).max()),
+            "kinetic_energy": float(d1["kinetic_energy"] / d164["kinetic_energy"] - 1.0),
+            "spectrum_l2": float(np.sqrt(((e - e64) ** 2).sum() / (e64 ** 2).sum())),
+            "mass_drift": float(d1["mass"] / d0["mass"] - 1.0),
+            "momentum_drift": float(max(abs(a - b) for a, b in zip(d1["momentum"], d0["momentum"])) / d0["mass"]),
+        }
+    out = {"metric": "MLUPS per storage variant and per-field error vs the FP64 run, decaying turbulence",
+           "value": perf.get("f32", {}).get("mlups"), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "data": "synthetic (seeded random-phase field)",
+           "config": {"workload": "D3Q27 TRT tau=0.52 periodic decaying turbulence, k^-5/3 random-phase start, "
+                                  "max|u| = 0.05, AA pattern", "throughput_size": n_perf,
+                      "throughput_steps": perf_steps, "error_size": n, "error_steps": args.steps,
+                      "generator_s": round(t_gen, 1)},
+           "throughput": perf, "error_vs_fp64": err}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -467,8 +573,15 @@ def main(argv=None):
     ap.add_argument("--variant", choices=list(VARIANTS), default="fp32-twogrid")
     ap.add_argument("--headline-only", action="store_true", help="skip the other variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["channel", "porous"], default="channel",
-                    help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed")
+    ap.add_argument("--graph", action="store_true", help="porous: replay step pairs as CUDA graphs")
+    ap.add_argument("--autotune", action="store_true", help="porous: pick the sweep tile with lbm_autotune")
+    ap.add_argument("--per-block", action="store_true", help="porous: one sweep launch per block (comparison)")
+    ap.add_argument("--workload", choices=["channel", "porous", "turbulence"], default="channel",
+                    help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed; "
+                         "turbulence: D3Q27 decaying turbulence, storage variants and their errors")
+    ap.add_argument("--turb-size", type=int, default=512)
+    ap.add_argument("--turb-err-size", type=int, default=256)
+    ap.add_argument("--turb-fp64-perf", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -476,6 +589,8 @@ def main(argv=None):
         run_reference(args)
     elif args.workload == "porous":
         run_porous(args)
+    elif args.workload == "turbulence":
+        run_turbulence(args)
     else:
         run_ours(args)
 

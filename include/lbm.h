@@ -203,6 +203,24 @@ lbm_status lbm_set_tile(lbm_ctx *ctx, int32_t tx, int32_t ty, int32_t tz);
 lbm_status lbm_enable_timing(lbm_ctx *ctx, int32_t enable);
 lbm_status lbm_read_timing(lbm_ctx *ctx, double ms[2], int64_t count[2], int32_t reset);
 
+/* batched = 1 (default): one sweep launch per step covers the tiles of every block.
+ * batched = 0: one sweep launch per block, as a per-block sweep would be issued; results are
+ * bitwise the same (kept to measure what batching gains). */
+lbm_status lbm_set_batching(lbm_ctx *ctx, int32_t batched);
+
+/* Graph mode: lbm_step replays pairs of steps as one captured CUDA graph (one graph per
+ * starting parity, re-captured after the lists change); the last step of each call and the
+ * diag_interval steps run as ordinary launches.  Needs a context created with a non-default
+ * stream.  Per-kernel tracing (lbm_enable_timing) bypasses the graphs.  Errors:
+ * LBM_ERR_UNSUPPORTED on the default stream. */
+lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t enable);
+
+/* Autotuner: times trial_steps steps for each candidate sweep tile shape (a fixed list from
+ * 256x1x2 to 32x8x4), keeps the fastest (best[3], and its time per step in *best_ms if
+ * non-NULL) and restores the simulation state exactly (the PDF arrays are snapshot to a
+ * temporary device buffer, which is cudaMalloc'd).  The step count and parity are unchanged. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trial_steps, int32_t best[3], double *best_ms);
+
 /* Number of kernels lbm_step launched since the context was created. */
 int64_t lbm_kernel_launches(const lbm_ctx *ctx);
 

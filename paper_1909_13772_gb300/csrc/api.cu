@@ -67,6 +67,16 @@ struct lbm_ctx {
     int64_t steps_done = 0;
     std::string err;
 
+    // per-block launches (one sweep launch per block instead of one batched launch)
+    bool per_block = false;
+    std::vector<int64_t> tile_start;  // first tile of each block (+ total at the end)
+
+    // CUDA-graph replay of step pairs (graph mode): one executable graph per starting parity
+    bool graph_mode = false;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_epoch[2] = {-1, -1};
+    int64_t list_epoch = 0;  // bumped whenever device lists are (re)uploaded
+
     // tracing: events around fill and sweep launches (pairs of [start, end])
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -271,7 +281,11 @@ lbm_status ensure_lists(lbm_ctx *c)
         c->partials_cap = need;
     }
     c->step_diag_valid = false;
+    c->tile_start.assign(c->blocks.size() + 1, 0);
+    for (const Tile &t : P.tiles) c->tile_start[t.block + 1]++;
+    for (size_t b = 0; b < c->blocks.size(); ++b) c->tile_start[b + 1] += c->tile_start[b];
     c->plan_uploaded = true;
+    c->list_epoch++;
     return LBM_OK;
 }
 
@@ -492,14 +506,13 @@ lbm_status lbm_init_macroscopic(lbm_ctx *c, int32_t block, const double *rho, co
     return LBM_OK;
 }
 
-lbm_status lbm_step(lbm_ctx *c, int64_t n)
+namespace {
+
+// Launch arguments of a step that do not change from step to step.
+void step_args(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
 {
-    if (!c) return LBM_ERR_ARG;
-    if (n < 0) return fail(c, LBM_ERR_ARG, "negative step count");
-    lbm_status s = prepare(c);
-    if (s != LBM_OK) return s;
     const Plan &P = c->plan;
-    SweepArgs sw{};
+    sw = SweepArgs{};
     sw.blocks = c->d_blocks;
     sw.tiles = c->d_tiles;
     sw.ntiles = (int64_t)P.tiles.size();
@@ -519,7 +532,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
     sw.cd = c->cd;
     sw.cf = c->cf;
     sw.stream = c->stream;
-    FillArgs fa{};
+    fa = FillArgs{};
     fa.blocks = c->d_blocks;
     fa.links = c->d_links;
     fa.nlinks = (int64_t)P.links.size();
@@ -527,59 +540,239 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
     for (int a = 0; a < 3; ++a) fa.F[a] = c->p.force[a];
     for (int i = 0; i < 27; ++i) fa.base[i] = c->base[i];
     fa.stream = c->stream;
-    for (int64_t t = 0; t < n; ++t) {
-        if (c->pattern == LBM_TWO_GRID) {
-            fa.a = c->arr[c->cur];
-            fa.mode = FILL_PULL;
-            fa.runs = c->d_runs_pull;
-            fa.nruns = (int64_t)P.runs_pull.size();
-            sw.a = c->arr[c->cur];
-            sw.b = c->arr[1 - c->cur];
-            sw.kind = SWEEP_PULL;
-        } else {
-            const bool even = c->aa_layout == LAYOUT_AA_E;
-            fa.a = c->arr[0];
-            fa.mode = even ? FILL_AA_E : FILL_AA_O;
-            fa.runs = c->d_runs_aa;
-            fa.nruns = (int64_t)P.runs_aa.size();
-            sw.a = c->arr[0];
-            sw.b = nullptr;
-            sw.kind = even ? SWEEP_AA_NBR : SWEEP_AA_LOCAL;
-        }
-        int e0 = -1, e1 = -1, e2 = -1;
-        if (c->timing && (s = mark(c, &e0)) != LBM_OK) return s;
-        if (fa.nlinks + fa.nruns > 0) {
-            CK(do_fill(c->q, c->storage, fa), "boundary/ghost fill launch");
+}
+
+// Issue one step (fill if needed, then the sweep) on the context's stream and advance the
+// layout parity.  diag: the sweep writes the step diagnostics.
+lbm_status issue_step(lbm_ctx *c, SweepArgs &sw, FillArgs &fa, bool diag, bool trace)
+{
+    const Plan &P = c->plan;
+    lbm_status s = LBM_OK;
+    if (c->pattern == LBM_TWO_GRID) {
+        fa.a = c->arr[c->cur];
+        fa.mode = FILL_PULL;
+        fa.runs = c->d_runs_pull;
+        fa.nruns = (int64_t)P.runs_pull.size();
+        sw.a = c->arr[c->cur];
+        sw.b = c->arr[1 - c->cur];
+        sw.kind = SWEEP_PULL;
+    } else {
+        const bool even = c->aa_layout == LAYOUT_AA_E;
+        fa.a = c->arr[0];
+        fa.mode = even ? FILL_AA_E : FILL_AA_O;
+        fa.runs = c->d_runs_aa;
+        fa.nruns = (int64_t)P.runs_aa.size();
+        sw.a = c->arr[0];
+        sw.b = nullptr;
+        sw.kind = even ? SWEEP_AA_NBR : SWEEP_AA_LOCAL;
+    }
+    int e0 = -1, e1 = -1, e2 = -1;
+    if (trace && (s = mark(c, &e0)) != LBM_OK) return s;
+    if (fa.nlinks + fa.nruns > 0) {
+        CK(do_fill(c->q, c->storage, fa), "boundary/ghost fill launch");
+        c->launches++;
+    }
+    if (trace && (s = mark(c, &e1)) != LBM_OK) return s;
+    sw.partials = diag ? c->d_step_partials : nullptr;
+    if (sw.ntiles > 0 && c->per_block) {
+        // one launch per block over its own tile range (comparison mode)
+        SweepArgs one = sw;
+        for (size_t b = 0; b + 1 < c->tile_start.size(); ++b) {
+            one.tiles = sw.tiles + c->tile_start[b];
+            one.ntiles = c->tile_start[b + 1] - c->tile_start[b];
+            one.partials = diag ? c->d_step_partials + 8 * c->tile_start[b] : nullptr;
+            if (one.ntiles == 0) continue;
+            CK(do_sweep(c->q, c->storage, one), "sweep launch");
             c->launches++;
         }
-        if (c->timing && (s = mark(c, &e1)) != LBM_OK) return s;
-        const bool diag_due = c->p.diag_interval > 0 && (c->steps_done + 1) % c->p.diag_interval == 0;
-        sw.partials = (t == n - 1 || diag_due) ? c->d_step_partials : nullptr;
-        if (sw.ntiles > 0) {
-            CK(do_sweep(c->q, c->storage, sw), "sweep launch");
-            c->launches++;
+    } else if (sw.ntiles > 0) {
+        CK(do_sweep(c->q, c->storage, sw), "sweep launch");
+        c->launches++;
+    }
+    if (trace) {
+        if ((s = mark(c, &e2)) != LBM_OK) return s;
+        if (fa.nlinks + fa.nruns > 0) c->ev_marks[0].push_back({e0, e1});
+        if (sw.ntiles > 0) c->ev_marks[1].push_back({e1, e2});
+    }
+    if (c->pattern == LBM_TWO_GRID)
+        c->cur = 1 - c->cur;
+    else
+        c->aa_layout = c->aa_layout == LAYOUT_AA_E ? LAYOUT_AA_O : LAYOUT_AA_E;
+    return LBM_OK;
+}
+
+int parity(const lbm_ctx *c) { return c->pattern == LBM_TWO_GRID ? c->cur : (c->aa_layout == LAYOUT_AA_E ? 0 : 1); }
+
+void drop_graphs(lbm_ctx *c)
+{
+    for (int k = 0; k < 2; ++k) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        c->graph_epoch[k] = -1;
+    }
+}
+
+// Two steps (no diagnostics) as one CUDA-graph launch; the pair ends in the parity it started
+// from, so one graph per starting parity serves every later pair.
+lbm_status graph_pair(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
+{
+    const int k = parity(c);
+    if (!c->graph[k] || c->graph_epoch[k] != c->list_epoch) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        c->graph[k] = nullptr;
+        const int64_t launches = c->launches;
+        const int cur = c->cur, lay = c->aa_layout;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "begin graph capture");
+        lbm_status s1 = issue_step(c, sw, fa, false, false);
+        lbm_status s2 = s1 == LBM_OK ? issue_step(c, sw, fa, false, false) : s1;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->launches = launches;  // captured, not yet run
+        c->cur = cur;
+        c->aa_layout = lay;
+        if (s2 != LBM_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s2;
         }
-        c->step_diag_valid = sw.partials != nullptr;
-        if (c->timing) {
-            if ((s = mark(c, &e2)) != LBM_OK) return s;
-            if (fa.nlinks + fa.nruns > 0) c->ev_marks[0].push_back({e0, e1});
-            if (sw.ntiles > 0) c->ev_marks[1].push_back({e1, e2});
+        if (e != cudaSuccess) return cuda_fail(c, e, "end graph capture");
+        e = cudaGraphInstantiate(&c->graph[k], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "instantiate step graph");
+        c->graph_epoch[k] = c->list_epoch;
+    }
+    CK(cudaGraphLaunch(c->graph[k], c->stream), "graph launch");
+    // account for the two steps the graph ran
+    const Plan &P = c->plan;
+    const int64_t sweeps = c->per_block ? (int64_t)c->blocks.size() : 1;
+    const int64_t per_step = (sw.ntiles > 0 ? sweeps : 0) +
+                             ((P.links.size() + (c->pattern == LBM_TWO_GRID ? P.runs_pull.size() : P.runs_aa.size())) > 0 ? 1 : 0);
+    c->launches += 2 * per_step;
+    return LBM_OK;
+}
+
+lbm_status check_diag(lbm_ctx *c)
+{
+    lbm_diagnostics d;
+    lbm_status r = lbm_step_diagnostics(c, &d);
+    if (r != LBM_OK) return r;
+    if (d.nonfinite > 0 || !std::isfinite(d.mass))
+        return fail(c, LBM_ERR_DIVERGED, "non-finite state after step %lld (%lld cells)", (long long)c->steps_done,
+                    (long long)d.nonfinite);
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_step(lbm_ctx *c, int64_t n)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (n < 0) return fail(c, LBM_ERR_ARG, "negative step count");
+    lbm_status s = prepare(c);
+    if (s != LBM_OK) return s;
+    SweepArgs sw;
+    FillArgs fa;
+    step_args(c, sw, fa);
+    const int64_t di = c->p.diag_interval;
+    const bool graphs = c->graph_mode && c->stream != nullptr && !c->timing;
+    for (int64_t t = 0; t < n;) {
+        // diagnostics on the call's last step and on every diag_interval-th step
+        auto diag_at = [&](int64_t k) { return k == n - 1 || (di > 0 && (c->steps_done + (k - t) + 1) % di == 0); };
+        if (graphs && t + 2 <= n - 1 && !diag_at(t) && !diag_at(t + 1)) {
+            if ((s = graph_pair(c, sw, fa)) != LBM_OK) return s;
+            c->steps_done += 2;
+            c->step_diag_valid = false;
+            t += 2;
+            continue;
         }
-        if (c->pattern == LBM_TWO_GRID)
-            c->cur = 1 - c->cur;
-        else
-            c->aa_layout = c->aa_layout == LAYOUT_AA_E ? LAYOUT_AA_O : LAYOUT_AA_E;
+        const bool diag = diag_at(t);
+        if ((s = issue_step(c, sw, fa, diag, c->timing)) != LBM_OK) return s;
+        c->step_diag_valid = diag;
         c->steps_done++;
-        if (c->p.diag_interval > 0 && c->steps_done % c->p.diag_interval == 0) {
-            lbm_diagnostics d;
-            lbm_status r = lbm_step_diagnostics(c, &d);
-            if (r != LBM_OK) return r;
-            if (d.nonfinite > 0 || !std::isfinite(d.mass))
-                return fail(c, LBM_ERR_DIVERGED, "non-finite state after step %lld (%lld cells)", (long long)c->steps_done,
-                            (long long)d.nonfinite);
-        }
+        ++t;
+        if (di > 0 && c->steps_done % di == 0 && (s = check_diag(c)) != LBM_OK) return s;
     }
     return LBM_OK;
+}
+
+lbm_status lbm_set_batching(lbm_ctx *c, int32_t batched)
+{
+    if (!c) return LBM_ERR_ARG;
+    c->per_block = batched == 0;
+    drop_graphs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_graph(lbm_ctx *c, int32_t enable)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (enable && c->stream == nullptr)
+        return fail(c, LBM_ERR_UNSUPPORTED, "graph mode needs a non-default stream (capture is not allowed on stream 0)");
+    c->graph_mode = enable != 0;
+    if (!enable) drop_graphs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], double *best_ms)
+{
+    if (!c || !best) return LBM_ERR_ARG;
+    if (trial_steps < 1) return fail(c, LBM_ERR_ARG, "trial_steps must be >= 1");
+    lbm_status s = prepare(c);
+    if (s != LBM_OK) return s;
+    // keep the simulation state: snapshot the PDF arrays and restore them afterwards
+    const int narr = c->pattern == LBM_TWO_GRID ? 2 : 1;
+    const size_t bytes1 = (size_t)c->arena_elems * c->bpp;
+    void *snap = nullptr;
+    CK(cudaMalloc(&snap, narr * bytes1), "cudaMalloc(autotune snapshot)");
+    for (int k = 0; k < narr; ++k)
+        CK(cudaMemcpyAsync((char *)snap + k * bytes1, c->arr[k], bytes1, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
+    const int cur = c->cur, lay = c->aa_layout;
+    const int64_t steps_done = c->steps_done, launches = c->launches;
+    const bool diag_valid = c->step_diag_valid, timing = c->timing;
+    const int old[3] = {c->tile[0], c->tile[1], c->tile[2]};
+    static const int cand[][3] = {{256, 1, 4}, {256, 1, 2}, {256, 1, 8}, {256, 1, 16}, {128, 2, 4}, {128, 2, 8},
+                                  {64, 4, 4},  {64, 4, 8},  {32, 8, 4},  {128, 1, 8},  {64, 2, 8}, {64, 1, 16}};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0), "event");
+    CK(cudaEventCreate(&e1), "event");
+    float best_t = 1e30f;
+    int bi = -1;
+    c->timing = false;
+    for (int k = 0; k < (int)(sizeof cand / sizeof cand[0]); ++k) {
+        c->tile[0] = cand[k][0];
+        c->tile[1] = cand[k][1];
+        c->tile[2] = cand[k][2];
+        c->plan_built = false;
+        if ((s = prepare(c)) != LBM_OK) break;
+        if ((s = lbm_step(c, 2)) != LBM_OK) break;
+        CK(cudaEventRecord(e0, c->stream), "event");
+        if ((s = lbm_step(c, trial_steps)) != LBM_OK) break;
+        CK(cudaEventRecord(e1, c->stream), "event");
+        CK(cudaEventSynchronize(e1), "event");
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1), "event");
+        if (ms < best_t) {
+            best_t = ms;
+            bi = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const int *pick = bi >= 0 ? cand[bi] : old;
+    for (int a = 0; a < 3; ++a) c->tile[a] = best[a] = pick[a];
+    c->plan_built = false;
+    lbm_status s2 = prepare(c);
+    for (int k = 0; k < narr; ++k)
+        CK(cudaMemcpyAsync(c->arr[k], (char *)snap + k * bytes1, bytes1, cudaMemcpyDeviceToDevice, c->stream), "restore");
+    CK(cudaStreamSynchronize(c->stream), "autotune restore");
+    cudaFree(snap);
+    c->cur = cur;
+    c->aa_layout = lay;
+    c->steps_done = steps_done;
+    c->launches = launches;
+    c->step_diag_valid = diag_valid;
+    c->timing = timing;
+    if (best_ms) *best_ms = bi >= 0 ? best_t / trial_steps : 0.0;
+    return s != LBM_OK ? s : s2;
 }
 
 lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u)
@@ -892,6 +1085,7 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_out);
     dfree(c->d_scratch);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    drop_graphs(c);
     delete c;
 }
 

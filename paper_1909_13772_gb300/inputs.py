@@ -84,6 +84,13 @@ def turbulence(n: int, seed: int = 1909, kmax: int = 32, umax: float = 0.05, dty
     with np.errstate(invalid="ignore", divide="ignore"):
         uh = uh - kv * np.where(k2 > 0, kdotu / np.where(k2 > 0, k2, 1.0), 0.0)[None]
     u = np.stack([np.fft.irfftn(uh[a], s=(n, n, n), axes=(0, 1, 2)) for a in range(3)])
+    # the real part of a half spectrum is not exactly Hermitian on the kx = 0 and Nyquist
+    # planes: project the real field once more so it is solenoidal to rounding
+    uh = np.stack([np.fft.rfftn(u[a], axes=(0, 1, 2)) for a in range(3)])
+    kdotu = (kv * uh).sum(axis=0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        uh = uh - kv * np.where(k2 > 0, kdotu / np.where(k2 > 0, k2, 1.0), 0.0)[None]
+    u = np.stack([np.fft.irfftn(uh[a], s=(n, n, n), axes=(0, 1, 2)) for a in range(3)])
     speed = np.sqrt((u * u).sum(axis=0)).max()
     u *= umax / speed
     return np.ones((n, n, n), dtype=dtype), u.astype(dtype)

@@ -70,6 +70,9 @@ _SIGS = {
     "lbm_get_info": ([_vp, _P(lbm_info)], ctypes.c_int),
     "lbm_set_tile": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "lbm_kernel_launches": ([_vp], ctypes.c_int64),
+    "lbm_set_graph": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "lbm_set_batching": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "lbm_autotune": ([_vp, ctypes.c_int32, _i32p, _dp], ctypes.c_int),
     "lbm_enable_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_read_timing": ([_vp, _dp, _i64p, ctypes.c_int32], ctypes.c_int),
     "lbm_stencil_table": ([ctypes.c_int32, _i32p, _dp, _i32p], ctypes.c_int),
@@ -215,6 +218,22 @@ def lbm_get_info(ctx) -> dict:
 
 def lbm_set_tile(ctx, tx, ty, tz):
     _check(ctx, load_library().lbm_set_tile(ctx, tx, ty, tz))
+
+
+def lbm_set_batching(ctx, batched=True):
+    _check(ctx, load_library().lbm_set_batching(ctx, 1 if batched else 0))
+
+
+def lbm_set_graph(ctx, enable=True):
+    _check(ctx, load_library().lbm_set_graph(ctx, 1 if enable else 0))
+
+
+def lbm_autotune(ctx, trial_steps=20):
+    """(best tile (tx, ty, tz), ms per step of the best candidate); the state is unchanged."""
+    best = np.zeros(3, dtype=np.int32)
+    ms = ctypes.c_double()
+    _check(ctx, load_library().lbm_autotune(ctx, int(trial_steps), _ptr(best, ctypes.c_int32), ctypes.byref(ms)))
+    return tuple(int(v) for v in best), ms.value
 
 
 def lbm_kernel_launches(ctx) -> int:

@@ -292,3 +292,69 @@ def test_full_size_channel_equals_column_oracle():
             assert normwise(f[:, z, :, x], want[:, 0, :, 0]) <= TOL[storage]
         # x/z invariance of the whole field
         assert np.abs(f - f[:, :1, :, :1]).max() <= TOL[storage] * np.abs(f).max()
+
+
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+def test_graph_mode_equals_plain_launches(pattern):
+    """Step pairs replayed as CUDA graphs give bitwise the same state as plain launches,
+    including an odd step count and a call that spans both graph parities."""
+    import torch
+    case = _porous_case(lbm.FP32, pattern)
+    rho, u = inputs.random_state(case.shape, seed=17, rho_amp=0.01, u_amp=0.02)
+    out = []
+    for graphs in (False, True):
+        stream = torch.cuda.Stream()
+        s = case.make_sim(stream=stream.cuda_stream)
+        if graphs:
+            lbm.lbm_set_graph(s.ctx, True)
+        init_sim(s, rho, u)
+        s.step(9)
+        s.step(4)
+        out.append(gather_pdfs(s, case))
+        launches = s.launches()
+        s.close()
+    np.testing.assert_array_equal(out[1], out[0])
+
+
+def test_graph_mode_needs_a_stream():
+    case = Case(shape=(40, 9, 6), storage=lbm.FP32)
+    s = case.make_sim()
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_set_graph(s.ctx, True)
+    s.close()
+
+
+def test_autotune_keeps_state_and_results():
+    case = _porous_case(lbm.FP32, lbm.AA)
+    rho, u = inputs.random_state(case.shape, seed=19, rho_amp=0.01, u_amp=0.02)
+    a = case.make_sim()
+    init_sim(a, rho, u)
+    a.step(3)
+    before = gather_pdfs(a, case)
+    best, ms = lbm.lbm_autotune(a.ctx, 4)
+    assert ms > 0 and best[0] * best[1] <= 256
+    np.testing.assert_array_equal(gather_pdfs(a, case), before)
+    a.step(5)
+    tuned = gather_pdfs(a, case)
+    a.close()
+    b = case.make_sim()
+    init_sim(b, rho, u)
+    b.step(8)
+    np.testing.assert_array_equal(gather_pdfs(b, case), tuned)
+    b.close()
+
+
+def test_per_block_launches_equal_batched():
+    case = _porous_case(lbm.FP32, lbm.TWO_GRID)
+    rho, u = inputs.random_state(case.shape, seed=23, rho_amp=0.01, u_amp=0.02)
+    out = []
+    for batched in (True, False):
+        s = case.make_sim()
+        lbm.lbm_set_batching(s.ctx, batched)
+        init_sim(s, rho, u)
+        s.step(5)
+        out.append((gather_pdfs(s, case), s.step_diagnostics(), s.launches()))
+        s.close()
+    np.testing.assert_array_equal(out[1][0], out[0][0])
+    assert out[1][1] == out[0][1]
+    assert out[1][2] == 5 * len(case.blocks) + (out[0][2] - 5)  # one sweep per block per step
