@@ -184,16 +184,122 @@ static void moments_post(const lattice_t *L, const double *f, const double F[3],
     for (int a = 0; a < 3; ++a) u[a] = (j[a] - 0.5 * F[a]) / r;
 }
 
+/* ---------------------------------------------------------------------------------------
+ * Locally varying relaxation (Sec. 5.1.1: methods that vary the relaxation rate per cell
+ * from a local fluid property, e.g. turbulence models after Yu et al. 2005, cited there;
+ * waLBerla reads such rates from a separate field).  The closure gives the cell's omega+
+ * from its pre-collision state; omega- follows from the same Lambda.
+ *   Pi_neq_ab = sum_i c_ia c_ib f_i - rho (delta_ab / 3 + u_a u_b)   (non-equilibrium stress)
+ *   kind 1, Smagorinsky with constant cs (grid spacing 1): the total relaxation time tau
+ *   solves nu_t = (tau - tau0)/3 = cs^2 |S| with |S| = 3 sqrt(2 Pi:Pi) / (2 rho tau), i.e.
+ *       tau = ( tau0 + sqrt(tau0^2 + 18 cs^2 sqrt(2 Pi:Pi) / rho) ) / 2
+ *   kind 2, MLP: features (rho - 1) s_rho and s_pi Pi_neq (xx, yy, zz, xy, xz, yz), two
+ *   hidden layers of 32 SiLU units, one output y; tau = tau0 + s_tau softplus(y).  The
+ *   features and both hidden layers are rounded to BF16 (round to nearest even) before each
+ *   product, weights are BF16, sums exact (double here): the same rounding points as the
+ *   GPU's tensor-core inference.  Packed parameters (float): W1[32][7], b1[32],
+ *   W2[32][32], b2[32], w3[32], b3, s_rho, s_pi, s_tau.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t kind; /* 0 none, 1 Smagorinsky, 2 MLP */
+    int32_t pad;
+    double cs;
+    const float *mlp;
+} orc_closure;
+
+#define MLP_H 32
+#define MLP_IN 7
+
+static double bf16(double v)
+{
+    float f = (float)v;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b += 0x7fffu + ((b >> 16) & 1u);
+    b &= 0xffff0000u;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+static double silu(double z) { return z / (1.0 + exp(-z)); }
+
+static double softplus(double y) { return y > 30.0 ? y : log1p(exp(y)); }
+
+/* Non-equilibrium stress of a pre-collision state (rho, u with the half-force shift). */
+static void pi_neq(const lattice_t *L, const double *f, double rho, const double u[3], double pi[6])
+{
+    double m[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < L->q; ++i) {
+        double cx = L->c[3 * i], cy = L->c[3 * i + 1], cz = L->c[3 * i + 2];
+        m[0] += cx * cx * f[i];
+        m[1] += cy * cy * f[i];
+        m[2] += cz * cz * f[i];
+        m[3] += cx * cy * f[i];
+        m[4] += cx * cz * f[i];
+        m[5] += cy * cz * f[i];
+    }
+    pi[0] = m[0] - rho * (1.0 / 3.0 + u[0] * u[0]);
+    pi[1] = m[1] - rho * (1.0 / 3.0 + u[1] * u[1]);
+    pi[2] = m[2] - rho * (1.0 / 3.0 + u[2] * u[2]);
+    pi[3] = m[3] - rho * u[0] * u[1];
+    pi[4] = m[4] - rho * u[0] * u[2];
+    pi[5] = m[5] - rho * u[1] * u[2];
+}
+
+/* MLP output y for one cell's features (BF16 rounding points as described above). */
+static double mlp_y(const float *P, const double feat[MLP_IN])
+{
+    const float *W1 = P, *b1 = P + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H, *w3 = b2 + MLP_H,
+                *b3 = w3 + MLP_H;
+    double x[MLP_IN], h1[MLP_H], h2[MLP_H];
+    for (int k = 0; k < MLP_IN; ++k) x[k] = bf16(feat[k]);
+    for (int j = 0; j < MLP_H; ++j) {
+        double z = b1[j];
+        for (int k = 0; k < MLP_IN; ++k) z += bf16(W1[j * MLP_IN + k]) * x[k];
+        h1[j] = bf16(silu(z));
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+        double z = b2[j];
+        for (int k = 0; k < MLP_H; ++k) z += bf16(W2[j * MLP_H + k]) * h1[k];
+        h2[j] = bf16(silu(z));
+    }
+    double y = b3[0];
+    for (int k = 0; k < MLP_H; ++k) y += bf16(w3[k]) * h2[k];
+    return y;
+}
+
+/* omega+ of a cell under the closure (p->omega is the base rate 1/tau0). */
+static double closure_omega(const lattice_t *L, const orc_params *p, const orc_closure *cl, const double *f,
+                            double rho, const double u[3])
+{
+    if (!cl || cl->kind == 0) return p->omega;
+    const double tau0 = 1.0 / p->omega;
+    double pi[6];
+    pi_neq(L, f, rho, u, pi);
+    if (cl->kind == 1) {
+        double q = pi[0] * pi[0] + pi[1] * pi[1] + pi[2] * pi[2] + 2.0 * (pi[3] * pi[3] + pi[4] * pi[4] + pi[5] * pi[5]);
+        double tau = 0.5 * (tau0 + sqrt(tau0 * tau0 + 18.0 * cl->cs * cl->cs * sqrt(2.0 * q) / rho));
+        return 1.0 / tau;
+    }
+    const float *P = cl->mlp;
+    const float *tail = P + MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1;
+    const double s_rho = tail[0], s_pi = tail[1], s_tau = tail[2];
+    double feat[MLP_IN] = {(rho - 1.0) * s_rho, pi[0] * s_pi, pi[1] * s_pi, pi[2] * s_pi,
+                           pi[3] * s_pi,        pi[4] * s_pi, pi[5] * s_pi};
+    return 1.0 / (tau0 + s_tau * softplus(mlp_y(P, feat)));
+}
+
 /* Collision operator Omega of Eq. 2, SRT or TRT (Eq. 3 with special S), with Guo forcing:
  *   S_i = w_i [3 (c_i - u) + 9 (c_i.u) c_i] . F
  *   SRT: f*_i = f_i - w (f_i - feq_i) + (1 - w/2) S_i
  *   TRT: g+- = (g_i +- g_opp(i)) / 2 for g in {f, feq, S};
  *        f*_i = f_i - w+ (f+ - feq+) - w- (f- - feq-) + (1 - w+/2) S+ + (1 - w-/2) S-.     */
-static void collide(const lattice_t *L, const orc_params *p, const double *f, double *fout)
+static void collide(const lattice_t *L, const orc_params *p, const orc_closure *cl, const double *f, double *fout)
 {
     const double *F = p->force;
     double rho, u[3];
     moments_pre(L, f, F, &rho, u);
+    const double om = closure_omega(L, p, cl, f, rho, u);
     double feq[QMAX], S[QMAX];
     equilibrium(L, rho, u, feq);
     for (int i = 0; i < L->q; ++i) {
@@ -205,10 +311,10 @@ static void collide(const lattice_t *L, const orc_params *p, const double *f, do
         S[i] = L->w[i] * (ax * F[0] + ay * F[1] + az * F[2]);
     }
     if (p->collision == ORC_SRT) {
-        double w = p->omega;
+        double w = om;
         for (int i = 0; i < L->q; ++i) fout[i] = f[i] - w * (f[i] - feq[i]) + (1.0 - 0.5 * w) * S[i];
     } else {
-        double wp = p->omega;
+        double wp = om;
         double wm = orc_omega_minus(wp, p->magic_lambda);
         for (int i = 0; i < L->q; ++i) {
             int o = L->opp[i];
@@ -224,7 +330,18 @@ void orc_collide(const orc_params *p, const double *f, double *fout)
 {
     lattice_t L;
     if (get_lattice(p->q, &L) != 0) return;
-    collide(&L, p, f, fout);
+    collide(&L, p, NULL, f, fout);
+}
+
+/* One cell under a closure: its omega+ and post-collision populations. */
+double orc_collide_closure(const orc_params *p, const orc_closure *cl, const double *f, double *fout)
+{
+    lattice_t L;
+    if (get_lattice(p->q, &L) != 0) return -1.0;
+    double rho, u[3];
+    moments_pre(&L, f, p->force, &rho, u);
+    if (fout) collide(&L, p, cl, f, fout);
+    return closure_omega(&L, p, cl, f, rho, u);
 }
 
 void orc_set_threads(int n)
@@ -269,7 +386,7 @@ int orc_init(const orc_params *p, const uint8_t *flags, const double *rho, const
         for (int a = 0; a < 3; ++a) uu[a] = u[a * N + n] - 0.5 * p->force[a] / r;
         double feq[QMAX], fs[QMAX];
         equilibrium(&L, r, uu, feq);
-        collide(&L, p, feq, fs);
+        collide(&L, p, NULL, feq, fs);
         for (int i = 0; i < q; ++i) f[i * N + n] = fs[i];
     }
     return 0;
@@ -315,8 +432,18 @@ static int resolve(const orc_params *p, const uint8_t *flags, int x, int y, int 
  *                with u_b the velocity of x at time t (anti-bounce-back, no extrapolation)
  * The wall lies halfway between x and y.  Then every fluid cell collides.
  * ------------------------------------------------------------------------------------- */
+int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *flags, const double *cell_u,
+                    const double *cell_rho, double *f, double *work, int64_t nsteps);
+
 int orc_run(const orc_params *p, const uint8_t *flags, const double *cell_u, const double *cell_rho, double *f,
             double *work, int64_t nsteps)
+{
+    return orc_run_closure(p, NULL, flags, cell_u, cell_rho, f, work, nsteps);
+}
+
+/* Time stepping as orc_run, with a locally varying omega+ from the closure. */
+int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *flags, const double *cell_u,
+                    const double *cell_rho, double *f, double *work, int64_t nsteps)
 {
     lattice_t L;
     if (get_lattice(p->q, &L) != 0) return -1;
@@ -384,7 +511,7 @@ int orc_run(const orc_params *p, const uint8_t *flags, const double *cell_u, con
             if (flags[n] != ORC_FLUID) continue;
             double fin[QMAX], fout[QMAX];
             for (int i = 0; i < q; ++i) fin[i] = work[i * N + n];
-            collide(&L, p, fin, fout);
+            collide(&L, p, cl, fin, fout);
             for (int i = 0; i < q; ++i) f[i * N + n] = fout[i];
         }
     }

@@ -79,6 +79,24 @@ class OracleParams:
         return c
 
 
+class _CClosure(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("cs", ctypes.c_double),
+                ("mlp", ctypes.POINTER(ctypes.c_float))]
+
+
+NO_CLOSURE, SMAGORINSKY, MLP = 0, 1, 2
+
+
+def _closure(kind=NO_CLOSURE, cs=0.0, mlp=None):
+    c = _CClosure()
+    c.kind, c.cs = int(kind), float(cs)
+    keep = None
+    if mlp is not None:
+        keep = np.ascontiguousarray(mlp, dtype=np.float32)
+        c.mlp = keep.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    return c, keep
+
+
 _lib = None
 
 
@@ -103,6 +121,10 @@ def _L():
         lib.orc_run.restype = ctypes.c_int
         lib.orc_macroscopic.argtypes = [pp, u8p, dp, dp, dp]
         lib.orc_macroscopic.restype = ctypes.c_int
+        lib.orc_collide_closure.argtypes = [pp, P(_CClosure), dp, dp]
+        lib.orc_collide_closure.restype = ctypes.c_double
+        lib.orc_run_closure.argtypes = [pp, P(_CClosure), u8p, dp, dp, dp, dp, ctypes.c_int64]
+        lib.orc_run_closure.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_threads.restype = None
         lib.orc_get_threads.argtypes = []
@@ -182,8 +204,20 @@ def init(p: OracleParams, rho, u, flags=None) -> np.ndarray:
     return f
 
 
-def run(p: OracleParams, f, nsteps: int, flags=None, cell_u=None, cell_rho=None) -> np.ndarray:
-    """Advance the post-collision state ``f`` by ``nsteps`` steps (returns a new array)."""
+def collide_closure(p: OracleParams, f, kind=NO_CLOSURE, cs=0.0, mlp=None):
+    """(omega+, post-collision populations) of one cell under a closure."""
+    fin = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros(p.q, dtype=np.float64)
+    cp = p.cstruct()
+    cl, keep = _closure(kind, cs, mlp)
+    om = _L().orc_collide_closure(ctypes.byref(cp), ctypes.byref(cl), _dp(fin), _dp(out))
+    del keep
+    return float(om), out
+
+
+def run(p: OracleParams, f, nsteps: int, flags=None, cell_u=None, cell_rho=None, closure=None) -> np.ndarray:
+    """Advance the post-collision state ``f`` by ``nsteps`` steps (returns a new array).
+    ``closure``: optional dict(kind=SMAGORINSKY, cs=...) or dict(kind=MLP, mlp=params)."""
     flags = _check_flags(p, flags)
     f = np.array(f, dtype=np.float64, order="C", copy=True)
     work = np.zeros_like(f)
@@ -195,8 +229,10 @@ def run(p: OracleParams, f, nsteps: int, flags=None, cell_u=None, cell_rho=None)
     if (VELOCITY in kinds and (cell_u is None or cell_rho is None)) or (PRESSURE in kinds and cell_rho is None):
         raise ValueError("interior velocity/pressure cells need cell_u / cell_rho")
     cp = p.cstruct()
-    rc = _L().orc_run(ctypes.byref(cp), _u8(flags), _dp(cell_u), _dp(cell_rho), _dp(f), _dp(work),
-                      int(nsteps))
+    cl, keep = _closure(**(closure or {}))
+    rc = _L().orc_run_closure(ctypes.byref(cp), ctypes.byref(cl), _u8(flags), _dp(cell_u), _dp(cell_rho), _dp(f),
+                              _dp(work), int(nsteps))
+    del keep
     if rc != 0:
         raise RuntimeError("orc_run failed: %d" % rc)
     return f
