@@ -283,6 +283,53 @@ lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
 lbm_status lbm_reduce_noalloc(const void *f_dev, int32_t stencil, int32_t storage, int64_t ncells,
                               const double force[3], double *out_dev, void *cuda_stream);
 
+/* ---- Locally varying relaxation --------------------------------------------------------
+ * Sec. 5.1.1: the relaxation rate may vary per cell from a local fluid property (turbulence
+ * models, cited there after Yu et al. 2005).  With a closure set, every sweep computes omega+
+ * of each cell from its pre-collision populations; omega- follows from the context's Lambda
+ * (TRT) or equals omega+ (SRT).  tau0 = 1/params.omega.  Non-equilibrium stress:
+ *   Pi_ab = sum_i c_ia c_ib f_i - rho (delta_ab / 3 + u_a u_b)
+ *   LBM_CLOSURE_SMAGORINSKY: tau = (tau0 + sqrt(tau0^2 + 18 cs^2 sqrt(2 Pi:Pi) / rho)) / 2
+ *   LBM_CLOSURE_MLP: tau = tau0 + s_tau softplus(y), y the output of a 7-32-32-1 network
+ *     with SiLU hidden units on the features ((rho - 1) s_rho, s_pi Pi_xx, Pi_yy, Pi_zz, Pi_xy,
+ *     Pi_xz, Pi_yz), evaluated on the tensor cores: features, weights and hidden activations
+ *     rounded to BF16 (nearest even), sums in FP32.
+ * Packed network parameters (LBM_MLP_NPARAM floats, row-major): W1[32][7], b1[32],
+ * W2[32][32], b2[32], w3[32], b3, s_rho, s_pi, s_tau. */
+enum { LBM_CLOSURE_NONE = 0, LBM_CLOSURE_SMAGORINSKY = 1, LBM_CLOSURE_MLP = 2 };
+#define LBM_MLP_NPARAM 1348
+
+/* Set the closure of a context.  cs: Smagorinsky constant (kind 1); mlp_params: host array of
+ * LBM_MLP_NPARAM floats (kind 2), copied.  Supported for D3Q19, LBM_FP32 storage and zero
+ * body force (any block set and boundary kinds); other contexts get LBM_ERR_UNSUPPORTED.  kind LBM_CLOSURE_NONE restores the constant
+ * rate.  Errors: LBM_ERR_ARG (unknown kind, null params, cs < 0), LBM_ERR_UNSUPPORTED. */
+lbm_status lbm_set_closure(lbm_ctx *ctx, int32_t kind, double cs, const float *mlp_params);
+
+/* The network alone: inference on the tensor cores and training in FP32 (loss
+ * mean_s (softplus(y_s) - t_s)^2 over a batch, its gradient, Adam steps).  Device arrays:
+ * features X[n][7] (FP32, already scaled), targets T[n], outputs y[n]. */
+typedef struct lbm_mlp lbm_mlp; /* opaque; owned by the library */
+
+/* Create a network from LBM_MLP_NPARAM packed parameters (host, copied) for batches of up
+ * to max_batch samples, issuing work on cuda_stream.  Errors: LBM_ERR_ARG, LBM_ERR_OOM. */
+lbm_status lbm_mlp_create(const float *params, int64_t max_batch, void *cuda_stream, lbm_mlp **out);
+/* Replace / read the parameters (host arrays of LBM_MLP_NPARAM floats); set resets Adam. */
+lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *params);
+lbm_status lbm_mlp_get_params(lbm_mlp *m, float *params);
+/* y[s] for n samples (asynchronous on the stream), with the BF16 rounding of the sweep. */
+lbm_status lbm_mlp_infer(lbm_mlp *m, const float *X_dev, int64_t n, float *y_dev);
+/* Loss and gradient (FP32 arithmetic, deterministic summation order) of n <= max_batch
+ * samples; loss_host (1 double) and grad_host (LBM_MLP_NPARAM floats, zero for the three
+ * scales) may each be NULL.  Synchronises the stream when either is given. */
+lbm_status lbm_mlp_loss_grad(lbm_mlp *m, const float *X_dev, const float *T_dev, int64_t n, double *loss_host,
+                             float *grad_host);
+/* `iters` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr; scales held fixed) on
+ * consecutive batches of `batch` samples cycling through the n samples; loss_history
+ * (iters doubles, host, may be NULL) receives each step's batch loss.  Synchronises. */
+lbm_status lbm_mlp_train(lbm_mlp *m, const float *X_dev, const float *T_dev, int64_t n, int64_t batch,
+                         int64_t iters, float lr, double *loss_history);
+void lbm_mlp_destroy(lbm_mlp *m);
+
 /* Last error message of the context (never NULL). */
 const char *lbm_last_error(const lbm_ctx *ctx);
 

@@ -1,7 +1,8 @@
 """Build liblbm.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
-Translation units: api.cu (C ABI, scheduler), plan.cpp (host list builder, OpenMP), and
-sweep.cu / aux.cu compiled once per (stencil, storage) variant.  Objects are compiled in
+Translation units: api.cu (C ABI, scheduler), plan.cpp (host list builder, OpenMP), diag.cu,
+reduce_static.cu, closure.cu (closure sweep and network kernels, D3Q19 FP32), and sweep.cu /
+aux.cu compiled once per (stencil, storage) variant.  Objects are compiled in
 parallel; the library lands in ``paper_1909_13772_gb300/_build/liblbm.so``.
 """
 from __future__ import annotations
@@ -38,7 +39,7 @@ def _sources():
 
 def _jobs(nvcc, extra, build_dir):
     jobs = []
-    for name in ("api.cu", "plan.cpp", "diag.cu", "reduce_static.cu"):
+    for name in ("api.cu", "plan.cpp", "diag.cu", "reduce_static.cu", "closure.cu"):
         src = os.path.join(CSRC, name)
         obj = os.path.join(build_dir, name.replace(".", "_") + ".o")
         lang = [] if name.endswith(".cu") else ["-x", "cu"]

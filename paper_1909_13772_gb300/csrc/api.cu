@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "closure.hpp"
 #include "lbm.h"
 #include "launch.hpp"
 #include "plan.hpp"
@@ -77,6 +78,11 @@ struct lbm_ctx {
     int64_t graph_epoch[2] = {-1, -1};
     int64_t list_epoch = 0;  // bumped whenever device lists are (re)uploaded
 
+    // locally varying relaxation (closure.cu): kind, Smagorinsky constant, network
+    int closure = CLOSURE_NONE;
+    double closure_cs = 0.0;
+    MlpDev *d_mlp = nullptr;
+
     // tracing: events around fill and sweep launches (pairs of [start, end])
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -137,6 +143,21 @@ void dfree(T *&p)
     } while (0)
 
 cudaError_t do_sweep(int q, int st, const SweepArgs &s) { LBM_SWITCH(q, st, launch_sweep_, s); }
+
+// The step's sweep: the plain sweep, or the closure sweep when a closure is set.
+cudaError_t sweep_of(const lbm_ctx *c, const SweepArgs &s)
+{
+    if (c->closure == CLOSURE_NONE) return do_sweep(c->q, c->storage, s);
+    ClosureLaunch cl;
+    cl.sw = s;
+    cl.closure = c->closure;
+    cl.trt = c->p.collision == LBM_TRT ? 1 : 0;
+    cl.tau0 = (float)(1.0 / c->p.omega);
+    cl.cs = (float)c->closure_cs;
+    cl.lambda = (float)c->p.magic_lambda;
+    cl.mlp = c->d_mlp;
+    return launch_closure_sweep(cl);
+}
 cudaError_t do_fill(int q, int st, const FillArgs &s) { LBM_SWITCH(q, st, launch_fill_, s); }
 cudaError_t do_cells(int q, int st, int op, int force, const CellArgs &s) { LBM_SWITCH(q, st, launch_cells_, op, force, s); }
 cudaError_t do_reduce(int q, int st, const ReduceArgs &s) { LBM_SWITCH(q, st, launch_reduce_, s); }
@@ -582,11 +603,11 @@ lbm_status issue_step(lbm_ctx *c, SweepArgs &sw, FillArgs &fa, bool diag, bool t
             one.ntiles = c->tile_start[b + 1] - c->tile_start[b];
             one.partials = diag ? c->d_step_partials + 8 * c->tile_start[b] : nullptr;
             if (one.ntiles == 0) continue;
-            CK(do_sweep(c->q, c->storage, one), "sweep launch");
+            CK(sweep_of(c, one), "sweep launch");
             c->launches++;
         }
     } else if (sw.ntiles > 0) {
-        CK(do_sweep(c->q, c->storage, sw), "sweep launch");
+        CK(sweep_of(c, sw), "sweep launch");
         c->launches++;
     }
     if (trace) {
@@ -691,6 +712,33 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
         ++t;
         if (di > 0 && c->steps_done % di == 0 && (s = check_diag(c)) != LBM_OK) return s;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_closure(lbm_ctx *c, int32_t kind, double cs, const float *mlp_params)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (kind != LBM_CLOSURE_NONE && kind != LBM_CLOSURE_SMAGORINSKY && kind != LBM_CLOSURE_MLP)
+        return fail(c, LBM_ERR_ARG, "unknown closure kind %d", kind);
+    if (kind == LBM_CLOSURE_NONE) {
+        c->closure = CLOSURE_NONE;
+        drop_graphs(c);
+        return LBM_OK;
+    }
+    if (kind == LBM_CLOSURE_SMAGORINSKY && !(std::isfinite(cs) && cs >= 0.0))
+        return fail(c, LBM_ERR_ARG, "bad Smagorinsky constant");
+    if (kind == LBM_CLOSURE_MLP && !mlp_params) return fail(c, LBM_ERR_ARG, "null network parameters");
+    if (c->q != 19 || c->storage != LBM_FP32 || c->force)
+        return fail(c, LBM_ERR_UNSUPPORTED, "closures need D3Q19, FP32 storage and no body force");
+    if (kind == LBM_CLOSURE_MLP) {
+        const MlpDev d = mlp_device_form(mlp_params);
+        if (!c->d_mlp) CK(cudaMalloc((void **)&c->d_mlp, sizeof(MlpDev)), "cudaMalloc(network)");
+        CK(cudaMemcpyAsync(c->d_mlp, &d, sizeof d, cudaMemcpyHostToDevice, c->stream), "copy network");
+        CK(cudaStreamSynchronize(c->stream), "copy network");
+    }
+    c->closure = kind;
+    c->closure_cs = cs;
+    drop_graphs(c);  // captured sweeps carry the old closure
     return LBM_OK;
 }
 
@@ -1084,6 +1132,7 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_step_partials);
     dfree(c->d_out);
     dfree(c->d_scratch);
+    dfree(c->d_mlp);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     drop_graphs(c);
     delete c;

@@ -19,7 +19,7 @@
 // column of the tile and walks tz cells along z.  A warp covers 32 consecutive x cells,
 // so every direction's load and store is one contiguous 32-element row segment
 // (coalesced; c_x = +-1 directions are shifted by one element).
-#include "select.cuh"
+#include "cell.cuh"
 
 // Occupancy: minimum resident CTAs of 256 threads per SM.  For 4- and 2-byte storage, 4
 // caps the sweeps at 64 registers (1024 threads per SM); measured on the 256^3 channel it
@@ -37,145 +37,10 @@ namespace lbm {
 
 namespace {
 
-constexpr int kQ = LBM_Q;
-using S = Storage<StoreT>;
-using R = typename S::R;
-
 // The diagnostics variant (DIAG) keeps eight running sums in registers; one CTA fewer per
 // SM leaves it room for them without spilling.
 constexpr int kMinB = LBM_SWEEP_MINB;
 constexpr int kMinBDiag = LBM_SWEEP_MINB > 3 ? 3 : (LBM_SWEEP_MINB > 1 ? 1 : LBM_SWEEP_MINB);
-
-// Per-CTA diagnostics record of the cells this CTA updated (DIAG): sums accumulated per
-// thread and per warp in the sweep's arithmetic type, across warps in FP64:
-// mass, momentum (rho u, half-force corrected), kinetic energy, max |u|, non-finite
-// cells, fluid cells.
-template <bool DIAG>
-struct Diag {
-    R m = R(0), jx = R(0), jy = R(0), jz = R(0), e = R(0), umax = R(0), bad = R(0), n = R(0);
-    __device__ __forceinline__ void add(R rho, R ux, R uy, R uz)
-    {
-        if (!DIAG) return;
-        const R u2 = ux * ux + uy * uy + uz * uz;
-        const bool ok = isfinite(rho) && isfinite(u2);
-        m += rho;
-        jx += rho * ux;
-        jy += rho * uy;
-        jz += rho * uz;
-        e += R(0.5) * rho * u2;
-        umax = fmax(umax, sqrt(u2));
-        bad += ok ? R(0) : R(1);
-        n += R(1);
-    }
-};
-
-template <class T>
-__device__ __forceinline__ T wsum(T v)
-{
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-template <class T>
-__device__ __forceinline__ T wmax(T v)
-{
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// Geometry of a neighbour block read in place (one per ghost-shell region), staged in
-// shared memory once per CTA.
-struct NbrGeo {
-    int64_t offset, slab, plane;
-    int32_t pitch, xo, nx, ny, nz, valid;
-};
-
-// Per-thread face flags: lo/hi bit a set when the cell is on the low/high face of axis a
-// of a block that reads its neighbours in place.
-struct Face {
-    int lo, hi;
-};
-
-// Arena offset of slot `q` of the neighbour (x, y, z) + (DX, DY, DZ) when it may lie in a
-// neighbour block (shared-memory table nb); otherwise (inside the block, or a boundary
-// region) `own` = the plain own-layout offset.
-// (DX, DY, DZ are compile-time constants after the direction loops unroll.)
-__device__ __forceinline__ int64_t nbr_addr(const NbrGeo *nb, Face fc, int x, int y, int z, int DX, int DY, int DZ,
-                                            int q, int64_t own)
-{
-    const int rx = DX > 0 ? ((fc.hi & 1) ? 1 : 0) : (DX < 0 ? ((fc.lo & 1) ? -1 : 0) : 0);
-    const int ry = DY > 0 ? ((fc.hi & 2) ? 1 : 0) : (DY < 0 ? ((fc.lo & 2) ? -1 : 0) : 0);
-    const int rz = DZ > 0 ? ((fc.hi & 4) ? 1 : 0) : (DZ < 0 ? ((fc.lo & 4) ? -1 : 0) : 0);
-    if ((rx | ry | rz) == 0) return own;
-    const NbrGeo &N = nb[(rx + 1) + 3 * (ry + 1) + 9 * (rz + 1)];
-    if (!N.valid) return own;
-    const int sx = rx > 0 ? 0 : (rx < 0 ? N.nx - 1 : x + DX);
-    const int sy = ry > 0 ? 0 : (ry < 0 ? N.ny - 1 : y + DY);
-    const int sz = rz > 0 ? 0 : (rz < 0 ? N.nz - 1 : z + DZ);
-    return N.offset + (int64_t)q * N.slab + (int64_t)(sz + 1) * N.plane + (int64_t)(sy + 1) * N.pitch + N.xo + sx;
-}
-
-// One cell: gather, collide, scatter (see the file header).  FACE: the warp has cells on a
-// face of a block that reads its neighbours in place; directions that leave the block there
-// are wrapped (FACE 1: the block is its own neighbour) or resolved through the
-// shared-memory neighbour table (FACE 2).  m: the cell's bounce-back
-// bits (bit i: the source x - c_i is a no-slip cell; halfway bounce-back then supplies
-// f_i(x, t+1) = f*_opp(i)(x, t), read from the cell's own slot).
-//   pull: bounce source src[opp i][x]
-//   AA neighbour: bounce source A[i][x] (where the E layout keeps f*_opp(i)(x)); the value
-//   f*_i(x) whose target x + c_i is no-slip (bit opp(i)) goes to A[opp i][x], where the next
-//   local sweep reads it as f_opp(i)(x, t+1).
-template <bool FORCE, int KIND, bool DIAG, int FACE, bool MASK>
-__device__ __forceinline__ void update_cell(StoreT *__restrict__ A, StoreT *__restrict__ Bout, const DevBlock &B,
-                                            const NbrGeo *nb, Face fc, int x, int y, int z, int64_t cell, uint32_t m,
-                                            const Coll<R> &k, Diag<DIAG> &dg)
-{
-    using L = Lattice<kQ>;
-    StoreT *a = A + B.offset;
-    R f[kQ];
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
-        const bool bounce = MASK && i > 0 && ((m >> i) & 1u);
-        if (KIND == SWEEP_AA_LOCAL) {
-            f[i] = S::ld_rw(a + (int64_t)i * B.slab + cell, k.base[i]);
-            continue;
-        }
-        const int sl = KIND == SWEEP_PULL ? i : L::opp(i);  // slot read from the source cell
-        const int bs = KIND == SWEEP_PULL ? L::opp(i) : i;  // own slot read on bounce-back
-        int64_t o = bounce ? (int64_t)bs * B.slab + cell : (int64_t)sl * B.slab + cell - off;
-        if (FACE == 1 && !bounce) o += wrap_shift(B, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
-        if (FACE == 2 && !bounce)
-            o = nbr_addr(nb, fc, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i), sl, o + B.offset) - B.offset;
-        f[i] = KIND == SWEEP_PULL ? S::ld(a + o, k.base[i]) : S::ld_rw(a + o, k.base[i]);
-    }
-    R rho, ux, uy, uz;
-    collide<kQ, FORCE, R>(f, k, rho, ux, uy, uz);
-    // The neighbour sweep's store offsets equal its load offsets of the opposite directions;
-    // hide the coordinates from the optimiser so it recomputes them here instead of keeping
-    // 19 offsets live across the collision.
-    int xs = x, ys = y, zs = z;
-    if (KIND == SWEEP_AA_NBR) asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs));
-#pragma unroll
-    for (int i = 0; i < kQ; ++i) {
-        const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
-        if (KIND == SWEEP_PULL) {
-            S::st(Bout + B.offset + (int64_t)i * B.slab + cell, f[i], k.base[i]);
-        } else if (KIND == SWEEP_AA_LOCAL) {
-            const int o = L::opp(i);
-            S::st(a + (int64_t)o * B.slab + cell, f[i], k.base[i]);
-        } else {
-            const int o = L::opp(i);
-            const bool bounce = MASK && i > 0 && ((m >> o) & 1u);
-            const int64_t c2 = B.cell(xs, ys, zs);
-            int64_t d = bounce ? (int64_t)o * B.slab + c2 : (int64_t)i * B.slab + c2 + off;
-            if (FACE == 1 && !bounce) d += wrap_shift(B, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i));
-            if (FACE == 2 && !bounce)
-                d = nbr_addr(nb, fc, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i), i, d + B.offset) - B.offset;
-            S::st(a + d, f[i], k.base[i]);
-        }
-    }
-    dg.add(rho, ux, uy, uz);
-}
 
 // The cells of one tile.  A thread owns one (x, y) column and walks the tile's z range.  A
 // warp with a cell on a face of a block that reads its neighbours in place takes the
@@ -188,33 +53,12 @@ __device__ __forceinline__ void sweep_cells(StoreT *__restrict__ A, StoreT *__re
 {
     const DevTile t = tiles[blockIdx.x];
     const DevBlock *Bp = blocks + t.block;
-    // scalar geometry in registers (the neighbour table stays out of them)
-    DevBlock B;
-    B.nx = Bp->nx;
-    B.ny = Bp->ny;
-    B.nz = Bp->nz;
-    B.pitch = Bp->pitch;
-    B.plane = Bp->plane;
-    B.slab = Bp->slab;
-    B.offset = Bp->offset;
-    B.mask = Bp->mask;
-    B.xo = Bp->xo;
-    B.through = Bp->through;
-    B.wrap = Bp->wrap;
+    const DevBlock B = block_geo(Bp);  // scalar geometry in registers
     constexpr bool kThr = THROUGH != 0 && KIND != SWEEP_AA_LOCAL;
     constexpr bool kTable = THROUGH == 2 && KIND != SWEEP_AA_LOCAL;
     __shared__ NbrGeo nb[kTable ? 27 : 1];
     if (kTable) {
-        if (threadIdx.x < 27) {
-            const int r = threadIdx.x;
-            const int n = (B.through && r != 13) ? Bp->nbr[r] : -1;
-            NbrGeo g{};
-            if (n >= 0) {
-                const DevBlock *N = blocks + n;
-                g = NbrGeo{N->offset, N->slab, N->plane, N->pitch, N->xo, N->nx, N->ny, N->nz, 1};
-            }
-            nb[r] = g;
-        }
+        stage_neighbours(nb, blocks, Bp);
         __syncthreads();
     }
     const int ttx = (int)t.width_m1 + 1;  // this tile's width (the block's own if narrower)

@@ -83,6 +83,15 @@ _SIGS = {
     "lbm_plan_params": ([_vp, _dp, ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_plan_mask": ([_vp, ctypes.c_int32, _P(ctypes.c_uint32), ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_reduce_noalloc": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _dp, _vp, _vp], ctypes.c_int),
+    "lbm_set_closure": ([_vp, ctypes.c_int32, ctypes.c_double, _P(ctypes.c_float)], ctypes.c_int),
+    "lbm_mlp_create": ([_P(ctypes.c_float), ctypes.c_int64, _vp, _P(_vp)], ctypes.c_int),
+    "lbm_mlp_set_params": ([_vp, _P(ctypes.c_float)], ctypes.c_int),
+    "lbm_mlp_get_params": ([_vp, _P(ctypes.c_float)], ctypes.c_int),
+    "lbm_mlp_infer": ([_vp, _vp, ctypes.c_int64, _vp], ctypes.c_int),
+    "lbm_mlp_loss_grad": ([_vp, _vp, _vp, ctypes.c_int64, _dp, _P(ctypes.c_float)], ctypes.c_int),
+    "lbm_mlp_train": ([_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, _dp],
+                      ctypes.c_int),
+    "lbm_mlp_destroy": ([_vp], None),
     "lbm_last_error": ([_vp], ctypes.c_char_p),
     "lbm_destroy": ([_vp], None),
 }
@@ -331,6 +340,73 @@ def lbm_reduce_noalloc(f_dev_ptr: int, stencil: int, storage: int, ncells: int, 
         raise LbmError(st, "lbm_reduce_noalloc: " + why)
 
 
+CLOSURE_NONE, CLOSURE_SMAGORINSKY, CLOSURE_MLP = 0, 1, 2
+MLP_NPARAM = 1348
+
+
+def lbm_set_closure(ctx, kind, cs=0.0, mlp_params=None):
+    """Per-cell relaxation from a closure (Smagorinsky constant cs, or packed network
+    parameters, MLP_NPARAM floats)."""
+    P = _arr(mlp_params, np.float32) if mlp_params is not None else None
+    if P is not None and P.size != MLP_NPARAM:
+        raise ValueError("network parameters must have %d entries" % MLP_NPARAM)
+    _check(ctx, load_library().lbm_set_closure(ctx, int(kind), float(cs), _ptr(P, ctypes.c_float)))
+
+
+def _mlp_check(status, what):
+    if status != 0:
+        raise LbmError(status, what)
+
+
+def lbm_mlp_create(params, max_batch, stream=None):
+    P = _arr(params, np.float32)
+    if P.size != MLP_NPARAM:
+        raise ValueError("network parameters must have %d entries" % MLP_NPARAM)
+    h = _vp()
+    _mlp_check(load_library().lbm_mlp_create(_ptr(P, ctypes.c_float), int(max_batch), _vp(stream or 0),
+                                             ctypes.byref(h)), "lbm_mlp_create")
+    return h
+
+
+def lbm_mlp_set_params(m, params):
+    P = _arr(params, np.float32)
+    if P.size != MLP_NPARAM:
+        raise ValueError("network parameters must have %d entries" % MLP_NPARAM)
+    _mlp_check(load_library().lbm_mlp_set_params(m, _ptr(P, ctypes.c_float)), "lbm_mlp_set_params")
+
+
+def lbm_mlp_get_params(m) -> np.ndarray:
+    P = np.empty(MLP_NPARAM, np.float32)
+    _mlp_check(load_library().lbm_mlp_get_params(m, _ptr(P, ctypes.c_float)), "lbm_mlp_get_params")
+    return P
+
+
+def lbm_mlp_infer(m, X_dev_ptr: int, n: int, y_dev_ptr: int):
+    """y[s] = network output for features X[n][7] (device pointers, FP32)."""
+    _mlp_check(load_library().lbm_mlp_infer(m, _vp(X_dev_ptr), int(n), _vp(y_dev_ptr)), "lbm_mlp_infer")
+
+
+def lbm_mlp_loss_grad(m, X_dev_ptr: int, T_dev_ptr: int, n: int):
+    """(loss, gradient[MLP_NPARAM]) of mean (softplus(y) - t)^2 over n samples."""
+    loss = np.zeros(1, np.float64)
+    g = np.empty(MLP_NPARAM, np.float32)
+    _mlp_check(load_library().lbm_mlp_loss_grad(m, _vp(X_dev_ptr), _vp(T_dev_ptr), int(n), _ptr(loss, ctypes.c_double),
+                                                _ptr(g, ctypes.c_float)), "lbm_mlp_loss_grad")
+    return float(loss[0]), g
+
+
+def lbm_mlp_train(m, X_dev_ptr: int, T_dev_ptr: int, n: int, batch: int, iters: int, lr: float) -> np.ndarray:
+    """Adam steps on consecutive batches; returns the per-step batch losses."""
+    hist = np.zeros(max(int(iters), 1), np.float64)
+    _mlp_check(load_library().lbm_mlp_train(m, _vp(X_dev_ptr), _vp(T_dev_ptr), int(n), int(batch), int(iters),
+                                            float(lr), _ptr(hist, ctypes.c_double)), "lbm_mlp_train")
+    return hist[:int(iters)]
+
+
+def lbm_mlp_destroy(m):
+    load_library().lbm_mlp_destroy(m)
+
+
 def lbm_last_error(ctx) -> str:
     return load_library().lbm_last_error(ctx).decode()
 
@@ -427,3 +503,6 @@ class Simulation:
 
     def launches(self):
         return lbm_kernel_launches(self.ctx)
+
+    def set_closure(self, kind, cs=0.0, mlp_params=None):
+        lbm_set_closure(self.ctx, kind, cs, mlp_params)

@@ -397,3 +397,33 @@ def test_channel_link_and_ghost_counts():
         assert nbr[region(0, 0, -1)] == b and nbr[region(0, 0, 1)] == b  # itself (periodic)
         assert nbr[region(0, 1, 0)] == -1 and nbr[region(1, -1, 0)] == -1  # walls
     sim.close()
+
+
+def test_closure_rejects_unsupported_contexts_and_bad_arguments():
+    """Host-side checks of lbm_set_closure (no device work on these paths)."""
+    def ctx(**kw):
+        return lbm.lbm_create_blocks(lbm.make_params(**kw), [((0, 0, 0), (8, 8, 8))])
+
+    for kw in (dict(stencil=27), dict(storage=lbm.FP64), dict(storage=lbm.BF16_DEV), dict(force=(1e-5, 0, 0))):
+        c = ctx(**kw)
+        try:
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_set_closure(c, lbm.CLOSURE_SMAGORINSKY, cs=0.17)
+            assert e.value.status == 7, kw
+        finally:
+            lbm.lbm_destroy(c)
+    c = ctx()
+    try:
+        for kind, cs in ((3, 0.1), (-1, 0.1), (lbm.CLOSURE_SMAGORINSKY, -0.1), (lbm.CLOSURE_SMAGORINSKY, float("nan"))):
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_set_closure(c, kind, cs=cs)
+            assert e.value.status == 1
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_set_closure(c, lbm.CLOSURE_MLP)  # no parameters
+        assert e.value.status == 1
+        with pytest.raises(ValueError):
+            lbm.lbm_set_closure(c, lbm.CLOSURE_MLP, mlp_params=np.zeros(10, np.float32))
+        lbm.lbm_set_closure(c, lbm.CLOSURE_SMAGORINSKY, cs=0.17)
+        lbm.lbm_set_closure(c, lbm.CLOSURE_NONE)
+    finally:
+        lbm.lbm_destroy(c)
