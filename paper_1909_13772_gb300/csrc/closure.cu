@@ -51,7 +51,9 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+// SiLU of the inference path with the fast intrinsics (__expf, __fdividef: errors of a few
+// FP32 ulp, far below the BF16 rounding applied to the result); z -> -inf gives -0.
+__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
 __device__ __forceinline__ float softplus(float y) { return y > 30.0f ? y : log1pf(expf(y)); }
 
 // Per-warp MLP on 32 cells (one per lane): the features of all lanes form A = X (32 x 16,
@@ -165,8 +167,18 @@ struct ClosureArgsDev {
 // Closure sweep: like the plain sweep, but every lane stays in the z loop (the network's
 // MMAs need the whole warp); lanes without a fluid cell feed zero features and skip the
 // loads and stores.
+// Minimum resident CTAs of 256 threads per SM (register cap) per closure kind, measured on a
+// 256^3 periodic box (two-grid, ms per step): Smagorinsky 0.46 at 4 (64 registers), 0.50 at 3,
+// 0.61 at 2; network 0.89 at 3 (80 registers), 1.00 at 2.
+#ifndef LBM_CLOSURE_MINB_SMAG
+#define LBM_CLOSURE_MINB_SMAG 4
+#endif
+#ifndef LBM_CLOSURE_MINB_MLP
+#define LBM_CLOSURE_MINB_MLP 3
+#endif
+
 template <int KIND, int CLOSURE, bool DIAG, int THROUGH>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LBM_CLOSURE_MINB_MLP)
     k_closure_sweep(StoreT *__restrict__ A, StoreT *__restrict__ Bout, const DevBlock *__restrict__ blocks,
                     const DevTile *__restrict__ tiles, int tz, Coll<float> k, const MlpDev *__restrict__ mlp,
                     ClosureArgsDev ca, double *__restrict__ partials)

@@ -222,7 +222,7 @@ def test_closure_with_graph_replay_and_diagnostics(torch):
             sim.close()
     assert np.array_equal(res[0][0], res[1][0])
     full = oracle.diagnostics(case.oracle_params(), res[0][0].astype(np.float64))
-    assert abs(res[0][1]["mass"] - full["mass"]) < 1e-9 * full["mass"]
+    assert abs(res[0][1]["mass"] - full["mass"]) < 1e-6 * full["mass"]  # FP32 per-thread sums
 
 
 def test_clearing_the_closure_restores_the_plain_sweep(torch):
