@@ -330,6 +330,14 @@ lbm_status lbm_mlp_train(lbm_mlp *m, const float *X_dev, const float *T_dev, int
                          int64_t iters, float lr, double *loss_history);
 void lbm_mlp_destroy(lbm_mlp *m);
 
+/* Box sums of a block for coarse-graining (the filtered fine-grid fields that train and judge
+ * the learned closure): for each coarse cell of ratio^3 interior cells (every block edge
+ * divisible by ratio), the sums over its fluid cells of rho, rho u_x, rho u_y, rho u_z and
+ * rho u_a u_b (xx, yy, zz, xy, xz, yz), with rho and u as lbm_get_macroscopic gives them.
+ * out: host array of 10 * Nc doubles, out[m * Nc + c], c = X + NX (Y + NY Z), NX = nx / ratio.
+ * Synchronises the stream.  Errors: LBM_ERR_ARG (bad block, null out, ratio not dividing). */
+lbm_status lbm_coarse_moments(lbm_ctx *ctx, int32_t block, int32_t ratio, double *out);
+
 /* Last error message of the context (never NULL). */
 const char *lbm_last_error(const lbm_ctx *ctx);
 

@@ -843,6 +843,29 @@ lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u
     return LBM_OK;
 }
 
+lbm_status lbm_coarse_moments(lbm_ctx *c, int32_t block, int32_t ratio, double *out)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if (!out) return fail(c, LBM_ERR_ARG, "null output");
+    const BlockLayout &L = c->blocks[block];
+    if (ratio < 1 || L.n[0] % ratio || L.n[1] % ratio || L.n[2] % ratio)
+        return fail(c, LBM_ERR_ARG, "block %d (%d x %d x %d) is not divisible by ratio %d", block, L.n[0], L.n[1], L.n[2],
+                    ratio);
+    if ((s = prepare(c)) != LBM_OK) return s;
+    const int64_t Nc = (int64_t)(L.n[0] / ratio) * (L.n[1] / ratio) * (L.n[2] / ratio);
+    if ((s = ensure_scratch(c, 10 * Nc)) != LBM_OK) return s;
+    CellArgs a = cell_args(c, block);
+    a.f64 = c->d_scratch;
+    a.ratio = ratio;
+    CK(do_cells(c->q, c->storage, CELL_COARSE, 0, a), "coarse moments kernel");
+    CK(cudaMemcpyAsync(out, c->d_scratch, 10 * Nc * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "copy coarse moments");
+    CK(cudaStreamSynchronize(c->stream), "coarse_moments");
+    return LBM_OK;
+}
+
 lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
 {
     if (!c) return LBM_ERR_ARG;

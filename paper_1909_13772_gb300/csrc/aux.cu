@@ -259,6 +259,54 @@ __global__ void k_macro(const StoreT *__restrict__ A, const DevBlock *__restrict
     u_out[2 * N + n] = j[2] / rho;
 }
 
+// Box sums for coarse-graining: one thread per coarse cell of r^3 interior cells; sums over
+// its fluid cells of rho, rho u (3) and rho u_a u_b (xx, yy, zz, xy, xz, yz), with u as in
+// k_macro.  out[m * Nc + c], c = X + NX (Y + NY Z).
+__global__ void __launch_bounds__(256) k_coarse(const StoreT *__restrict__ A, const DevBlock *__restrict__ blocks,
+                                                int blk, int layout, int r, double *__restrict__ out,
+                                                const uint32_t *__restrict__ mask, FillConst k, double Fx, double Fy,
+                                                double Fz)
+{
+    const DevBlock *Bp = blocks + blk;
+    const DevBlock &B = *Bp;
+    const int NX = B.nx / r, NY = B.ny / r, NZ = B.nz / r;
+    const int64_t Nc = (int64_t)NX * NY * NZ;
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= Nc) return;
+    const int X = (int)(c % NX);
+    const int Y = (int)((c / NX) % NY);
+    const int Z = (int)(c / ((int64_t)NX * NY));
+    const double F[3] = {Fx, Fy, Fz};
+    double acc[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int dz = 0; dz < r; ++dz)
+        for (int dy = 0; dy < r; ++dy)
+            for (int dx = 0; dx < r; ++dx) {
+                const int x = X * r + dx, y = Y * r + dy, z = Z * r + dz;
+                const int64_t cell = (int64_t)(z + 1) * B.plane + (int64_t)(y + 1) * B.pitch + B.xo + x;
+                const uint32_t m = mask ? mask[cell] : 0u;
+                if (m & kMaskSolid) continue;
+                double f[kQ];
+#pragma unroll
+                for (int i = 0; i < kQ; ++i)
+                    f[i] = (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]);
+                double rho, j[3];
+                moments_post<kQ>(f, F, rho, j);
+                const double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
+                acc[0] += rho;
+                acc[1] += rho * u[0];
+                acc[2] += rho * u[1];
+                acc[3] += rho * u[2];
+                acc[4] += rho * u[0] * u[0];
+                acc[5] += rho * u[1] * u[1];
+                acc[6] += rho * u[2] * u[2];
+                acc[7] += rho * u[0] * u[1];
+                acc[8] += rho * u[0] * u[2];
+                acc[9] += rho * u[1] * u[2];
+            }
+#pragma unroll
+    for (int q = 0; q < 10; ++q) out[(int64_t)q * Nc + c] = acc[q];
+}
+
 // ---------------------------------------------------------------------------------------
 // Deterministic FP64 reduction over all fluid cells: per tile (CTA) partial sums reduced by
 // warp shuffles, then one CTA sums the partials in a fixed order.
@@ -410,6 +458,14 @@ cudaError_t LBM_CAT(launch_cells_, LBM_Q, LBM_ST)(int op, int force, const CellA
         case CELL_SET:
             k_set<<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, fk);
             break;
+        case CELL_COARSE: {
+            const int r = s.ratio;
+            if (r < 1 || s.blk.nx % r || s.blk.ny % r || s.blk.nz % r) return cudaErrorInvalidValue;
+            const int64_t Nc = N / ((int64_t)r * r * r);
+            k_coarse<<<(unsigned)((Nc + threads - 1) / threads), threads, 0, s.stream>>>(
+                (const StoreT *)s.a, s.blocks, s.block, s.layout, r, s.f64, s.mask, fk, s.F[0], s.F[1], s.F[2]);
+            break;
+        }
         case CELL_MACRO:
             k_macro<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blocks, s.block, s.layout, s.rho, s.u, s.mask,
                                                               fk, s.F[0], s.F[1], s.F[2]);

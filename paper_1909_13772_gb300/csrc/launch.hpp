@@ -53,6 +53,7 @@ struct CellArgs {
     double *f64;        // get: out f[Q*N]; set: in; init: rho[N] then u[3N]
     double *rho, *u;    // macroscopic out
     const uint32_t *mask;
+    int ratio;  // coarse: edge of the coarse cell in interior cells
     double F[3];
     double base[27];
     Coll<double> cd;
@@ -78,7 +79,7 @@ inline const Coll<double> &coll_of(const Coll<double> &d, const Coll<float> &, d
 inline const Coll<float> &coll_of(const Coll<double> &, const Coll<float> &f, float *) { return f; }
 
 // Cell-kernel operations of launch_cells.
-enum CellOp { CELL_INIT = 0, CELL_GET = 1, CELL_SET = 2, CELL_MACRO = 3 };
+enum CellOp { CELL_INIT = 0, CELL_GET = 1, CELL_SET = 2, CELL_MACRO = 3, CELL_COARSE = 4 };
 
 // Entry points of the per-(stencil, storage) objects; storage 0 fp64, 1 fp32, 2 bf16-dev,
 // 3 fp16-dev.  sweep.cu defines launch_sweep_<Q>_<ST>; aux.cu the other three.

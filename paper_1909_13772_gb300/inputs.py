@@ -16,6 +16,7 @@ porous beds of Sec. 5.1.3 -- are not available; these stand in for them):
 from __future__ import annotations
 
 import math
+import os
 
 import numpy as np
 
@@ -69,31 +70,47 @@ def turbulence(n: int, seed: int = 1909, kmax: int = 32, umax: float = 0.05, dty
     Returns rho[z,y,x], u[3,z,y,x].
     """
     rng = np.random.default_rng(seed)
+    try:  # multithreaded transforms when SciPy is present (same transforms, same results)
+        import scipy.fft as _fft
+        kw = {"workers": os.cpu_count() or 1}
+    except ImportError:  # pragma: no cover
+        _fft, kw = np.fft, {}
     kf = np.fft.fftfreq(n, d=1.0 / n)
     kr = np.fft.rfftfreq(n, d=1.0 / n)
-    KZ, KY, KX = np.meshgrid(kf, kf, kr, indexing="ij")  # half spectrum along x
+    KZ, KY, KX = kf[:, None, None], kf[None, :, None], kr[None, None, :]  # half spectrum along x
     k2 = KX * KX + KY * KY + KZ * KZ
     kmag = np.sqrt(k2)
     shell = np.rint(kmag)
     amp = np.where((shell >= 1) & (shell <= kmax), np.maximum(kmag, 1e-30) ** (-11.0 / 6.0), 0.0)
-    phase = np.exp(1j * rng.uniform(0.0, 2.0 * math.pi, size=kmag.shape))
-    direc = rng.standard_normal((3,) + kmag.shape)
-    uh = direc * (amp * phase)[None]
-    kv = np.stack([KX, KY, KZ])
-    kdotu = (kv * uh).sum(axis=0)
+    del shell, kmag
+    uh = np.exp(1j * rng.uniform(0.0, 2.0 * math.pi, size=k2.shape))
+    uh *= amp
+    del amp
+    uh = rng.standard_normal((3,) + k2.shape) * uh[None]
     with np.errstate(invalid="ignore", divide="ignore"):
-        uh = uh - kv * np.where(k2 > 0, kdotu / np.where(k2 > 0, k2, 1.0), 0.0)[None]
-    u = np.stack([np.fft.irfftn(uh[a], s=(n, n, n), axes=(0, 1, 2)) for a in range(3)])
+        inv_k2 = np.where(k2 > 0, 1.0 / np.where(k2 > 0, k2, 1.0), 0.0)
+    del k2
+
+    def project(uh):
+        # Leray projection: remove the component along k
+        kdotu = (KX * uh[0] + KY * uh[1] + KZ * uh[2]) * inv_k2
+        uh[0] -= KX * kdotu
+        uh[1] -= KY * kdotu
+        uh[2] -= KZ * kdotu
+        return uh
+
+    def to_real(uh):
+        return np.stack([_fft.irfftn(uh[a], s=(n, n, n), axes=(0, 1, 2), **kw) for a in range(3)])
+
+    u = to_real(project(uh))
     # the real part of a half spectrum is not exactly Hermitian on the kx = 0 and Nyquist
     # planes: project the real field once more so it is solenoidal to rounding
-    uh = np.stack([np.fft.rfftn(u[a], axes=(0, 1, 2)) for a in range(3)])
-    kdotu = (kv * uh).sum(axis=0)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        uh = uh - kv * np.where(k2 > 0, kdotu / np.where(k2 > 0, k2, 1.0), 0.0)[None]
-    u = np.stack([np.fft.irfftn(uh[a], s=(n, n, n), axes=(0, 1, 2)) for a in range(3)])
+    uh = np.stack([_fft.rfftn(u[a], axes=(0, 1, 2), **kw) for a in range(3)])
+    u = to_real(project(uh))
+    del uh
     speed = np.sqrt((u * u).sum(axis=0)).max()
     u *= umax / speed
-    return np.ones((n, n, n), dtype=dtype), u.astype(dtype)
+    return np.ones((n, n, n), dtype=dtype), u.astype(dtype, copy=False)
 
 
 def log_uniform_slabs(nslabs: int, lo: int, hi: int, rng) -> np.ndarray:
