@@ -132,8 +132,16 @@ def spectrum(u):
 
 
 def spectrum_error(E, E_ref):
+    """Relative L1 error of the spectrum over shells 1 .. N/2 (dominated by the energetic shells)."""
     k = slice(1, len(E_ref))
     return float(np.abs(E[k] - E_ref[k]).sum() / E_ref[k].sum())
+
+
+def log_spectrum_error(E, E_ref):
+    """Mean |ln(E / E_ref)| over shells 1 .. N/2 (every shell counts alike: shows pile-up or
+    over-damping near the grid cut-off)."""
+    k = slice(1, len(E_ref))
+    return float(np.mean(np.abs(np.log(np.maximum(E[k], 1e-300) / E_ref[k]))))
 
 
 # ---- runs through the library ------------------------------------------------------------
@@ -260,7 +268,8 @@ def study(n_f=512, r=4, tau_c=0.502, coarse_steps=256, snap_every=32, train_seed
     S = np.concatenate([b for _, b, _ in parts], axis=1)
     tau = np.concatenate([c for _, _, c in parts])
     P, hist, scales = train(rho, S, tau, tau_c, iters, batch, lr)
-    log("trained on %d samples: loss %.4g -> %.4g" % (tau.size, hist[0], hist[-1]))
+    log("trained on %d samples: loss %.4g -> %.4g; target nu_t mean %.3g, zero for %.1f %% of cells" % (
+        tau.size, hist[0], hist[-1], (tau.mean() - tau_c) / 3, 100 * np.mean(tau == tau_c)))
     # test seed: fine reference and the three coarse runs from its filtered initial state
     snaps = fine_run(n_f, r, test_seed, tau_c, coarse_steps, snap_every, kmax, umax)
     ref = {t: filtered_fields(m, r) for t, m in snaps}
@@ -271,20 +280,28 @@ def study(n_f=512, r=4, tau_c=0.502, coarse_steps=256, snap_every=32, train_seed
                           test_seed=test_seed, kmax=kmax, umax=umax, samples=int(tau.size), iters=iters,
                           batch=batch, lr=lr, cs=cs, scales=scales),
            "loss": [float(hist[0]), float(hist[-1])],
-           "target_tau_mean": float(tau.mean()), "runs": {}}
+           "target_tau_mean": float(tau.mean()), "target_zero_fraction": float(np.mean(tau == tau_c)),
+           "runs": {}}
     for name, cl in (("trt", None), ("smagorinsky", ("smag", cs)), ("mlp", ("mlp", P))):
         out, ms = coarse_run(rho0, u0, tau_c, coarse_steps, cl, snap_every)
-        errs = {t: spectrum_error(spectrum(u), E_ref[t]) for t, u in out if t > 0}
+        spec = {t: spectrum(u) for t, u in out if t > 0}
+        errs = {t: spectrum_error(E, E_ref[t]) for t, E in spec.items()}
+        lerrs = {t: log_spectrum_error(E, E_ref[t]) for t, E in spec.items()}
         final = out[-1][1]
         res["runs"][name] = {"ms_per_step": ms, "mlups": N ** 3 / ms / 1e3,
                              "spectrum_error": {str(t): e for t, e in errs.items()},
                              "spectrum_error_final": errs[coarse_steps],
                              "spectrum_error_mean": float(np.mean(list(errs.values()))),
-                             "energy_final": float(0.5 * (final * final).sum()),
+                             "log_spectrum_error": {str(t): e for t, e in lerrs.items()},
+                             "log_spectrum_error_final": lerrs[coarse_steps],
+                             "log_spectrum_error_mean": float(np.mean(list(lerrs.values()))),
+                             "energy": {str(t): float(0.5 * (u * u).sum()) for t, u in out},
+                             "E_final": spec[coarse_steps].tolist(),
                              "finite": bool(np.isfinite(final).all())}
-        log("%-12s %.3f ms/step  spectrum error final %.4f mean %.4f" % (
-            name, ms, errs[coarse_steps], res["runs"][name]["spectrum_error_mean"]))
-    res["energy_ref_final"] = float(0.5 * (ref[coarse_steps][1] ** 2).sum())
+        log("%-12s %.3f ms/step  spectrum error final %.4f mean %.4f | log final %.4f mean %.4f" % (
+            name, ms, errs[coarse_steps], res["runs"][name]["spectrum_error_mean"], lerrs[coarse_steps],
+            res["runs"][name]["log_spectrum_error_mean"]))
+    res["energy_ref"] = {str(t): float(0.5 * (v[1] ** 2).sum()) for t, v in ref.items()}
     res["E_ref_final"] = E_ref[coarse_steps].tolist()
     res["seconds"] = time.time() - t0
     return res
@@ -303,17 +320,21 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3000)
     ap.add_argument("--batch", type=int, default=16384)
     ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--umax", type=float, default=0.05)
+    ap.add_argument("--kmax", type=int, default=None)
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     lo, _, hi = a.train_seeds.partition("-")
     seeds = range(int(lo), int(hi or lo) + 1)
-    res = study(a.fine, a.ratio, a.tau, a.steps, a.snap, seeds, a.test_seed, sample=a.sample, iters=a.iters,
-                batch=a.batch, lr=a.lr)
+    res = study(a.fine, a.ratio, a.tau, a.steps, a.snap, seeds, a.test_seed, kmax=a.kmax, umax=a.umax,
+                sample=a.sample, iters=a.iters, batch=a.batch, lr=a.lr)
     txt = json.dumps(res)
     if a.out:
         with open(a.out, "w") as f:
             f.write(txt + "\n")
-    print(json.dumps({k: v for k, v in res.items() if k != "E_ref_final"}, indent=1))
+    short = {k: v for k, v in res.items() if k != "E_ref_final"}
+    short["runs"] = {k: {kk: vv for kk, vv in v.items() if kk != "E_final"} for k, v in res["runs"].items()}
+    print(json.dumps(short, indent=1))
 
 
 if __name__ == "__main__":
