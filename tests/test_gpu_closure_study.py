@@ -64,10 +64,19 @@ def test_coarse_moments_rejects_non_dividing_ratio(torch):
 
 
 def test_trained_closure_beats_plain_trt(torch):
-    """Small study: 128^3 fine FP64 runs (3 training seeds), 32^3 coarse runs at tau = 0.502."""
-    res = cs.study(n_f=128, r=4, tau_c=0.502, coarse_steps=96, snap_every=16, train_seeds=range(1, 4),
-                   test_seed=9, umax=0.05, sample=8192, iters=600, batch=4096, lr=3e-3, log=lambda *a: None)
+    """Small study in the under-resolved regime: 128^3 fine FP64 runs (3 training seeds), 32^3
+    coarse runs at tau = 0.502, max |u| = 0.1, about three large-eddy turnovers.  Plain TRT
+    piles up energy at the grid scale (or diverges); the trained network must do better on
+    both spectrum scores, and its run must stay finite."""
+    res = cs.study(n_f=128, r=4, tau_c=0.502, coarse_steps=512, snap_every=64, train_seeds=range(1, 4),
+                   test_seed=9, umax=0.1, sample=16384, iters=1500, batch=8192, lr=2e-3, log=lambda *a: None)
     runs = res["runs"]
-    assert all(v["finite"] for v in runs.values())
-    assert res["loss"][1] < res["loss"][0]
-    assert runs["mlp"]["spectrum_error_final"] < runs["trt"]["spectrum_error_final"], runs
+    assert runs["mlp"]["finite"] and runs["smagorinsky"]["finite"]
+    assert res["loss"][1] < 0.5 * res["loss"][0]
+
+    def score(name, key):
+        v = runs[name][key]
+        return v if runs[name]["finite"] and np.isfinite(v) else np.inf
+
+    for key in ("spectrum_error_final", "log_spectrum_error_final"):
+        assert score("mlp", key) < score("trt", key), (key, runs["mlp"][key], runs["trt"][key])
