@@ -162,7 +162,7 @@ def measured_peaks():
 def sweep_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1909_13772_gb300", "csrc")
-    for name in ("sweep.cu", "kernels.cuh", "lattice.cuh", "select.cuh"):
+    for name in ("sweep.cu", "cell.cuh", "kernels.cuh", "lattice.cuh", "select.cuh"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -531,6 +531,94 @@ def run_turbulence(args):
         print(json.dumps(out), flush=True)
 
 
+def run_closure(args):
+    """Locally varying relaxation (learned closure, C5 coarse grid): D3Q19 TRT tau0 = 0.502,
+    FP32 storage, AA pattern, periodic N^3 box of decaying turbulence (random-phase k^(-5/3)
+    start, default_rng(9), shells 1..N/4, max|u| = 0.1).  Each step once with the constant
+    rate, once with Smagorinsky (C_s = 0.17) and once with the tensor-core network fused into
+    the collision.  Value: MLUPS of the network step at 128^3; roofline of the network sweep at
+    the largest size (its cost is the SiLU evaluations on the special-function unit)."""
+    import torch
+    rank, world, local = dist_setup()
+    from paper_1909_13772_gb300 import closure_study, inputs, lbm
+    lbm.load_library()
+    stream = torch.cuda.Stream()
+    net = closure_study.init_params(0, 100.0, 300.0, 1e-3)
+    sizes = [128, 256]
+    res = {}
+    kt_net = None
+    for n in sizes:
+        rho, u = inputs.turbulence(n, seed=9, kmax=n // 4, umax=0.1)
+        for name in ("trt", "smagorinsky", "mlp"):
+            p = lbm.make_params(stencil=lbm.D3Q19, collision=lbm.TRT, storage=lbm.FP32, pattern=lbm.AA,
+                                omega=1 / 0.502, magic_lambda=LAMBDA, periodic=(1, 1, 1))
+            sim = lbm.Simulation(p, [((0, 0, 0), (n, n, n))], stream=stream.cuda_stream)
+            if name == "smagorinsky":
+                sim.set_closure(lbm.CLOSURE_SMAGORINSKY, cs=0.17)
+            elif name == "mlp":
+                sim.set_closure(lbm.CLOSURE_MLP, mlp_params=net)
+            sim.init(0, rho, u)
+            sim.step(args.warmup)
+            torch.cuda.synchronize()
+            barrier(world)
+            lbm.lbm_read_timing(sim.ctx, reset=True)
+            lbm.lbm_enable_timing(sim.ctx, True)
+            sim.step(min(args.steps, 50))
+            lbm.lbm_enable_timing(sim.ctx, False)
+            kt = lbm.lbm_read_timing(sim.ctx, reset=True)
+            torch.cuda.synchronize()
+            sampler = ClockSampler(torch.cuda.current_device())
+            start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            sim.step(args.steps)
+            end.record(stream)
+            torch.cuda.synchronize()
+            clocks = sampler.stop()
+            ms = start.elapsed_time(end)
+            d = sim.step_diagnostics()
+            sim.close()
+            ups, tmax = aggregate(n ** 3 * args.steps, ms / 1e3, world)
+            sweep_ms = kt["sweep"][0] / max(1, kt["sweep"][1])
+            res["%s-%d" % (name, n)] = {"mlups": round(ups / 1e6, 1), "ms_per_step": round(tmax * 1e3 / args.steps, 4),
+                                        "sweep_ms": round(sweep_ms, 4), "finite": d["nonfinite"] == 0,
+                                        "clocks": clocks}
+            if name == "mlp" and n == sizes[-1]:
+                kt_net = (sweep_ms, clocks)
+        del rho, u
+    n = sizes[-1]
+    sweep_ms, clocks = kt_net
+    peak_hbm, peak_kind = measured_peaks()
+    # special-function-unit work per cell: 64 hidden units x (exp2 + reciprocal) in the SiLU,
+    # softplus (exp2 + log2), 3 reciprocals (1/rho, 1/tau, omega-): 133 operations
+    sfu_per_cell = 133
+    sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
+    sfu_peak = 16 * 152 * sm_clock * 1e6 / 1e12  # T operations/s: 16 per clock per SM
+    sfu_ach = sfu_per_cell * n ** 3 / (sweep_ms / 1e3) / 1e12
+    alg_bytes = 2 * 19 * 4 * n ** 3
+    mma_flops = 2 * (16 * 32 + 32 * 32 + 32 * 8) * n ** 3  # padded MMA shapes per cell
+    out = {"metric": "MLUPS of the learned-closure step (tensor-core network fused into the collision)",
+           "value": res["mlp-128"]["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["mlp-128"]["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16 x bf16 -> f32)",
+           "data": "synthetic (seeded random-phase turbulence)",
+           "config": {"workload": "learned closure, D3Q19 TRT tau0=0.502 periodic 128^3 decaying turbulence, "
+                                  "FP32 AA, 7-32-32-1 SiLU network", "sizes": sizes,
+                      "l2": "no flush: 128^3 FP32 state 318 MB > 129 MB L2"},
+           "roofline": {"bound": "alu", "achieved": round(sfu_ach, 3), "peak": round(sfu_peak, 3),
+                        "unit": "Tops/s (special-function unit)", "frac": round(sfu_ach / sfu_peak, 4),
+                        "traffic": None, "kernel": "k_closure_sweep<network> at %d^3" % n,
+                        "peak_source": "16 SFU operations per clock per SM x 152 SMs x max SM clock",
+                        "sweep_ms": round(sweep_ms, 4),
+                        "hbm_gbs": round(alg_bytes / (sweep_ms / 1e3) / 1e9, 1),
+                        "hbm_frac": round(alg_bytes / (sweep_ms / 1e3) / 1e9 / peak_hbm, 4),
+                        "tensor_tflops": round(mma_flops / (sweep_ms / 1e3) / 1e12, 2)},
+           "cost_vs_constant_rate": {k: round(res["mlp-%d" % k]["ms_per_step"] / res["trt-%d" % k]["ms_per_step"], 3)
+                                     for k in sizes},
+           "variants": res, "clocks": res["mlp-128"]["clocks"]}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -576,9 +664,10 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="porous: replay step pairs as CUDA graphs")
     ap.add_argument("--autotune", action="store_true", help="porous: pick the sweep tile with lbm_autotune")
     ap.add_argument("--per-block", action="store_true", help="porous: one sweep launch per block (comparison)")
-    ap.add_argument("--workload", choices=["channel", "porous", "turbulence"], default="channel",
+    ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure"], default="channel",
                     help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed; "
-                         "turbulence: D3Q27 decaying turbulence, storage variants and their errors")
+                         "turbulence: D3Q27 decaying turbulence, storage variants and their errors; "
+                         "closure: constant rate vs Smagorinsky vs the learned closure")
     ap.add_argument("--turb-size", type=int, default=512)
     ap.add_argument("--turb-err-size", type=int, default=256)
     ap.add_argument("--turb-fp64-perf", action="store_true")
@@ -591,6 +680,8 @@ def main(argv=None):
         run_porous(args)
     elif args.workload == "turbulence":
         run_turbulence(args)
+    elif args.workload == "closure":
+        run_closure(args)
     else:
         run_ours(args)
 

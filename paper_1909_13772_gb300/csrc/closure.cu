@@ -51,9 +51,38 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// SiLU of the inference path with the fast intrinsics (__expf, __fdividef: errors of a few
-// FP32 ulp, far below the BF16 rounding applied to the result); z -> -inf gives -0.
-__device__ __forceinline__ float silu(float z) { return __fdividef(z, 1.0f + __expf(-z)); }
+#ifndef LBM_SILU_MODE
+#define LBM_SILU_MODE 1
+#endif
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// SiLU of the inference path, z sigma(z).  Mode 1: one special-function operation per unit.
+// With a = |z|, e = 2^(-a log2 e) in (0, 1] (ex2.approx, relative error ~2^-22) and
+// d = 1 + e in (1, 2], r = 1/d by Newton-Raphson on the FMA pipe from the linear seed
+// 24/17 - 8/17 d (relative error <= 1/17 on [1, 2]); three iterations square the error three
+// times, to below FP32 rounding.  sigma(z) = r for z >= 0 and e r for z < 0 (no cancellation).
+// Mode 0: the fast intrinsics __expf and __fdividef (two special-function operations).
+// Either way the error is far below the BF16 rounding applied to the result.
+__device__ __forceinline__ float silu(float z)
+{
+#if LBM_SILU_MODE == 1
+    const float a = fabsf(z);
+    const float e = ex2_approx(-1.4426950408889634f * a);
+    const float d = 1.0f + e;
+    float r = fmaf(-8.0f / 17.0f, d, 24.0f / 17.0f);
+#pragma unroll
+    for (int it = 0; it < 3; ++it) r = fmaf(r, fmaf(-d, r, 1.0f), r);
+    return z * (z >= 0.0f ? r : e * r);
+#else
+    return __fdividef(z, 1.0f + __expf(-z));
+#endif
+}
 __device__ __forceinline__ float softplus(float y) { return y > 30.0f ? y : log1pf(expf(y)); }
 
 // Per-warp MLP on 32 cells (one per lane): the features of all lanes form A = X (32 x 16,

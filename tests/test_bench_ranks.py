@@ -1,0 +1,57 @@
+"""Rank logic of bench.py on CPU: two gloo ranks (max-over-ranks timing, whole-job
+aggregation), and the reference arm's rule that only rank 0 works."""
+import multiprocessing as mp
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    import torch.distributed as dist
+    r, w, _ = bench.dist_setup(backend="gloo")
+    bench.barrier(w)
+    tmax = bench.reduce_max(0.5 + r, w)             # rank 1 is the slow one
+    value, t = bench.aggregate(1000.0, 1.0 + r, w)  # 1000 units per rank
+    q.put((r, w, tmax, value, t))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_max_time_and_sum_the_units():
+    pytest.importorskip("torch")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r, (rank, world, tmax, value, t) in enumerate(out):
+        assert (rank, world) == (r, 2)
+        assert tmax == 1.5
+        assert t == 2.0 and value == 2000.0 / 2.0
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"])
+    assert capsys.readouterr().out == ""
