@@ -330,6 +330,14 @@ lbm_status lbm_mlp_train(lbm_mlp *m, const float *X_dev, const float *T_dev, int
                          int64_t iters, float lr, double *loss_history);
 void lbm_mlp_destroy(lbm_mlp *m);
 
+/* Per-block diagnostics of the stored state (the per-block reductions of the paper's
+ * per-block data layout, Sec. 4.1-4.2): out[8 b + k] for block b, k = mass, momentum x, y, z,
+ * kinetic energy, max speed, non-finite cells, fluid cells (the lbm_diagnostics fields, as
+ * doubles), FP64 sums in a fixed order over the block's tiles.  out: host array of
+ * 8 * nblocks doubles.  Synchronises the stream.  Summing the blocks' records gives
+ * lbm_reduce up to the order of the sums. */
+lbm_status lbm_reduce_blocks(lbm_ctx *ctx, double *out);
+
 /* Box sums of a block for coarse-graining (the filtered fine-grid fields that train and judge
  * the learned closure): for each coarse cell of ratio^3 interior cells (every block edge
  * divisible by ratio), the sums over its fluid cells of rho, rho u_x, rho u_y, rho u_z and

@@ -6,6 +6,7 @@
 // lists handled by their own kernel; Sec. 5.1.2 fused stream-collide sweep.)
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -902,6 +903,41 @@ lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
     CK(do_cells(c->q, c->storage, CELL_SET, 0, a), "set_pdfs kernel");
     c->step_diag_valid = false;
     CK(cudaStreamSynchronize(c->stream), "set_pdfs");
+    return LBM_OK;
+}
+
+lbm_status lbm_reduce_blocks(lbm_ctx *c, double *out)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    lbm_status s = prepare(c);
+    if (s != LBM_OK) return s;
+    const int64_t nb = (int64_t)c->blocks.size();
+    std::fill(out, out + 8 * nb, 0.0);
+    if (c->plan.tiles.empty()) return LBM_OK;
+    if ((s = ensure_scratch(c, 8 * nb + nb + 1)) != LBM_OK) return s;  // records + int64 ranges
+    // tile ranges of the blocks (tiles are stored block by block) after the output records
+    int64_t *d_start = reinterpret_cast<int64_t *>(c->d_scratch + 8 * nb);
+    CK(cudaMemcpyAsync(d_start, c->tile_start.data(), (nb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream),
+       "copy tile ranges");
+    ReduceArgs r{};
+    r.a = c->pattern == LBM_TWO_GRID ? c->arr[c->cur] : c->arr[0];
+    r.blocks = c->d_blocks;
+    r.tiles = c->d_tiles;
+    r.ntiles = (int64_t)c->plan.tiles.size();
+    r.tx = c->tile[0];
+    r.ty = c->tile[1];
+    r.tz = c->tile[2];
+    r.layout = state_layout(c);
+    for (int a = 0; a < 3; ++a) r.F[a] = c->p.force[a];
+    for (int i = 0; i < 27; ++i) r.base[i] = c->base[i];
+    r.partials = c->d_partials;
+    r.out = c->d_out;
+    r.stream = c->stream;
+    CK(do_reduce(c->q, c->storage, r), "reduction kernels");
+    CK(launch_block_final(c->d_partials, d_start, nb, c->d_scratch, c->stream), "per-block reduction");
+    CK(cudaMemcpyAsync(out, c->d_scratch, 8 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "copy per-block diagnostics");
+    CK(cudaStreamSynchronize(c->stream), "reduce_blocks");
     return LBM_OK;
 }
 

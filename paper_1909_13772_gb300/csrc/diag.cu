@@ -1,6 +1,7 @@
-// diag.cu -- second pass of the step diagnostics: the sweep writes one record of 8 partial
-// sums per CTA (tile); one CTA adds them up in a fixed order, so the result is the same from
-// run to run.  Record: mass, momentum x/y/z, kinetic energy, max |u| (max, not sum),
+// diag.cu -- second pass of the step diagnostics and of the per-block reduction: the sweep
+// (or k_reduce_tiles) writes one record of 8 partial sums per CTA (tile); one CTA adds up the
+// records of the whole domain, or one CTA per block those of its tiles, in a fixed order, so
+// the result is the same from run to run.  Record: mass, momentum x/y/z, kinetic energy, max |u| (max, not sum),
 // non-finite cells, fluid cells.
 #include "launch.hpp"
 
@@ -18,7 +19,8 @@ __device__ __forceinline__ double dmax(double v)
     return v;
 }
 
-__global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partials, int64_t n, double *__restrict__ out)
+// Fixed-order sum of n records into out[8] by the calling CTA.
+__device__ __forceinline__ void final_sum(const double *__restrict__ partials, int64_t n, double *__restrict__ out)
 {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t p = threadIdx.x; p < n; p += blockDim.x)
@@ -39,11 +41,33 @@ __global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ p
     }
 }
 
+__global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partials, int64_t n, double *__restrict__ out)
+{
+    final_sum(partials, n, out);
+}
+
+// Per block: CTA b sums the records of tiles start[b] .. start[b+1] - 1 into out[8 b ..].
+__global__ void __launch_bounds__(256) k_block_final(const double *__restrict__ partials,
+                                                     const int64_t *__restrict__ start, double *__restrict__ out)
+{
+    const int64_t b = blockIdx.x;
+    final_sum(partials + start[b] * 8, start[b + 1] - start[b], out + b * 8);
+}
+
 }  // namespace
 
 cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, cudaStream_t s)
 {
     k_diag_final<<<1, 256, 0, s>>>(partials, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_final(const double *partials, const int64_t *start, int64_t nblocks, double *out,
+                               cudaStream_t s)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_block_final<<<(unsigned)nblocks, 256, 0, s>>>(partials, start, out);
     return cudaGetLastError();
 }
 

@@ -85,6 +85,10 @@ enum CellOp { CELL_INIT = 0, CELL_GET = 1, CELL_SET = 2, CELL_MACRO = 3, CELL_CO
 // 3 fp16-dev.  sweep.cu defines launch_sweep_<Q>_<ST>; aux.cu the other three.
 // Second pass of the diagnostics: fixed-order sum of n per-CTA records into out[8].
 cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, cudaStream_t s);
+// Per-block second pass: block b sums the records of tiles start[b] .. start[b+1] - 1 (tiles
+// are stored block by block) into out[8 b .. 8 b + 7].
+cudaError_t launch_block_final(const double *partials, const int64_t *start, int64_t nblocks, double *out,
+                               cudaStream_t s);
 
 #define LBM_DECLARE(Q, ST)                                                  \
     cudaError_t launch_sweep_##Q##_##ST(const SweepArgs &s);                \

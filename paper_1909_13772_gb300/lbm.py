@@ -83,6 +83,7 @@ _SIGS = {
     "lbm_plan_params": ([_vp, _dp, ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_plan_mask": ([_vp, ctypes.c_int32, _P(ctypes.c_uint32), ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_reduce_noalloc": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _dp, _vp, _vp], ctypes.c_int),
+    "lbm_reduce_blocks": ([_vp, _dp], ctypes.c_int),
     "lbm_coarse_moments": ([_vp, ctypes.c_int32, ctypes.c_int32, _dp], ctypes.c_int),
     "lbm_set_closure": ([_vp, ctypes.c_int32, ctypes.c_double, _P(ctypes.c_float)], ctypes.c_int),
     "lbm_mlp_create": ([_P(ctypes.c_float), ctypes.c_int64, _vp, _P(_vp)], ctypes.c_int),
@@ -341,6 +342,14 @@ def lbm_reduce_noalloc(f_dev_ptr: int, stencil: int, storage: int, ncells: int, 
         raise LbmError(st, "lbm_reduce_noalloc: " + why)
 
 
+def lbm_reduce_blocks(ctx, nblocks) -> np.ndarray:
+    """Per-block diagnostics: array [nblocks, 8] (mass, momentum x/y/z, kinetic energy, max
+    speed, non-finite cells, fluid cells)."""
+    out = np.empty((nblocks, 8), np.float64)
+    _check(ctx, load_library().lbm_reduce_blocks(ctx, _ptr(out, ctypes.c_double)))
+    return out
+
+
 def lbm_coarse_moments(ctx, block, ratio, shape) -> np.ndarray:
     """Box sums over ratio^3 cells: array [10, NZ, NY, NX] (rho, rho u (3), rho u_a u_b (6));
     ``shape`` = the block's interior size (nx, ny, nz)."""
@@ -513,6 +522,9 @@ class Simulation:
 
     def launches(self):
         return lbm_kernel_launches(self.ctx)
+
+    def reduce_blocks(self):
+        return lbm_reduce_blocks(self.ctx, len(self.blocks))
 
     def coarse_moments(self, b, ratio):
         return lbm_coarse_moments(self.ctx, b, ratio, self.blocks[b][1])

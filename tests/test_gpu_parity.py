@@ -206,6 +206,41 @@ def test_reduction_matches_oracle_and_is_deterministic():
     assert d1["fluid_cells"] == int((case.global_flags() == 0).sum())
 
 
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+def test_per_block_reduction_matches_oracle(pattern):
+    """lbm_reduce_blocks: each block's record against the oracle's moments over that block's
+    region; the records add up to lbm_reduce."""
+    case = _porous_case(lbm.FP64, pattern)
+    rho, u = inputs.random_state(case.shape, seed=13, rho_amp=0.02, u_amp=0.02)
+    s = case.make_sim()
+    init_sim(s, rho, u)
+    s.step(5)
+    per = s.reduce_blocks()
+    tot = s.reduce()
+    blocks = s.blocks
+    s.close()
+    _, f = oracle_run(case, rho, u, 5)
+    orho, ou = oracle.macroscopic(case.oracle_params(), f, case.global_flags())
+    fluid = case.global_flags() == 0
+    assert per.shape == (len(blocks), 8)
+    for b, (o, sz) in enumerate(blocks):
+        sl = (slice(o[2], o[2] + sz[2]), slice(o[1], o[1] + sz[1]), slice(o[0], o[0] + sz[0]))
+        fl, r, v = fluid[sl], orho[sl], ou[(slice(None),) + sl]
+        assert per[b, 7] == fl.sum()
+        if not fl.any():
+            assert np.all(per[b, :7] == 0)
+            continue
+        assert abs(per[b, 0] - r[fl].sum()) <= 1e-13 * r[fl].sum()
+        for a in range(3):
+            assert abs(per[b, 1 + a] - (r * v[a])[fl].sum()) <= 1e-10 * r[fl].sum() * 0.02
+        e = (0.5 * r * (v * v).sum(axis=0))[fl].sum()
+        assert abs(per[b, 4] - e) <= 1e-10 * e
+        assert abs(per[b, 5] - np.sqrt((v * v).sum(axis=0))[fl].max()) <= 1e-12
+        assert per[b, 6] == 0
+    assert abs(per[:, 0].sum() - tot["mass"]) <= 1e-13 * tot["mass"]
+    assert per[:, 7].sum() == tot["fluid_cells"]
+
+
 def test_divergence_is_reported():
     case = Case(shape=(40, 9, 6), storage=lbm.FP32)
     p = lbm.make_params(stencil=19, storage=lbm.FP32, omega=1.2, diag_interval=2)
