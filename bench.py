@@ -588,9 +588,9 @@ def run_closure(args):
     n = sizes[-1]
     sweep_ms, clocks = kt_net
     peak_hbm, peak_kind = measured_peaks()
-    # special-function-unit work per cell: one exp2 per hidden unit (64; the SiLU's reciprocal
-    # runs on the FMA pipe), softplus (exp2 + log2), 3 reciprocals (1/rho, 1/tau, omega-)
-    sfu_per_cell = 69
+    # special-function-unit work per cell: 64 hidden units x (exp2 + reciprocal) in the SiLU,
+    # softplus (exp2 + log2), 3 reciprocals (1/rho, 1/tau, omega-): 133 operations
+    sfu_per_cell = 133
     sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
     sfu_peak = 16 * 152 * sm_clock * 1e6 / 1e12  # T operations/s: 16 per clock per SM
     sfu_ach = sfu_per_cell * n ** 3 / (sweep_ms / 1e3) / 1e12

@@ -429,20 +429,48 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
     // TRT: Lambda = (1/w+ - 1/2)(1/w- - 1/2); at w+ = 0 (no relaxation of the even part) the
     // IEEE evaluation gives the limit w- = 2.
     if (p.collision == LBM_TRT) wm = 1.0 / (p.magic_lambda / (1.0 / wp - 0.5) + 0.5);
-    c->cd.omega_p = wp;
-    c->cd.omega_m = wm;
-    c->cd.a_p = 1.0 - 0.5 * wp;
-    c->cd.a_m = 1.0 - 0.5 * wm;
-    for (int a = 0; a < 3; ++a) c->cd.F[a] = p.force[a];
     const LatticeView L = lattice_view(c->q);
-    for (int i = 0; i < 27; ++i) c->base[i] = (c->storage >= LBM_BF16_DEV && i < L.q) ? L.w[i] * p.rho0 : 0.0;
-    for (int i = 0; i < 27; ++i) c->cd.base[i] = c->base[i];
-    c->cf.omega_p = (float)wp;
-    c->cf.omega_m = (float)wm;
-    c->cf.a_p = (float)c->cd.a_p;
-    c->cf.a_m = (float)c->cd.a_m;
-    for (int a = 0; a < 3; ++a) c->cf.F[a] = (float)p.force[a];
-    for (int i = 0; i < 27; ++i) c->cf.base[i] = (float)c->base[i];
+    const bool dev = c->storage >= LBM_BF16_DEV;
+    for (int i = 0; i < 27; ++i) c->base[i] = (dev && i < L.q) ? L.w[i] * p.rho0 : 0.0;
+    Coll<double> &d = c->cd;
+    d = Coll<double>{};
+    d.omega_p = wp;
+    d.omega_m = wm;
+    d.a_p = 1.0 - 0.5 * wp;
+    d.a_m = 1.0 - 0.5 * wm;
+    double wc[4] = {0, 0, 0, 0};  // weight per class |c|^2
+    for (int i = 0; i < L.q; ++i) wc[L.cx[i] * L.cx[i] + L.cy[i] * L.cy[i] + L.cz[i] * L.cz[i]] = L.w[i];
+    d.r = rates_of<double>(wp, wm, wc);
+    for (int k2 = 0; k2 < 4; ++k2) d.bw[k2] = 3.0 * d.a_p * wc[k2];
+    for (int i = 0; i < L.q; ++i) {
+        const double cF = L.cx[i] * p.force[0] + L.cy[i] * p.force[1] + L.cz[i] * p.force[2];
+        d.fa[i] = 9.0 * d.a_p * L.w[i] * cF;
+        d.fc[i] = 3.0 * d.a_m * L.w[i] * cF;
+    }
+    for (int a = 0; a < 3; ++a) d.F[a] = p.force[a];
+    d.rho0 = dev ? p.rho0 : 0.0;
+    for (int i = 0; i < 27; ++i) d.base[i] = c->base[i];
+    // FP32 copy of every constant
+    Coll<float> &f = c->cf;
+    f.omega_p = (float)d.omega_p;
+    f.omega_m = (float)d.omega_m;
+    f.a_p = (float)d.a_p;
+    f.a_m = (float)d.a_m;
+    f.r.rest = (float)d.r.rest;
+    f.r.alpha = (float)d.r.alpha;
+    f.r.beta = (float)d.r.beta;
+    for (int k2 = 0; k2 < 4; ++k2) {
+        f.r.pw[k2] = (float)d.r.pw[k2];
+        f.r.mw[k2] = (float)d.r.mw[k2];
+        f.bw[k2] = (float)d.bw[k2];
+    }
+    for (int i = 0; i < 27; ++i) {
+        f.fa[i] = (float)d.fa[i];
+        f.fc[i] = (float)d.fc[i];
+        f.base[i] = (float)d.base[i];
+    }
+    for (int a = 0; a < 3; ++a) f.F[a] = (float)d.F[a];
+    f.rho0 = (float)d.rho0;
     *out = c;
     return LBM_OK;
 }

@@ -91,7 +91,8 @@ __device__ __forceinline__ int64_t nbr_addr(const NbrGeo *nb, Face fc, int x, in
 //   AA neighbour: bounce source A[i][x] (where the E layout keeps f*_opp(i)(x)); the value
 //   f*_i(x) whose target x + c_i is no-slip (bit opp(i)) goes to A[opp i][x], where the next
 //   local sweep reads it as f_opp(i)(x, t+1).
-// Gather the populations streaming into cell (x, y, z) (see the file header of sweep.cu).
+// Gather the populations streaming into cell (x, y, z) (see the file header of sweep.cu), as
+// stored: deviations f_i - w_i rho0 for the *_DEV storages (the collision works on them).
 template <int KIND, int FACE, bool MASK>
 __device__ __forceinline__ void gather_cell(R (&f)[kQ], StoreT *__restrict__ A, const DevBlock &B, const NbrGeo *nb,
                                             Face fc, int x, int y, int z, int64_t cell, uint32_t m, const R *base)
@@ -103,7 +104,7 @@ __device__ __forceinline__ void gather_cell(R (&f)[kQ], StoreT *__restrict__ A, 
         const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
         const bool bounce = MASK && i > 0 && ((m >> i) & 1u);
         if (KIND == SWEEP_AA_LOCAL) {
-            f[i] = S::ld_rw(a + (int64_t)i * B.slab + cell, base[i]);
+            f[i] = S::raw_rw(a + (int64_t)i * B.slab + cell);
             continue;
         }
         const int sl = KIND == SWEEP_PULL ? i : L::opp(i);  // slot read from the source cell
@@ -112,7 +113,7 @@ __device__ __forceinline__ void gather_cell(R (&f)[kQ], StoreT *__restrict__ A, 
         if (FACE == 1 && !bounce) o += wrap_shift(B, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
         if (FACE == 2 && !bounce)
             o = nbr_addr(nb, fc, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i), sl, o + B.offset) - B.offset;
-        f[i] = KIND == SWEEP_PULL ? S::ld(a + o, base[i]) : S::ld_rw(a + o, base[i]);
+        f[i] = KIND == SWEEP_PULL ? S::raw(a + o) : S::raw_rw(a + o);
     }
 }
 
@@ -133,10 +134,10 @@ __device__ __forceinline__ void scatter_cell(const R (&f)[kQ], StoreT *__restric
     for (int i = 0; i < kQ; ++i) {
         const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
         if (KIND == SWEEP_PULL) {
-            S::st(Bout + B.offset + (int64_t)i * B.slab + cell, f[i], base[i]);
+            S::st_raw(Bout + B.offset + (int64_t)i * B.slab + cell, f[i]);
         } else if (KIND == SWEEP_AA_LOCAL) {
             const int o = L::opp(i);
-            S::st(a + (int64_t)o * B.slab + cell, f[i], base[i]);
+            S::st_raw(a + (int64_t)o * B.slab + cell, f[i]);
         } else {
             const int o = L::opp(i);
             const bool bounce = MASK && i > 0 && ((m >> o) & 1u);
@@ -145,7 +146,7 @@ __device__ __forceinline__ void scatter_cell(const R (&f)[kQ], StoreT *__restric
             if (FACE == 1 && !bounce) d += wrap_shift(B, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i));
             if (FACE == 2 && !bounce)
                 d = nbr_addr(nb, fc, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i), i, d + B.offset) - B.offset;
-            S::st(a + d, f[i], base[i]);
+            S::st_raw(a + d, f[i]);
         }
     }
 }
@@ -168,7 +169,7 @@ __device__ __forceinline__ void update_cell(StoreT *__restrict__ A, StoreT *__re
     R f[kQ];
     gather_cell<KIND, FACE, MASK>(f, A, B, nb, fc, x, y, z, cell, m, k.base);
     R rho, ux, uy, uz;
-    collide<kQ, FORCE, R>(f, k, rho, ux, uy, uz);
+    collide<kQ, FORCE, R>(f, k, k.r, k.rho0, rho, ux, uy, uz);
     scatter_cell<KIND, FACE, MASK>(f, A, Bout, B, nb, fc, x, y, z, cell, m, k.base);
     dg.add(rho, ux, uy, uz);
 }

@@ -74,14 +74,42 @@ struct DevRun {
     int32_t len, sstride, dstride, pad;
 };
 
+// Relaxation constants of the pair form of the collision (see collide below), per weight
+// class c = |c_i|^2 (0 rest, 1 axis, 2 face diagonal, 3 corner).
+template <class R>
+struct Rates {
+    R rest;          // 1 - omega+
+    R alpha, beta;   // 1 - (omega+ + omega-)/2, (omega- - omega+)/2
+    R pw[4], mw[4];  // omega+ w_c, 3 omega- w_c
+};
+
 // Collision constants, in the arithmetic type R of the sweep.
 template <class R>
 struct Coll {
-    R omega_p, omega_m;  // TRT rates (SRT: equal)
-    R a_p, a_m;          // 1 - omega/2 factors of the Guo source
-    R F[3];              // body force
-    R base[27];          // storage offset per direction (w_i rho0 for *_DEV storages, else 0)
+    R omega_p, omega_m;    // TRT rates (SRT: equal)
+    R a_p, a_m;            // 1 - omega/2 factors of the Guo source
+    Rates<R> r;            // the rates in pair form
+    R bw[4];               // Guo source: 3 a+ w_c (multiplies u.F)
+    R fa[27], fc[27];      // Guo source per direction: 9 a+ w_i (c_i.F), 3 a- w_i (c_i.F)
+    R F[3];                // body force
+    R rho0;                // deviation base density of the storage (rho0 for *_DEV, else 0)
+    R base[27];            // storage offset per direction (w_i rho0 for *_DEV storages, else 0)
 };
+
+// Pair-form rates for omega+ / omega- (host or device).
+template <class R>
+__host__ __device__ __forceinline__ Rates<R> rates_of(R wp, R wm, const R (&wc)[4])
+{
+    Rates<R> r;
+    r.rest = R(1) - wp;
+    r.alpha = R(1) - R(0.5) * (wp + wm);
+    r.beta = R(0.5) * (wm - wp);
+    for (int c = 0; c < 4; ++c) {
+        r.pw[c] = wp * wc[c];
+        r.mw[c] = R(3) * wm * wc[c];
+    }
+    return r;
+}
 
 // ---------------------------------------------------------------------------------------
 // Storage formats.  T is the stored type, R the arithmetic type.  The *_DEV formats store
@@ -114,6 +142,10 @@ struct Storage<double> {
     static __device__ __forceinline__ R ld_rw(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { __stcs(p, v); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R) { *p = v; }
+    // stored value as is (the deviation for *_DEV formats): conversion only
+    static __device__ __forceinline__ R raw(const T *p) { return ld_src(p); }
+    static __device__ __forceinline__ R raw_rw(const T *p) { return *p; }
+    static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, v); }
 };
 
 template <>
@@ -124,6 +156,9 @@ struct Storage<float> {
     static __device__ __forceinline__ R ld_rw(const T *p, R) { return *p; }
     static __device__ __forceinline__ void st(T *p, R v, R) { __stcs(p, v); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R) { *p = v; }
+    static __device__ __forceinline__ R raw(const T *p) { return ld_src(p); }
+    static __device__ __forceinline__ R raw_rw(const T *p) { return *p; }
+    static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, v); }
 };
 
 template <>
@@ -134,6 +169,9 @@ struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ R ld_rw(const T *p, R base) { return base + __bfloat162float(*p); }
     static __device__ __forceinline__ void st(T *p, R v, R base) { __stcs(p, __float2bfloat16_rn(v - base)); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R base) { *p = __float2bfloat16_rn(v - base); }
+    static __device__ __forceinline__ R raw(const T *p) { return __bfloat162float(ld_src(p)); }
+    static __device__ __forceinline__ R raw_rw(const T *p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, __float2bfloat16_rn(v)); }
 };
 
 template <>
@@ -144,26 +182,35 @@ struct Storage<__half> {
     static __device__ __forceinline__ R ld_rw(const T *p, R base) { return base + __half2float(*p); }
     static __device__ __forceinline__ void st(T *p, R v, R base) { __stcs(p, __float2half_rn(v - base)); }
     static __device__ __forceinline__ void st_plain(T *p, R v, R base) { *p = __float2half_rn(v - base); }
+    static __device__ __forceinline__ R raw(const T *p) { return __half2float(ld_src(p)); }
+    static __device__ __forceinline__ R raw_rw(const T *p) { return __half2float(*p); }
+    static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, __float2half_rn(v)); }
 };
 
 // ---------------------------------------------------------------------------------------
 // Collision operator (Eq. 2-3 of the paper with SRT/TRT relaxation and Guo forcing), fused
-// over opposite direction pairs.  For each pair (i, o = opp(i)):
-//   s = f_i + f_o, d = f_i - f_o                     (even / odd parts, times 2)
-//   rho = f_0 + sum s,  rho u = sum c_i d + F/2
-//   feq+ = w rho (1 + 4.5 (c.u)^2 - 1.5 u.u),  feq- = 3 w rho c.u
-//   S+ = w (9 (c.u)(c.F) - 3 u.F),  S- = 3 w c.F
+// over opposite direction pairs.  TRT per pair (i, o = opp(i)), with s = f_i + f_o and
+// d = f_i - f_o:
 //   f*_i = f_i - w+ (s/2 - feq+) - w- (d/2 - feq-) + a+ S+ + a- S-
 //   f*_o = f_o - w+ (s/2 - feq+) + w- (d/2 - feq-) + a+ S+ - a- S-
-// which is the TRT operator written per pair; SRT is the case w- = w+.
+//   feq+ = w rho (1 + 4.5 (c.u)^2 - 1.5 u.u),  feq- = 3 w rho c.u,
+//   S+ = w (9 (c.u)(c.F) - 3 u.F),  S- = 3 w c.F,  rho u = sum c f + F/2
+// (SRT is the case w- = w+).  Collecting f_i and f_o:
+//   f*_i = alpha f_i + beta f_o + P + M,   f*_o = alpha f_o + beta f_i + P - M
+//   alpha = 1 - (w+ + w-)/2,  beta = (w- - w+)/2,  P = w+ feq+ + a+ S+,  M = w- feq- + a- S-.
+// The same update holds for values stored as deviations v_i = f_i - w_i rho0 (rho0 = the
+// deviation base; 0 for plain storage): since alpha + beta - 1 = -w+, the shift folds into P
+// through rb = rho (1 - 1.5 u.u) - rho0, and rho = rho0 + sum v, rho u = sum c v + F/2
+// (sum w = 1, sum w c = 0).  P, M use per-class constants w+ w, 3 w- w (Rates) and the
+// per-direction Guo constants of Coll.
 // ---------------------------------------------------------------------------------------
 template <int Q, bool FORCE, class R>
-__device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, R &rho_out, R &ux_out, R &uy_out, R &uz_out)
+__device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates<R> &rt, R rho0, R &rho_out,
+                                        R &ux_out, R &uy_out, R &uz_out)
 {
     using L = Lattice<Q>;
-    // pass 1: moments from the pair sums / differences (not kept: pass 2 recomputes them,
-    // which costs two adds per pair but keeps only the Q populations live)
-    R rho = f[0], jx = R(0), jy = R(0), jz = R(0);
+    // moments from the pair sums / differences (pass 2 does not need them again)
+    R rho = rho0 + f[0], jx = R(0), jy = R(0), jz = R(0);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
@@ -194,19 +241,21 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, R &rho_out,
     uy_out = uy;
     uz_out = uz;
     const R usq = ux * ux + uy * uy + uz * uz;
-    const R rb = rho * (R(1) - R(1.5) * usq);  // rho (1 - 1.5 u.u)
+    const R rb = rho * (R(1) - R(1.5) * usq) - rho0;
     const R uF = FORCE ? ux * k.F[0] + uy * k.F[1] + uz * k.F[2] : R(0);
+    R buF[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) buF[c] = FORCE ? k.bw[c] * uF : R(0);
     {
-        const R w0 = R(L::w(0));
-        R fs = f[0] - k.omega_p * (f[0] - w0 * rb);
-        if (FORCE) fs += k.a_p * (w0 * R(-3) * uF);
-        f[0] = fs;
+        R f0 = rt.rest * f[0] + rt.pw[0] * rb;
+        if (FORCE) f0 -= buF[0];
+        f[0] = f0;
     }
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
-        const R w = R(L::w(i));
+        const int c = L::cx(i) * L::cx(i) + L::cy(i) * L::cy(i) + L::cz(i) * L::cz(i);
         R cu = R(0);
         if (L::cx(i) > 0) cu += ux;
         if (L::cx(i) < 0) cu -= ux;
@@ -214,37 +263,25 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, R &rho_out,
         if (L::cy(i) < 0) cu -= uy;
         if (L::cz(i) > 0) cu += uz;
         if (L::cz(i) < 0) cu -= uz;
-        const R si = f[i] + f[o];
-        const R di = f[i] - f[o];
-        const R feqp = w * (rb + R(4.5) * rho * cu * cu);
-        const R feqm = w * R(3) * rho * cu;
-        const R ep = k.omega_p * (R(0.5) * si - feqp);
-        const R em = k.omega_m * (R(0.5) * di - feqm);
-        R fi = f[i] - ep - em;
-        R fo = f[o] - ep + em;
+        const R rcu = rho * cu;
+        R P = rt.pw[c] * fma(R(4.5) * cu, rcu, rb);
+        R M = rt.mw[c] * rcu;
         if (FORCE) {
-            R cF = R(0);
-            if (L::cx(i) > 0) cF += k.F[0];
-            if (L::cx(i) < 0) cF -= k.F[0];
-            if (L::cy(i) > 0) cF += k.F[1];
-            if (L::cy(i) < 0) cF -= k.F[1];
-            if (L::cz(i) > 0) cF += k.F[2];
-            if (L::cz(i) < 0) cF -= k.F[2];
-            const R sp = k.a_p * (w * (R(9) * cu * cF - R(3) * uF));
-            const R sm = k.a_m * (w * R(3) * cF);
-            fi += sp + sm;
-            fo += sp - sm;
+            P = fma(k.fa[i], cu, P) - buF[c];
+            M += k.fc[i];
         }
-        f[i] = fi;
-        f[o] = fo;
+        const R fi = f[i], fo = f[o];
+        f[i] = fma(rt.alpha, fi, fma(rt.beta, fo, P + M));
+        f[o] = fma(rt.alpha, fo, fma(rt.beta, fi, P - M));
     }
 }
 
+// Collision of full populations f (not deviations) with the context's constant rates.
 template <int Q, bool FORCE, class R>
 __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
 {
     R rho, ux, uy, uz;
-    collide<Q, FORCE, R>(f, k, rho, ux, uy, uz);
+    collide<Q, FORCE, R>(f, k, k.r, R(0), rho, ux, uy, uz);
 }
 
 // Moments of a stored post-collision state, in FP64: rho = sum f*, j = sum c f* - F/2.

@@ -25,10 +25,6 @@
 // caps the sweeps at 64 registers (1024 threads per SM); measured on the 256^3 channel it
 // beats the uncapped build by 6 % (two-grid) and 23 % (AA neighbour sweep).  The FP64 sweep
 // is bound by the FP64 pipe, not by memory parallelism: 2 CTAs per SM avoid spilling.
-#ifndef LBM_SWEEP_ZPAIR
-#define LBM_SWEEP_ZPAIR 0
-#endif
-
 #ifndef LBM_SWEEP_MINB
 #if LBM_ST == 0
 #define LBM_SWEEP_MINB 2
@@ -81,71 +77,6 @@ __device__ __forceinline__ void sweep_cells(StoreT *__restrict__ A, StoreT *__re
         fc.lo = ((x == 0 ? 1 : 0) | (y == 0 ? 2 : 0)) & axes;
         fc.hi = ((x == B.nx - 1 ? 1 : 0) | (y == B.ny - 1 ? 2 : 0)) & axes;
     }
-#if LBM_SWEEP_ZPAIR
-    {
-        // two cells (z, z + 1) per iteration: both gathers are issued before either collision,
-        // so each warp keeps 2 Q loads in flight; the face path is taken for the pair when any
-        // cell of the warp's pair lies on a face read in place
-        constexpr int kFace = kTable ? 2 : 1;
-        for (int z = t.z0; z < zend; z += 2) {
-            const bool two = z + 1 < zend;
-            const int64_t ca = B.cell(x, y, z);
-            const int64_t cb = ca + B.plane;
-            const uint32_t ma = masked ? B.mask[ca] : 0u;
-            const uint32_t mb = (masked && two) ? B.mask[cb] : 0u;
-            const bool la = !(ma & kMaskSolid), lb = two && !(mb & kMaskSolid);
-            Face fa_ = fc, fb_ = fc;
-            if (thr) {
-                fa_.lo |= (z == 0 ? 4 : 0) & axes;
-                fa_.hi |= (z == B.nz - 1 ? 4 : 0) & axes;
-                fb_.lo |= (z + 1 == 0 ? 4 : 0) & axes;
-                fb_.hi |= (z + 1 == B.nz - 1 ? 4 : 0) & axes;
-            }
-            const bool face = thr && ((fa_.lo | fa_.hi | fb_.lo | fb_.hi) != 0);
-            const bool use_face = kThr && __any_sync(__activemask(), face);
-            R fa[kQ], fb[kQ];
-#define LBM_PAIR_GATHER(FC, MK)                                                                   \
-    do {                                                                                          \
-        if (la) gather_cell<KIND, FC, MK>(fa, A, B, nb, fa_, x, y, z, ca, MK ? ma : 0u, k.base);     \
-        if (lb) gather_cell<KIND, FC, MK>(fb, A, B, nb, fb_, x, y, z + 1, cb, MK ? mb : 0u, k.base); \
-    } while (0)
-#define LBM_PAIR_SCATTER(F, C, M, FF, ZZ, FC, MK) \
-    scatter_cell<KIND, FC, MK>(F, A, Bout, B, nb, FF, x, y, ZZ, C, MK ? M : 0u, k.base)
-            const bool mk = masked && KIND != SWEEP_AA_LOCAL;
-            if (use_face) {
-                if (mk) LBM_PAIR_GATHER(kFace, true); else LBM_PAIR_GATHER(kFace, false);
-            } else {
-                if (mk) LBM_PAIR_GATHER(0, true); else LBM_PAIR_GATHER(0, false);
-            }
-            R rho, ux, uy, uz;
-            if (la) {
-                collide<kQ, FORCE, R>(fa, k, rho, ux, uy, uz);
-                if (use_face) {
-                    if (mk) LBM_PAIR_SCATTER(fa, ca, ma, fa_, z, kFace, true);
-                    else LBM_PAIR_SCATTER(fa, ca, ma, fa_, z, kFace, false);
-                } else {
-                    if (mk) LBM_PAIR_SCATTER(fa, ca, ma, fa_, z, 0, true);
-                    else LBM_PAIR_SCATTER(fa, ca, ma, fa_, z, 0, false);
-                }
-                dg.add(rho, ux, uy, uz);
-            }
-            if (lb) {
-                collide<kQ, FORCE, R>(fb, k, rho, ux, uy, uz);
-                if (use_face) {
-                    if (mk) LBM_PAIR_SCATTER(fb, cb, mb, fb_, z + 1, kFace, true);
-                    else LBM_PAIR_SCATTER(fb, cb, mb, fb_, z + 1, kFace, false);
-                } else {
-                    if (mk) LBM_PAIR_SCATTER(fb, cb, mb, fb_, z + 1, 0, true);
-                    else LBM_PAIR_SCATTER(fb, cb, mb, fb_, z + 1, 0, false);
-                }
-                dg.add(rho, ux, uy, uz);
-            }
-#undef LBM_PAIR_GATHER
-#undef LBM_PAIR_SCATTER
-        }
-        return;
-    }
-#endif
     for (int z = t.z0; z < zend; ++z) {
         const int64_t cell = B.cell(x, y, z);
         const uint32_t m = masked ? B.mask[cell] : 0u;
