@@ -11,7 +11,8 @@ namespace lbm {
 
 // The network in the form the tensor-core inference reads (staged in shared memory once per
 // CTA): weights in BF16, W1 padded to 16 inputs, w3 as row 0 of an 8-row block (the other
-// rows zero) so the output layer is one more MMA; biases and scales in FP32.
+// rows zero) so the output layer is one more MMA; biases and scales in FP32.  W1, b1, W2, b2
+// are stored halved (the SiLU is evaluated from z/2).
 struct MlpDev {
     __nv_bfloat16 w1[32][16];
     __nv_bfloat16 w2[32][32];

@@ -41,9 +41,33 @@ def _net(seed, s_rho=20.0, s_pi=200.0, s_tau=0.02):
     return mlp.pack(p)
 
 
+# Error of one SiLU evaluation of the inference path against the oracle's exact SiLU, both
+# rounded to BF16 at the same point.  With h = z/2 and SiLU = g(h) = h (1 + tanh h):
+#   tanh.approx.f32 (relative error <= 2^-10.9, |tanh| <= 1)  -> |h| 2^-10.9
+#   a BF16 rounding that falls the other way (one unit, 2^-7 |g| <= 2^-6 |h|)
+# in all <= 0.0161 |h| = 0.0081 |z|; the test allows 0.0125 |z|.
+SILU_REL = 0.0125
+
+
+def _inference_bound(P, X):
+    """First-order bound of |y_gpu - y_oracle| per sample: per-unit SiLU errors of SILU_REL |z|
+    propagated through |W2| and |w3| (SiLU' <= 1.1), plus FP32 summation (1e-5)."""
+    d = mlp.unpack(P)
+    bf = mlp._bf16
+    x = bf(X)
+    z1 = x @ bf(d["W1"]).T + d["b1"]
+    h1 = bf(z1 / (1 + np.exp(-z1)))
+    z2 = h1 @ bf(d["W2"]).T + d["b2"]
+    e1 = SILU_REL * np.abs(z1)
+    e2 = 1.1 * (e1 @ np.abs(bf(d["W2"])).T) + SILU_REL * np.abs(z2)
+    return e2 @ np.abs(bf(d["w3"])) + 1e-5
+
+
 def test_network_inference_matches_bf16_oracle(torch):
-    """Tensor-core inference (BF16 operands, FP32 sums) against the FP64 network with BF16
-    rounding at the same points.  Ragged n (not a multiple of the 32-sample warp tile)."""
+    """Tensor-core inference (BF16 operands, FP32 sums, SiLU from BF16 arithmetic) against the
+    FP64 network with BF16 rounding at the same points: every sample within the first-order
+    bound of the SiLU evaluation error, and the typical error well inside it.  Ragged n (not a
+    multiple of the 32-sample warp tile)."""
     P = _net(5)
     n = 4099
     X = _features(n, 1)
@@ -59,11 +83,12 @@ def test_network_inference_matches_bf16_oracle(torch):
         lbm.lbm_mlp_destroy(m)
     assert np.all(got[n:] == 7.0)
     err = np.abs(got[:n] - want)
-    # FP32 sums against FP64 sums: ~1e-6.  A BF16 rounding of a hidden unit decided the other
-    # way (the pre-activation within FP32 rounding of a BF16 tie) moves y by one BF16 step of
-    # that unit times its outgoing weights: rare, and bounded well below 1e-2.
-    assert np.quantile(err, 0.99) < 2e-5, np.quantile(err, 0.99)
-    assert err.max() < 1e-2, err.max()
+    bound = _inference_bound(P, X.astype(np.float64))
+    ratio = err / bound
+    assert np.all(ratio <= 1.0), (ratio.max(), err.max())
+    assert np.median(ratio) < 0.25, np.median(ratio)
+    # a wrong layer, bias or fragment mapping would be off by O(1)
+    assert np.abs(want).mean() > 20 * err.mean()
 
 
 def test_network_inference_zero_and_one_sample(torch):
@@ -76,7 +101,8 @@ def test_network_inference_zero_and_one_sample(torch):
         lbm.lbm_mlp_infer(m, Xd.data_ptr(), 0, yd.data_ptr())  # n = 0: nothing launched
         lbm.lbm_mlp_infer(m, Xd.data_ptr(), 1, yd.data_ptr())
         torch.cuda.synchronize()
-        assert abs(float(yd[0]) - mlp.forward_bf16(P, X.astype(np.float64))[0]) < 1e-3
+        err = abs(float(yd[0]) - mlp.forward_bf16(P, X.astype(np.float64))[0])
+        assert err <= _inference_bound(P, X.astype(np.float64))[0]
     finally:
         lbm.lbm_mlp_destroy(m)
 
