@@ -215,7 +215,6 @@ lbm_status ensure_arena(lbm_ctx *c)
     c->arr[1] = narr == 2 ? (void *)((b + bytes1 + 255) & ~(uintptr_t)255) : nullptr;
     CK(cudaMemsetAsync(c->arr[0], 0, bytes1, c->stream), "clear PDF array");
     if (narr == 2) CK(cudaMemsetAsync(c->arr[1], 0, bytes1, c->stream), "clear PDF array");
-    CK(cudaMalloc((void **)&c->d_out, 8 * sizeof(double)), "cudaMalloc(reduction output)");
     c->dev_ready = true;
     return LBM_OK;
 }
@@ -298,8 +297,12 @@ lbm_status ensure_lists(lbm_ctx *c)
     if (need > c->partials_cap) {
         dfree(c->d_partials);
         dfree(c->d_step_partials);
+        dfree(c->d_out);
         CK(cudaMalloc((void **)&c->d_partials, need * sizeof(double)), "cudaMalloc(reduction partials)");
         CK(cudaMalloc((void **)&c->d_step_partials, need * sizeof(double)), "cudaMalloc(step diagnostics)");
+        // the 8 results of the fixed-order sum plus its first-level records
+        CK(cudaMalloc((void **)&c->d_out, reduce_final_scratch(need / 8) * sizeof(double)),
+           "cudaMalloc(reduction output)");
         c->partials_cap = need;
     }
     c->step_diag_valid = false;

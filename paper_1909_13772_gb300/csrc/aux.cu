@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) k_coarse(const StoreT *__restrict__ A, co
 
 // ---------------------------------------------------------------------------------------
 // Deterministic FP64 reduction over all fluid cells: per tile (CTA) partial sums reduced by
-// warp shuffles, then one CTA sums the partials in a fixed order.
+// warp shuffles, then a fixed-order sum of the partials (diag.cu, launch_reduce_final).
 // Partial record: mass, j_x, j_y, j_z, kinetic energy, max |u|, non-finite cells, fluid cells.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v)
@@ -380,27 +380,6 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const StoreT *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(256) k_reduce_final(const double *__restrict__ partials, int64_t n,
-                                                      double *__restrict__ out)
-{
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    for (int64_t p = threadIdx.x; p < n; p += blockDim.x)
-        for (int c = 0; c < 8; ++c) acc[c] = c == 5 ? fmax(acc[c], partials[p * 8 + c]) : acc[c] + partials[p * 8 + c];
-    __shared__ double sh[8][8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const double v = c == 5 ? warp_max(acc[c]) : warp_sum(acc[c]);
-        if (lane == 0) sh[warp][c] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 8) {
-        const int c = threadIdx.x;
-        double v = 0.0;
-        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) v = c == 5 ? fmax(v, sh[w2][c]) : v + sh[w2][c];
-        out[c] = v;
-    }
-}
 
 FillConst fill_const(const double F[3], const double base[27])
 {
@@ -484,8 +463,7 @@ cudaError_t LBM_CAT(launch_reduce_, LBM_Q, LBM_ST)(const ReduceArgs &s)
                                                                     s.layout, fk, s.F[0], s.F[1], s.F[2], s.partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_reduce_final<<<1, 256, 0, s.stream>>>(s.partials, s.ntiles, s.out);
-    return cudaGetLastError();
+    return launch_reduce_final(s.partials, s.ntiles, s.out, s.stream);
 }
 
 }  // namespace lbm

@@ -56,11 +56,35 @@ __global__ void __launch_bounds__(256) k_block_final(const double *__restrict__ 
 
 }  // namespace
 
+// Records per CTA of the first level of the two-level sum (a fixed partition of the records).
+constexpr int64_t kChunk = 256;
+
+__global__ void __launch_bounds__(256) k_diag_chunks(const double *__restrict__ partials, int64_t n,
+                                                     double *__restrict__ out)
+{
+    const int64_t c0 = (int64_t)blockIdx.x * kChunk;
+    final_sum(partials + c0 * 8, min(kChunk, n - c0), out + (int64_t)blockIdx.x * 8);
+}
+
 cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, cudaStream_t s)
 {
-    k_diag_final<<<1, 256, 0, s>>>(partials, n, out);
+    // up to kChunk records: one CTA; more: one CTA per chunk of kChunk records into a scratch
+    // area after the output (out[8 ..]), then one CTA over the chunk records.  The partition
+    // depends on n only, so the result is the same from run to run.
+    if (n <= kChunk) {
+        k_diag_final<<<1, 256, 0, s>>>(partials, n, out);
+        return cudaGetLastError();
+    }
+    const int64_t chunks = (n + kChunk - 1) / kChunk;
+    if (chunks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_diag_chunks<<<(unsigned)chunks, 256, 0, s>>>(partials, n, out + 8);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_diag_final<<<1, 256, 0, s>>>(out + 8, chunks, out);
     return cudaGetLastError();
 }
+
+int64_t reduce_final_scratch(int64_t n) { return n <= kChunk ? 8 : 8 + 8 * ((n + kChunk - 1) / kChunk); }
 
 cudaError_t launch_block_final(const double *partials, const int64_t *start, int64_t nblocks, double *out,
                                cudaStream_t s)

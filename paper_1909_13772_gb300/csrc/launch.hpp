@@ -71,7 +71,7 @@ struct ReduceArgs {
     double F[3];
     double base[27];
     double *partials;  // ntiles * 8 doubles
-    double *out;       // 8 doubles (device)
+    double *out;       // reduce_final_scratch(ntiles) doubles (device); results in out[0..7]
     cudaStream_t stream;
 };
 
@@ -84,7 +84,9 @@ enum CellOp { CELL_INIT = 0, CELL_GET = 1, CELL_SET = 2, CELL_MACRO = 3, CELL_CO
 // Entry points of the per-(stencil, storage) objects; storage 0 fp64, 1 fp32, 2 bf16-dev,
 // 3 fp16-dev.  sweep.cu defines launch_sweep_<Q>_<ST>; aux.cu the other three.
 // Second pass of the diagnostics: fixed-order sum of n per-CTA records into out[8].
+// out must hold reduce_final_scratch(n) doubles: the 8 results, then the first-level records.
 cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, cudaStream_t s);
+int64_t reduce_final_scratch(int64_t n);
 // Per-block second pass: block b sums the records of tiles start[b] .. start[b+1] - 1 (tiles
 // are stored block by block) into out[8 b .. 8 b + 7].
 cudaError_t launch_block_final(const double *partials, const int64_t *start, int64_t nblocks, double *out,

@@ -40,7 +40,11 @@ namespace {
 // The diagnostics variant (DIAG) keeps eight running sums in registers; one CTA fewer per
 // SM leaves it room for them without spilling.
 constexpr int kMinB = LBM_SWEEP_MINB;
+#ifdef LBM_SWEEP_MINB_DIAG
+constexpr int kMinBDiag = LBM_SWEEP_MINB_DIAG;
+#else
 constexpr int kMinBDiag = LBM_SWEEP_MINB > 3 ? 3 : (LBM_SWEEP_MINB > 1 ? 1 : LBM_SWEEP_MINB);
+#endif
 
 // The cells of one tile.  A thread owns one (x, y) column and walks the tile's z range.  A
 // warp with a cell on a face of a block that reads its neighbours in place takes the
