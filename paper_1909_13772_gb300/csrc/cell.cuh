@@ -16,23 +16,36 @@ using R = typename S::R;
 // Per-CTA diagnostics record of the cells this CTA updated (DIAG): sums accumulated per
 // thread and per warp in the sweep's arithmetic type, across warps in FP64:
 // mass, momentum (rho u, half-force corrected), kinetic energy, max |u|, non-finite
-// cells, fluid cells.
+// cells, fluid cells.  Per cell the thread keeps sum rho |u|^2 and max |u|^2; the halving and
+// the square root are taken once per thread (record()).  A cell counts as non-finite when
+// rho + |u|^2 is (an infinity or NaN in either propagates to the sum).
 template <bool DIAG>
 struct Diag {
-    R m = R(0), jx = R(0), jy = R(0), jz = R(0), e = R(0), umax = R(0), bad = R(0), n = R(0);
+    R m = R(0), jx = R(0), jy = R(0), jz = R(0), e2 = R(0), u2max = R(0), bad = R(0), n = R(0);
     __device__ __forceinline__ void add(R rho, R ux, R uy, R uz)
     {
         if (!DIAG) return;
         const R u2 = ux * ux + uy * uy + uz * uz;
-        const bool ok = isfinite(rho) && isfinite(u2);
         m += rho;
-        jx += rho * ux;
-        jy += rho * uy;
-        jz += rho * uz;
-        e += R(0.5) * rho * u2;
-        umax = fmax(umax, sqrt(u2));
-        bad += ok ? R(0) : R(1);
+        jx = fma(rho, ux, jx);
+        jy = fma(rho, uy, jy);
+        jz = fma(rho, uz, jz);
+        e2 = fma(rho, u2, e2);
+        u2max = fmax(u2max, u2);
+        bad += isfinite(rho + u2) ? R(0) : R(1);
         n += R(1);
+    }
+    // the thread's record: mass, momentum x/y/z, kinetic energy, max |u|, non-finite, cells
+    __device__ __forceinline__ void record(R (&v)[8]) const
+    {
+        v[0] = m;
+        v[1] = jx;
+        v[2] = jy;
+        v[3] = jz;
+        v[4] = R(0.5) * e2;
+        v[5] = sqrt(u2max);
+        v[6] = bad;
+        v[7] = n;
     }
 };
 

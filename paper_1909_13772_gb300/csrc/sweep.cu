@@ -122,8 +122,10 @@ __global__ void __launch_bounds__(256, DIAG ? kMinBDiag : kMinB)
     if (DIAG) {
         __shared__ double sh[8][8];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        const R v[8] = {wsum(dg.m), wsum(dg.jx), wsum(dg.jy), wsum(dg.jz),
-                        wsum(dg.e), wmax(dg.umax), wsum(dg.bad), wsum(dg.n)};
+        R v[8];
+        dg.record(v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = c == 5 ? wmax(v[c]) : wsum(v[c]);
         if (lane == 0)
             for (int c = 0; c < 8; ++c) sh[warp][c] = (double)v[c];
         __syncthreads();
