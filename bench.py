@@ -168,6 +168,28 @@ def sweep_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def closure_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1909_13772_gb300", "csrc")
+    for name in ("closure.cu", "closure.hpp", "cell.cuh", "kernels.cuh", "lattice.cuh", "select.cuh"):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_instructions(kernel: str):
+    """Thread-instructions per cell of a kernel from a committed ncu summary, if it was taken on
+    the current closure source (a line 'INSTR kernel=<k> per_cell=<n> source=<hash>')."""
+    cur = closure_source_hash()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        with open(path) as fh:
+            for line in fh:
+                m = re.search(r"INSTR kernel=(\S+) per_cell=([0-9.eE+]+) source=([0-9a-f]+)", line)
+                if m and m.group(1) == kernel and m.group(3) == cur:
+                    return float(m.group(2))
+    return None
+
+
 def recorded_traffic(variant: str):
     """DRAM bytes per sweep launch from a committed ncu summary, if it was taken on the
     current sweep source (a line 'TRAFFIC variant=<v> bytes_per_launch=<n> source=<hash>')."""
@@ -536,8 +558,9 @@ def run_closure(args):
     FP32 storage, AA pattern, periodic N^3 box of decaying turbulence (random-phase k^(-5/3)
     start, default_rng(9), shells 1..N/4, max|u| = 0.1).  Each step once with the constant
     rate, once with Smagorinsky (C_s = 0.17) and once with the tensor-core network fused into
-    the collision.  Value: MLUPS of the network step at 128^3; roofline of the network sweep at
-    the largest size (its cost is the SiLU evaluations on the special-function unit)."""
+    the collision.  Value: MLUPS of the network step at 128^3; roofline of the network sweep
+    there against instruction issue, its bound (instructions per cell from the committed ncu
+    summary of the same source)."""
     import torch
     rank, world, local = dist_setup()
     from paper_1909_13772_gb300 import closure_study, inputs, lbm
@@ -546,7 +569,6 @@ def run_closure(args):
     net = closure_study.init_params(0, 100.0, 300.0, 1e-3)
     sizes = [128, 256]
     res = {}
-    kt_net = None
     for n in sizes:
         rho, u = inputs.turbulence(n, seed=9, kmax=n // 4, umax=0.1)
         for name in ("trt", "smagorinsky", "mlp"):
@@ -582,18 +604,17 @@ def run_closure(args):
             res["%s-%d" % (name, n)] = {"mlups": round(ups / 1e6, 1), "ms_per_step": round(tmax * 1e3 / args.steps, 4),
                                         "sweep_ms": round(sweep_ms, 4), "finite": d["nonfinite"] == 0,
                                         "clocks": clocks}
-            if name == "mlp" and n == sizes[-1]:
-                kt_net = (sweep_ms, clocks)
         del rho, u
-    n = sizes[-1]
-    sweep_ms, clocks = kt_net
+    n = sizes[0]
     peak_hbm, peak_kind = measured_peaks()
-    # special-function-unit work per cell: 64 hidden units x (exp2 + reciprocal) in the SiLU,
-    # softplus (exp2 + log2), 3 reciprocals (1/rho, 1/tau, omega-): 133 operations
-    sfu_per_cell = 133
+    sweep_ms = res["mlp-%d" % n]["sweep_ms"]
+    clocks = res["mlp-%d" % n]["clocks"]
     sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
-    sfu_peak = 16 * 152 * sm_clock * 1e6 / 1e12  # T operations/s: 16 per clock per SM
-    sfu_ach = sfu_per_cell * n ** 3 / (sweep_ms / 1e3) / 1e12
+    # the network sweep is bound by instruction issue: four schedulers per SM, one warp
+    # instruction (32 thread-instructions) each per clock
+    issue_peak = 4 * 32 * 152 * sm_clock * 1e6 / 1e12  # T thread-instructions/s
+    per_cell = recorded_instructions("closure-mlp-aa-%d" % n)
+    issue_ach = per_cell * n ** 3 / (sweep_ms / 1e3) / 1e12 if per_cell else None
     alg_bytes = 2 * 19 * 4 * n ** 3
     mma_flops = 2 * (16 * 32 + 32 * 32 + 32 * 8) * n ** 3  # padded MMA shapes per cell
     out = {"metric": "MLUPS of the learned-closure step (tensor-core network fused into the collision)",
@@ -604,10 +625,12 @@ def run_closure(args):
            "config": {"workload": "learned closure, D3Q19 TRT tau0=0.502 periodic 128^3 decaying turbulence, "
                                   "FP32 AA, 7-32-32-1 SiLU network", "sizes": sizes,
                       "l2": "no flush: 128^3 FP32 state 318 MB > 129 MB L2"},
-           "roofline": {"bound": "alu", "achieved": round(sfu_ach, 3), "peak": round(sfu_peak, 3),
-                        "unit": "Tops/s (special-function unit)", "frac": round(sfu_ach / sfu_peak, 4),
-                        "traffic": None, "kernel": "k_closure_sweep<network> at %d^3" % n,
-                        "peak_source": "16 SFU operations per clock per SM x 152 SMs x max SM clock",
+           "roofline": {"bound": "alu", "achieved": round(issue_ach, 3) if issue_ach else None,
+                        "peak": round(issue_peak, 3), "unit": "T thread-instructions/s (issue)",
+                        "frac": round(issue_ach / issue_peak, 4) if issue_ach else None,
+                        "traffic": None, "kernel": "k_closure_sweep<network>, AA pair at %d^3" % n,
+                        "peak_source": "4 schedulers x 32 lanes per clock per SM x 152 SMs x max SM clock",
+                        "instructions_per_cell": per_cell,
                         "sweep_ms": round(sweep_ms, 4),
                         "hbm_gbs": round(alg_bytes / (sweep_ms / 1e3) / 1e9, 1),
                         "hbm_frac": round(alg_bytes / (sweep_ms / 1e3) / 1e9 / peak_hbm, 4),
