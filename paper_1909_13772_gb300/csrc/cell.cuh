@@ -75,6 +75,33 @@ struct Face {
     int lo, hi;
 };
 
+// Index shifts that bring a neighbour across a wrapped face back into the block, per axis and
+// side (lo: the cell is on the low face, the neighbour is at -1, shift +n stride; hi: -n
+// stride), zero where the cell is not on that face.  Taken once per cell from its face flags.
+struct WrapD {
+    int32_t xl, xh, yl, yh;
+    int64_t zl, zh;
+};
+
+__device__ __forceinline__ WrapD wrap_deltas(const DevBlock &B, Face f)
+{
+    WrapD w;
+    w.xl = (f.lo & 1) ? B.nx : 0;
+    w.xh = (f.hi & 1) ? -B.nx : 0;
+    w.yl = (f.lo & 2) ? B.ny * B.pitch : 0;
+    w.yh = (f.hi & 2) ? -B.ny * B.pitch : 0;
+    w.zl = (f.lo & 4) ? (int64_t)B.nz * B.plane : 0;
+    w.zh = (f.hi & 4) ? -(int64_t)B.nz * B.plane : 0;
+    return w;
+}
+
+// Shift of the neighbour (x, y, z) + (DX, DY, DZ) (compile-time after unrolling).
+__device__ __forceinline__ int64_t wrap_of(const WrapD &w, int DX, int DY, int DZ)
+{
+    const int32_t s = (DX < 0 ? w.xl : (DX > 0 ? w.xh : 0)) + (DY < 0 ? w.yl : (DY > 0 ? w.yh : 0));
+    return (int64_t)s + (DZ < 0 ? w.zl : (DZ > 0 ? w.zh : 0));
+}
+
 // Arena offset of slot `q` of the neighbour (x, y, z) + (DX, DY, DZ) when it may lie in a
 // neighbour block (shared-memory table nb); otherwise (inside the block, or a boundary
 // region) `own` = the plain own-layout offset.
@@ -112,6 +139,7 @@ __device__ __forceinline__ void gather_cell(R (&f)[kQ], StoreT *__restrict__ A, 
 {
     using L = Lattice<kQ>;
     StoreT *a = A + B.offset;
+    const WrapD wd = FACE == 1 ? wrap_deltas(B, fc) : WrapD{};
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
@@ -123,7 +151,7 @@ __device__ __forceinline__ void gather_cell(R (&f)[kQ], StoreT *__restrict__ A, 
         const int sl = KIND == SWEEP_PULL ? i : L::opp(i);  // slot read from the source cell
         const int bs = KIND == SWEEP_PULL ? L::opp(i) : i;  // own slot read on bounce-back
         int64_t o = bounce ? (int64_t)bs * B.slab + cell : (int64_t)sl * B.slab + cell - off;
-        if (FACE == 1 && !bounce) o += wrap_shift(B, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i));
+        if (FACE == 1 && !bounce) o += wrap_of(wd, -L::cx(i), -L::cy(i), -L::cz(i));
         if (FACE == 2 && !bounce)
             o = nbr_addr(nb, fc, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i), sl, o + B.offset) - B.offset;
         f[i] = KIND == SWEEP_PULL ? S::raw(a + o) : S::raw_rw(a + o);
@@ -142,7 +170,9 @@ __device__ __forceinline__ void scatter_cell(const R (&f)[kQ], StoreT *__restric
     // hide the coordinates from the optimiser so it recomputes them here instead of keeping
     // 19 offsets live across the collision.
     int xs = x, ys = y, zs = z;
-    if (KIND == SWEEP_AA_NBR) asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs));
+    Face fs = fc;
+    if (KIND == SWEEP_AA_NBR) asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs), "+r"(fs.lo), "+r"(fs.hi));
+    const WrapD wd = (FACE == 1 && KIND == SWEEP_AA_NBR) ? wrap_deltas(B, fs) : WrapD{};
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
@@ -156,9 +186,9 @@ __device__ __forceinline__ void scatter_cell(const R (&f)[kQ], StoreT *__restric
             const bool bounce = MASK && i > 0 && ((m >> o) & 1u);
             const int64_t c2 = B.cell(xs, ys, zs);
             int64_t d = bounce ? (int64_t)o * B.slab + c2 : (int64_t)i * B.slab + c2 + off;
-            if (FACE == 1 && !bounce) d += wrap_shift(B, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i));
+            if (FACE == 1 && !bounce) d += wrap_of(wd, L::cx(i), L::cy(i), L::cz(i));
             if (FACE == 2 && !bounce)
-                d = nbr_addr(nb, fc, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i), i, d + B.offset) - B.offset;
+                d = nbr_addr(nb, fs, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i), i, d + B.offset) - B.offset;
             S::st_raw(a + d, f[i]);
         }
     }
