@@ -405,6 +405,8 @@ def run_porous(args):
     t_init = time.perf_counter() - t0
     if args.per_block:
         lbm.lbm_set_batching(sim.ctx, False)
+    if args.ghost:
+        lbm.lbm_set_in_place(sim.ctx, False)
     tuned = None
     if args.autotune:
         tuned = lbm.lbm_autotune(sim.ctx, 10)
@@ -455,7 +457,8 @@ def run_porous(args):
                         "fill_ms": round(fill_ms, 4)},
            "clocks": clocks, "finite": diag["nonfinite"] == 0, "max_speed": diag["max_speed"],
            "graph": bool(args.graph), "autotuned_tile": list(tuned[0]) if tuned else None,
-           "launch": "one sweep launch per block" if args.per_block else "one batched sweep launch"}
+           "launch": "one sweep launch per block" if args.per_block else "one batched sweep launch",
+           "neighbours": "ghost-layer copies" if args.ghost else "in place where faces match"}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -687,6 +690,7 @@ def main(argv=None):
     ap.add_argument("--graph", action="store_true", help="porous: replay step pairs as CUDA graphs")
     ap.add_argument("--autotune", action="store_true", help="porous: pick the sweep tile with lbm_autotune")
     ap.add_argument("--per-block", action="store_true", help="porous: one sweep launch per block (comparison)")
+    ap.add_argument("--ghost", action="store_true", help="porous: ghost-layer copies instead of in-place neighbours")
     ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure"], default="channel",
                     help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed; "
                          "turbulence: D3Q27 decaying turbulence, storage variants and their errors; "

@@ -330,6 +330,16 @@ lbm_status lbm_mlp_train(lbm_mlp *m, const float *X_dev, const float *T_dev, int
                          int64_t iters, float lr, double *loss_history);
 void lbm_mlp_destroy(lbm_mlp *m);
 
+/* Neighbour access across block faces (Sec. 3.3: blocks on one process exchange ghost layers
+ * by direct copies): enable != 0 (default) lets a block whose every ghost-shell region is
+ * covered exactly by one block read and write those cells in place during the sweep (no
+ * ghost copy; a block spanning a periodic axis alone wraps onto itself); enable = 0 gives
+ * every block ghost layers filled by the copy runs of the fill kernel before each sweep.  The
+ * lists are rebuilt before the next step; the stored state is kept.  Results are identical.
+ * Errors: LBM_ERR_STATE when an AA context is after an odd number of steps (its two forms of
+ * the odd layout differ: switch after an even number). */
+lbm_status lbm_set_in_place(lbm_ctx *ctx, int32_t enable);
+
 /* Per-block diagnostics of the stored state (the per-block reductions of the paper's
  * per-block data layout, Sec. 4.1-4.2): out[8 b + k] for block b, k = mass, momentum x, y, z,
  * kinetic energy, max speed, non-finite cells, fluid cells (the lbm_diagnostics fields, as

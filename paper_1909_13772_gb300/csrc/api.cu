@@ -31,6 +31,7 @@ struct lbm_ctx {
     int face_kind[6];
     WallParam face_param[6];
     int tile[3] = {256, 1, 4};
+    int in_place = 1;  // read matching neighbour blocks in place (else ghost copies)
     int64_t arena_elems = 0;
     cudaStream_t stream = nullptr;
 
@@ -177,6 +178,7 @@ lbm_status build_lists(lbm_ctx *c)
         in.face_param[f] = c->face_param[f];
     }
     for (int a = 0; a < 3; ++a) in.tile[a] = c->tile[a];
+    in.in_place = c->in_place;
     in.blocks = &c->blocks;
     in.flags = &c->flags;
     in.block_param = &c->block_param;
@@ -771,6 +773,21 @@ lbm_status lbm_set_closure(lbm_ctx *c, int32_t kind, double cs, const float *mlp
     c->closure = kind;
     c->closure_cs = cs;
     drop_graphs(c);  // captured sweeps carry the old closure
+    return LBM_OK;
+}
+
+lbm_status lbm_set_in_place(lbm_ctx *c, int32_t enable)
+{
+    if (!c) return LBM_ERR_ARG;
+    if ((enable != 0) != (c->in_place != 0)) {
+        // an AA state after an odd number of steps may hold values in ghost slots (ghost mode)
+        // or in neighbour cells (in-place mode): the two forms only agree in the even layout
+        if (c->pattern == LBM_AA && c->aa_layout != LAYOUT_AA_E)
+            return fail(c, LBM_ERR_STATE, "switch the neighbour mode of an AA context after an even number of steps");
+        c->in_place = enable != 0;
+        c->plan_built = false;  // rebuilt (and re-uploaded) before the next step
+        drop_graphs(c);
+    }
     return LBM_OK;
 }
 

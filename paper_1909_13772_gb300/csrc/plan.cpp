@@ -213,6 +213,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
             if (touched && !exact) through[b] = 0;
         }
     }
+    if (!in.in_place) std::fill(through.begin(), through.end(), uint8_t(0));
 
     std::vector<BlockOut> bo(nb);
     std::string err;

@@ -81,6 +81,7 @@ struct PlanInput {
     int face_kind[6];
     WallParam face_param[6];
     int tile[3];
+    int in_place = 1;  // 1: blocks whose faces match their neighbours read them in place; 0: ghost copies only
     std::vector<BlockLayout> const *blocks;
     std::vector<std::vector<uint8_t>> const *flags;  // per block, interior, may be empty (all fluid)
     std::vector<WallParam> const *block_param;       // per block

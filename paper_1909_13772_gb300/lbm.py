@@ -72,6 +72,7 @@ _SIGS = {
     "lbm_kernel_launches": ([_vp], ctypes.c_int64),
     "lbm_set_graph": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_set_batching": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "lbm_set_in_place": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_autotune": ([_vp, ctypes.c_int32, _i32p, _dp], ctypes.c_int),
     "lbm_enable_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_read_timing": ([_vp, _dp, _i64p, ctypes.c_int32], ctypes.c_int),
@@ -233,6 +234,11 @@ def lbm_set_tile(ctx, tx, ty, tz):
 
 def lbm_set_batching(ctx, batched=True):
     _check(ctx, load_library().lbm_set_batching(ctx, 1 if batched else 0))
+
+
+def lbm_set_in_place(ctx, enable=True):
+    """Read matching neighbour blocks in place (True, default) or fill ghost layers by copies."""
+    _check(ctx, load_library().lbm_set_in_place(ctx, 1 if enable else 0))
 
 
 def lbm_set_graph(ctx, enable=True):

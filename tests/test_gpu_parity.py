@@ -241,6 +241,35 @@ def test_per_block_reduction_matches_oracle(pattern):
     assert per[:, 7].sum() == tot["fluid_cells"]
 
 
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+def test_ghost_copies_equal_in_place_neighbours(pattern):
+    """lbm_set_in_place(0) (ghost layers filled by copy runs) gives the same state bit for bit
+    as in-place neighbour access, including a switch between the two after an even number of
+    steps; an AA switch after an odd number is refused."""
+    case = _porous_case(lbm.FP32, pattern)
+    rho, u = inputs.random_state(case.shape, seed=21, rho_amp=0.02, u_amp=0.02)
+    out = []
+    for mode in ("in_place", "ghost", "switch"):
+        s = case.make_sim()
+        if mode == "ghost":
+            lbm.lbm_set_in_place(s.ctx, False)
+        init_sim(s, rho, u)
+        s.step(4)
+        if mode == "switch":
+            lbm.lbm_set_in_place(s.ctx, False)
+        s.step(5)
+        if mode == "switch" and pattern == lbm.AA:
+            with pytest.raises(lbm.LbmError):
+                lbm.lbm_set_in_place(s.ctx, True)
+        s.step(1)
+        out.append(gather_pdfs(s, case))
+        if mode == "ghost":
+            info = s.info()
+            assert info["ghost_runs"] > 0
+        s.close()
+    assert np.array_equal(out[0], out[1]) and np.array_equal(out[0], out[2])
+
+
 def test_divergence_is_reported():
     case = Case(shape=(40, 9, 6), storage=lbm.FP32)
     p = lbm.make_params(stencil=19, storage=lbm.FP32, omega=1.2, diag_interval=2)
