@@ -457,8 +457,10 @@ def run_porous(args):
                         "fill_ms": round(fill_ms, 4)},
            "clocks": clocks, "finite": diag["nonfinite"] == 0, "max_speed": diag["max_speed"],
            "graph": bool(args.graph), "autotuned_tile": list(tuned[0]) if tuned else None,
+           "autotuned_in_place": tuned[2] if tuned else None,
            "launch": "one sweep launch per block" if args.per_block else "one batched sweep launch",
-           "neighbours": "ghost-layer copies" if args.ghost else "in place where faces match"}
+           "neighbours": ("in place where faces match" if (tuned[2] if tuned else not args.ghost)
+                          else "ghost-layer copies")}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -688,7 +690,8 @@ def main(argv=None):
     ap.add_argument("--headline-only", action="store_true", help="skip the other variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--graph", action="store_true", help="porous: replay step pairs as CUDA graphs")
-    ap.add_argument("--autotune", action="store_true", help="porous: pick the sweep tile with lbm_autotune")
+    ap.add_argument("--autotune", action="store_true",
+                    help="porous: pick the sweep tile and the neighbour mode with lbm_autotune")
     ap.add_argument("--per-block", action="store_true", help="porous: one sweep launch per block (comparison)")
     ap.add_argument("--ghost", action="store_true", help="porous: ghost-layer copies instead of in-place neighbours")
     ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure"], default="channel",

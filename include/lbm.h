@@ -216,10 +216,14 @@ lbm_status lbm_set_batching(lbm_ctx *ctx, int32_t batched);
 lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t enable);
 
 /* Autotuner: times trial_steps steps for each candidate sweep tile shape (a fixed list from
- * 256x1x2 to 32x8x4), keeps the fastest (best[3], and its time per step in *best_ms if
- * non-NULL) and restores the simulation state exactly (the PDF arrays are snapshot to a
- * temporary device buffer, which is cudaMalloc'd).  The step count and parity are unchanged. */
-lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trial_steps, int32_t best[3], double *best_ms);
+ * 256x1x2 to 32x8x4) and each neighbour mode (lbm_set_in_place; the other mode is tried only
+ * where it may be switched: two-grid, or AA after an even number of steps), every trial from
+ * the same state; keeps the fastest (best[3], *best_in_place and the time per step in
+ * *best_ms, each pointer may be NULL but best) and restores the simulation state exactly (the
+ * PDF arrays are snapshot to a temporary device buffer, which is cudaMalloc'd).  The step
+ * count and parity are unchanged; diag_interval checks are off during the trials. */
+lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trial_steps, int32_t best[3], int32_t *best_in_place,
+                        double *best_ms);
 
 /* Number of kernels lbm_step launched since the context was created. */
 int64_t lbm_kernel_launches(const lbm_ctx *ctx);

@@ -809,13 +809,13 @@ lbm_status lbm_set_graph(lbm_ctx *c, int32_t enable)
     return LBM_OK;
 }
 
-lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], double *best_ms)
+lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], int32_t *best_in_place, double *best_ms)
 {
     if (!c || !best) return LBM_ERR_ARG;
     if (trial_steps < 1) return fail(c, LBM_ERR_ARG, "trial_steps must be >= 1");
     lbm_status s = prepare(c);
     if (s != LBM_OK) return s;
-    // keep the simulation state: snapshot the PDF arrays and restore them afterwards
+    // keep the simulation state: snapshot the PDF arrays, start every trial from it, restore
     const int narr = c->pattern == LBM_TWO_GRID ? 2 : 1;
     const size_t bytes1 = (size_t)c->arena_elems * c->bpp;
     void *snap = nullptr;
@@ -823,40 +823,56 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], double
     for (int k = 0; k < narr; ++k)
         CK(cudaMemcpyAsync((char *)snap + k * bytes1, c->arr[k], bytes1, cudaMemcpyDeviceToDevice, c->stream), "snapshot");
     const int cur = c->cur, lay = c->aa_layout;
-    const int64_t steps_done = c->steps_done, launches = c->launches;
+    const int64_t steps_done = c->steps_done, launches = c->launches, di = c->p.diag_interval;
     const bool diag_valid = c->step_diag_valid, timing = c->timing;
-    const int old[3] = {c->tile[0], c->tile[1], c->tile[2]};
+    const int old[3] = {c->tile[0], c->tile[1], c->tile[2]}, old_in_place = c->in_place;
+    // the neighbour mode may change only where both forms of the state agree (see lbm_set_in_place)
+    const bool try_modes = c->pattern == LBM_TWO_GRID || lay == LAYOUT_AA_E;
     static const int cand[][3] = {{256, 1, 4}, {256, 1, 2}, {256, 1, 8}, {256, 1, 16}, {128, 2, 4}, {128, 2, 8},
                                   {64, 4, 4},  {64, 4, 8},  {32, 8, 4},  {128, 1, 8},  {64, 2, 8}, {64, 1, 16}};
+    const int ncand = (int)(sizeof cand / sizeof cand[0]);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
     CK(cudaEventCreate(&e1), "event");
     float best_t = 1e30f;
-    int bi = -1;
+    int bi = -1, bmode = old_in_place;
     c->timing = false;
-    for (int k = 0; k < (int)(sizeof cand / sizeof cand[0]); ++k) {
-        c->tile[0] = cand[k][0];
-        c->tile[1] = cand[k][1];
-        c->tile[2] = cand[k][2];
-        c->plan_built = false;
-        if ((s = prepare(c)) != LBM_OK) break;
-        if ((s = lbm_step(c, 2)) != LBM_OK) break;
-        CK(cudaEventRecord(e0, c->stream), "event");
-        if ((s = lbm_step(c, trial_steps)) != LBM_OK) break;
-        CK(cudaEventRecord(e1, c->stream), "event");
-        CK(cudaEventSynchronize(e1), "event");
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1), "event");
-        if (ms < best_t) {
-            best_t = ms;
-            bi = k;
+    c->p.diag_interval = 0;  // trial steps are timed only
+    for (int mode = 0; mode < 2 && s == LBM_OK; ++mode) {
+        const int in_place = mode == 0 ? old_in_place : !old_in_place;
+        if (mode == 1 && !try_modes) break;
+        for (int k = 0; k < ncand; ++k) {
+            for (int a = 0; a < 3; ++a) c->tile[a] = cand[k][a];
+            c->in_place = in_place;
+            c->plan_built = false;
+            if ((s = prepare(c)) != LBM_OK) break;
+            for (int j = 0; j < narr; ++j)
+                CK(cudaMemcpyAsync(c->arr[j], (char *)snap + j * bytes1, bytes1, cudaMemcpyDeviceToDevice, c->stream),
+                   "trial start");
+            c->cur = cur;
+            c->aa_layout = lay;
+            if ((s = lbm_step(c, 2)) != LBM_OK) break;
+            CK(cudaEventRecord(e0, c->stream), "event");
+            if ((s = lbm_step(c, trial_steps)) != LBM_OK) break;
+            CK(cudaEventRecord(e1, c->stream), "event");
+            CK(cudaEventSynchronize(e1), "event");
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1), "event");
+            if (ms < best_t) {
+                best_t = ms;
+                bi = k;
+                bmode = in_place;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const int *pick = bi >= 0 ? cand[bi] : old;
     for (int a = 0; a < 3; ++a) c->tile[a] = best[a] = pick[a];
+    c->in_place = bi >= 0 ? bmode : old_in_place;
+    if (best_in_place) *best_in_place = c->in_place;
     c->plan_built = false;
+    drop_graphs(c);
     lbm_status s2 = prepare(c);
     for (int k = 0; k < narr; ++k)
         CK(cudaMemcpyAsync(c->arr[k], (char *)snap + k * bytes1, bytes1, cudaMemcpyDeviceToDevice, c->stream), "restore");
@@ -868,6 +884,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], double
     c->launches = launches;
     c->step_diag_valid = diag_valid;
     c->timing = timing;
+    c->p.diag_interval = di;
     if (best_ms) *best_ms = bi >= 0 ? best_t / trial_steps : 0.0;
     return s != LBM_OK ? s : s2;
 }

@@ -73,7 +73,7 @@ _SIGS = {
     "lbm_set_graph": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_set_batching": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_set_in_place": ([_vp, ctypes.c_int32], ctypes.c_int),
-    "lbm_autotune": ([_vp, ctypes.c_int32, _i32p, _dp], ctypes.c_int),
+    "lbm_autotune": ([_vp, ctypes.c_int32, _i32p, _i32p, _dp], ctypes.c_int),
     "lbm_enable_timing": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_read_timing": ([_vp, _dp, _i64p, ctypes.c_int32], ctypes.c_int),
     "lbm_stencil_table": ([ctypes.c_int32, _i32p, _dp, _i32p], ctypes.c_int),
@@ -246,11 +246,14 @@ def lbm_set_graph(ctx, enable=True):
 
 
 def lbm_autotune(ctx, trial_steps=20):
-    """(best tile (tx, ty, tz), ms per step of the best candidate); the state is unchanged."""
+    """(best tile (tx, ty, tz), ms per step of the best candidate, in-place neighbour mode of
+    it); the state is unchanged."""
     best = np.zeros(3, dtype=np.int32)
+    mode = ctypes.c_int32()
     ms = ctypes.c_double()
-    _check(ctx, load_library().lbm_autotune(ctx, int(trial_steps), _ptr(best, ctypes.c_int32), ctypes.byref(ms)))
-    return tuple(int(v) for v in best), ms.value
+    _check(ctx, load_library().lbm_autotune(ctx, int(trial_steps), _ptr(best, ctypes.c_int32), ctypes.byref(mode),
+                                            ctypes.byref(ms)))
+    return tuple(int(v) for v in best), ms.value, bool(mode.value)
 
 
 def lbm_kernel_launches(ctx) -> int:

@@ -388,17 +388,20 @@ def test_graph_mode_needs_a_stream():
     s.close()
 
 
-def test_autotune_keeps_state_and_results():
-    case = _porous_case(lbm.FP32, lbm.AA)
+@pytest.mark.parametrize("pattern,at", [(lbm.AA, 3), (lbm.AA, 4), (lbm.TWO_GRID, 3)])
+def test_autotune_keeps_state_and_results(pattern, at):
+    """The autotuner (tile shapes and, where allowed, the neighbour mode) leaves the state, step
+    count and parity as they were, and later steps equal those of an untuned run bit for bit."""
+    case = _porous_case(lbm.FP32, pattern)
     rho, u = inputs.random_state(case.shape, seed=19, rho_amp=0.01, u_amp=0.02)
     a = case.make_sim()
     init_sim(a, rho, u)
-    a.step(3)
+    a.step(at)
     before = gather_pdfs(a, case)
-    best, ms = lbm.lbm_autotune(a.ctx, 4)
+    best, ms, in_place = lbm.lbm_autotune(a.ctx, 4)
     assert ms > 0 and best[0] * best[1] <= 256
     np.testing.assert_array_equal(gather_pdfs(a, case), before)
-    a.step(5)
+    a.step(8 - at)
     tuned = gather_pdfs(a, case)
     a.close()
     b = case.make_sim()
