@@ -382,7 +382,8 @@ def run_porous(args):
     from paper_1909_13772_gb300 import inputs, lbm
     lbm.load_library()
     t0 = time.perf_counter()
-    blocks, shape, _ = inputs.rectilinear_blocks(nb=(16, 16, 16), lo=16, hi=64, seed=4096)
+    nbk = args.porous_blocks
+    blocks, shape, _ = inputs.rectilinear_blocks(nb=(nbk, nbk, nbk), lo=16, hi=64, seed=4096)
     flags = inputs.sphere_packing(shape, radius=8.0, porosity=0.40, seed=7)
     t_geom = time.perf_counter() - t0
     storage, pattern = VARIANTS[args.variant]
@@ -444,8 +445,9 @@ def run_porous(args):
            "unit": "MFLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(tmax * 1e3 / args.steps, 4), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": args.variant, "data": "synthetic (seeded sphere packing)",
-           "config": {"workload": "porous bed, 4096 uneven blocks (16^3, edges log-uniform 16..64), spheres R=8, "
-                                  "porosity 0.40, velocity inlet 0.02 / pressure outlet, D3Q19 TRT tau=0.8",
+           "config": {"workload": "porous bed, %d uneven blocks (%d^3, edges log-uniform 16..64), spheres R=8, "
+                                  "porosity 0.40, velocity inlet 0.02 / pressure outlet, D3Q19 TRT tau=0.8"
+                                  % (nbk ** 3, nbk),
                       "domain": list(shape), "cells": info["cells"], "fluid_cells": fluid, "tiles": info["tiles"],
                       "links": list(info["links"]), "ghost_slots": info["ghost_slots"],
                       "ghost_runs": info["ghost_runs"], "setup_s": {"geometry": round(t_geom, 1),
@@ -572,11 +574,12 @@ def run_closure(args):
     lbm.load_library()
     stream = torch.cuda.Stream()
     net = closure_study.init_params(0, 100.0, 300.0, 1e-3)
-    sizes = [128, 256]
+    sizes = [int(v) for v in args.closure_sizes.split(",")]
+    kinds = [k for k in ("trt", "smagorinsky", "mlp") if k in args.closure_kinds.split(",")]
     res = {}
     for n in sizes:
         rho, u = inputs.turbulence(n, seed=9, kmax=n // 4, umax=0.1)
-        for name in ("trt", "smagorinsky", "mlp"):
+        for name in kinds:
             p = lbm.make_params(stencil=lbm.D3Q19, collision=lbm.TRT, storage=lbm.FP32, pattern=lbm.AA,
                                 omega=1 / 0.502, magic_lambda=LAMBDA, periodic=(1, 1, 1))
             sim = lbm.Simulation(p, [((0, 0, 0), (n, n, n))], stream=stream.cuda_stream)
@@ -612,6 +615,10 @@ def run_closure(args):
         del rho, u
     n = sizes[0]
     peak_hbm, peak_kind = measured_peaks()
+    if "mlp" not in kinds:
+        if rank == 0:
+            print(json.dumps({"metric": "closure step timings", "variants": res}), flush=True)
+        return
     sweep_ms = res["mlp-%d" % n]["sweep_ms"]
     clocks = res["mlp-%d" % n]["clocks"]
     sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
@@ -623,13 +630,13 @@ def run_closure(args):
     alg_bytes = 2 * 19 * 4 * n ** 3
     mma_flops = 2 * (16 * 32 + 32 * 32 + 32 * 8) * n ** 3  # padded MMA shapes per cell
     out = {"metric": "MLUPS of the learned-closure step (tensor-core network fused into the collision)",
-           "value": res["mlp-128"]["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": res["mlp-128"]["ms_per_step"], "higher_is_better": True,
+           "value": res["mlp-%d" % n]["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": res["mlp-%d" % n]["ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16 x bf16 -> f32)",
            "data": "synthetic (seeded random-phase turbulence)",
-           "config": {"workload": "learned closure, D3Q19 TRT tau0=0.502 periodic 128^3 decaying turbulence, "
-                                  "FP32 AA, 7-32-32-1 SiLU network", "sizes": sizes,
-                      "l2": "no flush: 128^3 FP32 state 318 MB > 129 MB L2"},
+           "config": {"workload": "learned closure, D3Q19 TRT tau0=0.502 periodic %d^3 decaying turbulence, "
+                                  "FP32 AA, 7-32-32-1 SiLU network" % n, "sizes": sizes,
+                      "l2": "no flush: %d^3 FP32 state %d MB vs 129 MB L2" % (n, 19 * 4 * n ** 3 // 10 ** 6)},
            "roofline": {"bound": "alu", "achieved": round(issue_ach, 3) if issue_ach else None,
                         "peak": round(issue_peak, 3), "unit": "T thread-instructions/s (issue)",
                         "frac": round(issue_ach / issue_peak, 4) if issue_ach else None,
@@ -641,8 +648,8 @@ def run_closure(args):
                         "hbm_frac": round(alg_bytes / (sweep_ms / 1e3) / 1e9 / peak_hbm, 4),
                         "tensor_tflops": round(mma_flops / (sweep_ms / 1e3) / 1e12, 2)},
            "cost_vs_constant_rate": {k: round(res["mlp-%d" % k]["ms_per_step"] / res["trt-%d" % k]["ms_per_step"], 3)
-                                     for k in sizes},
-           "variants": res, "clocks": res["mlp-128"]["clocks"]}
+                                     for k in sizes if "trt" in kinds},
+           "variants": res, "clocks": res["mlp-%d" % n]["clocks"]}
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -698,6 +705,9 @@ def main(argv=None):
                     help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed; "
                          "turbulence: D3Q27 decaying turbulence, storage variants and their errors; "
                          "closure: constant rate vs Smagorinsky vs the learned closure")
+    ap.add_argument("--porous-blocks", type=int, default=16, help="porous: blocks per axis (16: 4096 blocks)")
+    ap.add_argument("--closure-sizes", default="128,256", help="closure: box sizes; the first is the value's")
+    ap.add_argument("--closure-kinds", default="trt,smagorinsky,mlp", help="closure: which steps to time")
     ap.add_argument("--turb-size", type=int, default=512)
     ap.add_argument("--turb-err-size", type=int, default=256)
     ap.add_argument("--turb-fp64-perf", action="store_true")
