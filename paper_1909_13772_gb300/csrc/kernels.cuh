@@ -34,17 +34,6 @@ constexpr uint32_t kMaskSolid = 1u << 31;
 // first (+) or last (-) layer, along the other axes the same coordinate (faces of such
 // neighbours match exactly); a block spanning a periodic axis alone is its own neighbour,
 // which wraps the index.
-// Index shift that brings the neighbour (x, y, z) + (dx, dy, dz) back into a block that is
-// its own neighbour across the crossed faces (wrap bits): -n or +n times the axis stride.
-__device__ __forceinline__ int64_t wrap_shift(const DevBlock &B, int x, int y, int z, int dx, int dy, int dz)
-{
-    int sx = 0, sy = 0, sz = 0;
-    if (dx != 0 && (B.wrap & 1)) sx = (x + dx < 0) ? 1 : (x + dx >= B.nx ? -1 : 0);
-    if (dy != 0 && (B.wrap & 2)) sy = (y + dy < 0) ? 1 : (y + dy >= B.ny ? -1 : 0);
-    if (dz != 0 && (B.wrap & 4)) sz = (z + dz < 0) ? 1 : (z + dz >= B.nz ? -1 : 0);
-    return (int64_t)(sx * B.nx + sy * B.ny * B.pitch) + (int64_t)sz * B.nz * B.plane;
-}
-
 __device__ __forceinline__ int64_t resolve(const DevBlock *__restrict__ blocks, const DevBlock *Bp, int x, int y,
                                            int z, int dx, int dy, int dz, int q)
 {
