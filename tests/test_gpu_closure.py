@@ -267,3 +267,25 @@ def test_clearing_the_closure_restores_the_plain_sweep(torch):
         finally:
             sim.close()
     assert np.array_equal(out[0], out[1])
+
+
+def test_mlp_sweep_at_the_coarse_study_size(torch):
+    """The learned-closure coarse configuration itself: 128^3 periodic box, D3Q19 TRT
+    tau0 = 0.502, FP32 AA, random-phase start with max|u| = 0.1, a trained-like network; three
+    steps (neighbour, local, neighbour sweep) against the oracle."""
+    n = 128
+    rho, u = inputs.turbulence(n, seed=9, kmax=n // 4, umax=0.1)
+    net = _net(61, s_rho=100.0, s_pi=300.0, s_tau=1e-3)
+    case = Case(shape=(n, n, n), storage=lbm.FP32, pattern=lbm.AA, omega=1 / 0.502)
+    cl = dict(kind=oracle.MLP, mlp=net)
+    sim = case.make_sim()
+    try:
+        sim.set_closure(lbm.CLOSURE_MLP, mlp_params=net)
+        init_sim(sim, rho, u)
+        sim.step(3)
+        got = gather_pdfs(sim, case)
+    finally:
+        sim.close()
+    p = case.oracle_params()
+    want = oracle.run(p, oracle.init(p, rho, u), 3, closure=cl)
+    assert normwise(got, want) < TOL[lbm.FP32]
