@@ -461,6 +461,8 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
     f.omega_m = (float)d.omega_m;
     f.a_p = (float)d.a_p;
     f.a_m = (float)d.a_m;
+    f.r.wp = (float)d.r.wp;
+    f.r.wm = (float)d.r.wm;
     f.r.rest = (float)d.r.rest;
     f.r.alpha = (float)d.r.alpha;
     f.r.beta = (float)d.r.beta;

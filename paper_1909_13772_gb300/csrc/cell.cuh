@@ -12,6 +12,9 @@ namespace {
 constexpr int kQ = LBM_Q;
 using S = Storage<StoreT>;
 using R = typename S::R;
+// the collision relaxes the non-equilibrium parts first for full populations in FP32 (see
+// collide in kernels.cuh); FP64 and the deviation storages take the pair form
+constexpr bool kAccurate = LBM_ST == 1;
 
 // Per-CTA diagnostics record of the cells this CTA updated (DIAG): sums accumulated per
 // thread and per warp in the sweep's arithmetic type, across warps in FP64:
@@ -212,7 +215,7 @@ __device__ __forceinline__ void update_cell(StoreT *__restrict__ A, StoreT *__re
     R f[kQ];
     gather_cell<KIND, FACE, MASK>(f, A, B, nb, fc, x, y, z, cell, m, k.base);
     R rho, ux, uy, uz;
-    collide<kQ, FORCE, R>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+    collide<kQ, FORCE, R, kAccurate>(f, k, k.r, k.rho0, rho, ux, uy, uz);
     scatter_cell<KIND, FACE, MASK>(f, A, Bout, B, nb, fc, x, y, z, cell, m, k.base);
     dg.add(rho, ux, uy, uz);
 }

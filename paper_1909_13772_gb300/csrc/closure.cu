@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
             constexpr float wc[4] = {1.f / 3.f, 1.f / 18.f, 1.f / 36.f, 0.f};  // D3Q19 weight classes
             const Rates<float> rt = rates_of<float>(wp, wm, wc);
             float r2, ux, uy, uz;
-            collide<kQ, false, float>(f, k, rt, 0.f, r2, ux, uy, uz);
+            collide<kQ, false, float, true>(f, k, rt, 0.f, r2, ux, uy, uz);
             if (kThr && any_face) {
                 if (masked)
                     scatter_cell<KIND, kFace, true>(f, A, Bout, B, nb, f2, x, y, z, cell, m, k.base);

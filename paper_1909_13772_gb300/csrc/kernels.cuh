@@ -67,6 +67,7 @@ struct DevRun {
 // class c = |c_i|^2 (0 rest, 1 axis, 2 face diagonal, 3 corner).
 template <class R>
 struct Rates {
+    R wp, wm;        // omega+, omega-
     R rest;          // 1 - omega+
     R alpha, beta;   // 1 - (omega+ + omega-)/2, (omega- - omega+)/2
     R pw[4], mw[4];  // omega+ w_c, 3 omega- w_c
@@ -90,6 +91,8 @@ template <class R>
 __host__ __device__ __forceinline__ Rates<R> rates_of(R wp, R wm, const R (&wc)[4])
 {
     Rates<R> r;
+    r.wp = wp;
+    r.wm = wm;
     r.rest = R(1) - wp;
     r.alpha = R(1) - R(0.5) * (wp + wm);
     r.beta = R(0.5) * (wm - wp);
@@ -193,7 +196,12 @@ struct Storage<__half> {
 // (sum w = 1, sum w c = 0).  P, M use per-class constants w+ w, 3 w- w (Rates) and the
 // per-direction Guo constants of Coll.
 // ---------------------------------------------------------------------------------------
-template <int Q, bool FORCE, class R>
+// ACCURATE: relax the non-equilibrium parts s/2 - feq+ and d/2 - feq- first (the form of the
+// equations above), for full populations stored in FP32: the pair form below adds terms of
+// about 2 f that cancel, which near omega+ = 2 (tau -> 1/2) gives 2-3 times the rounding error
+// of this form; the pair form takes about 3 fewer instructions per pair and is used where the
+// arithmetic is FP64 (rounding far below any tolerance) or the stored values are deviations.
+template <int Q, bool FORCE, class R, bool ACCURATE = false>
 __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates<R> &rt, R rho0, R &rho_out,
                                         R &ux_out, R &uy_out, R &uz_out)
 {
@@ -235,8 +243,15 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
     R buF[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) buF[c] = FORCE ? k.bw[c] * uF : R(0);
+    const R wp = rt.wp, wm = rt.wm;
     {
-        R f0 = rt.rest * f[0] + rt.pw[0] * rb;
+        R f0;
+        if (ACCURATE) {
+            const R w0 = R(L::w(0));
+            f0 = fma(-wp, fma(-w0, rb, f[0]), f[0]);  // f0 - w+ (f0 - feq0)
+        } else {
+            f0 = rt.rest * f[0] + rt.pw[0] * rb;
+        }
         if (FORCE) f0 -= buF[0];
         f[0] = f0;
     }
@@ -253,15 +268,30 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
         if (L::cz(i) > 0) cu += uz;
         if (L::cz(i) < 0) cu -= uz;
         const R rcu = rho * cu;
-        R P = rt.pw[c] * fma(R(4.5) * cu, rcu, rb);
-        R M = rt.mw[c] * rcu;
-        if (FORCE) {
-            P = fma(k.fa[i], cu, P) - buF[c];
-            M += k.fc[i];
-        }
         const R fi = f[i], fo = f[o];
-        f[i] = fma(rt.alpha, fi, fma(rt.beta, fo, P + M));
-        f[o] = fma(rt.alpha, fo, fma(rt.beta, fi, P - M));
+        if (ACCURATE) {
+            const R w = R(L::w(i));
+            const R ep = fma(R(0.5), fi + fo, -w * fma(R(4.5) * cu, rcu, rb));  // s/2 - feq+
+            const R em = fma(R(0.5), fi - fo, -R(3) * w * rcu);                 // d/2 - feq-
+            R gi = fma(-wp, ep, fma(-wm, em, fi));
+            R go = fma(-wp, ep, fma(wm, em, fo));
+            if (FORCE) {
+                const R sp = fma(k.fa[i], cu, -buF[c]);  // a+ S+
+                gi += sp + k.fc[i];
+                go += sp - k.fc[i];
+            }
+            f[i] = gi;
+            f[o] = go;
+        } else {
+            R P = rt.pw[c] * fma(R(4.5) * cu, rcu, rb);
+            R M = rt.mw[c] * rcu;
+            if (FORCE) {
+                P = fma(k.fa[i], cu, P) - buF[c];
+                M += k.fc[i];
+            }
+            f[i] = fma(rt.alpha, fi, fma(rt.beta, fo, P + M));
+            f[o] = fma(rt.alpha, fo, fma(rt.beta, fi, P - M));
+        }
     }
 }
 

@@ -23,11 +23,15 @@
 
 // Occupancy: minimum resident CTAs of 256 threads per SM.  For 4- and 2-byte storage, 4
 // caps the sweeps at 64 registers (1024 threads per SM); measured on the 256^3 channel it
-// beats the uncapped build by 6 % (two-grid) and 23 % (AA neighbour sweep).  The FP64 sweep
-// is bound by the FP64 pipe, not by memory parallelism: 2 CTAs per SM avoid spilling.
+// beats the uncapped build by 6 % (two-grid) and 23 % (AA neighbour sweep).  D3Q27 with FP32
+// storage needs 80 registers (3: 21 % faster than 4 on the 512^3 AA turbulence box, 2 slower).
+// The FP64 sweep is bound by the FP64 pipe, not by memory parallelism: 2 CTAs per SM avoid
+// spilling.
 #ifndef LBM_SWEEP_MINB
 #if LBM_ST == 0
 #define LBM_SWEEP_MINB 2
+#elif LBM_Q == 27 && LBM_ST == 1
+#define LBM_SWEEP_MINB 3
 #else
 #define LBM_SWEEP_MINB 4
 #endif
@@ -43,7 +47,7 @@ constexpr int kMinB = LBM_SWEEP_MINB;
 #ifdef LBM_SWEEP_MINB_DIAG
 constexpr int kMinBDiag = LBM_SWEEP_MINB_DIAG;
 #else
-constexpr int kMinBDiag = LBM_SWEEP_MINB > 3 ? 3 : (LBM_SWEEP_MINB > 1 ? 1 : LBM_SWEEP_MINB);
+constexpr int kMinBDiag = LBM_SWEEP_MINB >= 4 ? 3 : (LBM_SWEEP_MINB >= 3 ? 2 : 1);
 #endif
 
 // The cells of one tile.  A thread owns one (x, y) column and walks the tile's z range.  A
