@@ -26,6 +26,7 @@
 #include "cell.cuh"
 #include "closure.hpp"
 #include "lbm.h"
+#include "mlp_tc.cuh"
 
 namespace lbm {
 namespace {
@@ -184,6 +185,10 @@ struct ClosureArgsDev {
 // Closure sweep: like the plain sweep, but every lane stays in the z loop (the network's
 // MMAs need the whole warp); lanes without a fluid cell feed zero features and skip the
 // loads and stores.
+#ifndef LBM_MLP_TC
+#define LBM_MLP_TC 0
+#endif
+
 // Minimum resident CTAs of 256 threads per SM (register cap) per closure kind, measured on a
 // 256^3 periodic box (two-grid, ms per step): Smagorinsky 0.46 at 4 (64 registers), 0.50 at 3,
 // 0.61 at 2; network 0.89 at 3 (80 registers), 1.00 at 2.
@@ -359,6 +364,93 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const MlpDev *__restrict__ ml
     for (int k = 0; k < kIn; ++k) feat[k] = s < n ? X[s * kIn + k] : 0.f;
     const float out = warp_mlp(P, feat, xs[threadIdx.x >> 5]);
     if (s < n) y[s] = out;
+}
+
+// Inference on the fifth-generation tensor cores (mlp_tc.cuh): one CTA of 128 threads per
+// tile of 128 samples; thread t owns sample (row) t.  Same rounding points as warp_mlp: BF16
+// features, weights and hidden activations, FP32 sums; the output layer in FP32 on the CUDA
+// cores.  err: set to 1 when a bounded wait on the MMA completion gives up.
+constexpr uint32_t kTcWaitLimit = 1u << 22;
+
+__global__ void __launch_bounds__(128) k_mlp_infer_tc(const MlpDev *__restrict__ mlp, const float *__restrict__ X,
+                                                      int64_t n, float *__restrict__ y, int *__restrict__ err)
+{
+    extern __shared__ unsigned char smem_raw[];
+    tc::TcSmem &S = *reinterpret_cast<tc::TcSmem *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) tc::tmem_alloc(&S.tmem, 64);
+    if (tid == 0) {
+        tc::mbar_init(&S.bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::stage_weights(S, *mlp);
+    // features of sample `tid` -> row tid of A1 (K chunks 0 and 1)
+    const int64_t s = (int64_t)blockIdx.x * 128 + tid;
+    float f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = (s < n && k < kIn) ? X[s * kIn + k] : 0.f;
+    const uint4 c0 = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
+                                pack_bf16(f[6], f[7]));
+    *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 0, 2)) = c0;
+    *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 8, 2)) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = S.tmem;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+    if (tid == 0) {
+        tc::mma_f16(tmem, tc::operand_desc(tc::smem_u32(S.a1), 2), tc::operand_desc(tc::smem_u32(S.b1), 2), idesc, 0);
+        tc::mma_commit(&S.bar);
+    }
+    bool ok = tc::mbar_wait(&S.bar, 0, kTcWaitLimit);
+    float out = 0.f;
+    if (ok) {
+        tc::fence_after_sync();
+        float v[32];
+        tc::tmem_ld32(tmem + lane_off, v);  // D1 row tid: halved pre-activations of the 32 units
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint4 q;
+            q.x = silu_pair(v[8 * c + 0] + S.bias1[8 * c + 0], v[8 * c + 1] + S.bias1[8 * c + 1]);
+            q.y = silu_pair(v[8 * c + 2] + S.bias1[8 * c + 2], v[8 * c + 3] + S.bias1[8 * c + 3]);
+            q.z = silu_pair(v[8 * c + 4] + S.bias1[8 * c + 4], v[8 * c + 5] + S.bias1[8 * c + 5]);
+            q.w = silu_pair(v[8 * c + 6] + S.bias1[8 * c + 6], v[8 * c + 7] + S.bias1[8 * c + 7]);
+            *reinterpret_cast<uint4 *>(S.a2 + tc::core_off(tid, 8 * c, 4)) = q;
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    ok = __syncthreads_and(ok);
+    if (ok) {
+        if (tid == 0) {
+            const uint32_t a2 = tc::smem_u32(S.a2), b2 = tc::smem_u32(S.b2);
+            tc::mma_f16(tmem + 32, tc::operand_desc(a2, 4), tc::operand_desc(b2, 4), idesc, 0);
+            tc::mma_f16(tmem + 32, tc::operand_desc(a2 + 256, 4), tc::operand_desc(b2 + 256, 4), idesc, 1);
+            tc::mma_commit(&S.bar);
+        }
+        ok = tc::mbar_wait(&S.bar, 1, kTcWaitLimit);
+        if (ok) {
+            tc::fence_after_sync();
+            float v[32];
+            tc::tmem_ld32(tmem + lane_off + 32, v);
+            out = mlp->b3;
+#pragma unroll
+            for (int j = 0; j < 32; j += 2) {
+                const uint32_t h = silu_pair(v[j] + S.bias2[j], v[j + 1] + S.bias2[j + 1]);
+                out = fmaf(S.w3[j], __uint_as_float(h << 16), out);
+                out = fmaf(S.w3[j + 1], __uint_as_float(h & 0xffff0000u), out);
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1);
+    if (s < n) y[s] = out;
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 // Network in FP32 (training): forward and backward of one sample.  Parameters in global
@@ -650,9 +742,27 @@ lbm_status lbm_mlp_infer(lbm_mlp *m, const float *X_dev, int64_t n, float *y_dev
     if (s != LBM_OK) return s;
     MlpDev d = mlp_device_form(h.data());
     if ((s = mlp_ck(cudaMemcpyAsync(m->dev, &d, sizeof d, cudaMemcpyHostToDevice, m->stream))) != LBM_OK) return s;
+#if LBM_MLP_TC
+    int *d_err = nullptr;
+    if ((s = mlp_ck(cudaMalloc(&d_err, sizeof(int)))) != LBM_OK) return s;
+    cudaMemsetAsync(d_err, 0, sizeof(int), m->stream);
+    const int64_t tiles = (n + 127) / 128;
+    k_mlp_infer_tc<<<(unsigned)tiles, 128, sizeof(tc::TcSmem) + 1024, m->stream>>>(m->dev, X_dev, n, y_dev, d_err);
+    if ((s = mlp_ck(cudaGetLastError())) != LBM_OK) {
+        cudaFree(d_err);
+        return s;
+    }
+    int herr = 0;
+    s = mlp_ck(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
+    if (s == LBM_OK) s = mlp_ck(cudaStreamSynchronize(m->stream));
+    cudaFree(d_err);
+    if (s != LBM_OK) return s;
+    return herr ? LBM_ERR_TIMEOUT : LBM_OK;
+#else
     const int64_t ctas = (n + 255) / 256;
     k_mlp_infer<<<(unsigned)ctas, 256, 0, m->stream>>>(m->dev, X_dev, n, y_dev);
     return mlp_ck(cudaGetLastError());
+#endif
 }
 
 lbm_status lbm_mlp_loss_grad(lbm_mlp *m, const float *X_dev, const float *T_dev, int64_t n, double *loss_host,
