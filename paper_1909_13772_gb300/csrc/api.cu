@@ -84,6 +84,7 @@ struct lbm_ctx {
     int closure = CLOSURE_NONE;
     double closure_cs = 0.0;
     MlpDev *d_mlp = nullptr;
+    int *d_tc_err = nullptr;  // set by the tensor-core network when a bounded wait gives up
 
     // tracing: events around fill and sweep launches (pairs of [start, end])
     bool timing = false;
@@ -158,6 +159,7 @@ cudaError_t sweep_of(const lbm_ctx *c, const SweepArgs &s)
     cl.cs = (float)c->closure_cs;
     cl.lambda = (float)c->p.magic_lambda;
     cl.mlp = c->d_mlp;
+    cl.err = c->d_tc_err;
     return launch_closure_sweep(cl);
 }
 cudaError_t do_fill(int q, int st, const FillArgs &s) { LBM_SWITCH(q, st, launch_fill_, s); }
@@ -769,6 +771,10 @@ lbm_status lbm_set_closure(lbm_ctx *c, int32_t kind, double cs, const float *mlp
     if (kind == LBM_CLOSURE_MLP) {
         const MlpDev d = mlp_device_form(mlp_params);
         if (!c->d_mlp) CK(cudaMalloc((void **)&c->d_mlp, sizeof(MlpDev)), "cudaMalloc(network)");
+        if (!c->d_tc_err) {
+            CK(cudaMalloc((void **)&c->d_tc_err, sizeof(int)), "cudaMalloc(network status)");
+            CK(cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream), "clear network status");
+        }
         CK(cudaMemcpyAsync(c->d_mlp, &d, sizeof d, cudaMemcpyHostToDevice, c->stream), "copy network");
         CK(cudaStreamSynchronize(c->stream), "copy network");
     }
@@ -1055,6 +1061,14 @@ lbm_status lbm_step_diagnostics(lbm_ctx *c, lbm_diagnostics *out)
         CK(cudaMemcpyAsync(h, c->d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
         CK(cudaStreamSynchronize(c->stream), "step diagnostics");
     }
+    if (c->d_tc_err && c->closure == CLOSURE_MLP) {
+        int e = 0;
+        CK(cudaMemcpy(&e, c->d_tc_err, sizeof e, cudaMemcpyDeviceToHost), "read network status");
+        if (e) {
+            CK(cudaMemset(c->d_tc_err, 0, sizeof e), "clear network status");
+            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the tensor-core network gave up; the state is invalid");
+        }
+    }
     out->mass = h[0];
     out->momentum[0] = h[1];
     out->momentum[1] = h[2];
@@ -1259,6 +1273,7 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_out);
     dfree(c->d_scratch);
     dfree(c->d_mlp);
+    dfree(c->d_tc_err);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     drop_graphs(c);
     delete c;

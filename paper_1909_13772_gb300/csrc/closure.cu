@@ -180,7 +180,80 @@ __device__ __forceinline__ void cell_stress(const float (&f)[kQ], float &rho, fl
 struct ClosureArgsDev {
     float tau0, cs, lambda;
     int trt;
+    int *err;  // set to 1 when a bounded wait of the tensor-core network gives up
 };
+
+constexpr uint32_t kTcWaitLimit = 1u << 22;
+
+// The network of 256 cells (one per thread of the CTA) on the fifth-generation tensor cores:
+// see mlp_tc.cuh.  Every thread of the CTA calls it (CTA barriers inside); ok: false once a
+// wait has given up (the outputs are then undefined and *err is set by the caller).
+__device__ __forceinline__ float tc_mlp_256(tc::TcSmem256 &S, float b3, const float (&feat)[kIn], uint32_t tmem,
+                                            bool &ok)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 0, 2)) =
+        make_uint4(pack_bf16(feat[0], feat[1]), pack_bf16(feat[2], feat[3]), pack_bf16(feat[4], feat[5]),
+                   pack_bf16(feat[6], 0.f));
+    *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 8, 2)) = make_uint4(0u, 0u, 0u, 0u);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok);
+    tc::fence_after_sync();
+    constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
+    const uint32_t a1 = tc::smem_u32(S.a1), a2 = tc::smem_u32(S.a2), b1 = tc::smem_u32(S.b1),
+                   b2 = tc::smem_u32(S.b2);
+    if (tid == 0 && ok) {
+        tc::mma_f16(tmem, tc::operand_desc(a1, 2), tc::operand_desc(b1, 2), idesc, 0);
+        tc::mma_f16(tmem + 32, tc::operand_desc(a1 + 4096, 2), tc::operand_desc(b1, 2), idesc, 0);
+        tc::mma_commit(&S.bar);
+    }
+    if (ok) ok = tc::mbar_wait(&S.bar, 0, kTcWaitLimit);
+    // warp w reads TMEM lanes 32 (w % 4) .., the half w / 4 of the tile
+    const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16, half = 32u * (uint32_t)(warp >> 2);
+    if (ok) {
+        tc::fence_after_sync();
+        float v[32];
+        tc::tmem_ld32(tmem + lane_off + half, v);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            uint4 q;
+            q.x = silu_pair(v[8 * c + 0] + S.bias1[8 * c + 0], v[8 * c + 1] + S.bias1[8 * c + 1]);
+            q.y = silu_pair(v[8 * c + 2] + S.bias1[8 * c + 2], v[8 * c + 3] + S.bias1[8 * c + 3]);
+            q.z = silu_pair(v[8 * c + 4] + S.bias1[8 * c + 4], v[8 * c + 5] + S.bias1[8 * c + 5]);
+            q.w = silu_pair(v[8 * c + 6] + S.bias1[8 * c + 6], v[8 * c + 7] + S.bias1[8 * c + 7]);
+            *reinterpret_cast<uint4 *>(S.a2 + tc::core_off(tid, 8 * c, 4)) = q;
+        }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    ok = __syncthreads_and(ok);
+    tc::fence_after_sync();
+    if (tid == 0 && ok) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            tc::mma_f16(tmem + 64 + 32 * h, tc::operand_desc(a2 + 8192 * h, 4), tc::operand_desc(b2, 4), idesc, 0);
+            tc::mma_f16(tmem + 64 + 32 * h, tc::operand_desc(a2 + 8192 * h + 256, 4), tc::operand_desc(b2 + 256, 4),
+                        idesc, 1);
+        }
+        tc::mma_commit(&S.bar);
+    }
+    if (ok) ok = tc::mbar_wait(&S.bar, 1, kTcWaitLimit);
+    float y = b3;
+    if (ok) {
+        tc::fence_after_sync();
+        float v[32];
+        tc::tmem_ld32(tmem + lane_off + 64 + half, v);
+#pragma unroll
+        for (int j = 0; j < 32; j += 2) {
+            const uint32_t h = silu_pair(v[j] + S.bias2[j], v[j + 1] + S.bias2[j + 1]);
+            y = fmaf(S.w3[j], __uint_as_float(h << 16), y);
+            y = fmaf(S.w3[j + 1], __uint_as_float(h & 0xffff0000u), y);
+        }
+    }
+    tc::fence_before_sync();
+    return y;
+}
 
 // Closure sweep: like the plain sweep, but every lane stays in the z loop (the network's
 // MMAs need the whole warp); lanes without a fluid cell feed zero features and skip the
@@ -206,7 +279,21 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
                     ClosureArgsDev ca, double *__restrict__ partials)
 {
     __shared__ MlpDev P;
+#if LBM_MLP_TC
+    __shared__ tc::TcSmem256 S;
+    uint32_t tmem = 0;
+    bool tc_ok = true;
+    if (CLOSURE == 2) {
+        if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(&S.tmem, 128);
+        if (threadIdx.x == 0) {
+            tc::mbar_init(&S.bar, 1);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        }
+        tc::stage_weights(S, *mlp);
+    }
+#else
     __shared__ uint32_t xs[8][256];
+#endif
     if (CLOSURE == 2) {
         const uint32_t *src = reinterpret_cast<const uint32_t *>(mlp);
         uint32_t *dst = reinterpret_cast<uint32_t *>(&P);
@@ -236,7 +323,16 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
         fc.hi = ((x == B.nx - 1 ? 1 : 0) | (y == B.ny - 1 ? 2 : 0)) & axes;
     }
     Diag<DIAG> dg;
+#if LBM_MLP_TC
+    if (CLOSURE == 2) {
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        tmem = S.tmem;
+    }
+#else
     uint32_t *wx = xs[threadIdx.x >> 5];
+#endif
     for (int z = t.z0; z < zend; ++z) {
         const int64_t cell = B.cell(active ? x : 0, active ? y : 0, z);
         const uint32_t m = (active && masked) ? B.mask[cell] : 0u;
@@ -276,7 +372,11 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
                                pi[3] * P.s_pi,        pi[4] * P.s_pi, pi[5] * P.s_pi};
             if (!live)
                 for (int kk = 0; kk < kIn; ++kk) feat[kk] = 0.f;
+#if LBM_MLP_TC
+            tau = ca.tau0 + P.s_tau * softplus(tc_mlp_256(S, P.b3, feat, tmem, tc_ok));
+#else
             tau = ca.tau0 + P.s_tau * softplus(warp_mlp(P, feat, wx));
+#endif
         }
         if (live) {
             const float wp = 1.f / tau;
@@ -299,6 +399,14 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
             dg.add(r2, ux, uy, uz);
         }
     }
+#if LBM_MLP_TC
+    if (CLOSURE == 2) {
+        if (!tc_ok && threadIdx.x == 0 && ca.err) atomicExch(ca.err, 1);
+        tc::fence_before_sync();
+        __syncthreads();
+        if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(tmem, 128);
+    }
+#endif
     if (DIAG) {
         __shared__ double sh[8][8];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -322,7 +430,7 @@ template <int KIND, int CLOSURE, bool DIAG>
 cudaError_t go3(const ClosureLaunch &s)
 {
     dim3 grid((unsigned)s.sw.ntiles), block((unsigned)(s.sw.tx * s.sw.ty));
-    const ClosureArgsDev ca{s.tau0, s.cs, s.lambda, s.trt};
+    const ClosureArgsDev ca{s.tau0, s.cs, s.lambda, s.trt, s.err};
     if (s.sw.through == 2)
         k_closure_sweep<KIND, CLOSURE, DIAG, 2><<<grid, block, 0, s.sw.stream>>>(
             (StoreT *)s.sw.a, (StoreT *)s.sw.b, s.sw.blocks, s.sw.tiles, s.sw.tz, s.sw.cf, s.mlp, ca, s.sw.partials);
@@ -370,8 +478,6 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const MlpDev *__restrict__ ml
 // tile of 128 samples; thread t owns sample (row) t.  Same rounding points as warp_mlp: BF16
 // features, weights and hidden activations, FP32 sums; the output layer in FP32 on the CUDA
 // cores.  err: set to 1 when a bounded wait on the MMA completion gives up.
-constexpr uint32_t kTcWaitLimit = 1u << 22;
-
 __global__ void __launch_bounds__(128) k_mlp_infer_tc(const MlpDev *__restrict__ mlp, const float *__restrict__ X,
                                                       int64_t n, float *__restrict__ y, int *__restrict__ err)
 {
@@ -649,6 +755,9 @@ cudaError_t launch_closure_sweep(const ClosureLaunch &s)
 {
     if (s.sw.ntiles <= 0) return cudaSuccess;
     if (s.sw.force || s.sw.tx * s.sw.ty > 256 || s.sw.tx % 32 != 0) return cudaErrorNotSupported;
+#if LBM_MLP_TC
+    if (s.closure == CLOSURE_MLP && s.sw.tx * s.sw.ty != 256) return cudaErrorNotSupported;  // 256-row MMA tile
+#endif
     switch (s.sw.kind) {
         case SWEEP_PULL: return go1<SWEEP_PULL>(s);
         case SWEEP_AA_LOCAL: return go1<SWEEP_AA_LOCAL>(s);

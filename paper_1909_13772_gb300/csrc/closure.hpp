@@ -31,6 +31,7 @@ struct ClosureLaunch {
     int trt;            // 1: omega- from Lambda; 0: SRT (omega- = omega+)
     float tau0, cs, lambda;
     const MlpDev *mlp;  // device copy (CLOSURE_MLP)
+    int *err;           // device flag: a bounded wait of the tensor-core network gave up
 };
 
 // Packed FP32 parameters (1348 values) -> device form.

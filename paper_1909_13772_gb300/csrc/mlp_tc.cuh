@@ -142,10 +142,22 @@ struct __align__(1024) TcSmem {
     uint32_t tmem;
 };
 
+// Shared memory of a 256-row tile (two M = 128 halves; TMEM columns 0-31 / 32-63 hold the
+// layer-1 accumulators of rows 0-127 / 128-255, columns 64-95 / 96-127 those of layer 2).
+struct __align__(1024) TcSmem256 {
+    unsigned char a1[256 * 16 * 2];
+    unsigned char a2[256 * 32 * 2];
+    unsigned char b1[32 * 16 * 2];
+    unsigned char b2[32 * 32 * 2];
+    float bias1[32], bias2[32], w3[32];
+    uint64_t bar;
+    uint32_t tmem;
+};
+
 // Stage the weights of the device-form network P into the tile's operand layout (all threads
 // of the CTA; caller syncs).
-template <class MLP>
-__device__ __forceinline__ void stage_weights(TcSmem &S, const MLP &P)
+template <class SM, class MLP>
+__device__ __forceinline__ void stage_weights(SM &S, const MLP &P)
 {
     for (int e = threadIdx.x; e < 32 * 16; e += blockDim.x) {
         const int n = e >> 4, k = e & 15;
