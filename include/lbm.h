@@ -317,10 +317,14 @@ typedef struct lbm_mlp lbm_mlp; /* opaque; owned by the library */
 /* Create a network from LBM_MLP_NPARAM packed parameters (host, copied) for batches of up
  * to max_batch samples, issuing work on cuda_stream.  Errors: LBM_ERR_ARG, LBM_ERR_OOM. */
 lbm_status lbm_mlp_create(const float *params, int64_t max_batch, void *cuda_stream, lbm_mlp **out);
-/* Replace / read the parameters (host arrays of LBM_MLP_NPARAM floats); set resets Adam. */
+/* Replace / read the parameters (host arrays of LBM_MLP_NPARAM floats); set resets Adam; get
+ * synchronises the stream and returns LBM_ERR_TIMEOUT once if an earlier inference gave up. */
 lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *params);
 lbm_status lbm_mlp_get_params(lbm_mlp *m, float *params);
-/* y[s] for n samples (asynchronous on the stream), with the BF16 rounding of the sweep. */
+/* y[s] for n samples (asynchronous on the stream), with the BF16 rounding points of the sweep,
+ * on the fifth-generation tensor cores (tcgen05, 128-sample tiles, accumulators in tensor
+ * memory).  A bounded wait inside that gives up is reported by the next lbm_mlp_get_params as
+ * LBM_ERR_TIMEOUT. */
 lbm_status lbm_mlp_infer(lbm_mlp *m, const float *X_dev, int64_t n, float *y_dev);
 /* Loss and gradient (FP32 arithmetic, deterministic summation order) of n <= max_batch
  * samples; loss_host (1 double) and grad_host (LBM_MLP_NPARAM floats, zero for the three

@@ -258,8 +258,14 @@ __device__ __forceinline__ float tc_mlp_256(tc::TcSmem256 &S, float b3, const fl
 // Closure sweep: like the plain sweep, but every lane stays in the z loop (the network's
 // MMAs need the whole warp); lanes without a fluid cell feed zero features and skip the
 // loads and stores.
-#ifndef LBM_MLP_TC
-#define LBM_MLP_TC 0
+// Tensor-core form of the network (mlp_tc.cuh): in the closure sweep (measured slower: its CTA
+// barriers per z-step serialize the gathers of the CTA's warps) and in the standalone
+// batched inference.
+#ifndef LBM_MLP_TC_SWEEP
+#define LBM_MLP_TC_SWEEP 0
+#endif
+#ifndef LBM_MLP_TC_INFER
+#define LBM_MLP_TC_INFER 1
 #endif
 
 // Minimum resident CTAs of 256 threads per SM (register cap) per closure kind, measured on a
@@ -279,7 +285,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
                     ClosureArgsDev ca, double *__restrict__ partials)
 {
     __shared__ MlpDev P;
-#if LBM_MLP_TC
+#if LBM_MLP_TC_SWEEP
     __shared__ tc::TcSmem256 S;
     uint32_t tmem = 0;
     bool tc_ok = true;
@@ -323,7 +329,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
         fc.hi = ((x == B.nx - 1 ? 1 : 0) | (y == B.ny - 1 ? 2 : 0)) & axes;
     }
     Diag<DIAG> dg;
-#if LBM_MLP_TC
+#if LBM_MLP_TC_SWEEP
     if (CLOSURE == 2) {
         tc::fence_before_sync();
         __syncthreads();
@@ -372,7 +378,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
                                pi[3] * P.s_pi,        pi[4] * P.s_pi, pi[5] * P.s_pi};
             if (!live)
                 for (int kk = 0; kk < kIn; ++kk) feat[kk] = 0.f;
-#if LBM_MLP_TC
+#if LBM_MLP_TC_SWEEP
             tau = ca.tau0 + P.s_tau * softplus(tc_mlp_256(S, P.b3, feat, tmem, tc_ok));
 #else
             tau = ca.tau0 + P.s_tau * softplus(warp_mlp(P, feat, wx));
@@ -399,7 +405,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
             dg.add(r2, ux, uy, uz);
         }
     }
-#if LBM_MLP_TC
+#if LBM_MLP_TC_SWEEP
     if (CLOSURE == 2) {
         if (!tc_ok && threadIdx.x == 0 && ca.err) atomicExch(ca.err, 1);
         tc::fence_before_sync();
@@ -481,6 +487,7 @@ __global__ void __launch_bounds__(256) k_mlp_infer(const MlpDev *__restrict__ ml
 __global__ void __launch_bounds__(128) k_mlp_infer_tc(const MlpDev *__restrict__ mlp, const float *__restrict__ X,
                                                       int64_t n, float *__restrict__ y, int *__restrict__ err)
 {
+    // persistent: TMEM, barrier and weights set up once; the CTA walks tiles of 128 samples
     extern __shared__ unsigned char smem_raw[];
     tc::TcSmem &S = *reinterpret_cast<tc::TcSmem *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -490,15 +497,7 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(const MlpDev *__restrict__
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     tc::stage_weights(S, *mlp);
-    // features of sample `tid` -> row tid of A1 (K chunks 0 and 1)
-    const int64_t s = (int64_t)blockIdx.x * 128 + tid;
-    float f[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) f[k] = (s < n && k < kIn) ? X[s * kIn + k] : 0.f;
-    const uint4 c0 = make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]),
-                                pack_bf16(f[6], f[7]));
-    *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 0, 2)) = c0;
-    *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 8, 2)) = make_uint4(0u, 0u, 0u, 0u);
+    const float b3 = mlp->b3;
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -506,44 +505,59 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(const MlpDev *__restrict__
     const uint32_t tmem = S.tmem;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
     constexpr uint32_t idesc = tc::idesc_bf16(128, 32);
-    if (tid == 0) {
-        tc::mma_f16(tmem, tc::operand_desc(tc::smem_u32(S.a1), 2), tc::operand_desc(tc::smem_u32(S.b1), 2), idesc, 0);
-        tc::mma_commit(&S.bar);
-    }
-    bool ok = tc::mbar_wait(&S.bar, 0, kTcWaitLimit);
-    float out = 0.f;
-    if (ok) {
-        tc::fence_after_sync();
-        float v[32];
-        tc::tmem_ld32(tmem + lane_off, v);  // D1 row tid: halved pre-activations of the 32 units
+    const uint32_t a1 = tc::smem_u32(S.a1), a2 = tc::smem_u32(S.a2), b1 = tc::smem_u32(S.b1),
+                   b2 = tc::smem_u32(S.b2);
+    const int64_t tiles = (n + 127) / 128;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+        // features of sample `tid` of the tile -> row tid of A1 (K chunks 0 and 1)
+        const int64_t s = tile * 128 + tid;
+        float f[8];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            uint4 q;
-            q.x = silu_pair(v[8 * c + 0] + S.bias1[8 * c + 0], v[8 * c + 1] + S.bias1[8 * c + 1]);
-            q.y = silu_pair(v[8 * c + 2] + S.bias1[8 * c + 2], v[8 * c + 3] + S.bias1[8 * c + 3]);
-            q.z = silu_pair(v[8 * c + 4] + S.bias1[8 * c + 4], v[8 * c + 5] + S.bias1[8 * c + 5]);
-            q.w = silu_pair(v[8 * c + 6] + S.bias1[8 * c + 6], v[8 * c + 7] + S.bias1[8 * c + 7]);
-            *reinterpret_cast<uint4 *>(S.a2 + tc::core_off(tid, 8 * c, 4)) = q;
-        }
-    }
-    tc::fence_async_smem();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    ok = __syncthreads_and(ok);
-    if (ok) {
+        for (int k = 0; k < 8; ++k) f[k] = (s < n && k < kIn) ? X[s * kIn + k] : 0.f;
+        *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 0, 2)) =
+            make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
+        *reinterpret_cast<uint4 *>(S.a1 + tc::core_off(tid, 8, 2)) = make_uint4(0u, 0u, 0u, 0u);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
         if (tid == 0) {
-            const uint32_t a2 = tc::smem_u32(S.a2), b2 = tc::smem_u32(S.b2);
+            tc::mma_f16(tmem, tc::operand_desc(a1, 2), tc::operand_desc(b1, 2), idesc, 0);
+            tc::mma_commit(&S.bar);
+        }
+        ok = tc::mbar_wait(&S.bar, 0, kTcWaitLimit);
+        if (ok) {
+            tc::fence_after_sync();
+            float v[32];
+            tc::tmem_ld32(tmem + lane_off, v);  // D1 row tid: halved pre-activations of the 32 units
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                uint4 q;
+                q.x = silu_pair(v[8 * c + 0] + S.bias1[8 * c + 0], v[8 * c + 1] + S.bias1[8 * c + 1]);
+                q.y = silu_pair(v[8 * c + 2] + S.bias1[8 * c + 2], v[8 * c + 3] + S.bias1[8 * c + 3]);
+                q.z = silu_pair(v[8 * c + 4] + S.bias1[8 * c + 4], v[8 * c + 5] + S.bias1[8 * c + 5]);
+                q.w = silu_pair(v[8 * c + 6] + S.bias1[8 * c + 6], v[8 * c + 7] + S.bias1[8 * c + 7]);
+                *reinterpret_cast<uint4 *>(S.a2 + tc::core_off(tid, 8 * c, 4)) = q;
+            }
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        tc::fence_after_sync();
+        if (!ok) break;
+        if (tid == 0) {
             tc::mma_f16(tmem + 32, tc::operand_desc(a2, 4), tc::operand_desc(b2, 4), idesc, 0);
             tc::mma_f16(tmem + 32, tc::operand_desc(a2 + 256, 4), tc::operand_desc(b2 + 256, 4), idesc, 1);
             tc::mma_commit(&S.bar);
         }
         ok = tc::mbar_wait(&S.bar, 1, kTcWaitLimit);
+        float out = 0.f;
         if (ok) {
             tc::fence_after_sync();
             float v[32];
             tc::tmem_ld32(tmem + lane_off + 32, v);
-            out = mlp->b3;
+            out = b3;
 #pragma unroll
             for (int j = 0; j < 32; j += 2) {
                 const uint32_t h = silu_pair(v[j] + S.bias2[j], v[j + 1] + S.bias2[j + 1]);
@@ -551,9 +565,13 @@ __global__ void __launch_bounds__(128) k_mlp_infer_tc(const MlpDev *__restrict__
                 out = fmaf(S.w3[j + 1], __uint_as_float(h & 0xffff0000u), out);
             }
         }
+        if (s < n) y[s] = out;
+        // the next tile overwrites A1, A2 and the accumulators: every thread is done with them
+        tc::fence_before_sync();
+        ok = __syncthreads_and(ok);
+        tc::fence_after_sync();
     }
     if (!ok && tid == 0) atomicExch(err, 1);
-    if (s < n) y[s] = out;
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) tc::tmem_dealloc(tmem, 64);
@@ -727,6 +745,31 @@ __global__ void k_adam(float *__restrict__ Pg, const float *__restrict__ grad, f
     Pg[p] -= lr * mh / (sqrtf(vh) + 1e-8f);
 }
 
+// Device form of packed parameters P on the device (the same values as mlp_device_form).
+__global__ void __launch_bounds__(256) k_mlp_device_form(const float *__restrict__ P, MlpDev *__restrict__ d)
+{
+    for (int e = threadIdx.x; e < kH * 16; e += blockDim.x) {
+        const int j = e >> 4, l = e & 15;
+        d->w1[j][l] = __float2bfloat16_rn(l < kIn ? 0.5f * P[kOffW1 + j * kIn + l] : 0.f);
+    }
+    for (int e = threadIdx.x; e < kH * kH; e += blockDim.x)
+        d->w2[e / kH][e % kH] = __float2bfloat16_rn(0.5f * P[kOffW2 + e]);
+    for (int e = threadIdx.x; e < 8 * kH; e += blockDim.x) {
+        const int r = e / kH, j = e % kH;
+        d->w3[r][j] = __float2bfloat16_rn(r == 0 ? P[kOffW3 + j] : 0.f);
+    }
+    for (int j = threadIdx.x; j < kH; j += blockDim.x) {
+        d->b1[j] = 0.5f * P[kOffB1 + j];
+        d->b2[j] = 0.5f * P[kOffB2 + j];
+    }
+    if (threadIdx.x == 0) {
+        d->b3 = P[kOffB3];
+        d->s_rho = P[kOffScale];
+        d->s_pi = P[kOffScale + 1];
+        d->s_tau = P[kOffScale + 2];
+    }
+}
+
 }  // namespace
 
 MlpDev mlp_device_form(const float *P)
@@ -755,7 +798,7 @@ cudaError_t launch_closure_sweep(const ClosureLaunch &s)
 {
     if (s.sw.ntiles <= 0) return cudaSuccess;
     if (s.sw.force || s.sw.tx * s.sw.ty > 256 || s.sw.tx % 32 != 0) return cudaErrorNotSupported;
-#if LBM_MLP_TC
+#if LBM_MLP_TC_SWEEP
     if (s.closure == CLOSURE_MLP && s.sw.tx * s.sw.ty != 256) return cudaErrorNotSupported;  // 256-row MMA tile
 #endif
     switch (s.sw.kind) {
@@ -776,7 +819,8 @@ using namespace lbm;
 struct lbm_mlp {
     float *P = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr, *partials = nullptr;
     double *loss = nullptr;
-    MlpDev *dev = nullptr;
+    MlpDev *dev = nullptr;  // device form of P (refreshed on the device after training)
+    int *err = nullptr;     // tensor-core inference status
     int64_t max_batch = 0, nrec_cap = 0, adam_t = 0;
     cudaStream_t stream = nullptr;
 };
@@ -805,12 +849,14 @@ lbm_status lbm_mlp_create(const float *params, int64_t max_batch, void *cuda_str
         (s = mlp_ck(cudaMalloc(&m->m2, kParams * sizeof(float)))) != LBM_OK ||
         (s = mlp_ck(cudaMalloc(&m->partials, m->nrec_cap * (kParams + 1) * sizeof(float)))) != LBM_OK ||
         (s = mlp_ck(cudaMalloc(&m->loss, sizeof(double)))) != LBM_OK ||
-        (s = mlp_ck(cudaMalloc(&m->dev, sizeof(MlpDev)))) != LBM_OK) {
+        (s = mlp_ck(cudaMalloc(&m->dev, sizeof(MlpDev)))) != LBM_OK ||
+        (s = mlp_ck(cudaMalloc(&m->err, sizeof(int)))) != LBM_OK) {
         lbm_mlp_destroy(m);
         return s;
     }
     cudaMemsetAsync(m->m1, 0, kParams * sizeof(float), m->stream);
     cudaMemsetAsync(m->m2, 0, kParams * sizeof(float), m->stream);
+    cudaMemsetAsync(m->err, 0, sizeof(int), m->stream);
     if ((s = lbm_mlp_set_params(m, params)) != LBM_OK) {
         lbm_mlp_destroy(m);
         return s;
@@ -836,42 +882,36 @@ lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *params)
 lbm_status lbm_mlp_get_params(lbm_mlp *m, float *params)
 {
     if (!m || !params) return LBM_ERR_ARG;
+    int e = 0;
     lbm_status s = mlp_ck(cudaMemcpyAsync(params, m->P, kParams * sizeof(float), cudaMemcpyDeviceToHost, m->stream));
+    if (s == LBM_OK) s = mlp_ck(cudaMemcpyAsync(&e, m->err, sizeof e, cudaMemcpyDeviceToHost, m->stream));
+    if (s == LBM_OK) s = mlp_ck(cudaStreamSynchronize(m->stream));
     if (s != LBM_OK) return s;
-    return mlp_ck(cudaStreamSynchronize(m->stream));
+    if (e) {
+        cudaMemset(m->err, 0, sizeof e);
+        return LBM_ERR_TIMEOUT;
+    }
+    return LBM_OK;
 }
 
 lbm_status lbm_mlp_infer(lbm_mlp *m, const float *X_dev, int64_t n, float *y_dev)
 {
     if (!m || !X_dev || !y_dev || n < 0) return LBM_ERR_ARG;
     if (n == 0) return LBM_OK;
-    // the device form follows the latest parameters (training updates m->P)
-    std::vector<float> h(kParams);
-    lbm_status s = lbm_mlp_get_params(m, h.data());
-    if (s != LBM_OK) return s;
-    MlpDev d = mlp_device_form(h.data());
-    if ((s = mlp_ck(cudaMemcpyAsync(m->dev, &d, sizeof d, cudaMemcpyHostToDevice, m->stream))) != LBM_OK) return s;
-#if LBM_MLP_TC
-    int *d_err = nullptr;
-    if ((s = mlp_ck(cudaMalloc(&d_err, sizeof(int)))) != LBM_OK) return s;
-    cudaMemsetAsync(d_err, 0, sizeof(int), m->stream);
+#if LBM_MLP_TC_INFER
+    // persistent CTAs: 8 per SM (8 x 64 = 512 TMEM columns, 8 x 17 KB of shared memory)
     const int64_t tiles = (n + 127) / 128;
-    k_mlp_infer_tc<<<(unsigned)tiles, 128, sizeof(tc::TcSmem) + 1024, m->stream>>>(m->dev, X_dev, n, y_dev, d_err);
-    if ((s = mlp_ck(cudaGetLastError())) != LBM_OK) {
-        cudaFree(d_err);
-        return s;
-    }
-    int herr = 0;
-    s = mlp_ck(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, m->stream));
-    if (s == LBM_OK) s = mlp_ck(cudaStreamSynchronize(m->stream));
-    cudaFree(d_err);
-    if (s != LBM_OK) return s;
-    return herr ? LBM_ERR_TIMEOUT : LBM_OK;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t grid = std::min<int64_t>(tiles, (int64_t)sms * 8);
+    k_mlp_infer_tc<<<(unsigned)grid, 128, sizeof(tc::TcSmem) + 1024, m->stream>>>(m->dev, X_dev, n, y_dev, m->err);
 #else
     const int64_t ctas = (n + 255) / 256;
+    if (ctas > 0x7fffffffLL) return LBM_ERR_ARG;
     k_mlp_infer<<<(unsigned)ctas, 256, 0, m->stream>>>(m->dev, X_dev, n, y_dev);
-    return mlp_ck(cudaGetLastError());
 #endif
+    return mlp_ck(cudaGetLastError());
 }
 
 lbm_status lbm_mlp_loss_grad(lbm_mlp *m, const float *X_dev, const float *T_dev, int64_t n, double *loss_host,
@@ -921,6 +961,9 @@ lbm_status lbm_mlp_train(lbm_mlp *m, const float *X_dev, const float *T_dev, int
         start += nb;
         if (start >= n) start = 0;
     }
+    k_mlp_device_form<<<1, 256, 0, m->stream>>>(m->P, m->dev);  // inference follows the trained P
+    lbm_status s2 = mlp_ck(cudaGetLastError());
+    if (s2 != LBM_OK) return s2;
     return mlp_ck(cudaStreamSynchronize(m->stream));
 }
 
@@ -934,6 +977,7 @@ void lbm_mlp_destroy(lbm_mlp *m)
     cudaFree(m->partials);
     cudaFree(m->loss);
     cudaFree(m->dev);
+    cudaFree(m->err);
     delete m;
 }
 

@@ -289,3 +289,29 @@ def test_mlp_sweep_at_the_coarse_study_size(torch):
     p = case.oracle_params()
     want = oracle.run(p, oracle.init(p, rho, u), 3, closure=cl)
     assert normwise(got, want) < TOL[lbm.FP32]
+
+
+def test_inference_after_training_uses_the_trained_parameters(torch):
+    """lbm_mlp_train converts the trained parameters to the inference form on the device; the
+    result must equal, bit for bit, a network created from the read-back parameters (host
+    conversion)."""
+    X = _features(5000, 8)
+    T = np.abs(np.random.default_rng(9).standard_normal(5000)).astype(np.float32)
+    Xd, Td = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    m = lbm.lbm_mlp_create(_net(71), 1024, None)
+    m2 = None
+    try:
+        lbm.lbm_mlp_train(m, Xd.data_ptr(), Td.data_ptr(), 5000, 1024, 25, 3e-3)
+        y1 = torch.empty(5000, device="cuda")
+        lbm.lbm_mlp_infer(m, Xd.data_ptr(), 5000, y1.data_ptr())
+        trained = lbm.lbm_mlp_get_params(m)
+        m2 = lbm.lbm_mlp_create(trained, 16, None)
+        y2 = torch.empty(5000, device="cuda")
+        lbm.lbm_mlp_infer(m2, Xd.data_ptr(), 5000, y2.data_ptr())
+        torch.cuda.synchronize()
+        assert torch.equal(y1, y2)
+        assert not np.array_equal(trained, _net(71))
+    finally:
+        lbm.lbm_mlp_destroy(m)
+        if m2 is not None:
+            lbm.lbm_mlp_destroy(m2)
