@@ -169,6 +169,13 @@ lbm_status lbm_get_macroscopic(lbm_ctx *ctx, int32_t block, double *rho, double 
  * AA parity.  Non-fluid cells give 0.  Synchronises the stream. */
 lbm_status lbm_get_pdfs(lbm_ctx *ctx, int32_t block, double *f);
 
+/* PDFs of a box of a block's interior cells: origin[3] and size[3] in the block's interior
+ * coordinates (inside the block), f[i * N + n] with n = x + sx (y + sy z) relative to the box,
+ * N = sx sy sz, canonical direction order, FP64 (non-fluid cells read 0).  Synchronises the
+ * stream.  Errors: LBM_ERR_ARG (null pointer, box outside the block). */
+lbm_status lbm_get_pdfs_region(lbm_ctx *ctx, int32_t block, const int32_t origin[3], const int32_t size[3],
+                               double *f);
+
 /* Overwrite one block's state with canonical post-collision PDFs f[Q*N] (host FP64),
  * converted to the storage format.  Checkpoint restart: get_pdfs of every block, then
  * set_pdfs of every block continues the run exactly.  Synchronises the stream. */

@@ -959,6 +959,32 @@ lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
     return LBM_OK;
 }
 
+lbm_status lbm_get_pdfs_region(lbm_ctx *c, int32_t block, const int32_t origin[3], const int32_t size[3], double *f)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if (!f || !origin || !size) return fail(c, LBM_ERR_ARG, "null argument");
+    const BlockLayout &L = c->blocks[block];
+    for (int a = 0; a < 3; ++a)
+        if (size[a] < 1 || origin[a] < 0 || (int64_t)origin[a] + size[a] > L.n[a])
+            return fail(c, LBM_ERR_ARG, "region outside block %d along axis %d", block, a);
+    if ((s = prepare(c)) != LBM_OK) return s;
+    const int64_t N = (int64_t)size[0] * size[1] * size[2];
+    if ((s = ensure_scratch(c, (int64_t)c->q * N)) != LBM_OK) return s;
+    CellArgs a = cell_args(c, block);
+    a.f64 = c->d_scratch;
+    for (int k = 0; k < 3; ++k) {
+        a.r0[k] = origin[k];
+        a.rn[k] = size[k];
+    }
+    CK(do_cells(c->q, c->storage, CELL_GET, 0, a), "get_pdfs_region kernel");
+    CK(cudaMemcpyAsync(f, c->d_scratch, (size_t)c->q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "copy pdfs");
+    CK(cudaStreamSynchronize(c->stream), "get_pdfs_region");
+    return LBM_OK;
+}
+
 lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
 {
     if (!c) return LBM_ERR_ARG;

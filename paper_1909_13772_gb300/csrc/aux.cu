@@ -191,17 +191,20 @@ __global__ void k_init(StoreT *__restrict__ A, const DevBlock *__restrict__ bloc
     for (int i = 0; i < kQ; ++i) S::st_plain(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), f[i], k.base[i]);
 }
 
+// PDFs of the box [r0, r0 + rn) of the block's interior cells, out[i * N + n], n = x + rx (y + ry z)
+// relative to the box (the whole block: r0 = 0, rn = its size).
 __global__ void k_get(const StoreT *__restrict__ A, const DevBlock *__restrict__ blocks, int blk, int layout,
-                      double *__restrict__ out,
-                      const uint32_t *__restrict__ mask, FillConst k)
+                      double *__restrict__ out, const uint32_t *__restrict__ mask, FillConst k, int3 r0, int3 rn)
 {
     const DevBlock *Bp = blocks + blk;
     const DevBlock &B = *Bp;
-    const int64_t N = (int64_t)B.nx * B.ny * B.nz;
+    const int64_t N = (int64_t)rn.x * rn.y * rn.z;
     const int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= N) return;
-    int x, y, z;
-    const int64_t cell = cell_of(n, B, x, y, z);
+    const int x = r0.x + (int)(n % rn.x);
+    const int y = r0.y + (int)((n / rn.x) % rn.y);
+    const int z = r0.z + (int)(n / ((int64_t)rn.x * rn.y));
+    const int64_t cell = B.cell(x, y, z);
     const StoreT *a = A + B.offset;
     const uint32_t m = mask ? mask[cell] : 0u;
     const bool fluid = !(m & kMaskSolid);
@@ -431,9 +434,15 @@ cudaError_t LBM_CAT(launch_cells_, LBM_Q, LBM_ST)(int op, int force, const CellA
             else
                 k_init<false><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, k);
             break;
-        case CELL_GET:
-            k_get<<<(unsigned)ctas, threads, 0, s.stream>>>((const StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, fk);
+        case CELL_GET: {
+            // region (the whole block when rn is zero)
+            const int3 r0 = s.rn[0] ? make_int3(s.r0[0], s.r0[1], s.r0[2]) : make_int3(0, 0, 0);
+            const int3 rn = s.rn[0] ? make_int3(s.rn[0], s.rn[1], s.rn[2]) : make_int3(s.blk.nx, s.blk.ny, s.blk.nz);
+            const int64_t Nr = (int64_t)rn.x * rn.y * rn.z;
+            k_get<<<(unsigned)((Nr + threads - 1) / threads), threads, 0, s.stream>>>(
+                (const StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, fk, r0, rn);
             break;
+        }
         case CELL_SET:
             k_set<<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, fk);
             break;

@@ -54,6 +54,7 @@ struct CellArgs {
     double *rho, *u;    // macroscopic out
     const uint32_t *mask;
     int ratio;  // coarse: edge of the coarse cell in interior cells
+    int r0[3], rn[3];  // get: box origin and size in interior cells (rn[0] == 0: the whole block)
     double F[3];
     double base[27];
     Coll<double> cd;

@@ -65,6 +65,7 @@ _SIGS = {
     "lbm_get_macroscopic": ([_vp, ctypes.c_int32, _dp, _dp], ctypes.c_int),
     "lbm_get_pdfs": ([_vp, ctypes.c_int32, _dp], ctypes.c_int),
     "lbm_set_pdfs": ([_vp, ctypes.c_int32, _dp], ctypes.c_int),
+    "lbm_get_pdfs_region": ([_vp, ctypes.c_int32, _i32p, _i32p, _dp], ctypes.c_int),
     "lbm_reduce": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
     "lbm_step_diagnostics": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
     "lbm_get_info": ([_vp, _P(lbm_info)], ctypes.c_int),
@@ -199,6 +200,16 @@ def lbm_get_macroscopic(ctx, block, rho_out, u_out):
 
 def lbm_get_pdfs(ctx, block, f_out):
     _check(ctx, load_library().lbm_get_pdfs(ctx, block, _ptr(f_out, ctypes.c_double)))
+
+
+def lbm_get_pdfs_region(ctx, block, origin, size, q):
+    """PDFs [q, sz, sy, sx] of the box origin (x, y, z) / size (sx, sy, sz) of a block."""
+    o = _arr(origin, np.int32)
+    n = _arr(size, np.int32)
+    f = np.empty((q, int(n[2]), int(n[1]), int(n[0])), np.float64)
+    _check(ctx, load_library().lbm_get_pdfs_region(ctx, block, _ptr(o, ctypes.c_int32), _ptr(n, ctypes.c_int32),
+                                                   _ptr(f, ctypes.c_double)))
+    return f
 
 
 def lbm_set_pdfs(ctx, block, f):
@@ -534,6 +545,9 @@ class Simulation:
 
     def reduce_blocks(self):
         return lbm_reduce_blocks(self.ctx, len(self.blocks))
+
+    def pdfs_region(self, b, origin, size):
+        return lbm_get_pdfs_region(self.ctx, b, origin, size, self.q)
 
     def coarse_moments(self, b, ratio):
         return lbm_coarse_moments(self.ctx, b, ratio, self.blocks[b][1])

@@ -84,3 +84,60 @@ def test_dev_storage_rest_state_stays_at_weights(storage):
     from oracle import lattice
     _, w, _ = lattice(19)
     assert np.abs(got - w[:, None, None, None]).max() <= 1e-6
+
+
+def _oracle_region(q, omega, rho, u, origin, size, steps):
+    """Oracle PDFs of the box origin/size of a periodic field after `steps` steps, from the
+    (2 steps + box) neighbourhood only: init of the neighbourhood, then per step streaming
+    f_i(x) = f*_i(x - c_i) and the single-cell collision of the oracle."""
+    import oracle
+    n = rho.shape[0]
+    h = steps
+    idx = [(np.arange(o - h, o + s + h) % n) for o, s in zip(origin, size)]  # x, y, z
+    sub_rho = rho[np.ix_(idx[2], idx[1], idx[0])]
+    sub_u = u[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+    ext = tuple(s + 2 * h for s in size)
+    p = oracle.OracleParams(shape=ext, q=q, collision=oracle.TRT, omega=omega, magic_lambda=3 / 16,
+                            periodic=(1, 1, 1))
+    f = oracle.init(p, sub_rho, sub_u)
+    c, _, _ = oracle.lattice(q)
+    for k in range(1, steps + 1):
+        nz, ny, nx = f.shape[1] - 2, f.shape[2] - 2, f.shape[3] - 2
+        g = np.empty((q, nz, ny, nx))
+        for i in range(q):
+            cx, cy, cz = c[i]
+            g[i] = f[i, 1 - cz:1 - cz + nz, 1 - cy:1 - cy + ny, 1 - cx:1 - cx + nx]
+        out = np.empty_like(g)
+        for zz in range(nz):
+            for yy in range(ny):
+                for xx in range(nx):
+                    out[:, zz, yy, xx] = oracle.collide_cell(p, g[:, zz, yy, xx])
+        f = out
+    return f
+
+
+@pytest.mark.parametrize("storage", [lbm.FP32, lbm.FP16_DEV])
+def test_full_size_d3q27_turbulence_regions_match_oracle(storage):
+    """The decaying-turbulence configuration at its full size: 512^3 periodic box, D3Q27 TRT
+    tau = 0.52, AA pattern (the bench's launch), random-phase start; after two steps (one
+    neighbour and one local sweep) two 8^3 regions -- one inside, one at the corner where every
+    neighbour wraps -- against the oracle computed from their neighbourhoods."""
+    n, steps = 512, 2
+    rho, u = inputs.turbulence(n, seed=1909, kmax=32, umax=0.05)
+    p = lbm.make_params(stencil=27, collision=lbm.TRT, storage=storage, pattern=lbm.AA, omega=1 / 0.52,
+                        periodic=(1, 1, 1))
+    sim = lbm.Simulation(p, [((0, 0, 0), (n, n, n))])
+    try:
+        sim.init(0, rho, u)
+        sim.step(steps)
+        regions = [((301, 77, 190), (8, 8, 8)), ((0, 0, 0), (8, 8, 8))]
+        got = [sim.pdfs_region(0, o, s) for o, s in regions]
+    finally:
+        sim.close()
+    for (o, s), g in zip(regions, got):
+        want = _oracle_region(27, 1 / 0.52, rho, u, o, s, steps)
+        err = normwise(g, want)
+        if storage == lbm.FP32:
+            assert err < 1e-5, err
+        else:
+            assert err <= _bound(storage, steps + 1, want, 27), err
