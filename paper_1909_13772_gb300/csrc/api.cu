@@ -85,6 +85,8 @@ struct lbm_ctx {
     double closure_cs = 0.0;
     MlpDev *d_mlp = nullptr;
     int *d_tc_err = nullptr;  // set by the tensor-core network when a bounded wait gives up
+    size_t stage_bytes = 0;   // shared memory of the staged sweep tiles (0: none)
+    int *d_sweep_err = nullptr;  // set by the staged sweep when a bounded wait gives up
 
     // tracing: events around fill and sweep launches (pairs of [start, end])
     bool timing = false;
@@ -219,6 +221,8 @@ lbm_status ensure_arena(lbm_ctx *c)
     c->arr[1] = narr == 2 ? (void *)((b + bytes1 + 255) & ~(uintptr_t)255) : nullptr;
     CK(cudaMemsetAsync(c->arr[0], 0, bytes1, c->stream), "clear PDF array");
     if (narr == 2) CK(cudaMemsetAsync(c->arr[1], 0, bytes1, c->stream), "clear PDF array");
+    CK(cudaMalloc((void **)&c->d_sweep_err, sizeof(int)), "cudaMalloc(sweep status)");
+    CK(cudaMemsetAsync(c->d_sweep_err, 0, sizeof(int), c->stream), "clear sweep status");
     c->dev_ready = true;
     return LBM_OK;
 }
@@ -288,6 +292,32 @@ lbm_status ensure_lists(lbm_ctx *c)
     if ((s2 = upload(c, c->d_runs_aa, ra, "upload runs")) != LBM_OK) return s2;
     std::vector<DevTile> dt(P.tiles.size());
     if (!dt.empty()) memcpy(dt.data(), P.tiles.data(), dt.size() * sizeof(DevTile));
+    // tiles of the two-grid sweep whose source rows are staged in shared memory by bulk copies
+    // (see sweep_staged): full block width in at most two rows, no masks, in-place neighbours
+    // only the block itself, rows x = -8 .. nx + 7 inside the padded row, 16-byte aligned
+    c->stage_bytes = 0;
+    if (c->pattern == LBM_TWO_GRID && c->storage != LBM_FP64) {
+        const int threads = c->tile[0] * c->tile[1];
+        std::vector<uint8_t> ok_block(c->blocks.size(), 0);
+        for (size_t b = 0; b < c->blocks.size(); ++b) {
+            const BlockLayout &L = c->blocks[b];
+            const int nx = L.n[0];
+            bool ok = nx <= threads && 2 * nx >= threads && (nx * c->bpp) % 16 == 0 &&
+                      ((L.xo - 8) * c->bpp) % 16 == 0 && L.xo >= 8 && L.pitch - L.xo - nx >= 8 &&
+                      (L.offset * c->bpp) % 16 == 0;
+            if (ok && !P.through.empty() && P.through[b])
+                for (int r = 0; r < 27; ++r)
+                    if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) ok = false;
+            ok_block[b] = ok;
+            if (ok) {
+                const size_t rows = (size_t)threads / nx;
+                c->stage_bytes = std::max(c->stage_bytes, 2 * (size_t)c->q * rows * (nx + 16) * c->bpp + 16);
+            }
+        }
+        for (DevTile &t : dt)
+            if (ok_block[t.block] && !(t.flags & 1) && t.x0 == 0 && t.width_m1 + 1 == c->blocks[t.block].n[0])
+                t.flags |= 2;
+    }
     if ((s2 = upload(c, c->d_tiles, dt, "upload tiles")) != LBM_OK) return s2;
     std::vector<double> par;
     for (const auto &w : P.params) {
@@ -588,6 +618,8 @@ void step_args(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
         for (int r = 0; r < 27; ++r)
             if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) sw.through = 2;
     }
+    sw.stage_bytes = c->stage_bytes;
+    sw.err = c->d_sweep_err;
     sw.cd = c->cd;
     sw.cf = c->cf;
     sw.stream = c->stream;
@@ -1087,6 +1119,14 @@ lbm_status lbm_step_diagnostics(lbm_ctx *c, lbm_diagnostics *out)
         CK(cudaMemcpyAsync(h, c->d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
         CK(cudaStreamSynchronize(c->stream), "step diagnostics");
     }
+    if (c->d_sweep_err) {
+        int e = 0;
+        CK(cudaMemcpy(&e, c->d_sweep_err, sizeof e, cudaMemcpyDeviceToHost), "read sweep status");
+        if (e) {
+            CK(cudaMemset(c->d_sweep_err, 0, sizeof e), "clear sweep status");
+            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the staged sweep gave up; the state is invalid");
+        }
+    }
     if (c->d_tc_err && c->closure == CLOSURE_MLP) {
         int e = 0;
         CK(cudaMemcpy(&e, c->d_tc_err, sizeof e, cudaMemcpyDeviceToHost), "read network status");
@@ -1300,6 +1340,7 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_scratch);
     dfree(c->d_mlp);
     dfree(c->d_tc_err);
+    dfree(c->d_sweep_err);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     drop_graphs(c);
     delete c;

@@ -238,6 +238,42 @@ __device__ __forceinline__ DevBlock block_geo(const DevBlock *Bp)
     return B;
 }
 
+// ---- bulk-copy staging of source rows (two-grid pull sweep) ---------------------------------
+// Bounded wait for phase `parity` of an mbarrier; false when it gave up.
+__device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    for (uint32_t it = 0; it < (1u << 22); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void stage_expect(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk copy (TMA, non-tensor) of `bytes` from global to shared memory, completing on *bar.
+// Both addresses 16-byte aligned, bytes a multiple of 16 (the plan only stages such rows).
+__device__ __forceinline__ void stage_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(dst)),
+        "l"(src), "r"(bytes), "r"((uint32_t)__cvta_generic_to_shared(bar))
+        : "memory");
+}
+
 // Fill the shared-memory neighbour table of block *Bp (threads 0..26; caller syncs).
 __device__ __forceinline__ void stage_neighbours(NbrGeo *nb, const DevBlock *__restrict__ blocks, const DevBlock *Bp)
 {

@@ -24,6 +24,8 @@ struct SweepArgs {
     int force;  // body force non-zero
     double *partials;  // non-null: write per-CTA diagnostics records (8 doubles per tile)
     int through;       // in-place neighbours: 0 none, 1 only the block itself (wrap), 2 other blocks
+    size_t stage_bytes;  // dynamic shared memory of the staged tiles (DevTile flag bit 1), 0: none
+    int *err;            // device flag: a bounded wait gave up
     Coll<double> cd;
     Coll<float> cf;
     cudaStream_t stream;
