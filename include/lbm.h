@@ -114,6 +114,8 @@ typedef struct {
     int64_t tiles;          /* sweep tiles (CTAs) per step */
     int64_t bytes_per_pdf;  /* bytes of one stored PDF value */
     int64_t device_bytes;   /* device memory held by the context */
+    int64_t staged_tiles;   /* tiles whose source rows the two-grid sweep stages in shared
+                               memory by bulk copies (16-bit storage, unmasked full-width tiles) */
 } lbm_info;
 
 /* Create a context for `nblocks` blocks.  `cuda_stream` is a cudaStream_t (or NULL for the
@@ -199,7 +201,7 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 /* Sweep tile shape (cells per CTA along x, y, z; threads = tx * ty).  tx must be a
  * multiple of 32, tx*ty <= 256.  A block narrower than tx gets tiles of its width rounded
  * up to 32 and proportionally more rows.  Takes effect at the next list build.
- * Default 256 x 1 x 4. */
+ * Default 256 x 1 x 4 (256 x 1 x 8 for the two-grid pattern with 16-bit storage). */
 lbm_status lbm_set_tile(lbm_ctx *ctx, int32_t tx, int32_t ty, int32_t tz);
 
 /* Per-kernel device timing of lbm_step (tracing): when enabled, lbm_step records CUDA events

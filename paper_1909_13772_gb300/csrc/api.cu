@@ -251,6 +251,45 @@ DevBlock dev_block(const lbm_ctx *c, int b)
     return d;
 }
 
+// Tiles of the two-grid sweep whose source rows are staged in shared memory by bulk copies
+// (see sweep_staged): 16-bit storage (the issue-bound case: staging takes the per-direction
+// address arithmetic off the threads; with FP32 storage the sweep is at the HBM roofline
+// without it and the staged form measured slower), full block width in at most two rows, no
+// masks, in-place neighbours only the block itself, rows x = -8 .. nx + 7 inside the padded
+// row, 16-byte aligned.  Sets flag bit 1 of those tiles when `tiles` is given, counts them in
+// *count, and returns the dynamic shared memory a staged CTA needs (0: none staged).
+size_t stage_tiles(const lbm_ctx *c, const Plan &P, DevTile *tiles, int64_t *count = nullptr)
+{
+    size_t bytes = 0;
+    int64_t n = 0;
+    if (c->pattern == LBM_TWO_GRID && c->storage >= LBM_BF16_DEV) {
+        const int threads = c->tile[0] * c->tile[1];
+        std::vector<uint8_t> ok_block(c->blocks.size(), 0);
+        for (size_t b = 0; b < c->blocks.size(); ++b) {
+            const BlockLayout &L = c->blocks[b];
+            const int nx = L.n[0];
+            bool ok = nx <= threads && 2 * nx >= threads && (nx * c->bpp) % 16 == 0 &&
+                      ((L.xo - 8) * c->bpp) % 16 == 0 && L.xo >= 8 && L.pitch - L.xo - nx >= 8 &&
+                      (L.offset * c->bpp) % 16 == 0;
+            if (ok && !P.through.empty() && P.through[b])
+                for (int r = 0; r < 27; ++r)
+                    if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) ok = false;
+            ok_block[b] = ok;
+        }
+        for (size_t i = 0; i < P.tiles.size(); ++i) {
+            const Tile &t = P.tiles[i];
+            const int nx = c->blocks[t.block].n[0];
+            if (!ok_block[t.block] || (t.flags & 1) || t.x0 != 0 || t.width_m1 + 1 != nx) continue;
+            ++n;
+            if (tiles) tiles[i].flags |= 2;
+            const size_t rows = (size_t)threads / nx;
+            bytes = std::max(bytes, kSweepStages * (size_t)c->q * rows * (nx + 16) * c->bpp + 8 * kSweepStages);
+        }
+    }
+    if (count) *count = n;
+    return bytes;
+}
+
 lbm_status ensure_lists(lbm_ctx *c)
 {
     lbm_status s = build_lists(c);
@@ -292,32 +331,7 @@ lbm_status ensure_lists(lbm_ctx *c)
     if ((s2 = upload(c, c->d_runs_aa, ra, "upload runs")) != LBM_OK) return s2;
     std::vector<DevTile> dt(P.tiles.size());
     if (!dt.empty()) memcpy(dt.data(), P.tiles.data(), dt.size() * sizeof(DevTile));
-    // tiles of the two-grid sweep whose source rows are staged in shared memory by bulk copies
-    // (see sweep_staged): full block width in at most two rows, no masks, in-place neighbours
-    // only the block itself, rows x = -8 .. nx + 7 inside the padded row, 16-byte aligned
-    c->stage_bytes = 0;
-    if (c->pattern == LBM_TWO_GRID && c->storage != LBM_FP64) {
-        const int threads = c->tile[0] * c->tile[1];
-        std::vector<uint8_t> ok_block(c->blocks.size(), 0);
-        for (size_t b = 0; b < c->blocks.size(); ++b) {
-            const BlockLayout &L = c->blocks[b];
-            const int nx = L.n[0];
-            bool ok = nx <= threads && 2 * nx >= threads && (nx * c->bpp) % 16 == 0 &&
-                      ((L.xo - 8) * c->bpp) % 16 == 0 && L.xo >= 8 && L.pitch - L.xo - nx >= 8 &&
-                      (L.offset * c->bpp) % 16 == 0;
-            if (ok && !P.through.empty() && P.through[b])
-                for (int r = 0; r < 27; ++r)
-                    if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) ok = false;
-            ok_block[b] = ok;
-            if (ok) {
-                const size_t rows = (size_t)threads / nx;
-                c->stage_bytes = std::max(c->stage_bytes, 2 * (size_t)c->q * rows * (nx + 16) * c->bpp + 16);
-            }
-        }
-        for (DevTile &t : dt)
-            if (ok_block[t.block] && !(t.flags & 1) && t.x0 == 0 && t.width_m1 + 1 == c->blocks[t.block].n[0])
-                t.flags |= 2;
-    }
+    c->stage_bytes = stage_tiles(c, P, dt.data());
     if ((s2 = upload(c, c->d_tiles, dt, "upload tiles")) != LBM_OK) return s2;
     std::vector<double> par;
     for (const auto &w : P.params) {
@@ -437,6 +451,7 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
     c->storage = p.storage;
     c->pattern = p.pattern;
     c->bpp = bytes_of(p.storage);
+    if (p.pattern == LBM_TWO_GRID && p.storage >= LBM_BF16_DEV) c->tile[2] = 8;  // staged tiles: longer z runs
     c->force = p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0;
     c->stream = (cudaStream_t)cuda_stream;
     c->blocks.resize(nblocks);
@@ -1162,6 +1177,7 @@ lbm_status lbm_get_info(lbm_ctx *c, lbm_info *out)
     out->bytes_per_pdf = c->bpp;
     out->device_bytes = (int64_t)(c->arena_owned ? c->arena_bytes : 0) + (int64_t)c->list_bytes +
                         c->partials_cap * 8 + c->scratch_cap * 8;
+    stage_tiles(c, P, nullptr, &out->staged_tiles);
     return LBM_OK;
 }
 

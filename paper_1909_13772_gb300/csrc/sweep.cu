@@ -50,30 +50,30 @@ constexpr int kMinBDiag = LBM_SWEEP_MINB_DIAG;
 constexpr int kMinBDiag = LBM_SWEEP_MINB >= 4 ? 3 : (LBM_SWEEP_MINB >= 3 ? 2 : 1);
 #endif
 
-// The cells of one tile.  A thread owns one (x, y) column and walks the tile's z range.  A
-// warp with a cell on a face of a block that reads its neighbours in place takes the
-// resolving path, all other warps the plain one (the test is warp-uniform, so neither path
-// diverges); THROUGH = some block of the launch reads its neighbours in place.
-// Staged tile of the two-grid pull sweep (DevTile flag bit 1, set by the host only for tiles
-// that span their block's full width in at most two rows, carry no masks, belong to a block
-// whose in-place neighbours are only itself, and whose rows x = -8 .. nx + 7 lie inside the
-// padded row with 16-byte aligned start and length).  For every z step the 19 (27) source rows
-// (y - c_y, z - c_z) of the tile's rows are brought into shared memory by bulk copies, one step
-// ahead, double-buffered on two mbarriers; a thread reads its populations there (x - c_x,
-// wrapped within the row when the block is its own x neighbour).  Wrapped y and z rows are
-// mapped when the copies are issued.  A wait that gives up sets *err.
+// Staged tile of the two-grid pull sweep (DevTile flag bit 1, set by the host only for 16-bit
+// storage and for tiles that span their block's full width in at most two rows, carry no
+// masks, belong to a block whose in-place neighbours are only itself, and whose rows
+// x = -8 .. nx + 7 lie inside the padded row with 16-byte aligned start and length).  For every
+// z step the 19 (27) source rows (y - c_y, z - c_z) of the tile's rows are brought into shared
+// memory by bulk copies, kStages - 1 steps ahead, on kStages buffers with one mbarrier each; a
+// thread reads its populations there (x - c_x, wrapped within the row when the block is its own
+// x neighbour).  Wrapped y and z rows are mapped when the copies are issued.  A wait that gives
+// up sets *err.
+constexpr int kStages = kSweepStages;
+
 template <bool FORCE, bool DIAG>
 __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__restrict__ Bout, const DevBlock &B,
                                              const DevTile &t, int tz, const Coll<R> &k, Diag<DIAG> &dg,
                                              unsigned char *smem, int *err)
 {
     using L = Lattice<kQ>;
+    constexpr int NS = kStages;
     const int nx = B.nx, RW = nx + 16;
     const int rows = blockDim.x / nx;
     const int nrows = min(rows, B.ny - (int)t.y0);  // rows of the tile inside the block
     const uint32_t rowbytes = (uint32_t)RW * (uint32_t)sizeof(StoreT);
     StoreT *buf = reinterpret_cast<StoreT *>(smem);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * (size_t)kQ * rows * rowbytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)NS * kQ * rows * rowbytes);
     const int tid = threadIdx.x;
     const int lx = tid % nx, ly = tid / nx;
     const bool active = ly < nrows;
@@ -81,33 +81,34 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
     const int z0 = t.z0, zend = min(z0 + tz, B.nz);
     const bool wx = (B.wrap & 1) && B.through, wy = (B.wrap & 2) && B.through, wz = (B.wrap & 4) && B.through;
     if (tid == 0) {
-        const uint32_t b0 = (uint32_t)__cvta_generic_to_shared(&bar[0]), b1 = (uint32_t)__cvta_generic_to_shared(&bar[1]);
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b1) : "memory");
+        for (int b = 0; b < NS; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bar[b]))
+                         : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const StoreT *a = A + B.offset;
+    const int lane = tid & 31;
+    // the copies of one step, issued by the lanes of warp 0 (one row each)
     auto issue = [&](int zz, int st) {
-        stage_expect(&bar[st], (uint32_t)(kQ * nrows) * rowbytes);
-        for (int i = 0; i < kQ; ++i)
-            for (int r = 0; r < nrows; ++r) {
-                int yy = t.y0 + r - L::cy(i), zs = zz - L::cz(i);
-                if (wy) yy = yy < 0 ? yy + B.ny : (yy >= B.ny ? yy - B.ny : yy);
-                if (wz) zs = zs < 0 ? zs + B.nz : (zs >= B.nz ? zs - B.nz : zs);
-                const StoreT *src =
-                    a + (int64_t)i * B.slab + (int64_t)(zs + 1) * B.plane + (int64_t)(yy + 1) * B.pitch + B.xo - 8;
-                stage_copy(buf + ((size_t)(st * kQ + i) * rows + r) * RW, src, rowbytes, &bar[st]);
-            }
+        if (lane == 0) stage_expect(&bar[st], (uint32_t)(kQ * nrows) * rowbytes);
+        __syncwarp();
+        for (int c = lane; c < kQ * nrows; c += 32) {
+            const int i = c / nrows, r = c - i * nrows;
+            int yy = t.y0 + r - L::cy(i), zs = zz - L::cz(i);
+            if (wy) yy = yy < 0 ? yy + B.ny : (yy >= B.ny ? yy - B.ny : yy);
+            if (wz) zs = zs < 0 ? zs + B.nz : (zs >= B.nz ? zs - B.nz : zs);
+            const StoreT *src =
+                a + (int64_t)i * B.slab + (int64_t)(zs + 1) * B.plane + (int64_t)(yy + 1) * B.pitch + B.xo - 8;
+            stage_copy(buf + ((size_t)(st * kQ + i) * rows + r) * RW, src, rowbytes, &bar[st]);
+        }
     };
-    if (tid == 0) {
-        issue(z0, 0);
-        if (z0 + 1 < zend) issue(z0 + 1, 1);
-    }
+    if (tid < 32)
+        for (int j = 0; j < NS && z0 + j < zend; ++j) issue(z0 + j, j);
     bool ok = true;
     for (int z = z0; z < zend; ++z) {
-        const int st = (z - z0) & 1;
-        ok = stage_wait(&bar[st], ((z - z0) >> 1) & 1) && ok;
+        const int st = (z - z0) % NS;
+        ok = stage_wait(&bar[st], ((z - z0) / NS) & 1) && ok;
         if (active && ok) {
             R f[kQ];
             const StoreT *row0 = buf + (size_t)st * kQ * rows * RW + (size_t)ly * RW + 8;
@@ -125,11 +126,15 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
             dg.add(rho, ux, uy, uz);
         }
         __syncthreads();  // every thread is done with stage st
-        if (tid == 0 && z + 2 < zend) issue(z + 2, st);
+        if (tid < 32 && z + NS < zend) issue(z + NS, st);
     }
     if (!ok && tid == 0 && err) atomicExch(err, 1);
 }
 
+// The cells of one tile.  A thread owns one (x, y) column and walks the tile's z range.  A
+// warp with a cell on a face of a block that reads its neighbours in place takes the
+// resolving path, all other warps the plain one (the test is warp-uniform, so neither path
+// diverges); THROUGH = some block of the launch reads its neighbours in place.
 template <bool FORCE, int KIND, bool DIAG, int THROUGH>
 __device__ __forceinline__ void sweep_cells(StoreT *__restrict__ A, StoreT *__restrict__ Bout,
                                             const DevBlock *__restrict__ blocks, const DevTile *__restrict__ tiles,
@@ -138,7 +143,7 @@ __device__ __forceinline__ void sweep_cells(StoreT *__restrict__ A, StoreT *__re
     const DevTile t = tiles[blockIdx.x];
     const DevBlock *Bp = blocks + t.block;
     const DevBlock B = block_geo(Bp);  // scalar geometry in registers
-    if (KIND == SWEEP_PULL && THROUGH != 2 && LBM_ST != 0 && (t.flags & 2)) {
+    if (KIND == SWEEP_PULL && THROUGH != 2 && LBM_ST >= 2 && (t.flags & 2)) {
         sweep_staged<FORCE, DIAG>(A, Bout, B, t, tz, k, dg, smem, err);
         return;
     }
@@ -244,7 +249,7 @@ cudaError_t go(const SweepArgs &s, const Coll<R> &k)
     if (s.ntiles <= 0) return cudaSuccess;
     if (s.ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     // shared memory of the staged tiles (pull sweep only)
-    const size_t smem = (KIND == SWEEP_PULL && THROUGH != 2 && LBM_ST != 0) ? s.stage_bytes : 0;
+    const size_t smem = (KIND == SWEEP_PULL && THROUGH != 2 && LBM_ST >= 2) ? s.stage_bytes : 0;
     return s.partials ? go1<FORCE, KIND, true, THROUGH>(s, k, smem) : go1<FORCE, KIND, false, THROUGH>(s, k, smem);
 }
 

@@ -47,7 +47,7 @@ class lbm_diagnostics(ctypes.Structure):
 class lbm_info(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_int64), ("fluid_cells", ctypes.c_int64), ("links", ctypes.c_int64 * 4),
                 ("ghost_slots", ctypes.c_int64), ("ghost_runs", ctypes.c_int64), ("tiles", ctypes.c_int64),
-                ("bytes_per_pdf", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("bytes_per_pdf", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("staged_tiles", ctypes.c_int64)]
 
 
 _lib = None
@@ -236,7 +236,7 @@ def lbm_get_info(ctx) -> dict:
     _check(ctx, load_library().lbm_get_info(ctx, ctypes.byref(i)))
     return {"cells": i.cells, "fluid_cells": i.fluid_cells, "links": tuple(i.links), "ghost_slots": i.ghost_slots,
             "ghost_runs": i.ghost_runs, "tiles": i.tiles, "bytes_per_pdf": i.bytes_per_pdf,
-            "device_bytes": i.device_bytes}
+            "device_bytes": i.device_bytes, "staged_tiles": i.staged_tiles}
 
 
 def lbm_set_tile(ctx, tx, ty, tz):

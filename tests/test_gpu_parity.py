@@ -428,19 +428,35 @@ def test_per_block_launches_equal_batched():
 
 
 @pytest.mark.parametrize("storage", [lbm.FP32, lbm.FP16_DEV, lbm.BF16_DEV])
-@pytest.mark.parametrize("shape,periodic,in_place", [((256, 12, 10), (1, 1, 1), True), ((128, 9, 7), (1, 0, 1), True),
-                                                     ((128, 9, 7), (1, 0, 1), False), ((256, 6, 5), (0, 1, 1), True)])
-def test_two_grid_staged_rows_match_oracle(storage, shape, periodic, in_place):
-    """Blocks 128 or 256 cells wide: the two-grid sweep stages the source rows of their unmasked
-    tiles in shared memory by bulk copies (wrapped rows for self-periodic blocks, ghost rows
-    otherwise); walls in y or x give masked tiles that take the direct path.  The last step writes
-    the diagnostics (the staged path of that variant too)."""
+@pytest.mark.parametrize("shape,periodic,in_place,tz", [((256, 12, 10), (1, 1, 1), True, None),
+                                                        ((128, 9, 7), (1, 0, 1), True, None),
+                                                        ((128, 9, 7), (1, 0, 1), False, None),
+                                                        ((256, 6, 5), (0, 1, 1), True, None),
+                                                        ((256, 12, 10), (1, 1, 1), True, 3),
+                                                        ((128, 9, 7), (1, 0, 1), False, 1)])
+def test_two_grid_staged_rows_match_oracle(storage, shape, periodic, in_place, tz):
+    """Blocks 128 or 256 cells wide: with 16-bit storage the two-grid sweep stages the source
+    rows of their unmasked tiles in shared memory by bulk copies (wrapped rows for self-periodic
+    blocks, ghost rows otherwise); walls in y or x give masked tiles that take the direct path,
+    and FP32 storage takes the direct path everywhere.  Tile depths 8 (the 16-bit default), 4, 3
+    and 1 leave ragged z runs and runs shorter than the two stages.  The last step writes the
+    diagnostics (the staged path of that variant too)."""
     case = Case(shape=shape, storage=storage, pattern=lbm.TWO_GRID, omega=1.3, force=(1e-5, 2e-6, 0.0),
                 periodic=periodic)
     rho, u = inputs.random_state(shape, seed=31, rho_amp=0.02, u_amp=0.03)
     s = case.make_sim()
     if not in_place:
         lbm.lbm_set_in_place(s.ctx, False)
+    if tz is not None:
+        s.set_tile(256, 1, tz)
+    info = s.info()
+    if storage == lbm.FP32:
+        assert info["staged_tiles"] == 0
+    elif all(periodic):
+        assert info["staged_tiles"] == info["tiles"]
+    elif periodic[0] == 1:
+        # walls in y: the tiles of the rows next to them carry masks, the others are staged
+        assert 0 < info["staged_tiles"] < info["tiles"]
     init_sim(s, rho, u)
     steps = 7
     s.step(steps)
