@@ -283,7 +283,7 @@ size_t stage_tiles(const lbm_ctx *c, const Plan &P, DevTile *tiles, int64_t *cou
             ++n;
             if (tiles) tiles[i].flags |= 2;
             const size_t rows = (size_t)threads / nx;
-            bytes = std::max(bytes, kSweepStages * (size_t)c->q * rows * (nx + 16) * c->bpp + 8 * kSweepStages);
+            bytes = std::max(bytes, kSweepStages * ((size_t)c->q * rows * (nx + 16) * c->bpp + 16));
         }
     }
     if (count) *count = n;

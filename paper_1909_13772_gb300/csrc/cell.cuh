@@ -255,6 +255,12 @@ __device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity)
     return false;
 }
 
+__device__ __forceinline__ void stage_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count)
+                 : "memory");
+}
+
 __device__ __forceinline__ void stage_expect(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(

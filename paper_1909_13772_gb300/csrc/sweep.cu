@@ -55,10 +55,11 @@ constexpr int kMinBDiag = LBM_SWEEP_MINB >= 4 ? 3 : (LBM_SWEEP_MINB >= 3 ? 2 : 1
 // masks, belong to a block whose in-place neighbours are only itself, and whose rows
 // x = -8 .. nx + 7 lie inside the padded row with 16-byte aligned start and length).  For every
 // z step the 19 (27) source rows (y - c_y, z - c_z) of the tile's rows are brought into shared
-// memory by bulk copies, kStages - 1 steps ahead, on kStages buffers with one mbarrier each; a
-// thread reads its populations there (x - c_x, wrapped within the row when the block is its own
-// x neighbour).  Wrapped y and z rows are mapped when the copies are issued.  A wait that gives
-// up sets *err.
+// memory by bulk copies, one step ahead, double-buffered on two mbarriers (a CTA barrier per
+// step frees a buffer: waiting warps are parked, where polling an "empty" mbarrier instead
+// costs issue slots this issue-bound sweep does not have).  A thread reads its populations
+// there (x - c_x, wrapped within the row when the block is its own x neighbour).  Wrapped y
+// and z rows are mapped when the copies are issued.  A wait that gives up sets *err.
 constexpr int kStages = kSweepStages;
 
 template <bool FORCE, bool DIAG>
@@ -71,36 +72,46 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
     const int nx = B.nx, RW = nx + 16;
     const int rows = blockDim.x / nx;
     const int nrows = min(rows, B.ny - (int)t.y0);  // rows of the tile inside the block
-    const uint32_t rowbytes = (uint32_t)RW * (uint32_t)sizeof(StoreT);
+    const uint32_t rowbytes = (uint32_t)nx * (uint32_t)sizeof(StoreT);  // x = 0 .. nx - 1, 128-byte aligned
+    constexpr uint32_t kHalo = 8 * sizeof(StoreT);                        // x = -8 .. -1 or nx .. nx + 7
     StoreT *buf = reinterpret_cast<StoreT *>(smem);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + (size_t)NS * kQ * rows * rowbytes);
+    // full[s]: the copies of the step in stage s have landed
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)NS * kQ * rows * RW * sizeof(StoreT));
     const int tid = threadIdx.x;
     const int lx = tid % nx, ly = tid / nx;
     const bool active = ly < nrows;
     const int x = lx, y = t.y0 + ly;
     const int z0 = t.z0, zend = min(z0 + tz, B.nz);
     const bool wx = (B.wrap & 1) && B.through, wy = (B.wrap & 2) && B.through, wz = (B.wrap & 4) && B.through;
+    int qx = 0;  // directions with c_x != 0: they read one element beyond the row
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) qx += L::cx(i) != 0;
+    const uint32_t stepbytes = (uint32_t)nrows * ((uint32_t)kQ * rowbytes + (wx ? 0u : (uint32_t)qx * kHalo));
     if (tid == 0) {
-        for (int b = 0; b < NS; ++b)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"((uint32_t)__cvta_generic_to_shared(&bar[b]))
-                         : "memory");
+        for (int b = 0; b < NS; ++b) stage_init(&full[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const StoreT *a = A + B.offset;
     const int lane = tid & 31;
-    // the copies of one step, issued by the lanes of warp 0 (one row each)
+    // The copies of one step, issued by the lanes of warp 0 (one row each).  Only the row's own
+    // 128-byte lines are copied: with the x wrap in place the row is its own neighbour; otherwise
+    // the one ghost element a direction reads comes with a 16-byte copy on that side only.
     auto issue = [&](int zz, int st) {
-        if (lane == 0) stage_expect(&bar[st], (uint32_t)(kQ * nrows) * rowbytes);
+        if (lane == 0) stage_expect(&full[st], stepbytes);
         __syncwarp();
         for (int c = lane; c < kQ * nrows; c += 32) {
             const int i = c / nrows, r = c - i * nrows;
             int yy = t.y0 + r - L::cy(i), zs = zz - L::cz(i);
             if (wy) yy = yy < 0 ? yy + B.ny : (yy >= B.ny ? yy - B.ny : yy);
             if (wz) zs = zs < 0 ? zs + B.nz : (zs >= B.nz ? zs - B.nz : zs);
-            const StoreT *src =
-                a + (int64_t)i * B.slab + (int64_t)(zs + 1) * B.plane + (int64_t)(yy + 1) * B.pitch + B.xo - 8;
-            stage_copy(buf + ((size_t)(st * kQ + i) * rows + r) * RW, src, rowbytes, &bar[st]);
+            const StoreT *src = a + (int64_t)i * B.slab + (int64_t)(zs + 1) * B.plane + (int64_t)(yy + 1) * B.pitch + B.xo;
+            StoreT *dst = buf + ((size_t)(st * kQ + i) * rows + r) * RW + 8;
+            stage_copy(dst, src, rowbytes, &full[st]);
+            if (!wx && L::cx(i) != 0) {
+                const int h = L::cx(i) > 0 ? -8 : nx;
+                stage_copy(dst + h, src + h, kHalo, &full[st]);
+            }
         }
     };
     if (tid < 32)
@@ -108,7 +119,7 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
     bool ok = true;
     for (int z = z0; z < zend; ++z) {
         const int st = (z - z0) % NS;
-        ok = stage_wait(&bar[st], ((z - z0) / NS) & 1) && ok;
+        ok = stage_wait(&full[st], ((z - z0) / NS) & 1) && ok;
         if (active && ok) {
             R f[kQ];
             const StoreT *row0 = buf + (size_t)st * kQ * rows * RW + (size_t)ly * RW + 8;
@@ -128,7 +139,7 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
         __syncthreads();  // every thread is done with stage st
         if (tid < 32 && z + NS < zend) issue(z + NS, st);
     }
-    if (!ok && tid == 0 && err) atomicExch(err, 1);
+    if (!ok && err) atomicExch(err, 1);
 }
 
 // The cells of one tile.  A thread owns one (x, y) column and walks the tile's z range.  A
