@@ -22,33 +22,53 @@ constexpr bool kAccurate = LBM_ST == 1;
 // cells, fluid cells.  Per cell the thread keeps sum rho |u|^2 and max |u|^2; the halving and
 // the square root are taken once per thread (record()).  A cell counts as non-finite when
 // rho + |u|^2 is (an infinity or NaN in either propagates to the sum).
+// The running sums of a thread live in shared memory, column threadIdx.x of an [8][256]
+// array (CTAs of at most 256 threads), not in registers: there they would stay live across
+// the thread's whole z loop next to the cell's populations, which costs the sweep a CTA per SM
+// or spills.  Each thread touches only its own column, in the same order of operations.
+template <bool DIAG>
+__device__ __forceinline__ R *diag_home()
+{
+    __shared__ R home[DIAG ? 8 * 256 : 1];
+    return home + threadIdx.x;
+}
+
 template <bool DIAG>
 struct Diag {
-    R m = R(0), jx = R(0), jy = R(0), jz = R(0), e2 = R(0), u2max = R(0), bad = R(0), n = R(0);
+    __device__ __forceinline__ Diag()
+    {
+        if (!DIAG) return;
+        R *h = diag_home<DIAG>();
+#pragma unroll
+        for (int c = 0; c < 8; ++c) h[c * 256] = R(0);
+    }
     __device__ __forceinline__ void add(R rho, R ux, R uy, R uz)
     {
         if (!DIAG) return;
+        R *h = diag_home<DIAG>();
         const R u2 = ux * ux + uy * uy + uz * uz;
-        m += rho;
-        jx = fma(rho, ux, jx);
-        jy = fma(rho, uy, jy);
-        jz = fma(rho, uz, jz);
-        e2 = fma(rho, u2, e2);
-        u2max = fmax(u2max, u2);
-        bad += isfinite(rho + u2) ? R(0) : R(1);
-        n += R(1);
+        h[0] += rho;
+        h[256] = fma(rho, ux, h[256]);
+        h[512] = fma(rho, uy, h[512]);
+        h[768] = fma(rho, uz, h[768]);
+        h[1024] = fma(rho, u2, h[1024]);
+        h[1280] = fmax(h[1280], u2);
+        h[1536] += isfinite(rho + u2) ? R(0) : R(1);
+        h[1792] += R(1);
     }
     // the thread's record: mass, momentum x/y/z, kinetic energy, max |u|, non-finite, cells
     __device__ __forceinline__ void record(R (&v)[8]) const
     {
-        v[0] = m;
-        v[1] = jx;
-        v[2] = jy;
-        v[3] = jz;
-        v[4] = R(0.5) * e2;
-        v[5] = sqrt(u2max);
-        v[6] = bad;
-        v[7] = n;
+        if (!DIAG) return;
+        const R *h = diag_home<DIAG>();
+        v[0] = h[0];
+        v[1] = h[256];
+        v[2] = h[512];
+        v[3] = h[768];
+        v[4] = R(0.5) * h[1024];
+        v[5] = sqrt(h[1280]);
+        v[6] = h[1536];
+        v[7] = h[1792];
     }
 };
 

@@ -41,13 +41,13 @@ namespace lbm {
 
 namespace {
 
-// The diagnostics variant (DIAG) keeps eight running sums in registers; one CTA fewer per
-// SM leaves it room for them without spilling.
+// The diagnostics variant (DIAG) keeps its running sums in shared memory (Diag), so it runs
+// at the occupancy of the plain sweep.
 constexpr int kMinB = LBM_SWEEP_MINB;
 #ifdef LBM_SWEEP_MINB_DIAG
 constexpr int kMinBDiag = LBM_SWEEP_MINB_DIAG;
 #else
-constexpr int kMinBDiag = LBM_SWEEP_MINB >= 4 ? 3 : (LBM_SWEEP_MINB >= 3 ? 2 : 1);
+constexpr int kMinBDiag = LBM_SWEEP_MINB;
 #endif
 
 // Staged tile of the two-grid pull sweep (DevTile flag bit 1, set by the host only for 16-bit
