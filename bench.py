@@ -19,7 +19,7 @@ a bounded sample of the same workload: each step is one oracle time step of a
 that the run takes about a minute.
 
 Multi-GPU: every rank runs an independent replica of the workload on its own GPU (the
-path is not sharded in this build); value = total lattice updates of all ranks / max time.
+path is not sharded); value = total lattice updates of all ranks / max time.
 """
 from __future__ import annotations
 
@@ -166,6 +166,37 @@ def sweep_source_hash() -> str:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+# FP64 pipe of one GB300: ncu's peak for DFMA-pipe thread-instructions is 2 per clock per SM;
+# x 152 SMs x 2,070 MHz (maximum SM clock) = 629.3 G thread-instructions/s (derived, not measured).
+FP64_PIPE_PEAK_GINST = 2 * 152 * 2.070
+
+
+def recorded_fp64_ops(variant: str):
+    """FP64-pipe thread-instructions (DADD + DFMA + DMUL) per cell of one sweep launch from a
+    committed ncu summary taken on the current sweep source (a line 'FP64OPS variant=<v>
+    per_cell=<n> source=<hash>')."""
+    cur = sweep_source_hash()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "*.md")) + glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
+        with open(path) as fh:
+            for line in fh:
+                m = re.search(r"FP64OPS variant=(\S+) per_cell=([0-9.eE+]+) source=([0-9a-f]+)", line)
+                if m and m.group(1) == variant and m.group(3) == cur:
+                    return float(m.group(2))
+    return None
+
+
+def fp64_pipe(variant: str, cells: int, sweep_ms: float):
+    """The FP64 sweep against the FP64 pipe (it is bound there, not by HBM): recorded
+    instructions per cell x cells / sweep time over the derived peak; None without a record."""
+    per_cell = recorded_fp64_ops(variant)
+    if per_cell is None or sweep_ms <= 0:
+        return None
+    achieved = per_cell * cells / (sweep_ms / 1e3) / 1e9
+    return {"per_cell": per_cell, "achieved": round(achieved, 1), "peak": round(FP64_PIPE_PEAK_GINST, 1),
+            "unit": "G FP64 thread-instructions/s", "frac": round(achieved / FP64_PIPE_PEAK_GINST, 4),
+            "peak_source": "derived: 2 per clock per SM x 152 SMs x 2,070 MHz"}
 
 
 def closure_source_hash() -> str:
@@ -343,6 +374,15 @@ def run_ours(args):
             "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured" else "fallback",
             "alg_bytes_per_launch": res["alg_bytes_per_sweep"], "sweep_ms": round(res["sweep_ms"], 4),
             "sweep_share_of_step": round(res["sweep_share"], 4)}
+    fp64 = fp64_pipe(head, res["info"]["cells"], res["sweep_ms"]) if head.startswith("fp64") else None
+    if fp64 is not None:
+        # bound by the FP64 pipe: that is the roofline; the HBM figures stay beside it
+        roof = {"bound": "alu", "achieved": fp64["achieved"], "peak": fp64["peak"], "unit": fp64["unit"],
+                "frac": fp64["frac"], "traffic": traffic, "kernel": roof["kernel"],
+                "peak_source": fp64["peak_source"], "fp64_per_cell": fp64["per_cell"],
+                "hbm": {"achieved": roof["achieved"], "peak": peak, "unit": "GB/s", "frac": roof["frac"]},
+                "alg_bytes_per_launch": roof["alg_bytes_per_launch"], "sweep_ms": roof["sweep_ms"],
+                "sweep_share_of_step": roof["sweep_share_of_step"]}
     out = {
         "metric": METRIC, "value": round(res["mlups"], 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(res["ms_per_step"], 4), "higher_is_better": True,
@@ -360,9 +400,11 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
-        "variants": {k: {"mlups": round(v["mlups"], 1), "sweep_gbs": round(v["sweep_gbs"], 1),
-                         "frac_hbm": round(v["sweep_gbs"] / peak, 4), "ms_per_step": round(v["ms_per_step"], 4),
-                         "sweep_ms": round(v["sweep_ms"], 4), "fill_ms": round(v["fill_ms"], 4)}
+        "variants": {k: dict({"mlups": round(v["mlups"], 1), "sweep_gbs": round(v["sweep_gbs"], 1),
+                              "frac_hbm": round(v["sweep_gbs"] / peak, 4), "ms_per_step": round(v["ms_per_step"], 4),
+                              "sweep_ms": round(v["sweep_ms"], 4), "fill_ms": round(v["fill_ms"], 4)},
+                             **({"fp64_pipe": fp64_pipe(k, v["info"]["cells"], v["sweep_ms"])}
+                                if k.startswith("fp64") else {}))
                      for k, v in variants.items()},
     }
     if rank == 0:

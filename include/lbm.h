@@ -57,7 +57,7 @@ typedef enum {
     LBM_ERR_OOM = 4,         /* device or host allocation failed / bound buffer too small */
     LBM_ERR_DIVERGED = 5,    /* diagnostics found non-finite values */
     LBM_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
-    LBM_ERR_UNSUPPORTED = 7  /* valid request this build does not support */
+    LBM_ERR_UNSUPPORTED = 7  /* valid request the library does not support */
 } lbm_status;
 
 enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 };
@@ -365,7 +365,7 @@ lbm_status lbm_set_in_place(lbm_ctx *ctx, int32_t enable);
  * lbm_reduce up to the order of the sums. */
 lbm_status lbm_reduce_blocks(lbm_ctx *ctx, double *out);
 
-/* Box sums of a block for coarse-graining (the filtered fine-grid fields that train and judge
+/* Box sums of a block for coarse-graining (the filtered fine-grid fields that train and score
  * the learned closure): for each coarse cell of ratio^3 interior cells (every block edge
  * divisible by ratio), the sums over its fluid cells of rho, rho u_x, rho u_y, rho u_z and
  * rho u_a u_b (xx, yy, zz, xy, xz, yz), with rho and u as lbm_get_macroscopic gives them.
