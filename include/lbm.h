@@ -195,6 +195,17 @@ lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
  * Errors: LBM_ERR_STATE when the state was set (init, set_pdfs) after the last step. */
 lbm_status lbm_step_diagnostics(lbm_ctx *ctx, lbm_diagnostics *out);
 
+/* Bounded device-side waits.  The kernels that wait on an mbarrier (the staged sweep for the
+ * completion of its bulk copies, the tensor-core network for its MMAs) give up after a fixed
+ * number of polls, set a device status flag and return; every call that synchronises the
+ * stream and reads results (lbm_step_diagnostics, lbm_reduce, lbm_reduce_blocks,
+ * lbm_get_macroscopic, lbm_get_pdfs, lbm_get_pdfs_region, lbm_coarse_moments) then returns
+ * LBM_ERR_TIMEOUT once and clears the flag; the context stays usable.
+ * lbm_selfcheck_wait exercises that path: one device thread waits at most `polls` polls
+ * (1 <= polls <= 2^20) on an mbarrier nothing arrives on, gives up and sets the flag; the
+ * state is not touched.  Synchronises the stream.  Errors: LBM_ERR_ARG (polls out of range). */
+lbm_status lbm_selfcheck_wait(lbm_ctx *ctx, int32_t polls);
+
 /* Work sizes of one step (builds the boundary lists if needed). */
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 

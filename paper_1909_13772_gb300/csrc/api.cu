@@ -424,6 +424,34 @@ lbm_status check_block(lbm_ctx *c, int32_t block)
     return LBM_OK;
 }
 
+// Status of the bounded device-side waits, read after the stream has been synchronised:
+// LBM_ERR_TIMEOUT once after a wait gave up (the flag is then cleared), else LBM_OK.
+lbm_status wait_status(lbm_ctx *c)
+{
+    if (c->d_sweep_err) {
+        int e = 0;
+        CK(cudaMemcpyAsync(&e, c->d_sweep_err, sizeof e, cudaMemcpyDeviceToHost, c->stream), "read wait status");
+        CK(cudaStreamSynchronize(c->stream), "read wait status");
+        if (e) {
+            CK(cudaMemsetAsync(c->d_sweep_err, 0, sizeof e, c->stream), "clear wait status");
+            CK(cudaStreamSynchronize(c->stream), "clear wait status");
+            if (e == 2) return fail(c, LBM_ERR_TIMEOUT, "the wait self-check gave up as designed; the state is untouched");
+            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the staged sweep gave up; the state is invalid");
+        }
+    }
+    if (c->d_tc_err && c->closure == CLOSURE_MLP) {
+        int e = 0;
+        CK(cudaMemcpyAsync(&e, c->d_tc_err, sizeof e, cudaMemcpyDeviceToHost, c->stream), "read network status");
+        CK(cudaStreamSynchronize(c->stream), "read network status");
+        if (e) {
+            CK(cudaMemsetAsync(c->d_tc_err, 0, sizeof e, c->stream), "clear network status");
+            CK(cudaStreamSynchronize(c->stream), "clear network status");
+            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the tensor-core network gave up; the state is invalid");
+        }
+    }
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -961,7 +989,7 @@ lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u
     CK(cudaMemcpyAsync(rho, c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy rho");
     CK(cudaMemcpyAsync(u, c->d_scratch + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy u");
     CK(cudaStreamSynchronize(c->stream), "get_macroscopic");
-    return LBM_OK;
+    return wait_status(c);
 }
 
 lbm_status lbm_coarse_moments(lbm_ctx *c, int32_t block, int32_t ratio, double *out)
@@ -984,7 +1012,7 @@ lbm_status lbm_coarse_moments(lbm_ctx *c, int32_t block, int32_t ratio, double *
     CK(cudaMemcpyAsync(out, c->d_scratch, 10 * Nc * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
        "copy coarse moments");
     CK(cudaStreamSynchronize(c->stream), "coarse_moments");
-    return LBM_OK;
+    return wait_status(c);
 }
 
 lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
@@ -1003,7 +1031,7 @@ lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
     CK(cudaMemcpyAsync(f, c->d_scratch, (size_t)c->q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
        "copy pdfs");
     CK(cudaStreamSynchronize(c->stream), "get_pdfs");
-    return LBM_OK;
+    return wait_status(c);
 }
 
 lbm_status lbm_get_pdfs_region(lbm_ctx *c, int32_t block, const int32_t origin[3], const int32_t size[3], double *f)
@@ -1029,7 +1057,7 @@ lbm_status lbm_get_pdfs_region(lbm_ctx *c, int32_t block, const int32_t origin[3
     CK(cudaMemcpyAsync(f, c->d_scratch, (size_t)c->q * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
        "copy pdfs");
     CK(cudaStreamSynchronize(c->stream), "get_pdfs_region");
-    return LBM_OK;
+    return wait_status(c);
 }
 
 lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
@@ -1084,7 +1112,7 @@ lbm_status lbm_reduce_blocks(lbm_ctx *c, double *out)
     CK(cudaMemcpyAsync(out, c->d_scratch, 8 * nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
        "copy per-block diagnostics");
     CK(cudaStreamSynchronize(c->stream), "reduce_blocks");
-    return LBM_OK;
+    return wait_status(c);
 }
 
 lbm_status lbm_reduce(lbm_ctx *c, lbm_diagnostics *out)
@@ -1120,6 +1148,17 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_diagnostics *out)
     out->max_speed = h[5];
     out->nonfinite = (int64_t)h[6];
     out->fluid_cells = (int64_t)h[7];
+    return wait_status(c);
+}
+
+lbm_status lbm_selfcheck_wait(lbm_ctx *c, int32_t polls)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (polls < 1 || polls > (1 << 20)) return fail(c, LBM_ERR_ARG, "polls %d outside [1, 2^20]", polls);
+    lbm_status s = prepare(c);
+    if (s != LBM_OK) return s;
+    CK(launch_wait_selfcheck(c->d_sweep_err, (uint32_t)polls, c->stream), "wait self-check");
+    CK(cudaStreamSynchronize(c->stream), "wait self-check");
     return LBM_OK;
 }
 
@@ -1134,22 +1173,8 @@ lbm_status lbm_step_diagnostics(lbm_ctx *c, lbm_diagnostics *out)
         CK(cudaMemcpyAsync(h, c->d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
         CK(cudaStreamSynchronize(c->stream), "step diagnostics");
     }
-    if (c->d_sweep_err) {
-        int e = 0;
-        CK(cudaMemcpy(&e, c->d_sweep_err, sizeof e, cudaMemcpyDeviceToHost), "read sweep status");
-        if (e) {
-            CK(cudaMemset(c->d_sweep_err, 0, sizeof e), "clear sweep status");
-            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the staged sweep gave up; the state is invalid");
-        }
-    }
-    if (c->d_tc_err && c->closure == CLOSURE_MLP) {
-        int e = 0;
-        CK(cudaMemcpy(&e, c->d_tc_err, sizeof e, cudaMemcpyDeviceToHost), "read network status");
-        if (e) {
-            CK(cudaMemset(c->d_tc_err, 0, sizeof e), "clear network status");
-            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the tensor-core network gave up; the state is invalid");
-        }
-    }
+    const lbm_status ws = wait_status(c);
+    if (ws != LBM_OK) return ws;
     out->mass = h[0];
     out->momentum[0] = h[1];
     out->momentum[1] = h[2];

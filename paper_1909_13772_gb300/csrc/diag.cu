@@ -4,6 +4,7 @@
 // the result is the same from run to run.  Record: mass, momentum x/y/z, kinetic energy, max |u| (max, not sum),
 // non-finite cells, fluid cells.
 #include "launch.hpp"
+#include "mlp_tc.cuh"
 
 namespace lbm {
 namespace {
@@ -92,6 +93,26 @@ cudaError_t launch_block_final(const double *partials, const int64_t *start, int
     if (nblocks <= 0) return cudaSuccess;
     if (nblocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     k_block_final<<<(unsigned)nblocks, 256, 0, s>>>(partials, start, out);
+    return cudaGetLastError();
+}
+
+namespace {
+// One thread waits, at most `polls` polls, on an mbarrier nothing arrives on (phase 0 of a
+// barrier initialised for one arrival), gives up and records value 2 in *err: the path a
+// staged sweep takes when its bounded wait runs out, without any copy in flight.
+__global__ void k_wait_selfcheck(int *err, uint32_t polls)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tc::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!tc::mbar_wait(&bar, 0, polls)) atomicExch(err, 2);
+}
+}  // namespace
+
+cudaError_t launch_wait_selfcheck(int *err, uint32_t polls, cudaStream_t s)
+{
+    k_wait_selfcheck<<<1, 32, 0, s>>>(err, polls);
     return cudaGetLastError();
 }
 

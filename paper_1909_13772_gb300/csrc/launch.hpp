@@ -92,6 +92,8 @@ enum CellOp { CELL_INIT = 0, CELL_GET = 1, CELL_SET = 2, CELL_MACRO = 3, CELL_CO
 // Second pass of the diagnostics: fixed-order sum of n per-CTA records into out[8].
 // out must hold reduce_final_scratch(n) doubles: the 8 results, then the first-level records.
 cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, cudaStream_t s);
+// One thread waits `polls` polls on an mbarrier that never completes and sets *err = 2.
+cudaError_t launch_wait_selfcheck(int *err, uint32_t polls, cudaStream_t s);
 int64_t reduce_final_scratch(int64_t n);
 // Per-block second pass: block b sums the records of tiles start[b] .. start[b+1] - 1 (tiles
 // are stored block by block) into out[8 b .. 8 b + 7].

@@ -68,6 +68,7 @@ _SIGS = {
     "lbm_get_pdfs_region": ([_vp, ctypes.c_int32, _i32p, _i32p, _dp], ctypes.c_int),
     "lbm_reduce": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
     "lbm_step_diagnostics": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
+    "lbm_selfcheck_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_get_info": ([_vp, _P(lbm_info)], ctypes.c_int),
     "lbm_set_tile": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "lbm_kernel_launches": ([_vp], ctypes.c_int64),
@@ -229,6 +230,10 @@ def lbm_step_diagnostics(ctx) -> dict:
     _check(ctx, load_library().lbm_step_diagnostics(ctx, ctypes.byref(d)))
     return {"mass": d.mass, "momentum": tuple(d.momentum), "kinetic_energy": d.kinetic_energy,
             "max_speed": d.max_speed, "nonfinite": d.nonfinite, "fluid_cells": d.fluid_cells}
+
+
+def lbm_selfcheck_wait(ctx, polls=1024):
+    _check(ctx, load_library().lbm_selfcheck_wait(ctx, polls))
 
 
 def lbm_get_info(ctx) -> dict:

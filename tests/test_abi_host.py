@@ -55,6 +55,10 @@ def test_create_rejects_bad_arguments():
         lbm.lbm_create_blocks(p, [((0, 0, 0), (4, 4, 4)), ((2, 0, 0), (4, 4, 4))])
     ctx = lbm.lbm_create_blocks(p, [((0, 0, 0), (4, 4, 4))])
     try:
+        for polls in (0, -3, (1 << 20) + 1):  # checked before any device work
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_selfcheck_wait(ctx, polls)
+            assert e.value.status == 1
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_tile(ctx, 48, 4, 4)
         with pytest.raises(lbm.LbmError):
