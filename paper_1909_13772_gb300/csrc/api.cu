@@ -87,6 +87,12 @@ struct lbm_ctx {
     int *d_tc_err = nullptr;  // set by the tensor-core network when a bounded wait gives up
     size_t stage_bytes = 0;   // shared memory of the staged sweep tiles (0: none)
     int *d_sweep_err = nullptr;  // set by the staged sweep when a bounded wait gives up
+    // pinned host landing zone of the per-step reads (diagnostics record, wait-status flags), so
+    // their copies are asynchronous and one stream synchronisation covers them
+    struct HostIO {
+        double diag[8];
+        int wait_err[2];
+    } *h_io = nullptr;
 
     // tracing: events around fill and sweep launches (pairs of [start, end])
     bool timing = false;
@@ -223,6 +229,7 @@ lbm_status ensure_arena(lbm_ctx *c)
     if (narr == 2) CK(cudaMemsetAsync(c->arr[1], 0, bytes1, c->stream), "clear PDF array");
     CK(cudaMalloc((void **)&c->d_sweep_err, sizeof(int)), "cudaMalloc(sweep status)");
     CK(cudaMemsetAsync(c->d_sweep_err, 0, sizeof(int), c->stream), "clear sweep status");
+    CK(cudaMallocHost((void **)&c->h_io, sizeof(lbm_ctx::HostIO)), "cudaMallocHost(status)");
     c->dev_ready = true;
     return LBM_OK;
 }
@@ -424,32 +431,45 @@ lbm_status check_block(lbm_ctx *c, int32_t block)
     return LBM_OK;
 }
 
-// Status of the bounded device-side waits, read after the stream has been synchronised:
+// Status of the bounded device-side waits.  wait_status_enqueue queues the copies of the flags
+// into the pinned landing zone; after the stream has been synchronised wait_status_take reports
 // LBM_ERR_TIMEOUT once after a wait gave up (the flag is then cleared), else LBM_OK.
-lbm_status wait_status(lbm_ctx *c)
+lbm_status wait_status_enqueue(lbm_ctx *c)
 {
-    if (c->d_sweep_err) {
-        int e = 0;
-        CK(cudaMemcpyAsync(&e, c->d_sweep_err, sizeof e, cudaMemcpyDeviceToHost, c->stream), "read wait status");
-        CK(cudaStreamSynchronize(c->stream), "read wait status");
-        if (e) {
-            CK(cudaMemsetAsync(c->d_sweep_err, 0, sizeof e, c->stream), "clear wait status");
-            CK(cudaStreamSynchronize(c->stream), "clear wait status");
-            if (e == 2) return fail(c, LBM_ERR_TIMEOUT, "the wait self-check gave up as designed; the state is untouched");
-            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the staged sweep gave up; the state is invalid");
-        }
+    c->h_io->wait_err[0] = c->h_io->wait_err[1] = 0;
+    if (c->d_sweep_err)
+        CK(cudaMemcpyAsync(&c->h_io->wait_err[0], c->d_sweep_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "read wait status");
+    if (c->d_tc_err && c->closure == CLOSURE_MLP)
+        CK(cudaMemcpyAsync(&c->h_io->wait_err[1], c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "read network status");
+    return LBM_OK;
+}
+
+lbm_status wait_status_take(lbm_ctx *c)
+{
+    const int e0 = c->h_io->wait_err[0], e1 = c->h_io->wait_err[1];
+    if (e0) {
+        CK(cudaMemsetAsync(c->d_sweep_err, 0, sizeof(int), c->stream), "clear wait status");
+        CK(cudaStreamSynchronize(c->stream), "clear wait status");
+        if (e0 == 2) return fail(c, LBM_ERR_TIMEOUT, "the wait self-check gave up as designed; the state is untouched");
+        return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the staged sweep gave up; the state is invalid");
     }
-    if (c->d_tc_err && c->closure == CLOSURE_MLP) {
-        int e = 0;
-        CK(cudaMemcpyAsync(&e, c->d_tc_err, sizeof e, cudaMemcpyDeviceToHost, c->stream), "read network status");
-        CK(cudaStreamSynchronize(c->stream), "read network status");
-        if (e) {
-            CK(cudaMemsetAsync(c->d_tc_err, 0, sizeof e, c->stream), "clear network status");
-            CK(cudaStreamSynchronize(c->stream), "clear network status");
-            return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the tensor-core network gave up; the state is invalid");
-        }
+    if (e1) {
+        CK(cudaMemsetAsync(c->d_tc_err, 0, sizeof(int), c->stream), "clear network status");
+        CK(cudaStreamSynchronize(c->stream), "clear network status");
+        return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the tensor-core network gave up; the state is invalid");
     }
     return LBM_OK;
+}
+
+// Both steps around a synchronisation of their own (calls that read other results first).
+lbm_status wait_status(lbm_ctx *c)
+{
+    lbm_status s = wait_status_enqueue(c);
+    if (s != LBM_OK) return s;
+    CK(cudaStreamSynchronize(c->stream), "read wait status");
+    return wait_status_take(c);
 }
 
 }  // namespace
@@ -1165,16 +1185,18 @@ lbm_status lbm_selfcheck_wait(lbm_ctx *c, int32_t polls)
 lbm_status lbm_step_diagnostics(lbm_ctx *c, lbm_diagnostics *out)
 {
     if (!c || !out) return LBM_ERR_ARG;
-    if (!c->step_diag_valid) return fail(c, LBM_ERR_STATE, "no step has run since the state was last set");
-    double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (!c->step_diag_valid || !c->h_io) return fail(c, LBM_ERR_STATE, "no step has run since the state was last set");
+    double *h = c->h_io->diag;
+    std::fill(h, h + 8, 0.0);
     if (!c->plan.tiles.empty()) {
         CK(launch_reduce_final(c->d_step_partials, (int64_t)c->plan.tiles.size(), c->d_out, c->stream),
            "diagnostics kernel");
-        CK(cudaMemcpyAsync(h, c->d_out, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
-        CK(cudaStreamSynchronize(c->stream), "step diagnostics");
+        CK(cudaMemcpyAsync(h, c->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
     }
-    const lbm_status ws = wait_status(c);
+    lbm_status ws = wait_status_enqueue(c);
     if (ws != LBM_OK) return ws;
+    CK(cudaStreamSynchronize(c->stream), "step diagnostics");  // one synchronisation for both reads
+    if ((ws = wait_status_take(c)) != LBM_OK) return ws;
     out->mass = h[0];
     out->momentum[0] = h[1];
     out->momentum[1] = h[2];
@@ -1382,6 +1404,7 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_mlp);
     dfree(c->d_tc_err);
     dfree(c->d_sweep_err);
+    if (c->h_io) cudaFreeHost(c->h_io);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     drop_graphs(c);
     delete c;
