@@ -67,6 +67,10 @@ __device__ __forceinline__ float tanh_approx(float x)
 }
 
 __device__ __forceinline__ float softplus(float y) { return y > 30.0f ? y : log1pf(expf(y)); }
+// The sweep's softplus from the fast exponential and logarithm: its error (a few 1e-7 of the
+// value, at most 2^-24 absolute where exp(y) vanishes next to 1) is far below the network's
+// own (tanh.approx.f32, BF16 operands) and reaches tau scaled by s_tau.
+__device__ __forceinline__ float softplus_fast(float y) { return y > 30.0f ? y : __logf(1.0f + __expf(y)); }
 
 // SiLU of two units from their halved pre-activations h0, h1, packed as BF16 (lo = h0).
 __device__ __forceinline__ uint32_t silu_pair(float h0, float h1)
@@ -93,48 +97,66 @@ __device__ float warp_mlp(const MlpDev &P, const float (&feat)[kIn], uint32_t *x
     const uint32_t *w1 = reinterpret_cast<const uint32_t *>(P.w1);  // [32][16] bf16 = [32][8] words
     const uint32_t *w2 = reinterpret_cast<const uint32_t *>(P.w2);  // [32][32] bf16 = [32][16] words
     const uint32_t *w3 = reinterpret_cast<const uint32_t *>(P.w3);  // [8][32] bf16 = [8][16] words
+    // Both 16-row tiles (mt) go through each hidden-unit tile (nt) together, so every weight
+    // fragment and bias is loaded from shared memory once per warp and z step.
+    uint32_t a[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+        a[mt][0] = xs[(mt * 16 + g) * 8 + t];
+        a[mt][1] = xs[(mt * 16 + g + 8) * 8 + t];
+        a[mt][2] = xs[(mt * 16 + g) * 8 + t + 4];
+        a[mt][3] = xs[(mt * 16 + g + 8) * 8 + t + 4];
+    }
+    // layer 1: 4 tiles of 8 hidden units; tile nt is half (nt & 1) of k-step nt / 2 of the next
+    // layer's A fragment (registers 0/1 or 2/3)
+    uint32_t h1[2][2][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        const float b0 = P.b1[c], b1 = P.b1[c + 1];
+        const uint32_t wa = w1[(nt * 8 + g) * 8 + t], wb = w1[(nt * 8 + g) * 8 + t + 4];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            float d[4] = {b0, b1, b0, b1};  // bias as the initial accumulator
+            mma_bf16(d, a[mt], wa, wb);
+            h1[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_pair(d[0], d[1]);
+            h1[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_pair(d[2], d[3]);
+        }
+    }
+    // layer 2
+    uint32_t h2[2][2][4];
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+        const int c = nt * 8 + 2 * t;
+        const float b0 = P.b2[c], b1 = P.b2[c + 1];
+        uint32_t wk[2][2];
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            wk[ks][0] = w2[(nt * 8 + g) * 16 + ks * 8 + t];
+            wk[ks][1] = w2[(nt * 8 + g) * 16 + ks * 8 + t + 4];
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+            float d[4] = {b0, b1, b0, b1};
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) mma_bf16(d, h1[mt][ks], wk[ks][0], wk[ks][1]);
+            h2[mt][nt >> 1][(nt & 1) * 2 + 0] = silu_pair(d[0], d[1]);
+            h2[mt][nt >> 1][(nt & 1) * 2 + 1] = silu_pair(d[2], d[3]);
+        }
+    }
+    // layer 3: w3 as column 0 of an 8-column B
+    uint32_t w3k[2][2];
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+        w3k[ks][0] = w3[g * 16 + ks * 8 + t];
+        w3k[ks][1] = w3[g * 16 + ks * 8 + t + 4];
+    }
     float y = 0.f;
 #pragma unroll
     for (int mt = 0; mt < 2; ++mt) {
-        uint32_t a[4];
-        a[0] = xs[(mt * 16 + g) * 8 + t];
-        a[1] = xs[(mt * 16 + g + 8) * 8 + t];
-        a[2] = xs[(mt * 16 + g) * 8 + t + 4];
-        a[3] = xs[(mt * 16 + g + 8) * 8 + t + 4];
-        // layer 1: 4 tiles of 8 hidden units
-        uint32_t h1[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int c = nt * 8 + 2 * t;
-            float d[4] = {P.b1[c], P.b1[c + 1], P.b1[c], P.b1[c + 1]};  // bias as the initial accumulator
-            mma_bf16(d, a, w1[(nt * 8 + g) * 8 + t], w1[(nt * 8 + g) * 8 + t + 4]);
-            const uint32_t lo = silu_pair(d[0], d[1]);
-            const uint32_t hi = silu_pair(d[2], d[3]);
-            // tile nt is half (nt & 1) of k-step nt / 2: registers 0/1 or 2/3 of that A fragment
-            h1[nt >> 1][(nt & 1) * 2 + 0] = lo;
-            h1[nt >> 1][(nt & 1) * 2 + 1] = hi;
-        }
-        // layer 2
-        uint32_t h2[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const int c = nt * 8 + 2 * t;
-            float d[4] = {P.b2[c], P.b2[c + 1], P.b2[c], P.b2[c + 1]};
-#pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint32_t af[4] = {h1[ks][0], h1[ks][1], h1[ks][2], h1[ks][3]};
-                mma_bf16(d, af, w2[(nt * 8 + g) * 16 + ks * 8 + t], w2[(nt * 8 + g) * 16 + ks * 8 + t + 4]);
-            }
-            h2[nt >> 1][(nt & 1) * 2 + 0] = silu_pair(d[0], d[1]);
-            h2[nt >> 1][(nt & 1) * 2 + 1] = silu_pair(d[2], d[3]);
-        }
-        // layer 3: w3 as column 0 of an 8-column B
         float d[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int ks = 0; ks < 2; ++ks) {
-            const uint32_t af[4] = {h2[ks][0], h2[ks][1], h2[ks][2], h2[ks][3]};
-            mma_bf16(d, af, w3[g * 16 + ks * 8 + t], w3[g * 16 + ks * 8 + t + 4]);
-        }
+        for (int ks = 0; ks < 2; ++ks) mma_bf16(d, h2[mt][ks], w3k[ks][0], w3k[ks][1]);
         // column 0 sits in lanes with t == 0: d[0] for row g, d[2] for row g + 8
         const int r = (lane - mt * 16) & 15;
         const float ylo = __shfl_sync(0xffffffffu, d[0], 4 * (r & 7));
@@ -379,9 +401,9 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
             if (!live)
                 for (int kk = 0; kk < kIn; ++kk) feat[kk] = 0.f;
 #if LBM_MLP_TC_SWEEP
-            tau = ca.tau0 + P.s_tau * softplus(tc_mlp_256(S, P.b3, feat, tmem, tc_ok));
+            tau = ca.tau0 + P.s_tau * softplus_fast(tc_mlp_256(S, P.b3, feat, tmem, tc_ok));
 #else
-            tau = ca.tau0 + P.s_tau * softplus(warp_mlp(P, feat, wx));
+            tau = ca.tau0 + P.s_tau * softplus_fast(warp_mlp(P, feat, wx));
 #endif
         }
         if (live) {
