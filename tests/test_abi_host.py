@@ -431,3 +431,41 @@ def test_closure_rejects_unsupported_contexts_and_bad_arguments():
         lbm.lbm_set_closure(c, lbm.CLOSURE_NONE)
     finally:
         lbm.lbm_destroy(c)
+
+
+def test_staged_tile_selection_on_the_host():
+    """Which sweep tiles stage their source rows in shared memory (lbm_info.staged_tiles, decided
+    on the host when the lists are built): 16-bit storage, two-grid, tiles spanning the block's
+    full width in at most two rows, no masks, in-place neighbours only the block itself; the
+    16-bit two-grid default tile depth is 8."""
+    def info(storage, pattern, blocks, periodic, in_place=True, tile=None):
+        p = lbm.make_params(stencil=19, collision=lbm.TRT, storage=storage, pattern=pattern, omega=1.2,
+                            periodic=periodic)
+        c = lbm.lbm_create_blocks(p, blocks)
+        try:
+            if not in_place:
+                lbm.lbm_set_in_place(c, False)
+            if tile:
+                lbm.lbm_set_tile(c, *tile)
+            return lbm.lbm_get_info(c)
+        finally:
+            lbm.lbm_destroy(c)
+
+    one = [((0, 0, 0), (256, 12, 9))]
+    for st in (lbm.BF16_DEV, lbm.FP16_DEV):
+        i = info(st, lbm.TWO_GRID, one, (1, 1, 1))
+        assert i["tiles"] == 12 * 2 and i["staged_tiles"] == i["tiles"]  # 12 rows x 2 z-tiles of depth 8
+        assert info(st, lbm.AA, one, (1, 1, 1))["staged_tiles"] == 0
+    for st in (lbm.FP64, lbm.FP32):
+        i = info(st, lbm.TWO_GRID, one, (1, 1, 1))
+        assert i["tiles"] == 12 * 3 and i["staged_tiles"] == 0  # depth 4
+    # walls in y: the rows next to them carry masks (2 rows x 2 z-tiles)
+    assert info(lbm.FP16_DEV, lbm.TWO_GRID, one, (1, 0, 1))["staged_tiles"] == 24 - 4
+    # a block narrower than half the CTA (several rows per tile) and tiles narrower than the block
+    assert info(lbm.FP16_DEV, lbm.TWO_GRID, [((0, 0, 0), (64, 12, 9))], (1, 1, 1))["staged_tiles"] == 0
+    assert info(lbm.FP16_DEV, lbm.TWO_GRID, one, (1, 1, 1), tile=(128, 2, 4))["staged_tiles"] == 0
+    # two blocks side by side: in place each reads the other (not staged); with ghost copies the
+    # unmasked row pairs are (5 row pairs x 2 z-tiles per block, 2 of them next to a wall)
+    two = [((0, 0, 0), (128, 10, 9)), ((128, 0, 0), (128, 10, 9))]
+    assert info(lbm.FP16_DEV, lbm.TWO_GRID, two, (1, 0, 1))["staged_tiles"] == 0
+    assert info(lbm.FP16_DEV, lbm.TWO_GRID, two, (1, 0, 1), in_place=False)["staged_tiles"] == 2 * (10 - 4)
