@@ -509,6 +509,87 @@ def run_porous(args):
         print(json.dumps(out), flush=True)
 
 
+def run_tgv(args):
+    """C1, the correctness configuration: 2-D Taylor-Green vortex extruded in z on a 32^3 fully
+    periodic box, D3Q19 SRT tau = 0.6, FP64, u0 = 0.01.  The state (two 4.7 MB arrays) lives in
+    L2, so the step rate is reported without a roofline fraction.  With the tile picked by
+    lbm_autotune, times K steps for both patterns, launched plainly and as CUDA-graph replays of
+    step pairs; fits the vortex's decay
+    rate over the timed steps (after a 20-step start-up transient) against 2 nu k^2; times the
+    oracle on the full configuration (100 steps) on the host cores."""
+    import math
+    import torch
+    rank, world, local = dist_setup()
+    from paper_1909_13772_gb300 import inputs, lbm
+    lbm.load_library()
+    n, tau, u0 = 32, 0.6, 0.01
+    shape = (n, n, n)
+    cells = n ** 3
+    rho, u = inputs.taylor_green(n, u0=u0)
+    k = 2.0 * math.pi / n
+    nu = (tau - 0.5) / 3.0
+    X, Y = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    mode = np.cos(k * X) * np.sin(k * Y)
+
+    def amplitude(v):
+        return float((v[0] * mode[None]).sum() / (mode * mode).sum() / n)
+
+    runs = {}
+    for pattern in ("TWO_GRID", "AA"):
+        for graph in (False, True):
+            p = lbm.make_params(stencil=lbm.D3Q19, collision=lbm.SRT, storage=lbm.FP64,
+                                pattern=getattr(lbm, pattern), omega=1.0 / tau, periodic=(1, 1, 1))
+            stream = torch.cuda.Stream()
+            sim = lbm.Simulation(p, [((0, 0, 0), shape)], stream=stream.cuda_stream)
+            sim.init(0, rho, u)
+            tuned = lbm.lbm_autotune(sim.ctx, 10)  # restores the state; picks tile and neighbour mode
+            if graph:
+                lbm.lbm_set_graph(sim.ctx, True)
+            sim.step(max(20, args.warmup))
+            torch.cuda.synchronize()
+            a0 = amplitude(sim.macroscopic(0)[1])
+            barrier(world)
+            launches0 = sim.launches()
+            sampler = ClockSampler(torch.cuda.current_device())
+            start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            sim.step(args.steps)
+            end.record(stream)
+            torch.cuda.synchronize()
+            clocks = sampler.stop()
+            ms = start.elapsed_time(end)
+            launches = sim.launches() - launches0
+            a1 = amplitude(sim.macroscopic(0)[1])
+            sim.close()
+            lups, tmax = aggregate(cells * args.steps, ms / 1e3, world)
+            runs["%s%s" % (pattern.lower().replace("_", ""), "-graph" if graph else "")] = {
+                "mlups": round(lups / 1e6, 1), "ms_per_step": round(tmax * 1e3 / args.steps, 5),
+                "decay_rate_vs_2nuk2": round(-math.log(a1 / a0) / args.steps / (2 * nu * k * k), 5),
+                "launches": launches, "autotuned_tile": list(tuned[0]), "autotuned_in_place": tuned[2],
+                "clocks": clocks}
+    best = max(runs, key=lambda r: runs[r]["mlups"])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        op = oracle.OracleParams(shape=shape, q=19, collision=oracle.SRT, omega=1.0 / tau)
+        f = oracle.init(op, rho, u)
+        t0 = time.perf_counter()
+        oracle.run(op, f, 100)
+        t = time.perf_counter() - t0
+        cpu = {"value": round(cells * 100 / t / 1e6, 3), "unit": "MLUPS", "cores": oracle.get_threads(),
+               "kind": "oracle", "sample": "the full configuration: 100 oracle steps of the 32^3 vortex (FP64)"}
+    out = {"metric": "MLUPS of the Taylor-Green correctness configuration (L2-resident: no roofline fraction)",
+           "value": runs[best]["mlups"], "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+           "warmup": max(20, args.warmup), "ms_per_step": runs[best]["ms_per_step"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic vortex)",
+           "config": {"workload": "2-D Taylor-Green vortex extruded in z, 32^3 periodic, D3Q19 SRT tau=0.6, "
+                                  "u0=0.01, FP64", "value_from": best},
+           "roofline": None, "cpu_baseline": cpu, "gpu_launches": runs[best]["launches"],
+           "clocks": runs[best]["clocks"], "variants": runs}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def _spectrum(u):
     """Shell-averaged kinetic-energy spectrum E(k), k = 1..n/2, of a periodic u[3, z, y, x]."""
     n = u.shape[-1]
@@ -743,8 +824,9 @@ def main(argv=None):
                     help="porous: pick the sweep tile and the neighbour mode with lbm_autotune")
     ap.add_argument("--per-block", action="store_true", help="porous: one sweep launch per block (comparison)")
     ap.add_argument("--ghost", action="store_true", help="porous: ghost-layer copies instead of in-place neighbours")
-    ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure"], default="channel",
+    ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure", "tgv"], default="channel",
                     help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed; "
+                         "tgv: the 32^3 Taylor-Green correctness configuration; "
                          "turbulence: D3Q27 decaying turbulence, storage variants and their errors; "
                          "closure: constant rate vs Smagorinsky vs the learned closure")
     ap.add_argument("--porous-blocks", type=int, default=16, help="porous: blocks per axis (16: 4096 blocks)")
@@ -764,6 +846,8 @@ def main(argv=None):
         run_turbulence(args)
     elif args.workload == "closure":
         run_closure(args)
+    elif args.workload == "tgv":
+        run_tgv(args)
     else:
         run_ours(args)
 

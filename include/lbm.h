@@ -236,7 +236,8 @@ lbm_status lbm_set_batching(lbm_ctx *ctx, int32_t batched);
 lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t enable);
 
 /* Autotuner: times trial_steps steps for each candidate sweep tile shape (a fixed list from
- * 256x1x2 to 32x8x4) and each neighbour mode (lbm_set_in_place; the other mode is tried only
+ * 256x1x16 to 32x4x1, including shapes with few cells per CTA for small blocks) and each
+ * neighbour mode (lbm_set_in_place; the other mode is tried only
  * where it may be switched: two-grid, or AA after an even number of steps), every trial from
  * the same state; keeps the fastest (best[3], *best_in_place and the time per step in
  * *best_ms, each pointer may be NULL but best) and restores the simulation state exactly (the

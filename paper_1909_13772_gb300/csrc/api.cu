@@ -931,8 +931,10 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], int32_
     const int old[3] = {c->tile[0], c->tile[1], c->tile[2]}, old_in_place = c->in_place;
     // the neighbour mode may change only where both forms of the state agree (see lbm_set_in_place)
     const bool try_modes = c->pattern == LBM_TWO_GRID || lay == LAYOUT_AA_E;
+    // the last three give small blocks (a 32^3 box: 32 tiles of 256 x 1 x 4) enough CTAs
     static const int cand[][3] = {{256, 1, 4}, {256, 1, 2}, {256, 1, 8}, {256, 1, 16}, {128, 2, 4}, {128, 2, 8},
-                                  {64, 4, 4},  {64, 4, 8},  {32, 8, 4},  {128, 1, 8},  {64, 2, 8}, {64, 1, 16}};
+                                  {64, 4, 4},  {64, 4, 8},  {32, 8, 4},  {128, 1, 8},  {64, 2, 8}, {64, 1, 16},
+                                  {256, 1, 1}, {64, 2, 2},  {32, 4, 1}};
     const int ncand = (int)(sizeof cand / sizeof cand[0]);
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0), "event");
