@@ -121,24 +121,29 @@ typedef struct {
 /* Create a context for `nblocks` blocks.  `cuda_stream` is a cudaStream_t (or NULL for the
  * default stream) on which all work of the context is issued.  Uses the current CUDA
  * device.  No device memory is allocated yet (see lbm_bind_device_memory).
- * Errors: LBM_ERR_ARG for invalid parameters or overlapping blocks. */
+ * Errors: LBM_ERR_ARG for invalid parameters or overlapping blocks.
+ * Paper: Sec. 4.1 (the domain as a set of blocks of cells), Sec. 4.2 (per-block fields, SoA, one
+ * ghost layer, padded rows). */
 lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks,
                              void *cuda_stream, lbm_ctx **out);
 
 /* Bytes of device memory the PDF arrays need (two arrays for two-grid, one for AA),
- * including 256-byte alignment slack. */
+ * including 256-byte alignment slack.
+ * Paper: Sec. 4.2 (field memory layout); the caller-owned buffer has no counterpart there. */
 size_t lbm_required_bytes(const lbm_ctx *ctx);
 
 /* Optional: place the PDF arrays in caller-owned device memory `dev_ptr` of `bytes` bytes
  * (at least lbm_required_bytes).  Must be called before any call that touches PDFs.  The
  * caller keeps the buffer alive until lbm_destroy.  Without it the library cudaMallocs.
  * Boundary lists, masks and reduction scratch are always allocated by the library.
- * Errors: LBM_ERR_OOM if too small, LBM_ERR_STATE if the arrays already exist. */
+ * Errors: LBM_ERR_OOM if too small, LBM_ERR_STATE if the arrays already exist.
+ * Paper: Sec. 4.2 (field memory layout); the caller-owned buffer has no counterpart there. */
 lbm_status lbm_bind_device_memory(lbm_ctx *ctx, void *dev_ptr, size_t bytes);
 
 /* Kind of the region outside a domain face (axis 0..2, side 0 = low, 1 = high):
  * LBM_NOSLIP, LBM_VELOCITY (wall velocity u_wall, density rho_wall) or LBM_PRESSURE
- * (density rho_wall).  Faces of periodic axes are ignored.  Default: LBM_NOSLIP. */
+ * (density rho_wall).  Faces of periodic axes are ignored.  Default: LBM_NOSLIP.
+ * Paper: Sec. 5.1.1 (no-slip, velocity and pressure boundary kinds), Sec. 4.1 (periodic domain). */
 lbm_status lbm_set_face(lbm_ctx *ctx, int32_t axis, int32_t side, int32_t kind, const double u_wall[3],
                         double rho_wall);
 
@@ -146,7 +151,8 @@ lbm_status lbm_set_face(lbm_ctx *ctx, int32_t axis, int32_t side, int32_t kind, 
  * LBM_PRESSURE).  Velocity and pressure cells of this block use (u_wall, rho_wall).  NULL
  * flags = all fluid.  Boundary link lists and ghost-copy lists are (re)built on the host
  * before the next step.  Set flags before lbm_init_macroscopic: a cell that becomes fluid
- * later has no valid PDFs. */
+ * later has no valid PDFs.
+ * Paper: Sec. 4.4 (cell flags turned into one index list per boundary kind). */
 lbm_status lbm_set_boundary(lbm_ctx *ctx, int32_t block, const uint8_t *flags, const double u_wall[3],
                             double rho_wall);
 
@@ -154,37 +160,47 @@ lbm_status lbm_set_boundary(lbm_ctx *ctx, int32_t block, const uint8_t *flags, c
  * populations are the equilibrium at (rho, u - F/(2 rho)), so the half-force-corrected
  * velocity equals u; the stored state is their post-collision image, written in the
  * context's current storage layout (two-grid source array or the current AA parity).
- * Non-fluid cells are left untouched. */
+ * Non-fluid cells are left untouched.
+ * Paper: Eq. 1 (moments of the equilibrium populations), Sec. 4.3 (set-up on the host, copied to
+ * the GPU field). */
 lbm_status lbm_init_macroscopic(lbm_ctx *ctx, int32_t block, const double *rho, const double *u);
 
 /* Advance all blocks by n time steps (asynchronous on the context's stream).  Each step:
  * ghost-layer copy and boundary links, then the fused stream-collide sweep.  With
  * diag_interval > 0 the host reads the step diagnostics (lbm_step_diagnostics) every
- * diag_interval steps and returns LBM_ERR_DIVERGED when a value is non-finite. */
+ * diag_interval steps and returns LBM_ERR_DIVERGED when a value is non-finite.
+ * Paper: Eq. 2 (stream and collide), Sec. 5.1.2 (one fused kernel), Sec. 4.4 (boundary sweeps),
+ * Sec. 3.3 and 4.2 (ghost layers exchanged between sweeps). */
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
 
 /* Density rho[N] and velocity u[3N] of one block's stored state (host FP64 buffers).
- * Non-fluid cells give 0.  Synchronises the stream. */
+ * Non-fluid cells give 0.  Synchronises the stream.
+ * Paper: Eq. 1 (density and velocity moments), Sec. 4.3 (output through the host mirror). */
 lbm_status lbm_get_macroscopic(lbm_ctx *ctx, int32_t block, double *rho, double *u);
 
 /* Canonical post-collision PDFs f[Q*N] of one block (host FP64), whatever the pattern and
- * AA parity.  Non-fluid cells give 0.  Synchronises the stream. */
+ * AA parity.  Non-fluid cells give 0.  Synchronises the stream.
+ * Paper: Sec. 4.3 (the GPU field mirrored on the host). */
 lbm_status lbm_get_pdfs(lbm_ctx *ctx, int32_t block, double *f);
 
 /* PDFs of a box of a block's interior cells: origin[3] and size[3] in the block's interior
  * coordinates (inside the block), f[i * N + n] with n = x + sx (y + sy z) relative to the box,
  * N = sx sy sz, canonical direction order, FP64 (non-fluid cells read 0).  Synchronises the
- * stream.  Errors: LBM_ERR_ARG (null pointer, box outside the block). */
+ * stream.  Errors: LBM_ERR_ARG (null pointer, box outside the block).
+ * Paper: Sec. 4.3 (the GPU field mirrored on the host, here a box of it). */
 lbm_status lbm_get_pdfs_region(lbm_ctx *ctx, int32_t block, const int32_t origin[3], const int32_t size[3],
                                double *f);
 
 /* Overwrite one block's state with canonical post-collision PDFs f[Q*N] (host FP64),
  * converted to the storage format.  Checkpoint restart: get_pdfs of every block, then
- * set_pdfs of every block continues the run exactly.  Synchronises the stream. */
+ * set_pdfs of every block continues the run exactly.  Synchronises the stream.
+ * Paper: Sec. 4.3 (host mirror copied to the GPU field). */
 lbm_status lbm_set_pdfs(lbm_ctx *ctx, int32_t block, const double *f);
 
 /* Domain totals of the stored state over all fluid cells (FP64, deterministic: fixed
- * per-CTA partial sums reduced in a fixed order).  Synchronises the stream. */
+ * per-CTA partial sums reduced in a fixed order).  Synchronises the stream.
+ * Paper: Eq. 1 (moments), summed over the domain; the reduction itself has no counterpart in the
+ * paper. */
 lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
 
 /* Diagnostics of the state produced by the most recent lbm_step, computed inside that
@@ -192,7 +208,9 @@ lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
  * and per-warp sums in the sweep's arithmetic type (FP32 for FP32 and 16-bit storage, FP64 for
  * FP64), FP64 across warps and tiles, fixed order.  Cheap enough to read after every step;
  * lbm_reduce is the full-FP64 pass over the stored values.  Synchronises the stream.
- * Errors: LBM_ERR_STATE when the state was set (init, set_pdfs) after the last step. */
+ * Errors: LBM_ERR_STATE when the state was set (init, set_pdfs) after the last step.
+ * Paper: Eq. 1 (moments), summed over the domain inside the Sec. 5.1.2 sweep; no counterpart in
+ * the paper. */
 lbm_status lbm_step_diagnostics(lbm_ctx *ctx, lbm_diagnostics *out);
 
 /* Bounded device-side waits.  The kernels that wait on an mbarrier (the staged sweep for the
@@ -203,36 +221,42 @@ lbm_status lbm_step_diagnostics(lbm_ctx *ctx, lbm_diagnostics *out);
  * LBM_ERR_TIMEOUT once and clears the flag; the context stays usable.
  * lbm_selfcheck_wait exercises that path: one device thread waits at most `polls` polls
  * (1 <= polls <= 2^20) on an mbarrier nothing arrives on, gives up and sets the flag; the
- * state is not touched.  Synchronises the stream.  Errors: LBM_ERR_ARG (polls out of range). */
+ * state is not touched.  Synchronises the stream.  Errors: LBM_ERR_ARG (polls out of range).
+ * Paper: none (failure path of this library's bounded device waits). */
 lbm_status lbm_selfcheck_wait(lbm_ctx *ctx, int32_t polls);
 
-/* Work sizes of one step (builds the boundary lists if needed). */
+/* Work sizes of one step (builds the boundary lists if needed).
+ * Paper: Sec. 4.4 (sizes of the boundary lists); the other sizes have no counterpart. */
 lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *out);
 
 /* Sweep tile shape (cells per CTA along x, y, z; threads = tx * ty).  tx must be a
  * multiple of 32, tx*ty <= 256.  A block narrower than tx gets tiles of its width rounded
  * up to 32 and proportionally more rows.  Takes effect at the next list build.
- * Default 256 x 1 x 4 (256 x 1 x 8 for the two-grid pattern with 16-bit storage). */
+ * Default 256 x 1 x 4 (256 x 1 x 8 for the two-grid pattern with 16-bit storage).
+ * Paper: none (execution shape of the Sec. 5.1.2 sweep on the GPU). */
 lbm_status lbm_set_tile(lbm_ctx *ctx, int32_t tx, int32_t ty, int32_t tz);
 
 /* Per-kernel device timing of lbm_step (tracing): when enabled, lbm_step records CUDA events
  * around its fill and sweep launches on the context's stream.  lbm_read_timing synchronises
  * the stream and returns, since the last reset, the summed device milliseconds and launch
  * counts of the two kernels: ms[0]/count[0] = boundary-and-ghost fill, ms[1]/count[1] =
- * stream-collide sweep.  enable = 0 stops recording; lbm_read_timing(ctx, ..., 1) resets. */
+ * stream-collide sweep.  enable = 0 stops recording; lbm_read_timing(ctx, ..., 1) resets.
+ * Paper: none (tracing of the Sec. 5.1.2 sweep and the boundary/ghost kernel). */
 lbm_status lbm_enable_timing(lbm_ctx *ctx, int32_t enable);
 lbm_status lbm_read_timing(lbm_ctx *ctx, double ms[2], int64_t count[2], int32_t reset);
 
 /* batched = 1 (default): one sweep launch per step covers the tiles of every block.
  * batched = 0: one sweep launch per block, as a per-block sweep would be issued; results are
- * bitwise the same (kept to measure what batching gains). */
+ * bitwise the same (kept to measure what batching gains).
+ * Paper: none (launch structure of the Sec. 5.1.2 sweep over all blocks). */
 lbm_status lbm_set_batching(lbm_ctx *ctx, int32_t batched);
 
 /* Graph mode: lbm_step replays pairs of steps as one captured CUDA graph (one graph per
  * starting parity, re-captured after the lists change); the last step of each call and the
  * diag_interval steps run as ordinary launches.  Needs a context created with a non-default
  * stream.  Per-kernel tracing (lbm_enable_timing) bypasses the graphs.  Errors:
- * LBM_ERR_UNSUPPORTED on the default stream. */
+ * LBM_ERR_UNSUPPORTED on the default stream.
+ * Paper: none (launch structure of the Sec. 5.1.2 sweep). */
 lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t enable);
 
 /* Autotuner: times trial_steps steps for each candidate sweep tile shape (a fixed list from
@@ -242,15 +266,18 @@ lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t enable);
  * the same state; keeps the fastest (best[3], *best_in_place and the time per step in
  * *best_ms, each pointer may be NULL but best) and restores the simulation state exactly (the
  * PDF arrays are snapshot to a temporary device buffer, which is cudaMalloc'd).  The step
- * count and parity are unchanged; diag_interval checks are off during the trials. */
+ * count and parity are unchanged; diag_interval checks are off during the trials.
+ * Paper: none (execution shape of the Sec. 5.1.2 sweep and the Sec. 3.3 neighbour mode). */
 lbm_status lbm_autotune(lbm_ctx *ctx, int32_t trial_steps, int32_t best[3], int32_t *best_in_place,
                         double *best_ms);
 
-/* Number of kernels lbm_step launched since the context was created. */
+/* Number of kernels lbm_step launched since the context was created.
+ * Paper: none (launch count of the Sec. 5.1.2 step). */
 int64_t lbm_kernel_launches(const lbm_ctx *ctx);
 
 /* Canonical velocity set of a stencil (host only, no GPU needed): c[3*q] (cx, cy, cz per
- * direction), w[q], opp[q].  Returns LBM_ERR_ARG for an unknown q. */
+ * direction), w[q], opp[q].  Returns LBM_ERR_ARG for an unknown q.
+ * Paper: Sec. 5.1.1 (D3Q19 and D3Q27 stencils; order and weights as stated above). */
 lbm_status lbm_stencil_table(int32_t q, int32_t *c, double *w, int32_t *opp);
 
 /* Host-side view of the built lists, for inspection and tests (no GPU needed; builds the
@@ -258,7 +285,8 @@ lbm_status lbm_stencil_table(int32_t q, int32_t *c, double *w, int32_t *opp);
  * cell into the boundary), 5-6 kind, 7-9 reserved, 10-17 wall-parameter index, 18-31 block,
  * 32-63 cell index in the block's padded layout.  Runs of `pattern` (LBM_TWO_GRID or LBM_AA): five
  * int64 per run (src, dst, len, src stride, dst stride), offsets in elements from the base
- * of a PDF array.  With out == NULL only the count is returned in *n. */
+ * of a PDF array.  With out == NULL only the count is returned in *n.
+ * Paper: Sec. 4.4 (per-kind boundary index lists). */
 lbm_status lbm_plan_links(lbm_ctx *ctx, uint64_t *out, int64_t cap, int64_t *n);
 lbm_status lbm_plan_runs(lbm_ctx *ctx, int32_t pattern, int64_t *out, int64_t cap, int64_t *n);
 /* Padded layout of a block: out[0..7] = xo, pitch, plane, slab, offset (elements), and the
@@ -266,13 +294,15 @@ lbm_status lbm_plan_runs(lbm_ctx *ctx, int32_t pattern, int64_t *out, int64_t ca
  * (z+1) plane + (y+1) pitch + xo + x; direction i of it lives at offset + i slab + index.
  * out[8] = arena size in elements; out[9] = 1 when the block reads and writes its neighbour
  * cells in place (every region of its ghost shell is covered by exactly one block with a
- * matching face, or lies outside the domain), 0 when it keeps ghost copies. */
+ * matching face, or lies outside the domain), 0 when it keeps ghost copies.
+ * Paper: Sec. 4.2 (field layout with ghost layers and padded rows). */
 lbm_status lbm_plan_layout(lbm_ctx *ctx, int32_t block, int64_t out[10]);
 /* Neighbour table of a block: out[r], r = (rx+1) + 3 (ry+1) + 9 (rz+1) for the ghost-shell
  * region on side r_a in {-1, 0, 1} of each axis, is the block covering that region exactly
  * (the block itself across a periodic axis it spans alone), or -1 (outside the domain,
  * uncovered, or no exact match).  The cell of a neighbour read in place is the first (+) or
- * last (-) layer of that block along the crossed axes, the same coordinate along the others. */
+ * last (-) layer of that block along the crossed axes, the same coordinate along the others.
+ * Paper: Sec. 3.3 (blocks of one process exchanging ghost layers directly). */
 lbm_status lbm_plan_neighbors(lbm_ctx *ctx, int32_t block, int32_t out[27]);
 /* Cell masks of a block in its padded layout (uint32 per cell; *n = 0 when the block needs
  * none): bit 31 = the cell is not fluid; bit i = the pull source x - c_i of direction i is a
@@ -280,7 +310,8 @@ lbm_status lbm_plan_neighbors(lbm_ctx *ctx, int32_t block, int32_t out[27]);
  * no-slip needs no link list). */
 lbm_status lbm_plan_mask(lbm_ctx *ctx, int32_t block, uint32_t *out, int64_t cap, int64_t *n);
 
-/* Wall-parameter table of the built lists: (ux, uy, uz, rho) per index. */
+/* Wall-parameter table of the built lists: (ux, uy, uz, rho) per index.
+ * Paper: Sec. 5.1.1 (boundary parameters of the velocity and pressure kinds). */
 lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
 
 /* Allocation-free diagnostics of a caller-owned PDF field.  The paper has no counterpart:
@@ -326,8 +357,10 @@ enum { LBM_CLOSURE_NONE = 0, LBM_CLOSURE_SMAGORINSKY = 1, LBM_CLOSURE_MLP = 2 };
 
 /* Set the closure of a context.  cs: Smagorinsky constant (kind 1); mlp_params: host array of
  * LBM_MLP_NPARAM floats (kind 2), copied.  Supported for D3Q19, LBM_FP32 storage and zero
- * body force (any block set and boundary kinds); other contexts get LBM_ERR_UNSUPPORTED.  kind LBM_CLOSURE_NONE restores the constant
- * rate.  Errors: LBM_ERR_ARG (unknown kind, null params, cs < 0), LBM_ERR_UNSUPPORTED. */
+ * body force (any block set and boundary kinds); other contexts get LBM_ERR_UNSUPPORTED.
+ * kind LBM_CLOSURE_NONE restores the constant rate.  Errors: LBM_ERR_ARG (unknown kind, null
+ * params, cs < 0), LBM_ERR_UNSUPPORTED.
+ * Paper: Sec. 5.1.1 (per-cell relaxation rates for turbulence models). */
 lbm_status lbm_set_closure(lbm_ctx *ctx, int32_t kind, double cs, const float *mlp_params);
 
 /* The network alone: inference on the tensor cores and training in FP32 (loss
@@ -336,25 +369,33 @@ lbm_status lbm_set_closure(lbm_ctx *ctx, int32_t kind, double cs, const float *m
 typedef struct lbm_mlp lbm_mlp; /* opaque; owned by the library */
 
 /* Create a network from LBM_MLP_NPARAM packed parameters (host, copied) for batches of up
- * to max_batch samples, issuing work on cuda_stream.  Errors: LBM_ERR_ARG, LBM_ERR_OOM. */
+ * to max_batch samples, issuing work on cuda_stream.  Errors: LBM_ERR_ARG, LBM_ERR_OOM.
+ * Paper: Sec. 5.1.1 (per-cell relaxation rates for turbulence models); the network itself is not
+ * in the paper. */
 lbm_status lbm_mlp_create(const float *params, int64_t max_batch, void *cuda_stream, lbm_mlp **out);
 /* Replace / read the parameters (host arrays of LBM_MLP_NPARAM floats); set resets Adam; get
- * synchronises the stream and returns LBM_ERR_TIMEOUT once if an earlier inference gave up. */
+ * synchronises the stream and returns LBM_ERR_TIMEOUT once if an earlier inference gave up.
+ * Paper: Sec. 5.1.1 (per-cell relaxation rates for turbulence models); the network itself is not
+ * in the paper. */
 lbm_status lbm_mlp_set_params(lbm_mlp *m, const float *params);
 lbm_status lbm_mlp_get_params(lbm_mlp *m, float *params);
 /* y[s] for n samples (asynchronous on the stream), with the BF16 rounding points of the sweep,
  * on the fifth-generation tensor cores (tcgen05, 128-sample tiles, accumulators in tensor
  * memory).  A bounded wait inside that gives up is reported by the next lbm_mlp_get_params as
- * LBM_ERR_TIMEOUT. */
+ * LBM_ERR_TIMEOUT.
+ * Paper: Sec. 5.1.1 (per-cell relaxation rates for turbulence models); the network itself is not
+ * in the paper. */
 lbm_status lbm_mlp_infer(lbm_mlp *m, const float *X_dev, int64_t n, float *y_dev);
 /* Loss and gradient (FP32 arithmetic, deterministic summation order) of n <= max_batch
  * samples; loss_host (1 double) and grad_host (LBM_MLP_NPARAM floats, zero for the three
- * scales) may each be NULL.  Synchronises the stream when either is given. */
+ * scales) may each be NULL.  Synchronises the stream when either is given.
+ * Paper: none (training of the closure network). */
 lbm_status lbm_mlp_loss_grad(lbm_mlp *m, const float *X_dev, const float *T_dev, int64_t n, double *loss_host,
                              float *grad_host);
 /* `iters` Adam steps (beta 0.9 / 0.999, eps 1e-8, learning rate lr; scales held fixed) on
  * consecutive batches of `batch` samples cycling through the n samples; loss_history
- * (iters doubles, host, may be NULL) receives each step's batch loss.  Synchronises. */
+ * (iters doubles, host, may be NULL) receives each step's batch loss.  Synchronises.
+ * Paper: none (training of the closure network). */
 lbm_status lbm_mlp_train(lbm_mlp *m, const float *X_dev, const float *T_dev, int64_t n, int64_t batch,
                          int64_t iters, float lr, double *loss_history);
 void lbm_mlp_destroy(lbm_mlp *m);
@@ -382,13 +423,16 @@ lbm_status lbm_reduce_blocks(lbm_ctx *ctx, double *out);
  * divisible by ratio), the sums over its fluid cells of rho, rho u_x, rho u_y, rho u_z and
  * rho u_a u_b (xx, yy, zz, xy, xz, yz), with rho and u as lbm_get_macroscopic gives them.
  * out: host array of 10 * Nc doubles, out[m * Nc + c], c = X + NX (Y + NY Z), NX = nx / ratio.
- * Synchronises the stream.  Errors: LBM_ERR_ARG (bad block, null out, ratio not dividing). */
+ * Synchronises the stream.  Errors: LBM_ERR_ARG (bad block, null out, ratio not dividing).
+ * Paper: none (box filter of the learned-closure study). */
 lbm_status lbm_coarse_moments(lbm_ctx *ctx, int32_t block, int32_t ratio, double *out);
 
-/* Last error message of the context (never NULL). */
+/* Last error message of the context (never NULL).
+ * Paper: none. */
 const char *lbm_last_error(const lbm_ctx *ctx);
 
-/* Free the context and all device memory it owns (not memory bound by the caller). */
+/* Free the context and all device memory it owns (not memory bound by the caller).
+ * Paper: Sec. 4.2 (the block fields are released with the context). */
 void lbm_destroy(lbm_ctx *ctx);
 
 #ifdef __cplusplus
