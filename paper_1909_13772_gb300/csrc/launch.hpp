@@ -13,7 +13,8 @@ enum SweepKind { SWEEP_PULL = 0, SWEEP_AA_LOCAL = 1, SWEEP_AA_NBR = 2 };
 enum FillMode { FILL_PULL = 0, FILL_AA_E = 1, FILL_AA_O = 2 };
 enum Layout { LAYOUT_PULL = 0, LAYOUT_AA_E = 1, LAYOUT_AA_O = 2 };
 
-// z steps of source rows a staged sweep tile keeps in flight (must match LBM_STAGES of sweep.cu)
+// Shared-memory buffers (one z step of source rows each) of a staged sweep tile; the sweep and
+// the host's shared-memory size both take it from here
 constexpr int kSweepStages = 2;
 
 struct SweepArgs {
