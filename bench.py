@@ -349,6 +349,52 @@ def cpu_baseline(min_seconds=10.0, max_steps=200):
             "sample": "%d oracle steps of a 256x256x8 slab of the channel (FP64, D3Q19 TRT, walls in y)" % steps}
 
 
+def _oracle_rate(p, rho, u, flags=None, min_seconds=10.0, max_steps=2000):
+    """Steps of the oracle as it stands from (rho, u), one at a time after one untimed step,
+    until min_seconds have passed or max_steps were run (at least one): (steps, seconds)."""
+    import oracle
+    kw = {} if flags is None else {"flags": flags}
+    f = oracle.run(p, oracle.init(p, rho, u, **kw), 1, **kw)
+    steps, t = 0, 0.0
+    while steps == 0 or (t < min_seconds and steps < max_steps):
+        t0 = time.perf_counter()
+        f = oracle.run(p, f, 1, **kw)
+        t += time.perf_counter() - t0
+        steps += 1
+    return steps, t
+
+
+def cpu_baseline_turbulence(min_seconds=10.0, n=64):
+    """The oracle on the n^3 member of the decaying-turbulence family (D3Q27 TRT tau = 0.52,
+    FP64; the size at which the oracle checks the family's FP64 reference run)."""
+    import oracle
+    from paper_1909_13772_gb300 import inputs
+    rho, u = inputs.turbulence(n, seed=1909, kmax=min(32, n // 2), umax=0.05)
+    p = oracle.OracleParams(shape=(n, n, n), q=27, collision=oracle.TRT, omega=1 / 0.52, magic_lambda=LAMBDA,
+                            periodic=(1, 1, 1))
+    steps, t = _oracle_rate(p, rho, u, min_seconds=min_seconds)
+    return {"value": round(n ** 3 * steps / t / 1e6, 3), "unit": "MLUPS", "cores": oracle.get_threads(),
+            "kind": "oracle", "sample": "%d oracle steps of the %d^3 member of the family (FP64, D3Q27 TRT)" % (steps, n)}
+
+
+def cpu_baseline_porous(min_seconds=10.0, nb=4):
+    """The oracle on the mini-bed: the porous-bed generator at nb^3 blocks (same seeds, spheres,
+    inlet/outlet, D3Q19 TRT tau = 0.8), as one flagged domain, FP64."""
+    import oracle
+    from paper_1909_13772_gb300 import inputs
+    _, shape, _ = inputs.rectilinear_blocks(nb=(nb, nb, nb), lo=16, hi=64, seed=4096)
+    flags = inputs.sphere_packing(shape, radius=8.0, porosity=0.40, seed=7)
+    p = oracle.OracleParams(shape=shape, q=19, collision=oracle.TRT, omega=1 / 0.8, magic_lambda=LAMBDA,
+                            periodic=(0, 1, 1), face_kind=(oracle.VELOCITY, oracle.PRESSURE, 1, 1, 1, 1),
+                            face_u=((0.02, 0.0, 0.0),) + ((0.0, 0.0, 0.0),) * 5, face_rho=(1.0,) * 6)
+    rho, u = inputs.rest(shape)
+    steps, t = _oracle_rate(p, rho, u, flags=flags, min_seconds=min_seconds)
+    fluid = int((flags == 0).sum())
+    return {"value": round(fluid * steps / t / 1e6, 3), "unit": "MFLUPS", "cores": oracle.get_threads(),
+            "kind": "oracle", "sample": "%d oracle steps of the %d^3-block mini-bed (%d x %d x %d cells, %d fluid; FP64)"
+                                        % (steps, nb, shape[0], shape[1], shape[2], fluid)}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_setup()
@@ -499,6 +545,7 @@ def run_porous(args):
                         "unit": "GB/s", "frac": round(alg / (sweep_ms / 1e3) / 1e9 / peak, 4), "traffic": None,
                         "kernel": "k_sweep (fluid cells only)", "sweep_ms": round(sweep_ms, 4),
                         "fill_ms": round(fill_ms, 4)},
+           "cpu_baseline": cpu_baseline_porous() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None,
            "clocks": clocks, "finite": diag["nonfinite"] == 0, "max_speed": diag["max_speed"],
            "graph": bool(args.graph), "autotuned_tile": list(tuned[0]) if tuned else None,
            "autotuned_in_place": tuned[2] if tuned else None,
@@ -678,7 +725,9 @@ def run_turbulence(args):
                                   "max|u| = 0.05, AA pattern", "throughput_size": n_perf,
                       "throughput_steps": perf_steps, "error_size": n, "error_steps": args.steps,
                       "generator_s": round(t_gen, 1)},
-           "throughput": perf, "error_vs_fp64": err}
+           "throughput": perf, "error_vs_fp64": err,
+           "cpu_baseline": cpu_baseline_turbulence() if (rank == 0 and world == 1 and not args.no_cpu_baseline)
+           else None}
     if rank == 0:
         print(json.dumps(out), flush=True)
 

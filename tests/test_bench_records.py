@@ -62,3 +62,13 @@ def test_committed_records_name_existing_variants():
             m = re.search(r"INSTR kernel=(\S+)", line)
             if m:
                 assert m.group(1).startswith("closure-"), (path, line)
+
+
+def test_oracle_baselines_of_the_other_workloads_run_bounded():
+    """The CPU-baseline legs of the turbulence and porous workloads (the oracle as it stands on
+    a bounded sample) at small sizes: at least one step, a positive rate, the keys the bench
+    reports."""
+    for r, unit in ((bench.cpu_baseline_turbulence(min_seconds=0.0, n=16), "MLUPS"),
+                    (bench.cpu_baseline_porous(min_seconds=0.0, nb=2), "MFLUPS")):
+        assert r["kind"] == "oracle" and r["unit"] == unit and r["value"] > 0 and r["cores"] >= 1
+        assert r["sample"].startswith("1 oracle steps")
