@@ -39,3 +39,17 @@ def test_device_work_without_a_gpu_is_an_error():
             lbm.lbm_step(ctx, 1)
     finally:
         lbm.lbm_destroy(ctx)
+
+
+def test_product_package_never_touches_the_oracle():
+    """The oracle is test infrastructure: no module or source of the package imports, loads or
+    names it (the tests, smoke() and the bench's CPU legs are the only users)."""
+    import re
+    pkg = os.path.join(ROOT, "paper_1909_13772_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for name in files:
+            if name.endswith((".py", ".cu", ".cuh", ".cpp", ".hpp", ".h")):
+                text = open(os.path.join(dirpath, name)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b|lbm_oracle|liboracle", text, re.M), name
