@@ -1,12 +1,12 @@
-"""The FP64 reference run of the decaying-turbulence family -- the run the FP32 and 16-bit
-storage errors of the turbulence workload are measured against -- parity-checked against the
-oracle over a long run: the 64^3 member (D3Q27 TRT, Lambda = 3/16, tau = 0.52, random-phase
-k^-5/3 start of inputs.turbulence with seed 1909, shells 1..32, max|u| = 0.05; fully periodic)
-after 2,000 steps, AA pattern as the bench launches it.  The oracle's values come from
-tests/golden/make_turbulence64.py (2 min of oracle time, so they are stored): 1,024 sampled
-PDFs, max |f| and the FP64 mass and momentum.  A relative 1e-14 perturbation of the start stays
-at ~1e-14 over the first 400 oracle steps (no chaotic growth at this Reynolds number), so the
-gate 1e-12 of max |f| tests the kernels, not the flow."""
+"""(Long runs sort last among the GPU tests.) The FP64 reference run of the decaying-turbulence
+family -- the run the FP32 and 16-bit storage errors of the turbulence workload are measured
+against -- parity-checked against the oracle over a long run: the 64^3 member (D3Q27 TRT, Lambda
+= 3/16, tau = 0.52, random-phase k^-5/3 start of inputs.turbulence with seed 1909, shells 1..32,
+max|u| = 0.05; fully periodic) after 2,000 steps, AA pattern as the bench launches it. The
+oracle's values come from tests/golden/make_turbulence64.py (2 min of oracle time, so they are
+stored): 1,024 sampled PDFs, max |f| and the FP64 mass and momentum. A relative 1e-14
+perturbation of the start stays at ~1e-14 over the first 400 oracle steps (no chaotic growth at
+this Reynolds number), so the gate 1e-12 of max |f| tests the kernels, not the flow."""
 import os
 
 import numpy as np
