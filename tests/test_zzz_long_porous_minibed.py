@@ -2,7 +2,7 @@
 over a long run: the porous-bed generator at 4^3 blocks (64 uneven blocks reading each other in
 place, spheres, velocity inlet and pressure outlet), D3Q19 TRT tau = 0.8, FP64, 1,000 steps from
 rest, both patterns, against the oracle's values stored by tests/golden/make_porous_minibed.py
-(13 min of oracle time): 1,024 sampled fluid PDFs (gate 1e-12 of max |f|) and the FP64 mass and
+(5 min of oracle time): 1,024 sampled fluid PDFs (gate 1e-12 of max |f|) and the FP64 mass and
 momentum of the fluid cells. Written when no GPU time was left: its first run is the next GPU
 test run."""
 import importlib.util
