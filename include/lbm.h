@@ -213,9 +213,11 @@ lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
  * the paper. */
 lbm_status lbm_step_diagnostics(lbm_ctx *ctx, lbm_diagnostics *out);
 
-/* Bounded device-side waits.  The kernels that wait on an mbarrier (the staged sweep for the
- * completion of its bulk copies, the tensor-core network for its MMAs) give up after a fixed
- * number of polls, set a device status flag and return; every call that synchronises the
+/* Bounded device-side waits.  The kernels that wait on an mbarrier give up, set a device
+ * status flag and return: the staged sweep after 1 s of the GPU's global timer per wait for its
+ * bulk copies (the give-up is taken by the whole CTA, which then issues no more copies, waits
+ * once more for the copies in flight and returns; later CTAs skip their tiles), the
+ * tensor-core network after a fixed number of polls for its MMAs.  Every call that synchronises the
  * stream and reads results (lbm_step_diagnostics, lbm_reduce, lbm_reduce_blocks,
  * lbm_get_macroscopic, lbm_get_pdfs, lbm_get_pdfs_region, lbm_coarse_moments) then returns
  * LBM_ERR_TIMEOUT once and clears the flag; the context stays usable.
@@ -330,7 +332,10 @@ lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
  * library holds until the process exits.  Fields with more than LBM_REDUCE_NOALLOC_MAX_CELLS
  * cells are rejected with LBM_ERR_UNSUPPORTED; BF16/FP16 storages too.  The first call on each
  * device looks up that array's device address (cudaGetSymbolAddress) with the device current;
- * make that first call before any stream capture.  All calls share the array: each call
+ * make that first call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset (or anything else that destroys and re-creates the device's
+ * primary context) it is stale, so do not call this function again in such a process.  All
+ * calls share the array: each call
  * writes every record it reads, so nothing needs clearing, but calls whose kernels overlap
  * on the GPU (different streams, no ordering between them) race on it.
  * Errors: LBM_ERR_ARG (null pointer, bad stencil, ncells <= 0), LBM_ERR_UNSUPPORTED (storage

@@ -2,8 +2,9 @@
 // scheduler.  Every step runs on the context's stream as two launches:
 //   two-grid:  fill(links + ghost runs into src) -> pull sweep src -> dst, swap
 //   AA:        fill(E) -> neighbour sweep  |  fill(O) -> local sweep   (alternating)
-// (Sec. 4.2: "a ghost layer exchange before or after the kernel call"; Sec. 4.4 boundary
-// lists handled by their own kernel; Sec. 5.1.2 fused stream-collide sweep.)
+// (Sec. 4.2: ghost layers of neighbouring blocks are brought up to date around each sweep;
+// Sec. 4.4: each boundary list is handled by its own kernel; Sec. 5.1.2: one fused
+// stream-collide sweep.)
 #include <cuda_runtime.h>
 
 #include <algorithm>

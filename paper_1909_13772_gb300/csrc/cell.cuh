@@ -259,11 +259,24 @@ __device__ __forceinline__ DevBlock block_geo(const DevBlock *Bp)
 }
 
 // ---- bulk-copy staging of source rows (two-grid pull sweep) ---------------------------------
-// Bounded wait for phase `parity` of an mbarrier; false when it gave up.
+// Limit of one bounded wait on a staging mbarrier, in nanoseconds of the global timer.  A bulk
+// copy of a few kilobytes lands in microseconds; a wait that reaches this limit is a fault.
+constexpr uint64_t kStageWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait for phase `parity` of an mbarrier: polls until the phase completes or
+// kStageWaitNs have passed since the first poll; false when it gave up.
 __device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity)
 {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
+    const uint64_t t0 = global_ns();
+    for (;;) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -271,8 +284,8 @@ __device__ __forceinline__ bool stage_wait(uint64_t *bar, uint32_t parity)
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
+        if (global_ns() - t0 > kStageWaitNs) return false;
     }
-    return false;
 }
 
 __device__ __forceinline__ void stage_init(uint64_t *bar, uint32_t count)

@@ -59,7 +59,12 @@ constexpr int kMinBDiag = LBM_SWEEP_MINB;
 // step frees a buffer: waiting warps are parked, where polling an "empty" mbarrier instead
 // costs issue slots this issue-bound sweep does not have).  A thread reads its populations
 // there (x - c_x, wrapped within the row when the block is its own x neighbour).  Wrapped y
-// and z rows are mapped when the copies are issued.  A wait that gives up sets *err.
+// and z rows are mapped when the copies are issued.
+// Failure path: a wait that gives up (stage_wait, limit in time) is made CTA-wide at the
+// step's barrier; the CTA then issues no further copies and skips the remaining steps, thread
+// 0 waits (bounded again) for the copies still in flight into its shared memory, and *err is
+// set to 1.  A CTA that starts after another one gave up (*err == 1) does nothing.  The state
+// is invalid after a give-up and the host reports it as such.
 constexpr int kStages = kSweepStages;
 
 template <bool FORCE, bool DIAG>
@@ -91,7 +96,9 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
         for (int b = 0; b < NS; ++b) stage_init(&full[b], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
+    // skip the tile when an earlier CTA of this launch (or of an earlier one) already gave up
+    const bool healthy = tid != 0 || !err || *(volatile int *)err != 1;
+    if (!__syncthreads_and(healthy)) return;
     const StoreT *a = A + B.offset;
     const int lane = tid & 31;
     // The copies of one step, issued by the lanes of warp 0 (one row each).  Only the row's own
@@ -116,11 +123,12 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
     };
     if (tid < 32)
         for (int j = 0; j < NS && z0 + j < zend; ++j) issue(z0 + j, j);
-    bool ok = true;
-    for (int z = z0; z < zend; ++z) {
+    int z = z0;
+    bool ok = true;  // CTA-wide: the same in every thread after each step's barrier
+    for (; z < zend; ++z) {
         const int st = (z - z0) % NS;
-        ok = stage_wait(&full[st], ((z - z0) / NS) & 1) && ok;
-        if (active && ok) {
+        const bool landed = stage_wait(&full[st], ((z - z0) / NS) & 1);
+        if (active && landed) {
             R f[kQ];
             const StoreT *row0 = buf + (size_t)st * kQ * rows * RW + (size_t)ly * RW + 8;
 #pragma unroll
@@ -136,10 +144,19 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
             for (int i = 0; i < kQ; ++i) S::st_raw(Bout + B.offset + (int64_t)i * B.slab + cell, f[i]);
             dg.add(rho, ux, uy, uz);
         }
-        __syncthreads();  // every thread is done with stage st
+        ok = __syncthreads_and(landed);  // every thread is done with stage st
+        if (!ok) break;
         if (tid < 32 && z + NS < zend) issue(z + NS, st);
     }
-    if (!ok && err) atomicExch(err, 1);
+    if (!ok) {
+        // steps z .. z + NS - 1 have copies issued that may not have landed; thread 0 keeps the
+        // CTA (and its shared memory) alive until they do, within the same bounded wait
+        if (tid == 0) {
+            for (int j = 0; j < NS && z + j < zend; ++j)
+                stage_wait(&full[(z + j - z0) % NS], ((z + j - z0) / NS) & 1);
+            if (err) atomicExch(err, 1);
+        }
+    }
 }
 
 // The cells of one tile.  A thread owns one (x, y) column and walks the tile's z range.  A
