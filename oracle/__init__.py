@@ -8,6 +8,6 @@ restatement of the single-cell collision used to cross-check it.
 from .oracle import (  # noqa: F401
     FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC, SRT, TRT,
     OracleParams, build_oracle, lattice, omega_minus, equilibrium, collide_cell,
-    init, run, macroscopic, diagnostics, set_threads, get_threads,
+    init, run, stream, macroscopic, diagnostics, set_threads, get_threads,
     NO_CLOSURE, SMAGORINSKY, MLP, collide_closure,
 )

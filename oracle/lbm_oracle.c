@@ -195,10 +195,11 @@ static void moments_post(const lattice_t *L, const double *f, const double F[3],
  *       tau = ( tau0 + sqrt(tau0^2 + 18 cs^2 sqrt(2 Pi:Pi) / rho) ) / 2
  *   kind 2, MLP: features (rho - 1) s_rho and s_pi Pi_neq (xx, yy, zz, xy, xz, yz), two
  *   hidden layers of 32 SiLU units, one output y; tau = tau0 + s_tau softplus(y).  The
- *   features and both hidden layers are rounded to BF16 (round to nearest even) before each
- *   product, weights are BF16, sums exact (double here): the same rounding points as the
- *   GPU's tensor-core inference.  Packed parameters (float): W1[32][7], b1[32],
- *   W2[32][32], b2[32], w3[32], b3, s_rho, s_pi, s_tau.
+ *   network is the model as deployed: its three weight matrices are BF16 numbers (the
+ *   packed FP32 weights rounded to nearest even), its biases the packed FP32 values;
+ *   features, sums, SiLU and hidden activations are exact FP64 (no rounding of features or
+ *   activations).  Packed parameters (float): W1[32][7], b1[32], W2[32][32], b2[32],
+ *   w3[32], b3, s_rho, s_pi, s_tau.
  * ------------------------------------------------------------------------------------- */
 typedef struct {
     int32_t kind; /* 0 none, 1 Smagorinsky, 2 MLP */
@@ -246,22 +247,21 @@ static void pi_neq(const lattice_t *L, const double *f, double rho, const double
     pi[5] = m[5] - rho * u[1] * u[2];
 }
 
-/* MLP output y for one cell's features (BF16 rounding points as described above). */
+/* MLP output y for one cell's features: BF16 weights, everything else exact FP64. */
 static double mlp_y(const float *P, const double feat[MLP_IN])
 {
     const float *W1 = P, *b1 = P + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H, *w3 = b2 + MLP_H,
                 *b3 = w3 + MLP_H;
-    double x[MLP_IN], h1[MLP_H], h2[MLP_H];
-    for (int k = 0; k < MLP_IN; ++k) x[k] = bf16(feat[k]);
+    double h1[MLP_H], h2[MLP_H];
     for (int j = 0; j < MLP_H; ++j) {
         double z = b1[j];
-        for (int k = 0; k < MLP_IN; ++k) z += bf16(W1[j * MLP_IN + k]) * x[k];
-        h1[j] = bf16(silu(z));
+        for (int k = 0; k < MLP_IN; ++k) z += bf16(W1[j * MLP_IN + k]) * feat[k];
+        h1[j] = silu(z);
     }
     for (int j = 0; j < MLP_H; ++j) {
         double z = b2[j];
         for (int k = 0; k < MLP_H; ++k) z += bf16(W2[j * MLP_H + k]) * h1[k];
-        h2[j] = bf16(silu(z));
+        h2[j] = silu(z);
     }
     double y = b3[0];
     for (int k = 0; k < MLP_H; ++k) y += bf16(w3[k]) * h2[k];
@@ -434,6 +434,8 @@ static int resolve(const orc_params *p, const uint8_t *flags, int x, int y, int 
  * ------------------------------------------------------------------------------------- */
 int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *flags, const double *cell_u,
                     const double *cell_rho, double *f, double *work, int64_t nsteps);
+static int stream_pass(const lattice_t *Lp, const orc_params *p, const uint8_t *flags, const double *cell_u,
+                       const double *cell_rho, const double *f, double *work);
 
 int orc_run(const orc_params *p, const uint8_t *flags, const double *cell_u, const double *cell_rho, double *f,
             double *work, int64_t nsteps)
@@ -447,17 +449,56 @@ int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *f
 {
     lattice_t L;
     if (get_lattice(p->q, &L) != 0) return -1;
-    const int nx = p->nx, ny = p->ny, nz = p->nz, q = L.q;
-    const int64_t N = (int64_t)nx * ny * nz;
-    int bad = 0;
+    const int q = L.q;
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
     for (int a = 0; a < 6; ++a) {
         if (p->periodic[a / 2]) continue;
         int k = p->face_kind[a];
-        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE) bad = 1;
+        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE) return -2;
     }
-    if (bad) return -2;
 
     for (int64_t step = 0; step < nsteps; ++step) {
+        if (stream_pass(&L, p, flags, cell_u, cell_rho, f, work) != 0) return -3;
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < N; ++n) {
+            if (flags[n] != ORC_FLUID) continue;
+            double fin[QMAX], fout[QMAX];
+            for (int i = 0; i < q; ++i) fin[i] = work[i * N + n];
+            collide(&L, p, cl, fin, fout);
+            for (int i = 0; i < q; ++i) f[i * N + n] = fout[i];
+        }
+    }
+    return 0;
+}
+
+/* The streaming half of a step alone: the pre-collision field f(t + 1) of the post-collision
+ * state f*(t), boundaries included (the first pass of orc_run); non-fluid cells get zeros. */
+int orc_stream(const orc_params *p, const uint8_t *flags, const double *cell_u, const double *cell_rho,
+               const double *f, double *fpre)
+{
+    lattice_t L;
+    if (get_lattice(p->q, &L) != 0) return -1;
+    for (int a = 0; a < 6; ++a) {
+        if (p->periodic[a / 2]) continue;
+        int k = p->face_kind[a];
+        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE) return -2;
+    }
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    for (int i = 0; i < L.q; ++i)
+        for (int64_t n = 0; n < N; ++n)
+            if (flags[n] != ORC_FLUID) fpre[i * N + n] = 0.0;
+    return stream_pass(&L, p, flags, cell_u, cell_rho, f, fpre) == 0 ? 0 : -3;
+}
+
+/* Push every post-collision PDF of f to its target (see above) into work. */
+static int stream_pass(const lattice_t *Lp, const orc_params *p, const uint8_t *flags, const double *cell_u,
+                       const double *cell_rho, const double *f, double *work)
+{
+    const lattice_t L = *Lp;
+    const int nx = p->nx, ny = p->ny, nz = p->nz, q = L.q;
+    const int64_t N = (int64_t)nx * ny * nz;
+    int bad = 0;
+    {
 #pragma omp parallel for schedule(static) reduction(| : bad)
         for (int z = 0; z < nz; ++z) {
             for (int y = 0; y < ny; ++y) {
@@ -505,17 +546,8 @@ int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *f
                 }
             }
         }
-        if (bad) return -3;
-#pragma omp parallel for schedule(static)
-        for (int64_t n = 0; n < N; ++n) {
-            if (flags[n] != ORC_FLUID) continue;
-            double fin[QMAX], fout[QMAX];
-            for (int i = 0; i < q; ++i) fin[i] = work[i * N + n];
-            collide(&L, p, cl, fin, fout);
-            for (int i = 0; i < q; ++i) f[i * N + n] = fout[i];
-        }
     }
-    return 0;
+    return bad ? -3 : 0;
 }
 
 /* Output moments of the stored state (Eq. 1, with the Guo shift for a post-collision

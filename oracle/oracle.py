@@ -125,6 +125,8 @@ def _L():
         lib.orc_collide_closure.restype = ctypes.c_double
         lib.orc_run_closure.argtypes = [pp, P(_CClosure), u8p, dp, dp, dp, dp, ctypes.c_int64]
         lib.orc_run_closure.restype = ctypes.c_int
+        lib.orc_stream.argtypes = [pp, u8p, dp, dp, dp, dp]
+        lib.orc_stream.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_threads.restype = None
         lib.orc_get_threads.argtypes = []
@@ -236,6 +238,23 @@ def run(p: OracleParams, f, nsteps: int, flags=None, cell_u=None, cell_rho=None,
     if rc != 0:
         raise RuntimeError("orc_run failed: %d" % rc)
     return f
+
+
+def stream(p: OracleParams, f, flags=None, cell_u=None, cell_rho=None) -> np.ndarray:
+    """Pre-collision field f(t + 1) of the post-collision state ``f`` = f*(t): the streaming
+    half of one step with its boundaries (zeros at non-fluid cells)."""
+    flags = _check_flags(p, flags)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    out = np.zeros_like(f)
+    if cell_u is not None:
+        cell_u = np.ascontiguousarray(cell_u, dtype=np.float64)
+    if cell_rho is not None:
+        cell_rho = np.ascontiguousarray(cell_rho, dtype=np.float64)
+    cp = p.cstruct()
+    rc = _L().orc_stream(ctypes.byref(cp), _u8(flags), _dp(cell_u), _dp(cell_rho), _dp(f), _dp(out))
+    if rc != 0:
+        raise RuntimeError("orc_stream failed: %d" % rc)
+    return out
 
 
 def macroscopic(p: OracleParams, f, flags=None):
