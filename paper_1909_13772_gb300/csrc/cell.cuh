@@ -16,62 +16,6 @@ using R = typename S::R;
 // collide in kernels.cuh); FP64 and the deviation storages take the pair form
 constexpr bool kAccurate = LBM_ST == 1;
 
-// Per-CTA diagnostics record of the cells this CTA updated (DIAG): sums accumulated per
-// thread and per warp in the sweep's arithmetic type, across warps in FP64:
-// mass, momentum (rho u, half-force corrected), kinetic energy, max |u|, non-finite
-// cells, fluid cells.  Per cell the thread keeps sum rho |u|^2 and max |u|^2; the halving and
-// the square root are taken once per thread (record()).  A cell counts as non-finite when
-// rho + |u|^2 is (an infinity or NaN in either propagates to the sum).
-// The running sums of a thread live in shared memory, column threadIdx.x of an [8][256]
-// array (CTAs of at most 256 threads), not in registers: there they would stay live across
-// the thread's whole z loop next to the cell's populations, which costs the sweep a CTA per SM
-// or spills.  Each thread touches only its own column, in the same order of operations.
-template <bool DIAG>
-__device__ __forceinline__ R *diag_home()
-{
-    __shared__ R home[DIAG ? 8 * 256 : 1];
-    return home + threadIdx.x;
-}
-
-template <bool DIAG>
-struct Diag {
-    __device__ __forceinline__ Diag()
-    {
-        if (!DIAG) return;
-        R *h = diag_home<DIAG>();
-#pragma unroll
-        for (int c = 0; c < 8; ++c) h[c * 256] = R(0);
-    }
-    __device__ __forceinline__ void add(R rho, R ux, R uy, R uz)
-    {
-        if (!DIAG) return;
-        R *h = diag_home<DIAG>();
-        const R u2 = ux * ux + uy * uy + uz * uz;
-        h[0] += rho;
-        h[256] = fma(rho, ux, h[256]);
-        h[512] = fma(rho, uy, h[512]);
-        h[768] = fma(rho, uz, h[768]);
-        h[1024] = fma(rho, u2, h[1024]);
-        h[1280] = fmax(h[1280], u2);
-        h[1536] += isfinite(rho + u2) ? R(0) : R(1);
-        h[1792] += R(1);
-    }
-    // the thread's record: mass, momentum x/y/z, kinetic energy, max |u|, non-finite, cells
-    __device__ __forceinline__ void record(R (&v)[8]) const
-    {
-        if (!DIAG) return;
-        const R *h = diag_home<DIAG>();
-        v[0] = h[0];
-        v[1] = h[256];
-        v[2] = h[512];
-        v[3] = h[768];
-        v[4] = R(0.5) * h[1024];
-        v[5] = sqrt(h[1280]);
-        v[6] = h[1536];
-        v[7] = h[1792];
-    }
-};
-
 template <class T>
 __device__ __forceinline__ T wsum(T v)
 {
@@ -84,6 +28,122 @@ __device__ __forceinline__ T wmax(T v)
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+
+// Per-CTA diagnostics record of the cells this CTA updated (DIAG): mass, momentum (rho u,
+// half-force corrected), kinetic energy, max |u|, non-finite cells, fluid cells.
+//   Mass is the sum of the values the sweep stores (post-collision, after rounding to the
+//   storage format), so it matches an FP64 sum over the stored field.  With FP32 arithmetic
+//   each cell's values are summed without rounding error as a float-float pair (Fast2Sum,
+//   Dekker 1971: s + x = t + e exactly when |s| >= |x|; the chain starts at rho0 for the
+//   deviation storages, at the rest population otherwise, which dominates every other value
+//   near equilibrium), the error terms in FP32, and the cells of a thread are accumulated the
+//   same way: a cell contributes at most Q^2 u^2 rho of error (u = 2^-24), 1.3e-12 relative.
+//   Momentum and kinetic energy come from the collision's moments and are accumulated per
+//   thread with Kahan's compensated sum (error at most 2u of the sum of magnitudes, whatever
+//   the number of cells).  Warp shuffles and everything after them are FP64.  With FP64
+//   arithmetic the sums are plain FP64.  A cell counts as non-finite when rho + |u|^2 is.
+// The running sums of a thread live in shared memory, column threadIdx.x of a [13][256]
+// array (CTAs of at most 256 threads), not in registers: there they would stay live across
+// the thread's whole z loop next to the cell's populations, which costs the sweep a CTA per SM
+// or spills.  Each thread touches only its own column.
+template <bool DIAG>
+struct Diag {
+    // slots: 0/1 mass (sum, error terms), 2-4 momentum, 5-7 their compensations, 8 sum rho
+    // |u|^2, 9 its compensation, 10 max |u|^2, 11 non-finite cells, 12 cells
+    static constexpr int kSlots = 13;
+    static constexpr bool kComp = sizeof(R) == 4;
+    static __device__ __forceinline__ R *home()
+    {
+        __shared__ R h[DIAG ? kSlots * 256 : 1];
+        return h + threadIdx.x;
+    }
+    static __device__ __forceinline__ void kahan(R *s, R *c, R x)
+    {
+        const R y = x - *c;
+        const R t = *s + y;
+        *c = (t - *s) - y;
+        *s = t;
+    }
+    __device__ __forceinline__ Diag()
+    {
+        if (!DIAG) return;
+        R *h = home();
+#pragma unroll
+        for (int c = 0; c < kSlots; ++c) h[c * 256] = R(0);
+    }
+    // f: the cell's post-collision values as the sweep is about to store them (deviations
+    // for the *_DEV storages), rho0: the deviation base (0 otherwise); rho, u: the collision's
+    // moments.
+    __device__ __forceinline__ void add(const R (&f)[kQ], R rho0, R rho, R ux, R uy, R uz)
+    {
+        if (!DIAG) return;
+        R *h = home();
+        const R u2 = ux * ux + uy * uy + uz * uz;
+        if (kComp) {
+            R m = rho0, e = R(0);
+#pragma unroll
+            for (int i = 0; i < kQ; ++i) {
+                const R x = S::stored(f[i]);
+                const R t = m + x;
+                e += x - (t - m);
+                m = t;
+            }
+            const R H = h[0];
+            const R t = H + m;
+            h[256] += (m - (t - H)) + e;
+            h[0] = t;
+            kahan(h + 512, h + 1280, rho * ux);
+            kahan(h + 768, h + 1536, rho * uy);
+            kahan(h + 1024, h + 1792, rho * uz);
+            kahan(h + 2048, h + 2304, rho * u2);
+        } else {
+            h[0] += rho;
+            h[512] = fma(rho, ux, h[512]);
+            h[768] = fma(rho, uy, h[768]);
+            h[1024] = fma(rho, uz, h[1024]);
+            h[2048] = fma(rho, u2, h[2048]);
+        }
+        h[2560] = fmax(h[2560], u2);
+        h[2816] += isfinite(rho + u2) ? R(0) : R(1);
+        h[3072] += R(1);
+    }
+    // the thread's record in FP64: mass, momentum x/y/z, kinetic energy, max |u|, non-finite,
+    // cells
+    __device__ __forceinline__ void record(double (&v)[8]) const
+    {
+        if (!DIAG) return;
+        const R *h = home();
+        v[0] = (double)h[0] + (double)h[256];
+        v[1] = (double)h[512] - (double)h[1280];
+        v[2] = (double)h[768] - (double)h[1536];
+        v[3] = (double)h[1024] - (double)h[1792];
+        v[4] = 0.5 * ((double)h[2048] - (double)h[2304]);
+        v[5] = sqrt((double)h[2560]);
+        v[6] = (double)h[2816];
+        v[7] = (double)h[3072];
+    }
+    // The CTA's record (every thread of the CTA calls this): FP64 warp shuffles, then the warps
+    // in order; partials[blockIdx.x * 8 + c].
+    __device__ __forceinline__ void tile_record(double *__restrict__ partials) const
+    {
+        if (!DIAG) return;
+        __shared__ double sh[8][8];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        double v[8];
+        record(v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) v[c] = c == 5 ? wmax(v[c]) : wsum(v[c]);
+        if (lane == 0)
+            for (int c = 0; c < 8; ++c) sh[warp][c] = v[c];
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            const int c = threadIdx.x;
+            double r = 0.0;
+            for (int w = 0; w < nw; ++w) r = c == 5 ? fmax(r, sh[w][c]) : r + sh[w][c];
+            partials[(int64_t)blockIdx.x * 8 + c] = r;
+        }
+    }
+};
 
 // Geometry of a neighbour block read in place (one per ghost-shell region), staged in
 // shared memory once per CTA.
@@ -236,8 +296,8 @@ __device__ __forceinline__ void update_cell(StoreT *__restrict__ A, StoreT *__re
     gather_cell<KIND, FACE, MASK>(f, A, B, nb, fc, x, y, z, cell, m, k.base);
     R rho, ux, uy, uz;
     collide<kQ, FORCE, R, kAccurate>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+    dg.add(f, k.rho0, rho, ux, uy, uz);
     scatter_cell<KIND, FACE, MASK>(f, A, Bout, B, nb, fc, x, y, z, cell, m, k.base);
-    dg.add(rho, ux, uy, uz);
 }
 
 // Copy the scalar geometry of a block into registers (its neighbour table stays out).

@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
             const Rates<float> rt = rates_of<float>(wp, wm, wc);
             float r2, ux, uy, uz;
             collide<kQ, false, float, true>(f, k, rt, 0.f, r2, ux, uy, uz);
+            dg.add(f, 0.f, r2, ux, uy, uz);
             if (kThr && any_face) {
                 if (masked)
                     scatter_cell<KIND, kFace, true>(f, A, Bout, B, nb, f2, x, y, z, cell, m, k.base);
@@ -424,7 +425,6 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
                 else
                     scatter_cell<KIND, 0, false>(f, A, Bout, B, nb, f2, x, y, z, cell, 0u, k.base);
             }
-            dg.add(r2, ux, uy, uz);
         }
     }
 #if LBM_MLP_TC_SWEEP
@@ -435,23 +435,7 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
         if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(tmem, 128);
     }
 #endif
-    if (DIAG) {
-        __shared__ double sh[8][8];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        float v[8];
-        dg.record(v);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) v[c] = c == 5 ? wmax(v[c]) : wsum(v[c]);
-        if (lane == 0)
-            for (int c = 0; c < 8; ++c) sh[warp][c] = (double)v[c];
-        __syncthreads();
-        if (threadIdx.x < 8) {
-            const int c = threadIdx.x;
-            double r = 0.0;
-            for (int w = 0; w < nw; ++w) r = c == 5 ? fmax(r, sh[w][c]) : r + sh[w][c];
-            partials[(int64_t)blockIdx.x * 8 + c] = r;
-        }
-    }
+    dg.tile_record(partials);
 }
 
 template <int KIND, int CLOSURE, bool DIAG>

@@ -138,6 +138,7 @@ struct Storage<double> {
     static __device__ __forceinline__ R raw(const T *p) { return ld_src(p); }
     static __device__ __forceinline__ R raw_rw(const T *p) { return *p; }
     static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, v); }
+    static __device__ __forceinline__ R stored(R v) { return v; }  // the value st_raw stores
 };
 
 template <>
@@ -151,6 +152,7 @@ struct Storage<float> {
     static __device__ __forceinline__ R raw(const T *p) { return ld_src(p); }
     static __device__ __forceinline__ R raw_rw(const T *p) { return *p; }
     static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, v); }
+    static __device__ __forceinline__ R stored(R v) { return v; }
 };
 
 template <>
@@ -164,6 +166,7 @@ struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ R raw(const T *p) { return __bfloat162float(ld_src(p)); }
     static __device__ __forceinline__ R raw_rw(const T *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, __float2bfloat16_rn(v)); }
+    static __device__ __forceinline__ R stored(R v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 };
 
 template <>
@@ -177,6 +180,7 @@ struct Storage<__half> {
     static __device__ __forceinline__ R raw(const T *p) { return __half2float(ld_src(p)); }
     static __device__ __forceinline__ R raw_rw(const T *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st_raw(T *p, R v) { __stcs(p, __float2half_rn(v)); }
+    static __device__ __forceinline__ R stored(R v) { return __half2float(__float2half_rn(v)); }
 };
 
 // ---------------------------------------------------------------------------------------

@@ -139,10 +139,10 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
             }
             R rho, ux, uy, uz;
             collide<kQ, FORCE, R, kAccurate>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+            dg.add(f, k.rho0, rho, ux, uy, uz);
             const int64_t cell = B.cell(x, y, z);
 #pragma unroll
             for (int i = 0; i < kQ; ++i) S::st_raw(Bout + B.offset + (int64_t)i * B.slab + cell, f[i]);
-            dg.add(rho, ux, uy, uz);
         }
         ok = __syncthreads_and(landed);  // every thread is done with stage st
         if (!ok) break;
@@ -238,23 +238,7 @@ __global__ void __launch_bounds__(256, DIAG ? kMinBDiag : kMinB)
     Diag<DIAG> dg;
     // every thread takes part in the block reduction, including those without cells
     sweep_cells<FORCE, KIND, DIAG, THROUGH>(A, Bout, blocks, tiles, tz, k, dg, stage_smem, err);
-    if (DIAG) {
-        __shared__ double sh[8][8];
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        R v[8];
-        dg.record(v);
-#pragma unroll
-        for (int c = 0; c < 8; ++c) v[c] = c == 5 ? wmax(v[c]) : wsum(v[c]);
-        if (lane == 0)
-            for (int c = 0; c < 8; ++c) sh[warp][c] = (double)v[c];
-        __syncthreads();
-        if (threadIdx.x < 8) {
-            const int c = threadIdx.x;
-            double r = 0.0;
-            for (int w = 0; w < nw; ++w) r = c == 5 ? fmax(r, sh[w][c]) : r + sh[w][c];
-            partials[(int64_t)blockIdx.x * 8 + c] = r;
-        }
-    }
+    dg.tile_record(partials);
 }
 
 template <bool FORCE, int KIND, bool DIAG, int THROUGH>

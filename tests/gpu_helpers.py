@@ -10,6 +10,7 @@ import oracle
 from paper_1909_13772_gb300 import lbm
 
 TOL = {lbm.FP64: 1e-12, lbm.FP32: 1e-5}
+UNIT_ROUNDOFF = {lbm.FP64: 2.0 ** -53, lbm.FP32: 2.0 ** -24}
 
 
 @dataclass
@@ -107,3 +108,36 @@ def oracle_run(case, rho, u, steps):
         raise NotImplementedError("interior velocity/pressure cells are not used in these cases")
     f0 = oracle.init(p, rho, u, flags=fl)
     return f0, oracle.run(p, f0, steps, flags=fl, cell_u=cu, cell_rho=cr)
+
+
+def flow_gates(got, want, storage, steps, q, fluid=None, rho0=1.0):
+    """Gates on the flow signal, not only on raw PDFs: the normwise errors of the deviations
+    f_i - w_i rho0 and of the velocity sum(c f) / sum(f), against derived tolerances.
+
+    Every step stores each value rounded (unit roundoff u of the storage).  The collision damps
+    those errors in the non-conserved moments; in the conserved ones (mass, momentum) they are
+    not damped and add up like a random walk: after n steps their typical size is
+    sqrt(n) u max|f| per value.  The deviation gate allows 10 times that (relative to
+    max|f - w rho0|); the velocity gate 10 times the error of a momentum sum over the
+    directions with c_a != 0 (relative to max|u|).  Returns (dev_err, dev_tol, u_err, u_tol)."""
+    c, w, _ = oracle.lattice(q)
+    g = got.reshape(q, -1)
+    o = want.reshape(q, -1)
+    if fluid is not None:
+        m = np.asarray(fluid).reshape(-1)
+        g, o = g[:, m], o[:, m]
+    n = max(int(steps), 1)
+    unit = UNIT_ROUNDOFF[storage]
+    per_value = 10.0 * np.sqrt(n) * unit * np.abs(o).max()
+    dev_o = o - w[:, None] * rho0
+    dev_err = float(np.abs(g - o).max() / np.abs(dev_o).max())
+    dev_tol = per_value / float(np.abs(dev_o).max())
+    ug = (c.T.astype(np.float64) @ g) / g.sum(0)
+    uo = (c.T.astype(np.float64) @ o) / o.sum(0)
+    umax = float(np.abs(uo).max())
+    u_err = float(np.abs(ug - uo).max() / umax)
+    moving = int((np.abs(c[:, 0]) > 0).sum())
+    u_tol = moving * per_value / float(o.sum(0).min()) / umax
+    assert dev_err <= dev_tol, ("deviation", dev_err, dev_tol)
+    assert u_err <= u_tol, ("velocity", u_err, u_tol)
+    return dev_err, dev_tol, u_err, u_tol
