@@ -10,7 +10,8 @@
  *   - Eq. 2: f_i(x + c_i, t + 1) = f_i(x, t) + Omega_i(f(x, t)): collide, then push each
  *     post-collision PDF to the neighbour it points at.
  *   - Eq. 3 with the special relaxation matrices named right after it: SRT (one rate) and
- *     TRT (one rate for the even part, one for the odd part of each direction pair).
+ *     TRT (one rate for the even part, one for the odd part of each direction pair); and
+ *     Eq. 3 itself (MRT) with a stated moment matrix and one rate per group of moments.
  *   - Sec. 5.1.1, body-force paragraph: a constant body force drives periodic set-ups; the
  *     force model is Guo et al. (the paper cites it), split into even/odd parts under TRT.
  *   - Sec. 5.1.1, boundary paragraph: no-slip, velocity and pressure boundaries.  The paper
@@ -46,6 +47,7 @@
 
 #define ORC_SRT 0
 #define ORC_TRT 1
+#define ORC_MRT 2
 
 #define QMAX 27
 
@@ -60,6 +62,8 @@ typedef struct {
     double force[3];      /* constant body force per cell, lattice units */
     double face_u[6][3];  /* wall velocity of a velocity face */
     double face_rho[6];   /* wall density of a velocity face / pressure of a pressure face */
+    double mrt_s[7];      /* MRT: rates of the row groups 1..7 (momentum, shear, bulk, third,
+                             fourth, fifth, sixth order; see the MRT section below) */
 } orc_params;
 
 /* ---------------------------------------------------------------------------------------
@@ -119,12 +123,139 @@ typedef struct {
     int c[3 * QMAX];
     double w[QMAX];
     int opp[QMAX];
+    double M[QMAX * QMAX];    /* MRT moment matrix, row k = moment k, M[k * q + i] */
+    double Minv[QMAX * QMAX]; /* its inverse, Minv[i * q + k] */
+    int group[QMAX];          /* row group of moment k (0 mass, 1..7 as mrt_s) */
 } lattice_t;
+
+static int mrt_matrix(lattice_t *L);
 
 static int get_lattice(int q, lattice_t *L)
 {
     L->q = q;
-    return orc_lattice(q, L->c, L->w, L->opp);
+    int r = orc_lattice(q, L->c, L->w, L->opp);
+    if (r != 0) return r;
+    return mrt_matrix(L);
+}
+
+/* ---------------------------------------------------------------------------------------
+ * MRT moment space (Eq. 3: Omega = -M^-1 S (M f - m_eq), M invertible, S diagonal).  The
+ * paper cites d'Humieres et al. 2002 for the method and fixes neither M nor S.  Reading:
+ * the rows of M are polynomials in c_i, each of one parity, taken in this order and grouped
+ * by degree (group number in brackets):
+ *   [0] 1;  [1] cx, cy, cz;
+ *   [2] cx cy, cx cz, cy cz, 2cx^2 - cy^2 - cz^2, cy^2 - cz^2 (shear);  [3] |c|^2 (bulk);
+ *   [4] cx(cy^2 + cz^2), cx(cy^2 - cz^2), cy(cx^2 + cz^2), cy(cx^2 - cz^2),
+ *       cz(cx^2 + cy^2), cz(cx^2 - cy^2), and for D3Q27 cx cy cz;
+ *   [5] cx^2 cy^2, cx^2 cz^2, cy^2 cz^2, and for D3Q27 cx^2 cy cz, cy^2 cx cz, cz^2 cx cy;
+ *   [6] (D3Q27) cx^2 cy^2 cz, cx^2 cz^2 cy, cy^2 cz^2 cx;  [7] (D3Q27) cx^2 cy^2 cz^2;
+ * evaluated at the lattice velocities and orthogonalised one after the other by Gram-Schmidt
+ * under the weighted product <a, b> = sum_i w_i a_i b_i.  Every row is then orthogonal to all
+ * rows before it, so a group's rows span the polynomials of its degree class with everything
+ * of lower classes removed, and relaxing a group with one rate does not depend on how the
+ * rows within it are chosen.  S holds one rate per group: mass (group 0) is conserved,
+ * groups 1..7 take mrt_s[0..6].  The Guo source enters moment space with the factor
+ * (1 - s/2) of its own moment's rate.  M^-1 is computed by Gauss-Jordan elimination, not
+ * from the orthogonality.
+ * ------------------------------------------------------------------------------------- */
+static double mrt_raw(int k27, const int *c, int *group)
+{
+    const double x = c[0], y = c[1], z = c[2];
+    const double xx = x * x, yy = y * y, zz = z * z;
+    switch (k27) {
+        case 0: *group = 0; return 1.0;
+        case 1: *group = 1; return x;
+        case 2: *group = 1; return y;
+        case 3: *group = 1; return z;
+        case 4: *group = 2; return x * y;
+        case 5: *group = 2; return x * z;
+        case 6: *group = 2; return y * z;
+        case 7: *group = 2; return 2.0 * xx - yy - zz;
+        case 8: *group = 2; return yy - zz;
+        case 9: *group = 3; return xx + yy + zz;
+        case 10: *group = 4; return x * (yy + zz);
+        case 11: *group = 4; return x * (yy - zz);
+        case 12: *group = 4; return y * (xx + zz);
+        case 13: *group = 4; return y * (xx - zz);
+        case 14: *group = 4; return z * (xx + yy);
+        case 15: *group = 4; return z * (xx - yy);
+        case 16: *group = 4; return x * y * z;
+        case 17: *group = 5; return xx * yy;
+        case 18: *group = 5; return xx * zz;
+        case 19: *group = 5; return yy * zz;
+        case 20: *group = 5; return xx * y * z;
+        case 21: *group = 5; return yy * x * z;
+        case 22: *group = 5; return zz * x * y;
+        case 23: *group = 6; return xx * yy * z;
+        case 24: *group = 6; return xx * zz * y;
+        case 25: *group = 6; return yy * zz * x;
+        default: *group = 7; return xx * yy * zz;
+    }
+}
+
+static int mrt_matrix(lattice_t *L)
+{
+    const int q = L->q;
+    /* D3Q19 takes the rows 0..15 and 17..19 of the D3Q27 list */
+    static const int rows19[19] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 17, 18, 19};
+    for (int k = 0; k < q; ++k) {
+        const int r = q == 19 ? rows19[k] : k;
+        for (int i = 0; i < q; ++i) L->M[k * q + i] = mrt_raw(r, L->c + 3 * i, &L->group[k]);
+    }
+    /* Gram-Schmidt under the weighted product, rows in order */
+    for (int k = 0; k < q; ++k) {
+        for (int j = 0; j < k; ++j) {
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < q; ++i) {
+                num += L->w[i] * L->M[k * q + i] * L->M[j * q + i];
+                den += L->w[i] * L->M[j * q + i] * L->M[j * q + i];
+            }
+            const double a = num / den;
+            for (int i = 0; i < q; ++i) L->M[k * q + i] -= a * L->M[j * q + i];
+        }
+        double nn = 0.0;
+        for (int i = 0; i < q; ++i) nn += L->w[i] * L->M[k * q + i] * L->M[k * q + i];
+        if (!(nn > 1e-12)) return -4; /* the rows are not independent on this lattice */
+    }
+    /* inverse by Gauss-Jordan elimination with partial pivoting on [M | I] */
+    double A[QMAX][2 * QMAX];
+    for (int r = 0; r < q; ++r)
+        for (int j = 0; j < 2 * q; ++j) A[r][j] = j < q ? L->M[r * q + j] : (j - q == r ? 1.0 : 0.0);
+    for (int col = 0; col < q; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < q; ++r)
+            if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+        if (fabs(A[piv][col]) < 1e-14) return -5;
+        if (piv != col)
+            for (int j = 0; j < 2 * q; ++j) {
+                double t = A[col][j];
+                A[col][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+        const double d = A[col][col];
+        for (int j = 0; j < 2 * q; ++j) A[col][j] /= d;
+        for (int r = 0; r < q; ++r) {
+            if (r == col) continue;
+            const double a = A[r][col];
+            if (a == 0.0) continue;
+            for (int j = 0; j < 2 * q; ++j) A[r][j] -= a * A[col][j];
+        }
+    }
+    for (int i = 0; i < q; ++i)
+        for (int k = 0; k < q; ++k) L->Minv[i * q + k] = A[i][q + k];
+    return 0;
+}
+
+/* The moment matrix, its inverse and the row groups (for the tests). */
+int orc_mrt_matrix(int q, double *M, double *Minv, int *group)
+{
+    lattice_t L;
+    int r = get_lattice(q, &L);
+    if (r != 0) return r;
+    memcpy(M, L.M, sizeof(double) * q * q);
+    memcpy(Minv, L.Minv, sizeof(double) * q * q);
+    memcpy(group, L.group, sizeof(int) * q);
+    return 0;
 }
 
 /* TRT: the second rate follows from the "magic" parameter
@@ -313,6 +444,25 @@ static void collide(const lattice_t *L, const orc_params *p, const orc_closure *
     if (p->collision == ORC_SRT) {
         double w = om;
         for (int i = 0; i < L->q; ++i) fout[i] = f[i] - w * (f[i] - feq[i]) + (1.0 - 0.5 * w) * S[i];
+    } else if (p->collision == ORC_MRT) {
+        /* Eq. 3 in moment space: m* = m - S (m - meq) + (I - S/2) g, f* = M^-1 m* */
+        const int q = L->q;
+        double ms[QMAX];
+        for (int k = 0; k < q; ++k) {
+            double m = 0.0, me = 0.0, g = 0.0;
+            for (int i = 0; i < q; ++i) {
+                m += L->M[k * q + i] * f[i];
+                me += L->M[k * q + i] * feq[i];
+                g += L->M[k * q + i] * S[i];
+            }
+            const double s = L->group[k] == 0 ? 0.0 : p->mrt_s[L->group[k] - 1];
+            ms[k] = m - s * (m - me) + (1.0 - 0.5 * s) * g;
+        }
+        for (int i = 0; i < q; ++i) {
+            double v = 0.0;
+            for (int k = 0; k < q; ++k) v += L->Minv[i * q + k] * ms[k];
+            fout[i] = v;
+        }
     } else {
         double wp = om;
         double wm = orc_omega_minus(wp, p->magic_lambda);

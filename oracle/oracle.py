@@ -13,7 +13,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
-SRT, TRT = 0, 1
+SRT, TRT, MRT = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
@@ -41,7 +41,7 @@ class _CParams(ctypes.Structure):
         ("periodic", ctypes.c_int32 * 3), ("face_kind", ctypes.c_int32 * 6),
         ("omega", ctypes.c_double), ("magic_lambda", ctypes.c_double),
         ("force", ctypes.c_double * 3), ("face_u", (ctypes.c_double * 3) * 6),
-        ("face_rho", ctypes.c_double * 6),
+        ("face_rho", ctypes.c_double * 6), ("mrt_s", ctypes.c_double * 7),
     ]
 
 
@@ -62,6 +62,8 @@ class OracleParams:
     face_kind: tuple = (NOSLIP,) * 6
     face_u: tuple = field(default_factory=lambda: ((0.0, 0.0, 0.0),) * 6)
     face_rho: tuple = (1.0,) * 6
+    # MRT: rates of the moment groups momentum, shear, bulk, third, fourth, fifth, sixth order
+    mrt_s: tuple = (1.0,) * 7
 
     def cstruct(self) -> _CParams:
         c = _CParams()
@@ -76,6 +78,8 @@ class OracleParams:
             for a in range(3):
                 c.face_u[k][a] = float(self.face_u[k][a])
         c.omega, c.magic_lambda = float(self.omega), float(self.magic_lambda)
+        for g in range(7):
+            c.mrt_s[g] = float(self.mrt_s[g])
         return c
 
 
@@ -127,6 +131,8 @@ def _L():
         lib.orc_run_closure.restype = ctypes.c_int
         lib.orc_stream.argtypes = [pp, u8p, dp, dp, dp, dp]
         lib.orc_stream.restype = ctypes.c_int
+        lib.orc_mrt_matrix.argtypes = [ctypes.c_int, dp, dp, ip]
+        lib.orc_mrt_matrix.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_threads.restype = None
         lib.orc_get_threads.argtypes = []
@@ -161,6 +167,25 @@ def lattice(q: int):
     if rc != 0:
         raise ValueError("orc_lattice(%d) failed: %d" % (q, rc))
     return c.reshape(q, 3).astype(np.int64), w, opp.astype(np.int64)
+
+
+def mrt_matrix(q: int):
+    """(M[q,q], M^-1[q,q], group[q]) of the oracle's MRT moment space."""
+    M = np.zeros((q, q), dtype=np.float64)
+    Mi = np.zeros((q, q), dtype=np.float64)
+    g = np.zeros(q, dtype=np.intc)
+    rc = _L().orc_mrt_matrix(q, _dp(M), _dp(Mi), g.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+    if rc != 0:
+        raise ValueError("orc_mrt_matrix(%d) failed: %d" % (q, rc))
+    return M, Mi, g.astype(np.int64)
+
+
+def mrt_rates(q: int, omega: float, magic_lambda: float, bulk=None, fourth=None, fifth=None, sixth=None):
+    """MRT group rates (momentum, shear, bulk, third, ..., sixth) for a shear rate omega and a
+    third-order rate from Lambda; groups left at None take the TRT rate of their parity."""
+    om = omega_minus(omega, magic_lambda)
+    pick = lambda v, d: d if v is None else float(v)  # noqa: E731
+    return (om, omega, pick(bulk, omega), om, pick(fourth, omega), pick(fifth, om), pick(sixth, omega))
 
 
 def omega_minus(omega_plus: float, magic_lambda: float) -> float:
