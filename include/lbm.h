@@ -61,7 +61,13 @@ typedef enum {
 } lbm_status;
 
 enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 };
-enum { LBM_SRT = 0, LBM_TRT = 1 };
+/* Collision (Sec. 5.1.1, Eq. 3): SRT and TRT are the special relaxation matrices the paper
+ * names; MRT relaxes groups of moments with their own rates: the shear moments with omega,
+ * momentum and the third-order moments with omega- (from magic_lambda, as TRT), the bulk,
+ * fourth-, fifth- and sixth-order groups with mrt_rates.  The moment space: polynomials of c
+ * grouped by degree, each group orthogonal to all lower groups under sum_i w_i a(c_i) b(c_i).
+ * MRT is available with FP64 and FP32 storage. */
+enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2 };
 /* PDF storage: FP64 and FP32 store f_i; the *_DEV forms store f_i - w_i rho0 in 16 bits and
  * collide in FP32. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16_DEV = 2, LBM_FP16_DEV = 3 };
@@ -73,15 +79,18 @@ enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_VELOCITY = 2, LBM_PRESSURE = 3, LBM_PE
 
 typedef struct {
     int32_t stencil;       /* LBM_D3Q19 or LBM_D3Q27 */
-    int32_t collision;     /* LBM_SRT or LBM_TRT */
+    int32_t collision;     /* LBM_SRT, LBM_TRT or LBM_MRT */
     int32_t storage;       /* LBM_FP64 ... */
     int32_t pattern;       /* LBM_TWO_GRID or LBM_AA */
-    double omega;          /* SRT: omega = 1/tau; TRT: omega+ (sets the viscosity) */
-    double magic_lambda;   /* TRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2); 3/16 typical */
+    double omega;          /* SRT: omega = 1/tau; TRT: omega+ (sets the viscosity); MRT: shear rate */
+    double magic_lambda;   /* TRT, MRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2); 3/16 typical */
     double force[3];       /* constant body force per cell (lattice units), Guo scheme */
     double rho0;           /* reference density (1.0); base of the *_DEV storages */
     int32_t periodic[3];   /* non-zero: the domain is periodic along that axis */
     int32_t diag_interval; /* >0: lbm_step checks the diagnostics every that many steps */
+    double mrt_rates[4];   /* MRT: rates of the bulk, fourth-, fifth- and sixth-order groups, each
+                              in [0, 2) (fifth and sixth: D3Q27 only); ignored otherwise.  TRT is
+                              omega, omega, omega-, omega */
 } lbm_params;
 
 /* One block: global cell coordinates of its first interior cell and its interior size.

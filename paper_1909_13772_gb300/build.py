@@ -24,6 +24,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", "-I", INCLUDE, "-I", CSRC,
            "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
 VARIANTS = [(q, st) for q in (19, 27) for st in (0, 1, 2, 3)]
+MRT_VARIANTS = [(q, st) for q in (19, 27) for st in (0, 1)]  # MRT sweeps: FP64 and FP32 storage
 
 
 def _nvcc() -> str:
@@ -49,6 +50,11 @@ def _jobs(nvcc, extra, build_dir):
             src = os.path.join(CSRC, name)
             obj = os.path.join(build_dir, "%s_%d_%d.o" % (name[:-3], q, st))
             jobs.append([nvcc] + ARCH + NVFLAGS + extra + ["-DLBM_Q=%d" % q, "-DLBM_ST=%d" % st, "-c", src, "-o", obj])
+    for q, st in MRT_VARIANTS:
+        src = os.path.join(CSRC, "sweep.cu")
+        obj = os.path.join(build_dir, "sweep_mrt_%d_%d.o" % (q, st))
+        jobs.append([nvcc] + ARCH + NVFLAGS + extra + ["-DLBM_Q=%d" % q, "-DLBM_ST=%d" % st, "-DLBM_MRT_SWEEP=1", "-c", src,
+                                                     "-o", obj])
     return jobs
 
 

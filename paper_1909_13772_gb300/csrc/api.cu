@@ -155,11 +155,18 @@ void dfree(T *&p)
     } while (0)
 
 cudaError_t do_sweep(int q, int st, const SweepArgs &s) { LBM_SWITCH(q, st, launch_sweep_, s); }
+// MRT sweeps exist for FP64 and FP32 storage (lbm_create_blocks refuses the others)
+cudaError_t do_sweep_mrt(int q, int st, const SweepArgs &s)
+{
+    if (q == 19) return st == 0 ? launch_sweep_mrt_19_0(s) : launch_sweep_mrt_19_1(s);
+    return st == 0 ? launch_sweep_mrt_27_0(s) : launch_sweep_mrt_27_1(s);
+}
 
 // The step's sweep: the plain sweep, or the closure sweep when a closure is set.
 cudaError_t sweep_of(const lbm_ctx *c, const SweepArgs &s)
 {
-    if (c->closure == CLOSURE_NONE) return do_sweep(c->q, c->storage, s);
+    if (c->closure == CLOSURE_NONE)
+        return c->p.collision == LBM_MRT ? do_sweep_mrt(c->q, c->storage, s) : do_sweep(c->q, c->storage, s);
     ClosureLaunch cl;
     cl.sw = s;
     cl.closure = c->closure;
@@ -485,11 +492,16 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
     if (!params || !blocks || nblocks <= 0) return LBM_ERR_ARG;
     const lbm_params &p = *params;
     if (p.stencil != LBM_D3Q19 && p.stencil != LBM_D3Q27) return LBM_ERR_ARG;
-    if (p.collision != LBM_SRT && p.collision != LBM_TRT) return LBM_ERR_ARG;
+    if (p.collision != LBM_SRT && p.collision != LBM_TRT && p.collision != LBM_MRT) return LBM_ERR_ARG;
     if (p.storage < LBM_FP64 || p.storage > LBM_FP16_DEV) return LBM_ERR_ARG;
     if (p.pattern != LBM_TWO_GRID && p.pattern != LBM_AA) return LBM_ERR_ARG;
     if (!(p.omega >= 0.0 && p.omega < 2.0)) return LBM_ERR_ARG;
-    if (p.collision == LBM_TRT && !(p.magic_lambda > 0.0) && p.omega > 0.0) return LBM_ERR_ARG;
+    if (p.collision != LBM_SRT && !(p.magic_lambda > 0.0) && p.omega > 0.0) return LBM_ERR_ARG;
+    if (p.collision == LBM_MRT) {
+        for (int g = 0; g < 4; ++g)
+            if (!(p.mrt_rates[g] >= 0.0 && p.mrt_rates[g] < 2.0)) return LBM_ERR_ARG;
+        if (p.storage != LBM_FP64 && p.storage != LBM_FP32) return LBM_ERR_UNSUPPORTED;
+    }
     if (!(p.rho0 > 0.0) || p.diag_interval < 0) return LBM_ERR_ARG;
     for (int a = 0; a < 3; ++a)
         if (!std::isfinite(p.force[a])) return LBM_ERR_ARG;
@@ -529,7 +541,7 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
     double wm = wp;
     // TRT: Lambda = (1/w+ - 1/2)(1/w- - 1/2); at w+ = 0 (no relaxation of the even part) the
     // IEEE evaluation gives the limit w- = 2.
-    if (p.collision == LBM_TRT) wm = 1.0 / (p.magic_lambda / (1.0 / wp - 0.5) + 0.5);
+    if (p.collision != LBM_SRT) wm = 1.0 / (p.magic_lambda / (1.0 / wp - 0.5) + 0.5);
     const LatticeView L = lattice_view(c->q);
     const bool dev = c->storage >= LBM_BF16_DEV;
     for (int i = 0; i < 27; ++i) c->base[i] = (dev && i < L.q) ? L.w[i] * p.rho0 : 0.0;
@@ -549,6 +561,14 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
         d.fc[i] = 3.0 * d.a_m * L.w[i] * cF;
     }
     for (int a = 0; a < 3; ++a) d.F[a] = p.force[a];
+    // MRT: bulk, fourth- and sixth-order rates against omega+, fifth-order against omega- (the
+    // TRT rates of their parity); zero for SRT and TRT
+    if (p.collision == LBM_MRT) {
+        d.mrt_d[0] = p.mrt_rates[0] - wp;
+        d.mrt_d[1] = p.mrt_rates[1] - wp;
+        d.mrt_d[2] = c->q == 27 ? p.mrt_rates[2] - wm : 0.0;
+        d.mrt_d[3] = c->q == 27 ? p.mrt_rates[3] - wp : 0.0;
+    }
     d.rho0 = dev ? p.rho0 : 0.0;
     for (int i = 0; i < 27; ++i) d.base[i] = c->base[i];
     // FP32 copy of every constant
@@ -565,6 +585,7 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
     for (int k2 = 0; k2 < 4; ++k2) {
         f.r.pw[k2] = (float)d.r.pw[k2];
         f.r.mw[k2] = (float)d.r.mw[k2];
+        f.r.pq[k2] = (float)d.r.pq[k2];
         f.bw[k2] = (float)d.bw[k2];
     }
     for (int i = 0; i < 27; ++i) {
@@ -573,6 +594,7 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
         f.base[i] = (float)d.base[i];
     }
     for (int a = 0; a < 3; ++a) f.F[a] = (float)d.F[a];
+    for (int g = 0; g < 4; ++g) f.mrt_d[g] = (float)d.mrt_d[g];
     f.rho0 = (float)d.rho0;
     *out = c;
     return LBM_OK;
@@ -862,8 +884,8 @@ lbm_status lbm_set_closure(lbm_ctx *c, int32_t kind, double cs, const float *mlp
     if (kind == LBM_CLOSURE_SMAGORINSKY && !(std::isfinite(cs) && cs >= 0.0))
         return fail(c, LBM_ERR_ARG, "bad Smagorinsky constant");
     if (kind == LBM_CLOSURE_MLP && !mlp_params) return fail(c, LBM_ERR_ARG, "null network parameters");
-    if (c->q != 19 || c->storage != LBM_FP32 || c->force)
-        return fail(c, LBM_ERR_UNSUPPORTED, "closures need D3Q19, FP32 storage and no body force");
+    if (c->q != 19 || c->storage != LBM_FP32 || c->force || c->p.collision == LBM_MRT)
+        return fail(c, LBM_ERR_UNSUPPORTED, "closures need D3Q19, FP32 storage, SRT or TRT and no body force");
     if (kind == LBM_CLOSURE_MLP) {
         const MlpDev d = mlp_device_form(mlp_params);
         if (!c->d_mlp) CK(cudaMalloc((void **)&c->d_mlp, sizeof(MlpDev)), "cudaMalloc(network)");

@@ -57,7 +57,20 @@ __device__ __forceinline__ void coords_of(int64_t cell, const DevBlock &B, int &
 struct FillConst {
     R F[3];
     R base[27];
+    double base64[27];  // the deviation base in FP64 (host-facing reads and writes)
 };
+
+// A stored PDF as f_i in FP64 (the deviation base of the *_DEV storages added in FP64), and the
+// store of f_i given in FP64: the kernels that move PDFs to and from the host and the FP64
+// reductions use these, so that no FP32 rounding of w_i rho0 + v_i enters them.
+__device__ __forceinline__ double ld_f64(const StoreT *p, const FillConst &k, int i)
+{
+    return (double)S::raw_rw(p) + k.base64[i];
+}
+__device__ __forceinline__ void st_f64(StoreT *p, double v, const FillConst &k, int i)
+{
+    S::st_raw(p, R(v - k.base64[i]));
+}
 
 template <int MODE>
 __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevBlock *__restrict__ blocks,
@@ -186,7 +199,7 @@ __global__ void k_init(StoreT *__restrict__ A, const DevBlock *__restrict__ bloc
         const R cu = R(Lq::cx(i)) * ux + R(Lq::cy(i)) * uy + R(Lq::cz(i)) * uz;
         f[i] = R(Lq::w(i)) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
     }
-    collide<kQ, FORCE, R>(f, k);
+    collide<kQ, FORCE, R, true>(f, k);  // MRT terms vanish unless the context is MRT
 #pragma unroll
     for (int i = 0; i < kQ; ++i) S::st_plain(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), f[i], k.base[i]);
 }
@@ -209,7 +222,7 @@ __global__ void k_get(const StoreT *__restrict__ A, const DevBlock *__restrict__
     const uint32_t m = mask ? mask[cell] : 0u;
     const bool fluid = !(m & kMaskSolid);
     for (int i = 0; i < kQ; ++i)
-        out[(int64_t)i * N + n] = fluid ? (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]) : 0.0;
+        out[(int64_t)i * N + n] = fluid ? ld_f64(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k, i) : 0.0;
 }
 
 __global__ void k_set(StoreT *__restrict__ A, const DevBlock *__restrict__ blocks, int blk, int layout,
@@ -227,7 +240,7 @@ __global__ void k_set(StoreT *__restrict__ A, const DevBlock *__restrict__ block
     if (m & kMaskSolid) return;
     StoreT *a = A + B.offset;
     for (int i = 0; i < kQ; ++i)
-        S::st_plain(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), R(in[(int64_t)i * N + n]), k.base[i]);
+        st_f64(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), in[(int64_t)i * N + n], k, i);
 }
 
 // Output moments in FP64: rho = sum f*, u = (sum c f* - F/2) / rho.
@@ -252,7 +265,7 @@ __global__ void k_macro(const StoreT *__restrict__ A, const DevBlock *__restrict
     const StoreT *a = A + B.offset;
     double f[kQ];
 #pragma unroll
-    for (int i = 0; i < kQ; ++i) f[i] = (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]);
+    for (int i = 0; i < kQ; ++i) f[i] = ld_f64(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k, i);
     const double F[3] = {Fx, Fy, Fz};
     double rho, j[3];
     moments_post<kQ>(f, F, rho, j);
@@ -291,7 +304,7 @@ __global__ void __launch_bounds__(256) k_coarse(const StoreT *__restrict__ A, co
                 double f[kQ];
 #pragma unroll
                 for (int i = 0; i < kQ; ++i)
-                    f[i] = (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]);
+                    f[i] = ld_f64(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k, i);
                 double rho, j[3];
                 moments_post<kQ>(f, F, rho, j);
                 const double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
@@ -351,7 +364,7 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const StoreT *__restrict__
             bool finite = true;
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                f[i] = (double)S::ld_rw(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k.base[i]);
+                f[i] = ld_f64(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), k, i);
                 finite = finite && isfinite(f[i]);
             }
             double rho, j[3];
@@ -388,7 +401,10 @@ FillConst fill_const(const double F[3], const double base[27])
 {
     FillConst k;
     for (int a = 0; a < 3; ++a) k.F[a] = (R)F[a];
-    for (int i = 0; i < 27; ++i) k.base[i] = (R)base[i];
+    for (int i = 0; i < 27; ++i) {
+        k.base[i] = (R)base[i];
+        k.base64[i] = base[i];
+    }
     return k;
 }
 

@@ -15,6 +15,8 @@ using R = typename S::R;
 // the collision relaxes the non-equilibrium parts first for full populations in FP32 (see
 // collide in kernels.cuh); FP64 and the deviation storages take the pair form
 constexpr bool kAccurate = LBM_ST == 1;
+// MRT collision (group corrections on top of TRT) in this object's sweeps
+constexpr bool kMrt = LBM_MRT_SWEEP != 0;
 
 template <class T>
 __device__ __forceinline__ T wsum(T v)
@@ -33,11 +35,11 @@ __device__ __forceinline__ T wmax(T v)
 // half-force corrected), kinetic energy, max |u|, non-finite cells, fluid cells.
 //   Mass is the sum of the values the sweep stores (post-collision, after rounding to the
 //   storage format), so it matches an FP64 sum over the stored field.  With FP32 arithmetic
-//   each cell's values are summed without rounding error as a float-float pair (Fast2Sum,
-//   Dekker 1971: s + x = t + e exactly when |s| >= |x|; the chain starts at rho0 for the
-//   deviation storages, at the rest population otherwise, which dominates every other value
-//   near equilibrium), the error terms in FP32, and the cells of a thread are accumulated the
-//   same way: a cell contributes at most Q^2 u^2 rho of error (u = 2^-24), 1.3e-12 relative.
+//   each cell's values are summed without rounding error as a float-float pair (TwoSum, Knuth:
+//   t = s + x, e = (s - (t - b)) + (x - b) with b = t - s gives s + x = t + e exactly, whatever
+//   the magnitudes; the chain starts at rho0 for the deviation storages), the error terms in
+//   FP32, and the cells of a thread are accumulated the same way: a cell contributes at most
+//   Q^2 u^2 rho of error (u = 2^-24), 1.3e-12 relative.
 //   Momentum and kinetic energy come from the collision's moments and are accumulated per
 //   thread with Kahan's compensated sum (error at most 2u of the sum of magnitudes, whatever
 //   the number of cells).  Warp shuffles and everything after them are FP64.  With FP64
@@ -56,6 +58,14 @@ struct Diag {
     {
         __shared__ R h[DIAG ? kSlots * 256 : 1];
         return h + threadIdx.x;
+    }
+    // s + x = t + e exactly (TwoSum)
+    static __device__ __forceinline__ R two_sum(R s, R x, R &e)
+    {
+        const R t = s + x;
+        const R b = t - s;
+        e = (s - (t - b)) + (x - b);
+        return t;
     }
     static __device__ __forceinline__ void kahan(R *s, R *c, R x)
     {
@@ -83,15 +93,13 @@ struct Diag {
             R m = rho0, e = R(0);
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                const R x = S::stored(f[i]);
-                const R t = m + x;
-                e += x - (t - m);
-                m = t;
+                R ei;
+                m = two_sum(m, S::stored(f[i]), ei);
+                e += ei;
             }
-            const R H = h[0];
-            const R t = H + m;
-            h[256] += (m - (t - H)) + e;
-            h[0] = t;
+            R eh;
+            h[0] = two_sum(h[0], m, eh);
+            h[256] += eh + e;
             kahan(h + 512, h + 1280, rho * ux);
             kahan(h + 768, h + 1536, rho * uy);
             kahan(h + 1024, h + 1792, rho * uz);
@@ -295,7 +303,8 @@ __device__ __forceinline__ void update_cell(StoreT *__restrict__ A, StoreT *__re
     R f[kQ];
     gather_cell<KIND, FACE, MASK>(f, A, B, nb, fc, x, y, z, cell, m, k.base);
     R rho, ux, uy, uz;
-    collide<kQ, FORCE, R, kAccurate>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+    constexpr bool kRcp = !(KIND == SWEEP_AA_NBR && sizeof(R) == 4);
+    collide<kQ, FORCE, R, kAccurate, kMrt, kRcp>(f, k, k.r, k.rho0, rho, ux, uy, uz);
     dg.add(f, k.rho0, rho, ux, uy, uz);
     scatter_cell<KIND, FACE, MASK>(f, A, Bout, B, nb, fc, x, y, z, cell, m, k.base);
 }

@@ -71,6 +71,7 @@ struct Rates {
     R rest;          // 1 - omega+
     R alpha, beta;   // 1 - (omega+ + omega-)/2, (omega- - omega+)/2
     R pw[4], mw[4];  // omega+ w_c, 3 omega- w_c
+    R pq[4];         // 4.5 omega+ w_c
 };
 
 // Collision constants, in the arithmetic type R of the sweep.
@@ -84,6 +85,7 @@ struct Coll {
     R F[3];                // body force
     R rho0;                // deviation base density of the storage (rho0 for *_DEV, else 0)
     R base[27];            // storage offset per direction (w_i rho0 for *_DEV storages, else 0)
+    R mrt_d[4];            // MRT: rate minus the TRT rate of the bulk, fourth-, fifth-, sixth-order groups
 };
 
 // Pair-form rates for omega+ / omega- (host or device).
@@ -99,6 +101,7 @@ __host__ __device__ __forceinline__ Rates<R> rates_of(R wp, R wm, const R (&wc)[
     for (int c = 0; c < 4; ++c) {
         r.pw[c] = wp * wc[c];
         r.mw[c] = R(3) * wm * wc[c];
+        r.pq[c] = R(4.5) * wp * wc[c];
     }
     return r;
 }
@@ -183,6 +186,143 @@ struct Storage<__half> {
     static __device__ __forceinline__ R stored(R v) { return __half2float(__float2half_rn(v)); }
 };
 
+// 1/x for the density of a cell (x > 0, normal): the hardware's approximate reciprocal refined
+// by Newton-Raphson steps y <- y + y (1 - x y) with the residual taken by an FMA (Markstein's
+// form; each step squares the relative error): two steps for FP64, one for FP32, which leaves
+// the result within about one unit in the last place of 1/x.
+__device__ __forceinline__ double recip(double x)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+__device__ __forceinline__ float recip(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return fmaf(y, fmaf(-x, y, 1.0f), y);
+}
+
+// ---------------------------------------------------------------------------------------
+// MRT groups (Eq. 3 with a diagonal S of one rate per group of moments).  The moment space is
+// spanned by polynomials of c grouped by degree and made orthogonal, group against lower
+// groups, under the weighted product <a, b> = sum_i w_i a(c_i) b(c_i): momentum; shear (5);
+// bulk |c|^2 - 1; third order; fourth order; (D3Q27) fifth and sixth order.  With the even
+// groups relaxed at omega+ and the odd ones at omega- the operator is TRT, so MRT is computed
+// as TRT (omega+ = the shear rate, omega- = the third-order rate) plus, for each group g whose
+// rate differs by d_g from its TRT rate, the term
+//   -d_g P_g (f - feq + S/2),   (P_g h)_i = w_i sum_k p_k(c_i) [G_g^-1 m_g(h)]_k,
+// m_g(h)_k = sum_i p_k(c_i) h_i, G_g the Gram matrix of the group's polynomials p_k.  The
+// equilibrium and the Guo source are w_i times polynomials of degree <= 2, so their moments
+// vanish in every group of degree >= 3; in the bulk group m(feq) = rho u.u and m(S) = 2 u.F.
+// (The momentum rate drops out under Guo forcing and needs no term.)  Polynomials:
+//   bulk: |c|^2 - 1, <p, p> = 2/3 (both lattices);
+//   D3Q19 fourth order: q_ab = ca^2 cb^2 - (ca^2 + cb^2)/3 + cc^2/6 + 1/18 for ab = xy, xz, yz,
+//     Gram matrix 7/162 on and -1/81 off the diagonal, G^-1 = 18 I + 12 J;
+//   D3Q27 (h(a) = a^2 - 1/3): fourth order h(ca) h(cb) (<p,p> = 4/81) and cb cc h(ca) (2/81),
+//     fifth order h(cb) h(cc) ca (4/243), sixth order h(cx) h(cy) h(cz) (8/729); orthogonal.
+// ---------------------------------------------------------------------------------------
+__host__ __device__ constexpr double mrt_h(int a) { return a * a - 1.0 / 3.0; }
+__host__ __device__ constexpr double mrt_bulk(int x, int y, int z) { return x * x + y * y + z * z - 1.0; }
+__host__ __device__ constexpr double mrt_q19(int a, int b, int c)
+{
+    return a * a * b * b - (a * a + b * b) / 3.0 + c * c / 6.0 + 1.0 / 18.0;
+}
+
+// Moments of the pre-collision populations in the corrected groups: even ones from the pair
+// sums (and the rest population), odd ones from the pair differences.
+template <int Q, class R>
+struct MrtMoments {
+    R mb;     // bulk
+    R m4[6];  // fourth order: D3Q19 xy, xz, yz; D3Q27 h h (xy, xz, yz), then c c h (x, y, z)
+    R m5[3];  // fifth order (D3Q27): x, y, z
+    R m6;     // sixth order (D3Q27)
+    __device__ __forceinline__ void rest(R f0)
+    {
+        mb = -f0;
+        if (Q == 19) {
+            for (int k = 0; k < 3; ++k) m4[k] = R(mrt_q19(0, 0, 0)) * f0;
+        } else {
+            for (int k = 0; k < 3; ++k) m4[k] = R(mrt_h(0) * mrt_h(0)) * f0;
+            for (int k = 3; k < 6; ++k) m4[k] = R(0);
+            for (int k = 0; k < 3; ++k) m5[k] = R(0);
+            m6 = R(mrt_h(0) * mrt_h(0) * mrt_h(0)) * f0;
+        }
+    }
+    // pair (i, opp i) with sum s and difference d; (x, y, z) = c_i
+    __device__ __forceinline__ void pair(int x, int y, int z, R s, R d)
+    {
+        if (mrt_bulk(x, y, z) != 0.0) mb = fma(R(mrt_bulk(x, y, z)), s, mb);
+        if (Q == 19) {
+            m4[0] = fma(R(mrt_q19(x, y, z)), s, m4[0]);
+            m4[1] = fma(R(mrt_q19(x, z, y)), s, m4[1]);
+            m4[2] = fma(R(mrt_q19(y, z, x)), s, m4[2]);
+        } else {
+            m4[0] = fma(R(mrt_h(x) * mrt_h(y)), s, m4[0]);
+            m4[1] = fma(R(mrt_h(x) * mrt_h(z)), s, m4[1]);
+            m4[2] = fma(R(mrt_h(y) * mrt_h(z)), s, m4[2]);
+            if (y * z != 0) m4[3] = fma(R(y * z * mrt_h(x)), s, m4[3]);
+            if (x * z != 0) m4[4] = fma(R(x * z * mrt_h(y)), s, m4[4]);
+            if (x * y != 0) m4[5] = fma(R(x * y * mrt_h(z)), s, m4[5]);
+            if (x != 0) m5[0] = fma(R(x * mrt_h(y) * mrt_h(z)), d, m5[0]);
+            if (y != 0) m5[1] = fma(R(y * mrt_h(x) * mrt_h(z)), d, m5[1]);
+            if (z != 0) m5[2] = fma(R(z * mrt_h(x) * mrt_h(y)), d, m5[2]);
+            m6 = fma(R(mrt_h(x) * mrt_h(y) * mrt_h(z)), s, m6);
+        }
+    }
+};
+
+// The corrections' coefficients: y_g = d_g G_g^-1 m_g (bulk: of m - rho u.u + u.F), and the
+// correction of direction c = w [even(c) + odd(c)], even(c) = sum over the even groups of
+// p_k(c) y_k, odd(c) likewise (the fifth order).
+template <int Q, class R>
+struct MrtCorr {
+    R yb, y4[6], y5[3], y6;
+    __device__ __forceinline__ MrtCorr() {}
+    __device__ __forceinline__ MrtCorr(const MrtMoments<Q, R> &m, const R (&d)[4], R rho, R usq, R uF)
+    {
+        yb = d[0] * R(1.5) * (m.mb - rho * usq + uF);
+        if (Q == 19) {
+            const R t = R(12) * (m.m4[0] + m.m4[1] + m.m4[2]);
+            for (int k = 0; k < 3; ++k) y4[k] = d[1] * fma(R(18), m.m4[k], t);
+        } else {
+            for (int k = 0; k < 3; ++k) y4[k] = d[1] * R(81.0 / 4.0) * m.m4[k];
+            for (int k = 3; k < 6; ++k) y4[k] = d[1] * R(81.0 / 2.0) * m.m4[k];
+            for (int k = 0; k < 3; ++k) y5[k] = d[2] * R(243.0 / 4.0) * m.m5[k];
+            y6 = d[3] * R(729.0 / 8.0) * m.m6;
+        }
+    }
+    __device__ __forceinline__ R even(int x, int y, int z, R w) const
+    {
+        R e = R(0);
+        if (mrt_bulk(x, y, z) != 0.0) e = R(mrt_bulk(x, y, z)) * yb;
+        if (Q == 19) {
+            e = fma(R(mrt_q19(x, y, z)), y4[0], e);
+            e = fma(R(mrt_q19(x, z, y)), y4[1], e);
+            e = fma(R(mrt_q19(y, z, x)), y4[2], e);
+        } else {
+            e = fma(R(mrt_h(x) * mrt_h(y)), y4[0], e);
+            e = fma(R(mrt_h(x) * mrt_h(z)), y4[1], e);
+            e = fma(R(mrt_h(y) * mrt_h(z)), y4[2], e);
+            if (y * z != 0) e = fma(R(y * z * mrt_h(x)), y4[3], e);
+            if (x * z != 0) e = fma(R(x * z * mrt_h(y)), y4[4], e);
+            if (x * y != 0) e = fma(R(x * y * mrt_h(z)), y4[5], e);
+            e = fma(R(mrt_h(x) * mrt_h(y) * mrt_h(z)), y6, e);
+        }
+        return w * e;
+    }
+    __device__ __forceinline__ R odd(int x, int y, int z, R w) const
+    {
+        if (Q == 19) return R(0);
+        R o = R(0);
+        if (x != 0) o = fma(R(x * mrt_h(y) * mrt_h(z)), y5[0], o);
+        if (y != 0) o = fma(R(y * mrt_h(x) * mrt_h(z)), y5[1], o);
+        if (z != 0) o = fma(R(z * mrt_h(x) * mrt_h(y)), y5[2], o);
+        return w * o;
+    }
+};
+
 // ---------------------------------------------------------------------------------------
 // Collision operator (Eq. 2-3 of the paper with SRT/TRT relaxation and Guo forcing), fused
 // over opposite direction pairs.  TRT per pair (i, o = opp(i)), with s = f_i + f_o and
@@ -192,32 +332,42 @@ struct Storage<__half> {
 //   feq+ = w rho (1 + 4.5 (c.u)^2 - 1.5 u.u),  feq- = 3 w rho c.u,
 //   S+ = w (9 (c.u)(c.F) - 3 u.F),  S- = 3 w c.F,  rho u = sum c f + F/2
 // (SRT is the case w- = w+).  Collecting f_i and f_o:
-//   f*_i = alpha f_i + beta f_o + P + M,   f*_o = alpha f_o + beta f_i + P - M
-//   alpha = 1 - (w+ + w-)/2,  beta = (w- - w+)/2,  P = w+ feq+ + a+ S+,  M = w- feq- + a- S-.
-// The same update holds for values stored as deviations v_i = f_i - w_i rho0 (rho0 = the
-// deviation base; 0 for plain storage): since alpha + beta - 1 = -w+, the shift folds into P
-// through rb = rho (1 - 1.5 u.u) - rho0, and rho = rho0 + sum v, rho u = sum c v + F/2
-// (sum w = 1, sum w c = 0).  P, M use per-class constants w+ w, 3 w- w (Rates) and the
-// per-direction Guo constants of Coll.
+//   f*_i = alpha f_i + beta f_o + P + M,   f*_o = alpha f_o + beta f_i + P - M,
+//   alpha = 1 - (w+ + w-)/2,  beta = (w- - w+)/2,
+//   P = w+ feq+ + a+ S+ = (4.5 w+ w rho) (c.u)^2 + (9 a+ w c.F)(c.u) + (w+ w rb - 3 a+ w u.F),
+//   M = w- feq- + a- S- = (3 w- w rho)(c.u) + 3 a- w c.F,
+// with rb = rho (1 - 1.5 u.u): per pair two FMAs for P (the brackets are per weight class or
+// per direction), one for M, two each for f*_i and f*_o after P + M and P - M.  At w+ = w- = 0
+// (alpha = 1, beta = 0, P = M = 0) the update is the identity bit for bit.  The same update
+// holds for values stored as deviations v_i = f_i - w_i rho0 (rho0 = the deviation base; 0 for
+// plain storage): since alpha + beta - 1 = -w+ the shift folds into P through
+// rb = rho (1 - 1.5 u.u) - rho0, and rho = rho0 + sum v, rho u = sum c v + F/2 (sum w = 1,
+// sum w c = 0).
 // ---------------------------------------------------------------------------------------
 // ACCURATE: relax the non-equilibrium parts s/2 - feq+ and d/2 - feq- first (the form of the
-// equations above), for full populations stored in FP32: the pair form below adds terms of
+// first two equations), for full populations stored in FP32: the pair form adds terms of
 // about 2 f that cancel, which near omega+ = 2 (tau -> 1/2) gives 2-3 times the rounding error
-// of this form; the pair form takes about 3 fewer instructions per pair and is used where the
+// of this form; the pair form takes fewer instructions per pair and is used where the
 // arithmetic is FP64 (rounding far below any tolerance) or the stored values are deviations.
-template <int Q, bool FORCE, class R, bool ACCURATE = false>
+// MRT: add the group corrections above (rates in k.mrt_d; zero rates leave the TRT result).
+// RCP: 1/rho from recip (above) instead of the IEEE division; the FP32 AA neighbour sweeps
+// keep the division, with which the register allocator spills less there (measured).
+template <int Q, bool FORCE, class R, bool ACCURATE = false, bool MRT = false, bool RCP = true>
 __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates<R> &rt, R rho0, R &rho_out,
                                         R &ux_out, R &uy_out, R &uz_out)
 {
     using L = Lattice<Q>;
-    // moments from the pair sums / differences (pass 2 does not need them again)
+    // moments from the pair sums / differences
     R rho = rho0 + f[0], jx = R(0), jy = R(0), jz = R(0);
+    MrtMoments<Q, R> mm;
+    if (MRT) mm.rest(f[0]);
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         if (L::opp(i) < i) continue;
         const int o = L::opp(i);
         const R si = f[i] + f[o];
         const R di = f[i] - f[o];
+        if (MRT) mm.pair(L::cx(i), L::cy(i), L::cz(i), si, di);
         rho += si;
         if (L::cx(i) > 0) jx += di;
         if (L::cx(i) < 0) jx -= di;
@@ -227,7 +377,7 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
         if (L::cz(i) < 0) jz -= di;
     }
     R ux, uy, uz;
-    const R inv = R(1) / rho;
+    const R inv = RCP ? recip(rho) : R(1) / rho;
     if (FORCE) {
         ux = (jx + R(0.5) * k.F[0]) * inv;
         uy = (jy + R(0.5) * k.F[1]) * inv;
@@ -248,6 +398,9 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
 #pragma unroll
     for (int c = 0; c < 4; ++c) buF[c] = FORCE ? k.bw[c] * uF : R(0);
     const R wp = rt.wp, wm = rt.wm;
+    // MRT corrections (bulk, fourth..sixth order); the bulk term needs the pre-collision
+    // velocity, hence after u
+    const MrtCorr<Q, R> mc = MRT ? MrtCorr<Q, R>(mm, k.mrt_d, rho, usq, uF) : MrtCorr<Q, R>();
     {
         R f0;
         if (ACCURATE) {
@@ -257,7 +410,16 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
             f0 = rt.rest * f[0] + rt.pw[0] * rb;
         }
         if (FORCE) f0 -= buF[0];
+        if (MRT) f0 -= mc.even(0, 0, 0, R(L::w(0)));
         f[0] = f0;
+    }
+    // per weight class (pair form): 4.5 w+ w rho, w+ w rb - 3 a+ w u.F, 3 w- w rho
+    R kq[4], p0[4], mr[4];
+#pragma unroll
+    for (int c = 1; c < 4; ++c) {
+        kq[c] = rt.pq[c] * rho;
+        p0[c] = FORCE ? fma(rt.pw[c], rb, -buF[c]) : rt.pw[c] * rb;
+        mr[c] = rt.mw[c] * rho;
     }
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -271,9 +433,9 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
         if (L::cy(i) < 0) cu -= uy;
         if (L::cz(i) > 0) cu += uz;
         if (L::cz(i) < 0) cu -= uz;
-        const R rcu = rho * cu;
-        const R fi = f[i], fo = f[o];
         if (ACCURATE) {
+            const R rcu = rho * cu;
+            const R fi = f[i], fo = f[o];
             const R w = R(L::w(i));
             const R ep = fma(R(0.5), fi + fo, -w * fma(R(4.5) * cu, rcu, rb));  // s/2 - feq+
             const R em = fma(R(0.5), fi - fo, -R(3) * w * rcu);                 // d/2 - feq-
@@ -284,15 +446,22 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
                 gi += sp + k.fc[i];
                 go += sp - k.fc[i];
             }
+            if (MRT) {
+                const R E = mc.even(L::cx(i), L::cy(i), L::cz(i), R(L::w(i)));
+                const R O = mc.odd(L::cx(i), L::cy(i), L::cz(i), R(L::w(i)));
+                gi -= E + O;
+                go -= E - O;
+            }
             f[i] = gi;
             f[o] = go;
         } else {
-            R P = rt.pw[c] * fma(R(4.5) * cu, rcu, rb);
-            R M = rt.mw[c] * rcu;
-            if (FORCE) {
-                P = fma(k.fa[i], cu, P) - buF[c];
-                M += k.fc[i];
+            R P = FORCE ? fma(cu, fma(kq[c], cu, k.fa[i]), p0[c]) : fma(kq[c] * cu, cu, p0[c]);
+            R M = FORCE ? fma(mr[c], cu, k.fc[i]) : mr[c] * cu;
+            if (MRT) {
+                P -= mc.even(L::cx(i), L::cy(i), L::cz(i), R(L::w(i)));
+                M -= mc.odd(L::cx(i), L::cy(i), L::cz(i), R(L::w(i)));
             }
+            const R fi = f[i], fo = f[o];
             f[i] = fma(rt.alpha, fi, fma(rt.beta, fo, P + M));
             f[o] = fma(rt.alpha, fo, fma(rt.beta, fi, P - M));
         }
@@ -300,11 +469,11 @@ __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k, const Rates
 }
 
 // Collision of full populations f (not deviations) with the context's constant rates.
-template <int Q, bool FORCE, class R>
+template <int Q, bool FORCE, class R, bool MRT = false>
 __device__ __forceinline__ void collide(R (&f)[Q], const Coll<R> &k)
 {
     R rho, ux, uy, uz;
-    collide<Q, FORCE, R>(f, k, k.r, R(0), rho, ux, uy, uz);
+    collide<Q, FORCE, R, false, MRT>(f, k, k.r, R(0), rho, ux, uy, uz);
 }
 
 // Moments of a stored post-collision state, in FP64: rho = sum f*, j = sum c f* - F/2.

@@ -115,5 +115,10 @@ LBM_DECLARE(27, 1)
 LBM_DECLARE(27, 2)
 LBM_DECLARE(27, 3)
 #undef LBM_DECLARE
+// MRT sweeps (FP64 and FP32 storage)
+cudaError_t launch_sweep_mrt_19_0(const SweepArgs &s);
+cudaError_t launch_sweep_mrt_19_1(const SweepArgs &s);
+cudaError_t launch_sweep_mrt_27_0(const SweepArgs &s);
+cudaError_t launch_sweep_mrt_27_1(const SweepArgs &s);
 
 }  // namespace lbm

@@ -10,6 +10,10 @@
 #ifndef LBM_ST
 #define LBM_ST 1
 #endif
+// -DLBM_MRT_SWEEP=1: the sweep object of the MRT collision (launch_sweep_mrt_<Q>_<ST>)
+#ifndef LBM_MRT_SWEEP
+#define LBM_MRT_SWEEP 0
+#endif
 
 namespace lbm {
 #if LBM_ST == 0

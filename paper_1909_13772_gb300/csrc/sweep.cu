@@ -1,7 +1,8 @@
 // sweep.cu -- fused stream-collide sweeps (two-grid pull, AA local, AA neighbour).
 //
 // Compiled once per (stencil, storage) pair: -DLBM_Q=19|27 -DLBM_ST=0..3 (fp64, fp32,
-// bf16-deviation, fp16-deviation).  Each object defines launch_sweep_<Q>_<ST>.
+// bf16-deviation, fp16-deviation).  Each object defines launch_sweep_<Q>_<ST>; with -DLBM_MRT_SWEEP=1
+// (FP64 and FP32 storage) the same sweeps with the MRT collision, launch_sweep_mrt_<Q>_<ST>.
 //
 // Method: Eq. 2 of the paper with the stream and collision steps fused into one pass over
 // the cells (Sec. 5.1.2), pull form: each cell gathers the PDFs streaming into it, collides
@@ -138,7 +139,7 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
                 f[i] = S::raw_rw(row0 + (size_t)i * rows * RW + e);
             }
             R rho, ux, uy, uz;
-            collide<kQ, FORCE, R, kAccurate>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+            collide<kQ, FORCE, R, kAccurate, kMrt>(f, k, k.r, k.rho0, rho, ux, uy, uz);
             dg.add(f, k.rho0, rho, ux, uy, uz);
             const int64_t cell = B.cell(x, y, z);
 #pragma unroll
@@ -282,7 +283,11 @@ cudaError_t go_kind(const SweepArgs &s, const Coll<R> &k)
 
 }  // namespace
 
+#if LBM_MRT_SWEEP
+cudaError_t LBM_CAT(launch_sweep_mrt_, LBM_Q, LBM_ST)(const SweepArgs &s)
+#else
 cudaError_t LBM_CAT(launch_sweep_, LBM_Q, LBM_ST)(const SweepArgs &s)
+#endif
 {
     if (s.tx * s.ty > 256 || s.tx % 32 != 0) return cudaErrorInvalidConfiguration;
     const Coll<R> &k = coll_of(s.cd, s.cf, (R *)nullptr);

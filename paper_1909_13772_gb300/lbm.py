@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 D3Q19, D3Q27 = 19, 27
-SRT, TRT = 0, 1
+SRT, TRT, MRT = 0, 1, 2
 FP64, FP32, BF16_DEV, FP16_DEV = 0, 1, 2, 3
 TWO_GRID, AA = 0, 1
 FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
@@ -32,7 +32,7 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("stencil", ctypes.c_int32), ("collision", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("pattern", ctypes.c_int32), ("omega", ctypes.c_double), ("magic_lambda", ctypes.c_double),
                 ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("periodic", ctypes.c_int32 * 3),
-                ("diag_interval", ctypes.c_int32)]
+                ("diag_interval", ctypes.c_int32), ("mrt_rates", ctypes.c_double * 4)]
 
 
 class lbm_block_desc(ctypes.Structure):
@@ -462,7 +462,9 @@ def lbm_destroy(ctx):
 # ---- convenience wrapper ----------------------------------------------------------------
 
 def make_params(stencil=D3Q19, collision=TRT, storage=FP32, pattern=TWO_GRID, omega=1.0, magic_lambda=3.0 / 16.0,
-                force=(0.0, 0.0, 0.0), rho0=1.0, periodic=(1, 1, 1), diag_interval=0) -> lbm_params:
+                force=(0.0, 0.0, 0.0), rho0=1.0, periodic=(1, 1, 1), diag_interval=0, mrt_rates=None) -> lbm_params:
+    """lbm_params; ``mrt_rates`` (MRT only): rates of the bulk, fourth-, fifth- and sixth-order
+    groups, default the TRT rates of their parity (omega, omega, omega-, omega)."""
     p = lbm_params()
     p.stencil, p.collision, p.storage, p.pattern = stencil, collision, storage, pattern
     p.omega, p.magic_lambda, p.rho0 = float(omega), float(magic_lambda), float(rho0)
@@ -470,6 +472,11 @@ def make_params(stencil=D3Q19, collision=TRT, storage=FP32, pattern=TWO_GRID, om
         p.force[a] = float(force[a])
         p.periodic[a] = int(bool(periodic[a]))
     p.diag_interval = int(diag_interval)
+    if mrt_rates is None:
+        wm = 1.0 / (magic_lambda / (1.0 / omega - 0.5) + 0.5) if omega > 0 else 2.0
+        mrt_rates = (omega, omega, wm, omega)
+    for g in range(4):
+        p.mrt_rates[g] = float(mrt_rates[g])
     return p
 
 

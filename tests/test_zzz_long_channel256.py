@@ -4,17 +4,23 @@ steps, in FP64 and FP32, two-grid and AA -- the launch configuration the benchma
 
 The flow is invariant in x and z, so every column of the field must equal the oracle's run of
 one 1 x 256 x 1 periodic column for the same 10,000 steps.  Compared: eight seeded columns, one
-full x-y plane and one full y-z plane (every column of those), PDFs against the gate (1e-12
-FP64, 1e-5 FP32 of max|f|), and the flow signal itself -- the deviations f_i - w_i and the
-velocity -- against the derived rounding gates of flow_gates: after 10,000 steps from rest the
-centre-line velocity is ~1e-2, so a wrong force or boundary term is far outside them.
+full x-y plane and one full y-z plane (every column of those).  Every column does the same
+arithmetic, so all of them are equal bit for bit.  FP64: PDFs within 1e-12 of max|f| and the
+flow signal itself -- the deviations f_i - w_i and the velocity -- within the derived rounding
+gates of flow_gates; after 10,000 steps from rest the centre-line velocity is ~1e-2, so a
+wrong force or boundary term is far outside them.  FP32: plain FP32 populations (f ~ w, ulp
+~ 4e-9) cannot carry 10,000 increments of ~1e-7 without drift -- the roundings of a slowly
+varying cell repeat their sign and the mass drifts linearly (7e-5 after 10,000 steps, the
+same in a float32 emulation of the column) -- so the FP32 gates are the linear-growth ones
+(flow_gates growth="linear", and 2 n u max|f| on the PDFs); the 1e-5 gate of FP32 holds at
+the short runs of the other tests.
 
 Run time: the FP64 steps take about a minute per pattern on one GB300 (FP64-pipe bound)."""
 import numpy as np
 import pytest
 
 import oracle
-from gpu_helpers import TOL, Case, flow_gates, oracle_run
+from gpu_helpers import TOL, UNIT_ROUNDOFF, Case, flow_gates, oracle_run
 from paper_1909_13772_gb300 import inputs, lbm
 
 pytestmark = pytest.mark.gpu
@@ -60,10 +66,13 @@ def test_channel256_10k_steps_equals_column_oracle(column, storage, pattern):
     # the walls), so the deviations carry the signal the gates below look at
     c, _, _ = oracle.lattice(19)
     assert (c[:, 0] @ want[:, N // 2]) / want[:, N // 2].sum() > 5e-3
+    growth = "sqrt" if storage == lbm.FP64 else "linear"
+    tol = TOL[storage] if storage == lbm.FP64 else 2.0 * STEPS * UNIT_ROUNDOFF[storage]
+    ref = got[0]
     for g in got:
-        assert np.abs(g - want).max() <= TOL[storage] * fmax
-        flow_gates(g, want, storage, STEPS, 19)
+        assert np.array_equal(g, ref)
     for a in range(N):
-        assert np.abs(xy[:, :, a] - want).max() <= TOL[storage] * fmax, ("x", a)
-        assert np.abs(yz[:, a, :] - want).max() <= TOL[storage] * fmax, ("z", a)
-    flow_gates(xy.transpose(0, 2, 1).reshape(19, -1), np.tile(want, (1, N)), storage, STEPS, 19)
+        assert np.array_equal(xy[:, :, a], ref), ("x", a)
+        assert np.array_equal(yz[:, a, :], ref), ("z", a)
+    assert np.abs(ref - want).max() <= tol * fmax
+    flow_gates(ref, want, storage, STEPS, 19, growth=growth)
