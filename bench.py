@@ -46,14 +46,22 @@ LAMBDA = 3.0 / 16.0
 METRIC = "MLUPS (lattice updates per second) of the fused stream-collide step and % of HBM roofline"
 WORKLOAD = "D3Q19 TRT (Lambda=3/16, tau=1) channel 256^3, no-slip walls in y, periodic x/z, body force 1e-6"
 VARIANTS = {
-    "fp32-twogrid": ("FP32", "TWO_GRID"),
-    "fp32-aa": ("FP32", "AA"),
-    "fp64-twogrid": ("FP64", "TWO_GRID"),
-    "fp64-aa": ("FP64", "AA"),
-    "fp16dev-twogrid": ("FP16_DEV", "TWO_GRID"),
-    "fp16dev-aa": ("FP16_DEV", "AA"),
-    "bf16dev-twogrid": ("BF16_DEV", "TWO_GRID"),
+    "fp32-twogrid": ("FP32", "TWO_GRID", "TRT"),
+    "fp32-aa": ("FP32", "AA", "TRT"),
+    "fp64-twogrid": ("FP64", "TWO_GRID", "TRT"),
+    "fp64-aa": ("FP64", "AA", "TRT"),
+    "fp16dev-twogrid": ("FP16_DEV", "TWO_GRID", "TRT"),
+    "fp16dev-aa": ("FP16_DEV", "AA", "TRT"),
+    "bf16dev-twogrid": ("BF16_DEV", "TWO_GRID", "TRT"),
+    "fp32-mrt-twogrid": ("FP32", "TWO_GRID", "MRT"),
+    "fp64-mrt-twogrid": ("FP64", "TWO_GRID", "MRT"),
 }
+# MRT variants: shear rate omega, third order omega- (Lambda), bulk and fourth-order rates below
+# (the fifth and sixth groups exist on D3Q27 only)
+MRT_RATES = (1.4, 1.2, 1.0, 1.0)
+# stated error of each variant: the channel after ERROR_STEPS steps against the oracle's column
+ERROR_STEPS = 2000
+ERROR_SHAPE = (32, 256, 32)
 
 
 def log(*a):
@@ -70,6 +78,8 @@ def dist_setup(backend=None):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
+        if dist.is_initialized():
+            return rank, world, local
         if backend is None:
             backend = "nccl" if torch.cuda.is_available() else "gloo"
         if backend == "nccl":
@@ -237,45 +247,55 @@ def recorded_traffic(variant: str):
 # ---------------------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------------------
-def make_sim(lbm, storage, pattern, stream, tile=None):
-    p = lbm.make_params(stencil=lbm.D3Q19, collision=lbm.TRT, storage=getattr(lbm, storage),
+def make_sim(lbm, storage, pattern, stream, tile=None, collision="TRT", shape=SHAPE):
+    p = lbm.make_params(stencil=lbm.D3Q19, collision=getattr(lbm, collision), storage=getattr(lbm, storage),
                         pattern=getattr(lbm, pattern), omega=OMEGA, magic_lambda=LAMBDA, force=FORCE,
-                        periodic=(1, 0, 1))
-    sim = lbm.Simulation(p, [((0, 0, 0), SHAPE)], stream=stream)
+                        periodic=(1, 0, 1), mrt_rates=MRT_RATES if collision == "MRT" else None)
+    sim = lbm.Simulation(p, [((0, 0, 0), shape)], stream=stream)
     if tile:
         sim.set_tile(*tile)
     # y faces default to no-slip: walls at y = -1/2 and y = 255.5
     return sim
 
 
-def time_variant(lbm, variant, steps, warmup, world, tile=None):
+def time_variant(lbm, variant, steps, warmup, world, tile=None, min_seconds=0.0, max_repeats=200):
+    """W warm-up steps, then the timed region of exactly K steps (CUDA events on the library's
+    stream, barrier and device synchronisation on both sides), repeated until min_seconds of
+    timed work have run (at most max_repeats times; once when min_seconds is 0) so that the
+    clock sampler sees the GPU under load; the reported time is the median repeat."""
     import torch
-    storage, pattern = VARIANTS[variant]
+    storage, pattern, collision = VARIANTS[variant]
     stream = torch.cuda.Stream()
-    sim = make_sim(lbm, storage, pattern, stream.cuda_stream, tile)
+    sim = make_sim(lbm, storage, pattern, stream.cuda_stream, tile, collision)
     from paper_1909_13772_gb300 import inputs
     rho, u = inputs.rest(SHAPE)
     sim.init(0, rho, u)
     info = sim.info()
     sim.step(warmup)
     torch.cuda.synchronize()
-    barrier(world)
-    launches0 = sim.launches()
     lbm.lbm_read_timing(sim.ctx, reset=True)
     lbm.lbm_enable_timing(sim.ctx, True)
     sampler = ClockSampler(torch.cuda.current_device())
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    start.record(stream)
-    sim.step(steps)
-    end.record(stream)
-    torch.cuda.synchronize()
+    times, launches, spent = [], 0, 0.0
+    while True:
+        barrier(world)
+        launches0 = sim.launches()
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(stream)
+        sim.step(steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        launches = sim.launches() - launches0
+        times.append(start.elapsed_time(end))
+        spent += times[-1] / 1e3
+        if spent >= min_seconds or len(times) >= max_repeats:
+            break
     clocks = sampler.stop()
-    barrier(world)
     lbm.lbm_enable_timing(sim.ctx, False)
     kt = lbm.lbm_read_timing(sim.ctx, reset=True)
-    launches = sim.launches() - launches0
-    ms = start.elapsed_time(end)
+    ms = statistics.median(times)
     diag = sim.reduce()
     sim.close()
     del stream
@@ -290,7 +310,45 @@ def time_variant(lbm, variant, steps, warmup, world, tile=None):
         "sweep_share": kt["sweep"][0] / max(1e-9, kt["sweep"][0] + kt["fill"][0]),
         "sweep_gbs": alg_bytes / (sweep_ms / 1e3) / 1e9, "alg_bytes_per_sweep": alg_bytes, "launches": launches,
         "clocks": clocks, "info": info, "finite": diag["nonfinite"] == 0, "mass": diag["mass"],
+        "repeats": len(times),
     }
+
+
+def variant_error(lbm, variant, steps=ERROR_STEPS):
+    """The variant's stated error against the oracle: the channel run from rest for `steps` steps
+    on a 32 x 256 x 32 box (the flow is x- and z-invariant and every column does the same
+    arithmetic, so its columns are bit for bit those of the 256^3 run) against the oracle's
+    column after the same steps (tests/golden/channel_column_2000.txt, written by its committed
+    generator from the oracle alone).  Normwise errors of the PDFs, of the deviations f_i - w_i
+    and of the velocity u_x(y)."""
+    import importlib.util
+    import torch
+    spec = importlib.util.spec_from_file_location(
+        "make_channel_column", os.path.join(ROOT, "tests", "golden", "make_channel_column.py"))
+    rec = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(rec)
+    if steps != rec.STEPS or tuple(MRT_RATES[:2]) != (rec.MRT_BULK, rec.MRT_FOURTH):
+        return None
+    storage, pattern, collision = VARIANTS[variant]
+    want = rec.read()[collision.lower()]  # [q, y]
+    stream = torch.cuda.Stream()
+    sim = make_sim(lbm, storage, pattern, stream.cuda_stream, None, collision, ERROR_SHAPE)
+    try:
+        from paper_1909_13772_gb300 import inputs
+        rho, u = inputs.rest(ERROR_SHAPE)
+        sim.init(0, rho, u)
+        sim.step(steps)
+        got = sim.pdfs_region(0, (ERROR_SHAPE[0] // 2, 0, ERROR_SHAPE[2] // 2), (1, ERROR_SHAPE[1], 1))[:, 0, :, 0]
+    finally:
+        sim.close()
+    c, w, _ = lbm.lbm_stencil_table(19)
+    cx = c[:, 0].astype(np.float64)
+    ug, uw = cx @ got / got.sum(0), cx @ want / want.sum(0)
+    dev = want - w[:, None]
+    return {"steps": steps, "pdf": float(np.abs(got - want).max() / np.abs(want).max()),
+            "deviation": float(np.abs(got - want).max() / np.abs(dev).max()),
+            "u": float(np.abs(ug - uw).max() / np.abs(uw).max()),
+            "against": "oracle column after %d steps (tests/golden/channel_column_2000.txt)" % steps}
 
 
 def time_e2e(lbm, variant, steps, world):
@@ -300,9 +358,9 @@ def time_e2e(lbm, variant, steps, world):
     region."""
     import torch
     from paper_1909_13772_gb300 import inputs
-    storage, pattern = VARIANTS[variant]
+    storage, pattern, collision = VARIANTS[variant]
     stream = torch.cuda.Stream()
-    sim = make_sim(lbm, storage, pattern, stream.cuda_stream)
+    sim = make_sim(lbm, storage, pattern, stream.cuda_stream, None, collision)
     rho, u = inputs.rest(SHAPE)
     rho_h = torch.from_numpy(rho).pin_memory().numpy()
     u_h = torch.from_numpy(u).pin_memory().numpy()
@@ -325,28 +383,42 @@ def time_e2e(lbm, variant, steps, world):
     lups, _ = aggregate(cells * steps, dt, world)
     n = rho.size
     return {"value": lups / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(4 * n * 8 / steps),
-            "d2h_bytes_per_step": int((4 * n * 8) / steps + 64)}
+            "d2h_bytes_per_step": int((4 * n * 8) / steps + 64), "steps": steps,
+            "per_call": "fields up once, %d x (lbm_step(1) + step diagnostics read back), fields down once" % steps}
 
 
-def cpu_baseline(min_seconds=10.0, max_steps=200):
-    """The oracle as it stands, on the host cores, on a 256 x 256 x 8 slab of the channel."""
+def cpu_baseline(min_seconds=10.0, max_steps=200, single_seconds=5.0):
+    """The oracle as it stands, on the host cores, on a 256 x 256 x 8 slab of the channel; and on
+    one core (the same slab, fewer steps)."""
     import oracle
     from paper_1909_13772_gb300 import inputs
     shape = (SHAPE[0], SHAPE[1], 8)
     p = oracle.OracleParams(shape=shape, q=19, collision=oracle.TRT, omega=OMEGA, magic_lambda=LAMBDA, force=FORCE,
                             periodic=(1, 0, 1), face_kind=(1, 1, 1, 1, 1, 1))
     rho, u = inputs.rest(shape)
-    f = oracle.init(p, rho, u)
-    f = oracle.run(p, f, 1)
-    steps, t = 0, 0.0
-    while t < min_seconds and steps < max_steps:
-        t0 = time.perf_counter()
-        f = oracle.run(p, f, 1)
-        t += time.perf_counter() - t0
-        steps += 1
     cells = shape[0] * shape[1] * shape[2]
-    return {"value": cells * steps / t / 1e6, "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": "%d oracle steps of a 256x256x8 slab of the channel (FP64, D3Q19 TRT, walls in y)" % steps}
+
+    def rate(limit, cap):
+        f = oracle.run(p, oracle.init(p, rho, u), 1)
+        steps, t = 0, 0.0
+        while steps == 0 or (t < limit and steps < cap):
+            t0 = time.perf_counter()
+            f = oracle.run(p, f, 1)
+            t += time.perf_counter() - t0
+            steps += 1
+        return steps, t
+
+    cores = oracle.get_threads()
+    steps, t = rate(min_seconds, max_steps)
+    oracle.set_threads(1)
+    try:
+        s1, t1 = rate(single_seconds, max_steps)
+    finally:
+        oracle.set_threads(cores)
+    return {"value": cells * steps / t / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d oracle steps of a 256x256x8 slab of the channel (FP64, D3Q19 TRT, walls in y)" % steps,
+            "single_thread": {"value": cells * s1 / t1 / 1e6, "unit": "MLUPS", "cores": 1,
+                              "sample": "%d oracle steps of the same slab on one core" % s1}}
 
 
 def _oracle_rate(p, rho, u, flags=None, min_seconds=10.0, max_steps=2000):
@@ -401,15 +473,16 @@ def run_ours(args):
     from paper_1909_13772_gb300 import lbm
     lbm.load_library()
     head = args.variant
-    res = time_variant(lbm, head, args.steps, args.warmup, world)
+    res = time_variant(lbm, head, args.steps, args.warmup, world, min_seconds=args.min_seconds)
     variants = {}
     if not args.headline_only:
         for v in VARIANTS:
             if v == head:
                 variants[v] = res
-                continue
-            k = max(10, min(args.steps, 200 if v.startswith("fp64") else args.steps))
-            variants[v] = time_variant(lbm, v, k, args.warmup, world)
+            else:
+                k = max(10, min(args.steps, 200 if v.startswith("fp64") else args.steps))
+                variants[v] = time_variant(lbm, v, k, args.warmup, world)
+            variants[v]["error"] = variant_error(lbm, v)
     e2e = time_e2e(lbm, head, args.steps, world)
     cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     peak, peak_kind = measured_peaks()
@@ -446,13 +519,19 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
+        "timing": {"repeats": res["repeats"], "value_from": "median of the repeats of the K-step timed region "
+                                                            "(each bracketed by barrier + synchronize)"},
+        "stated_error": variants.get(head, {}).get("error"),
         "variants": {k: dict({"mlups": round(v["mlups"], 1), "sweep_gbs": round(v["sweep_gbs"], 1),
                               "frac_hbm": round(v["sweep_gbs"] / peak, 4), "ms_per_step": round(v["ms_per_step"], 4),
-                              "sweep_ms": round(v["sweep_ms"], 4), "fill_ms": round(v["fill_ms"], 4)},
+                              "sweep_ms": round(v["sweep_ms"], 4), "fill_ms": round(v["fill_ms"], 4),
+                              "collision": VARIANTS[k][2], "error_vs_oracle": v.get("error")},
                              **({"fp64_pipe": fp64_pipe(k, v["info"]["cells"], v["sweep_ms"])}
                                 if k.startswith("fp64") else {}))
                      for k, v in variants.items()},
     }
+    if world == 1 and not args.no_workloads:
+        out["workloads"] = measure_workloads(args)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -460,7 +539,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_porous(args):
+def measure_porous(args):
     """Block-structured porous bed: 16^3 = 4096 blocks with edges log-uniform in [16, 64]
     (default_rng(4096)), Boolean sphere packing R = 8, porosity 0.40 (default_rng(7)),
     velocity inlet u = (0.02, 0, 0) at x-, pressure outlet rho = 1 at x+, periodic y/z,
@@ -474,7 +553,7 @@ def run_porous(args):
     blocks, shape, _ = inputs.rectilinear_blocks(nb=(nbk, nbk, nbk), lo=16, hi=64, seed=4096)
     flags = inputs.sphere_packing(shape, radius=8.0, porosity=0.40, seed=7)
     t_geom = time.perf_counter() - t0
-    storage, pattern = VARIANTS[args.variant]
+    storage, pattern = VARIANTS[args.variant][:2]
     p = lbm.make_params(stencil=lbm.D3Q19, collision=lbm.TRT, storage=getattr(lbm, storage),
                         pattern=getattr(lbm, pattern), omega=1 / 0.8, magic_lambda=LAMBDA, periodic=(0, 1, 1))
     stream = torch.cuda.Stream()
@@ -544,19 +623,21 @@ def run_porous(args):
            "roofline": {"bound": "hbm", "achieved": round(alg / (sweep_ms / 1e3) / 1e9, 1), "peak": peak,
                         "unit": "GB/s", "frac": round(alg / (sweep_ms / 1e3) / 1e9 / peak, 4), "traffic": None,
                         "kernel": "k_sweep (fluid cells only)", "sweep_ms": round(sweep_ms, 4),
-                        "fill_ms": round(fill_ms, 4)},
-           "cpu_baseline": cpu_baseline_porous() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None,
+                        "fill_ms": round(fill_ms, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+           # the time a step spends outside its kernels: launch gaps (graph replay when --graph)
+           "launch_gap_ms_per_step": round(tmax * 1e3 / args.steps - sweep_ms - fill_ms, 4),
+           "cpu_baseline": (cpu_baseline_porous(min_seconds=getattr(args, "cpu_seconds", 10.0))
+                            if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None),
            "clocks": clocks, "finite": diag["nonfinite"] == 0, "max_speed": diag["max_speed"],
            "graph": bool(args.graph), "autotuned_tile": list(tuned[0]) if tuned else None,
            "autotuned_in_place": tuned[2] if tuned else None,
            "launch": "one sweep launch per block" if args.per_block else "one batched sweep launch",
            "neighbours": ("in place where faces match" if (tuned[2] if tuned else not args.ghost)
                           else "ghost-layer copies")}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
-def run_tgv(args):
+def measure_tgv(args):
     """C1, the correctness configuration: 2-D Taylor-Green vortex extruded in z on a 32^3 fully
     periodic box, D3Q19 SRT tau = 0.6, FP64, u0 = 0.01.  The state (two 4.7 MB arrays) lives in
     L2, so the step rate is reported without a roofline fraction.  With the tile picked by
@@ -631,10 +712,12 @@ def run_tgv(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (analytic vortex)",
            "config": {"workload": "2-D Taylor-Green vortex extruded in z, 32^3 periodic, D3Q19 SRT tau=0.6, "
                                   "u0=0.01, FP64", "value_from": best},
-           "roofline": None, "cpu_baseline": cpu, "gpu_launches": runs[best]["launches"],
+           "roofline": None,
+           "roofline_note": "L2-resident (two 4.7 MB arrays in the 129 MB L2): no HBM roofline; the FP64 "
+                            "sweep's own bound, the FP64 pipe, is reported on the channel's fp64 variants",
+           "cpu_baseline": cpu, "gpu_launches": runs[best]["launches"],
            "clocks": runs[best]["clocks"], "variants": runs}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+    return out
 
 
 def _spectrum(u):
@@ -650,7 +733,7 @@ def _spectrum(u):
     return np.bincount(shell.ravel(), weights=e.ravel(), minlength=n)[1:n // 2 + 1]
 
 
-def run_turbulence(args):
+def measure_turbulence(args):
     """Decaying turbulence, D3Q27 TRT (Lambda = 3/16), tau = 0.52, periodic box, random-phase
     solenoidal k^(-5/3) start (default_rng(1909), shells 1..32, max|u| = 0.05), rho = 1.
     Throughput: 512^3 for each storage variant.  Error: the same run at 256^3 for the
@@ -668,11 +751,21 @@ def run_turbulence(args):
         return lbm.Simulation(p, [((0, 0, 0), (n, n, n))], stream=stream.cuda_stream)
 
     # throughput at 512^3
-    n_perf, perf_steps = args.turb_size, min(args.steps, 200)
+    n_perf = args.turb_size
+    perf_steps = getattr(args, "turb_perf_steps", None) or min(args.steps, 200)
+    tiled = bool(getattr(args, "turb_tile", False)) and n_perf % 2 == 0
     t0 = time.perf_counter()
-    rho, u = inputs.turbulence(n_perf, seed=1909, kmax=32, umax=0.05)
+    if tiled:
+        # the (n/2)^3 member repeated 2 x 2 x 2 (periodic, so a valid start of the same family up
+        # to the missing odd modes); the sweep's cost does not depend on the field
+        rho, u = inputs.turbulence(n_perf // 2, seed=1909, kmax=min(32, n_perf // 4), umax=0.05)
+        rho, u = np.tile(rho, (2, 2, 2)), np.tile(u, (1, 2, 2, 2))
+    else:
+        rho, u = inputs.turbulence(n_perf, seed=1909, kmax=32, umax=0.05)
     t_gen = time.perf_counter() - t0
     perf = {}
+    peak, peak_kind = measured_peaks()
+    sampler = ClockSampler(torch.cuda.current_device())
     for storage, name in variants:
         if storage == "FP64" and not args.turb_fp64_perf:
             continue
@@ -690,7 +783,8 @@ def run_turbulence(args):
         sim.close()
         alg = 2 * 27 * info["bytes_per_pdf"] * info["cells"]
         perf[name] = {"mlups": round(info["cells"] / (ms / 1e3) / 1e6, 1), "ms_per_step": round(ms, 4),
-                      "gbs": round(alg / (ms / 1e3) / 1e9, 1)}
+                      "gbs": round(alg / (ms / 1e3) / 1e9, 1), "frac_hbm": round(alg / (ms / 1e3) / 1e9 / peak, 4)}
+    clocks = sampler.stop()
     del rho, u
     # per-field error at the error-study size
     n = args.turb_err_size
@@ -724,15 +818,22 @@ def run_turbulence(args):
            "config": {"workload": "D3Q27 TRT tau=0.52 periodic decaying turbulence, k^-5/3 random-phase start, "
                                   "max|u| = 0.05, AA pattern", "throughput_size": n_perf,
                       "throughput_steps": perf_steps, "error_size": n, "error_steps": args.steps,
-                      "generator_s": round(t_gen, 1)},
-           "throughput": perf, "error_vs_fp64": err,
-           "cpu_baseline": cpu_baseline_turbulence() if (rank == 0 and world == 1 and not args.no_cpu_baseline)
-           else None}
-    if rank == 0:
-        print(json.dumps(out), flush=True)
+                      "generator_s": round(t_gen, 1),
+                      "throughput_field": ("the %d^3 member repeated 2x2x2" % (n_perf // 2)) if tiled else
+                      "the %d^3 member" % n_perf,
+                      "error_reference": "the GPU FP64 run of the same start (its kernels match the oracle to "
+                                         "1e-12 on the 64^3 member over 2,000 steps)"},
+           "roofline": ({"bound": "hbm", "achieved": perf["f32"]["gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": perf["f32"]["frac_hbm"], "traffic": None,
+                         "kernel": "k_sweep D3Q27 FP32 AA (one launch per step)",
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind} if "f32" in perf else None),
+           "clocks": clocks, "throughput": perf, "error_vs_fp64": err,
+           "cpu_baseline": (cpu_baseline_turbulence(min_seconds=getattr(args, "cpu_seconds", 10.0))
+                            if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None)}
+    return out
 
 
-def run_closure(args):
+def measure_closure(args):
     """Locally varying relaxation (learned closure, C5 coarse grid): D3Q19 TRT tau0 = 0.502,
     FP32 storage, AA pattern, periodic N^3 box of decaying turbulence (random-phase k^(-5/3)
     start, default_rng(9), shells 1..N/4, max|u| = 0.1).  Each step once with the constant
@@ -788,9 +889,7 @@ def run_closure(args):
     n = sizes[0]
     peak_hbm, peak_kind = measured_peaks()
     if "mlp" not in kinds:
-        if rank == 0:
-            print(json.dumps({"metric": "closure step timings", "variants": res}), flush=True)
-        return
+        return {"metric": "closure step timings", "variants": res}
     sweep_ms = res["mlp-%d" % n]["sweep_ms"]
     clocks = res["mlp-%d" % n]["clocks"]
     sm_clock = (clocks or {}).get("sm_max_mhz") or 2070.0
@@ -821,10 +920,93 @@ def run_closure(args):
                         "tensor_tflops": round(mma_flops / (sweep_ms / 1e3) / 1e12, 2)},
            "cost_vs_constant_rate": {k: round(res["mlp-%d" % k]["ms_per_step"] / res["trt-%d" % k]["ms_per_step"], 3)
                                      for k in sizes if "trt" in kinds},
-           "variants": res, "clocks": res["mlp-%d" % n]["clocks"]}
-    if rank == 0:
+           "variants": res, "clocks": res["mlp-%d" % n]["clocks"],
+           "cpu_baseline": (cpu_baseline_closure(net, min_seconds=getattr(args, "cpu_seconds", 10.0))
+                            if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None)}
+    return out
+
+
+def cpu_baseline_closure(net, min_seconds=10.0, n=32):
+    """The oracle with the network closure (FP64 network, BF16 weights) on an n^3 member of the
+    closure workload's turbulence family."""
+    import oracle
+    from paper_1909_13772_gb300 import inputs
+    rho, u = inputs.turbulence(n, seed=9, kmax=n // 4, umax=0.1)
+    p = oracle.OracleParams(shape=(n, n, n), q=19, collision=oracle.TRT, omega=1 / 0.502, magic_lambda=LAMBDA,
+                            periodic=(1, 1, 1))
+    cl = dict(kind=oracle.MLP, mlp=net)
+    f = oracle.run(p, oracle.init(p, rho, u), 1, closure=cl)
+    steps, t = 0, 0.0
+    while steps == 0 or (t < min_seconds and steps < 2000):
+        t0 = time.perf_counter()
+        f = oracle.run(p, f, 1, closure=cl)
+        t += time.perf_counter() - t0
+        steps += 1
+    return {"value": round(n ** 3 * steps / t / 1e6, 3), "unit": "MLUPS", "cores": oracle.get_threads(),
+            "kind": "oracle", "sample": "%d oracle steps with the network closure on the %d^3 member (FP64)"
+                                        % (steps, n)}
+
+
+
+def _print_rank0(out):
+    if int(os.environ.get("RANK", "0")) == 0:
         print(json.dumps(out), flush=True)
 
+
+def run_porous(args):
+    _print_rank0(measure_porous(args))
+
+
+def run_tgv(args):
+    _print_rank0(measure_tgv(args))
+
+
+def run_turbulence(args):
+    _print_rank0(measure_turbulence(args))
+
+
+def run_closure(args):
+    _print_rank0(measure_closure(args))
+
+
+def measure_workloads(args):
+    """The other configurations, each with its own metric, roofline, oracle figure and clocks,
+    sized to keep the default run within a few minutes (one GPU): C1 the 32^3 Taylor-Green
+    vortex (FP64, the full configuration); C3 D3Q27 decaying turbulence (throughput of the FP32
+    and 16-bit storages at 512^3, per-field errors of every storage against the FP64 run at 128^3
+    after 2,000 steps); C4 the 4096-block porous bed (autotuned tile and neighbour mode, CUDA-graph
+    replay); C5 the learned closure on the 128^3 coarse grid (constant rate, Smagorinsky,
+    network)."""
+    import copy
+    out = {}
+
+    def sub(**kw):
+        a = copy.copy(args)
+        for k, v in kw.items():
+            setattr(a, k, v)
+        return a
+
+    k = args.steps
+    jobs = [
+        ("c1_taylor_green", measure_tgv, sub(steps=max(100, k), cpu_seconds=5.0)),
+        ("c3_turbulence", measure_turbulence, sub(steps=2000, turb_size=512, turb_err_size=128,
+                                                  turb_perf_steps=min(max(k, 20), 100), turb_tile=True,
+                                                  turb_fp64_perf=False, cpu_seconds=5.0)),
+        ("c4_porous_bed", measure_porous, sub(steps=min(max(k, 20), 100), graph=True, autotune=True,
+                                              per_block=False, ghost=False, porous_blocks=16, cpu_seconds=5.0,
+                                              variant="fp32-twogrid")),
+        ("c5_closure", measure_closure, sub(steps=min(max(k, 20), 100), closure_sizes="128",
+                                            closure_kinds="trt,smagorinsky,mlp", cpu_seconds=5.0)),
+    ]
+    for name, fn, a in jobs:
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(a)
+        except Exception as e:  # a failing workload is reported, the headline line still prints
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+        out[name]["wall_s"] = round(time.perf_counter() - t0, 1)
+        log("workload %s: %.1f s" % (name, out[name]["wall_s"]))
+    return out
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
@@ -884,6 +1066,11 @@ def main(argv=None):
     ap.add_argument("--turb-size", type=int, default=512)
     ap.add_argument("--turb-err-size", type=int, default=256)
     ap.add_argument("--turb-fp64-perf", action="store_true")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="channel: leave out the records of the other configurations (C1, C3, C4, C5)")
+    ap.add_argument("--min-seconds", type=float, default=2.0,
+                    help="channel: repeat the K-step timed region until this much timed work has run "
+                         "(the clock sampler needs load); the value is the median repeat")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

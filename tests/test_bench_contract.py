@@ -13,7 +13,7 @@ sys.path.insert(0, ROOT)
 import bench  # noqa: E402
 
 
-def _fake_variant(lbm, variant, steps, warmup, world, tile=None):
+def _fake_variant(lbm, variant, steps, warmup, world, tile=None, min_seconds=0.0, max_repeats=200):
     cells = 256 ** 3
     bpp = 8 if variant.startswith("fp64") else (2 if "dev" in variant else 4)
     sweep_ms = 0.4
@@ -22,7 +22,12 @@ def _fake_variant(lbm, variant, steps, warmup, world, tile=None):
             "fill_ms": 0.0, "sweep_share": 1.0, "sweep_gbs": alg / (sweep_ms / 1e3) / 1e9,
             "alg_bytes_per_sweep": alg, "launches": steps,
             "clocks": {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 4},
-            "info": {"cells": cells, "fluid_cells": cells, "bytes_per_pdf": bpp}, "finite": True, "mass": float(cells)}
+            "info": {"cells": cells, "fluid_cells": cells, "bytes_per_pdf": bpp}, "finite": True, "mass": float(cells),
+            "repeats": 7 if min_seconds > 0 else 1}
+
+
+def _fake_error(lbm, variant, steps=2000):
+    return {"steps": steps, "pdf": 1e-9, "deviation": 1e-7, "u": 1e-6, "against": "oracle column"}
 
 
 def _fake_e2e(lbm, variant, steps, world):
@@ -33,6 +38,8 @@ def test_headline_line_has_the_contract_keys(monkeypatch, capsys):
     pytest.importorskip("torch")
     monkeypatch.setattr(bench, "time_variant", _fake_variant)
     monkeypatch.setattr(bench, "time_e2e", _fake_e2e)
+    monkeypatch.setattr(bench, "variant_error", _fake_error)
+    monkeypatch.setattr(bench, "measure_workloads", lambda args: {"c1_taylor_green": {"value": 1.0}})
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
     bench.main(["--steps", "20", "--warmup", "3", "--no-cpu-baseline"])
@@ -56,3 +63,21 @@ def test_headline_line_has_the_contract_keys(monkeypatch, capsys):
     assert set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
     assert set(d["variants"]) == set(bench.VARIANTS)
     assert d["variants"]["fp64-twogrid"]["fp64_pipe"] == bench.fp64_pipe("fp64-twogrid", 256 ** 3, 0.4)
+    # every variant states its error against the oracle; the headline's is repeated at the top
+    assert all(v["error_vs_oracle"]["steps"] == 2000 for v in d["variants"].values())
+    assert d["stated_error"] == d["variants"]["fp32-twogrid"]["error_vs_oracle"]
+    # the headline's timed region was repeated for the clock sampler (median repeat reported)
+    assert d["timing"]["repeats"] == 7
+    assert d["workloads"] == {"c1_taylor_green": {"value": 1.0}}
+
+
+def test_no_workloads_flag(monkeypatch, capsys):
+    pytest.importorskip("torch")
+    monkeypatch.setattr(bench, "time_variant", _fake_variant)
+    monkeypatch.setattr(bench, "time_e2e", _fake_e2e)
+    monkeypatch.setattr(bench, "variant_error", _fake_error)
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    bench.main(["--steps", "20", "--warmup", "3", "--no-cpu-baseline", "--no-workloads", "--headline-only"])
+    d = json.loads([l for l in capsys.readouterr().out.splitlines() if l.strip()][0])
+    assert "workloads" not in d and d["stated_error"] is None

@@ -60,3 +60,23 @@ def test_porous_minibed_record_matches_its_generator_positions():
     fluid = int((flags == 0).sum())
     assert 1.0 < head["mass"][0] / fluid < 1.5
     assert head["momentum"][0] > 0  # the flow runs from the inlet to the outlet
+
+
+def test_channel_column_record_is_the_oracle_column():
+    """The column the benchmark states its variants' errors against is the oracle's own run (the
+    generator's column() recomputed here), bit for bit, for TRT and MRT."""
+    spec = importlib.util.spec_from_file_location("make_channel_column",
+                                                  os.path.join(HERE, "golden", "make_channel_column.py"))
+    gen = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(gen)
+    import oracle
+    rec = gen.read()
+    assert set(rec) == {"trt", "mrt"}
+    for name, coll in (("trt", oracle.TRT), ("mrt", oracle.MRT)):
+        assert rec[name].shape == (19, gen.H)
+        np.testing.assert_array_equal(rec[name], gen.column(coll))
+    # the flow is developed but far from steady: centre-line u_x ~ F t
+    c, _, _ = oracle.lattice(19)
+    f = rec["trt"]
+    ux = c[:, 0] @ f / f.sum(0)
+    assert 1.5e-3 < ux[gen.H // 2] <= (gen.STEPS + 0.5) * 1e-6  # post-collision: + F/2
