@@ -372,18 +372,22 @@ def time_e2e(lbm, variant, steps, world):
     barrier(world)
     t0 = time.perf_counter()
     lbm.lbm_init_macroscopic(sim.ctx, 0, rho_h, u_h)
+    t1 = time.perf_counter()
     for _ in range(steps):
         lbm.lbm_step(sim.ctx, 1)
         lbm.lbm_step_diagnostics(sim.ctx)
+    t2 = time.perf_counter()
     lbm.lbm_get_macroscopic(sim.ctx, 0, rho_o, u_o)
     dt = time.perf_counter() - t0
+    parts = {"upload_and_init_ms": round((t1 - t0) * 1e3, 3), "steps_ms": round((t2 - t1) * 1e3, 3),
+             "download_ms": round((t0 + dt - t2) * 1e3, 3)}
     barrier(world)
     cells = sim.info()["cells"]
     sim.close()
     lups, _ = aggregate(cells * steps, dt, world)
     n = rho.size
     return {"value": lups / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(4 * n * 8 / steps),
-            "d2h_bytes_per_step": int((4 * n * 8) / steps + 64), "steps": steps,
+            "d2h_bytes_per_step": int((4 * n * 8) / steps + 64), "steps": steps, "breakdown": parts,
             "per_call": "fields up once, %d x (lbm_step(1) + step diagnostics read back), fields down once" % steps}
 
 

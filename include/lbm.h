@@ -136,6 +136,68 @@ typedef struct {
 lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks,
                              void *cuda_stream, lbm_ctx **out);
 
+/* ---- partitioned runs (one context per rank / GPU) ---------------------------------------
+ * The blocks of one domain are distributed over ranks; each rank holds the PDFs of its own
+ * blocks, and the ghost layers of blocks next to another rank's blocks are filled by a halo
+ * exchange between steps (Sec. 3.1: blocks distributed over processes along a space-filling
+ * curve; Sec. 3.3: ghost-layer exchange of only the PDFs that cross into a neighbour, packed
+ * into one message per neighbour process).  The library packs and unpacks; the caller moves
+ * the buffers between ranks (NCCL send/recv, or any transport) -- the C ABI carries no
+ * communicator.  One step of a partitioned run:
+ *     for every peer: lbm_halo_pack(ctx, peer, send_buf[peer])
+ *     exchange: send_buf[peer] -> peer, receive recv_buf[peer] from peer (sizes from lbm_halo_sizes)
+ *     for every peer: lbm_halo_unpack(ctx, peer, recv_buf[peer])
+ *     lbm_step(ctx, 1)
+ * and once before the first step after lbm_init_macroscopic / lbm_set_pdfs.  Pack and unpack
+ * are enqueued on the context's stream; the buffers must stay valid until that work is done. */
+
+/* Owner rank of every block along the Morton (Z-order) curve of the block centres: blocks in
+ * curve order are cut into nranks contiguous pieces of nearly equal weight (weights[b], or the
+ * block's cell count when weights is NULL).  Host only (no GPU needed).
+ * Errors: LBM_ERR_ARG for empty input, sizes < 1, negative or non-finite weights.
+ * Paper: Sec. 3.1 (blocks assigned to processes along a space-filling curve). */
+lbm_status lbm_partition_morton(const lbm_block_desc *blocks, int32_t nblocks, int32_t nranks, const double *weights,
+                                int32_t *owner);
+
+/* A context for rank `rank` of `nranks` that holds the blocks with owner[b] == rank (owner:
+ * nblocks entries in [0, nranks)); the other blocks describe the domain (neighbours, ghost
+ * shells) but get no device memory.  Every rank must be created with the same parameters,
+ * blocks, owner array, faces and flags: lbm_set_boundary is accepted for every block (the
+ * ghost shells of owned blocks take kinds from their neighbours' flags) and must be given for
+ * all of them.  Per-block calls that touch PDFs (init, get, set, macroscopic) accept owned
+ * blocks only (LBM_ERR_ARG otherwise); lbm_reduce covers the owned blocks (sum the ranks'
+ * results).  With a halo to exchange, lbm_step advances one step per call (LBM_ERR_STATE for
+ * n > 1), and graph replay and lbm_autotune are refused (LBM_ERR_UNSUPPORTED).
+ * Errors: as lbm_create_blocks; LBM_ERR_ARG for a bad owner array or a rank that owns no block.
+ * Paper: Sec. 3.1 (distributed blocks), Sec. 4.2 (per-block fields with one ghost layer). */
+lbm_status lbm_create_partition(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks,
+                                const int32_t *owner, int32_t nranks, int32_t rank, void *cuda_stream,
+                                lbm_ctx **out);
+
+/* Elements (of the storage type: 8, 4 or 2 bytes) this rank sends to and receives from `peer`
+ * in the exchange that must precede the next step.  Two-grid: the crossing PDFs of the
+ * owned cells next to the peer's blocks go to the peer's ghost layers.  AA: before the
+ * neighbour sweep the same forward exchange of the AA slots; before the local sweep the
+ * reverse one (the values the neighbour sweep wrote into ghost slots go back to the peer
+ * that owns those cells), so send and receive sizes swap from step to step.  0 and 0 when
+ * the two ranks share no face.  Host only.
+ * Errors: LBM_ERR_STATE for a context that is not partitioned, LBM_ERR_ARG for a bad peer.
+ * Paper: Sec. 3.3 (ghost-layer exchange, only the directions that cross). */
+lbm_status lbm_halo_sizes(lbm_ctx *ctx, int32_t peer, int64_t *send_elems, int64_t *recv_elems);
+
+/* Enqueue the pack of this step's halo for `peer` into the device buffer dev_buf (at least
+ * send_elems elements of lbm_halo_sizes; caller-owned) on the context's stream.  Nothing is
+ * launched when send_elems is 0.
+ * Errors: as lbm_halo_sizes; LBM_ERR_ARG for a null buffer; LBM_ERR_CUDA.
+ * Paper: Sec. 3.3 (PackInfo: the data of a block face packed into a message buffer). */
+lbm_status lbm_halo_pack(lbm_ctx *ctx, int32_t peer, void *dev_buf);
+
+/* Enqueue the unpack of the halo received from `peer` (device buffer of at least recv_elems
+ * elements) into this rank's PDF array on the context's stream.
+ * Errors: as lbm_halo_pack.
+ * Paper: Sec. 3.3 (PackInfo: unpacking the message into the ghost layer). */
+lbm_status lbm_halo_unpack(lbm_ctx *ctx, int32_t peer, const void *dev_buf);
+
 /* Bytes of device memory the PDF arrays need (two arrays for two-grid, one for AA),
  * including 256-byte alignment slack.
  * Paper: Sec. 4.2 (field memory layout); the caller-owned buffer has no counterpart there. */
@@ -324,6 +386,15 @@ lbm_status lbm_plan_mask(lbm_ctx *ctx, int32_t block, uint32_t *out, int64_t cap
 /* Wall-parameter table of the built lists: (ux, uy, uz, rho) per index.
  * Paper: Sec. 5.1.1 (boundary parameters of the velocity and pressure kinds). */
 lbm_status lbm_plan_params(lbm_ctx *ctx, double *out, int64_t cap, int64_t *n);
+
+/* Host-only inspection of a partitioned context's halo lists with `peer`: list 0 send (pull
+ * selection), 1 receive (pull), 2 send (AA), 3 receive (AA).  Each run is 4 int64: arena
+ * element offset, buffer element offset, length, arena stride; element k of a run moves
+ * between arena[offset + k * stride] (in this rank's PDF array) and buffer[buffer offset + k].
+ * Send runs read owned interior slots, receive runs address own ghost slots; the peer's
+ * matching list covers the same buffer elements in the same order.  out = NULL: *n only.
+ * Paper: Sec. 3.3 (ghost-layer exchange lists). */
+lbm_status lbm_plan_halo(lbm_ctx *ctx, int32_t peer, int32_t list, int64_t *out, int64_t cap, int64_t *n);
 
 /* Allocation-free diagnostics of a caller-owned PDF field.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc -- code that takes all

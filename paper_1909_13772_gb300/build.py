@@ -1,8 +1,9 @@
 """Build liblbm.so (the C-ABI library) in-tree with nvcc for sm_103a.
 
 Translation units: api.cu (C ABI, scheduler), plan.cpp (host list builder, OpenMP), diag.cu,
-reduce_static.cu, closure.cu (closure sweep and network kernels, D3Q19 FP32), and sweep.cu /
-aux.cu compiled once per (stencil, storage) variant.  Objects are compiled in
+reduce_static.cu, closure.cu (closure sweep and network kernels, D3Q19 FP32), halo.cu (halo
+pack/unpack of partitioned runs), sweep.cu / aux.cu compiled once per (stencil, storage)
+variant, and sweep.cu once more per (stencil, FP64/FP32) with the MRT collision.  Objects are compiled in
 parallel; the library lands in ``paper_1909_13772_gb300/_build/liblbm.so``.
 """
 from __future__ import annotations
@@ -40,7 +41,7 @@ def _sources():
 
 def _jobs(nvcc, extra, build_dir):
     jobs = []
-    for name in ("api.cu", "plan.cpp", "diag.cu", "reduce_static.cu", "closure.cu"):
+    for name in ("api.cu", "plan.cpp", "diag.cu", "reduce_static.cu", "closure.cu", "halo.cu"):
         src = os.path.join(CSRC, name)
         obj = os.path.join(build_dir, name.replace(".", "_") + ".o")
         lang = [] if name.endswith(".cu") else ["-x", "cu"]

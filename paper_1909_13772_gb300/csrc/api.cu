@@ -35,6 +35,11 @@ struct lbm_ctx {
     int in_place = 1;  // read matching neighbour blocks in place (else ghost copies)
     int64_t arena_elems = 0;
     cudaStream_t stream = nullptr;
+    // partitioned run (lbm_create_partition): owner rank of every block, this context's rank;
+    // empty owner: the context owns every block
+    std::vector<int32_t> owner;
+    int rank = 0, nranks = 1;
+    std::vector<HaloDevRun *> d_halo;  // per peer, 4 lists: send pull, recv pull, send AA, recv AA
 
     // device state
     bool dev_ready = false;
@@ -200,6 +205,8 @@ lbm_status build_lists(lbm_ctx *c)
     in.blocks = &c->blocks;
     in.flags = &c->flags;
     in.block_param = &c->block_param;
+    in.owner = c->owner.empty() ? nullptr : &c->owner;
+    in.rank = c->rank;
     std::string e = build_plan(in, c->plan);
     if (!e.empty()) return fail(c, LBM_ERR_UNSUPPORTED, "%s", e.c_str());
     if ((int64_t)c->plan.tiles.size() > 0x7fffffffLL) return fail(c, LBM_ERR_UNSUPPORTED, "too many tiles");
@@ -344,6 +351,18 @@ lbm_status ensure_lists(lbm_ctx *c)
     if (!ra.empty()) memcpy(ra.data(), P.runs_aa.data(), ra.size() * sizeof(DevRun));
     if ((s2 = upload(c, c->d_runs_pull, rp, "upload runs")) != LBM_OK) return s2;
     if ((s2 = upload(c, c->d_runs_aa, ra, "upload runs")) != LBM_OK) return s2;
+    static_assert(sizeof(HaloRun) == sizeof(HaloDevRun), "halo run layout");
+    for (HaloDevRun *&h : c->d_halo) dfree(h);
+    c->d_halo.assign(4 * P.halo.size(), nullptr);
+    for (size_t p = 0; p < P.halo.size(); ++p) {
+        const std::vector<HaloRun> *lists[4] = {&P.halo[p].send_pull, &P.halo[p].recv_pull, &P.halo[p].send_aa,
+                                                &P.halo[p].recv_aa};
+        for (int k = 0; k < 4; ++k) {
+            std::vector<HaloDevRun> hv(lists[k]->size());
+            if (!hv.empty()) memcpy(hv.data(), lists[k]->data(), hv.size() * sizeof(HaloDevRun));
+            if ((s2 = upload(c, c->d_halo[4 * p + k], hv, "upload halo runs")) != LBM_OK) return s2;
+        }
+    }
     std::vector<DevTile> dt(P.tiles.size());
     if (!dt.empty()) memcpy(dt.data(), P.tiles.data(), dt.size() * sizeof(DevTile));
     c->stage_bytes = stage_tiles(c, P, dt.data());
@@ -439,6 +458,55 @@ lbm_status check_block(lbm_ctx *c, int32_t block)
     return LBM_OK;
 }
 
+// A block whose PDFs this context holds (every block, or in a partitioned run those of its rank).
+lbm_status check_owned(lbm_ctx *c, int32_t block)
+{
+    lbm_status s = check_block(c, block);
+    if (s != LBM_OK) return s;
+    if (!c->owner.empty() && c->owner[block] != c->rank)
+        return fail(c, LBM_ERR_ARG, "block %d belongs to rank %d, not to this context (rank %d)", block,
+                    c->owner[block], c->rank);
+    return LBM_OK;
+}
+
+// The context exchanges a halo with some peer (then it advances one step per lbm_step call).
+bool has_halo(const lbm_ctx *c)
+{
+    for (const PeerHalo &h : c->plan.halo)
+        if (h.n_send_pull + h.n_recv_pull + h.n_send_aa + h.n_recv_aa > 0) return true;
+    return false;
+}
+
+// The lists of the exchange that must precede the next step with `peer`: two-grid, the pull
+// selection forward (owned interior -> the peer's ghosts); AA before the neighbour sweep (layout
+// E) the AA selection forward, before the local sweep (layout O) backward (the ghost slots the
+// neighbour sweep wrote -> the peer's interior).  ipack/iunpack index the context's device
+// lists (4 per peer).
+void halo_lists(const lbm_ctx *c, int peer, int *ipack, int *iunpack, int64_t *nsend, int64_t *nrecv)
+{
+    const PeerHalo &h = c->plan.halo[peer];
+    if (c->pattern == LBM_TWO_GRID) {
+        *ipack = 0, *iunpack = 1, *nsend = h.n_send_pull, *nrecv = h.n_recv_pull;
+    } else if (c->aa_layout == LAYOUT_AA_E) {
+        *ipack = 2, *iunpack = 3, *nsend = h.n_send_aa, *nrecv = h.n_recv_aa;
+    } else {
+        *ipack = 3, *iunpack = 2, *nsend = h.n_recv_aa, *nrecv = h.n_send_aa;
+    }
+}
+
+const std::vector<HaloRun> &halo_runs(const lbm_ctx *c, int peer, int k)
+{
+    const PeerHalo &h = c->plan.halo[peer];
+    return k == 0 ? h.send_pull : (k == 1 ? h.recv_pull : (k == 2 ? h.send_aa : h.recv_aa));
+}
+
+lbm_status check_peer(lbm_ctx *c, int32_t peer)
+{
+    if (c->owner.empty()) return fail(c, LBM_ERR_STATE, "not a partitioned context");
+    if (peer < 0 || peer >= c->nranks || peer == c->rank) return fail(c, LBM_ERR_ARG, "bad peer rank %d", peer);
+    return LBM_OK;
+}
+
 // Status of the bounded device-side waits.  wait_status_enqueue queues the copies of the flags
 // into the pinned landing zone; after the stream has been synchronised wait_status_take reports
 // LBM_ERR_TIMEOUT once after a wait gave up (the flag is then cleared), else LBM_OK.
@@ -484,8 +552,139 @@ lbm_status wait_status(lbm_ctx *c)
 
 extern "C" {
 
+namespace {
+lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks, const int32_t *owner,
+                      int32_t nranks, int32_t rank, void *cuda_stream, lbm_ctx **out);
+}  // namespace
+
 lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks,
                              void *cuda_stream, lbm_ctx **out)
+{
+    return create_ctx(params, blocks, nblocks, nullptr, 1, 0, cuda_stream, out);
+}
+
+lbm_status lbm_create_partition(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks,
+                                const int32_t *owner, int32_t nranks, int32_t rank, void *cuda_stream, lbm_ctx **out)
+{
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    if (!owner || nranks < 1 || rank < 0 || rank >= nranks) return LBM_ERR_ARG;
+    bool mine = false;
+    for (int32_t b = 0; b < nblocks; ++b) {
+        if (owner[b] < 0 || owner[b] >= nranks) return LBM_ERR_ARG;
+        mine = mine || owner[b] == rank;
+    }
+    if (!mine) return LBM_ERR_ARG;
+    return create_ctx(params, blocks, nblocks, owner, nranks, rank, cuda_stream, out);
+}
+
+lbm_status lbm_partition_morton(const lbm_block_desc *blocks, int32_t nblocks, int32_t nranks, const double *weights,
+                                int32_t *owner)
+{
+    if (!blocks || !owner || nblocks <= 0 || nranks < 1) return LBM_ERR_ARG;
+    std::vector<BlockLayout> bl(nblocks);
+    std::vector<double> w;
+    for (int b = 0; b < nblocks; ++b) {
+        for (int a = 0; a < 3; ++a) {
+            bl[b].origin[a] = blocks[b].origin[a];
+            bl[b].n[a] = blocks[b].size[a];
+            if (blocks[b].size[a] < 1) return LBM_ERR_ARG;
+        }
+        if (weights) {
+            if (!(weights[b] >= 0.0) || !std::isfinite(weights[b])) return LBM_ERR_ARG;
+            w.push_back(weights[b]);
+        }
+    }
+    std::vector<int32_t> own;
+    partition_morton(bl, nranks, weights ? &w : nullptr, own);
+    for (int b = 0; b < nblocks; ++b) owner[b] = own[b];
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_sizes(lbm_ctx *c, int32_t peer, int64_t *send_elems, int64_t *recv_elems)
+{
+    if (!c || !send_elems || !recv_elems) return LBM_ERR_ARG;
+    lbm_status s = check_peer(c, peer);
+    if (s != LBM_OK) return s;
+    if ((s = build_lists(c)) != LBM_OK) return s;
+    int ip, iu;
+    halo_lists(c, peer, &ip, &iu, send_elems, recv_elems);
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_pack(lbm_ctx *c, int32_t peer, void *dev_buf)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_peer(c, peer);
+    if (s != LBM_OK) return s;
+    if ((s = prepare(c)) != LBM_OK) return s;
+    int ip, iu;
+    int64_t ns, nr;
+    halo_lists(c, peer, &ip, &iu, &ns, &nr);
+    if (ns == 0) return LBM_OK;
+    if (!dev_buf) return fail(c, LBM_ERR_ARG, "null halo buffer");
+    HaloArgs h{};
+    h.arena = c->pattern == LBM_TWO_GRID ? c->arr[c->cur] : c->arr[0];
+    h.buf = dev_buf;
+    h.runs = c->d_halo[4 * peer + ip];
+    h.nruns = (int64_t)halo_runs(c, peer, ip).size();
+    h.to_buf = 1;
+    h.elem_bytes = c->bpp;
+    h.stream = c->stream;
+    CK(launch_halo(h), "halo pack launch");
+    c->launches++;
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_unpack(lbm_ctx *c, int32_t peer, const void *dev_buf)
+{
+    if (!c) return LBM_ERR_ARG;
+    lbm_status s = check_peer(c, peer);
+    if (s != LBM_OK) return s;
+    if ((s = prepare(c)) != LBM_OK) return s;
+    int ip, iu;
+    int64_t ns, nr;
+    halo_lists(c, peer, &ip, &iu, &ns, &nr);
+    if (nr == 0) return LBM_OK;
+    if (!dev_buf) return fail(c, LBM_ERR_ARG, "null halo buffer");
+    HaloArgs h{};
+    h.arena = c->pattern == LBM_TWO_GRID ? c->arr[c->cur] : c->arr[0];
+    h.buf = const_cast<void *>(dev_buf);
+    h.runs = c->d_halo[4 * peer + iu];
+    h.nruns = (int64_t)halo_runs(c, peer, iu).size();
+    h.to_buf = 0;
+    h.elem_bytes = c->bpp;
+    h.stream = c->stream;
+    CK(launch_halo(h), "halo unpack launch");
+    c->launches++;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_halo(lbm_ctx *c, int32_t peer, int32_t list, int64_t *out, int64_t cap, int64_t *n)
+{
+    if (!c || !n) return LBM_ERR_ARG;
+    lbm_status s = check_peer(c, peer);
+    if (s != LBM_OK) return s;
+    if (list < 0 || list > 3) return fail(c, LBM_ERR_ARG, "bad halo list %d", list);
+    if ((s = build_lists(c)) != LBM_OK) return s;
+    const std::vector<HaloRun> &R = halo_runs(c, peer, list);
+    *n = (int64_t)R.size();
+    if (!out) return LBM_OK;
+    if (cap < 4 * *n) return fail(c, LBM_ERR_ARG, "buffer too small");
+    for (size_t r = 0; r < R.size(); ++r) {
+        out[4 * r] = R[r].arena;
+        out[4 * r + 1] = R[r].buf;
+        out[4 * r + 2] = R[r].len;
+        out[4 * r + 3] = R[r].astride;
+    }
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, int32_t nblocks, const int32_t *owner,
+                      int32_t nranks, int32_t rank, void *cuda_stream, lbm_ctx **out)
 {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
@@ -522,8 +721,13 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
             c->blocks[b].n[a] = blocks[b].size[a];
         }
     }
+    if (owner) {
+        c->owner.assign(owner, owner + nblocks);
+        c->nranks = nranks;
+        c->rank = rank;
+    }
     int64_t elems = 0;
-    layout_blocks(c->blocks, c->bpp, c->q, 128, &elems);
+    layout_blocks(c->blocks, c->bpp, c->q, 128, &elems, owner ? &c->owner : nullptr, rank);
     std::string e = check_blocks(c->blocks);
     if (!e.empty()) {
         delete c;
@@ -599,6 +803,9 @@ lbm_status lbm_create_blocks(const lbm_params *params, const lbm_block_desc *blo
     *out = c;
     return LBM_OK;
 }
+}  // namespace
+
+extern "C" {
 
 size_t lbm_required_bytes(const lbm_ctx *c)
 {
@@ -664,7 +871,7 @@ lbm_status lbm_set_boundary(lbm_ctx *c, int32_t block, const uint8_t *flags, con
 lbm_status lbm_init_macroscopic(lbm_ctx *c, int32_t block, const double *rho, const double *u)
 {
     if (!c) return LBM_ERR_ARG;
-    lbm_status s = check_block(c, block);
+    lbm_status s = check_owned(c, block);
     if (s != LBM_OK) return s;
     if (!rho || !u) return fail(c, LBM_ERR_ARG, "null rho or u");
     if ((s = prepare(c)) != LBM_OK) return s;
@@ -846,6 +1053,8 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
     if (n < 0) return fail(c, LBM_ERR_ARG, "negative step count");
     lbm_status s = prepare(c);
     if (s != LBM_OK) return s;
+    if (n > 1 && has_halo(c))
+        return fail(c, LBM_ERR_STATE, "partitioned context: one step per call (the halo exchange comes between steps)");
     SweepArgs sw;
     FillArgs fa;
     step_args(c, sw, fa);
@@ -930,6 +1139,9 @@ lbm_status lbm_set_graph(lbm_ctx *c, int32_t enable)
     if (!c) return LBM_ERR_ARG;
     if (enable && c->stream == nullptr)
         return fail(c, LBM_ERR_UNSUPPORTED, "graph mode needs a non-default stream (capture is not allowed on stream 0)");
+    if (enable && !c->owner.empty())
+        return fail(c, LBM_ERR_UNSUPPORTED, "graph mode replays step pairs; a partitioned context exchanges its halo "
+                                            "between steps");
     c->graph_mode = enable != 0;
     if (!enable) drop_graphs(c);
     return LBM_OK;
@@ -939,6 +1151,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], int32_
 {
     if (!c || !best) return LBM_ERR_ARG;
     if (trial_steps < 1) return fail(c, LBM_ERR_ARG, "trial_steps must be >= 1");
+    if (!c->owner.empty()) return fail(c, LBM_ERR_UNSUPPORTED, "autotune runs steps without a halo exchange");
     lbm_status s = prepare(c);
     if (s != LBM_OK) return s;
     // keep the simulation state: snapshot the PDF arrays, start every trial from it, restore
@@ -1020,7 +1233,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], int32_
 lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u)
 {
     if (!c) return LBM_ERR_ARG;
-    lbm_status s = check_block(c, block);
+    lbm_status s = check_owned(c, block);
     if (s != LBM_OK) return s;
     if (!rho || !u) return fail(c, LBM_ERR_ARG, "null output");
     if ((s = prepare(c)) != LBM_OK) return s;
@@ -1040,7 +1253,7 @@ lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u
 lbm_status lbm_coarse_moments(lbm_ctx *c, int32_t block, int32_t ratio, double *out)
 {
     if (!c) return LBM_ERR_ARG;
-    lbm_status s = check_block(c, block);
+    lbm_status s = check_owned(c, block);
     if (s != LBM_OK) return s;
     if (!out) return fail(c, LBM_ERR_ARG, "null output");
     const BlockLayout &L = c->blocks[block];
@@ -1063,7 +1276,7 @@ lbm_status lbm_coarse_moments(lbm_ctx *c, int32_t block, int32_t ratio, double *
 lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
 {
     if (!c) return LBM_ERR_ARG;
-    lbm_status s = check_block(c, block);
+    lbm_status s = check_owned(c, block);
     if (s != LBM_OK) return s;
     if (!f) return fail(c, LBM_ERR_ARG, "null output");
     if ((s = prepare(c)) != LBM_OK) return s;
@@ -1082,7 +1295,7 @@ lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
 lbm_status lbm_get_pdfs_region(lbm_ctx *c, int32_t block, const int32_t origin[3], const int32_t size[3], double *f)
 {
     if (!c) return LBM_ERR_ARG;
-    lbm_status s = check_block(c, block);
+    lbm_status s = check_owned(c, block);
     if (s != LBM_OK) return s;
     if (!f || !origin || !size) return fail(c, LBM_ERR_ARG, "null argument");
     const BlockLayout &L = c->blocks[block];
@@ -1108,7 +1321,7 @@ lbm_status lbm_get_pdfs_region(lbm_ctx *c, int32_t block, const int32_t origin[3
 lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
 {
     if (!c) return LBM_ERR_ARG;
-    lbm_status s = check_block(c, block);
+    lbm_status s = check_owned(c, block);
     if (s != LBM_OK) return s;
     if (!f) return fail(c, LBM_ERR_ARG, "null input");
     if ((s = prepare(c)) != LBM_OK) return s;
@@ -1419,6 +1632,7 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_links);
     dfree(c->d_runs_pull);
     dfree(c->d_runs_aa);
+    for (HaloDevRun *&h : c->d_halo) dfree(h);
     dfree(c->d_tiles);
     dfree(c->d_params);
     dfree(c->d_masks);

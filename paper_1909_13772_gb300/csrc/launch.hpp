@@ -49,6 +49,25 @@ struct FillArgs {
     cudaStream_t stream;
 };
 
+// Halo pack / unpack of a partitioned run (halo.cu): element moves between the PDF array and a
+// caller-owned buffer along runs (the device copy of plan.hpp HaloRun).
+struct HaloDevRun {
+    int64_t arena;
+    int64_t buf;
+    int32_t len;
+    int32_t astride;
+};
+struct HaloArgs {
+    void *arena;  // the PDF array the next sweep reads
+    void *buf;    // device buffer of the exchange with one peer
+    const HaloDevRun *runs;
+    int64_t nruns;
+    int to_buf;      // 1: pack (arena -> buffer), 0: unpack
+    int elem_bytes;  // 8, 4 or 2
+    cudaStream_t stream;
+};
+cudaError_t launch_halo(const HaloArgs &h);
+
 // Per-cell kernels over the interior cells of one block (get/set/macroscopic/init).
 struct CellArgs {
     void *a;

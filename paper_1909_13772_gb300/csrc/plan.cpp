@@ -10,20 +10,80 @@
 
 namespace lbm {
 
-void layout_blocks(std::vector<BlockLayout> &blocks, int bytes_per_pdf, int q, int align_bytes, int64_t *total_elems)
+void layout_blocks(std::vector<BlockLayout> &blocks, int bytes_per_pdf, int q, int align_bytes, int64_t *total_elems,
+                   const std::vector<int32_t> *owner, int rank)
 {
     int a = std::max(1, align_bytes / bytes_per_pdf);
     int64_t off = 0;
-    for (auto &b : blocks) {
+    for (size_t i = 0; i < blocks.size(); ++i) {
+        auto &b = blocks[i];
         b.xo = a;
         int need = a + b.n[0] + 1;
         b.pitch = (need + a - 1) / a * a;
         b.plane = (int64_t)b.pitch * (b.n[1] + 2);
         b.slab = b.plane * (b.n[2] + 2);
+        if (owner && (*owner)[i] != rank) {
+            b.offset = -1;
+            continue;
+        }
         b.offset = off;
         off += (int64_t)q * b.slab;
     }
     *total_elems = off;
+}
+
+namespace {
+// interleave the low 21 bits of v with two zero bits between them
+uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffULL;
+    v = (v | v << 32) & 0x1f00000000ffffULL;
+    v = (v | v << 16) & 0x1f0000ff0000ffULL;
+    v = (v | v << 8) & 0x100f00f00f00f00fULL;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+    v = (v | v << 2) & 0x1249249249249249ULL;
+    return v;
+}
+}  // namespace
+
+void partition_morton(const std::vector<BlockLayout> &blocks, int nranks, const std::vector<double> *weights,
+                      std::vector<int32_t> &owner)
+{
+    const int nb = (int)blocks.size();
+    owner.assign(nb, 0);
+    if (nb == 0 || nranks <= 1) return;
+    int64_t lo[3];
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = blocks[0].origin[a];
+        for (const auto &b : blocks) lo[a] = std::min(lo[a], b.origin[a]);
+    }
+    // key of a block: Morton code of its centre (twice the centre, to stay in integers)
+    std::vector<std::pair<uint64_t, int>> key(nb);
+    for (int b = 0; b < nb; ++b) {
+        uint64_t k = 0;
+        for (int a = 0; a < 3; ++a) {
+            const uint64_t c = (uint64_t)(2 * (blocks[b].origin[a] - lo[a]) + blocks[b].n[a]);
+            k |= spread3(c) << a;
+        }
+        key[b] = {k, b};
+    }
+    std::sort(key.begin(), key.end());
+    double total = 0.0;
+    std::vector<double> w(nb);
+    for (int b = 0; b < nb; ++b) {
+        w[b] = weights ? (*weights)[b] : (double)blocks[b].n[0] * blocks[b].n[1] * blocks[b].n[2];
+        total += w[b];
+    }
+    // block k of the curve goes to the rank whose share [r, r + 1) total / nranks holds the
+    // middle of its weight interval
+    double acc = 0.0;
+    for (int k = 0; k < nb; ++k) {
+        const int b = key[k].second;
+        const double mid = acc + 0.5 * w[b];
+        int r = (int)(mid / total * nranks);
+        owner[b] = std::min(std::max(r, 0), nranks - 1);
+        acc += w[b];
+    }
 }
 
 std::string check_blocks(const std::vector<BlockLayout> &blocks)
@@ -67,6 +127,35 @@ struct Elem {
 
 // Append one element copy to a run list, extending the last run when the element continues
 // it: along x (strides 1, 1) or along y (strides = the two blocks' row pitches).
+// Append one halo element (arena slot, next buffer element) to a halo run list, extending the
+// last run along a constant arena stride.
+void append_halo(std::vector<HaloRun> &runs, int64_t arena, int64_t buf)
+{
+    if (!runs.empty()) {
+        HaloRun &r = runs.back();
+        if (buf == r.buf + r.len && r.len < (1 << 30)) {
+            if (r.len == 1 && arena - r.arena != 0 && std::llabs(arena - r.arena) < ((int64_t)1 << 31)) {
+                r.astride = (int32_t)(arena - r.arena);
+                r.len = 2;
+                return;
+            }
+            if (r.len > 1 && arena == r.arena + (int64_t)r.len * r.astride) {
+                r.len += 1;
+                return;
+            }
+        }
+    }
+    runs.push_back(HaloRun{arena, buf, 1, 1});
+}
+
+// One halo element of a block's ghost shell: peer rank, arena slot on this rank, selection
+// (bit 0: two-grid pull, bit 1: AA).
+struct HaloElem {
+    int32_t peer;
+    int32_t sel;
+    int64_t arena;
+};
+
 void append_run(std::vector<GhostRun> &runs, int64_t src, int64_t dst, int32_t spitch, int32_t dpitch)
 {
     if (!runs.empty()) {
@@ -89,6 +178,7 @@ void append_run(std::vector<GhostRun> &runs, int64_t src, int64_t dst, int32_t s
 }
 
 struct BlockOut {
+    std::vector<HaloElem> send, recv;  // partitioned context: halo elements of this block's shell
     std::vector<uint64_t> links[4];
     std::vector<GhostRun> runs_pull, runs_aa;
     int64_t slots_pull = 0, slots_aa = 0;
@@ -214,12 +304,33 @@ std::string build_plan(const PlanInput &in, Plan &out)
         }
     }
     if (!in.in_place) std::fill(through.begin(), through.end(), uint8_t(0));
+    // partitioned context: blocks of other ranks are not swept here, and a block with a
+    // neighbour on another rank receives that neighbour's PDFs into its ghost layer
+    const auto owned = [&](int b) { return !in.owner || (*in.owner)[b] == in.rank; };
+    if (in.owner) {
+        for (int b = 0; b < nb; ++b) {
+            if (!owned(b)) {
+                through[b] = 0;
+                continue;
+            }
+            for (const Candidate &cd : cand[b])
+                if (!owned(cd.block)) through[b] = 0;
+        }
+    }
 
     std::vector<BlockOut> bo(nb);
     std::string err;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int b = 0; b < nb; ++b) {
         const auto &B = blocks[b];
+        const bool own = owned(b);
+        if (!own) {
+            // a block of another rank matters here only when it mirrors cells of this rank's
+            // blocks in its ghost shell: those are sent to it
+            bool feeds = false;
+            for (const Candidate &cd : cand[b]) feeds = feeds || owned(cd.block);
+            if (!feeds) continue;
+        }
         const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
         const int px = nx + 2, py = ny + 2, pz = nz + 2;
         const int64_t np = (int64_t)px * py * pz;
@@ -296,6 +407,29 @@ std::string build_plan(const PlanInput &in, Plan &out)
                         param[p] = 0;
                     }
                 }
+        if (!own) {
+            // halo send elements: for each direction, shell cells of this remote block that
+            // mirror a fluid cell of an owned block, in the order the owner of the remote block
+            // lists them as receive elements (direction, then z, y, x)
+            for (int j = 0; j < L.q; ++j)
+                for (int z = -1; z <= nz; ++z)
+                    for (int y = -1; y <= ny; ++y)
+                        for (int x = -1; x <= nx; ++x) {
+                            if (!(x < 0 || x >= nx || y < 0 || y >= ny || z < 0 || z >= nz)) continue;
+                            const int64_t p = pidx(x, y, z);
+                            if (kind[p] != K_MIRROR || !owned(sblock[p])) continue;
+                            const auto &S = blocks[sblock[p]];
+                            int sel = 0;
+                            int ax = x + L.cx[j], ay = y + L.cy[j], az = z + L.cz[j];
+                            if (inside(ax, ay, az) && kind[pidx(ax, ay, az)] == K_FLUID) sel |= 1;
+                            int bx = x - L.cx[j], by = y - L.cy[j], bz = z - L.cz[j];
+                            if (inside(bx, by, bz) && kind[pidx(bx, by, bz)] == K_FLUID) sel |= 2;
+                            if (sel)
+                                o.send.push_back(HaloElem{(*in.owner)[b], sel,
+                                                          S.offset + (int64_t)j * S.slab + scell[p]});
+                        }
+            continue;
+        }
         // links: fluid interior cell x, direction q with a boundary neighbour
         for (int qd = 1; qd < L.q; ++qd) {
             for (int z = 0; z < nz; ++z)
@@ -321,17 +455,25 @@ std::string build_plan(const PlanInput &in, Plan &out)
                         int64_t p = pidx(x, y, z);
                         if (kind[p] != K_MIRROR) continue;
                         const auto &S = blocks[sblock[p]];
-                        int64_t src = S.offset + (int64_t)j * S.slab + scell[p];
                         int64_t dst = base + (int64_t)j * B.slab + B.cell(x, y, z);
                         // two-grid pull: interior fluid cell g + c_j reads slot j of g
                         int ax = x + L.cx[j], ay = y + L.cy[j], az = z + L.cz[j];
-                        if (inside(ax, ay, az) && kind[pidx(ax, ay, az)] == K_FLUID) {
+                        const bool pull = inside(ax, ay, az) && kind[pidx(ax, ay, az)] == K_FLUID;
+                        // AA: interior fluid cell g - c_j reads and writes slot j of g
+                        int bx = x - L.cx[j], by = y - L.cy[j], bz = z - L.cz[j];
+                        const bool aa = inside(bx, by, bz) && kind[pidx(bx, by, bz)] == K_FLUID;
+                        if (!owned(sblock[p])) {
+                            // the source lives on another rank: received into this ghost slot
+                            if (pull || aa)
+                                o.recv.push_back(HaloElem{(*in.owner)[sblock[p]], (pull ? 1 : 0) | (aa ? 2 : 0), dst});
+                            continue;
+                        }
+                        int64_t src = S.offset + (int64_t)j * S.slab + scell[p];
+                        if (pull) {
                             append_run(o.runs_pull, src, dst, S.pitch, B.pitch);
                             o.slots_pull++;
                         }
-                        // AA: interior fluid cell g - c_j reads and writes slot j of g
-                        int bx = x - L.cx[j], by = y - L.cy[j], bz = z - L.cz[j];
-                        if (inside(bx, by, bz) && kind[pidx(bx, by, bz)] == K_FLUID) {
+                        if (aa) {
                             append_run(o.runs_aa, src, dst, S.pitch, B.pitch);
                             o.slots_aa++;
                         }
@@ -405,6 +547,25 @@ std::string build_plan(const PlanInput &in, Plan &out)
             out.link_count[k] += (int64_t)bo[b].links[k].size();
         }
     for (int b = 0; b < nb; ++b) out.link_count[K_NOSLIP] += bo[b].bounce;
+    // halo lists per peer, elements in block order (the same order on both sides)
+    out.halo.clear();
+    if (in.owner) {
+        int nranks = in.rank + 1;
+        for (int32_t r : *in.owner) nranks = std::max(nranks, (int)r + 1);
+        out.halo.assign(nranks, PeerHalo{});
+        for (int b = 0; b < nb; ++b) {
+            for (const HaloElem &e : bo[b].send) {
+                PeerHalo &h = out.halo[e.peer];
+                if (e.sel & 1) append_halo(h.send_pull, e.arena, h.n_send_pull++);
+                if (e.sel & 2) append_halo(h.send_aa, e.arena, h.n_send_aa++);
+            }
+            for (const HaloElem &e : bo[b].recv) {
+                PeerHalo &h = out.halo[e.peer];
+                if (e.sel & 1) append_halo(h.recv_pull, e.arena, h.n_recv_pull++);
+                if (e.sel & 2) append_halo(h.recv_aa, e.arena, h.n_recv_aa++);
+            }
+        }
+    }
     for (int b = 0; b < nb; ++b) {
         out.runs_pull.insert(out.runs_pull.end(), bo[b].runs_pull.begin(), bo[b].runs_pull.end());
         out.runs_aa.insert(out.runs_aa.end(), bo[b].runs_aa.begin(), bo[b].runs_aa.end());

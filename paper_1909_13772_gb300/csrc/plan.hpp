@@ -9,7 +9,11 @@
 //     condition, each treated by its own kernel),
 //   * the ghost-copy run lists between blocks on the same GPU and across periodic faces
 //     (Sec. 3.3 PackInfo local transfer; only the PDFs that cross into the block are copied),
-//   * the sweep tile list (which CTA sweeps which cells of which block).
+//   * the sweep tile list (which CTA sweeps which cells of which block),
+//   * for a context that owns only some of the blocks (one rank of a partitioned run, blocks
+//     given to ranks along a space-filling curve, Sec. 3.1), the halo lists: per peer rank the
+//     PDFs this rank sends to the peer's ghost layers and the ones it receives into its own
+//     (Sec. 3.3: ghost-layer exchange of the crossing directions only, packed into buffers).
 #pragma once
 
 #include <array>
@@ -49,6 +53,23 @@ struct GhostRun {
     int32_t pad;
 };
 
+// One halo run of a partitioned context: len elements, element k between the arena slot
+// arena + k*astride and buffer element buf + k (the peer's matching run has the same buffer
+// range).  Send runs read owned interior slots; receive runs address own ghost slots.
+struct HaloRun {
+    int64_t arena;
+    int64_t buf;
+    int32_t len;
+    int32_t astride;
+};
+
+// The halo lists exchanged with one peer rank, for the two-grid (pull) and the AA selection of
+// ghost slots, and their lengths in elements.
+struct PeerHalo {
+    std::vector<HaloRun> send_pull, recv_pull, send_aa, recv_aa;
+    int64_t n_send_pull = 0, n_recv_pull = 0, n_send_aa = 0, n_recv_aa = 0;
+};
+
 // Sweep tile: x0, y0, z0 of a box of one block, `width` cells wide, (threads / width) rows
 // high and TZ planes deep; flags bit 0: some cell of the tile has a non-zero mask (the kernel
 // reads the mask).  The width adapts to the block: a block narrower than the CTA gets tiles
@@ -85,6 +106,11 @@ struct PlanInput {
     std::vector<BlockLayout> const *blocks;
     std::vector<std::vector<uint8_t>> const *flags;  // per block, interior, may be empty (all fluid)
     std::vector<WallParam> const *block_param;       // per block
+    // partitioned context: owner rank of every block (nullptr: this context owns all blocks);
+    // only blocks with owner == rank get tiles, links, masks and device storage, and the flags
+    // of every block must be known (the ghost shells of owned blocks take kinds from them)
+    std::vector<int32_t> const *owner = nullptr;
+    int rank = 0;
 };
 
 struct Plan {
@@ -109,10 +135,22 @@ struct Plan {
     std::vector<std::array<int32_t, 27>> nbr;
     std::vector<uint8_t> through;
     int64_t cells = 0, fluid_cells = 0;
+    // partitioned context: halo lists per peer rank (index = rank; empty for this rank).  A block
+    // with a neighbour on another rank keeps ghost copies (through = 0).
+    std::vector<PeerHalo> halo;
 };
 
-// Compute the padded layout of each block (alignment in bytes for rows).
-void layout_blocks(std::vector<BlockLayout> &blocks, int bytes_per_pdf, int q, int align_bytes, int64_t *total_elems);
+// Compute the padded layout of each block (alignment in bytes for rows).  With owner (one rank
+// of a partitioned run) only the blocks of `rank` are placed in the arena; the others get
+// offset -1.
+void layout_blocks(std::vector<BlockLayout> &blocks, int bytes_per_pdf, int q, int align_bytes, int64_t *total_elems,
+                   const std::vector<int32_t> *owner = nullptr, int rank = 0);
+
+// Partition blocks over nranks along the Morton (Z-order) curve of their centres: blocks in
+// curve order are cut into nranks contiguous pieces of nearly equal cell counts (weights, when
+// given, replace the cell counts).  owner[b] receives the rank of block b.
+void partition_morton(const std::vector<BlockLayout> &blocks, int nranks, const std::vector<double> *weights,
+                      std::vector<int32_t> &owner);
 
 // Validate the layout (non-overlapping blocks); returns an empty string or an error.
 std::string check_blocks(const std::vector<BlockLayout> &blocks);

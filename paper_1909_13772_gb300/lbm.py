@@ -56,6 +56,13 @@ _vp, _dp, _u8p, _i32p, _i64p, _u64p = (ctypes.c_void_p, _P(ctypes.c_double), _P(
                                        _P(ctypes.c_int32), _P(ctypes.c_int64), _P(ctypes.c_uint64))
 _SIGS = {
     "lbm_create_blocks": ([_P(lbm_params), _P(lbm_block_desc), ctypes.c_int32, _vp, _P(_vp)], ctypes.c_int),
+    "lbm_create_partition": ([_P(lbm_params), _P(lbm_block_desc), ctypes.c_int32, _i32p, ctypes.c_int32,
+                              ctypes.c_int32, _vp, _P(_vp)], ctypes.c_int),
+    "lbm_partition_morton": ([_P(lbm_block_desc), ctypes.c_int32, ctypes.c_int32, _dp, _i32p], ctypes.c_int),
+    "lbm_halo_sizes": ([_vp, ctypes.c_int32, _i64p, _i64p], ctypes.c_int),
+    "lbm_halo_pack": ([_vp, ctypes.c_int32, _vp], ctypes.c_int),
+    "lbm_halo_unpack": ([_vp, ctypes.c_int32, _vp], ctypes.c_int),
+    "lbm_plan_halo": ([_vp, ctypes.c_int32, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_required_bytes": ([_vp], ctypes.c_size_t),
     "lbm_bind_device_memory": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "lbm_set_face": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dp, ctypes.c_double], ctypes.c_int),
@@ -149,19 +156,77 @@ def _check(ctx, status):
 
 # ---- the C ABI under its own names ------------------------------------------------------
 
-def lbm_create_blocks(params: lbm_params, blocks, stream=None):
-    """blocks: sequence of (origin(3), size(3)).  Returns an opaque context handle."""
-    L = load_library()
+def _block_array(blocks):
     arr = (lbm_block_desc * len(blocks))()
     for k, (o, s) in enumerate(blocks):
         for a in range(3):
             arr[k].origin[a] = int(o[a])
             arr[k].size[a] = int(s[a])
+    return arr
+
+
+def lbm_create_blocks(params: lbm_params, blocks, stream=None):
+    """blocks: sequence of (origin(3), size(3)).  Returns an opaque context handle."""
+    L = load_library()
+    arr = _block_array(blocks)
     out = ctypes.c_void_p()
     st = L.lbm_create_blocks(ctypes.byref(params), arr, len(blocks), ctypes.c_void_p(stream or 0), ctypes.byref(out))
     if st != 0:
         raise LbmError(st, "lbm_create_blocks rejected the parameters or block layout")
     return out
+
+
+def lbm_create_partition(params: lbm_params, blocks, owner, nranks, rank, stream=None):
+    """A context of rank `rank` holding the blocks with owner[b] == rank."""
+    L = load_library()
+    arr = _block_array(blocks)
+    own = np.ascontiguousarray(owner, dtype=np.int32)
+    if own.shape != (len(blocks),):
+        raise ValueError("owner needs one entry per block")
+    out = ctypes.c_void_p()
+    st = L.lbm_create_partition(ctypes.byref(params), arr, len(blocks), _ptr(own, ctypes.c_int32), int(nranks),
+                                int(rank), ctypes.c_void_p(stream or 0), ctypes.byref(out))
+    if st != 0:
+        raise LbmError(st, "lbm_create_partition rejected the parameters, blocks or owner array")
+    return out
+
+
+def lbm_partition_morton(blocks, nranks, weights=None) -> np.ndarray:
+    """Owner rank of every block along the Morton curve of the block centres (host only)."""
+    L = load_library()
+    arr = _block_array(blocks)
+    own = np.zeros(len(blocks), dtype=np.int32)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64)
+    st = L.lbm_partition_morton(arr, len(blocks), int(nranks), _ptr(w, ctypes.c_double), _ptr(own, ctypes.c_int32))
+    if st != 0:
+        raise LbmError(st, "lbm_partition_morton rejected its arguments")
+    return own
+
+
+def lbm_halo_sizes(ctx, peer):
+    """(send, receive) elements of the exchange with `peer` that must precede the next step."""
+    ns, nr = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load_library().lbm_halo_sizes(ctx, int(peer), ctypes.byref(ns), ctypes.byref(nr)))
+    return ns.value, nr.value
+
+
+def lbm_halo_pack(ctx, peer, dev_ptr: int):
+    _check(ctx, load_library().lbm_halo_pack(ctx, int(peer), ctypes.c_void_p(dev_ptr)))
+
+
+def lbm_halo_unpack(ctx, peer, dev_ptr: int):
+    _check(ctx, load_library().lbm_halo_unpack(ctx, int(peer), ctypes.c_void_p(dev_ptr)))
+
+
+def lbm_plan_halo(ctx, peer, which) -> np.ndarray:
+    """Halo runs with `peer` (which: 0 send pull, 1 receive pull, 2 send AA, 3 receive AA) as
+    rows (arena offset, buffer offset, length, arena stride)."""
+    L = load_library()
+    n = ctypes.c_int64()
+    _check(ctx, L.lbm_plan_halo(ctx, int(peer), int(which), None, 0, ctypes.byref(n)))
+    out = np.zeros(4 * n.value, dtype=np.int64)
+    _check(ctx, L.lbm_plan_halo(ctx, int(peer), int(which), _ptr(out, ctypes.c_int64), 4 * n.value, ctypes.byref(n)))
+    return out.reshape(n.value, 4)
 
 
 def lbm_required_bytes(ctx) -> int:
@@ -484,11 +549,18 @@ class Simulation:
     """A context plus NumPy marshalling.  Per-block host arrays are [z, y, x] (scalars),
     [3, z, y, x] (velocity) and [q, z, y, x] (PDFs)."""
 
-    def __init__(self, params: lbm_params, blocks, stream=None, device_buffer=None):
+    def __init__(self, params: lbm_params, blocks, stream=None, device_buffer=None, owner=None, nranks=1, rank=0):
+        """owner (optional): owner rank of every block -- the context of rank `rank` of a
+        partitioned run (lbm_create_partition) holds only that rank's blocks."""
         self.params = params
         self.q = params.stencil
         self.blocks = [(tuple(int(v) for v in o), tuple(int(v) for v in s)) for o, s in blocks]
-        self.ctx = lbm_create_blocks(params, self.blocks, stream)
+        self.owner = None if owner is None else np.asarray(owner, dtype=np.int32)
+        self.rank, self.nranks = int(rank), int(nranks)
+        if self.owner is None:
+            self.ctx = lbm_create_blocks(params, self.blocks, stream)
+        else:
+            self.ctx = lbm_create_partition(params, self.blocks, self.owner, nranks, rank, stream)
         self._buffer = device_buffer
         if device_buffer is not None:
             lbm_bind_device_memory(self.ctx, device_buffer.data_ptr(), device_buffer.numel() * device_buffer.element_size())
