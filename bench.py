@@ -579,8 +579,11 @@ def measure_porous(args):
         lbm.lbm_set_batching(sim.ctx, False)
     if args.ghost:
         lbm.lbm_set_in_place(sim.ctx, False)
+    sparse = bool(getattr(args, "sparse", False))
+    if sparse:
+        lbm.lbm_set_sparse(sim.ctx, True)
     tuned = None
-    if args.autotune:
+    if args.autotune and not sparse:
         tuned = lbm.lbm_autotune(sim.ctx, 10)
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -611,6 +614,7 @@ def measure_porous(args):
     fill_ms = kt["fill"][0] / max(1, kt["fill"][1])
     bpp = info["bytes_per_pdf"]
     alg = 2 * 19 * bpp * fluid
+    table = 4 * 18 * fluid if sparse else 0  # the list layout's pull table, read once per step
     peak, peak_kind = measured_peaks()
     out = {"metric": "MFLUPS (fluid-cell lattice updates per second), porous bed", "value": round(flups / 1e6, 1),
            "unit": "MFLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -627,7 +631,10 @@ def measure_porous(args):
            "roofline": {"bound": "hbm", "achieved": round(alg / (sweep_ms / 1e3) / 1e9, 1), "peak": peak,
                         "unit": "GB/s", "frac": round(alg / (sweep_ms / 1e3) / 1e9 / peak, 4), "traffic": None,
                         "kernel": "k_sweep (fluid cells only)", "sweep_ms": round(sweep_ms, 4),
-                        "fill_ms": round(fill_ms, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+                        "fill_ms": round(fill_ms, 4), "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind,
+                        "bytes": "fluid PDF bytes 2 Q s per fluid cell" + (" (plus the list table, 4 (Q - 1) B per fluid "
+                                                                           "cell: frac_with_table)" if sparse else ""),
+                        "frac_with_table": round((alg + table) / (sweep_ms / 1e3) / 1e9 / peak, 4) if sparse else None},
            # the time a step spends outside its kernels: launch gaps (graph replay when --graph)
            "launch_gap_ms_per_step": round(tmax * 1e3 / args.steps - sweep_ms - fill_ms, 4),
            "cpu_baseline": (cpu_baseline_porous(min_seconds=getattr(args, "cpu_seconds", 10.0))
@@ -636,6 +643,7 @@ def measure_porous(args):
            "graph": bool(args.graph), "autotuned_tile": list(tuned[0]) if tuned else None,
            "autotuned_in_place": tuned[2] if tuned else None,
            "launch": "one sweep launch per block" if args.per_block else "one batched sweep launch",
+           "layout": "fluid-cell list (lbm_set_sparse)" if sparse else "dense blocks",
            "neighbours": ("in place where faces match" if (tuned[2] if tuned else not args.ghost)
                           else "ghost-layer copies")}
     return out
@@ -996,9 +1004,12 @@ def measure_workloads(args):
         ("c3_turbulence", measure_turbulence, sub(steps=2000, turb_size=512, turb_err_size=128,
                                                   turb_perf_steps=min(max(k, 20), 100), turb_tile=True,
                                                   turb_fp64_perf=False, cpu_seconds=5.0)),
-        ("c4_porous_bed", measure_porous, sub(steps=min(max(k, 20), 100), graph=True, autotune=True,
+        ("c4_porous_bed", measure_porous, sub(steps=min(max(k, 20), 100), graph=True, autotune=False,
                                               per_block=False, ghost=False, porous_blocks=16, cpu_seconds=5.0,
-                                              variant="fp32-twogrid")),
+                                              variant="fp32-twogrid", sparse=True)),
+        ("c4_porous_bed_dense", measure_porous, sub(steps=min(max(k, 20), 100), graph=True, autotune=True,
+                                                    per_block=False, ghost=False, porous_blocks=16,
+                                                    no_cpu_baseline=True, variant="fp32-twogrid", sparse=False)),
         ("c5_closure", measure_closure, sub(steps=min(max(k, 20), 100), closure_sizes="128",
                                             closure_kinds="trt,smagorinsky,mlp", cpu_seconds=5.0)),
     ]
@@ -1059,6 +1070,7 @@ def main(argv=None):
                     help="porous: pick the sweep tile and the neighbour mode with lbm_autotune")
     ap.add_argument("--per-block", action="store_true", help="porous: one sweep launch per block (comparison)")
     ap.add_argument("--ghost", action="store_true", help="porous: ghost-layer copies instead of in-place neighbours")
+    ap.add_argument("--sparse", action="store_true", help="porous: the fluid-cell list layout of the two-grid sweep")
     ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure", "tgv"], default="channel",
                     help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed; "
                          "tgv: the 32^3 Taylor-Green correctness configuration; "

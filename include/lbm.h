@@ -125,6 +125,8 @@ typedef struct {
     int64_t device_bytes;   /* device memory held by the context */
     int64_t staged_tiles;   /* tiles whose source rows the two-grid sweep stages in shared
                                memory by bulk copies (16-bit storage, unmasked full-width tiles) */
+    int64_t list_entries;   /* fluid-cell list layout (lbm_set_sparse): entries per direction
+                               (fluid cells + boundary link slots); 0 for the dense layout */
 } lbm_info;
 
 /* Create a context for `nblocks` blocks.  `cuda_stream` is a cudaStream_t (or NULL for the
@@ -494,6 +496,30 @@ void lbm_mlp_destroy(lbm_mlp *m);
  * Errors: LBM_ERR_STATE when an AA context is after an odd number of steps (its two forms of
  * the odd layout differ: switch after an even number). */
 lbm_status lbm_set_in_place(lbm_ctx *ctx, int32_t enable);
+
+/* Fluid-cell list layout of the two-grid sweep (enable != 0) or the dense block layout (0,
+ * default).  The list layout keeps only fluid cells -- numbered block by block in (z, y, x)
+ * order, one array per direction plus one slot per velocity/pressure link -- and a table with
+ * the pull source of each direction of each cell (a fluid cell of the same or a neighbour
+ * block, a link slot, or halfway bounce-back): on porous geometries a dense block spends DRAM
+ * sectors and warp lanes on solid cells, the list does not (4 (Q - 1) bytes of table per cell
+ * and step instead).  Every cell does the dense sweep's arithmetic: results are the same bit
+ * for bit.  The dense arrays stay allocated: the state moves to the list before the next
+ * step and back when a call reads or writes PDFs (get/set/init/macroscopic/reduce).  Graph
+ * replay works; lbm_autotune is refused.
+ * Errors: LBM_ERR_UNSUPPORTED for the AA pattern, a partitioned context, MRT or a closure.
+ * Paper: Sec. 4.4 (boundary handling by index lists), Sec. 5.1.3 (porous beds of randomly
+ * arranged spheres); the list layout itself has no counterpart there. */
+lbm_status lbm_set_sparse(lbm_ctx *ctx, int32_t enable);
+
+/* Host-only inspection of the fluid-cell list layout: what = 0 the pull table ((Q - 1) x
+ * fluid cells, direction-major: entry index, or INT32_MIN for halfway bounce-back), 1 the
+ * block of each fluid cell, 2 its padded-layout cell index in that block, 3 the link words
+ * (bits 0-4 direction q, 5-6 kind, 10-17 wall parameter, 32-63 fluid cell; link k fills entry
+ * fluid cells + k of direction opp(q)), each as int64.  out = NULL: *n only.
+ * Errors: LBM_ERR_STATE unless lbm_set_sparse is on.
+ * Paper: Sec. 4.4 (index lists); the list layout itself has no counterpart there. */
+lbm_status lbm_plan_sparse(lbm_ctx *ctx, int32_t what, int64_t *out, int64_t cap, int64_t *n);
 
 /* Per-block diagnostics of the stored state (the per-block reductions of the paper's
  * per-block data layout, Sec. 4.1-4.2): out[8 b + k] for block b, k = mass, momentum x, y, z,

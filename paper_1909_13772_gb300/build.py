@@ -2,8 +2,8 @@
 
 Translation units: api.cu (C ABI, scheduler), plan.cpp (host list builder, OpenMP), diag.cu,
 reduce_static.cu, closure.cu (closure sweep and network kernels, D3Q19 FP32), halo.cu (halo
-pack/unpack of partitioned runs), sweep.cu / aux.cu compiled once per (stencil, storage)
-variant, and sweep.cu once more per (stencil, FP64/FP32) with the MRT collision.  Objects are compiled in
+pack/unpack of partitioned runs), sweep.cu / aux.cu / sweep_sparse.cu (the fluid-cell list
+sweep) compiled once per (stencil, storage) variant, and sweep.cu once more per (stencil, FP64/FP32) with the MRT collision.  Objects are compiled in
 parallel; the library lands in ``paper_1909_13772_gb300/_build/liblbm.so``.
 """
 from __future__ import annotations
@@ -47,7 +47,7 @@ def _jobs(nvcc, extra, build_dir):
         lang = [] if name.endswith(".cu") else ["-x", "cu"]
         jobs.append([nvcc] + ARCH + NVFLAGS + extra + lang + ["-c", src, "-o", obj])
     for q, st in VARIANTS:
-        for name in ("sweep.cu", "aux.cu"):
+        for name in ("sweep.cu", "aux.cu", "sweep_sparse.cu"):
             src = os.path.join(CSRC, name)
             obj = os.path.join(build_dir, "%s_%d_%d.o" % (name[:-3], q, st))
             jobs.append([nvcc] + ARCH + NVFLAGS + extra + ["-DLBM_Q=%d" % q, "-DLBM_ST=%d" % st, "-c", src, "-o", obj])

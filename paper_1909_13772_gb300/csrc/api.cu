@@ -40,6 +40,16 @@ struct lbm_ctx {
     std::vector<int32_t> owner;
     int rank = 0, nranks = 1;
     std::vector<HaloDevRun *> d_halo;  // per peer, 4 lists: send pull, recv pull, send AA, recv AA
+    // fluid-cell list layout of the two-grid sweep (lbm_set_sparse): two list arrays (state in
+    // sarr[cur]), the pull table, links, cell maps; which of the layouts holds the state
+    bool sparse = false;
+    bool list_valid = false, dense_valid = true;
+    void *sarr_raw = nullptr;
+    void *sarr[2] = {nullptr, nullptr};
+    int64_t s_stride = 0;
+    int32_t *d_snbr = nullptr, *d_sblock = nullptr;
+    int64_t *d_scell = nullptr;
+    uint64_t *d_slinks = nullptr;
 
     // device state
     bool dev_ready = false;
@@ -207,6 +217,7 @@ lbm_status build_lists(lbm_ctx *c)
     in.block_param = &c->block_param;
     in.owner = c->owner.empty() ? nullptr : &c->owner;
     in.rank = c->rank;
+    in.sparse = c->sparse ? 1 : 0;
     std::string e = build_plan(in, c->plan);
     if (!e.empty()) return fail(c, LBM_ERR_UNSUPPORTED, "%s", e.c_str());
     if ((int64_t)c->plan.tiles.size() > 0x7fffffffLL) return fail(c, LBM_ERR_UNSUPPORTED, "too many tiles");
@@ -375,7 +386,33 @@ lbm_status ensure_lists(lbm_ctx *c)
         par.push_back(w.rho);
     }
     if ((s2 = upload(c, c->d_params, par, "upload params")) != LBM_OK) return s2;
-    const int64_t need = std::max<int64_t>(1, (int64_t)P.tiles.size()) * 8;
+    // the list layout: tables, links, cell maps and its two arrays
+    dfree(c->d_snbr);
+    dfree(c->d_sblock);
+    dfree(c->d_scell);
+    dfree(c->d_slinks);
+    if (c->sarr_raw) cudaFree(c->sarr_raw);
+    c->sarr_raw = c->sarr[0] = c->sarr[1] = nullptr;
+    c->list_valid = false;
+    if (c->sparse) {
+        const SparsePlan &SP = P.sparse;
+        if ((s2 = upload(c, c->d_snbr, SP.nbr, "upload list table")) != LBM_OK) return s2;
+        if ((s2 = upload(c, c->d_sblock, SP.block_of, "upload list cell map")) != LBM_OK) return s2;
+        if ((s2 = upload(c, c->d_scell, SP.cell_of, "upload list cell map")) != LBM_OK) return s2;
+        if ((s2 = upload(c, c->d_slinks, SP.links, "upload list links")) != LBM_OK) return s2;
+        // entries per direction rounded to 256 bytes, so every direction starts aligned
+        const int64_t per = 256 / c->bpp;
+        c->s_stride = std::max<int64_t>(per, (SP.nslots + per - 1) / per * per);
+        const size_t one = (size_t)c->s_stride * c->q * c->bpp;
+        CK(cudaMalloc(&c->sarr_raw, 2 * one + 256), "cudaMalloc(list arrays)");
+        CK(cudaMemsetAsync(c->sarr_raw, 0, 2 * one + 256, c->stream), "clear list arrays");
+        c->list_bytes += 2 * one + 256;
+        const uintptr_t b0 = ((uintptr_t)c->sarr_raw + 255) & ~(uintptr_t)255;
+        c->sarr[0] = (void *)b0;
+        c->sarr[1] = (void *)(b0 + one);
+    }
+    const int64_t list_ctas = c->sparse ? (P.sparse.nfluid + 255) / 256 : 0;
+    const int64_t need = std::max<int64_t>(1, std::max<int64_t>((int64_t)P.tiles.size(), list_ctas)) * 8;
     if (need > c->partials_cap) {
         dfree(c->d_partials);
         dfree(c->d_step_partials);
@@ -498,6 +535,70 @@ const std::vector<HaloRun> &halo_runs(const lbm_ctx *c, int peer, int k)
 {
     const PeerHalo &h = c->plan.halo[peer];
     return k == 0 ? h.send_pull : (k == 1 ? h.recv_pull : (k == 2 ? h.send_aa : h.recv_aa));
+}
+
+// Records of the per-CTA diagnostics the last sweep wrote (tiles, or CTAs of the list sweep).
+int64_t diag_records(const lbm_ctx *c)
+{
+    return c->sparse ? (c->plan.sparse.nfluid + 255) / 256 : (int64_t)c->plan.tiles.size();
+}
+
+lbm_status sparse_args(lbm_ctx *c, int op, SparseArgs &a)
+{
+    a = SparseArgs{};
+    a.op = op;
+    a.nbr = c->d_snbr;
+    a.links = c->d_slinks;
+    a.nlinks = (int64_t)c->plan.sparse.links.size();
+    a.params = c->d_params;
+    a.blocks = c->d_blocks;
+    a.block_of = c->d_sblock;
+    a.cell_of = c->d_scell;
+    a.nfluid = c->plan.sparse.nfluid;
+    a.stride = c->s_stride;
+    a.force = c->force ? 1 : 0;
+    a.cd = c->cd;
+    a.cf = c->cf;
+    a.stream = c->stream;
+    return LBM_OK;
+}
+
+cudaError_t do_sparse(int q, int st, const SparseArgs &s) { LBM_SWITCH(q, st, launch_sparse_, s); }
+
+// The list layout holds the state (copy it from the dense array if it does not).
+lbm_status ensure_list(lbm_ctx *c)
+{
+    if (!c->sparse || c->list_valid) return LBM_OK;
+    SparseArgs a;
+    sparse_args(c, SPARSE_TO_LIST, a);
+    a.dense = c->arr[c->cur];
+    a.list = c->sarr[c->cur];
+    CK(do_sparse(c->q, c->storage, a), "dense to list copy");
+    c->launches++;
+    c->list_valid = true;
+    return LBM_OK;
+}
+
+// The dense arrays hold the state (copy it back from the list layout if they do not).
+lbm_status ensure_dense(lbm_ctx *c)
+{
+    if (!c->sparse || c->dense_valid) return LBM_OK;
+    SparseArgs a;
+    sparse_args(c, SPARSE_TO_DENSE, a);
+    a.dense = c->arr[c->cur];
+    a.list = c->sarr[c->cur];
+    CK(do_sparse(c->q, c->storage, a), "list to dense copy");
+    c->launches++;
+    c->dense_valid = true;
+    return LBM_OK;
+}
+
+// A setter is about to rebuild the lists: a state held only by the list layout goes back to
+// the dense arrays first (the rebuilt lists may number the fluid cells differently).
+lbm_status before_replan(lbm_ctx *c)
+{
+    if (c->sparse && c->dev_ready && c->plan_uploaded) return ensure_dense(c);
+    return LBM_OK;
 }
 
 lbm_status check_peer(lbm_ctx *c, int32_t peer)
@@ -839,6 +940,8 @@ lbm_status lbm_set_face(lbm_ctx *c, int32_t axis, int32_t side, int32_t kind, co
         return LBM_OK;
     }
     if (!std::isfinite(rho_wall) || rho_wall <= 0.0) return fail(c, LBM_ERR_ARG, "bad wall density");
+    lbm_status s0 = before_replan(c);
+    if (s0 != LBM_OK) return s0;
     const int f = 2 * axis + side;
     c->face_kind[f] = kind;
     for (int a = 0; a < 3; ++a) c->face_param[f].u[a] = u_wall ? u_wall[a] : 0.0;
@@ -855,6 +958,7 @@ lbm_status lbm_set_boundary(lbm_ctx *c, int32_t block, const uint8_t *flags, con
     const BlockLayout &L = c->blocks[block];
     const size_t N = (size_t)L.n[0] * L.n[1] * L.n[2];
     if (!std::isfinite(rho_wall) || rho_wall <= 0.0) return fail(c, LBM_ERR_ARG, "bad wall density");
+    if ((s = before_replan(c)) != LBM_OK) return s;
     if (!flags) {
         c->flags[block].clear();
     } else {
@@ -875,6 +979,7 @@ lbm_status lbm_init_macroscopic(lbm_ctx *c, int32_t block, const double *rho, co
     if (s != LBM_OK) return s;
     if (!rho || !u) return fail(c, LBM_ERR_ARG, "null rho or u");
     if ((s = prepare(c)) != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     const BlockLayout &L = c->blocks[block];
     const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
     if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
@@ -883,6 +988,7 @@ lbm_status lbm_init_macroscopic(lbm_ctx *c, int32_t block, const double *rho, co
     CellArgs a = cell_args(c, block);
     a.f64 = c->d_scratch;
     CK(do_cells(c->q, c->storage, CELL_INIT, c->force ? 1 : 0, a), "init kernel");
+    c->list_valid = false;  // the dense arrays hold the new state
     c->step_diag_valid = false;
     CK(cudaStreamSynchronize(c->stream), "init");
     return LBM_OK;
@@ -951,6 +1057,35 @@ lbm_status issue_step(lbm_ctx *c, SweepArgs &sw, FillArgs &fa, bool diag, bool t
         sw.kind = even ? SWEEP_AA_NBR : SWEEP_AA_LOCAL;
     }
     int e0 = -1, e1 = -1, e2 = -1;
+    if (c->sparse) {
+        // the fluid-cell list layout: link slots, then the list sweep (two-grid)
+        if ((s = ensure_list(c)) != LBM_OK) return s;
+        SparseArgs fl, sp;
+        sparse_args(c, SPARSE_FILL, fl);
+        fl.dst = c->sarr[c->cur];
+        sparse_args(c, SPARSE_SWEEP, sp);
+        sp.src = c->sarr[c->cur];
+        sp.dst = c->sarr[1 - c->cur];
+        sp.partials = diag ? c->d_step_partials : nullptr;
+        if (trace && (s = mark(c, &e0)) != LBM_OK) return s;
+        if (fl.nlinks > 0) {
+            CK(do_sparse(c->q, c->storage, fl), "list boundary fill launch");
+            c->launches++;
+        }
+        if (trace && (s = mark(c, &e1)) != LBM_OK) return s;
+        if (sp.nfluid > 0) {
+            CK(do_sparse(c->q, c->storage, sp), "list sweep launch");
+            c->launches++;
+        }
+        if (trace) {
+            if ((s = mark(c, &e2)) != LBM_OK) return s;
+            if (fl.nlinks > 0) c->ev_marks[0].push_back({e0, e1});
+            if (sp.nfluid > 0) c->ev_marks[1].push_back({e1, e2});
+        }
+        c->cur = 1 - c->cur;
+        c->dense_valid = false;
+        return LBM_OK;
+    }
     if (trace && (s = mark(c, &e0)) != LBM_OK) return s;
     if (fa.nlinks + fa.nruns > 0) {
         CK(do_fill(c->q, c->storage, fa), "boundary/ghost fill launch");
@@ -1055,6 +1190,8 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
     if (s != LBM_OK) return s;
     if (n > 1 && has_halo(c))
         return fail(c, LBM_ERR_STATE, "partitioned context: one step per call (the halo exchange comes between steps)");
+    if ((s = ensure_list(c)) != LBM_OK) return s;  // outside any graph capture
+    if (c->sparse && n > 0) c->dense_valid = false;  // replayed graphs do not pass through issue_step
     SweepArgs sw;
     FillArgs fa;
     step_args(c, sw, fa);
@@ -1119,6 +1256,8 @@ lbm_status lbm_set_in_place(lbm_ctx *c, int32_t enable)
         // or in neighbour cells (in-place mode): the two forms only agree in the even layout
         if (c->pattern == LBM_AA && c->aa_layout != LAYOUT_AA_E)
             return fail(c, LBM_ERR_STATE, "switch the neighbour mode of an AA context after an even number of steps");
+        lbm_status s = before_replan(c);
+        if (s != LBM_OK) return s;
         c->in_place = enable != 0;
         c->plan_built = false;  // rebuilt (and re-uploaded) before the next step
         drop_graphs(c);
@@ -1152,6 +1291,7 @@ lbm_status lbm_autotune(lbm_ctx *c, int32_t trial_steps, int32_t best[3], int32_
     if (!c || !best) return LBM_ERR_ARG;
     if (trial_steps < 1) return fail(c, LBM_ERR_ARG, "trial_steps must be >= 1");
     if (!c->owner.empty()) return fail(c, LBM_ERR_UNSUPPORTED, "autotune runs steps without a halo exchange");
+    if (c->sparse) return fail(c, LBM_ERR_UNSUPPORTED, "autotune picks dense tiles; the list layout has none");
     lbm_status s = prepare(c);
     if (s != LBM_OK) return s;
     // keep the simulation state: snapshot the PDF arrays, start every trial from it, restore
@@ -1237,6 +1377,7 @@ lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u
     if (s != LBM_OK) return s;
     if (!rho || !u) return fail(c, LBM_ERR_ARG, "null output");
     if ((s = prepare(c)) != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     const BlockLayout &L = c->blocks[block];
     const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
     if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
@@ -1261,6 +1402,7 @@ lbm_status lbm_coarse_moments(lbm_ctx *c, int32_t block, int32_t ratio, double *
         return fail(c, LBM_ERR_ARG, "block %d (%d x %d x %d) is not divisible by ratio %d", block, L.n[0], L.n[1], L.n[2],
                     ratio);
     if ((s = prepare(c)) != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     const int64_t Nc = (int64_t)(L.n[0] / ratio) * (L.n[1] / ratio) * (L.n[2] / ratio);
     if ((s = ensure_scratch(c, 10 * Nc)) != LBM_OK) return s;
     CellArgs a = cell_args(c, block);
@@ -1280,6 +1422,7 @@ lbm_status lbm_get_pdfs(lbm_ctx *c, int32_t block, double *f)
     if (s != LBM_OK) return s;
     if (!f) return fail(c, LBM_ERR_ARG, "null output");
     if ((s = prepare(c)) != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     const BlockLayout &L = c->blocks[block];
     const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
     if ((s = ensure_scratch(c, (int64_t)c->q * N)) != LBM_OK) return s;
@@ -1303,6 +1446,7 @@ lbm_status lbm_get_pdfs_region(lbm_ctx *c, int32_t block, const int32_t origin[3
         if (size[a] < 1 || origin[a] < 0 || (int64_t)origin[a] + size[a] > L.n[a])
             return fail(c, LBM_ERR_ARG, "region outside block %d along axis %d", block, a);
     if ((s = prepare(c)) != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     const int64_t N = (int64_t)size[0] * size[1] * size[2];
     if ((s = ensure_scratch(c, (int64_t)c->q * N)) != LBM_OK) return s;
     CellArgs a = cell_args(c, block);
@@ -1325,6 +1469,7 @@ lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
     if (s != LBM_OK) return s;
     if (!f) return fail(c, LBM_ERR_ARG, "null input");
     if ((s = prepare(c)) != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     const BlockLayout &L = c->blocks[block];
     const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
     if ((s = ensure_scratch(c, (int64_t)c->q * N)) != LBM_OK) return s;
@@ -1333,6 +1478,7 @@ lbm_status lbm_set_pdfs(lbm_ctx *c, int32_t block, const double *f)
     CellArgs a = cell_args(c, block);
     a.f64 = c->d_scratch;
     CK(do_cells(c->q, c->storage, CELL_SET, 0, a), "set_pdfs kernel");
+    c->list_valid = false;  // the dense arrays hold the new state
     c->step_diag_valid = false;
     CK(cudaStreamSynchronize(c->stream), "set_pdfs");
     return LBM_OK;
@@ -1343,6 +1489,7 @@ lbm_status lbm_reduce_blocks(lbm_ctx *c, double *out)
     if (!c || !out) return LBM_ERR_ARG;
     lbm_status s = prepare(c);
     if (s != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     const int64_t nb = (int64_t)c->blocks.size();
     std::fill(out, out + 8 * nb, 0.0);
     if (c->plan.tiles.empty()) return LBM_OK;
@@ -1378,6 +1525,7 @@ lbm_status lbm_reduce(lbm_ctx *c, lbm_diagnostics *out)
     if (!c || !out) return LBM_ERR_ARG;
     lbm_status s = prepare(c);
     if (s != LBM_OK) return s;
+    if ((s = ensure_dense(c)) != LBM_OK) return s;
     double h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (!c->plan.tiles.empty()) {
         ReduceArgs r{};
@@ -1426,9 +1574,8 @@ lbm_status lbm_step_diagnostics(lbm_ctx *c, lbm_diagnostics *out)
     if (!c->step_diag_valid || !c->h_io) return fail(c, LBM_ERR_STATE, "no step has run since the state was last set");
     double *h = c->h_io->diag;
     std::fill(h, h + 8, 0.0);
-    if (!c->plan.tiles.empty()) {
-        CK(launch_reduce_final(c->d_step_partials, (int64_t)c->plan.tiles.size(), c->d_out, c->stream),
-           "diagnostics kernel");
+    if (diag_records(c) > 0) {
+        CK(launch_reduce_final(c->d_step_partials, diag_records(c), c->d_out, c->stream), "diagnostics kernel");
         CK(cudaMemcpyAsync(h, c->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy diagnostics");
     }
     lbm_status ws = wait_status_enqueue(c);
@@ -1463,6 +1610,47 @@ lbm_status lbm_get_info(lbm_ctx *c, lbm_info *out)
     out->device_bytes = (int64_t)(c->arena_owned ? c->arena_bytes : 0) + (int64_t)c->list_bytes +
                         c->partials_cap * 8 + c->scratch_cap * 8;
     stage_tiles(c, P, nullptr, &out->staged_tiles);
+    out->list_entries = c->sparse ? P.sparse.nslots : 0;
+    if (c->sparse) out->links[LBM_VELOCITY] = out->links[LBM_PRESSURE] = 0;
+    for (const uint64_t w : P.sparse.links) out->links[(w >> 5) & 3u]++;
+    return LBM_OK;
+}
+
+lbm_status lbm_plan_sparse(lbm_ctx *c, int32_t what, int64_t *out, int64_t cap, int64_t *n)
+{
+    if (!c || !n) return LBM_ERR_ARG;
+    if (!c->sparse) return fail(c, LBM_ERR_STATE, "the context does not use the fluid-cell list layout");
+    if (what < 0 || what > 3) return fail(c, LBM_ERR_ARG, "bad list part %d", what);
+    lbm_status s = build_lists(c);
+    if (s != LBM_OK) return s;
+    const SparsePlan &S = c->plan.sparse;
+    const int64_t len = what == 0 ? (int64_t)S.nbr.size()
+                                  : (what == 1 ? S.nfluid : (what == 2 ? S.nfluid : (int64_t)S.links.size()));
+    *n = len;
+    if (!out) return LBM_OK;
+    if (cap < len) return fail(c, LBM_ERR_ARG, "buffer too small");
+    for (int64_t k = 0; k < len; ++k)
+        out[k] = what == 0 ? (int64_t)S.nbr[k]
+                           : (what == 1 ? S.block_of[k] : (what == 2 ? S.cell_of[k] : (int64_t)S.links[k]));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_sparse(lbm_ctx *c, int32_t enable)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (enable && c->pattern != LBM_TWO_GRID)
+        return fail(c, LBM_ERR_UNSUPPORTED, "the fluid-cell list layout is built for the two-grid pattern");
+    if (enable && (!c->owner.empty() || c->closure != CLOSURE_NONE || c->p.collision == LBM_MRT))
+        return fail(c, LBM_ERR_UNSUPPORTED, "the fluid-cell list layout is for SRT/TRT contexts holding every block, "
+                                            "without a closure");
+    if ((enable != 0) == c->sparse) return LBM_OK;
+    lbm_status s = LBM_OK;
+    if (c->dev_ready && (s = ensure_dense(c)) != LBM_OK) return s;  // the state moves back to the dense arrays
+    c->sparse = enable != 0;
+    c->plan_built = false;
+    c->dense_valid = true;
+    c->list_valid = false;
+    drop_graphs(c);
     return LBM_OK;
 }
 
@@ -1471,6 +1659,8 @@ lbm_status lbm_set_tile(lbm_ctx *c, int32_t tx, int32_t ty, int32_t tz)
     if (!c) return LBM_ERR_ARG;
     if (tx <= 0 || ty <= 0 || tz <= 0 || tx % 32 != 0 || tx * ty > 256 || tx > 32000 || ty > 32000 || tz > 32000)
         return fail(c, LBM_ERR_ARG, "bad tile %d x %d x %d (tx multiple of 32, tx*ty <= 256)", tx, ty, tz);
+    lbm_status s = before_replan(c);
+    if (s != LBM_OK) return s;
     c->tile[0] = tx;
     c->tile[1] = ty;
     c->tile[2] = tz;
@@ -1633,6 +1823,11 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_runs_pull);
     dfree(c->d_runs_aa);
     for (HaloDevRun *&h : c->d_halo) dfree(h);
+    dfree(c->d_snbr);
+    dfree(c->d_sblock);
+    dfree(c->d_scell);
+    dfree(c->d_slinks);
+    if (c->sarr_raw) cudaFree(c->sarr_raw);
     dfree(c->d_tiles);
     dfree(c->d_params);
     dfree(c->d_masks);

@@ -68,6 +68,33 @@ struct HaloArgs {
 };
 cudaError_t launch_halo(const HaloArgs &h);
 
+// The fluid-cell list layout of the two-grid sweep (sweep_sparse.cu, plan.hpp SparsePlan).
+enum SparseOp { SPARSE_SWEEP = 0, SPARSE_FILL = 1, SPARSE_TO_LIST = 2, SPARSE_TO_DENSE = 3 };
+// table entry of a no-slip source: halfway bounce-back from the cell's own opposite slot
+// (the same value as plan.hpp kSparseBounce)
+constexpr int32_t kListBounce = (int32_t)0x80000000u;
+struct SparseArgs {
+    int op;
+    const void *src;  // sweep: source list array
+    void *dst;        // sweep: destination list array; fill: the array the next sweep reads
+    void *dense;      // copies: a dense PDF array
+    void *list;       // copies: a list array
+    const int32_t *nbr;       // (Q - 1) x nfluid pull sources
+    const uint64_t *links;    // link words (fill)
+    int64_t nlinks;
+    const double *params;     // wall table (fill)
+    const DevBlock *blocks;   // copies
+    const int32_t *block_of;  // copies
+    const int64_t *cell_of;   // copies
+    int64_t nfluid;
+    int64_t stride;   // entries per direction (>= nfluid + links, padded)
+    int force;
+    double *partials;  // sweep: per-CTA diagnostics records or null
+    Coll<double> cd;
+    Coll<float> cf;
+    cudaStream_t stream;
+};
+
 // Per-cell kernels over the interior cells of one block (get/set/macroscopic/init).
 struct CellArgs {
     void *a;
@@ -134,6 +161,16 @@ LBM_DECLARE(27, 1)
 LBM_DECLARE(27, 2)
 LBM_DECLARE(27, 3)
 #undef LBM_DECLARE
+#define LBM_DECLARE_SPARSE(Q, ST) cudaError_t launch_sparse_##Q##_##ST(const SparseArgs &s);
+LBM_DECLARE_SPARSE(19, 0)
+LBM_DECLARE_SPARSE(19, 1)
+LBM_DECLARE_SPARSE(19, 2)
+LBM_DECLARE_SPARSE(19, 3)
+LBM_DECLARE_SPARSE(27, 0)
+LBM_DECLARE_SPARSE(27, 1)
+LBM_DECLARE_SPARSE(27, 2)
+LBM_DECLARE_SPARSE(27, 3)
+#undef LBM_DECLARE_SPARSE
 // MRT sweeps (FP64 and FP32 storage)
 cudaError_t launch_sweep_mrt_19_0(const SweepArgs &s);
 cudaError_t launch_sweep_mrt_19_1(const SweepArgs &s);

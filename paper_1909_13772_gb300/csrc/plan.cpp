@@ -178,6 +178,8 @@ void append_run(std::vector<GhostRun> &runs, int64_t src, int64_t dst, int32_t s
 }
 
 struct BlockOut {
+    std::vector<int32_t> snbr;        // sparse layout: (Q - 1) x (fluid cells of the block), local link marks
+    std::vector<uint64_t> slinks;     // sparse layout: the block's link slots, local order
     std::vector<HaloElem> send, recv;  // partitioned context: halo elements of this block's shell
     std::vector<uint64_t> links[4];
     std::vector<GhostRun> runs_pull, runs_aa;
@@ -320,6 +322,23 @@ std::string build_plan(const PlanInput &in, Plan &out)
 
     std::vector<BlockOut> bo(nb);
     std::string err;
+    // sparse layout, first pass: number the fluid cells of every block (z, y, x order)
+    std::vector<std::vector<int32_t>> fidx(in.sparse ? nb : 0);
+    std::vector<int64_t> fstart(nb + 1, 0);
+    if (in.sparse) {
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int b = 0; b < nb; ++b) {
+            const auto &B = blocks[b];
+            const size_t N = (size_t)B.n[0] * B.n[1] * B.n[2];
+            fidx[b].assign(N, -1);
+            int32_t k = 0;
+            for (size_t c = 0; c < N; ++c)
+                if (flags[b].empty() || flags[b][c] == K_FLUID) fidx[b][c] = k++;
+            fstart[b + 1] = k;
+        }
+        for (int b = 0; b < nb; ++b) fstart[b + 1] += fstart[b];
+        if (fstart[nb] >= ((int64_t)1 << 30)) return "sparse layout: too many fluid cells (max 2^30)";
+    }
 #pragma omp parallel for schedule(dynamic, 1)
     for (int b = 0; b < nb; ++b) {
         const auto &B = blocks[b];
@@ -341,6 +360,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
         std::vector<uint16_t> param(np, 0);
         std::vector<int32_t> sblock(np, -1);
         std::vector<int64_t> scell(np, 0);
+        std::vector<int64_t> slin(in.sparse ? np : 0, 0);  // sparse: source cell's linear interior index
         const std::vector<uint8_t> &fl = flags[b];
         BlockOut &o = bo[b];
         bool has_solid = false;
@@ -380,6 +400,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
                             kind[p] = K_MIRROR;
                             sblock[p] = cd.block;
                             scell[p] = C.cell(cx, cy, cz);
+                            if (in.sparse) slin[p] = cx + (int64_t)C.n[0] * (cy + (int64_t)C.n[1] * cz);
                         } else {
                             kind[p] = k;
                             param[p] = (uint16_t)bparam[cd.block];
@@ -429,6 +450,37 @@ std::string build_plan(const PlanInput &in, Plan &out)
                                                           S.offset + (int64_t)j * S.slab + scell[p]});
                         }
             continue;
+        }
+        // sparse layout: the pull source of every direction of every fluid cell
+        if (in.sparse) {
+            const int64_t nf = fstart[b + 1] - fstart[b];
+            o.snbr.assign((size_t)(L.q - 1) * nf, 0);
+            int64_t n = 0;
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) {
+                        if (kind[pidx(x, y, z)] != K_FLUID) continue;
+                        for (int i = 1; i < L.q; ++i) {
+                            const int sx = x - L.cx[i], sy = y - L.cy[i], sz = z - L.cz[i];
+                            const int64_t p = pidx(sx, sy, sz);
+                            const uint8_t k = kind[p];
+                            int32_t v;
+                            if (k == K_FLUID) {
+                                v = (int32_t)(fstart[b] + fidx[b][sx + (size_t)nx * (sy + (size_t)ny * sz)]);
+                            } else if (k == K_MIRROR) {
+                                v = (int32_t)(fstart[sblock[p]] + fidx[sblock[p]][slin[p]]);
+                            } else if (k == K_VELOCITY || k == K_PRESSURE) {
+                                // link slot (local number, made global below): the link of fluid
+                                // cell x along opp(i), whose value the sweep reads as direction i
+                                v = (int32_t)(0x40000000u | (uint32_t)o.slinks.size());
+                                o.slinks.push_back(pack_link(L.opp[i], k, param[p], 0, fstart[b] + n));
+                            } else {
+                                v = kSparseBounce;
+                            }
+                            o.snbr[(size_t)(i - 1) * nf + n] = v;
+                        }
+                        ++n;
+                    }
         }
         // links: fluid interior cell x, direction q with a boundary neighbour
         for (int qd = 1; qd < L.q; ++qd) {
@@ -547,6 +599,43 @@ std::string build_plan(const PlanInput &in, Plan &out)
             out.link_count[k] += (int64_t)bo[b].links[k].size();
         }
     for (int b = 0; b < nb; ++b) out.link_count[K_NOSLIP] += bo[b].bounce;
+    // sparse layout: global link slots, the index table direction-major, the cell maps
+    out.sparse = SparsePlan{};
+    if (in.sparse) {
+        SparsePlan &S = out.sparse;
+        S.nfluid = fstart[nb];
+        S.block_start = fstart;
+        std::vector<int64_t> lbase(nb + 1, 0);
+        for (int b = 0; b < nb; ++b) lbase[b + 1] = lbase[b] + (int64_t)bo[b].slinks.size();
+        S.nslots = S.nfluid + lbase[nb];
+        if (S.nslots >= ((int64_t)1 << 30)) return "sparse layout: too many entries (max 2^30)";
+        for (int b = 0; b < nb; ++b) S.links.insert(S.links.end(), bo[b].slinks.begin(), bo[b].slinks.end());
+        S.nbr.assign((size_t)(L.q - 1) * S.nfluid, 0);
+        S.block_of.assign(S.nfluid, 0);
+        S.cell_of.assign(S.nfluid, 0);
+#pragma omp parallel for schedule(dynamic, 4)
+        for (int b = 0; b < nb; ++b) {
+            const auto &B = blocks[b];
+            const int64_t nf = fstart[b + 1] - fstart[b];
+            for (int i = 1; i < L.q; ++i)
+                for (int64_t n = 0; n < nf; ++n) {
+                    int32_t v = bo[b].snbr[(size_t)(i - 1) * nf + n];
+                    if (v != kSparseBounce && (v & 0x40000000))
+                        v = (int32_t)(S.nfluid + lbase[b] + (v & 0x3fffffff));
+                    S.nbr[(size_t)(i - 1) * S.nfluid + fstart[b] + n] = v;
+                }
+            int64_t n = fstart[b];
+            for (int z = 0; z < B.n[2]; ++z)
+                for (int y = 0; y < B.n[1]; ++y)
+                    for (int x = 0; x < B.n[0]; ++x)
+                        if (fidx[b][x + (size_t)B.n[0] * (y + (size_t)B.n[1] * z)] >= 0) {
+                            S.block_of[n] = b;
+                            S.cell_of[n] = B.cell(x, y, z);
+                            ++n;
+                        }
+            std::vector<int32_t>().swap(bo[b].snbr);
+        }
+    }
     // halo lists per peer, elements in block order (the same order on both sides)
     out.halo.clear();
     if (in.owner) {

@@ -111,6 +111,25 @@ struct PlanInput {
     // of every block must be known (the ghost shells of owned blocks take kinds from them)
     std::vector<int32_t> const *owner = nullptr;
     int rank = 0;
+    int sparse = 0;  // also build the fluid-cell list layout (SparsePlan)
+};
+
+// Fluid-cell list layout of the two-grid sweep (for porous geometries, where a dense block
+// spends sectors and lanes on solid cells): the fluid cells of all blocks numbered block by
+// block in (z, y, x) order, n = 0 .. nfluid - 1; each direction's array holds nfluid entries
+// plus one slot per velocity/pressure boundary link (filled before each sweep, like the ghost
+// slot a dense block's link writes).  nbr[(i - 1) * nfluid + n] is the pull source of
+// direction i of cell n: the entry index (a fluid cell, here or in a neighbour block across a
+// face or a periodic image, or a link slot), or kSparseBounce: halfway bounce-back, read slot
+// opp(i) of n itself.
+constexpr int32_t kSparseBounce = (int32_t)0x80000000u;
+struct SparsePlan {
+    int64_t nfluid = 0, nslots = 0;
+    std::vector<int32_t> nbr;             // (Q - 1) x nfluid
+    std::vector<uint64_t> links;          // link k: pack_link(q, kind, param, 0, n); writes slot nfluid + k of opp(q)
+    std::vector<int32_t> block_of;        // block of each fluid cell
+    std::vector<int64_t> cell_of;         // its padded-layout cell index in that block
+    std::vector<int64_t> block_start;     // first fluid index of each block (+ nfluid at the end)
 };
 
 struct Plan {
@@ -138,6 +157,7 @@ struct Plan {
     // partitioned context: halo lists per peer rank (index = rank; empty for this rank).  A block
     // with a neighbour on another rank keeps ghost copies (through = 0).
     std::vector<PeerHalo> halo;
+    SparsePlan sparse;  // built when PlanInput.sparse is set
 };
 
 // Compute the padded layout of each block (alignment in bytes for rows).  With owner (one rank

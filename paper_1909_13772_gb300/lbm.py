@@ -47,7 +47,8 @@ class lbm_diagnostics(ctypes.Structure):
 class lbm_info(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_int64), ("fluid_cells", ctypes.c_int64), ("links", ctypes.c_int64 * 4),
                 ("ghost_slots", ctypes.c_int64), ("ghost_runs", ctypes.c_int64), ("tiles", ctypes.c_int64),
-                ("bytes_per_pdf", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("staged_tiles", ctypes.c_int64)]
+                ("bytes_per_pdf", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("staged_tiles", ctypes.c_int64),
+                ("list_entries", ctypes.c_int64)]
 
 
 _lib = None
@@ -63,6 +64,8 @@ _SIGS = {
     "lbm_halo_pack": ([_vp, ctypes.c_int32, _vp], ctypes.c_int),
     "lbm_halo_unpack": ([_vp, ctypes.c_int32, _vp], ctypes.c_int),
     "lbm_plan_halo": ([_vp, ctypes.c_int32, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p], ctypes.c_int),
+    "lbm_set_sparse": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "lbm_plan_sparse": ([_vp, ctypes.c_int32, _i64p, ctypes.c_int64, _i64p], ctypes.c_int),
     "lbm_required_bytes": ([_vp], ctypes.c_size_t),
     "lbm_bind_device_memory": ([_vp, _vp, ctypes.c_size_t], ctypes.c_int),
     "lbm_set_face": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _dp, ctypes.c_double], ctypes.c_int),
@@ -306,7 +309,7 @@ def lbm_get_info(ctx) -> dict:
     _check(ctx, load_library().lbm_get_info(ctx, ctypes.byref(i)))
     return {"cells": i.cells, "fluid_cells": i.fluid_cells, "links": tuple(i.links), "ghost_slots": i.ghost_slots,
             "ghost_runs": i.ghost_runs, "tiles": i.tiles, "bytes_per_pdf": i.bytes_per_pdf,
-            "device_bytes": i.device_bytes, "staged_tiles": i.staged_tiles}
+            "device_bytes": i.device_bytes, "staged_tiles": i.staged_tiles, "list_entries": i.list_entries}
 
 
 def lbm_set_tile(ctx, tx, ty, tz):
@@ -315,6 +318,22 @@ def lbm_set_tile(ctx, tx, ty, tz):
 
 def lbm_set_batching(ctx, batched=True):
     _check(ctx, load_library().lbm_set_batching(ctx, 1 if batched else 0))
+
+
+def lbm_set_sparse(ctx, enable=True):
+    """Fluid-cell list layout of the two-grid sweep (True) or the dense block layout (False)."""
+    _check(ctx, load_library().lbm_set_sparse(ctx, 1 if enable else 0))
+
+
+def lbm_plan_sparse(ctx, what) -> np.ndarray:
+    """Host copy of a part of the fluid-cell list layout (0 table, 1 block, 2 cell, 3 links)."""
+    L = load_library()
+    n = ctypes.c_int64()
+    _check(ctx, L.lbm_plan_sparse(ctx, int(what), None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.int64)
+    if n.value:
+        _check(ctx, L.lbm_plan_sparse(ctx, int(what), _ptr(out, ctypes.c_int64), n.value, ctypes.byref(n)))
+    return out
 
 
 def lbm_set_in_place(ctx, enable=True):

@@ -1,7 +1,7 @@
 """(Long runs sort last among the GPU tests.) The porous-bed configuration's reduced oracle case
 over a long run: the porous-bed generator at 4^3 blocks (64 uneven blocks reading each other in
 place, spheres, velocity inlet and pressure outlet), D3Q19 TRT tau = 0.8, FP64, 1,000 steps from
-rest, both patterns, against the oracle's values stored by tests/golden/make_porous_minibed.py
+rest, both patterns (and the fluid-cell list layout of the two-grid sweep), against the oracle's values stored by tests/golden/make_porous_minibed.py
 (5 min of oracle time): 1,024 sampled fluid PDFs (gate 1e-12 of max |f|) and the FP64 mass and
 momentum of the fluid cells. Written when no GPU time was left: its first run is the next GPU
 test run."""
@@ -52,8 +52,9 @@ def _record():
     return rec, rows
 
 
-@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
-def test_porous_minibed_fp64_1000_steps_matches_oracle_record(pattern):
+@pytest.mark.parametrize("pattern,sparse", [(lbm.TWO_GRID, False), (lbm.AA, False), (lbm.TWO_GRID, True)])
+def test_porous_minibed_fp64_1000_steps_matches_oracle_record(pattern, sparse):
+    """sparse: the fluid-cell list layout (lbm_set_sparse) instead of the dense blocks."""
     gen = _generator()
     rec, rows = _record()
     blocks, shape, flags = gen.geometry()
@@ -66,6 +67,8 @@ def test_porous_minibed_fp64_1000_steps_matches_oracle_record(pattern):
     rho, u = inputs.rest(shape)
     sim = case.make_sim()
     try:
+        if sparse:
+            lbm.lbm_set_sparse(sim.ctx, True)
         init_sim(sim, rho, u)
         sim.step(gen.STEPS)
         got = np.full(len(rows), np.nan)
