@@ -362,10 +362,11 @@ def time_e2e(lbm, variant, steps, world):
     stream = torch.cuda.Stream()
     sim = make_sim(lbm, storage, pattern, stream.cuda_stream, None, collision)
     rho, u = inputs.rest(SHAPE)
-    rho_h = torch.from_numpy(rho).pin_memory().numpy()
-    u_h = torch.from_numpy(u).pin_memory().numpy()
-    rho_o = torch.empty(rho.shape, dtype=torch.float64).pin_memory().numpy()
-    u_o = torch.empty(u.shape, dtype=torch.float64).pin_memory().numpy()
+    # pinned host buffers, kept alive (the NumPy views below do not own them)
+    pinned = [torch.from_numpy(rho).pin_memory(), torch.from_numpy(u).pin_memory(),
+              torch.empty(rho.shape, dtype=torch.float64).pin_memory(),
+              torch.empty(u.shape, dtype=torch.float64).pin_memory()]
+    rho_h, u_h, rho_o, u_o = (t.numpy() for t in pinned)
     sim.init(0, rho_h, u_h)  # allocates and builds lists outside the timed region
     sim.step(2)
     torch.cuda.synchronize()
@@ -384,6 +385,7 @@ def time_e2e(lbm, variant, steps, world):
     barrier(world)
     cells = sim.info()["cells"]
     sim.close()
+    del pinned
     lups, _ = aggregate(cells * steps, dt, world)
     n = rho.size
     return {"value": lups / 1e6, "unit": "MLUPS", "h2d_bytes_per_step": int(4 * n * 8 / steps),

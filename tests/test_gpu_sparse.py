@@ -60,8 +60,13 @@ def test_list_layout_equals_dense_bitwise(storage, q):
     assert info["list_entries"] >= info["fluid_cells"] > 0
     assert info["links"][lbm.VELOCITY] > 0 and info["links"][lbm.PRESSURE] > 0
     assert dl["fluid_cells"] == dd["fluid_cells"] == info["fluid_cells"]
+    # the same stored values: the exact (float-float) mass sums agree to FP64 order; momentum is a
+    # compensated sum in the arithmetic type per thread (a dense thread walks several cells, a
+    # list thread one), within 2 u sum |rho u| <= 2 u mass max|u| of each other, u its roundoff
     assert abs(dl["mass"] / dd["mass"] - 1) < 1e-12
-    assert np.abs(np.array(dl["momentum"]) - np.array(dd["momentum"])).max() < 1e-12 * dd["mass"]
+    u = 2.0 ** (-53 if storage == lbm.FP64 else -24)
+    assert np.abs(np.array(dl["momentum"]) - np.array(dd["momentum"])).max() <= (
+        4 * u * dd["mass"] * dd["max_speed"] + 1e-12 * dd["mass"])
 
 
 @pytest.mark.parametrize("switch_at", [3, 4])
