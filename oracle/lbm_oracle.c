@@ -44,6 +44,8 @@
 #define ORC_VELOCITY 2
 #define ORC_PRESSURE 3
 #define ORC_PERIODIC 4 /* face kind only */
+#define ORC_ZOUHE_VELOCITY 5 /* face kind only: wet-node velocity boundary (Zou & He) */
+#define ORC_ZOUHE_PRESSURE 6 /* face kind only: wet-node pressure boundary (Zou & He) */
 
 #define ORC_SRT 0
 #define ORC_TRT 1
@@ -586,6 +588,7 @@ int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *f
                     const double *cell_rho, double *f, double *work, int64_t nsteps);
 static int stream_pass(const lattice_t *Lp, const orc_params *p, const uint8_t *flags, const double *cell_u,
                        const double *cell_rho, const double *f, double *work);
+static void zouhe_pass(const lattice_t *Lp, const orc_params *p, const uint8_t *flags, double *work);
 
 int orc_run(const orc_params *p, const uint8_t *flags, const double *cell_u, const double *cell_rho, double *f,
             double *work, int64_t nsteps)
@@ -604,11 +607,15 @@ int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *f
     for (int a = 0; a < 6; ++a) {
         if (p->periodic[a / 2]) continue;
         int k = p->face_kind[a];
-        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE) return -2;
+        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE && k != ORC_ZOUHE_VELOCITY &&
+            k != ORC_ZOUHE_PRESSURE)
+            return -2;
+        if ((k == ORC_ZOUHE_VELOCITY || k == ORC_ZOUHE_PRESSURE) && L.q != 19) return -4;
     }
 
     for (int64_t step = 0; step < nsteps; ++step) {
         if (stream_pass(&L, p, flags, cell_u, cell_rho, f, work) != 0) return -3;
+        zouhe_pass(&L, p, flags, work);
 #pragma omp parallel for schedule(static)
         for (int64_t n = 0; n < N; ++n) {
             if (flags[n] != ORC_FLUID) continue;
@@ -631,13 +638,18 @@ int orc_stream(const orc_params *p, const uint8_t *flags, const double *cell_u, 
     for (int a = 0; a < 6; ++a) {
         if (p->periodic[a / 2]) continue;
         int k = p->face_kind[a];
-        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE) return -2;
+        if (k != ORC_NOSLIP && k != ORC_VELOCITY && k != ORC_PRESSURE && k != ORC_ZOUHE_VELOCITY &&
+            k != ORC_ZOUHE_PRESSURE)
+            return -2;
+        if ((k == ORC_ZOUHE_VELOCITY || k == ORC_ZOUHE_PRESSURE) && L.q != 19) return -4;
     }
     const int64_t N = (int64_t)p->nx * p->ny * p->nz;
     for (int i = 0; i < L.q; ++i)
         for (int64_t n = 0; n < N; ++n)
             if (flags[n] != ORC_FLUID) fpre[i * N + n] = 0.0;
-    return stream_pass(&L, p, flags, cell_u, cell_rho, f, fpre) == 0 ? 0 : -3;
+    if (stream_pass(&L, p, flags, cell_u, cell_rho, f, fpre) != 0) return -3;
+    zouhe_pass(&L, p, flags, fpre);
+    return 0;
 }
 
 /* Push every post-collision PDF of f to its target (see above) into work. */
@@ -666,6 +678,9 @@ static int stream_pass(const lattice_t *Lp, const orc_params *p, const uint8_t *
                         int o = L.opp[i];
                         if (kind == ORC_FLUID) {
                             work[i * N + m] = fs[i];
+                        } else if (kind == ORC_ZOUHE_VELOCITY || kind == ORC_ZOUHE_PRESSURE) {
+                            /* leaves the domain through a wet-node face: nothing comes back here;
+                               the node's incoming populations are reconstructed by zouhe_pass */
                         } else if (kind == ORC_NOSLIP) {
                             work[o * N + n] = fs[i];
                         } else if (kind == ORC_VELOCITY) {
@@ -698,6 +713,89 @@ static int stream_pass(const lattice_t *Lp, const orc_params *p, const uint8_t *
         }
     }
     return bad ? -3 : 0;
+}
+
+/* ---------------------------------------------------------------------------------------
+ * Wet-node velocity and pressure faces (Zou & He 1997; the paper cites the family of in- and
+ * outflow conditions in Sec. 5.1.1), D3Q19.  The boundary node is the fluid cell of the first
+ * layer at the face; after streaming, the populations entering it through the face (c_i.n > 0,
+ * n the inward normal) are unknown.  With K0 = sum of the populations with c.n = 0 and Km = sum of
+ * those with c.n < 0 (both known), mass and normal momentum give rho = K0 + 2 Km + j.n, where the
+ * node's momentum is j = rho u - F/2 (the Guo half-force shift of Eq. 1).
+ *   velocity face (u_w given):  rho = (K0 + 2 Km - F.n / 2) / (1 - u_w.n),  j = rho u_w - F/2;
+ *   pressure face (rho_w given): rho = rho_w, tangential velocity zero,
+ *                                j.n = rho_w - K0 - 2 Km,  j.t = -F.t / 2.
+ * The unknowns take the known opposite population plus the equilibrium difference, with the
+ * tangential momentum corrected (Hecht & Harting 2010 for D3Q19):
+ *   c = n:          f_c = f_-c + j.n / 3
+ *   c = n + s t:    f_c = f_-c + (j.n + s j.t) / 6 - s N_t,
+ *                   N_t = (1/2) sum_{c_k.n = 0} (c_k.t) f_k - j.t / 3,
+ * for the two tangential axes t and s = +-1.  Then the node collides as every fluid cell.
+ * Reading: the wall sits at the node; the face's two tangential axes are periodic or the
+ * node's neighbours along them are fluid (edges where two non-periodic faces meet are not
+ * treated).  Populations entering the node from solid cells of the flag field are bounced back
+ * by stream_pass before this pass.
+ * ------------------------------------------------------------------------------------- */
+static void zouhe_pass(const lattice_t *Lp, const orc_params *p, const uint8_t *flags, double *work)
+{
+    const lattice_t L = *Lp;
+    const int n3[3] = {p->nx, p->ny, p->nz};
+    const int64_t N = (int64_t)p->nx * p->ny * p->nz;
+    for (int face = 0; face < 6; ++face) {
+        const int kind = p->face_kind[face];
+        const int a = face / 2, side = face % 2;
+        if (p->periodic[a] || (kind != ORC_ZOUHE_VELOCITY && kind != ORC_ZOUHE_PRESSURE)) continue;
+        const int nrm = side == 0 ? 1 : -1; /* inward normal along axis a */
+        const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+        const int lay = side == 0 ? 0 : n3[a] - 1;
+        const int e1 = n3[t1], e2 = n3[t2];
+#pragma omp parallel for schedule(static)
+        for (int v = 0; v < e2; ++v) {
+            for (int w = 0; w < e1; ++w) {
+                int xyz[3];
+                xyz[a] = lay;
+                xyz[t1] = w;
+                xyz[t2] = v;
+                const int64_t cell = (int64_t)xyz[0] + (int64_t)p->nx * ((int64_t)xyz[1] + (int64_t)p->ny * xyz[2]);
+                if (flags[cell] != ORC_FLUID) continue;
+                double K0 = 0.0, Km = 0.0, T[3] = {0.0, 0.0, 0.0};
+                for (int i = 0; i < L.q; ++i) {
+                    const int cn = L.c[3 * i + a] * nrm;
+                    const double fi = work[i * N + cell];
+                    if (cn == 0) {
+                        K0 += fi;
+                        for (int b = 0; b < 3; ++b) T[b] += L.c[3 * i + b] * fi;
+                    } else if (cn < 0) {
+                        Km += fi;
+                    }
+                }
+                const double *F = p->force;
+                double rho, j[3];
+                if (kind == ORC_ZOUHE_VELOCITY) {
+                    const double *uw = p->face_u[face];
+                    rho = (K0 + 2.0 * Km - 0.5 * F[a] * nrm) / (1.0 - uw[a] * nrm);
+                    for (int b = 0; b < 3; ++b) j[b] = rho * uw[b] - 0.5 * F[b];
+                } else {
+                    rho = p->face_rho[face];
+                    for (int b = 0; b < 3; ++b) j[b] = -0.5 * F[b];
+                    j[a] = (rho - K0 - 2.0 * Km) * nrm;
+                }
+                const double jn = j[a] * nrm;
+                for (int i = 0; i < L.q; ++i) {
+                    if (L.c[3 * i + a] * nrm <= 0) continue;
+                    const int o = L.opp[i];
+                    double fi = work[o * N + cell] + jn / 3.0;
+                    const int tt = L.c[3 * i + t1] != 0 ? t1 : (L.c[3 * i + t2] != 0 ? t2 : -1);
+                    if (tt >= 0) {
+                        const double s = L.c[3 * i + tt];
+                        const double Nt = 0.5 * T[tt] - j[tt] / 3.0;
+                        fi = work[o * N + cell] + (jn + s * j[tt]) / 6.0 - s * Nt;
+                    }
+                    work[i * N + cell] = fi;
+                }
+            }
+        }
+    }
 }
 
 /* Output moments of the stored state (Eq. 1, with the Guo shift for a post-collision

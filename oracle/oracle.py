@@ -13,6 +13,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
+ZOUHE_VELOCITY, ZOUHE_PRESSURE = 5, 6  # face kinds only: wet-node (Zou-He) boundaries, D3Q19
 SRT, TRT, MRT = 0, 1, 2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
