@@ -369,6 +369,7 @@ def time_e2e(lbm, variant, steps, world):
     rho_h, u_h, rho_o, u_o = (t.numpy() for t in pinned)
     sim.init(0, rho_h, u_h)  # allocates and builds lists outside the timed region
     sim.step(2)
+    lbm.lbm_get_macroscopic(sim.ctx, 0, rho_o, u_o)  # first use of the output buffers, untimed
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()

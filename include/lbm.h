@@ -76,6 +76,10 @@ enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16_DEV = 2, LBM_FP16_DEV = 3 };
 enum { LBM_TWO_GRID = 0, LBM_AA = 1 };
 /* Cell kinds of a flag field, and kinds of a domain face. */
 enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_VELOCITY = 2, LBM_PRESSURE = 3, LBM_PERIODIC = 4 };
+/* Face kinds only: wet-node velocity and pressure faces (Zou & He; the node is the fluid cell of
+ * the first layer, the unknown populations entering it are rebuilt from mass and momentum before
+ * each sweep).  D3Q19, two-grid pattern, dense layout; the face's two tangential axes periodic. */
+enum { LBM_ZOUHE_VELOCITY = 5, LBM_ZOUHE_PRESSURE = 6 };
 
 typedef struct {
     int32_t stencil;       /* LBM_D3Q19 or LBM_D3Q27 */

@@ -64,6 +64,7 @@ struct lbm_ctx {
     bool plan_built = false, plan_uploaded = false;
     DevBlock *d_blocks = nullptr;
     uint64_t *d_links = nullptr;
+    uint64_t *d_zouhe = nullptr;  // wet-node entries
     DevRun *d_runs_pull = nullptr, *d_runs_aa = nullptr;
     DevTile *d_tiles = nullptr;
     double *d_params = nullptr;
@@ -194,6 +195,7 @@ cudaError_t sweep_of(const lbm_ctx *c, const SweepArgs &s)
     return launch_closure_sweep(cl);
 }
 cudaError_t do_fill(int q, int st, const FillArgs &s) { LBM_SWITCH(q, st, launch_fill_, s); }
+cudaError_t do_zouhe(int q, int st, const FillArgs &s) { LBM_SWITCH(q, st, launch_zouhe_, s); }
 cudaError_t do_cells(int q, int st, int op, int force, const CellArgs &s) { LBM_SWITCH(q, st, launch_cells_, op, force, s); }
 cudaError_t do_reduce(int q, int st, const ReduceArgs &s) { LBM_SWITCH(q, st, launch_reduce_, s); }
 
@@ -355,6 +357,7 @@ lbm_status ensure_lists(lbm_ctx *c)
     lbm_status s2;
     if ((s2 = upload(c, c->d_blocks, db, "upload blocks")) != LBM_OK) return s2;
     if ((s2 = upload(c, c->d_links, P.links, "upload links")) != LBM_OK) return s2;
+    if ((s2 = upload(c, c->d_zouhe, P.zouhe, "upload wet-node entries")) != LBM_OK) return s2;
     static_assert(sizeof(GhostRun) == sizeof(DevRun), "run layout");
     static_assert(sizeof(Tile) == sizeof(DevTile), "tile layout");
     std::vector<DevRun> rp(P.runs_pull.size()), ra(P.runs_aa.size());
@@ -933,8 +936,13 @@ lbm_status lbm_set_face(lbm_ctx *c, int32_t axis, int32_t side, int32_t kind, co
 {
     if (!c) return LBM_ERR_ARG;
     if (axis < 0 || axis > 2 || side < 0 || side > 1) return fail(c, LBM_ERR_ARG, "bad face");
-    if (kind != LBM_NOSLIP && kind != LBM_VELOCITY && kind != LBM_PRESSURE && kind != LBM_PERIODIC)
+    if (kind != LBM_NOSLIP && kind != LBM_VELOCITY && kind != LBM_PRESSURE && kind != LBM_PERIODIC &&
+        kind != LBM_ZOUHE_VELOCITY && kind != LBM_ZOUHE_PRESSURE)
         return fail(c, LBM_ERR_ARG, "bad face kind %d", kind);
+    if ((kind == LBM_ZOUHE_VELOCITY || kind == LBM_ZOUHE_PRESSURE) &&
+        (c->q != 19 || c->pattern != LBM_TWO_GRID || c->sparse || !c->owner.empty() || c->closure != CLOSURE_NONE))
+        return fail(c, LBM_ERR_UNSUPPORTED, "wet-node (Zou-He) faces are built for D3Q19, the two-grid pattern, the "
+                                            "dense layout of one context and no closure");
     if (kind == LBM_PERIODIC) {
         if (!c->p.periodic[axis]) return fail(c, LBM_ERR_ARG, "axis %d is not periodic in the parameters", axis);
         return LBM_OK;
@@ -1017,6 +1025,12 @@ void step_args(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
         for (int r = 0; r < 27; ++r)
             if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) sw.through = 2;
     }
+    // The wrap path (1) wraps each periodic axis of a source on its own, while the fill's
+    // boundary links and the wet-node pass find a boundary cell the way the neighbour table
+    // does: a source outside a non-periodic face is the block's own ghost cell, unwrapped along
+    // the other axes.  With such boundaries the launch takes the table path, so that the sweep
+    // reads the ghost slots where they were written.
+    if (sw.through == 1 && (!P.links.empty() || !P.zouhe.empty())) sw.through = 2;
     sw.stage_bytes = c->stage_bytes;
     sw.err = c->d_sweep_err;
     sw.cd = c->cd;
@@ -1027,6 +1041,11 @@ void step_args(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
     fa.links = c->d_links;
     fa.nlinks = (int64_t)P.links.size();
     fa.params = c->d_params;
+    fa.zouhe = c->d_zouhe;
+    fa.nzouhe = (int64_t)P.zouhe.size();
+    fa.zouhe_pressure = 0;
+    for (int f = 0; f < 6; ++f)
+        if (c->face_kind[f] == LBM_ZOUHE_PRESSURE) fa.zouhe_pressure |= 1 << f;
     for (int a = 0; a < 3; ++a) fa.F[a] = c->p.force[a];
     for (int i = 0; i < 27; ++i) fa.base[i] = c->base[i];
     fa.stream = c->stream;
@@ -1091,6 +1110,11 @@ lbm_status issue_step(lbm_ctx *c, SweepArgs &sw, FillArgs &fa, bool diag, bool t
         CK(do_fill(c->q, c->storage, fa), "boundary/ghost fill launch");
         c->launches++;
     }
+    if (fa.nzouhe > 0 && c->pattern == LBM_TWO_GRID) {
+        // after the fill: a node may read ghost slots the fill wrote
+        CK(do_zouhe(c->q, c->storage, fa), "wet-node boundary launch");
+        c->launches++;
+    }
     if (trace && (s = mark(c, &e1)) != LBM_OK) return s;
     sw.partials = diag ? c->d_step_partials : nullptr;
     if (sw.ntiles > 0 && c->per_block) {
@@ -1110,7 +1134,7 @@ lbm_status issue_step(lbm_ctx *c, SweepArgs &sw, FillArgs &fa, bool diag, bool t
     }
     if (trace) {
         if ((s = mark(c, &e2)) != LBM_OK) return s;
-        if (fa.nlinks + fa.nruns > 0) c->ev_marks[0].push_back({e0, e1});
+        if (fa.nlinks + fa.nruns + fa.nzouhe > 0) c->ev_marks[0].push_back({e0, e1});
         if (sw.ntiles > 0) c->ev_marks[1].push_back({e1, e2});
     }
     if (c->pattern == LBM_TWO_GRID)
@@ -1232,6 +1256,9 @@ lbm_status lbm_set_closure(lbm_ctx *c, int32_t kind, double cs, const float *mlp
     if (kind == LBM_CLOSURE_MLP && !mlp_params) return fail(c, LBM_ERR_ARG, "null network parameters");
     if (c->q != 19 || c->storage != LBM_FP32 || c->force || c->p.collision == LBM_MRT)
         return fail(c, LBM_ERR_UNSUPPORTED, "closures need D3Q19, FP32 storage, SRT or TRT and no body force");
+    for (int f = 0; f < 6; ++f)
+        if (c->face_kind[f] == LBM_ZOUHE_VELOCITY || c->face_kind[f] == LBM_ZOUHE_PRESSURE)
+            return fail(c, LBM_ERR_UNSUPPORTED, "closures are not combined with wet-node faces");
     if (kind == LBM_CLOSURE_MLP) {
         const MlpDev d = mlp_device_form(mlp_params);
         if (!c->d_mlp) CK(cudaMalloc((void **)&c->d_mlp, sizeof(MlpDev)), "cudaMalloc(network)");
@@ -1640,6 +1667,9 @@ lbm_status lbm_set_sparse(lbm_ctx *c, int32_t enable)
     if (!c) return LBM_ERR_ARG;
     if (enable && c->pattern != LBM_TWO_GRID)
         return fail(c, LBM_ERR_UNSUPPORTED, "the fluid-cell list layout is built for the two-grid pattern");
+    bool zouhe = false;
+    for (int f = 0; f < 6; ++f) zouhe = zouhe || c->face_kind[f] == LBM_ZOUHE_VELOCITY || c->face_kind[f] == LBM_ZOUHE_PRESSURE;
+    if (enable && zouhe) return fail(c, LBM_ERR_UNSUPPORTED, "the fluid-cell list layout has no wet-node faces");
     if (enable && (!c->owner.empty() || c->closure != CLOSURE_NONE || c->p.collision == LBM_MRT))
         return fail(c, LBM_ERR_UNSUPPORTED, "the fluid-cell list layout is for SRT/TRT contexts holding every block, "
                                             "without a closure");
@@ -1820,6 +1850,7 @@ void lbm_destroy(lbm_ctx *c)
     if (c->arena_owned) cudaFree(c->arena_raw);
     dfree(c->d_blocks);
     dfree(c->d_links);
+    dfree(c->d_zouhe);
     dfree(c->d_runs_pull);
     dfree(c->d_runs_aa);
     for (HaloDevRun *&h : c->d_halo) dfree(h);

@@ -157,6 +157,82 @@ __global__ void __launch_bounds__(256) k_fill(StoreT *__restrict__ A, const DevB
 }
 
 // ---------------------------------------------------------------------------------------
+// Wet-node (Zou-He) velocity and pressure faces, two-grid pull layout, D3Q19 (Sec. 5.1.1
+// names the in- and outflow family; Zou & He 1997, Hecht & Harting 2010 for D3Q19).  Run after
+// the fill, before the sweep: for a node x (fluid cell of the first layer at the face, inward
+// normal n) the populations the pull sweep will gather are known for c.n <= 0 (read where the
+// sweep reads them: the neighbour's slot, or the cell's own opposite slot where a no-slip bit
+// bounces); with K0 (c.n = 0) and Km (c.n < 0) their sums and j = rho u - F/2,
+//   velocity face: rho = (K0 + 2 Km - F.n/2) / (1 - u_w.n), j = rho u_w - F/2;
+//   pressure face: rho = rho_w, j.n = rho_w - K0 - 2 Km, j.t = -F.t/2;
+// the unknown c.n > 0 ones are f_c = f_-c + j.n/3 (c = n) and f_-c + (j.n + s j.t)/6 - s N_t
+// (c = n + s t), N_t = (1/2) sum_{c.n = 0} (c.t) f - j.t/3, written into the ghost slot the sweep
+// pulls them from.  One thread per node.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_zouhe(StoreT *__restrict__ A, const DevBlock *__restrict__ blocks,
+                                               const uint64_t *__restrict__ nodes, int64_t nnodes,
+                                               const double *__restrict__ params, int pressure_faces, FillConst k)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnodes || kQ != 19) return;
+    const uint64_t w = nodes[t];
+    const int face = (int)(w & 7u), a = face / 2;
+    const int nrm = (face & 1) ? -1 : 1;  // inward normal along axis a
+    const int blk = (int)((w >> 3) & 0x3fffu);
+    const int64_t cell = (int64_t)(w >> 32);
+    const DevBlock *Bp = blocks + blk;
+    const DevBlock &B = *Bp;
+    int x, y, z;
+    coords_of(cell, B, x, y, z);
+    const uint32_t m = mask_of(B, cell);
+    R f[kQ];
+    R K0 = R(0), Km = R(0), T[3] = {R(0), R(0), R(0)};
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int c3[3] = {Lq::cx(i), Lq::cy(i), Lq::cz(i)};
+        const int cn = c3[a] * nrm;
+        if (cn > 0) continue;
+        const int64_t src = (i > 0 && ((m >> i) & 1u)) ? B.offset + (int64_t)Lq::opp(i) * B.slab + cell
+                                                      : resolve(blocks, Bp, x, y, z, -c3[0], -c3[1], -c3[2], i);
+        f[i] = S::ld_rw(A + src, k.base[i]);
+        if (cn == 0) {
+            K0 += f[i];
+            T[0] += R(c3[0]) * f[i];
+            T[1] += R(c3[1]) * f[i];
+            T[2] += R(c3[2]) * f[i];
+        } else {
+            Km += f[i];
+        }
+    }
+    const double *p = params + 4 * face;
+    R rho, j[3];
+    if ((pressure_faces >> face) & 1) {
+        rho = R(p[3]);
+        for (int b = 0; b < 3; ++b) j[b] = -R(0.5) * k.F[b];
+        j[a] = (rho - K0 - R(2) * Km) * R(nrm);
+    } else {
+        rho = (K0 + R(2) * Km - R(0.5) * k.F[a] * R(nrm)) / (R(1) - R(p[a]) * R(nrm));
+        for (int b = 0; b < 3; ++b) j[b] = rho * R(p[b]) - R(0.5) * k.F[b];
+    }
+    const R jn = j[a] * R(nrm);
+    const int t1 = (a + 1) % 3, t2 = (a + 2) % 3;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+        const int c3[3] = {Lq::cx(i), Lq::cy(i), Lq::cz(i)};
+        if (c3[a] * nrm <= 0) continue;
+        const R fo = f[Lq::opp(i)];
+        R v = fo + jn / R(3);
+        const int tt = c3[t1] != 0 ? t1 : (c3[t2] != 0 ? t2 : -1);
+        if (tt >= 0) {
+            const R s = R(c3[tt]);
+            const R Nt = R(0.5) * T[tt] - j[tt] / R(3);
+            v = fo + (jn + s * j[tt]) / R(6) - s * Nt;
+        }
+        S::st_plain(A + resolve(blocks, Bp, x, y, z, -c3[0], -c3[1], -c3[2], i), v, k.base[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // Per-cell kernels over one block's interior (thread per cell, n = x + nx (y + ny z)).
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ int64_t cell_of(int64_t n, const DevBlock &B, int &x, int &y, int &z)
@@ -432,6 +508,17 @@ cudaError_t LBM_CAT(launch_fill_, LBM_Q, LBM_ST)(const FillArgs &s)
         case FILL_AA_O: return go_fill<FILL_AA_O>(s);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t LBM_CAT(launch_zouhe_, LBM_Q, LBM_ST)(const FillArgs &s)
+{
+    if (s.nzouhe <= 0) return cudaSuccess;
+    if (LBM_Q != 19) return cudaErrorInvalidValue;
+    const int64_t ctas = (s.nzouhe + 255) / 256;
+    if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_zouhe<<<(unsigned)ctas, 256, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.zouhe, s.nzouhe, s.params,
+                                                  s.zouhe_pressure, fill_const(s.F, s.base));
+    return cudaGetLastError();
 }
 
 cudaError_t LBM_CAT(launch_cells_, LBM_Q, LBM_ST)(int op, int force, const CellArgs &s)

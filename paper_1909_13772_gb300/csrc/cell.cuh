@@ -35,11 +35,14 @@ __device__ __forceinline__ T wmax(T v)
 // half-force corrected), kinetic energy, max |u|, non-finite cells, fluid cells.
 //   Mass is the sum of the values the sweep stores (post-collision, after rounding to the
 //   storage format), so it matches an FP64 sum over the stored field.  With FP32 arithmetic
-//   each cell's values are summed without rounding error as a float-float pair (TwoSum, Knuth:
-//   t = s + x, e = (s - (t - b)) + (x - b) with b = t - s gives s + x = t + e exactly, whatever
-//   the magnitudes; the chain starts at rho0 for the deviation storages), the error terms in
-//   FP32, and the cells of a thread are accumulated the same way: a cell contributes at most
-//   Q^2 u^2 rho of error (u = 2^-24), 1.3e-12 relative.
+//   each cell's values are summed without rounding error as a float-float pair: along the
+//   cell's values by Fast2Sum (Dekker 1971: t = s + x, e = x - (t - s) gives s + x = t + e
+//   exactly when the exponent of s is at least that of x -- the chain starts at rho0 for the
+//   deviation storages, whose |x| stay far below it, and at the rest population for full
+//   populations, which is at least every other population: w_0 >= 6 w_i), the error terms in
+//   FP32; the cells of a thread by TwoSum (Knuth: b = t - s, e = (s - (t - b)) + (x - b), exact
+//   whatever the magnitudes -- consecutive cell masses straddle powers of two).  A cell
+//   contributes at most Q^2 u^2 rho of error (u = 2^-24), 1.3e-12 relative.
 //   Momentum and kinetic energy come from the collision's moments and are accumulated per
 //   thread with Kahan's compensated sum (error at most 2u of the sum of magnitudes, whatever
 //   the number of cells).  Warp shuffles and everything after them are FP64.  With FP64
@@ -93,9 +96,10 @@ struct Diag {
             R m = rho0, e = R(0);
 #pragma unroll
             for (int i = 0; i < kQ; ++i) {
-                R ei;
-                m = two_sum(m, S::stored(f[i]), ei);
-                e += ei;
+                const R x = S::stored(f[i]);
+                const R t = m + x;
+                e += x - (t - m);  // Fast2Sum
+                m = t;
             }
             R eh;
             h[0] = two_sum(h[0], m, eh);

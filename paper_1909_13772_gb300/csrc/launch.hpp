@@ -42,8 +42,11 @@ struct FillArgs {
     int64_t nlinks;
     const DevRun *runs;
     int64_t nruns;
-    const double *params;  // wall table: (ux, uy, uz, rho) per entry
+    const double *params;  // wall table: (ux, uy, uz, rho) per entry (the six faces first)
     int mode;              // FillMode
+    const uint64_t *zouhe;  // wet-node entries (plan.hpp pack_zouhe), two-grid only
+    int64_t nzouhe;
+    int zouhe_pressure;     // bit f: face f is a wet-node pressure face (else velocity)
     double F[3];
     double base[27];
     cudaStream_t stream;
@@ -150,6 +153,7 @@ cudaError_t launch_block_final(const double *partials, const int64_t *start, int
 #define LBM_DECLARE(Q, ST)                                                  \
     cudaError_t launch_sweep_##Q##_##ST(const SweepArgs &s);                \
     cudaError_t launch_fill_##Q##_##ST(const FillArgs &s);                  \
+    cudaError_t launch_zouhe_##Q##_##ST(const FillArgs &s);                 \
     cudaError_t launch_cells_##Q##_##ST(int op, int force, const CellArgs &s); \
     cudaError_t launch_reduce_##Q##_##ST(const ReduceArgs &s);
 LBM_DECLARE(19, 0)

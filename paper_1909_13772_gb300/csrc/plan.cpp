@@ -178,6 +178,7 @@ void append_run(std::vector<GhostRun> &runs, int64_t src, int64_t dst, int32_t s
 }
 
 struct BlockOut {
+    std::vector<uint64_t> zouhe;      // wet-node entries of this block
     std::vector<int32_t> snbr;        // sparse layout: (Q - 1) x (fluid cells of the block), local link marks
     std::vector<uint64_t> slinks;     // sparse layout: the block's link slots, local order
     std::vector<HaloElem> send, recv;  // partitioned context: halo elements of this block's shell
@@ -197,6 +198,16 @@ std::string build_plan(const PlanInput &in, Plan &out)
     const auto &flags = *in.flags;
     const int nb = (int)blocks.size();
     const LatticeView L = lattice_view(in.q);
+    // wet-node faces: D3Q19, and the face's tangential axes periodic (no edges between two
+    // non-periodic faces, which the reconstruction does not treat)
+    for (int f = 0; f < 6; ++f) {
+        const int fk = in.face_kind[f], a = f / 2;
+        if (in.periodic[a] || (fk != kFaceZouHeVelocity && fk != kFaceZouHePressure)) continue;
+        if (in.q != 19) return "wet-node (Zou-He) faces are built for D3Q19";
+        if (!in.periodic[(a + 1) % 3] || !in.periodic[(a + 2) % 3])
+            return "a wet-node (Zou-He) face needs its two tangential axes periodic";
+        if (in.sparse || in.owner) return "wet-node (Zou-He) faces need the dense layout of one context";
+    }
 
     // domain bounding box
     int64_t lo[3], hi[3], ext[3];
@@ -421,7 +432,8 @@ std::string build_plan(const PlanInput &in, Plan &out)
                         face = 2 * a + (g[a] < lo[a] ? 0 : 1);
                     }
                     if (face >= 0) {
-                        kind[p] = (uint8_t)in.face_kind[face];
+                        const int fk = in.face_kind[face];
+                        kind[p] = (fk == kFaceZouHeVelocity || fk == kFaceZouHePressure) ? (uint8_t)K_ZOUHE : (uint8_t)fk;
                         param[p] = (uint16_t)face;
                     } else {
                         kind[p] = K_NOSLIP;
@@ -480,6 +492,20 @@ std::string build_plan(const PlanInput &in, Plan &out)
                             o.snbr[(size_t)(i - 1) * nf + n] = v;
                         }
                         ++n;
+                    }
+        }
+        // wet-node (Zou-He) faces: the fluid cells of the block's first layer at such a face
+        for (int fce = 0; fce < 6; ++fce) {
+            const int fk = in.face_kind[fce], a = fce / 2, side = fce % 2;
+            if (in.periodic[a] || (fk != kFaceZouHeVelocity && fk != kFaceZouHePressure)) continue;
+            if (side == 0 ? B.origin[a] != lo[a] : B.origin[a] + B.n[a] != hi[a]) continue;
+            const int layer = side == 0 ? 0 : B.n[a] - 1;
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int x = 0; x < nx; ++x) {
+                        const int xyz[3] = {x, y, z};
+                        if (xyz[a] != layer || kind[pidx(x, y, z)] != K_FLUID) continue;
+                        o.zouhe.push_back(pack_zouhe(fce, b, B.cell(x, y, z)));
                     }
         }
         // links: fluid interior cell x, direction q with a boundary neighbour
@@ -599,6 +625,8 @@ std::string build_plan(const PlanInput &in, Plan &out)
             out.link_count[k] += (int64_t)bo[b].links[k].size();
         }
     for (int b = 0; b < nb; ++b) out.link_count[K_NOSLIP] += bo[b].bounce;
+    out.zouhe.clear();
+    for (int b = 0; b < nb; ++b) out.zouhe.insert(out.zouhe.end(), bo[b].zouhe.begin(), bo[b].zouhe.end());
     // sparse layout: global link slots, the index table direction-major, the cell maps
     out.sparse = SparsePlan{};
     if (in.sparse) {

@@ -23,7 +23,19 @@
 
 namespace lbm {
 
-enum CellKind : uint8_t { K_FLUID = 0, K_NOSLIP = 1, K_VELOCITY = 2, K_PRESSURE = 3, K_PERIODIC = 4, K_MIRROR = 5 };
+enum CellKind : uint8_t {
+    K_FLUID = 0, K_NOSLIP = 1, K_VELOCITY = 2, K_PRESSURE = 3, K_PERIODIC = 4, K_MIRROR = 5,
+    K_ZOUHE = 6  // beyond a wet-node (Zou-He) face: its slots are written before each sweep
+};
+// face kinds of PlanInput.face_kind beyond the cell kinds (the C ABI's values)
+constexpr int kFaceZouHeVelocity = 5, kFaceZouHePressure = 6;
+
+// Wet-node entry: bits 0-2 face (2 axis + side), 3-16 block, 32-63 cell index of the node (a
+// fluid cell of the first layer at the face) in its block's padded layout.
+inline uint64_t pack_zouhe(int face, int block, int64_t cell)
+{
+    return (uint64_t)face | ((uint64_t)block << 3) | ((uint64_t)cell << 32);
+}
 
 struct WallParam {
     double u[3];
@@ -134,6 +146,7 @@ struct SparsePlan {
 
 struct Plan {
     std::vector<uint64_t> links;           // velocity and pressure links, sorted by (kind, block, q, cell)
+    std::vector<uint64_t> zouhe;           // wet-node boundary nodes (pack_zouhe), by block
     int64_t link_count[4] = {0, 0, 0, 0};  // by kind; no-slip ones are the mask bits the sweep applies
     std::vector<WallParam> params;         // wall parameter table (faces first)
     std::vector<GhostRun> runs_pull;       // two-grid: slots j of ghost g with g + c_j fluid interior

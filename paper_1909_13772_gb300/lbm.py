@@ -17,6 +17,7 @@ SRT, TRT, MRT = 0, 1, 2
 FP64, FP32, BF16_DEV, FP16_DEV = 0, 1, 2, 3
 TWO_GRID, AA = 0, 1
 FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
+ZOUHE_VELOCITY, ZOUHE_PRESSURE = 5, 6  # face kinds only: wet-node (Zou-He) faces
 
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_STATE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
           5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_UNSUPPORTED"}
