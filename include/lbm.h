@@ -517,9 +517,7 @@ lbm_status lbm_set_in_place(lbm_ctx *ctx, int32_t enable);
 lbm_status lbm_set_sparse(lbm_ctx *ctx, int32_t enable);
 
 /* Host-only inspection of the fluid-cell list layout: what = 0 the pull table ((Q - 1) x
- * fluid cells, direction-major: entry index, or INT32_MIN for halfway bounce-back), 4 the same
- * table as the sweep reads it in 16 bits (source - n; -32767 bounce-back; -32768: read the
- * 32-bit entry), 1 the
+ * fluid cells, direction-major: entry index, or INT32_MIN for halfway bounce-back), 1 the
  * block of each fluid cell, 2 its padded-layout cell index in that block, 3 the link words
  * (bits 0-4 direction q, 5-6 kind, 10-17 wall parameter, 32-63 fluid cell; link k fills entry
  * fluid cells + k of direction opp(q)), each as int64.  out = NULL: *n only.

@@ -48,7 +48,6 @@ struct lbm_ctx {
     void *sarr[2] = {nullptr, nullptr};
     int64_t s_stride = 0;
     int32_t *d_snbr = nullptr, *d_sblock = nullptr;
-    int16_t *d_srel = nullptr;
     int64_t *d_scell = nullptr;
     uint64_t *d_slinks = nullptr;
 
@@ -392,7 +391,6 @@ lbm_status ensure_lists(lbm_ctx *c)
     if ((s2 = upload(c, c->d_params, par, "upload params")) != LBM_OK) return s2;
     // the list layout: tables, links, cell maps and its two arrays
     dfree(c->d_snbr);
-    dfree(c->d_srel);
     dfree(c->d_sblock);
     dfree(c->d_scell);
     dfree(c->d_slinks);
@@ -402,7 +400,6 @@ lbm_status ensure_lists(lbm_ctx *c)
     if (c->sparse) {
         const SparsePlan &SP = P.sparse;
         if ((s2 = upload(c, c->d_snbr, SP.nbr, "upload list table")) != LBM_OK) return s2;
-        if ((s2 = upload(c, c->d_srel, SP.rel, "upload list table")) != LBM_OK) return s2;
         if ((s2 = upload(c, c->d_sblock, SP.block_of, "upload list cell map")) != LBM_OK) return s2;
         if ((s2 = upload(c, c->d_scell, SP.cell_of, "upload list cell map")) != LBM_OK) return s2;
         if ((s2 = upload(c, c->d_slinks, SP.links, "upload list links")) != LBM_OK) return s2;
@@ -554,7 +551,6 @@ lbm_status sparse_args(lbm_ctx *c, int op, SparseArgs &a)
     a = SparseArgs{};
     a.op = op;
     a.nbr = c->d_snbr;
-    a.rel = c->d_srel;
     a.links = c->d_slinks;
     a.nlinks = (int64_t)c->plan.sparse.links.size();
     a.params = c->d_params;
@@ -1651,19 +1647,18 @@ lbm_status lbm_plan_sparse(lbm_ctx *c, int32_t what, int64_t *out, int64_t cap, 
 {
     if (!c || !n) return LBM_ERR_ARG;
     if (!c->sparse) return fail(c, LBM_ERR_STATE, "the context does not use the fluid-cell list layout");
-    if (what < 0 || what > 4) return fail(c, LBM_ERR_ARG, "bad list part %d", what);
+    if (what < 0 || what > 3) return fail(c, LBM_ERR_ARG, "bad list part %d", what);
     lbm_status s = build_lists(c);
     if (s != LBM_OK) return s;
     const SparsePlan &S = c->plan.sparse;
-    const int64_t len = (what == 0 || what == 4) ? (int64_t)S.nbr.size()
-                                                 : (what == 1 ? S.nfluid : (what == 2 ? S.nfluid : (int64_t)S.links.size()));
+    const int64_t len = what == 0 ? (int64_t)S.nbr.size()
+                                  : (what == 1 ? S.nfluid : (what == 2 ? S.nfluid : (int64_t)S.links.size()));
     *n = len;
     if (!out) return LBM_OK;
     if (cap < len) return fail(c, LBM_ERR_ARG, "buffer too small");
     for (int64_t k = 0; k < len; ++k)
         out[k] = what == 0 ? (int64_t)S.nbr[k]
-                           : (what == 1 ? S.block_of[k]
-                                        : (what == 2 ? S.cell_of[k] : (what == 3 ? (int64_t)S.links[k] : (int64_t)S.rel[k])));
+                           : (what == 1 ? S.block_of[k] : (what == 2 ? S.cell_of[k] : (int64_t)S.links[k]));
     return LBM_OK;
 }
 
@@ -1860,7 +1855,6 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_runs_aa);
     for (HaloDevRun *&h : c->d_halo) dfree(h);
     dfree(c->d_snbr);
-    dfree(c->d_srel);
     dfree(c->d_sblock);
     dfree(c->d_scell);
     dfree(c->d_slinks);

@@ -76,7 +76,6 @@ enum SparseOp { SPARSE_SWEEP = 0, SPARSE_FILL = 1, SPARSE_TO_LIST = 2, SPARSE_TO
 // table entry of a no-slip source: halfway bounce-back from the cell's own opposite slot
 // (the same value as plan.hpp kSparseBounce)
 constexpr int32_t kListBounce = (int32_t)0x80000000u;
-constexpr int16_t kListRelFar = -32768, kListRelBounce = -32767;  // plan.hpp kRelFar, kRelBounce
 struct SparseArgs {
     int op;
     const void *src;  // sweep: source list array
@@ -84,7 +83,6 @@ struct SparseArgs {
     void *dense;      // copies: a dense PDF array
     void *list;       // copies: a list array
     const int32_t *nbr;       // (Q - 1) x nfluid pull sources
-    const int16_t *rel;       // (Q - 1) x nfluid: the same in 16 bits (relative, or bounce / read nbr)
     const uint64_t *links;    // link words (fill)
     int64_t nlinks;
     const double *params;     // wall table (fill)

@@ -639,7 +639,6 @@ std::string build_plan(const PlanInput &in, Plan &out)
         if (S.nslots >= ((int64_t)1 << 30)) return "sparse layout: too many entries (max 2^30)";
         for (int b = 0; b < nb; ++b) S.links.insert(S.links.end(), bo[b].slinks.begin(), bo[b].slinks.end());
         S.nbr.assign((size_t)(L.q - 1) * S.nfluid, 0);
-        S.rel.assign((size_t)(L.q - 1) * S.nfluid, 0);
         S.block_of.assign(S.nfluid, 0);
         S.cell_of.assign(S.nfluid, 0);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -651,11 +650,7 @@ std::string build_plan(const PlanInput &in, Plan &out)
                     int32_t v = bo[b].snbr[(size_t)(i - 1) * nf + n];
                     if (v != kSparseBounce && (v & 0x40000000))
                         v = (int32_t)(S.nfluid + lbase[b] + (v & 0x3fffffff));
-                    const size_t k = (size_t)(i - 1) * S.nfluid + fstart[b] + n;
-                    S.nbr[k] = v;
-                    const int64_t d = (int64_t)v - (fstart[b] + n);
-                    S.rel[k] = v == kSparseBounce ? kRelBounce
-                                                  : ((v < S.nfluid && d > kRelBounce && d <= 32767) ? (int16_t)d : kRelFar);
+                    S.nbr[(size_t)(i - 1) * S.nfluid + fstart[b] + n] = v;
                 }
             int64_t n = fstart[b];
             for (int z = 0; z < B.n[2]; ++z)

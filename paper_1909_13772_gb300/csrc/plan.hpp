@@ -135,13 +135,8 @@ struct PlanInput {
 // face or a periodic image, or a link slot), or kSparseBounce: halfway bounce-back, read slot
 // opp(i) of n itself.
 constexpr int32_t kSparseBounce = (int32_t)0x80000000u;
-// The sweep reads the table in 16 bits: rel = source - n where that fits (neighbours in the same
-// block are within a few planes of fluid cells), kRelBounce for bounce-back, kRelFar where the
-// int32 entry (nbr) must be read (a neighbour block, a link slot).
-constexpr int16_t kRelFar = -32768, kRelBounce = -32767;
 struct SparsePlan {
     int64_t nfluid = 0, nslots = 0;
-    std::vector<int16_t> rel;             // (Q - 1) x nfluid: the table as the sweep reads it
     std::vector<int32_t> nbr;             // (Q - 1) x nfluid
     std::vector<uint64_t> links;          // link k: pack_link(q, kind, param, 0, n); writes slot nfluid + k of opp(q)
     std::vector<int32_t> block_of;        // block of each fluid cell

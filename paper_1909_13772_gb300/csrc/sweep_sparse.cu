@@ -13,10 +13,7 @@
 // this or a neighbour block, or the slot a boundary link filled), or for a no-slip source the
 // halfway bounce-back src[opp i][n]; then the same collision as the dense sweep.  Every cell
 // does the dense sweep's arithmetic, so the two layouts give the same bits.
-// The table is read in 16 bits per entry (the source relative to n, or bounce-back), the
-// int32 entry only where the source is beyond 16 bits (a neighbour block, a link slot).
-// Algorithmic bytes per fluid-cell update: 2 Q s of PDFs plus 2 (Q - 1) of table (plus 4 B
-// per entry that points beyond 16 bits).
+// Algorithmic bytes per fluid-cell update: 2 Q s of PDFs plus 4 (Q - 1) of table.
 #include "cell.cuh"
 
 namespace lbm {
@@ -25,9 +22,8 @@ namespace {
 
 template <bool FORCE, bool DIAG>
 __global__ void __launch_bounds__(256, 4)
-    k_sparse_sweep(const StoreT *__restrict__ src, StoreT *__restrict__ dst, const int16_t *__restrict__ rel,
-                   const int32_t *__restrict__ nbr, int64_t nfluid, int64_t stride, Coll<R> k,
-                   double *__restrict__ partials)
+    k_sparse_sweep(const StoreT *__restrict__ src, StoreT *__restrict__ dst, const int32_t *__restrict__ nbr,
+                   int64_t nfluid, int64_t stride, Coll<R> k, double *__restrict__ partials)
 {
     using L = Lattice<kQ>;
     Diag<DIAG> dg;
@@ -37,17 +33,8 @@ __global__ void __launch_bounds__(256, 4)
         f[0] = S::raw(src + n);
 #pragma unroll
         for (int i = 1; i < kQ; ++i) {
-            const int64_t t = (int64_t)(i - 1) * nfluid + n;
-            const int16_t r = __ldg(rel + t);
-            int64_t e;
-            if (r == kListRelBounce) {
-                e = (int64_t)L::opp(i) * stride + n;
-            } else if (r == kListRelFar) {
-                const int32_t v = __ldg(nbr + t);
-                e = v == kListBounce ? (int64_t)L::opp(i) * stride + n : (int64_t)i * stride + v;
-            } else {
-                e = (int64_t)i * stride + n + r;
-            }
+            const int32_t v = __ldg(nbr + (int64_t)(i - 1) * nfluid + n);
+            const int64_t e = v == kListBounce ? (int64_t)L::opp(i) * stride + n : (int64_t)i * stride + v;
             f[i] = S::raw(src + e);
         }
         R rho, ux, uy, uz;
@@ -128,11 +115,11 @@ cudaError_t sweep(const SparseArgs &s, const Coll<R> &k)
     const int64_t ctas = (s.nfluid + 255) / 256;
     if (ctas > 0x7fffffffLL) return cudaErrorInvalidValue;
     if (s.partials)
-        k_sparse_sweep<FORCE, true><<<(unsigned)ctas, 256, 0, s.stream>>>(
-            (const StoreT *)s.src, (StoreT *)s.dst, s.rel, s.nbr, s.nfluid, s.stride, k, s.partials);
+        k_sparse_sweep<FORCE, true><<<(unsigned)ctas, 256, 0, s.stream>>>((const StoreT *)s.src, (StoreT *)s.dst,
+                                                                         s.nbr, s.nfluid, s.stride, k, s.partials);
     else
-        k_sparse_sweep<FORCE, false><<<(unsigned)ctas, 256, 0, s.stream>>>(
-            (const StoreT *)s.src, (StoreT *)s.dst, s.rel, s.nbr, s.nfluid, s.stride, k, nullptr);
+        k_sparse_sweep<FORCE, false><<<(unsigned)ctas, 256, 0, s.stream>>>((const StoreT *)s.src, (StoreT *)s.dst,
+                                                                          s.nbr, s.nfluid, s.stride, k, nullptr);
     return cudaGetLastError();
 }
 
