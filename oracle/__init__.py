@@ -6,7 +6,8 @@ import this package.  The product library never does, and nothing here imports t
 restatement of the single-cell collision used to cross-check it.
 """
 from .oracle import (  # noqa: F401
-    FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC, ZOUHE_VELOCITY, ZOUHE_PRESSURE, SRT, TRT, MRT, mrt_matrix, mrt_rates,
+    FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC, ZOUHE_VELOCITY, ZOUHE_PRESSURE, SRT, TRT, MRT, CUMULANT, mrt_matrix, mrt_rates,
+    cumulants, cumulants_to_f,
     OracleParams, build_oracle, lattice, omega_minus, equilibrium, collide_cell,
     init, run, stream, macroscopic, diagnostics, set_threads, get_threads,
     NO_CLOSURE, SMAGORINSKY, MLP, collide_closure,

@@ -11,7 +11,9 @@
  *     post-collision PDF to the neighbour it points at.
  *   - Eq. 3 with the special relaxation matrices named right after it: SRT (one rate) and
  *     TRT (one rate for the even part, one for the odd part of each direction pair); and
- *     Eq. 3 itself (MRT) with a stated moment matrix and one rate per group of moments.
+ *     Eq. 3 itself (MRT) with a stated moment matrix and one rate per group of moments;
+ *     and the cumulant collision the same section names (D3Q27: cumulants relaxed towards
+ *     their equilibria, one rate per group).
  *   - Sec. 5.1.1, body-force paragraph: a constant body force drives periodic set-ups; the
  *     force model is Guo et al. (the paper cites it), split into even/odd parts under TRT.
  *   - Sec. 5.1.1, boundary paragraph: no-slip, velocity and pressure boundaries.  The paper
@@ -50,12 +52,13 @@
 #define ORC_SRT 0
 #define ORC_TRT 1
 #define ORC_MRT 2
+#define ORC_CUMULANT 3
 
 #define QMAX 27
 
 typedef struct {
     int32_t q;            /* 19 or 27 */
-    int32_t collision;    /* ORC_SRT or ORC_TRT */
+    int32_t collision;    /* ORC_SRT, ORC_TRT, ORC_MRT or ORC_CUMULANT */
     int32_t nx, ny, nz;   /* global domain size in cells */
     int32_t periodic[3];  /* non-zero: axis is periodic */
     int32_t face_kind[6]; /* kind of the region outside face (axis, side) = index 2*axis+side */
@@ -66,6 +69,8 @@ typedef struct {
     double face_rho[6];   /* wall density of a velocity face / pressure of a pressure face */
     double mrt_s[7];      /* MRT: rates of the row groups 1..7 (momentum, shear, bulk, third,
                              fourth, fifth, sixth order; see the MRT section below) */
+    double cum_s[9];      /* cumulant: rates of the groups 2..10 (group 1, shear, takes omega;
+                             see the cumulant section below) */
 } orc_params;
 
 /* ---------------------------------------------------------------------------------------
@@ -132,11 +137,14 @@ typedef struct {
 
 static int mrt_matrix(lattice_t *L);
 
+static void cumulant_table(void);
+
 static int get_lattice(int q, lattice_t *L)
 {
     L->q = q;
     int r = orc_lattice(q, L->c, L->w, L->opp);
     if (r != 0) return r;
+    if (q == 27) cumulant_table();
     return mrt_matrix(L);
 }
 
@@ -427,8 +435,14 @@ static double closure_omega(const lattice_t *L, const orc_params *p, const orc_c
  *   SRT: f*_i = f_i - w (f_i - feq_i) + (1 - w/2) S_i
  *   TRT: g+- = (g_i +- g_opp(i)) / 2 for g in {f, feq, S};
  *        f*_i = f_i - w+ (f+ - feq+) - w- (f- - feq-) + (1 - w+/2) S+ + (1 - w-/2) S-.     */
+static void collide_cumulant(const lattice_t *L, const orc_params *p, const double *f, double *fout);
+
 static void collide(const lattice_t *L, const orc_params *p, const orc_closure *cl, const double *f, double *fout)
 {
+    if (p->collision == ORC_CUMULANT) {
+        collide_cumulant(L, p, f, fout);
+        return;
+    }
     const double *F = p->force;
     double rho, u[3];
     moments_pre(L, f, F, &rho, u);
@@ -478,10 +492,260 @@ static void collide(const lattice_t *L, const orc_params *p, const orc_closure *
     }
 }
 
+/* ---------------------------------------------------------------------------------------
+ * Cumulant collision (Sec. 5.1.1: cumulants instead of moments are relaxed towards their
+ * equilibria; the paper cites Geier et al. 2015 for the method and fixes none of its
+ * details).  D3Q27 only: its velocities are all of {-1,0,1}^3, so the 27 central moments
+ * kappa_abc with a, b, c in {0, 1, 2} determine the 27 populations.
+ *   rho = sum f,  u = (sum c f + F/2) / rho                          (the Guo half-force shift)
+ *   kappa_abc = sum_i f_i (c_ix - u_x)^a (c_iy - u_y)^b (c_iz - u_z)^c          (definition)
+ *   cumulants of order >= 2, density-scaled: C_abc = rho k_abc with k from mu = kappa / rho
+ *   by the moment-cumulant formula over the set partitions pi of the multiset of a x's,
+ *   b y's and c z's,
+ *       k = sum_pi (-1)^(|pi| - 1) (|pi| - 1)! prod_{B in pi} mu_B ,
+ *   where mu_B is the central moment of the block's variables.  Reading: the first central
+ *   moments are taken as zero in this formula (partitions with a one-element block drop
+ *   out), i.e. the cumulants of a distribution centred on u.  Without a body force that is
+ *   exact (u is the mean); with one, the populations' mean is u - F/(2 rho) and the
+ *   collision moves that first-order part separately: kappa_100 = -F_x/2 before it and
+ *   +F_x/2 after it, so that sum c f* = sum c f + F.
+ *   Relaxation, one rate per group (group 1 = omega, groups 2..10 = cum_s[0..8]); every
+ *   cumulant of order >= 3 has equilibrium 0, the second-order ones rho/3 on the diagonal:
+ *     [1] C_110, C_101, C_011 and C_200 - C_020, C_200 - C_002                 (shear)
+ *     [2] C_200 + C_020 + C_002, towards rho                                   (bulk)
+ *     [3] C_120 + C_102, C_210 + C_012, C_201 + C_021
+ *     [4] C_120 - C_102, C_210 - C_012, C_201 - C_021
+ *     [5] C_111
+ *     [6] C_220 - 2 C_202 + C_022, C_220 + C_202 - 2 C_022
+ *     [7] C_220 + C_202 + C_022
+ *     [8] C_211, C_121, C_112
+ *     [9] C_221, C_212, C_122
+ *    [10] C_222
+ *   each combination g going to g - s (g - g_eq).  Back: mu* from C* / rho by the same
+ *   formula solved for its one-block term, in order of increasing order (every other term
+ *   has blocks of lower order, already known); kappa* = rho mu*; f* from kappa* by
+ *   inverting the map f -> kappa, which is the tensor product of one 3 x 3 map per axis,
+ *   (p_-, p_0, p_+) -> (sum p, sum p d, sum p d^2) with d = c - u_axis, inverted in closed
+ *   form: A = m1 + u m0, B = m2 + 2 u m1 + u^2 m0, p_0 = m0 - B, p_+- = (B +- A) / 2.
+ * ------------------------------------------------------------------------------------- */
+#define CUM_MAXT 64
+
+typedef struct {
+    int nterm[27];             /* terms of cumulant (a, b, c), index a + 3 b + 9 c */
+    double coef[27][CUM_MAXT]; /* (-1)^(m - 1) (m - 1)! for a partition into m blocks */
+    int nblk[27][CUM_MAXT];
+    int blk[27][CUM_MAXT][3];  /* central-moment index of each block */
+} cum_table_t;
+
+static cum_table_t g_cum;
+static int g_cum_ready = 0;
+
+/* all set partitions of the n variables var[0..n-1] (0 = x, 1 = y, 2 = z) by restricted
+ * growth strings: element j joins one of the blocks used so far or opens a new one */
+static void cum_partitions(int k, const int *var, int n, int *blockof, int j, int nb)
+{
+    if (j == n) {
+        int cnt[6][3];
+        memset(cnt, 0, sizeof cnt);
+        for (int e = 0; e < n; ++e) cnt[blockof[e]][var[e]]++;
+        for (int b = 0; b < nb; ++b)
+            if (cnt[b][0] + cnt[b][1] + cnt[b][2] == 1) return; /* a one-element block: mu = 0 */
+        int t = g_cum.nterm[k]++;
+        double fact = 1.0;
+        for (int m = 2; m < nb; ++m) fact *= m;
+        g_cum.coef[k][t] = (nb % 2 == 1 ? 1.0 : -1.0) * fact;
+        g_cum.nblk[k][t] = nb;
+        for (int b = 0; b < nb; ++b) g_cum.blk[k][t][b] = cnt[b][0] + 3 * cnt[b][1] + 9 * cnt[b][2];
+        return;
+    }
+    for (int b = 0; b <= nb && b < 6; ++b) {
+        blockof[j] = b;
+        cum_partitions(k, var, n, blockof, j + 1, b == nb ? nb + 1 : nb);
+    }
+}
+
+static void cumulant_table(void)
+{
+    if (g_cum_ready) return;
+    memset(&g_cum, 0, sizeof g_cum);
+    for (int k = 0; k < 27; ++k) {
+        int a = k % 3, b = (k / 3) % 3, c = k / 9, var[6], n = 0, blockof[6];
+        for (int e = 0; e < a; ++e) var[n++] = 0;
+        for (int e = 0; e < b; ++e) var[n++] = 1;
+        for (int e = 0; e < c; ++e) var[n++] = 2;
+        if (n >= 2) cum_partitions(k, var, n, blockof, 0, 0);
+    }
+    g_cum_ready = 1;
+}
+
+static int cum_order(int k) { return k % 3 + (k / 3) % 3 + k / 9; }
+
+/* rho, u, and the density-scaled cumulants C[27] of f (C[0] = rho, C[first order] = the
+ * central first moments kappa_100, kappa_010, kappa_001) */
+static void cumulants(const lattice_t *L, const double *f, const double F[3], double *rho, double u[3],
+                      double *C)
+{
+    moments_pre(L, f, F, rho, u);
+    double mu[27];
+    for (int k = 0; k < 27; ++k) {
+        int a = k % 3, b = (k / 3) % 3, c = k / 9;
+        double m = 0.0;
+        for (int i = 0; i < 27; ++i) {
+            double dx = L->c[3 * i] - u[0], dy = L->c[3 * i + 1] - u[1], dz = L->c[3 * i + 2] - u[2];
+            double v = f[i];
+            for (int e = 0; e < a; ++e) v *= dx;
+            for (int e = 0; e < b; ++e) v *= dy;
+            for (int e = 0; e < c; ++e) v *= dz;
+            m += v;
+        }
+        mu[k] = m / *rho;
+        C[k] = m; /* orders 0 and 1: kappa itself */
+    }
+    for (int k = 0; k < 27; ++k) {
+        if (cum_order(k) < 2) continue;
+        double kk = 0.0;
+        for (int t = 0; t < g_cum.nterm[k]; ++t) {
+            double v = g_cum.coef[k][t];
+            for (int b = 0; b < g_cum.nblk[k][t]; ++b) v *= mu[g_cum.blk[k][t][b]];
+            kk += v;
+        }
+        C[k] = *rho * kk;
+    }
+}
+
+#define CI(a, b, c) ((a) + 3 * (b) + 9 * (c))
+
+static void cumulant_relax(const orc_params *p, double rho, double *C)
+{
+    const double w1 = p->omega;
+    const double *s = p->cum_s; /* groups 2..10 */
+    /* [1] shear, [2] bulk */
+    double dxy = C[CI(2, 0, 0)] - C[CI(0, 2, 0)], dxz = C[CI(2, 0, 0)] - C[CI(0, 0, 2)];
+    double tr = C[CI(2, 0, 0)] + C[CI(0, 2, 0)] + C[CI(0, 0, 2)];
+    dxy -= w1 * dxy;
+    dxz -= w1 * dxz;
+    tr -= s[0] * (tr - rho);
+    C[CI(2, 0, 0)] = (dxy + dxz + tr) / 3.0;
+    C[CI(0, 2, 0)] = C[CI(2, 0, 0)] - dxy;
+    C[CI(0, 0, 2)] = C[CI(2, 0, 0)] - dxz;
+    C[CI(1, 1, 0)] -= w1 * C[CI(1, 1, 0)];
+    C[CI(1, 0, 1)] -= w1 * C[CI(1, 0, 1)];
+    C[CI(0, 1, 1)] -= w1 * C[CI(0, 1, 1)];
+    /* [3], [4] third order in pairs, [5] C_111 */
+    const int pr[3][2] = {{CI(1, 2, 0), CI(1, 0, 2)}, {CI(2, 1, 0), CI(0, 1, 2)}, {CI(2, 0, 1), CI(0, 2, 1)}};
+    for (int k = 0; k < 3; ++k) {
+        double sm = C[pr[k][0]] + C[pr[k][1]], df = C[pr[k][0]] - C[pr[k][1]];
+        sm -= s[1] * sm;
+        df -= s[2] * df;
+        C[pr[k][0]] = 0.5 * (sm + df);
+        C[pr[k][1]] = 0.5 * (sm - df);
+    }
+    C[CI(1, 1, 1)] -= s[3] * C[CI(1, 1, 1)];
+    /* [6], [7] the diagonal-pair fourth-order cumulants, [8] the mixed ones */
+    {
+        double a = C[CI(2, 2, 0)], b = C[CI(2, 0, 2)], c = C[CI(0, 2, 2)];
+        double d1 = a - 2.0 * b + c, d2 = a + b - 2.0 * c, t = a + b + c;
+        d1 -= s[4] * d1;
+        d2 -= s[4] * d2;
+        t -= s[5] * t;
+        C[CI(2, 2, 0)] = (d1 + d2 + t) / 3.0;
+        C[CI(2, 0, 2)] = (t - d1) / 3.0;
+        C[CI(0, 2, 2)] = (t - d2) / 3.0;
+    }
+    C[CI(2, 1, 1)] -= s[6] * C[CI(2, 1, 1)];
+    C[CI(1, 2, 1)] -= s[6] * C[CI(1, 2, 1)];
+    C[CI(1, 1, 2)] -= s[6] * C[CI(1, 1, 2)];
+    /* [9] fifth, [10] sixth order */
+    C[CI(2, 2, 1)] -= s[7] * C[CI(2, 2, 1)];
+    C[CI(2, 1, 2)] -= s[7] * C[CI(2, 1, 2)];
+    C[CI(1, 2, 2)] -= s[7] * C[CI(1, 2, 2)];
+    C[CI(2, 2, 2)] -= s[8] * C[CI(2, 2, 2)];
+}
+
+/* populations from rho, u and the density-scaled cumulants (orders 0 and 1: kappa itself) */
+static void cumulants_to_f(const lattice_t *L, double rho, const double u[3], const double *C, double *f)
+{
+    double mu[27];
+    int ord[27];
+    for (int k = 0; k < 27; ++k) ord[k] = cum_order(k);
+    for (int k = 0; k < 27; ++k)
+        if (ord[k] < 2) mu[k] = C[k] / rho;
+    for (int o = 2; o <= 6; ++o)
+        for (int k = 0; k < 27; ++k) {
+            if (ord[k] != o) continue;
+            double v = C[k] / rho; /* k_abc; the one-block term is mu_abc itself */
+            for (int t = 0; t < g_cum.nterm[k]; ++t) {
+                if (g_cum.nblk[k][t] == 1) continue;
+                double w = g_cum.coef[k][t];
+                for (int b = 0; b < g_cum.nblk[k][t]; ++b) w *= mu[g_cum.blk[k][t][b]];
+                v -= w;
+            }
+            mu[k] = v;
+        }
+    /* kappa -> f, one axis at a time: g[a][b][c] indexes (x, y, z) slots, each either a
+     * moment order or a velocity component (0, 1, 2 = -1, 0, +1) */
+    double g[27];
+    for (int k = 0; k < 27; ++k) g[k] = rho * mu[k];
+    for (int ax = 0; ax < 3; ++ax) {
+        const int stride = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
+        for (int k = 0; k < 27; ++k) {
+            if ((k / stride) % 3 != 0) continue;
+            double m0 = g[k], m1 = g[k + stride], m2 = g[k + 2 * stride], ua = u[ax];
+            double A = m1 + ua * m0, B = m2 + 2.0 * ua * m1 + ua * ua * m0;
+            g[k] = 0.5 * (B - A);           /* c = -1 */
+            g[k + stride] = m0 - B;         /* c = 0 */
+            g[k + 2 * stride] = 0.5 * (B + A); /* c = +1 */
+        }
+    }
+    for (int i = 0; i < 27; ++i) {
+        int k = (L->c[3 * i] + 1) + 3 * (L->c[3 * i + 1] + 1) + 9 * (L->c[3 * i + 2] + 1);
+        f[i] = g[k];
+    }
+}
+
+static void collide_cumulant(const lattice_t *L, const orc_params *p, const double *f, double *fout)
+{
+    double rho, u[3], C[27];
+    cumulants(L, f, p->force, &rho, u, C);
+    cumulant_relax(p, rho, C);
+    C[CI(1, 0, 0)] = 0.5 * p->force[0];
+    C[CI(0, 1, 0)] = 0.5 * p->force[1];
+    C[CI(0, 0, 1)] = 0.5 * p->force[2];
+    cumulants_to_f(L, rho, u, C, fout);
+}
+
+/* the density-scaled cumulants of one D3Q27 cell (see above; C[0] = rho, first order: the
+ * central first moments) and its rho, u */
+int orc_cumulants(const orc_params *p, const double *f, double *C, double *rho_u)
+{
+    lattice_t L;
+    if (p->q != 27 || get_lattice(27, &L) != 0) return -1;
+    double rho, u[3];
+    cumulants(&L, f, p->force, &rho, u, C);
+    if (rho_u) {
+        rho_u[0] = rho;
+        rho_u[1] = u[0];
+        rho_u[2] = u[1];
+        rho_u[3] = u[2];
+    }
+    return 0;
+}
+
+/* populations of one D3Q27 cell with density rho, velocity u and density-scaled cumulants C
+ * (orders 0 and 1 are the central moments kappa_000 and kappa_100, kappa_010, kappa_001) */
+int orc_cumulants_to_f(double rho, const double *u, const double *C, double *f)
+{
+    lattice_t L;
+    if (get_lattice(27, &L) != 0) return -1;
+    cumulants_to_f(&L, rho, u, C, f);
+    return 0;
+}
+
 void orc_collide(const orc_params *p, const double *f, double *fout)
 {
     lattice_t L;
     if (get_lattice(p->q, &L) != 0) return;
+    if (p->collision == ORC_CUMULANT && L.q != 27) return;
     collide(&L, p, NULL, f, fout);
 }
 
@@ -525,6 +789,7 @@ int orc_init(const orc_params *p, const uint8_t *flags, const double *rho, const
 {
     lattice_t L;
     if (get_lattice(p->q, &L) != 0) return -1;
+    if (p->collision == ORC_CUMULANT && L.q != 27) return -5;
     const int64_t N = (int64_t)p->nx * p->ny * p->nz;
     const int q = L.q;
 #pragma omp parallel for schedule(static)
@@ -602,6 +867,7 @@ int orc_run_closure(const orc_params *p, const orc_closure *cl, const uint8_t *f
 {
     lattice_t L;
     if (get_lattice(p->q, &L) != 0) return -1;
+    if (p->collision == ORC_CUMULANT && (L.q != 27 || (cl && cl->kind != 0))) return -5;
     const int q = L.q;
     const int64_t N = (int64_t)p->nx * p->ny * p->nz;
     for (int a = 0; a < 6; ++a) {

@@ -14,7 +14,7 @@ import numpy as np
 
 FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
 ZOUHE_VELOCITY, ZOUHE_PRESSURE = 5, 6  # face kinds only: wet-node (Zou-He) boundaries, D3Q19
-SRT, TRT, MRT = 0, 1, 2
+SRT, TRT, MRT, CUMULANT = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
@@ -42,7 +42,7 @@ class _CParams(ctypes.Structure):
         ("periodic", ctypes.c_int32 * 3), ("face_kind", ctypes.c_int32 * 6),
         ("omega", ctypes.c_double), ("magic_lambda", ctypes.c_double),
         ("force", ctypes.c_double * 3), ("face_u", (ctypes.c_double * 3) * 6),
-        ("face_rho", ctypes.c_double * 6), ("mrt_s", ctypes.c_double * 7),
+        ("face_rho", ctypes.c_double * 6), ("mrt_s", ctypes.c_double * 7), ("cum_s", ctypes.c_double * 9),
     ]
 
 
@@ -65,6 +65,9 @@ class OracleParams:
     face_rho: tuple = (1.0,) * 6
     # MRT: rates of the moment groups momentum, shear, bulk, third, fourth, fifth, sixth order
     mrt_s: tuple = (1.0,) * 7
+    # cumulant (D3Q27): rates of the groups bulk; third order sums, differences, xyz; fourth
+    # order diagonal-pair differences, their sum, the mixed ones; fifth; sixth (shear = omega)
+    cum_s: tuple = (1.0,) * 9
 
     def cstruct(self) -> _CParams:
         c = _CParams()
@@ -81,6 +84,8 @@ class OracleParams:
         c.omega, c.magic_lambda = float(self.omega), float(self.magic_lambda)
         for g in range(7):
             c.mrt_s[g] = float(self.mrt_s[g])
+        for g in range(9):
+            c.cum_s[g] = float(self.cum_s[g])
         return c
 
 
@@ -134,6 +139,10 @@ def _L():
         lib.orc_stream.restype = ctypes.c_int
         lib.orc_mrt_matrix.argtypes = [ctypes.c_int, dp, dp, ip]
         lib.orc_mrt_matrix.restype = ctypes.c_int
+        lib.orc_cumulants.argtypes = [pp, dp, dp, dp]
+        lib.orc_cumulants.restype = ctypes.c_int
+        lib.orc_cumulants_to_f.argtypes = [ctypes.c_double, dp, dp, dp]
+        lib.orc_cumulants_to_f.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_threads.restype = None
         lib.orc_get_threads.argtypes = []
@@ -187,6 +196,29 @@ def mrt_rates(q: int, omega: float, magic_lambda: float, bulk=None, fourth=None,
     om = omega_minus(omega, magic_lambda)
     pick = lambda v, d: d if v is None else float(v)  # noqa: E731
     return (om, omega, pick(bulk, omega), om, pick(fourth, omega), pick(fifth, om), pick(sixth, omega))
+
+
+def cumulants(p: OracleParams, f):
+    """(C[3,3,3] indexed [c, b, a] for the cumulant of x^a y^b z^c, rho, u) of one D3Q27 cell:
+    density-scaled cumulants of order >= 2 about the force-shifted velocity u; C[0,0,0] = rho,
+    the first-order entries are the central first moments (-F/2)."""
+    fin = np.ascontiguousarray(f, dtype=np.float64)
+    C = np.zeros(27, dtype=np.float64)
+    ru = np.zeros(4, dtype=np.float64)
+    cp = p.cstruct()
+    if _L().orc_cumulants(ctypes.byref(cp), _dp(fin), _dp(C), _dp(ru)) != 0:
+        raise ValueError("orc_cumulants needs q = 27")
+    return C.reshape(3, 3, 3), float(ru[0]), ru[1:].copy()
+
+
+def cumulants_to_f(rho: float, u, C) -> np.ndarray:
+    """Populations of one D3Q27 cell from rho, u and C[3,3,3] (as returned by cumulants)."""
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    Cc = np.ascontiguousarray(C, dtype=np.float64).reshape(27)
+    f = np.zeros(27, dtype=np.float64)
+    if _L().orc_cumulants_to_f(float(rho), _dp(uu), _dp(Cc), _dp(f)) != 0:
+        raise ValueError("orc_cumulants_to_f failed")
+    return f
 
 
 def omega_minus(omega_plus: float, magic_lambda: float) -> float:
