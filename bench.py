@@ -172,7 +172,7 @@ def measured_peaks():
 def sweep_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1909_13772_gb300", "csrc")
-    for name in ("sweep.cu", "cell.cuh", "kernels.cuh", "lattice.cuh", "select.cuh"):
+    for name in ("sweep.cu", "cell.cuh", "cumulant.cuh", "kernels.cuh", "lattice.cuh", "select.cuh"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -212,7 +212,7 @@ def fp64_pipe(variant: str, cells: int, sweep_ms: float):
 def closure_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1909_13772_gb300", "csrc")
-    for name in ("closure.cu", "closure.hpp", "cell.cuh", "kernels.cuh", "lattice.cuh", "select.cuh"):
+    for name in ("closure.cu", "closure.hpp", "cell.cuh", "cumulant.cuh", "kernels.cuh", "lattice.cuh", "select.cuh"):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -751,17 +751,21 @@ def _spectrum(u):
 def measure_turbulence(args):
     """Decaying turbulence, D3Q27 TRT (Lambda = 3/16), tau = 0.52, periodic box, random-phase
     solenoidal k^(-5/3) start (default_rng(1909), shells 1..32, max|u| = 0.05), rho = 1.
-    Throughput: 512^3 for each storage variant.  Error: the same run at 256^3 for the
-    configured steps in every storage variant, compared field by field with the GPU FP64 run."""
+    Throughput: 512^3 for each storage variant, and for the cumulant collision (Sec. 5.1.1,
+    shear rate 1/tau, every other rate 1) in FP32.  Error: the same run at the error-study size
+    for the configured steps in every variant, compared field by field with the GPU FP64 run of
+    the same collision."""
     import torch
     rank, world, local = dist_setup()
     from paper_1909_13772_gb300 import inputs, lbm
     lbm.load_library()
-    variants = [("FP64", "f64"), ("FP32", "f32"), ("FP16_DEV", "f16-dev"), ("BF16_DEV", "bf16-dev")]
+    variants = [("FP64", "f64"), ("FP32", "f32"), ("FP16_DEV", "f16-dev"), ("BF16_DEV", "bf16-dev"),
+                ("FP64", "f64-cumulant"), ("FP32", "f32-cumulant")]
     stream = torch.cuda.Stream()
 
-    def make(n, storage):
-        p = lbm.make_params(stencil=lbm.D3Q27, collision=lbm.TRT, storage=getattr(lbm, storage), pattern=lbm.AA,
+    def make(n, storage, name=""):
+        coll = lbm.CUMULANT if name.endswith("cumulant") else lbm.TRT
+        p = lbm.make_params(stencil=lbm.D3Q27, collision=coll, storage=getattr(lbm, storage), pattern=lbm.AA,
                             omega=1 / 0.52, magic_lambda=LAMBDA, periodic=(1, 1, 1))
         return lbm.Simulation(p, [((0, 0, 0), (n, n, n))], stream=stream.cuda_stream)
 
@@ -784,7 +788,7 @@ def measure_turbulence(args):
     for storage, name in variants:
         if storage == "FP64" and not args.turb_fp64_perf:
             continue
-        sim = make(n_perf, storage)
+        sim = make(n_perf, storage, name)
         sim.init(0, rho, u)
         sim.step(args.warmup)
         torch.cuda.synchronize()
@@ -806,7 +810,7 @@ def measure_turbulence(args):
     rho, u = inputs.turbulence(n, seed=1909, kmax=32, umax=0.05)
     fields = {}
     for storage, name in variants:
-        sim = make(n, storage)
+        sim = make(n, storage, name)
         sim.init(0, rho, u)
         d0 = sim.reduce()
         sim.step(args.steps)
@@ -814,10 +818,12 @@ def measure_turbulence(args):
         d1 = sim.reduce()
         sim.close()
         fields[name] = (r, v, d0, d1)
-    r64, v64, d064, d164 = fields["f64"]
-    e64 = _spectrum(v64)
+    spectra = {k: _spectrum(fields[k][1]) for k in ("f64", "f64-cumulant")}
     err = {}
     for name, (r, v, d0, d1) in fields.items():
+        ref = "f64-cumulant" if name.endswith("cumulant") else "f64"
+        r64, v64, d064, d164 = fields[ref]
+        e64 = spectra[ref]
         e = _spectrum(v)
         err[name] = {
             "rho": float(np.abs(r - r64).max() / np.abs(r64 - 1.0).max()),
@@ -831,18 +837,24 @@ def measure_turbulence(args):
            "value": perf.get("f32", {}).get("mlups"), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "higher_is_better": True, "data": "synthetic (seeded random-phase field)",
            "config": {"workload": "D3Q27 TRT tau=0.52 periodic decaying turbulence, k^-5/3 random-phase start, "
-                                  "max|u| = 0.05, AA pattern", "throughput_size": n_perf,
+                                  "max|u| = 0.05, AA pattern (and the cumulant collision, shear 1/tau, other "
+                                  "rates 1)", "throughput_size": n_perf,
                       "throughput_steps": perf_steps, "error_size": n, "error_steps": args.steps,
                       "generator_s": round(t_gen, 1),
                       "throughput_field": ("the %d^3 member repeated 2x2x2" % (n_perf // 2)) if tiled else
                       "the %d^3 member" % n_perf,
-                      "error_reference": "the GPU FP64 run of the same start (its kernels match the oracle to "
-                                         "1e-12 on the 64^3 member over 2,000 steps)"},
+                      "error_reference": "the GPU FP64 run of the same start and collision (its kernels match "
+                                         "the oracle to 1e-12: TRT on the 64^3 member over 2,000 steps, the "
+                                         "cumulant collision on the 32^3 member over 300)"},
            "roofline": ({"bound": "hbm", "achieved": perf["f32"]["gbs"], "peak": peak, "unit": "GB/s",
                          "frac": perf["f32"]["frac_hbm"], "traffic": None,
                          "kernel": "k_sweep D3Q27 FP32 AA (one launch per step)",
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind} if "f32" in perf else None),
            "clocks": clocks, "throughput": perf, "error_vs_fp64": err,
+           "cumulant_vs_trt_fp64": {"u": float(np.abs(fields["f64-cumulant"][1] - fields["f64"][1]).max()
+                                               / np.abs(fields["f64"][1]).max()),
+                                    "spectrum_l2": float(np.sqrt(((spectra["f64-cumulant"] - spectra["f64"]) ** 2).sum()
+                                                                 / (spectra["f64"] ** 2).sum()))},
            "cpu_baseline": (cpu_baseline_turbulence(min_seconds=getattr(args, "cpu_seconds", 10.0))
                             if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None)}
     return out

@@ -66,8 +66,15 @@ enum { LBM_D3Q19 = 19, LBM_D3Q27 = 27 };
  * momentum and the third-order moments with omega- (from magic_lambda, as TRT), the bulk,
  * fourth-, fifth- and sixth-order groups with mrt_rates.  The moment space: polynomials of c
  * grouped by degree, each group orthogonal to all lower groups under sum_i w_i a(c_i) b(c_i).
- * MRT is available with FP64 and FP32 storage. */
-enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2 };
+ * MRT is available with FP64 and FP32 storage.
+ * Cumulant (Sec. 5.1.1: cumulants instead of moments relaxed towards their equilibria; Geier et
+ * al. 2015), D3Q27 with FP64 or FP32 storage: the density-scaled cumulants of the central
+ * moments about the half-force-shifted velocity, relaxed in ten groups -- shear (omega) and
+ * cumulant_rates[0..8] for the bulk, third-order sums, third-order differences, C_111,
+ * fourth-order differences, fourth-order sum, mixed fourth order, fifth and sixth order; all
+ * equilibria zero beyond the second order (rho/3 on its diagonal); the body force through the
+ * first central moments (-F/2 before, +F/2 after). */
+enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2, LBM_CUMULANT = 3 };
 /* PDF storage: FP64 and FP32 store f_i; the *_DEV forms store f_i - w_i rho0 in 16 bits and
  * collide in FP32. */
 enum { LBM_FP64 = 0, LBM_FP32 = 1, LBM_BF16_DEV = 2, LBM_FP16_DEV = 3 };
@@ -83,10 +90,11 @@ enum { LBM_ZOUHE_VELOCITY = 5, LBM_ZOUHE_PRESSURE = 6 };
 
 typedef struct {
     int32_t stencil;       /* LBM_D3Q19 or LBM_D3Q27 */
-    int32_t collision;     /* LBM_SRT, LBM_TRT or LBM_MRT */
+    int32_t collision;     /* LBM_SRT, LBM_TRT, LBM_MRT or LBM_CUMULANT */
     int32_t storage;       /* LBM_FP64 ... */
     int32_t pattern;       /* LBM_TWO_GRID or LBM_AA */
-    double omega;          /* SRT: omega = 1/tau; TRT: omega+ (sets the viscosity); MRT: shear rate */
+    double omega;          /* SRT: omega = 1/tau; TRT: omega+ (sets the viscosity); MRT, cumulant:
+                              shear rate */
     double magic_lambda;   /* TRT, MRT: Lambda = (1/omega+ - 1/2)(1/omega- - 1/2); 3/16 typical */
     double force[3];       /* constant body force per cell (lattice units), Guo scheme */
     double rho0;           /* reference density (1.0); base of the *_DEV storages */
@@ -95,6 +103,8 @@ typedef struct {
     double mrt_rates[4];   /* MRT: rates of the bulk, fourth-, fifth- and sixth-order groups, each
                               in [0, 2) (fifth and sixth: D3Q27 only); ignored otherwise.  TRT is
                               omega, omega, omega-, omega */
+    double cumulant_rates[9]; /* cumulant: rates of the groups after shear (see LBM_CUMULANT),
+                                 each in [0, 2); ignored otherwise */
 } lbm_params;
 
 /* One block: global cell coordinates of its first interior cell and its interior size.

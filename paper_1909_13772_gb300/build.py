@@ -3,8 +3,8 @@
 Translation units: api.cu (C ABI, scheduler), plan.cpp (host list builder, OpenMP), diag.cu,
 reduce_static.cu, closure.cu (closure sweep and network kernels, D3Q19 FP32), halo.cu (halo
 pack/unpack of partitioned runs), sweep.cu / aux.cu / sweep_sparse.cu (the fluid-cell list
-sweep) compiled once per (stencil, storage) variant, and sweep.cu once more per (stencil, FP64/FP32) with the MRT collision.  Objects are compiled in
-parallel; the library lands in ``paper_1909_13772_gb300/_build/liblbm.so``.
+sweep) compiled once per (stencil, storage) variant, sweep.cu once more per (stencil, FP64/FP32) with the MRT
+collision and per FP64/FP32 D3Q27 with the cumulant collision.  Objects are compiled in parallel; the library lands in ``paper_1909_13772_gb300/_build/liblbm.so``.
 """
 from __future__ import annotations
 
@@ -26,6 +26,7 @@ NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fopenmp", "-I
            "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
 VARIANTS = [(q, st) for q in (19, 27) for st in (0, 1, 2, 3)]
 MRT_VARIANTS = [(q, st) for q in (19, 27) for st in (0, 1)]  # MRT sweeps: FP64 and FP32 storage
+CUM_VARIANTS = [(27, 0), (27, 1)]  # cumulant sweeps: D3Q27, FP64 and FP32 storage
 
 
 def _nvcc() -> str:
@@ -56,6 +57,11 @@ def _jobs(nvcc, extra, build_dir):
         obj = os.path.join(build_dir, "sweep_mrt_%d_%d.o" % (q, st))
         jobs.append([nvcc] + ARCH + NVFLAGS + extra + ["-DLBM_Q=%d" % q, "-DLBM_ST=%d" % st, "-DLBM_MRT_SWEEP=1", "-c", src,
                                                      "-o", obj])
+    for q, st in CUM_VARIANTS:
+        src = os.path.join(CSRC, "sweep.cu")
+        obj = os.path.join(build_dir, "sweep_cum_%d_%d.o" % (q, st))
+        jobs.append([nvcc] + ARCH + NVFLAGS + extra + ["-DLBM_Q=%d" % q, "-DLBM_ST=%d" % st, "-DLBM_CUMULANT_SWEEP=1",
+                                                     "-c", src, "-o", obj])
     return jobs
 
 

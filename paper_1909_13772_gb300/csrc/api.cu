@@ -178,11 +178,19 @@ cudaError_t do_sweep_mrt(int q, int st, const SweepArgs &s)
     return st == 0 ? launch_sweep_mrt_27_0(s) : launch_sweep_mrt_27_1(s);
 }
 
+// Cumulant sweeps: D3Q27 with FP64 or FP32 storage (lbm_create_blocks refuses the others)
+cudaError_t do_sweep_cum(int st, const SweepArgs &s)
+{
+    return st == 0 ? launch_sweep_cum_27_0(s) : launch_sweep_cum_27_1(s);
+}
+
 // The step's sweep: the plain sweep, or the closure sweep when a closure is set.
 cudaError_t sweep_of(const lbm_ctx *c, const SweepArgs &s)
 {
-    if (c->closure == CLOSURE_NONE)
+    if (c->closure == CLOSURE_NONE) {
+        if (c->p.collision == LBM_CUMULANT) return do_sweep_cum(c->storage, s);
         return c->p.collision == LBM_MRT ? do_sweep_mrt(c->q, c->storage, s) : do_sweep(c->q, c->storage, s);
+    }
     ClosureLaunch cl;
     cl.sw = s;
     cl.closure = c->closure;
@@ -795,11 +803,18 @@ lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, in
     if (!params || !blocks || nblocks <= 0) return LBM_ERR_ARG;
     const lbm_params &p = *params;
     if (p.stencil != LBM_D3Q19 && p.stencil != LBM_D3Q27) return LBM_ERR_ARG;
-    if (p.collision != LBM_SRT && p.collision != LBM_TRT && p.collision != LBM_MRT) return LBM_ERR_ARG;
+    if (p.collision != LBM_SRT && p.collision != LBM_TRT && p.collision != LBM_MRT && p.collision != LBM_CUMULANT)
+        return LBM_ERR_ARG;
     if (p.storage < LBM_FP64 || p.storage > LBM_FP16_DEV) return LBM_ERR_ARG;
     if (p.pattern != LBM_TWO_GRID && p.pattern != LBM_AA) return LBM_ERR_ARG;
     if (!(p.omega >= 0.0 && p.omega < 2.0)) return LBM_ERR_ARG;
-    if (p.collision != LBM_SRT && !(p.magic_lambda > 0.0) && p.omega > 0.0) return LBM_ERR_ARG;
+    if ((p.collision == LBM_TRT || p.collision == LBM_MRT) && !(p.magic_lambda > 0.0) && p.omega > 0.0)
+        return LBM_ERR_ARG;
+    if (p.collision == LBM_CUMULANT) {
+        for (int g = 0; g < 9; ++g)
+            if (!(p.cumulant_rates[g] >= 0.0 && p.cumulant_rates[g] < 2.0)) return LBM_ERR_ARG;
+        if (p.stencil != LBM_D3Q27 || (p.storage != LBM_FP64 && p.storage != LBM_FP32)) return LBM_ERR_UNSUPPORTED;
+    }
     if (p.collision == LBM_MRT) {
         for (int g = 0; g < 4; ++g)
             if (!(p.mrt_rates[g] >= 0.0 && p.mrt_rates[g] < 2.0)) return LBM_ERR_ARG;
@@ -849,7 +864,7 @@ lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, in
     double wm = wp;
     // TRT: Lambda = (1/w+ - 1/2)(1/w- - 1/2); at w+ = 0 (no relaxation of the even part) the
     // IEEE evaluation gives the limit w- = 2.
-    if (p.collision != LBM_SRT) wm = 1.0 / (p.magic_lambda / (1.0 / wp - 0.5) + 0.5);
+    if (p.collision == LBM_TRT || p.collision == LBM_MRT) wm = 1.0 / (p.magic_lambda / (1.0 / wp - 0.5) + 0.5);
     const LatticeView L = lattice_view(c->q);
     const bool dev = c->storage >= LBM_BF16_DEV;
     for (int i = 0; i < 27; ++i) c->base[i] = (dev && i < L.q) ? L.w[i] * p.rho0 : 0.0;
@@ -877,6 +892,11 @@ lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, in
         d.mrt_d[2] = c->q == 27 ? p.mrt_rates[2] - wm : 0.0;
         d.mrt_d[3] = c->q == 27 ? p.mrt_rates[3] - wp : 0.0;
     }
+    if (p.collision == LBM_CUMULANT) {
+        d.cum[0] = wp;
+        for (int g = 0; g < 9; ++g) d.cum[g + 1] = p.cumulant_rates[g];
+        d.cumulant = 1;
+    }
     d.rho0 = dev ? p.rho0 : 0.0;
     for (int i = 0; i < 27; ++i) d.base[i] = c->base[i];
     // FP32 copy of every constant
@@ -903,6 +923,8 @@ lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, in
     }
     for (int a = 0; a < 3; ++a) f.F[a] = (float)d.F[a];
     for (int g = 0; g < 4; ++g) f.mrt_d[g] = (float)d.mrt_d[g];
+    for (int g = 0; g < 10; ++g) f.cum[g] = (float)d.cum[g];
+    f.cumulant = d.cumulant;
     f.rho0 = (float)d.rho0;
     *out = c;
     return LBM_OK;
@@ -1670,7 +1692,7 @@ lbm_status lbm_set_sparse(lbm_ctx *c, int32_t enable)
     bool zouhe = false;
     for (int f = 0; f < 6; ++f) zouhe = zouhe || c->face_kind[f] == LBM_ZOUHE_VELOCITY || c->face_kind[f] == LBM_ZOUHE_PRESSURE;
     if (enable && zouhe) return fail(c, LBM_ERR_UNSUPPORTED, "the fluid-cell list layout has no wet-node faces");
-    if (enable && (!c->owner.empty() || c->closure != CLOSURE_NONE || c->p.collision == LBM_MRT))
+    if (enable && (!c->owner.empty() || c->closure != CLOSURE_NONE || c->p.collision >= LBM_MRT))
         return fail(c, LBM_ERR_UNSUPPORTED, "the fluid-cell list layout is for SRT/TRT contexts holding every block, "
                                             "without a closure");
     if ((enable != 0) == c->sparse) return LBM_OK;

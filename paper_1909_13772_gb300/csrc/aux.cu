@@ -5,6 +5,7 @@
 //   LAYOUT_PULL (two-grid source array):  a[i][x]
 //   LAYOUT_AA_E (after an AA local sweep): a[opp i][x]
 //   LAYOUT_AA_O (after an AA neighbour sweep): a[i][x + c_i]
+#include "cumulant.cuh"
 #include "select.cuh"
 
 namespace lbm {
@@ -244,6 +245,21 @@ __device__ __forceinline__ int64_t cell_of(int64_t n, const DevBlock &B, int &x,
     return (int64_t)(z + 1) * B.plane + (int64_t)(y + 1) * B.pitch + B.xo + x;
 }
 
+// The context's collision of full populations: the cumulant one for D3Q27 contexts that use
+// it, else SRT/TRT/MRT (the MRT terms vanish unless the context is MRT).
+template <bool FORCE, int Q>
+__device__ __forceinline__ void init_collide(R (&f)[Q], const Coll<R> &k)
+{
+    if constexpr (Q == 27) {
+        if (k.cumulant) {
+            R rho, ux, uy, uz;
+            collide_cumulant<FORCE, true>(f, k, rho, ux, uy, uz);
+            return;
+        }
+    }
+    collide<Q, FORCE, R, true>(f, k);
+}
+
 // Initial state: populations = equilibrium at (rho, u - F/(2 rho)), then one collision
 // (the stored state is post-collision).  Equilibrium: w rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u).
 template <bool FORCE>
@@ -275,7 +291,7 @@ __global__ void k_init(StoreT *__restrict__ A, const DevBlock *__restrict__ bloc
         const R cu = R(Lq::cx(i)) * ux + R(Lq::cy(i)) * uy + R(Lq::cz(i)) * uz;
         f[i] = R(Lq::w(i)) * rho * (R(1) + R(3) * cu + R(4.5) * cu * cu - R(1.5) * usq);
     }
-    collide<kQ, FORCE, R, true>(f, k);  // MRT terms vanish unless the context is MRT
+    init_collide<FORCE>(f, k);
 #pragma unroll
     for (int i = 0; i < kQ; ++i) S::st_plain(A + slot(layout, i, cell, blocks, Bp, x, y, z, m), f[i], k.base[i]);
 }

@@ -4,6 +4,7 @@
 // select.cuh by translation units compiled for one (stencil, storage) pair.
 #pragma once
 
+#include "cumulant.cuh"
 #include "select.cuh"
 
 namespace lbm {
@@ -17,6 +18,19 @@ using R = typename S::R;
 constexpr bool kAccurate = LBM_ST == 1;
 // MRT collision (group corrections on top of TRT) in this object's sweeps
 constexpr bool kMrt = LBM_MRT_SWEEP != 0;
+// cumulant collision in this object's sweeps (D3Q27, FP64 and FP32 storage)
+constexpr bool kCum = LBM_CUMULANT_SWEEP != 0;
+static_assert(!kCum || (kQ == 27 && LBM_ST <= 1), "cumulant sweeps are D3Q27 with FP64 or FP32 storage");
+
+// The collision of this object's sweeps on the gathered values of one cell.
+template <bool FORCE, bool RCP, int Q>
+__device__ __forceinline__ void collide_cell(R (&f)[Q], const Coll<R> &k, R &rho, R &ux, R &uy, R &uz)
+{
+    if constexpr (kCum && Q == 27)
+        collide_cumulant<FORCE, true>(f, k, rho, ux, uy, uz);
+    else
+        collide<Q, FORCE, R, kAccurate, kMrt, RCP>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+}
 
 template <class T>
 __device__ __forceinline__ T wsum(T v)
@@ -308,7 +322,7 @@ __device__ __forceinline__ void update_cell(StoreT *__restrict__ A, StoreT *__re
     gather_cell<KIND, FACE, MASK>(f, A, B, nb, fc, x, y, z, cell, m, k.base);
     R rho, ux, uy, uz;
     constexpr bool kRcp = !(KIND == SWEEP_AA_NBR && sizeof(R) == 4);
-    collide<kQ, FORCE, R, kAccurate, kMrt, kRcp>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+    collide_cell<FORCE, kRcp>(f, k, rho, ux, uy, uz);
     dg.add(f, k.rho0, rho, ux, uy, uz);
     scatter_cell<KIND, FACE, MASK>(f, A, Bout, B, nb, fc, x, y, z, cell, m, k.base);
 }

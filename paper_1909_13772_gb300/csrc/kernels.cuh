@@ -86,6 +86,9 @@ struct Coll {
     R rho0;                // deviation base density of the storage (rho0 for *_DEV, else 0)
     R base[27];            // storage offset per direction (w_i rho0 for *_DEV storages, else 0)
     R mrt_d[4];            // MRT: rate minus the TRT rate of the bulk, fourth-, fifth-, sixth-order groups
+    R cum[10];             // cumulant (D3Q27): rates of the shear, bulk, third-order sum, difference, xyz,
+                           // fourth-order difference, sum, mixed, fifth- and sixth-order groups
+    int cumulant;          // non-zero: the context's collision is the cumulant one (init kernel)
 };
 
 // Pair-form rates for omega+ / omega- (host or device).

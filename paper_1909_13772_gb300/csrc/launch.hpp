@@ -180,5 +180,8 @@ cudaError_t launch_sweep_mrt_19_0(const SweepArgs &s);
 cudaError_t launch_sweep_mrt_19_1(const SweepArgs &s);
 cudaError_t launch_sweep_mrt_27_0(const SweepArgs &s);
 cudaError_t launch_sweep_mrt_27_1(const SweepArgs &s);
+// cumulant sweeps (D3Q27, FP64 and FP32 storage)
+cudaError_t launch_sweep_cum_27_0(const SweepArgs &s);
+cudaError_t launch_sweep_cum_27_1(const SweepArgs &s);
 
 }  // namespace lbm

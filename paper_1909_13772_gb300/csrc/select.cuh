@@ -14,6 +14,11 @@
 #ifndef LBM_MRT_SWEEP
 #define LBM_MRT_SWEEP 0
 #endif
+// -DLBM_CUMULANT_SWEEP=1: the sweep object of the cumulant collision (D3Q27,
+// launch_sweep_cum_27_<ST>)
+#ifndef LBM_CUMULANT_SWEEP
+#define LBM_CUMULANT_SWEEP 0
+#endif
 
 namespace lbm {
 #if LBM_ST == 0

@@ -2,7 +2,9 @@
 //
 // Compiled once per (stencil, storage) pair: -DLBM_Q=19|27 -DLBM_ST=0..3 (fp64, fp32,
 // bf16-deviation, fp16-deviation).  Each object defines launch_sweep_<Q>_<ST>; with -DLBM_MRT_SWEEP=1
-// (FP64 and FP32 storage) the same sweeps with the MRT collision, launch_sweep_mrt_<Q>_<ST>.
+// (FP64 and FP32 storage) the same sweeps with the MRT collision, launch_sweep_mrt_<Q>_<ST>;
+// with -DLBM_CUMULANT_SWEEP=1 (D3Q27, FP64 and FP32 storage) with the cumulant collision,
+// launch_sweep_cum_27_<ST>.
 //
 // Method: Eq. 2 of the paper with the stream and collision steps fused into one pass over
 // the cells (Sec. 5.1.2), pull form: each cell gathers the PDFs streaming into it, collides
@@ -139,7 +141,7 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
                 f[i] = S::raw_rw(row0 + (size_t)i * rows * RW + e);
             }
             R rho, ux, uy, uz;
-            collide<kQ, FORCE, R, kAccurate, kMrt>(f, k, k.r, k.rho0, rho, ux, uy, uz);
+            collide_cell<FORCE, true>(f, k, rho, ux, uy, uz);
             dg.add(f, k.rho0, rho, ux, uy, uz);
             const int64_t cell = B.cell(x, y, z);
 #pragma unroll
@@ -285,6 +287,8 @@ cudaError_t go_kind(const SweepArgs &s, const Coll<R> &k)
 
 #if LBM_MRT_SWEEP
 cudaError_t LBM_CAT(launch_sweep_mrt_, LBM_Q, LBM_ST)(const SweepArgs &s)
+#elif LBM_CUMULANT_SWEEP
+cudaError_t LBM_CAT(launch_sweep_cum_, LBM_Q, LBM_ST)(const SweepArgs &s)
 #else
 cudaError_t LBM_CAT(launch_sweep_, LBM_Q, LBM_ST)(const SweepArgs &s)
 #endif

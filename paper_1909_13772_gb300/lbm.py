@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 D3Q19, D3Q27 = 19, 27
-SRT, TRT, MRT = 0, 1, 2
+SRT, TRT, MRT, CUMULANT = 0, 1, 2, 3
 FP64, FP32, BF16_DEV, FP16_DEV = 0, 1, 2, 3
 TWO_GRID, AA = 0, 1
 FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
@@ -33,7 +33,8 @@ class lbm_params(ctypes.Structure):
     _fields_ = [("stencil", ctypes.c_int32), ("collision", ctypes.c_int32), ("storage", ctypes.c_int32),
                 ("pattern", ctypes.c_int32), ("omega", ctypes.c_double), ("magic_lambda", ctypes.c_double),
                 ("force", ctypes.c_double * 3), ("rho0", ctypes.c_double), ("periodic", ctypes.c_int32 * 3),
-                ("diag_interval", ctypes.c_int32), ("mrt_rates", ctypes.c_double * 4)]
+                ("diag_interval", ctypes.c_int32), ("mrt_rates", ctypes.c_double * 4),
+                ("cumulant_rates", ctypes.c_double * 9)]
 
 
 class lbm_block_desc(ctypes.Structure):
@@ -547,9 +548,12 @@ def lbm_destroy(ctx):
 # ---- convenience wrapper ----------------------------------------------------------------
 
 def make_params(stencil=D3Q19, collision=TRT, storage=FP32, pattern=TWO_GRID, omega=1.0, magic_lambda=3.0 / 16.0,
-                force=(0.0, 0.0, 0.0), rho0=1.0, periodic=(1, 1, 1), diag_interval=0, mrt_rates=None) -> lbm_params:
+                force=(0.0, 0.0, 0.0), rho0=1.0, periodic=(1, 1, 1), diag_interval=0, mrt_rates=None,
+                cumulant_rates=None) -> lbm_params:
     """lbm_params; ``mrt_rates`` (MRT only): rates of the bulk, fourth-, fifth- and sixth-order
-    groups, default the TRT rates of their parity (omega, omega, omega-, omega)."""
+    groups, default the TRT rates of their parity (omega, omega, omega-, omega);
+    ``cumulant_rates`` (cumulant only): the nine rates after shear (bulk, third-order sums,
+    differences, xyz, fourth-order differences, sum, mixed, fifth, sixth), default all 1."""
     p = lbm_params()
     p.stencil, p.collision, p.storage, p.pattern = stencil, collision, storage, pattern
     p.omega, p.magic_lambda, p.rho0 = float(omega), float(magic_lambda), float(rho0)
@@ -562,6 +566,8 @@ def make_params(stencil=D3Q19, collision=TRT, storage=FP32, pattern=TWO_GRID, om
         mrt_rates = (omega, omega, wm, omega)
     for g in range(4):
         p.mrt_rates[g] = float(mrt_rates[g])
+    for g, v in enumerate((1.0,) * 9 if cumulant_rates is None else cumulant_rates):
+        p.cumulant_rates[g] = float(v)
     return p
 
 

@@ -31,6 +31,7 @@ class Case:
     flags: np.ndarray | None = None
     tile: tuple | None = None
     mrt_rates: tuple | None = None  # MRT: bulk, fourth-, fifth-, sixth-order rates (None: TRT's)
+    cumulant_rates: tuple | None = None  # cumulant: the nine rates after shear (None: all 1)
 
     def block_list(self):
         return self.blocks or [((0, 0, 0), self.shape)]
@@ -42,7 +43,8 @@ class Case:
             mrt_s = oracle.mrt_rates(self.q, self.omega, self.magic_lambda, bulk=b, fourth=f4, fifth=f5, sixth=f6)
         return oracle.OracleParams(shape=self.shape, q=self.q, collision=self.collision, omega=self.omega,
                                    magic_lambda=self.magic_lambda, force=self.force, periodic=self.periodic,
-                                   face_kind=self.faces, face_u=self.face_u, face_rho=self.face_rho, mrt_s=mrt_s)
+                                   face_kind=self.faces, face_u=self.face_u, face_rho=self.face_rho, mrt_s=mrt_s,
+                                   cum_s=tuple(self.cumulant_rates or (1.0,) * 9))
 
     def global_flags(self):
         nx, ny, nz = self.shape
@@ -51,7 +53,7 @@ class Case:
     def make_sim(self, stream=None, device_buffer=None):
         p = lbm.make_params(stencil=self.q, collision=self.collision, storage=self.storage, pattern=self.pattern,
                             omega=self.omega, magic_lambda=self.magic_lambda, force=self.force,
-                            periodic=self.periodic, mrt_rates=self.mrt_rates)
+                            periodic=self.periodic, mrt_rates=self.mrt_rates, cumulant_rates=self.cumulant_rates)
         sim = lbm.Simulation(p, self.block_list(), stream=stream, device_buffer=device_buffer)
         if self.tile:
             sim.set_tile(*self.tile)
