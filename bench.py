@@ -761,6 +761,15 @@ def measure_turbulence(args):
     lbm.load_library()
     variants = [("FP64", "f64"), ("FP32", "f32"), ("FP16_DEV", "f16-dev"), ("BF16_DEV", "bf16-dev"),
                 ("FP64", "f64-cumulant"), ("FP32", "f32-cumulant")]
+    chosen = getattr(args, "turb_variants", None)
+    if chosen:
+        keep = set(chosen.split(","))
+        perf_variants = [v for v in variants if v[1] in keep]
+        # the error study always carries the FP64 reference of each chosen collision
+        keep |= {"f64-cumulant" if k.endswith("cumulant") else "f64" for k in keep}
+        variants = [v for v in variants if v[1] in keep]
+    else:
+        perf_variants = variants
     stream = torch.cuda.Stream()
 
     def make(n, storage, name=""):
@@ -785,7 +794,7 @@ def measure_turbulence(args):
     perf = {}
     peak, peak_kind = measured_peaks()
     sampler = ClockSampler(torch.cuda.current_device())
-    for storage, name in variants:
+    for storage, name in perf_variants:
         if storage == "FP64" and not args.turb_fp64_perf:
             continue
         sim = make(n_perf, storage, name)
@@ -818,7 +827,7 @@ def measure_turbulence(args):
         d1 = sim.reduce()
         sim.close()
         fields[name] = (r, v, d0, d1)
-    spectra = {k: _spectrum(fields[k][1]) for k in ("f64", "f64-cumulant")}
+    spectra = {k: _spectrum(fields[k][1]) for k in ("f64", "f64-cumulant") if k in fields}
     err = {}
     for name, (r, v, d0, d1) in fields.items():
         ref = "f64-cumulant" if name.endswith("cumulant") else "f64"
@@ -850,11 +859,17 @@ def measure_turbulence(args):
                          "frac": perf["f32"]["frac_hbm"], "traffic": None,
                          "kernel": "k_sweep D3Q27 FP32 AA (one launch per step)",
                          "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind} if "f32" in perf else None),
+           "roofline_cumulant": ({"bound": "hbm", "achieved": perf["f32-cumulant"]["gbs"], "peak": peak, "unit": "GB/s",
+                                  "frac": perf["f32-cumulant"]["frac_hbm"], "traffic": None,
+                                  "kernel": "k_sweep D3Q27 FP32 AA, cumulant collision (one launch per step)",
+                                  "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind}
+                                 if "f32-cumulant" in perf else None),
            "clocks": clocks, "throughput": perf, "error_vs_fp64": err,
-           "cumulant_vs_trt_fp64": {"u": float(np.abs(fields["f64-cumulant"][1] - fields["f64"][1]).max()
-                                               / np.abs(fields["f64"][1]).max()),
-                                    "spectrum_l2": float(np.sqrt(((spectra["f64-cumulant"] - spectra["f64"]) ** 2).sum()
-                                                                 / (spectra["f64"] ** 2).sum()))},
+           "cumulant_vs_trt_fp64": ({"u": float(np.abs(fields["f64-cumulant"][1] - fields["f64"][1]).max()
+                                                / np.abs(fields["f64"][1]).max()),
+                                     "spectrum_l2": float(np.sqrt(((spectra["f64-cumulant"] - spectra["f64"]) ** 2).sum()
+                                                                  / (spectra["f64"] ** 2).sum()))}
+                                    if len(spectra) == 2 else None),
            "cpu_baseline": (cpu_baseline_turbulence(min_seconds=getattr(args, "cpu_seconds", 10.0))
                             if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None)}
     return out
@@ -1097,6 +1112,8 @@ def main(argv=None):
     ap.add_argument("--turb-size", type=int, default=512)
     ap.add_argument("--turb-err-size", type=int, default=256)
     ap.add_argument("--turb-fp64-perf", action="store_true")
+    ap.add_argument("--turb-variants", default=None,
+                    help="comma-separated subset of f64,f32,f16-dev,bf16-dev,f64-cumulant,f32-cumulant")
     ap.add_argument("--no-workloads", action="store_true",
                     help="channel: leave out the records of the other configurations (C1, C3, C4, C5)")
     ap.add_argument("--min-seconds", type=float, default=2.0,

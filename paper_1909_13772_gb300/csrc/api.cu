@@ -896,6 +896,10 @@ lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, in
         d.cum[0] = wp;
         for (int g = 0; g < 9; ++g) d.cum[g + 1] = p.cumulant_rates[g];
         d.cumulant = 1;
+        // every rate beyond the bulk at 1: the sweep takes the path that resets the cumulants of
+        // order 3..6 without computing them
+        d.cum_unit = 1;
+        for (int g = 1; g < 9; ++g) d.cum_unit = d.cum_unit && p.cumulant_rates[g] == 1.0;
     }
     d.rho0 = dev ? p.rho0 : 0.0;
     for (int i = 0; i < 27; ++i) d.base[i] = c->base[i];
@@ -925,6 +929,7 @@ lbm_status create_ctx(const lbm_params *params, const lbm_block_desc *blocks, in
     for (int g = 0; g < 4; ++g) f.mrt_d[g] = (float)d.mrt_d[g];
     for (int g = 0; g < 10; ++g) f.cum[g] = (float)d.cum[g];
     f.cumulant = d.cumulant;
+    f.cum_unit = d.cum_unit;
     f.rho0 = (float)d.rho0;
     *out = c;
     return LBM_OK;

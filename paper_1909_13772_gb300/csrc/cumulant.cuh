@@ -137,46 +137,7 @@ __device__ __forceinline__ void collide_cumulant(R (&f)[27], const Coll<R> &k, R
     ux_out = ux;
     uy_out = uy;
     uz_out = uz;
-    // central shifts along z, y, x, each adding the equilibrium part r0 W W D(u) it changes
-    cum_shift<2, false>(g, uz, r0);
-    cum_shift<1, false>(g, uy, r0);
-    cum_shift<0, false>(g, ux, r0);
-    // excess central moments: remove rho W W W (r0 of it is already out)
-#pragma unroll
-    for (int kk = 1; kk < 27; ++kk) {
-        const double ww = cum_w(kk % 3) * cum_w((kk / 3) % 3) * cum_w(kk / 9);
-        if (ww != 0.0) g[kk] = fma(-R(ww), drho, g[kk]);
-    }
-    // cumulants of order 4..6 (orders 2 and 3: the excess central moments themselves)
     const R third = R(1.0 / 3.0);
-    R C[27];
-#pragma unroll
-    for (int kk = 0; kk < 27; ++kk) C[kk] = g[kk];
-    // 211-type: doubled axis d, singles p < q
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int p = d == 0 ? 1 : 0, q = d == 2 ? 1 : 2;
-        const int id = 2 * cax(d) + cax(p) + cax(q), pq = cax(p) + cax(q);
-        C[id] = g[id] - third * g[pq] - (g[cdd(d)] * g[pq] + R(2) * g[cax(d) + cax(p)] * g[cax(d) + cax(q)]) * inv;
-    }
-    // 220-type: doubled axes p < q
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
-        const int id = 2 * cax(p) + 2 * cax(q);
-        C[id] = g[id] - third * (g[cdd(p)] + g[cdd(q)]) - (g[cdd(p)] * g[cdd(q)] + R(2) * g[cax(p) + cax(q)] * g[cax(p) + cax(q)]) * inv;
-    }
-    // 122-type: single axis s, doubled p < q
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
-        const int id = cax(s) + 2 * cax(p) + 2 * cax(q);
-        const int s2q = cax(s) + 2 * cax(q), s2p = cax(s) + 2 * cax(p);
-        C[id] = g[id] - third * (g[s2q] + g[s2p]) -
-                (g[cdd(p)] * g[s2q] + g[cdd(q)] * g[s2p] + R(2) * g[cax(s) + cax(p)] * g[cax(p) + 2 * cax(q)] +
-                 R(2) * g[cax(s) + cax(q)] * g[2 * cax(p) + cax(q)] + R(4) * g[cax(p) + cax(q)] * g[cix(1, 1, 1)]) *
-                    inv;
-    }
     auto c222 = [&](const R (&m)[27], const R (&c4)[27]) {
         const R a = m[cix(2, 0, 0)], b = m[cix(0, 2, 0)], c = m[cix(0, 0, 2)];
         const R xy = m[cix(1, 1, 0)], xz = m[cix(1, 0, 1)], yz = m[cix(0, 1, 1)];
@@ -191,81 +152,156 @@ __device__ __forceinline__ void collide_cumulant(R (&f)[27], const Coll<R> &k, R
         R t3 = a * b * c + R(2) * (a * yz * yz + b * xz * xz + c * xy * xy) + R(8) * xy * xz * yz;
         return t1 + t2 * inv + t3 * inv2;
     };
-    C[cix(2, 2, 2)] = g[cix(2, 2, 2)] - c222(g, C);
-    // relaxation
-    const R *w = k.cum;  // shear, bulk, 3 sum, 3 diff, 111, 4 diff, 4 sum, 211, 5th, 6th
-    {
-        R dxy = C[cix(2, 0, 0)] - C[cix(0, 2, 0)], dxz = C[cix(2, 0, 0)] - C[cix(0, 0, 2)];
-        R tr = C[cix(2, 0, 0)] + C[cix(0, 2, 0)] + C[cix(0, 0, 2)];
-        dxy = fma(-w[0], dxy, dxy);
-        dxz = fma(-w[0], dxz, dxz);
-        tr = fma(-w[1], tr, tr);
-        const R a = third * (dxy + dxz + tr);
-        C[cix(2, 0, 0)] = a;
-        C[cix(0, 2, 0)] = a - dxy;
-        C[cix(0, 0, 2)] = a - dxz;
-        C[cix(1, 1, 0)] = fma(-w[0], C[cix(1, 1, 0)], C[cix(1, 1, 0)]);
-        C[cix(1, 0, 1)] = fma(-w[0], C[cix(1, 0, 1)], C[cix(1, 0, 1)]);
-        C[cix(0, 1, 1)] = fma(-w[0], C[cix(0, 1, 1)], C[cix(0, 1, 1)]);
-    }
+    // shear and bulk relaxation of the second-order excess (a, b, c, xy, xz, yz)
+    auto relax2 = [&](R &a, R &b, R &c, R &xy, R &xz, R &yz) {
+        R dxy = a - b, dxz = a - c, tr = a + b + c;
+        dxy = fma(-k.cum[0], dxy, dxy);
+        dxz = fma(-k.cum[0], dxz, dxz);
+        tr = fma(-k.cum[1], tr, tr);
+        a = third * (dxy + dxz + tr);
+        b = a - dxy;
+        c = a - dxz;
+        xy = fma(-k.cum[0], xy, xy);
+        xz = fma(-k.cum[0], xz, xz);
+        yz = fma(-k.cum[0], yz, yz);
+    };
+    if (k.cum_unit) {
+        // every rate beyond the bulk is 1: the cumulants of order 3..6 are reset to zero, so
+        // only the second-order excess is needed, from the raw moments:
+        //   k^_aa = sum v c_a^2 - drho/3 - rho u_a^2 (+ u_a F_a),
+        //   k^_ab = sum v c_a c_b - rho u_a u_b (+ (u_a F_b + u_b F_a)/2)
+        R a = fma(-third, drho, g[cix(2, 0, 0)]) - rho * ux * ux;
+        R b = fma(-third, drho, g[cix(0, 2, 0)]) - rho * uy * uy;
+        R c = fma(-third, drho, g[cix(0, 0, 2)]) - rho * uz * uz;
+        R xy = g[cix(1, 1, 0)] - rho * ux * uy, xz = g[cix(1, 0, 1)] - rho * ux * uz, yz = g[cix(0, 1, 1)] - rho * uy * uz;
+        if (FORCE) {
+            a = fma(ux, k.F[0], a);
+            b = fma(uy, k.F[1], b);
+            c = fma(uz, k.F[2], c);
+            xy += R(0.5) * (ux * k.F[1] + uy * k.F[0]);
+            xz += R(0.5) * (ux * k.F[2] + uz * k.F[0]);
+            yz += R(0.5) * (uy * k.F[2] + uz * k.F[1]);
+        }
+        relax2(a, b, c, xy, xz, yz);
+        // post-collision excess central moments (orders 3 and 5 vanish with their cumulants)
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
-        const int A = cax(s) + 2 * cax(p), B = cax(s) + 2 * cax(q);
-        R sm = C[A] + C[B], df = C[A] - C[B];
-        sm = fma(-w[2], sm, sm);
-        df = fma(-w[3], df, df);
-        C[A] = R(0.5) * (sm + df);
-        C[B] = R(0.5) * (sm - df);
-    }
-    C[cix(1, 1, 1)] = fma(-w[4], C[cix(1, 1, 1)], C[cix(1, 1, 1)]);
-    {
-        const R a = C[cix(2, 2, 0)], b = C[cix(2, 0, 2)], c = C[cix(0, 2, 2)];
-        R d1 = a - R(2) * b + c, d2 = a + b - R(2) * c, t = a + b + c;
-        d1 = fma(-w[5], d1, d1);
-        d2 = fma(-w[5], d2, d2);
-        t = fma(-w[6], t, t);
-        C[cix(2, 2, 0)] = third * (d1 + d2 + t);
-        C[cix(2, 0, 2)] = third * (t - d1);
-        C[cix(0, 2, 2)] = third * (t - d2);
-    }
+        for (int kk = 0; kk < 27; ++kk) g[kk] = R(0);
+        g[cix(2, 0, 0)] = a;
+        g[cix(0, 2, 0)] = b;
+        g[cix(0, 0, 2)] = c;
+        g[cix(1, 1, 0)] = xy;
+        g[cix(1, 0, 1)] = xz;
+        g[cix(0, 1, 1)] = yz;
+        g[cix(2, 2, 2)] = c222(g, g);  // every third- and fourth-order entry still zero here
+        g[cix(2, 2, 0)] = third * (a + b) + (a * b + R(2) * xy * xy) * inv;
+        g[cix(2, 0, 2)] = third * (a + c) + (a * c + R(2) * xz * xz) * inv;
+        g[cix(0, 2, 2)] = third * (b + c) + (b * c + R(2) * yz * yz) * inv;
+        g[cix(2, 1, 1)] = third * yz + (a * yz + R(2) * xy * xz) * inv;
+        g[cix(1, 2, 1)] = third * xz + (b * xz + R(2) * xy * yz) * inv;
+        g[cix(1, 1, 2)] = third * xy + (c * xy + R(2) * xz * yz) * inv;
+    } else {
+        // central shifts along z, y, x, each adding the equilibrium part r0 W W D(u) it changes
+        cum_shift<2, false>(g, uz, r0);
+        cum_shift<1, false>(g, uy, r0);
+        cum_shift<0, false>(g, ux, r0);
+        // excess central moments: remove rho W W W (r0 of it is already out)
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int id = cax(d) + 13;  // 2 cax(d) + the two other axes once (1 + 3 + 9 - cax(d))
-        C[id] = fma(-w[7], C[id], C[id]);
-    }
+        for (int kk = 1; kk < 27; ++kk) {
+            const double ww = cum_w(kk % 3) * cum_w((kk / 3) % 3) * cum_w(kk / 9);
+            if (ww != 0.0) g[kk] = fma(-R(ww), drho, g[kk]);
+        }
+        // cumulants of order 4..6 (orders 2 and 3: the excess central moments themselves)
+        R C[27];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int id = 26 - cax(s);  // cax(s) + the two other axes twice, 2 (13 - cax(s))
-        C[id] = fma(-w[8], C[id], C[id]);
-    }
-    C[cix(2, 2, 2)] = fma(-w[9], C[cix(2, 2, 2)], C[cix(2, 2, 2)]);
-    // back to excess central moments, in order of increasing order
+        for (int kk = 0; kk < 27; ++kk) C[kk] = g[kk];
+        // 211-type: doubled axis d, singles p < q
 #pragma unroll
-    for (int kk = 0; kk < 27; ++kk) g[kk] = C[kk];
+        for (int d = 0; d < 3; ++d) {
+            const int p = d == 0 ? 1 : 0, q = d == 2 ? 1 : 2;
+            const int id = 2 * cax(d) + cax(p) + cax(q), pq = cax(p) + cax(q);
+            C[id] = g[id] - third * g[pq] - (g[cdd(d)] * g[pq] + R(2) * g[cax(d) + cax(p)] * g[cax(d) + cax(q)]) * inv;
+        }
+        // 220-type: doubled axes p < q
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        const int p = d == 0 ? 1 : 0, q = d == 2 ? 1 : 2;
-        const int id = 2 * cax(d) + cax(p) + cax(q), pq = cax(p) + cax(q);
-        g[id] = C[id] + third * C[pq] + (C[cdd(d)] * C[pq] + R(2) * C[cax(d) + cax(p)] * C[cax(d) + cax(q)]) * inv;
-    }
+        for (int s = 0; s < 3; ++s) {
+            const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
+            const int id = 2 * cax(p) + 2 * cax(q);
+            C[id] = g[id] - third * (g[cdd(p)] + g[cdd(q)]) - (g[cdd(p)] * g[cdd(q)] + R(2) * g[cax(p) + cax(q)] * g[cax(p) + cax(q)]) * inv;
+        }
+        // 122-type: single axis s, doubled p < q
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
-        const int id = 2 * cax(p) + 2 * cax(q);
-        g[id] = C[id] + third * (C[cdd(p)] + C[cdd(q)]) + (C[cdd(p)] * C[cdd(q)] + R(2) * C[cax(p) + cax(q)] * C[cax(p) + cax(q)]) * inv;
-    }
+        for (int s = 0; s < 3; ++s) {
+            const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
+            const int id = cax(s) + 2 * cax(p) + 2 * cax(q);
+            const int s2q = cax(s) + 2 * cax(q), s2p = cax(s) + 2 * cax(p);
+            C[id] = g[id] - third * (g[s2q] + g[s2p]) -
+                    (g[cdd(p)] * g[s2q] + g[cdd(q)] * g[s2p] + R(2) * g[cax(s) + cax(p)] * g[cax(p) + 2 * cax(q)] +
+                     R(2) * g[cax(s) + cax(q)] * g[2 * cax(p) + cax(q)] + R(4) * g[cax(p) + cax(q)] * g[cix(1, 1, 1)]) *
+                        inv;
+        }
+        C[cix(2, 2, 2)] = g[cix(2, 2, 2)] - c222(g, C);
+        // relaxation
+        const R *w = k.cum;  // shear, bulk, 3 sum, 3 diff, 111, 4 diff, 4 sum, 211, 5th, 6th
+        relax2(C[cix(2, 0, 0)], C[cix(0, 2, 0)], C[cix(0, 0, 2)], C[cix(1, 1, 0)], C[cix(1, 0, 1)], C[cix(0, 1, 1)]);
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
-        const int id = cax(s) + 2 * cax(p) + 2 * cax(q);
-        const int s2q = cax(s) + 2 * cax(q), s2p = cax(s) + 2 * cax(p);
-        g[id] = C[id] + third * (C[s2q] + C[s2p]) +
-                (C[cdd(p)] * C[s2q] + C[cdd(q)] * C[s2p] + R(2) * C[cax(s) + cax(p)] * C[cax(p) + 2 * cax(q)] +
-                 R(2) * C[cax(s) + cax(q)] * C[2 * cax(p) + cax(q)] + R(4) * C[cax(p) + cax(q)] * C[cix(1, 1, 1)]) *
-                    inv;
+        for (int s = 0; s < 3; ++s) {
+            const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
+            const int A = cax(s) + 2 * cax(p), B = cax(s) + 2 * cax(q);
+            R sm = C[A] + C[B], df = C[A] - C[B];
+            sm = fma(-w[2], sm, sm);
+            df = fma(-w[3], df, df);
+            C[A] = R(0.5) * (sm + df);
+            C[B] = R(0.5) * (sm - df);
+        }
+        C[cix(1, 1, 1)] = fma(-w[4], C[cix(1, 1, 1)], C[cix(1, 1, 1)]);
+        {
+            const R a = C[cix(2, 2, 0)], b = C[cix(2, 0, 2)], c = C[cix(0, 2, 2)];
+            R d1 = a - R(2) * b + c, d2 = a + b - R(2) * c, t = a + b + c;
+            d1 = fma(-w[5], d1, d1);
+            d2 = fma(-w[5], d2, d2);
+            t = fma(-w[6], t, t);
+            C[cix(2, 2, 0)] = third * (d1 + d2 + t);
+            C[cix(2, 0, 2)] = third * (t - d1);
+            C[cix(0, 2, 2)] = third * (t - d2);
+        }
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int id = cax(d) + 13;  // 2 cax(d) + the two other axes once (1 + 3 + 9 - cax(d))
+            C[id] = fma(-w[7], C[id], C[id]);
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int id = 26 - cax(s);  // cax(s) + the two other axes twice, 2 (13 - cax(s))
+            C[id] = fma(-w[8], C[id], C[id]);
+        }
+        C[cix(2, 2, 2)] = fma(-w[9], C[cix(2, 2, 2)], C[cix(2, 2, 2)]);
+        // back to excess central moments, in order of increasing order
+#pragma unroll
+        for (int kk = 0; kk < 27; ++kk) g[kk] = C[kk];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int p = d == 0 ? 1 : 0, q = d == 2 ? 1 : 2;
+            const int id = 2 * cax(d) + cax(p) + cax(q), pq = cax(p) + cax(q);
+            g[id] = C[id] + third * C[pq] + (C[cdd(d)] * C[pq] + R(2) * C[cax(d) + cax(p)] * C[cax(d) + cax(q)]) * inv;
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
+            const int id = 2 * cax(p) + 2 * cax(q);
+            g[id] = C[id] + third * (C[cdd(p)] + C[cdd(q)]) + (C[cdd(p)] * C[cdd(q)] + R(2) * C[cax(p) + cax(q)] * C[cax(p) + cax(q)]) * inv;
+        }
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int p = s == 0 ? 1 : 0, q = s == 2 ? 1 : 2;
+            const int id = cax(s) + 2 * cax(p) + 2 * cax(q);
+            const int s2q = cax(s) + 2 * cax(q), s2p = cax(s) + 2 * cax(p);
+            g[id] = C[id] + third * (C[s2q] + C[s2p]) +
+                    (C[cdd(p)] * C[s2q] + C[cdd(q)] * C[s2p] + R(2) * C[cax(s) + cax(p)] * C[cax(p) + 2 * cax(q)] +
+                     R(2) * C[cax(s) + cax(q)] * C[2 * cax(p) + cax(q)] + R(4) * C[cax(p) + cax(q)] * C[cix(1, 1, 1)]) *
+                        inv;
+        }
+        g[cix(2, 2, 2)] = C[cix(2, 2, 2)] + c222(C, C);
     }
-    g[cix(2, 2, 2)] = C[cix(2, 2, 2)] + c222(C, C);
     // central moments less r0 W W W: add rho - r0 of W W W back; first order +F/2
 #pragma unroll
     for (int kk = 1; kk < 27; ++kk) {

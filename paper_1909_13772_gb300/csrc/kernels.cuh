@@ -89,6 +89,7 @@ struct Coll {
     R cum[10];             // cumulant (D3Q27): rates of the shear, bulk, third-order sum, difference, xyz,
                            // fourth-order difference, sum, mixed, fifth- and sixth-order groups
     int cumulant;          // non-zero: the context's collision is the cumulant one (init kernel)
+    int cum_unit;          // non-zero: every cumulant rate beyond the bulk is 1
 };
 
 // Pair-form rates for omega+ / omega- (host or device).

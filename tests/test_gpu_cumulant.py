@@ -59,6 +59,18 @@ def test_periodic_random_state_with_force(storage, pattern):
 
 @pytest.mark.parametrize("storage", [lbm.FP64, lbm.FP32])
 @pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
+def test_unit_higher_rates_with_force(storage, pattern):
+    """Every rate beyond the bulk at 1: the kernel resets the cumulants of order 3..6 without
+    computing them (the second-order excess from the raw moments alone); same oracle."""
+    shape = (45, 19, 13)
+    case = Case(shape=shape, q=27, collision=lbm.CUMULANT, storage=storage, pattern=pattern, omega=1.7,
+                force=(3e-6, 1e-6, -2e-6), cumulant_rates=(1.35,) + (1.0,) * 8)
+    rho, u = inputs.random_state(shape, seed=44, rho_amp=0.02, u_amp=0.04)
+    _compare(case, rho, u, 30)
+
+
+@pytest.mark.parametrize("storage", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
 def test_channel_walls_and_force(storage, pattern):
     shape = (70, 37, 11)
     case = Case(shape=shape, q=27, collision=lbm.CUMULANT, storage=storage, pattern=pattern, omega=1.0,
