@@ -11,6 +11,10 @@ library packs and unpacks (lbm_halo_pack / lbm_halo_unpack); this module moves t
 * ``LocalPartition`` -- every rank's context in one process on one GPU, the buffers handed over
   by device copies on one stream (no waits between kernels of different contexts).
 
+Domain totals (mass, momentum, kinetic energy, ...) are each rank's FP64 totals over its own
+blocks (lbm_reduce), gathered to every rank and combined there in rank order
+(``combine_diagnostics``), so every rank holds the same bits from run to run.
+
 Marshalling only: every PDF moves through the library's kernels.
 """
 from __future__ import annotations
@@ -43,6 +47,40 @@ def _capacity(sim, peer):
     rows = [lbm.lbm_plan_halo(sim.ctx, peer, k) for k in range(4)]
     n = [int((r[:, 1] + r[:, 2]).max()) if r.size else 0 for r in rows]
     return max(n)
+
+
+_DIAG_SUMS = ("mass", "momentum", "kinetic_energy", "nonfinite", "fluid_cells")
+
+
+def _diag_vector(d) -> list:
+    """One rank's totals as 8 doubles: mass, momentum x/y/z, kinetic energy, max speed,
+    non-finite cells, fluid cells (counts are exact in FP64 up to 2^53)."""
+    return [float(d["mass"])] + [float(v) for v in d["momentum"]] + [
+        float(d["kinetic_energy"]), float(d["max_speed"]), float(d["nonfinite"]), float(d["fluid_cells"])]
+
+
+def combine_diagnostics(per_rank: list) -> dict:
+    """Domain totals from the ranks' own totals, in rank order: sums for mass, momentum, kinetic
+    energy and the counts, maximum for the speed (FP64, a fixed order, no reassociation)."""
+    rows = [_diag_vector(d) if isinstance(d, dict) else [float(v) for v in d] for d in per_rank]
+    acc = list(rows[0])
+    for r in rows[1:]:
+        for k in range(8):
+            acc[k] = max(acc[k], r[k]) if k == 5 else acc[k] + r[k]
+    return {"mass": acc[0], "momentum": (acc[1], acc[2], acc[3]), "kinetic_energy": acc[4], "max_speed": acc[5],
+            "nonfinite": int(acc[6]), "fluid_cells": int(acc[7])}
+
+
+def allreduce_diagnostics(local: dict, group=None) -> dict:
+    """Every rank's totals gathered to every rank (one all-gather of 8 doubles per rank) and
+    combined in rank order: the same result, bit for bit, on every rank."""
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    v = torch.tensor(_diag_vector(local), dtype=torch.float64, device=dev)
+    parts = [torch.empty_like(v) for _ in range(dist.get_world_size(group))]
+    dist.all_gather(parts, v, group=group)
+    return combine_diagnostics([p.cpu().tolist() for p in parts])
 
 
 def exchange_buffers(send: dict, recv: dict, group=None):
@@ -108,6 +146,10 @@ class PartitionedRun:
             self.exchange()
             lbm.lbm_step(self.sim.ctx, 1)
 
+    def reduce(self):
+        """Domain totals of the current state (FP64, the same bits on every rank)."""
+        return allreduce_diagnostics(self.sim.reduce(), self.group)
+
     def close(self):
         self.sim.close()
 
@@ -157,6 +199,10 @@ class LocalPartition:
             self.exchange()
             for s in self.sims:
                 lbm.lbm_step(s.ctx, 1)
+
+    def reduce(self):
+        """Domain totals of the current state: every rank's own totals combined in rank order."""
+        return combine_diagnostics([s.reduce() for s in self.sims])
 
     def close(self):
         for s in self.sims:

@@ -144,3 +144,37 @@ def test_partitioned_step_refuses_several_steps_per_call():
         assert e.value.status == 2  # LBM_ERR_STATE
     finally:
         run.close()
+
+
+def test_partitioned_diagnostics_equal_the_one_context_totals():
+    """The ranks' FP64 totals combined in rank order against lbm_reduce of one context holding
+    every block: the same cells, summed in another order (mass and momentum to FP64 rounding,
+    the counts and the maximum speed exactly)."""
+    case = _case(lbm.FP64, lbm.AA, force=(1e-6, 0.0, 0.0))
+    rho, u = inputs.random_state(case.shape, seed=25, rho_amp=0.01, u_amp=0.02)
+    sim = case.make_sim()
+    try:
+        init_sim(sim, rho, u)
+        sim.step(6)
+        want = sim.reduce()
+    finally:
+        sim.close()
+    p = lbm.make_params(stencil=case.q, collision=case.collision, storage=case.storage, pattern=case.pattern,
+                        omega=case.omega, magic_lambda=case.magic_lambda, force=case.force, periodic=case.periodic)
+    run = shard.LocalPartition(p, case.block_list(), 3)
+    try:
+        for s in run.sims:
+            _setup(s, case)
+        for b, (o, sz) in enumerate(case.block_list()):
+            run.sims[run.owner[b]].init(b, rho[o[2]:o[2] + sz[2], o[1]:o[1] + sz[1], o[0]:o[0] + sz[0]],
+                                        u[:, o[2]:o[2] + sz[2], o[1]:o[1] + sz[1], o[0]:o[0] + sz[0]])
+        run.step(6)
+        got = run.reduce()
+    finally:
+        run.close()
+    assert got["fluid_cells"] == want["fluid_cells"] and got["nonfinite"] == 0
+    assert got["max_speed"] == want["max_speed"]
+    assert abs(got["mass"] - want["mass"]) <= 1e-13 * want["mass"]
+    for a in range(3):
+        assert abs(got["momentum"][a] - want["momentum"][a]) <= 1e-13 * want["mass"]
+    assert abs(got["kinetic_energy"] - want["kinetic_energy"]) <= 1e-12 * want["kinetic_energy"]

@@ -314,3 +314,52 @@ def test_two_gloo_ranks_exchange_the_halo():
     assert (r0, r1) == (0, 1)
     assert s0 == v1 > 0 and s1 == v0 > 0
     assert bad0 == 0 and bad1 == 0
+
+
+def test_combine_diagnostics_sums_in_rank_order_and_takes_the_max_speed():
+    from paper_1909_13772_gb300 import shard
+    a = {"mass": 1.0, "momentum": (1e-3, 0.0, -2e-3), "kinetic_energy": 0.5, "max_speed": 0.02, "nonfinite": 0,
+         "fluid_cells": 10}
+    b = {"mass": 1e-16, "momentum": (0.0, 1.0, 0.0), "kinetic_energy": 0.25, "max_speed": 0.05, "nonfinite": 2,
+         "fluid_cells": 7}
+    c = {"mass": -1.0, "momentum": (0.0, 0.0, 0.0), "kinetic_energy": 0.0, "max_speed": 0.01, "nonfinite": 0,
+         "fluid_cells": 3}
+    d = shard.combine_diagnostics([a, b, c])
+    assert d["mass"] == (1.0 + 1e-16) + -1.0  # the rank order, not a reassociated sum
+    assert d["momentum"] == (1e-3, 1.0, -2e-3)
+    assert d["kinetic_energy"] == 0.75 and d["max_speed"] == 0.05
+    assert d["nonfinite"] == 2 and d["fluid_cells"] == 20
+
+
+def _gloo_reduce_rank(rank, world, port, q_out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    from paper_1909_13772_gb300 import shard
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        local = {"mass": 0.1 * (rank + 1), "momentum": (1e-17 * rank, -rank, 3.0), "kinetic_energy": 2.0 ** -rank,
+                 "max_speed": 0.01 * (3 - rank), "nonfinite": rank, "fluid_cells": 1000 + rank}
+        q_out.put((rank, shard.allreduce_diagnostics(local)))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_three_gloo_ranks_allreduce_the_diagnostics_identically():
+    pytest.importorskip("torch")
+    from paper_1909_13772_gb300 import shard
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gloo_reduce_rank, args=(r, 3, port, q)) for r in range(3)]
+    for pr in procs:
+        pr.start()
+    out = sorted((q.get(timeout=180) for _ in procs), key=lambda t: t[0])
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    want = shard.combine_diagnostics([
+        {"mass": 0.1 * (r + 1), "momentum": (1e-17 * r, -r, 3.0), "kinetic_energy": 2.0 ** -r,
+         "max_speed": 0.01 * (3 - r), "nonfinite": r, "fluid_cells": 1000 + r} for r in range(3)])
+    for _, got in out:
+        assert got == want  # every rank the same bits, in rank order
