@@ -7,7 +7,7 @@ restatement of the single-cell collision used to cross-check it.
 """
 from .oracle import (  # noqa: F401
     FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC, ZOUHE_VELOCITY, ZOUHE_PRESSURE, SRT, TRT, MRT, CUMULANT, mrt_matrix, mrt_rates,
-    cumulants, cumulants_to_f,
+    cumulants, cumulants_to_f, refine_fine_params, refine_slab_flags, refine_init, refine_run,
     OracleParams, build_oracle, lattice, omega_minus, equilibrium, collide_cell,
     init, run, stream, macroscopic, diagnostics, set_threads, get_threads,
     NO_CLOSURE, SMAGORINSKY, MLP, collide_closure,

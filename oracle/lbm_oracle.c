@@ -1086,3 +1086,163 @@ int orc_macroscopic(const orc_params *p, const uint8_t *flags, const double *f, 
     }
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------------
+ * Static 2:1 grid refinement, mass-conserving (Sec. 5.1.1: non-uniform grids by the method of
+ * Rohde et al. 2006, which the paper names without giving its rules).  Reading, in the
+ * volumetric form of that method:
+ *   * cells are volumes and the populations densities in them; a coarse cell holds 2 x 2 x 2
+ *     fine cells; the fine grid takes two steps per coarse step; its rates follow from the
+ *     same physical viscosity under acoustic scaling, tau_f - 1/2 = 2 (tau_c - 1/2) (TRT: the
+ *     same Lambda on both grids), and its body force is F_c / 2 (so that the force per volume
+ *     and coarse step is the same);
+ *   * geometry: the coarse grid covers the periodic nx x ny x nz box; the coarse columns
+ *     x in [a, b) (periodic in x; 0 <= a < b <= nx, b - a < nx) are refined: the fine grid
+ *     covers them with 2 (b - a) x 2 ny x 2 nz cells; y and z are periodic on both grids;
+ *   * one coarse step:
+ *     1. explosion: a layer of fine ghost cells two deep on each side of the fine grid
+ *        (inside the coarse columns a - 1 and b) takes the post-collision populations of the
+ *        coarse cell it lies in, the same value in each of its 8 fine cells (no
+ *        interpolation, no rescaling of the non-equilibrium part);
+ *     2. two fine steps, each: push-stream every fine cell, ghosts included (values that would
+ *        leave the ghost layer are dropped), then collide the fine cells (ghosts keep what
+ *        streamed into them);
+ *     3. coalescence and coarse streaming: push-stream the coarse cells; a coarse population
+ *        whose target lies in the refined columns is dropped (the explosion delivered it); a
+ *        coarse cell next to the refined columns takes, for each direction whose source lies
+ *        there, the mean of that direction's values over the 8 fine ghost cells inside it
+ *        (the fine populations that left the fine grid into its volume during the two fine
+ *        steps); then collide the coarse cells.
+ *   Each population that crosses the interface is counted once on each side, so the mass
+ *   sum_coarse f + (1/8) sum_fine f is conserved exactly in exact arithmetic, and so is the
+ *   momentum apart from the body force.
+ * State: fc[i][z][y][x] over the coarse box (the refined columns hold zeros),
+ * ff[i][zf][yf][xf] over the fine grid, both post-collision.
+ * ------------------------------------------------------------------------------------- */
+int orc_refine_fine_params(const orc_params *pc, int32_t a, int32_t b, orc_params *pf)
+{
+    if (pc->collision != ORC_SRT && pc->collision != ORC_TRT) return -1;
+    if (!(pc->periodic[0] && pc->periodic[1] && pc->periodic[2])) return -2;
+    if (a < 0 || b > pc->nx || a >= b || b - a >= pc->nx) return -3;
+    if (!(pc->omega > 0.0 && pc->omega < 2.0)) return -4;
+    *pf = *pc;
+    pf->nx = 2 * (b - a);
+    pf->ny = 2 * pc->ny;
+    pf->nz = 2 * pc->nz;
+    pf->omega = 1.0 / (0.5 + 2.0 * (1.0 / pc->omega - 0.5));
+    for (int k = 0; k < 3; ++k) pf->force[k] = 0.5 * pc->force[k];
+    return 0;
+}
+
+int orc_refine_run(const orc_params *pc, int32_t a, int32_t b, double *fc, double *ff, int64_t nsteps)
+{
+    lattice_t L;
+    orc_params pf;
+    int r = orc_refine_fine_params(pc, a, b, &pf);
+    if (r != 0) return r;
+    if (get_lattice(pc->q, &L) != 0) return -1;
+    const int q = L.q;
+    const int nx = pc->nx, ny = pc->ny, nz = pc->nz;
+    const int64_t Nc = (int64_t)nx * ny * nz;
+    const int nf = pf.nx, nyf = pf.ny, nzf = pf.nz;
+    const int nxg = nf + 4; /* fine grid with its two ghost columns on each side: xg = xf + 2 */
+    const int64_t Ng = (int64_t)nxg * nyf * nzf;
+    const int64_t Nf = (int64_t)nf * nyf * nzf;
+    double *g = calloc((size_t)q * Ng, sizeof(double));
+    double *gw = calloc((size_t)q * Ng, sizeof(double));
+    double *cw = calloc((size_t)q * Nc, sizeof(double));
+    if (!g || !gw || !cw) {
+        free(g);
+        free(gw);
+        free(cw);
+        return -6;
+    }
+#define IN_SLAB(x) (((x) - a + nx) % nx < b - a)
+    for (int i = 0; i < q; ++i)
+        for (int z = 0; z < nzf; ++z)
+            for (int y = 0; y < nyf; ++y)
+                for (int x = 0; x < nf; ++x)
+                    g[i * Ng + ((int64_t)z * nyf + y) * nxg + x + 2] = ff[i * Nf + ((int64_t)z * nyf + y) * nf + x];
+    const int left = (a - 1 + nx) % nx, right = b % nx; /* coarse columns holding the ghosts */
+    for (int64_t step = 0; step < nsteps; ++step) {
+        /* 1. explosion */
+        for (int i = 0; i < q; ++i)
+            for (int z = 0; z < nzf; ++z)
+                for (int y = 0; y < nyf; ++y)
+                    for (int s = 0; s < 4; ++s) {
+                        const int xg = s < 2 ? s : nf + s; /* 0, 1 | nf + 2, nf + 3 */
+                        const int xc = s < 2 ? left : right;
+                        g[i * Ng + ((int64_t)z * nyf + y) * nxg + xg] = fc[i * Nc + ((int64_t)(z / 2) * ny + y / 2) * nx + xc];
+                    }
+        /* 2. two fine steps */
+        for (int sub = 0; sub < 2; ++sub) {
+            memset(gw, 0, sizeof(double) * (size_t)q * Ng);
+            for (int z = 0; z < nzf; ++z)
+                for (int y = 0; y < nyf; ++y)
+                    for (int x = 0; x < nxg; ++x)
+                        for (int i = 0; i < q; ++i) {
+                            const int xt = x + L.c[3 * i];
+                            if (xt < 0 || xt >= nxg) continue;
+                            const int yt = (y + L.c[3 * i + 1] + nyf) % nyf, zt = (z + L.c[3 * i + 2] + nzf) % nzf;
+                            gw[i * Ng + ((int64_t)zt * nyf + yt) * nxg + xt] = g[i * Ng + ((int64_t)z * nyf + y) * nxg + x];
+                        }
+            memcpy(g, gw, sizeof(double) * (size_t)q * Ng);
+#pragma omp parallel for schedule(static)
+            for (int64_t n = 0; n < Ng; ++n) {
+                const int xg = (int)(n % nxg);
+                if (xg < 2 || xg >= nf + 2) continue; /* ghosts are not collided */
+                double fin[QMAX], fout[QMAX];
+                for (int i = 0; i < q; ++i) fin[i] = g[i * Ng + n];
+                collide(&L, &pf, NULL, fin, fout);
+                for (int i = 0; i < q; ++i) g[i * Ng + n] = fout[i];
+            }
+        }
+        /* 3. coarse streaming with coalescence, then the coarse collision */
+        memset(cw, 0, sizeof(double) * (size_t)q * Nc);
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    if (IN_SLAB(x)) continue;
+                    for (int i = 0; i < q; ++i) {
+                        const int xt = (x + L.c[3 * i] + nx) % nx;
+                        if (IN_SLAB(xt)) continue;
+                        const int yt = (y + L.c[3 * i + 1] + ny) % ny, zt = (z + L.c[3 * i + 2] + nz) % nz;
+                        cw[i * Nc + ((int64_t)zt * ny + yt) * nx + xt] = fc[i * Nc + ((int64_t)z * ny + y) * nx + x];
+                    }
+                }
+        for (int side = 0; side < 2; ++side) {
+            const int xc = side == 0 ? left : right;
+            const int xg0 = side == 0 ? 0 : nf + 2;
+            for (int z = 0; z < nz; ++z)
+                for (int y = 0; y < ny; ++y)
+                    for (int i = 0; i < q; ++i) {
+                        const int xs = (xc - L.c[3 * i] + nx) % nx;
+                        if (!IN_SLAB(xs)) continue;
+                        double s = 0.0;
+                        for (int dz = 0; dz < 2; ++dz)
+                            for (int dy = 0; dy < 2; ++dy)
+                                for (int dx = 0; dx < 2; ++dx)
+                                    s += g[i * Ng + ((int64_t)(2 * z + dz) * nyf + 2 * y + dy) * nxg + xg0 + dx];
+                        cw[i * Nc + ((int64_t)z * ny + y) * nx + xc] = s / 8.0;
+                    }
+        }
+#pragma omp parallel for schedule(static)
+        for (int64_t n = 0; n < Nc; ++n) {
+            if (IN_SLAB((int)(n % nx))) continue;
+            double fin[QMAX], fout[QMAX];
+            for (int i = 0; i < q; ++i) fin[i] = cw[i * Nc + n];
+            collide(&L, pc, NULL, fin, fout);
+            for (int i = 0; i < q; ++i) fc[i * Nc + n] = fout[i];
+        }
+    }
+#undef IN_SLAB
+    for (int i = 0; i < q; ++i)
+        for (int z = 0; z < nzf; ++z)
+            for (int y = 0; y < nyf; ++y)
+                for (int x = 0; x < nf; ++x)
+                    ff[i * Nf + ((int64_t)z * nyf + y) * nf + x] = g[i * Ng + ((int64_t)z * nyf + y) * nxg + x + 2];
+    free(g);
+    free(gw);
+    free(cw);
+    return 0;
+}

@@ -139,6 +139,10 @@ def _L():
         lib.orc_stream.restype = ctypes.c_int
         lib.orc_mrt_matrix.argtypes = [ctypes.c_int, dp, dp, ip]
         lib.orc_mrt_matrix.restype = ctypes.c_int
+        lib.orc_refine_fine_params.argtypes = [pp, ctypes.c_int32, ctypes.c_int32, pp]
+        lib.orc_refine_fine_params.restype = ctypes.c_int
+        lib.orc_refine_run.argtypes = [pp, ctypes.c_int32, ctypes.c_int32, dp, dp, ctypes.c_int64]
+        lib.orc_refine_run.restype = ctypes.c_int
         lib.orc_cumulants.argtypes = [pp, dp, dp, dp]
         lib.orc_cumulants.restype = ctypes.c_int
         lib.orc_cumulants_to_f.argtypes = [ctypes.c_double, dp, dp, dp]
@@ -342,3 +346,45 @@ def diagnostics(p: OracleParams, f, flags=None) -> dict:
         "kinetic_energy": float((0.5 * rho * speed2)[fl].sum()),
         "max_speed": float(np.sqrt(speed2[fl].max())) if fl.any() else 0.0,
     }
+
+
+# ---- static 2:1 refinement (see the refinement section of lbm_oracle.c) ----------------------
+
+def refine_fine_params(p: OracleParams, a: int, b: int) -> OracleParams:
+    """Parameters of the fine grid over the coarse columns [a, b): 2x the cells per axis,
+    tau_f - 1/2 = 2 (tau_c - 1/2), force / 2."""
+    cp = p.cstruct()
+    out = _CParams()
+    rc = _L().orc_refine_fine_params(ctypes.byref(cp), int(a), int(b), ctypes.byref(out))
+    if rc != 0:
+        raise ValueError("refinement not supported for these parameters: %d" % rc)
+    from dataclasses import replace
+    return replace(p, shape=(out.nx, out.ny, out.nz), omega=out.omega, force=tuple(out.force))
+
+
+def refine_slab_flags(p: OracleParams, a: int, b: int) -> np.ndarray:
+    """Coarse flag field with the refined columns [a, b) marked non-fluid."""
+    nx, ny, nz = p.shape
+    fl = np.zeros((nz, ny, nx), np.uint8)
+    x = np.arange(nx)
+    fl[..., ((x - a) % nx) < (b - a)] = NOSLIP
+    return fl
+
+
+def refine_init(p: OracleParams, a: int, b: int, rho_c, u_c, rho_f, u_f):
+    """(fc, ff): the post-collision initial states of both grids from their own fields."""
+    pf = refine_fine_params(p, a, b)
+    fc = init(p, rho_c, u_c, flags=refine_slab_flags(p, a, b))
+    ff = init(pf, rho_f, u_f)
+    return fc, ff
+
+
+def refine_run(p: OracleParams, a: int, b: int, fc, ff, nsteps: int):
+    """Advance both grids by nsteps coarse steps (returns new arrays)."""
+    fc = np.array(fc, dtype=np.float64, order="C", copy=True)
+    ff = np.array(ff, dtype=np.float64, order="C", copy=True)
+    cp = p.cstruct()
+    rc = _L().orc_refine_run(ctypes.byref(cp), int(a), int(b), _dp(fc), _dp(ff), int(nsteps))
+    if rc != 0:
+        raise RuntimeError("orc_refine_run failed: %d" % rc)
+    return fc, ff
