@@ -87,6 +87,9 @@ enum { LBM_FLUID = 0, LBM_NOSLIP = 1, LBM_VELOCITY = 2, LBM_PRESSURE = 3, LBM_PE
  * the first layer, the unknown populations entering it are rebuilt from mass and momentum before
  * each sweep).  D3Q19, two-grid pattern, dense layout; the face's two tangential axes periodic. */
 enum { LBM_ZOUHE_VELOCITY = 5, LBM_ZOUHE_PRESSURE = 6 };
+/* Face kind only: a refinement interface (lbm_refine_create); the ghost slots the sweep reads
+ * through it are written by lbm_refine_step.  Two-grid pattern, FP64/FP32, dense layout. */
+enum { LBM_REFINE = 7 };
 
 typedef struct {
     int32_t stencil;       /* LBM_D3Q19 or LBM_D3Q27 */
@@ -213,6 +216,38 @@ lbm_status lbm_halo_pack(lbm_ctx *ctx, int32_t peer, void *dev_buf);
  * Errors: as lbm_halo_pack.
  * Paper: Sec. 3.3 (PackInfo: unpacking the message into the ghost layer). */
 lbm_status lbm_halo_unpack(lbm_ctx *ctx, int32_t peer, const void *dev_buf);
+
+/* ---- static 2:1 grid refinement (Sec. 5.1.1: non-uniform grids, the mass-conserving method of
+ * Rohde et al. 2006) --------------------------------------------------------------------------
+ * A coarse context and a fine context that together fill a domain periodic in x, y and z: the
+ * coarse block covers coarse columns [0, A) and the fine block the coarse columns [A, A + W) with
+ * 2W x 2ny x 2nz fine cells (the coarse block being A x ny x nz); both have y and z periodic and
+ * both x faces of kind LBM_REFINE.  Volumetric scheme, one coarse step:
+ *   1. explosion: each fine ghost cell (two layers beyond each fine x face, inside the coarse
+ *      column beside it) holds the post-collision populations of its coarse cell;
+ *   2. two fine steps (the ghost values streaming one fine cell per step);
+ *   3. coalescence: a coarse cell beside the fine block takes, for each direction coming out of
+ *      it, the mean over its 8 fine cells of the fine populations that streamed into them
+ *      during the two fine steps; then the coarse step.
+ * No interpolation and no rescaling of non-equilibrium parts; every population that crosses
+ * the interface is counted once on each side, so sum_coarse f + (1/8) sum_fine f is conserved.
+ * Requirements (else LBM_ERR_UNSUPPORTED): same stencil, FP64 or FP32 storage, two-grid, SRT or
+ * TRT with the same Lambda, one block per context without obstacle cells, no closure, no graph
+ * mode, one stream; fine omega = 1 / (1/2 + 2 (1/omega_c - 1/2)) (the same physical viscosity
+ * under acoustic scaling) and fine force = coarse force / 2.
+ * The object keeps pointers to both contexts: destroy it before them.  Errors: LBM_ERR_ARG for
+ * null or identical contexts, LBM_ERR_OOM, LBM_ERR_CUDA. */
+typedef struct lbm_refine lbm_refine;
+lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, lbm_refine **out);
+
+/* Enqueue n coarse steps (each: explosion, fine step, coalescence, explosion, fine step,
+ * coarse step; the coalescence runs while the fine states at t and t + 1/2, whose emitted
+ * populations it averages, both exist) on the contexts' stream.  The step diagnostics of both contexts are not
+ * written (lbm_reduce gives each grid's totals).  Errors: LBM_ERR_STATE if a context's x faces
+ * changed or it took graph mode since lbm_refine_create; as lbm_step. */
+lbm_status lbm_refine_step(lbm_refine *r, int64_t n);
+
+void lbm_refine_destroy(lbm_refine *r);
 
 /* Bytes of device memory the PDF arrays need (two arrays for two-grid, one for AA),
  * including 256-byte alignment slack.

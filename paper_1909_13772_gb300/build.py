@@ -2,7 +2,7 @@
 
 Translation units: api.cu (C ABI, scheduler), plan.cpp (host list builder, OpenMP), diag.cu,
 reduce_static.cu, closure.cu (closure sweep and network kernels, D3Q19 FP32), halo.cu (halo
-pack/unpack of partitioned runs), sweep.cu / aux.cu / sweep_sparse.cu (the fluid-cell list
+pack/unpack of partitioned runs), refine.cu (transfers of the 2:1 refinement), sweep.cu / aux.cu / sweep_sparse.cu (the fluid-cell list
 sweep) compiled once per (stencil, storage) variant, sweep.cu once more per (stencil, FP64/FP32) with the MRT
 collision and per FP64/FP32 D3Q27 with the cumulant collision.  Objects are compiled in parallel; the library lands in ``paper_1909_13772_gb300/_build/liblbm.so``.
 """
@@ -42,7 +42,7 @@ def _sources():
 
 def _jobs(nvcc, extra, build_dir):
     jobs = []
-    for name in ("api.cu", "plan.cpp", "diag.cu", "reduce_static.cu", "closure.cu", "halo.cu"):
+    for name in ("api.cu", "plan.cpp", "diag.cu", "reduce_static.cu", "closure.cu", "halo.cu", "refine.cu"):
         src = os.path.join(CSRC, name)
         obj = os.path.join(build_dir, name.replace(".", "_") + ".o")
         lang = [] if name.endswith(".cu") else ["-x", "cu"]

@@ -964,8 +964,12 @@ lbm_status lbm_set_face(lbm_ctx *c, int32_t axis, int32_t side, int32_t kind, co
     if (!c) return LBM_ERR_ARG;
     if (axis < 0 || axis > 2 || side < 0 || side > 1) return fail(c, LBM_ERR_ARG, "bad face");
     if (kind != LBM_NOSLIP && kind != LBM_VELOCITY && kind != LBM_PRESSURE && kind != LBM_PERIODIC &&
-        kind != LBM_ZOUHE_VELOCITY && kind != LBM_ZOUHE_PRESSURE)
+        kind != LBM_ZOUHE_VELOCITY && kind != LBM_ZOUHE_PRESSURE && kind != LBM_REFINE)
         return fail(c, LBM_ERR_ARG, "bad face kind %d", kind);
+    if (kind == LBM_REFINE && (c->pattern != LBM_TWO_GRID || c->sparse || !c->owner.empty() ||
+                               c->closure != CLOSURE_NONE || (c->storage != LBM_FP64 && c->storage != LBM_FP32)))
+        return fail(c, LBM_ERR_UNSUPPORTED, "refinement faces are built for the two-grid pattern, FP64 or FP32 "
+                                            "storage, the dense layout of one context and no closure");
     if ((kind == LBM_ZOUHE_VELOCITY || kind == LBM_ZOUHE_PRESSURE) &&
         (c->q != 19 || c->pattern != LBM_TWO_GRID || c->sparse || !c->owner.empty() || c->closure != CLOSURE_NONE))
         return fail(c, LBM_ERR_UNSUPPORTED, "wet-node (Zou-He) faces are built for D3Q19, the two-grid pattern, the "
@@ -1053,11 +1057,13 @@ void step_args(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
             if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) sw.through = 2;
     }
     // The wrap path (1) wraps each periodic axis of a source on its own, while the fill's
-    // boundary links and the wet-node pass find a boundary cell the way the neighbour table
-    // does: a source outside a non-periodic face is the block's own ghost cell, unwrapped along
-    // the other axes.  With such boundaries the launch takes the table path, so that the sweep
-    // reads the ghost slots where they were written.
-    if (sw.through == 1 && (!P.links.empty() || !P.zouhe.empty())) sw.through = 2;
+    // boundary links, the wet-node pass and the refinement transfers find a boundary cell the
+    // way the neighbour table does: a source outside a non-periodic face is the block's own
+    // ghost cell, unwrapped along the other axes.  With such boundaries the launch takes the
+    // table path, so that the sweep reads the ghost slots where they were written.
+    bool refine = false;
+    for (int f = 0; f < 6; ++f) refine = refine || c->face_kind[f] == LBM_REFINE;
+    if (sw.through == 1 && (!P.links.empty() || !P.zouhe.empty() || refine)) sw.through = 2;
     sw.stage_bytes = c->stage_bytes;
     sw.err = c->d_sweep_err;
     sw.cd = c->cd;
@@ -1862,6 +1868,196 @@ lbm_status lbm_plan_params(lbm_ctx *c, double *out, int64_t cap, int64_t *n)
         out[4 * k + 3] = c->plan.params[k].rho;
     }
     return LBM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Static 2:1 refinement (Sec. 5.1.1, Rohde et al.): a coarse and a fine context side by side
+// along x in a domain periodic in all three axes; the transfer lists (refine.cu) are built here
+// once from the two blocks' layouts.  See include/lbm.h for the scheme.
+// ---------------------------------------------------------------------------------------
+struct lbm_refine {
+    lbm_ctx *coarse = nullptr, *fine = nullptr;
+    int64_t *d_explode = nullptr, *d_coalesce = nullptr;
+    int64_t nexplode = 0, ncoalesce = 0;
+};
+
+namespace {
+
+bool refine_faces(const lbm_ctx *c) { return c->face_kind[0] == LBM_REFINE && c->face_kind[1] == LBM_REFINE; }
+
+// The transfer entries (element offsets relative to an array's base).
+void refine_entries(const lbm_ctx *cc, const lbm_ctx *cf, std::vector<int64_t> &ex, std::vector<int64_t> &co)
+{
+    const BlockLayout &C = cc->blocks[0], &F = cf->blocks[0];
+    const LatticeView L = lattice_view(cc->q);
+    const int nxc = C.n[0], nxf = F.n[0], nyf = F.n[1], nzf = F.n[2], nyc = C.n[1], nzc = C.n[2];
+    auto wrap = [](int v, int n) { return ((v % n) + n) % n; };
+    // explosion: fine cells of the first / last column, directions entering through the face;
+    // the value comes from the coarse column holding the fine ghost cells (the coarse block's
+    // last column beside the fine x- face, its first column beside the fine x+ face)
+    for (int side = 0; side < 2; ++side) {
+        const int xf = side == 0 ? 0 : nxf - 1, sx = side == 0 ? 1 : -1, xc = side == 0 ? nxc - 1 : 0;
+        for (int z = 0; z < nzf; ++z)
+            for (int y = 0; y < nyf; ++y)
+                for (int i = 0; i < L.q; ++i) {
+                    if (L.cx[i] != sx) continue;
+                    const int cy = L.cy[i], cz = L.cz[i];
+                    ex.push_back(F.offset + (int64_t)i * F.slab + F.cell(xf - sx, y - cy, z - cz));
+                    // first fine step: the ghost one cell out; second: the one two cells out
+                    ex.push_back(C.offset + (int64_t)i * C.slab + C.cell(xc, wrap(y - cy, nyf) / 2, wrap(z - cz, nzf) / 2));
+                    ex.push_back(C.offset + (int64_t)i * C.slab +
+                                 C.cell(xc, wrap(y - 2 * cy, nyf) / 2, wrap(z - 2 * cz, nzf) / 2));
+                }
+    }
+    // coalescence: coarse cells beside the fine block, directions coming out of it; the fine
+    // cells whose populations streamed into the coarse cell's 8 fine ghost cells: into the one
+    // cell out during the second fine step (emitted at t + 1/2), into the two cells out over
+    // both steps (emitted at t)
+    for (int side = 0; side < 2; ++side) {
+        const int xc = side == 0 ? nxc - 1 : 0, sx = side == 0 ? -1 : 1, xf = side == 0 ? 0 : nxf - 1;
+        for (int Z = 0; Z < nzc; ++Z)
+            for (int Y = 0; Y < nyc; ++Y)
+                for (int i = 0; i < L.q; ++i) {
+                    if (L.cx[i] != sx) continue;
+                    const int cy = L.cy[i], cz = L.cz[i];
+                    co.push_back(C.offset + (int64_t)i * C.slab + C.cell(xc - sx, Y - cy, Z - cz));
+                    for (int half = 0; half < 2; ++half)
+                        for (int dz = 0; dz < 2; ++dz)
+                            for (int dy = 0; dy < 2; ++dy) {
+                                const int k = half + 1;
+                                co.push_back(F.offset + (int64_t)i * F.slab +
+                                             F.cell(xf, wrap(2 * Y + dy - k * cy, nyf), wrap(2 * Z + dz - k * cz, nzf)));
+                            }
+                }
+    }
+}
+
+lbm_status refine_launch(lbm_ctx *c, bool explode, RefineArgs &a)
+{
+    CK(explode ? launch_refine_explode(a) : launch_refine_coalesce(a), explode ? "explosion launch" : "coalescence launch");
+    c->launches++;
+    return LBM_OK;
+}
+
+}  // namespace
+
+lbm_status lbm_refine_create(lbm_ctx *cc, lbm_ctx *cf, lbm_refine **out)
+{
+    if (!cc || !cf || !out || cc == cf) return LBM_ERR_ARG;
+    *out = nullptr;
+    const char *why = nullptr;
+    if (cc->q != cf->q || cc->storage != cf->storage) why = "the two contexts differ in stencil or storage";
+    for (const lbm_ctx *c : {cc, cf}) {
+        if (why) break;
+        if (c->storage != LBM_FP64 && c->storage != LBM_FP32) why = "FP64 or FP32 storage";
+        else if (c->pattern != LBM_TWO_GRID) why = "the two-grid pattern";
+        else if (c->p.collision != LBM_SRT && c->p.collision != LBM_TRT) why = "SRT or TRT";
+        else if (c->blocks.size() != 1 || !c->owner.empty() || c->sparse || c->closure != CLOSURE_NONE)
+            why = "one block per context, the dense layout, no closure";
+        else if (c->p.periodic[0] || !c->p.periodic[1] || !c->p.periodic[2] || !refine_faces(c))
+            why = "x faces of kind LBM_REFINE, y and z periodic";
+        else if (!c->flags[0].empty()) why = "no obstacle cells";
+        else if (c->graph_mode) why = "no graph mode";
+    }
+    if (!why && (cc->p.collision != cf->p.collision ||
+                 (cc->p.collision == LBM_TRT && cc->p.magic_lambda != cf->p.magic_lambda)))
+        why = "the same collision (and Lambda) on both grids";
+    if (!why && cc->stream != cf->stream) why = "one stream for both contexts";
+    if (!why) {
+        const BlockLayout &C = cc->blocks[0], &F = cf->blocks[0];
+        if (F.n[0] % 2 != 0 || F.n[1] != 2 * C.n[1] || F.n[2] != 2 * C.n[2])
+            why = "the fine block must be 2W x 2ny x 2nz for a coarse block of ny x nz";
+    }
+    if (!why) {
+        // acoustic scaling: the same physical viscosity and body force on both grids
+        const double wf = cc->p.omega > 0.0 ? 1.0 / (0.5 + 2.0 * (1.0 / cc->p.omega - 0.5)) : -1.0;
+        if (!(std::fabs(cf->p.omega - wf) <= 1e-12 * wf)) why = "fine omega = 1 / (1/2 + 2 (1/omega_c - 1/2))";
+        for (int a = 0; a < 3 && !why; ++a)
+            if (cf->p.force[a] != 0.5 * cc->p.force[a]) why = "fine force = coarse force / 2";
+    }
+    if (why) return fail(cc, LBM_ERR_UNSUPPORTED, "refinement: %s", why);
+    lbm_status s;
+    if ((s = prepare(cc)) != LBM_OK) return s;
+    if ((s = prepare(cf)) != LBM_OK) return s;
+    std::vector<int64_t> ex, co;
+    refine_entries(cc, cf, ex, co);
+    lbm_refine *r = new (std::nothrow) lbm_refine();
+    if (!r) return LBM_ERR_OOM;
+    r->coarse = cc;
+    r->fine = cf;
+    r->nexplode = (int64_t)ex.size() / 3;
+    r->ncoalesce = (int64_t)co.size() / 9;
+    lbm_ctx *c = cc;
+    cudaError_t e = cudaMalloc(&r->d_explode, ex.size() * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&r->d_coalesce, co.size() * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_explode, ex.data(), ex.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(r->d_coalesce, co.data(), co.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(r->d_explode);
+        cudaFree(r->d_coalesce);
+        delete r;
+        return cuda_fail(c, e, "refinement lists");
+    }
+    *out = r;
+    return LBM_OK;
+}
+
+lbm_status lbm_refine_step(lbm_refine *r, int64_t n)
+{
+    if (!r) return LBM_ERR_ARG;
+    lbm_ctx *cc = r->coarse, *cf = r->fine;
+    if (n < 0) return fail(cc, LBM_ERR_ARG, "negative step count");
+    if (!refine_faces(cc) || !refine_faces(cf) || cc->graph_mode || cf->graph_mode)
+        return fail(cc, LBM_ERR_STATE, "refinement: a context changed its x faces or took graph mode");
+    lbm_status s;
+    if ((s = prepare(cc)) != LBM_OK) return s;
+    if ((s = prepare(cf)) != LBM_OK) return s;
+    SweepArgs swc, swf;
+    FillArgs fac, faf;
+    step_args(cc, swc, fac);
+    step_args(cf, swf, faf);
+    RefineArgs a{};
+    a.elem_bytes = cc->bpp;
+    a.stream = cc->stream;
+    for (int64_t t = 0; t < n; ++t) {
+        // two fine steps, each after the explosion into the ghost slots it reads
+        for (int sub = 1; sub <= 2; ++sub) {
+            a.dst = cf->arr[cf->cur];
+            a.src = cc->arr[cc->cur];
+            a.src2 = nullptr;
+            a.ent = r->d_explode;
+            a.n = r->nexplode;
+            a.sub = sub;
+            if ((s = refine_launch(cf, true, a)) != LBM_OK) return s;
+            if ((s = issue_step(cf, swf, faf, false, cf->timing)) != LBM_OK) return s;
+            cf->steps_done++;
+            if (sub == 1) {
+                // coalescence into the coarse ghost slots while both fine states it needs exist:
+                // the populations the fine cells emit at the start of each fine step, f*(t)
+                // (still in the first step's source array) and f*(t + 1/2) (its result)
+                a.dst = cc->arr[cc->cur];
+                a.src = cf->arr[cf->cur];
+                a.src2 = cf->arr[1 - cf->cur];
+                a.ent = r->d_coalesce;
+                a.n = r->ncoalesce;
+                if ((s = refine_launch(cc, false, a)) != LBM_OK) return s;
+            }
+        }
+        // the coarse step
+        if ((s = issue_step(cc, swc, fac, false, cc->timing)) != LBM_OK) return s;
+        cc->steps_done++;
+    }
+    cc->step_diag_valid = cf->step_diag_valid = false;
+    return LBM_OK;
+}
+
+void lbm_refine_destroy(lbm_refine *r)
+{
+    if (!r) return;
+    if (r->coarse) cudaStreamSynchronize(r->coarse->stream);
+    cudaFree(r->d_explode);
+    cudaFree(r->d_coalesce);
+    delete r;
 }
 
 const char *lbm_last_error(const lbm_ctx *c)

@@ -184,4 +184,21 @@ cudaError_t launch_sweep_mrt_27_1(const SweepArgs &s);
 cudaError_t launch_sweep_cum_27_0(const SweepArgs &s);
 cudaError_t launch_sweep_cum_27_1(const SweepArgs &s);
 
+// Static 2:1 refinement coupling of a coarse and a fine context (refine.cu), FP64 or FP32
+// storage (elem_bytes 8 or 4).  Offsets are elements relative to the arrays' bases.
+//   explode:  dst[e[3k]] = src[e[3k + sub]]            (sub 1 or 2; src the coarse state)
+//   coalesce: dst[e[9k]] = (sum_{j=1..4} src[e[9k + j]] + sum_{j=5..8} src2[e[9k + j]]) / 8
+//             (src the fine state after the first of the two fine steps, src2 the one before it)
+struct RefineArgs {
+    void *dst;
+    const void *src, *src2;
+    const int64_t *ent;
+    int64_t n;
+    int elem_bytes;
+    int sub;
+    cudaStream_t stream;
+};
+cudaError_t launch_refine_explode(const RefineArgs &a);
+cudaError_t launch_refine_coalesce(const RefineArgs &a);
+
 }  // namespace lbm

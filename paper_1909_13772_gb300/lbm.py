@@ -18,6 +18,7 @@ FP64, FP32, BF16_DEV, FP16_DEV = 0, 1, 2, 3
 TWO_GRID, AA = 0, 1
 FLUID, NOSLIP, VELOCITY, PRESSURE, PERIODIC = 0, 1, 2, 3, 4
 ZOUHE_VELOCITY, ZOUHE_PRESSURE = 5, 6  # face kinds only: wet-node (Zou-He) faces
+REFINE = 7  # face kind only: a refinement interface (lbm_refine_create)
 
 STATUS = {0: "LBM_OK", 1: "LBM_ERR_ARG", 2: "LBM_ERR_STATE", 3: "LBM_ERR_CUDA", 4: "LBM_ERR_OOM",
           5: "LBM_ERR_DIVERGED", 6: "LBM_ERR_TIMEOUT", 7: "LBM_ERR_UNSUPPORTED"}
@@ -111,6 +112,9 @@ _SIGS = {
     "lbm_mlp_destroy": ([_vp], None),
     "lbm_last_error": ([_vp], ctypes.c_char_p),
     "lbm_destroy": ([_vp], None),
+    "lbm_refine_create": ([_vp, _vp, _P(_vp)], ctypes.c_int),
+    "lbm_refine_step": ([_vp, ctypes.c_int64], ctypes.c_int),
+    "lbm_refine_destroy": ([_vp], None),
 }
 
 
@@ -221,6 +225,22 @@ def lbm_halo_pack(ctx, peer, dev_ptr: int):
 
 def lbm_halo_unpack(ctx, peer, dev_ptr: int):
     _check(ctx, load_library().lbm_halo_unpack(ctx, int(peer), ctypes.c_void_p(dev_ptr)))
+
+
+def lbm_refine_create(coarse_ctx, fine_ctx):
+    """Coupling of a coarse and a fine context (static 2:1 refinement); errors reported on the
+    coarse context."""
+    r = _vp()
+    _check(coarse_ctx, load_library().lbm_refine_create(coarse_ctx, fine_ctx, ctypes.byref(r)))
+    return r
+
+
+def lbm_refine_step(r, n, coarse_ctx=None):
+    _check(coarse_ctx, load_library().lbm_refine_step(r, int(n)))
+
+
+def lbm_refine_destroy(r):
+    load_library().lbm_refine_destroy(r)
 
 
 def lbm_plan_halo(ctx, peer, which) -> np.ndarray:

@@ -1,0 +1,146 @@
+"""GPU parity of the static 2:1 refinement (lbm_refine_*) against the oracle's (the volumetric,
+mass-conserving scheme: explosion into a two-deep fine ghost layer, two fine steps, coalescence
+of the fine populations that left the fine grid), with the fine block over the last coarse
+columns [A, nx) of a periodic box.  The oracle works on the global coarse box with a push
+stream through explicit ghost cells; the library couples two contexts by per-slot transfer
+lists into the ghost slots their pull sweeps read.  Gates: 1e-12 (FP64) and 1e-5 (FP32)
+normwise on both grids' PDFs; conservation of the volume-weighted mass."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import TOL, normwise
+from paper_1909_13772_gb300 import lbm, refine
+
+pytestmark = pytest.mark.gpu
+ERR_UNSUPPORTED = 7
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lbm.load_library()
+
+
+def _fields(shape_c, shape_f, seed, u_amp=0.03):
+    rng = np.random.default_rng(seed)
+    (nx, ny, nz), (nf, nyf, nzf) = shape_c, shape_f
+    return (1 + 0.01 * rng.standard_normal((nz, ny, nx)), u_amp * rng.standard_normal((3, nz, ny, nx)),
+            1 + 0.01 * rng.standard_normal((nzf, nyf, nf)), u_amp * rng.standard_normal((3, nzf, nyf, nf)))
+
+
+def _both(q, coll, storage, tau, shape, a, steps, seed, force=(0.0, 0.0, 0.0)):
+    nx, ny, nz = shape
+    p = oracle.OracleParams(shape=shape, q=q, collision=coll, omega=1 / tau, periodic=(1, 1, 1), force=force)
+    pf = oracle.refine_fine_params(p, a, nx)
+    rc, uc, rf, uf = _fields(shape, pf.shape, seed)
+    # the oracle's coarse fields cover the whole box; the refined columns are ignored
+    fc, ff = oracle.refine_init(p, a, nx, rc, uc, rf, uf)
+    fc, ff = oracle.refine_run(p, a, nx, fc, ff, steps)
+    params = lbm.make_params(stencil=q, collision=coll, storage=storage, omega=1 / tau, force=force)
+    run = refine.RefinedRun(params, shape, a)
+    try:
+        run.init(rc[..., :a], uc[..., :a], rf, uf)
+        run.step(steps)
+        gc, gf = run.coarse.pdfs(0), run.fine.pdfs(0)
+    finally:
+        run.close()
+    return gc, fc[..., :a], gf, ff
+
+
+@pytest.mark.parametrize("storage", [lbm.FP64, lbm.FP32])
+@pytest.mark.parametrize("q,coll", [(19, lbm.TRT), (27, lbm.SRT)])
+def test_random_state_against_the_oracle(storage, q, coll):
+    gc, wc, gf, wf = _both(q, coll, storage, 0.7, (20, 6, 4), 12, 15, seed=3, force=(1e-5, -2e-6, 0.0))
+    assert normwise(gc, wc) <= TOL[storage]
+    assert normwise(gf, wf) <= TOL[storage]
+
+
+def test_long_run_fp64_d3q27_trt():
+    gc, wc, gf, wf = _both(27, lbm.TRT, lbm.FP64, 0.56, (24, 4, 6), 16, 120, seed=5)
+    assert normwise(gc, wc) <= TOL[lbm.FP64]
+    assert normwise(gf, wf) <= TOL[lbm.FP64]
+
+
+def test_volume_weighted_mass_is_conserved_and_momentum_grows_by_F():
+    shape, a, F = (32, 8, 8), 20, (2e-5, 0.0, -1e-5)
+    params = lbm.make_params(stencil=19, collision=lbm.TRT, storage=lbm.FP64, omega=1 / 0.8, force=F)
+    run = refine.RefinedRun(params, shape, a)
+    try:
+        rc, uc, rf, uf = _fields((a, 8, 8), (2 * (32 - a), 16, 16), seed=7)
+        run.init(rc, uc, rf, uf)
+        d0 = run.reduce()
+        steps = 100
+        run.step(steps)
+        d1 = run.reduce()
+    finally:
+        run.close()
+    assert abs(d1["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    vol = 32 * 8 * 8
+    for k in range(3):
+        assert abs(d1["momentum"][k] - d0["momentum"][k] - steps * vol * F[k]) <= 1e-12 * d0["mass"]
+
+
+def test_shear_wave_decays_at_the_viscous_rate():
+    """u_y = A sin(2 pi x / nx) across both interfaces, FP64: amplitude decay at nu k^2 (the
+    oracle gives 4e-4 for this set-up; an FP32 run's rounding at A = 1e-3 alone moves the
+    fitted rate by a few 1e-3, so the physics check runs in FP64)."""
+    nx, a, tau = 48, 24, 0.6
+    params = lbm.make_params(stencil=19, collision=lbm.TRT, storage=lbm.FP64, omega=1 / tau)
+    run = refine.RefinedRun(params, (nx, 2, 2), a)
+    try:
+        k, A = 2 * math.pi / nx, 1e-3
+        xc = np.arange(a) + 0.5
+        nf = 2 * (nx - a)
+        xf = a + (np.arange(nf) + 0.5) / 2
+        uc = np.zeros((3, 2, 2, a))
+        uc[1] = A * np.sin(k * xc)
+        uf = np.zeros((3, 4, 4, nf))
+        uf[1] = A * np.sin(k * xf)
+        run.init(np.ones((2, 2, a)), uc, np.ones((4, 4, nf)), uf)
+
+        def amp():
+            _, vc = run.coarse.macroscopic(0)
+            _, vf = run.fine.macroscopic(0)
+            num = (vc[1].mean(axis=(0, 1)) * np.sin(k * xc)).sum() + 0.5 * (vf[1].mean(axis=(0, 1)) * np.sin(k * xf)).sum()
+            return num / ((np.sin(k * xc) ** 2).sum() + 0.5 * (np.sin(k * xf) ** 2).sum())
+
+        run.step(200)
+        a1 = amp()
+        run.step(400)
+        a2 = amp()
+    finally:
+        run.close()
+    rate = math.log(a1 / a2) / 400
+    nu = (tau - 0.5) / 3
+    assert abs(rate / (nu * k * k) - 1.0) < 3e-3
+
+
+def test_unsupported_set_ups_are_refused():
+    # AA pattern: the refinement face itself is refused
+    p = lbm.make_params(stencil=19, storage=lbm.FP32, pattern=lbm.AA, periodic=(0, 1, 1))
+    sim = lbm.Simulation(p, [((0, 0, 0), (8, 4, 4))])
+    try:
+        with pytest.raises(lbm.LbmError) as e:
+            sim.set_face(0, 0, lbm.REFINE)
+        assert e.value.status == ERR_UNSUPPORTED
+    finally:
+        sim.close()
+    # a fine grid with the coarse grid's rate (not the acoustically scaled one)
+    pc = lbm.make_params(stencil=19, storage=lbm.FP32, omega=1.2, periodic=(0, 1, 1))
+    c = lbm.Simulation(pc, [((0, 0, 0), (8, 4, 4))])
+    f = lbm.Simulation(pc, [((0, 0, 0), (8, 8, 8))])
+    try:
+        for s in (c, f):
+            s.set_face(0, 0, lbm.REFINE)
+            s.set_face(0, 1, lbm.REFINE)
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_refine_create(c.ctx, f.ctx)
+        assert e.value.status == ERR_UNSUPPORTED
+    finally:
+        f.close()
+        c.close()
