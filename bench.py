@@ -990,6 +990,95 @@ def cpu_baseline_closure(net, min_seconds=10.0, n=32):
 
 
 
+def cpu_baseline_refine(min_seconds=5.0):
+    """The oracle's refined run on a 48 x 8 x 8 coarse box with its last 16 columns refined."""
+    import oracle
+    from paper_1909_13772_gb300 import inputs
+    shape, a = (48, 8, 8), 32
+    p = oracle.OracleParams(shape=shape, q=19, collision=oracle.TRT, omega=1 / 0.6, magic_lambda=LAMBDA,
+                            periodic=(1, 1, 1))
+    pf = oracle.refine_fine_params(p, a, shape[0])
+    rc, uc = inputs.random_state(shape, seed=61, rho_amp=0.01, u_amp=0.02)
+    rf, uf = inputs.random_state(pf.shape, seed=62, rho_amp=0.01, u_amp=0.02)
+    fc, ff = oracle.refine_init(p, a, shape[0], rc, uc, rf, uf)
+    fc, ff = oracle.refine_run(p, a, shape[0], fc, ff, 1)
+    steps, t = 0, 0.0
+    while steps == 0 or t < min_seconds:
+        t0 = time.perf_counter()
+        fc, ff = oracle.refine_run(p, a, shape[0], fc, ff, 1)
+        t += time.perf_counter() - t0
+        steps += 1
+    ups = a * 64 + 2 * int(np.prod(pf.shape))  # cell updates per coarse step
+    return {"value": round(ups * steps / t / 1e6, 3), "unit": "MLUPS", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": "%d coarse steps of a 48x8x8 coarse box with its last 16 columns refined 2:1 (FP64, D3Q19 TRT)"
+                      % steps}
+
+
+def measure_refine(args):
+    """Static 2:1 refinement: a periodic 256 x 128 x 128 coarse box (D3Q19 TRT tau_c = 0.6, FP32,
+    two-grid) whose last 64 columns are refined (fine block 128 x 256 x 256, two fine steps per
+    coarse step), started from a seeded random state on both grids.  Value: cell updates per
+    second (coarse updates + two per fine cell and coarse step)."""
+    import torch
+    rank, world, local = dist_setup()
+    from paper_1909_13772_gb300 import inputs, lbm, refine
+    lbm.load_library()
+    shape, a = (256, 128, 128), 192
+    nx, ny, nz = shape
+    stream = torch.cuda.Stream()
+    params = lbm.make_params(stencil=19, collision=lbm.TRT, storage=lbm.FP32, omega=1 / 0.6, magic_lambda=LAMBDA)
+    run = refine.RefinedRun(params, shape, a, stream=stream.cuda_stream)
+    try:
+        rc, uc = inputs.random_state((a, ny, nz), seed=61, rho_amp=0.01, u_amp=0.02)
+        rf, uf = inputs.random_state((2 * (nx - a), 2 * ny, 2 * nz), seed=62, rho_amp=0.01, u_amp=0.02)
+        run.init(rc, uc, rf, uf)
+        run.step(args.warmup)
+        torch.cuda.synchronize()
+        d0 = run.reduce()
+        for s in (run.coarse, run.fine):
+            lbm.lbm_read_timing(s.ctx, reset=True)
+            lbm.lbm_enable_timing(s.ctx, True)
+        launches0 = run.coarse.launches() + run.fine.launches()
+        sampler = ClockSampler(torch.cuda.current_device())
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(stream)
+        run.step(args.steps)
+        end.record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop()
+        ms = start.elapsed_time(end) / args.steps
+        launches = run.coarse.launches() + run.fine.launches() - launches0
+        kt = [lbm.lbm_read_timing(s.ctx, reset=True) for s in (run.coarse, run.fine)]
+        for s in (run.coarse, run.fine):
+            lbm.lbm_enable_timing(s.ctx, False)
+        d1 = run.reduce()
+    finally:
+        run.close()
+    nc, nf = a * ny * nz, 2 * (nx - a) * 4 * ny * nz
+    ups = nc + 2 * nf
+    sweep_ms = (kt[0]["sweep"][0] + kt[1]["sweep"][0]) / args.steps
+    alg = 2 * 19 * 4 * ups  # PDF bytes of the sweeps per coarse step
+    peak, peak_kind = measured_peaks()
+    gbs = alg / (sweep_ms / 1e3) / 1e9
+    return {"metric": "MLUPS of the 2:1 refined step (coarse and fine cell updates per second)",
+            "value": round(ups / (ms / 1e3) / 1e6, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random state on both grids)",
+            "config": {"workload": "static 2:1 refinement, periodic 256x128x128 coarse box, last 64 columns "
+                                   "refined (fine 128x256x256), D3Q19 TRT tau_c = 0.6, FP32 two-grid",
+                       "coarse_cells": nc, "fine_cells": nf, "updates_per_coarse_step": ups},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "traffic": None,
+                         "kernel": "k_sweep of both grids (3 launches per coarse step)",
+                         "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind},
+            "sweep_share_of_step": round(sweep_ms / ms, 4),
+            "transfers_ms_per_step": round(ms - sweep_ms, 4),
+            "mass_drift": d1["mass"] / d0["mass"] - 1.0,
+            "gpu_launches": launches, "clocks": clocks,
+            "cpu_baseline": cpu_baseline_refine() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None}
+
+
 def _print_rank0(out):
     if int(os.environ.get("RANK", "0")) == 0:
         print(json.dumps(out), flush=True)
@@ -1009,6 +1098,10 @@ def run_turbulence(args):
 
 def run_closure(args):
     _print_rank0(measure_closure(args))
+
+
+def run_refine(args):
+    _print_rank0(measure_refine(args))
 
 
 def measure_workloads(args):
@@ -1042,6 +1135,7 @@ def measure_workloads(args):
                                                     no_cpu_baseline=True, variant="fp32-twogrid", sparse=False)),
         ("c5_closure", measure_closure, sub(steps=min(max(k, 20), 100), closure_sizes="128",
                                             closure_kinds="trt,smagorinsky,mlp", cpu_seconds=5.0)),
+        ("refinement", measure_refine, sub(steps=min(max(k, 20), 100))),
     ]
     for name, fn, a in jobs:
         t0 = time.perf_counter()
@@ -1101,11 +1195,13 @@ def main(argv=None):
     ap.add_argument("--per-block", action="store_true", help="porous: one sweep launch per block (comparison)")
     ap.add_argument("--ghost", action="store_true", help="porous: ghost-layer copies instead of in-place neighbours")
     ap.add_argument("--sparse", action="store_true", help="porous: the fluid-cell list layout of the two-grid sweep")
-    ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure", "tgv"], default="channel",
+    ap.add_argument("--workload", choices=["channel", "porous", "turbulence", "closure", "tgv", "refine"],
+                    default="channel",
                     help="channel: the 256^3 benchmark (default); porous: the 4096-block porous bed; "
                          "tgv: the 32^3 Taylor-Green correctness configuration; "
                          "turbulence: D3Q27 decaying turbulence, storage variants and their errors; "
-                         "closure: constant rate vs Smagorinsky vs the learned closure")
+                         "closure: constant rate vs Smagorinsky vs the learned closure; "
+                         "refine: the static 2:1 refined box")
     ap.add_argument("--porous-blocks", type=int, default=16, help="porous: blocks per axis (16: 4096 blocks)")
     ap.add_argument("--closure-sizes", default="128,256", help="closure: box sizes; the first is the value's")
     ap.add_argument("--closure-kinds", default="trt,smagorinsky,mlp", help="closure: which steps to time")
@@ -1132,6 +1228,8 @@ def main(argv=None):
         run_closure(args)
     elif args.workload == "tgv":
         run_tgv(args)
+    elif args.workload == "refine":
+        run_refine(args)
     else:
         run_ours(args)
 
