@@ -242,7 +242,9 @@ lbm_status lbm_refine_create(lbm_ctx *coarse, lbm_ctx *fine, lbm_refine **out);
 
 /* Enqueue n coarse steps (each: explosion, fine step, coalescence, explosion, fine step,
  * coarse step; the coalescence runs while the fine states at t and t + 1/2, whose emitted
- * populations it averages, both exist) on the contexts' stream.  The step diagnostics of both contexts are not
+ * populations it averages, both exist) on the contexts' stream.  On a stream other than the
+ * legacy default stream, and with tracing off, each coarse step is replayed as a CUDA graph
+ * captured once per array parity (its six launches with no host work in between).  The step diagnostics of both contexts are not
  * written (lbm_reduce gives each grid's totals).  Errors: LBM_ERR_STATE if a context's x faces
  * changed or it took graph mode since lbm_refine_create; as lbm_step. */
 lbm_status lbm_refine_step(lbm_refine *r, int64_t n);

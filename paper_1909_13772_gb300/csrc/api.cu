@@ -1879,6 +1879,12 @@ struct lbm_refine {
     lbm_ctx *coarse = nullptr, *fine = nullptr;
     int64_t *d_explode = nullptr, *d_coalesce = nullptr;
     int64_t nexplode = 0, ncoalesce = 0;
+    // CUDA-graph replay of one coarse step, one graph per (coarse, fine) array parity; valid
+    // while both contexts' device lists and arrays are those it captured
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    int64_t graph_epoch[4][2] = {};
+    void *graph_arr[4][4] = {};
+    int64_t graph_launches[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -2002,6 +2008,44 @@ lbm_status lbm_refine_create(lbm_ctx *cc, lbm_ctx *cf, lbm_refine **out)
     return LBM_OK;
 }
 
+namespace {
+
+// One coarse step of the refined pair, enqueued on the contexts' stream.
+lbm_status refine_one(lbm_refine *r, SweepArgs &swc, FillArgs &fac, SweepArgs &swf, FillArgs &faf)
+{
+    lbm_ctx *cc = r->coarse, *cf = r->fine;
+    lbm_status s;
+    RefineArgs a{};
+    a.elem_bytes = cc->bpp;
+    a.stream = cc->stream;
+    // two fine steps, each after the explosion into the ghost slots it reads
+    for (int sub = 1; sub <= 2; ++sub) {
+        a.dst = cf->arr[cf->cur];
+        a.src = cc->arr[cc->cur];
+        a.src2 = nullptr;
+        a.ent = r->d_explode;
+        a.n = r->nexplode;
+        a.sub = sub;
+        if ((s = refine_launch(cf, true, a)) != LBM_OK) return s;
+        if ((s = issue_step(cf, swf, faf, false, cf->timing)) != LBM_OK) return s;
+        if (sub == 1) {
+            // coalescence into the coarse ghost slots while both fine states it needs exist:
+            // the populations the fine cells emit at the start of each fine step, f*(t)
+            // (still in the first step's source array) and f*(t + 1/2) (its result)
+            a.dst = cc->arr[cc->cur];
+            a.src = cf->arr[cf->cur];
+            a.src2 = cf->arr[1 - cf->cur];
+            a.ent = r->d_coalesce;
+            a.n = r->ncoalesce;
+            if ((s = refine_launch(cc, false, a)) != LBM_OK) return s;
+        }
+    }
+    // the coarse step
+    return issue_step(cc, swc, fac, false, cc->timing);
+}
+
+}  // namespace
+
 lbm_status lbm_refine_step(lbm_refine *r, int64_t n)
 {
     if (!r) return LBM_ERR_ARG;
@@ -2016,35 +2060,52 @@ lbm_status lbm_refine_step(lbm_refine *r, int64_t n)
     FillArgs fac, faf;
     step_args(cc, swc, fac);
     step_args(cf, swf, faf);
-    RefineArgs a{};
-    a.elem_bytes = cc->bpp;
-    a.stream = cc->stream;
+    // graph replay needs a stream that can be captured; traced steps run one launch at a time
+    const bool graphs = cc->stream != nullptr && !cc->timing && !cf->timing;
     for (int64_t t = 0; t < n; ++t) {
-        // two fine steps, each after the explosion into the ghost slots it reads
-        for (int sub = 1; sub <= 2; ++sub) {
-            a.dst = cf->arr[cf->cur];
-            a.src = cc->arr[cc->cur];
-            a.src2 = nullptr;
-            a.ent = r->d_explode;
-            a.n = r->nexplode;
-            a.sub = sub;
-            if ((s = refine_launch(cf, true, a)) != LBM_OK) return s;
-            if ((s = issue_step(cf, swf, faf, false, cf->timing)) != LBM_OK) return s;
-            cf->steps_done++;
-            if (sub == 1) {
-                // coalescence into the coarse ghost slots while both fine states it needs exist:
-                // the populations the fine cells emit at the start of each fine step, f*(t)
-                // (still in the first step's source array) and f*(t + 1/2) (its result)
-                a.dst = cc->arr[cc->cur];
-                a.src = cf->arr[cf->cur];
-                a.src2 = cf->arr[1 - cf->cur];
-                a.ent = r->d_coalesce;
-                a.n = r->ncoalesce;
-                if ((s = refine_launch(cc, false, a)) != LBM_OK) return s;
+        if (!graphs) {
+            if ((s = refine_one(r, swc, fac, swf, faf)) != LBM_OK) return s;
+        } else {
+            const int k = 2 * cc->cur + cf->cur;
+            void *arrs[4] = {cc->arr[0], cc->arr[1], cf->arr[0], cf->arr[1]};
+            bool stale = !r->graph[k] || r->graph_epoch[k][0] != cc->list_epoch || r->graph_epoch[k][1] != cf->list_epoch;
+            for (int j = 0; j < 4 && !stale; ++j) stale = r->graph_arr[k][j] != arrs[j];
+            if (stale) {
+                if (r->graph[k]) cudaGraphExecDestroy(r->graph[k]);
+                r->graph[k] = nullptr;
+                const int64_t lc = cc->launches, lf = cf->launches;
+                const int curc = cc->cur, curf = cf->cur;
+                lbm_ctx *c = cc;
+                CK(cudaStreamBeginCapture(cc->stream, cudaStreamCaptureModeThreadLocal), "begin refinement capture");
+                lbm_status s1 = refine_one(r, swc, fac, swf, faf);
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamEndCapture(cc->stream, &g);
+                r->graph_launches[k] = (cc->launches - lc) + (cf->launches - lf);
+                cc->launches = lc;  // captured, not yet run
+                cf->launches = lf;
+                cc->cur = curc;
+                cf->cur = curf;
+                if (s1 != LBM_OK) {
+                    if (g) cudaGraphDestroy(g);
+                    return s1;
+                }
+                if (e != cudaSuccess) return cuda_fail(c, e, "end refinement capture");
+                e = cudaGraphInstantiate(&r->graph[k], g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return cuda_fail(c, e, "instantiate refinement graph");
+                r->graph_epoch[k][0] = cc->list_epoch;
+                r->graph_epoch[k][1] = cf->list_epoch;
+                for (int j = 0; j < 4; ++j) r->graph_arr[k][j] = arrs[j];
             }
+            {
+                lbm_ctx *c = cc;
+                CK(cudaGraphLaunch(r->graph[k], cc->stream), "refinement graph launch");
+            }
+            // what the graph did: two fine steps (its arrays back where they were), one coarse
+            cc->cur = 1 - cc->cur;
+            cc->launches += r->graph_launches[k];
         }
-        // the coarse step
-        if ((s = issue_step(cc, swc, fac, false, cc->timing)) != LBM_OK) return s;
+        cf->steps_done += 2;
         cc->steps_done++;
     }
     cc->step_diag_valid = cf->step_diag_valid = false;
@@ -2055,6 +2116,8 @@ void lbm_refine_destroy(lbm_refine *r)
 {
     if (!r) return;
     if (r->coarse) cudaStreamSynchronize(r->coarse->stream);
+    for (cudaGraphExec_t &g : r->graph)
+        if (g) cudaGraphExecDestroy(g);
     cudaFree(r->d_explode);
     cudaFree(r->d_coalesce);
     delete r;
