@@ -319,13 +319,34 @@ size_t stage_tiles(const lbm_ctx *c, const Plan &P, DevTile *tiles, int64_t *cou
                     if (P.nbr[b][r] >= 0 && P.nbr[b][r] != (int)b) ok = false;
             ok_block[b] = ok;
         }
+        auto staged = [&](size_t i) {
+            const Tile &t = P.tiles[i];
+            const int nx = c->blocks[t.block].n[0];
+            return ok_block[t.block] && !(t.flags & 1) && t.x0 == 0 && t.width_m1 + 1 == nx;
+        };
         for (size_t i = 0; i < P.tiles.size(); ++i) {
             const Tile &t = P.tiles[i];
             const int nx = c->blocks[t.block].n[0];
-            if (!ok_block[t.block] || (t.flags & 1) || t.x0 != 0 || t.width_m1 + 1 != nx) continue;
+            if (!staged(i)) continue;
             ++n;
             if (tiles) tiles[i].flags |= 2;
-            const size_t rows = (size_t)threads / nx;
+            size_t rows = (size_t)threads / nx;
+#if LBM_STAGED_TWO
+            // one-row tiles in pairs (rows y0, y0 + 1 of the same block and z range, y0 even):
+            // the first sweeps both rows with two cells per thread, the second is skipped
+            if (rows == 1 && t.y0 % 2 == 0 && i + 1 < P.tiles.size() && staged(i + 1)) {
+                const Tile &u = P.tiles[i + 1];
+                if (u.block == t.block && u.z0 == t.z0 && u.y0 == t.y0 + 1) {
+                    if (tiles) {
+                        tiles[i].flags |= 4;
+                        tiles[i + 1].flags |= 2 | 8;
+                    }
+                    ++n;
+                    ++i;
+                    rows = 2;
+                }
+            }
+#endif
             bytes = std::max(bytes, kSweepStages * ((size_t)c->q * rows * (nx + 16) * c->bpp + 16));
         }
     }

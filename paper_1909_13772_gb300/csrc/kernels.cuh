@@ -54,7 +54,9 @@ __device__ __forceinline__ int64_t resolve(const DevBlock *__restrict__ blocks, 
 struct DevTile {
     int32_t block;
     int16_t x0, y0, z0;
-    uint8_t flags;     // bit 0: some cell of the tile has a non-zero mask; bit 1: rows staged by bulk copies
+    uint8_t flags;     // bit 0: some cell of the tile has a non-zero mask; bit 1: rows staged by bulk
+                       // copies; bit 2: staged, two cells per thread over this row and the next
+                       // tile's; bit 3: staged, the row is swept by the tile before
     uint8_t width_m1;  // tile width in cells - 1 (threads per CTA / width = tile height)
 };
 

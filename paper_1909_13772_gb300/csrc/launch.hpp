@@ -16,6 +16,10 @@ enum Layout { LAYOUT_PULL = 0, LAYOUT_AA_E = 1, LAYOUT_AA_O = 2 };
 // Shared-memory buffers (one z step of source rows each) of a staged sweep tile; the sweep and
 // the host's shared-memory size both take it from here
 constexpr int kSweepStages = 2;
+// staged 16-bit tiles: two x-adjacent cells per thread over pairs of one-row tiles
+#ifndef LBM_STAGED_TWO
+#define LBM_STAGED_TWO 1
+#endif
 
 struct SweepArgs {
     void *a;  // two-grid source / AA array
