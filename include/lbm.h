@@ -328,14 +328,36 @@ lbm_status lbm_set_pdfs(lbm_ctx *ctx, int32_t block, const double *f);
 lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
 
 /* Diagnostics of the state produced by the most recent lbm_step, computed inside that
- * step's last sweep from the values it was writing (no extra pass over the state): per-cell
- * and per-warp sums in the sweep's arithmetic type (FP32 for FP32 and 16-bit storage, FP64 for
- * FP64), FP64 across warps and tiles, fixed order.  Cheap enough to read after every step;
- * lbm_reduce is the full-FP64 pass over the stored values.  Synchronises the stream.
+ * step's last sweep from the values it was writing (no extra pass over the state): per-cell,
+ * per-thread and per-CTA sums in the sweep's arithmetic type (FP64 for FP64 storage; FP32 for
+ * FP32 and 16-bit storage, with the mass an exact float-float sum of the stored values per cell
+ * and float-float across cells, momentum and energy compensated per thread), FP64 across CTAs,
+ * fixed order.  FP32 bounds against the FP64 pass (u = 2^-24): mass (Q^2 + 6 Q) u^2 relative,
+ * momentum 20 u mass + 9 u sum |rho u|.  Cheap enough to read after every step; lbm_reduce is
+ * the full-FP64 pass over the stored values.  Synchronises the stream.
  * Errors: LBM_ERR_STATE when the state was set (init, set_pdfs) after the last step.
  * Paper: Eq. 1 (moments), summed over the domain inside the Sec. 5.1.2 sweep; no counterpart in
  * the paper. */
 lbm_status lbm_step_diagnostics(lbm_ctx *ctx, lbm_diagnostics *out);
+
+/* The same record read without synchronising the stream, so that a caller who reads every
+ * step's diagnostics keeps the GPU busy (step k, post k, take k-1: step k+1 runs while the host
+ * waits for record k).  lbm_step_diagnostics_post queues on the context's stream the final sum
+ * of the most recent step's per-tile records and its copy, with the wait-status flags, into one
+ * of LBM_DIAG_SLOTS pinned host slots, and returns in *ticket a number naming that slot's record;
+ * later steps may be issued at once (the stream runs the sum before the next sweep rewrites the
+ * tile records).  lbm_step_diagnostics_take waits for that record's copy (an event of its own,
+ * not the whole stream), fills *out exactly as lbm_step_diagnostics would have for that step and
+ * frees the slot.  Tickets may be taken in any order, each once.
+ * Errors: post -- LBM_ERR_ARG (null pointer), LBM_ERR_STATE (no step has run since the state
+ * was last set, or all LBM_DIAG_SLOTS slots hold records not yet taken); take -- LBM_ERR_ARG,
+ * LBM_ERR_STATE (ticket never posted or already taken), LBM_ERR_TIMEOUT (a bounded wait of a
+ * launch before the post gave up, see below; the slot is freed), LBM_ERR_CUDA.
+ * Paper: Eq. 1 (moments), summed over the domain inside the Sec. 5.1.2 sweep; the pipelined read
+ * has no counterpart in the paper. */
+#define LBM_DIAG_SLOTS 4
+lbm_status lbm_step_diagnostics_post(lbm_ctx *ctx, int64_t *ticket);
+lbm_status lbm_step_diagnostics_take(lbm_ctx *ctx, int64_t ticket, lbm_diagnostics *out);
 
 /* Bounded device-side waits.  The kernels that wait on an mbarrier give up, set a device
  * status flag and return: the staged sweep after 1 s of the GPU's global timer per wait for its

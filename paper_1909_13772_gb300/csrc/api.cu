@@ -109,7 +109,15 @@ struct lbm_ctx {
     struct HostIO {
         double diag[8];
         int wait_err[2];
+        // pipelined reads (lbm_step_diagnostics_post/take): one record and its flags per slot
+        struct Slot {
+            double diag[8];
+            int wait_err[2];
+        } slot[LBM_DIAG_SLOTS];
     } *h_io = nullptr;
+    cudaEvent_t slot_done[LBM_DIAG_SLOTS] = {};      // recorded after each slot's copies
+    int64_t slot_ticket[LBM_DIAG_SLOTS] = {-1, -1, -1, -1};  // untaken ticket per slot (-1: free)
+    int64_t next_ticket = 0;
 
     // tracing: events around fill and sweep launches (pairs of [start, end])
     bool timing = false;
@@ -1674,6 +1682,66 @@ lbm_status lbm_step_diagnostics(lbm_ctx *c, lbm_diagnostics *out)
     return LBM_OK;
 }
 
+lbm_status lbm_step_diagnostics_post(lbm_ctx *c, int64_t *ticket)
+{
+    if (!c || !ticket) return LBM_ERR_ARG;
+    if (!c->step_diag_valid || !c->h_io) return fail(c, LBM_ERR_STATE, "no step has run since the state was last set");
+    int k = -1;
+    for (int j = 0; j < LBM_DIAG_SLOTS && k < 0; ++j) {
+        const int s = (int)((c->next_ticket + j) % LBM_DIAG_SLOTS);
+        if (c->slot_ticket[s] < 0) k = s;
+    }
+    if (k < 0) return fail(c, LBM_ERR_STATE, "all %d diagnostics slots hold records not yet taken", LBM_DIAG_SLOTS);
+    if (!c->slot_done[k]) CK(cudaEventCreateWithFlags(&c->slot_done[k], cudaEventDisableTiming), "cudaEventCreate");
+    lbm_ctx::HostIO::Slot &h = c->h_io->slot[k];
+    std::fill(h.diag, h.diag + 8, 0.0);
+    h.wait_err[0] = h.wait_err[1] = 0;
+    if (diag_records(c) > 0) {
+        CK(launch_reduce_final(c->d_step_partials, diag_records(c), c->d_out, c->stream), "diagnostics kernel");
+        CK(cudaMemcpyAsync(h.diag, c->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+           "copy diagnostics");
+    }
+    if (c->d_sweep_err)
+        CK(cudaMemcpyAsync(&h.wait_err[0], c->d_sweep_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "read wait status");
+    if (c->d_tc_err && c->closure == CLOSURE_MLP)
+        CK(cudaMemcpyAsync(&h.wait_err[1], c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+           "read network status");
+    CK(cudaEventRecord(c->slot_done[k], c->stream), "cudaEventRecord");
+    // the ticket names its slot: ticket % LBM_DIAG_SLOTS == k
+    int64_t t = c->next_ticket;
+    while (t % LBM_DIAG_SLOTS != k) ++t;
+    c->slot_ticket[k] = t;
+    c->next_ticket = t + 1;
+    *ticket = t;
+    return LBM_OK;
+}
+
+lbm_status lbm_step_diagnostics_take(lbm_ctx *c, int64_t ticket, lbm_diagnostics *out)
+{
+    if (!c || !out || ticket < 0) return LBM_ERR_ARG;
+    const int k = (int)(ticket % LBM_DIAG_SLOTS);
+    if (c->slot_ticket[k] != ticket) return fail(c, LBM_ERR_STATE, "diagnostics ticket %lld is not pending", (long long)ticket);
+    c->slot_ticket[k] = -1;
+    CK(cudaEventSynchronize(c->slot_done[k]), "step diagnostics");
+    const lbm_ctx::HostIO::Slot &h = c->h_io->slot[k];
+    if (h.wait_err[0] || h.wait_err[1]) {
+        // the flags are cleared and reported as lbm_step_diagnostics reports them
+        c->h_io->wait_err[0] = h.wait_err[0];
+        c->h_io->wait_err[1] = h.wait_err[1];
+        return wait_status_take(c);
+    }
+    out->mass = h.diag[0];
+    out->momentum[0] = h.diag[1];
+    out->momentum[1] = h.diag[2];
+    out->momentum[2] = h.diag[3];
+    out->kinetic_energy = h.diag[4];
+    out->max_speed = h.diag[5];
+    out->nonfinite = (int64_t)h.diag[6];
+    out->fluid_cells = (int64_t)h.diag[7];
+    return LBM_OK;
+}
+
 lbm_status lbm_get_info(lbm_ctx *c, lbm_info *out)
 {
     if (!c || !out) return LBM_ERR_ARG;
@@ -2178,6 +2246,8 @@ void lbm_destroy(lbm_ctx *c)
     dfree(c->d_sweep_err);
     if (c->h_io) cudaFreeHost(c->h_io);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->slot_done)
+        if (e) cudaEventDestroy(e);
     drop_graphs(c);
     delete c;
 }

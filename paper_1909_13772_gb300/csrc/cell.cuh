@@ -59,8 +59,17 @@ __device__ __forceinline__ T wmax(T v)
 //   contributes at most Q^2 u^2 rho of error (u = 2^-24), 1.3e-12 relative.
 //   Momentum and kinetic energy come from the collision's moments and are accumulated per
 //   thread with Kahan's compensated sum (error at most 2u of the sum of magnitudes, whatever
-//   the number of cells).  Warp shuffles and everything after them are FP64.  With FP64
-//   arithmetic the sums are plain FP64.  A cell counts as non-finite when rho + |u|^2 is.
+//   the number of cells).  With FP64 arithmetic the sums are plain FP64.  A cell counts as
+//   non-finite when rho + |u|^2 is.
+// The CTA's record with FP32 arithmetic stays in FP32 until its 8 results: the FP64 pipe of
+// this GPU retires 2 lanes per clock per SM, so FP64 warp shuffles of 8 sums per tile of 4
+// cells per thread cost more than the rest of the diagnostics.  Mass: the threads' float-float
+// pairs are added pairwise (butterfly over the warp, then the warps in order), high parts by
+// TwoSum, low parts in FP32 -- 12 additions on every path, each rounding the low part by at
+// most u/2 of the low parts' magnitudes (<= Q u of the mass), so the record adds at most
+// 6 Q u^2 relative to the per-cell Q^2 u^2.  Momentum and energy: each thread's Kahan pair
+// s - c rounded once (u of the magnitudes), then the same 12 plain FP32 additions (6 u);
+// counts are integers below 2^24, exact; the maximum exact.  Then FP64.
 // The running sums of a thread live in shared memory, column threadIdx.x of a [13][256]
 // array (CTAs of at most 256 threads), not in registers: there they would stay live across
 // the thread's whole z loop next to the cell's populations, which costs the sweep a CTA per SM
@@ -148,11 +157,15 @@ struct Diag {
         v[6] = (double)h[2816];
         v[7] = (double)h[3072];
     }
-    // The CTA's record (every thread of the CTA calls this): FP64 warp shuffles, then the warps
-    // in order; partials[blockIdx.x * 8 + c].
+    // The CTA's record (every thread of the CTA calls this): warp shuffles, then the warps in
+    // order; partials[blockIdx.x * 8 + c].
     __device__ __forceinline__ void tile_record(double *__restrict__ partials) const
     {
         if (!DIAG) return;
+        if constexpr (kComp) {
+            tile_record_f32(partials);
+            return;
+        }
         __shared__ double sh[8][8];
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
         double v[8];
@@ -166,6 +179,62 @@ struct Diag {
             const int c = threadIdx.x;
             double r = 0.0;
             for (int w = 0; w < nw; ++w) r = c == 5 ? fmax(r, sh[w][c]) : r + sh[w][c];
+            partials[(int64_t)blockIdx.x * 8 + c] = r;
+        }
+    }
+    // FP32 form of the CTA's record (see above): slots 0 mass high, 1 mass low, 2-4 momentum,
+    // 5 energy (x 2), 6 max |u|^2, 7 non-finite cells, 8 cells.
+    static __device__ __forceinline__ float two_sum_f(float s, float x, float &e)
+    {
+        const float t = s + x;
+        const float b = t - s;
+        e = (s - (t - b)) + (x - b);
+        return t;
+    }
+    __device__ __forceinline__ void tile_record_f32(double *__restrict__ partials) const
+    {
+        __shared__ float sf[8][9];
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const R *h = home();
+        float mh = h[0], ml = h[256];
+        float v[7] = {h[512] - h[1280], h[768] - h[1536], h[1024] - h[1792], h[2048] - h[2304],
+                      h[2560], h[2816], h[3072]};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, mh, o), bl = __shfl_xor_sync(0xffffffffu, ml, o);
+            float e;
+            mh = two_sum_f(mh, bh, e);
+            ml = (ml + bl) + e;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) {
+                const float w = __shfl_xor_sync(0xffffffffu, v[c], o);
+                v[c] = c == 4 ? fmaxf(v[c], w) : v[c] + w;
+            }
+        }
+        if (lane == 0) {
+            sf[warp][0] = mh;
+            sf[warp][1] = ml;
+#pragma unroll
+            for (int c = 0; c < 7; ++c) sf[warp][2 + c] = v[c];
+        }
+        __syncthreads();
+        if (threadIdx.x < 8) {
+            const int c = threadIdx.x;
+            double r;
+            if (c == 0) {
+                float th = sf[0][0], tl = sf[0][1];
+                for (int w = 1; w < nw; ++w) {
+                    float e;
+                    th = two_sum_f(th, sf[w][0], e);
+                    tl = (tl + sf[w][1]) + e;
+                }
+                r = (double)th + (double)tl;
+            } else {
+                const int j = c + 1;  // slot of output c: momentum 2-4, energy 5, max 6, counts 7-8
+                float t = sf[0][j];
+                for (int w = 1; w < nw; ++w) t = c == 5 ? fmaxf(t, sf[w][j]) : t + sf[w][j];
+                r = c == 4 ? 0.5 * (double)t : (c == 5 ? sqrt((double)t) : (double)t);
+            }
             partials[(int64_t)blockIdx.x * 8 + c] = r;
         }
     }

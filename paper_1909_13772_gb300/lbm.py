@@ -81,6 +81,8 @@ _SIGS = {
     "lbm_get_pdfs_region": ([_vp, ctypes.c_int32, _i32p, _i32p, _dp], ctypes.c_int),
     "lbm_reduce": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
     "lbm_step_diagnostics": ([_vp, _P(lbm_diagnostics)], ctypes.c_int),
+    "lbm_step_diagnostics_post": ([_vp, _i64p], ctypes.c_int),
+    "lbm_step_diagnostics_take": ([_vp, ctypes.c_int64, _P(lbm_diagnostics)], ctypes.c_int),
     "lbm_selfcheck_wait": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_get_info": ([_vp, _P(lbm_info)], ctypes.c_int),
     "lbm_set_tile": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
@@ -322,6 +324,19 @@ def lbm_step_diagnostics(ctx) -> dict:
             "max_speed": d.max_speed, "nonfinite": d.nonfinite, "fluid_cells": d.fluid_cells}
 
 
+def lbm_step_diagnostics_post(ctx) -> int:
+    t = ctypes.c_int64()
+    _check(ctx, load_library().lbm_step_diagnostics_post(ctx, ctypes.byref(t)))
+    return t.value
+
+
+def lbm_step_diagnostics_take(ctx, ticket) -> dict:
+    d = lbm_diagnostics()
+    _check(ctx, load_library().lbm_step_diagnostics_take(ctx, ticket, ctypes.byref(d)))
+    return {"mass": d.mass, "momentum": tuple(d.momentum), "kinetic_energy": d.kinetic_energy,
+            "max_speed": d.max_speed, "nonfinite": d.nonfinite, "fluid_cells": d.fluid_cells}
+
+
 def lbm_selfcheck_wait(ctx, polls=1024):
     _check(ctx, load_library().lbm_selfcheck_wait(ctx, polls))
 
@@ -457,6 +472,7 @@ def lbm_plan_params(ctx) -> np.ndarray:
 
 
 REDUCE_NOALLOC_MAX_CELLS = 134217728
+DIAG_SLOTS = 4  # pinned slots of the pipelined step-diagnostics read
 
 
 def lbm_reduce_noalloc(f_dev_ptr: int, stencil: int, storage: int, ncells: int, force, out_dev_ptr: int, stream=None):

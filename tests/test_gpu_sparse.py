@@ -62,11 +62,12 @@ def test_list_layout_equals_dense_bitwise(storage, q):
     assert dl["fluid_cells"] == dd["fluid_cells"] == info["fluid_cells"]
     # the same stored values: the exact (float-float) mass sums agree to FP64 order; momentum is a
     # compensated sum in the arithmetic type per thread (a dense thread walks several cells, a
-    # list thread one), within 2 u sum |rho u| <= 2 u mass max|u| of each other, u its roundoff
+    # list thread one), then (FP32) the pair's difference and 12 pairwise FP32 additions per CTA:
+    # within 9 u sum |rho u| <= 9 u mass max|u| of the exact sum on each side, u its roundoff
     assert abs(dl["mass"] / dd["mass"] - 1) < 1e-12
     u = 2.0 ** (-53 if storage == lbm.FP64 else -24)
     assert np.abs(np.array(dl["momentum"]) - np.array(dd["momentum"])).max() <= (
-        4 * u * dd["mass"] * dd["max_speed"] + 1e-12 * dd["mass"])
+        18 * u * dd["mass"] * dd["max_speed"] + 1e-12 * dd["mass"])
 
 
 @pytest.mark.parametrize("switch_at", [3, 4])

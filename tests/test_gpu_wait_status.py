@@ -42,6 +42,12 @@ def test_wait_timeout_reported_once_and_context_stays_usable(storage):
         s.step_diagnostics()
     assert e.value.status == TIMEOUT
     s.step_diagnostics()  # reported once, then cleared
+    lbm.lbm_selfcheck_wait(s.ctx, 256)
+    t = lbm.lbm_step_diagnostics_post(s.ctx)
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.lbm_step_diagnostics_take(s.ctx, t)  # the pipelined read reports it too
+    assert e.value.status == TIMEOUT
+    lbm.lbm_step_diagnostics_take(s.ctx, lbm.lbm_step_diagnostics_post(s.ctx))
     lbm.lbm_selfcheck_wait(s.ctx, 1)
     with pytest.raises(lbm.LbmError) as e:
         s.pdfs(0)
