@@ -1095,6 +1095,7 @@ void step_args(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
     if (sw.through == 1 && (!P.links.empty() || !P.zouhe.empty() || refine)) sw.through = 2;
     sw.stage_bytes = c->stage_bytes;
     sw.err = c->d_sweep_err;
+    sw.idx32 = c->arena_elems <= ((int64_t)1 << 32) ? 1 : 0;
     sw.cd = c->cd;
     sw.cf = c->cf;
     sw.stream = c->stream;

@@ -311,13 +311,33 @@ __device__ __forceinline__ int64_t nbr_addr(const NbrGeo *nb, Face fc, int x, in
 //   local sweep reads it as f_opp(i)(x, t+1).
 // Gather the populations streaming into cell (x, y, z) (see the file header of sweep.cu), as
 // stored: deviations f_i - w_i rho0 for the *_DEV storages (the collision works on them).
-template <int KIND, int FACE, bool MASK>
+// I32: element indices in 32-bit arithmetic from the arena base, for arenas of at most 2^32
+// elements per array (the host checks): every true index is then below 2^32, so the
+// arithmetic modulo 2^32 gives it exactly, and one wide multiply-add forms the address.
+template <int KIND, int FACE, bool MASK, bool I32 = false>
 __device__ __forceinline__ void gather_cell(R (&f)[kQ], StoreT *__restrict__ A, const DevBlock &B, const NbrGeo *nb,
                                             Face fc, int x, int y, int z, int64_t cell, uint32_t m, const R *base)
 {
     using L = Lattice<kQ>;
     StoreT *a = A + B.offset;
     const WrapD wd = FACE == 1 ? wrap_deltas(B, fc) : WrapD{};
+    if constexpr (I32 && KIND != SWEEP_AA_LOCAL) {
+        const uint32_t pitch = (uint32_t)B.pitch, plane = (uint32_t)B.plane, slab = (uint32_t)B.slab;
+        const uint32_t own = (uint32_t)B.offset + (uint32_t)cell;
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const bool bounce = MASK && i > 0 && ((m >> i) & 1u);
+            const int sl = KIND == SWEEP_PULL ? i : L::opp(i);
+            const int bs = KIND == SWEEP_PULL ? L::opp(i) : i;
+            const uint32_t off = (uint32_t)L::cx(i) + (uint32_t)L::cy(i) * pitch + (uint32_t)L::cz(i) * plane;
+            uint32_t o = bounce ? (uint32_t)bs * slab + own : (uint32_t)sl * slab + own - off;
+            if (FACE == 1 && !bounce) o += (uint32_t)wrap_of(wd, -L::cx(i), -L::cy(i), -L::cz(i));
+            if (FACE == 2 && !bounce)
+                o = (uint32_t)nbr_addr(nb, fc, x, y, z, -L::cx(i), -L::cy(i), -L::cz(i), sl, (int64_t)o);
+            f[i] = KIND == SWEEP_PULL ? S::raw(A + o) : S::raw_rw(A + o);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
@@ -337,7 +357,7 @@ __device__ __forceinline__ void gather_cell(R (&f)[kQ], StoreT *__restrict__ A, 
 }
 
 // Scatter the post-collision populations of cell (x, y, z).
-template <int KIND, int FACE, bool MASK>
+template <int KIND, int FACE, bool MASK, bool I32 = false>
 __device__ __forceinline__ void scatter_cell(const R (&f)[kQ], StoreT *__restrict__ A, StoreT *__restrict__ Bout,
                                              const DevBlock &B, const NbrGeo *nb, Face fc, int x, int y, int z,
                                              int64_t cell, uint32_t m, const R *base)
@@ -351,6 +371,22 @@ __device__ __forceinline__ void scatter_cell(const R (&f)[kQ], StoreT *__restric
     Face fs = fc;
     if (KIND == SWEEP_AA_NBR) asm volatile("" : "+r"(xs), "+r"(ys), "+r"(zs), "+r"(fs.lo), "+r"(fs.hi));
     const WrapD wd = (FACE == 1 && KIND == SWEEP_AA_NBR) ? wrap_deltas(B, fs) : WrapD{};
+    if constexpr (I32 && KIND == SWEEP_AA_NBR) {
+        const uint32_t pitch = (uint32_t)B.pitch, plane = (uint32_t)B.plane, slab = (uint32_t)B.slab;
+        const uint32_t own = (uint32_t)B.offset + (uint32_t)B.cell(xs, ys, zs);
+#pragma unroll
+        for (int i = 0; i < kQ; ++i) {
+            const int o = L::opp(i);
+            const bool bounce = MASK && i > 0 && ((m >> o) & 1u);
+            const uint32_t off = (uint32_t)L::cx(i) + (uint32_t)L::cy(i) * pitch + (uint32_t)L::cz(i) * plane;
+            uint32_t d = bounce ? (uint32_t)o * slab + own : (uint32_t)i * slab + own + off;
+            if (FACE == 1 && !bounce) d += (uint32_t)wrap_of(wd, L::cx(i), L::cy(i), L::cz(i));
+            if (FACE == 2 && !bounce)
+                d = (uint32_t)nbr_addr(nb, fs, xs, ys, zs, L::cx(i), L::cy(i), L::cz(i), i, (int64_t)d);
+            S::st_raw(A + d, f[i]);
+        }
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const int64_t off = dir_offset<kQ>(i, B.pitch, B.plane);
@@ -382,18 +418,18 @@ __device__ __forceinline__ void scatter_cell(const R (&f)[kQ], StoreT *__restric
 //   AA neighbour: bounce source A[i][x] (where the E layout keeps f*_opp(i)(x)); the value
 //   f*_i(x) whose target x + c_i is no-slip (bit opp(i)) goes to A[opp i][x], where the next
 //   local sweep reads it as f_opp(i)(x, t+1).
-template <bool FORCE, int KIND, bool DIAG, int FACE, bool MASK>
+template <bool FORCE, int KIND, bool DIAG, int FACE, bool MASK, bool I32 = false>
 __device__ __forceinline__ void update_cell(StoreT *__restrict__ A, StoreT *__restrict__ Bout, const DevBlock &B,
                                             const NbrGeo *nb, Face fc, int x, int y, int z, int64_t cell, uint32_t m,
                                             const Coll<R> &k, Diag<DIAG> &dg)
 {
     R f[kQ];
-    gather_cell<KIND, FACE, MASK>(f, A, B, nb, fc, x, y, z, cell, m, k.base);
+    gather_cell<KIND, FACE, MASK, I32>(f, A, B, nb, fc, x, y, z, cell, m, k.base);
     R rho, ux, uy, uz;
     constexpr bool kRcp = !(KIND == SWEEP_AA_NBR && sizeof(R) == 4);
     collide_cell<FORCE, kRcp>(f, k, rho, ux, uy, uz);
     dg.add(f, k.rho0, rho, ux, uy, uz);
-    scatter_cell<KIND, FACE, MASK>(f, A, Bout, B, nb, fc, x, y, z, cell, m, k.base);
+    scatter_cell<KIND, FACE, MASK, I32>(f, A, Bout, B, nb, fc, x, y, z, cell, m, k.base);
 }
 
 // Copy the scalar geometry of a block into registers (its neighbour table stays out).

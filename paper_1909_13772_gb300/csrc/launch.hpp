@@ -34,6 +34,7 @@ struct SweepArgs {
     int through;       // in-place neighbours: 0 none, 1 only the block itself (wrap), 2 other blocks
     size_t stage_bytes;  // dynamic shared memory of the staged tiles (DevTile flag bit 1), 0: none
     int *err;            // device flag: a bounded wait gave up
+    int idx32;           // every element index of a PDF array is below 2^32 (32-bit index arithmetic)
     Coll<double> cd;
     Coll<float> cf;
     cudaStream_t stream;

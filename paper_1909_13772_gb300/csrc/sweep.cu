@@ -246,7 +246,7 @@ __device__ __forceinline__ void sweep_staged(StoreT *__restrict__ A, StoreT *__r
 // warp with a cell on a face of a block that reads its neighbours in place takes the
 // resolving path, all other warps the plain one (the test is warp-uniform, so neither path
 // diverges); THROUGH = some block of the launch reads its neighbours in place.
-template <bool FORCE, int KIND, bool DIAG, int THROUGH>
+template <bool FORCE, int KIND, bool DIAG, int THROUGH, bool I32>
 __device__ __forceinline__ void sweep_cells(StoreT *__restrict__ A, StoreT *__restrict__ Bout,
                                             const DevBlock *__restrict__ blocks, const DevTile *__restrict__ tiles,
                                             int tz, const Coll<R> &k, Diag<DIAG> &dg, unsigned char *smem, int *err)
@@ -294,25 +294,25 @@ __device__ __forceinline__ void sweep_cells(StoreT *__restrict__ A, StoreT *__re
         const bool face = (f2.lo | f2.hi) != 0;
         if (!kThr) {
             if (masked && KIND != SWEEP_AA_LOCAL)
-                update_cell<FORCE, KIND, DIAG, 0, true>(A, Bout, B, nb, f2, x, y, z, cell, m, k, dg);
+                update_cell<FORCE, KIND, DIAG, 0, true, I32>(A, Bout, B, nb, f2, x, y, z, cell, m, k, dg);
             else
-                update_cell<FORCE, KIND, DIAG, 0, false>(A, Bout, B, nb, f2, x, y, z, cell, 0u, k, dg);
+                update_cell<FORCE, KIND, DIAG, 0, false, I32>(A, Bout, B, nb, f2, x, y, z, cell, 0u, k, dg);
         } else if (__any_sync(__activemask(), face)) {
             constexpr int kFace = kTable ? 2 : 1;
             if (masked)
-                update_cell<FORCE, KIND, DIAG, kFace, true>(A, Bout, B, nb, f2, x, y, z, cell, m, k, dg);
+                update_cell<FORCE, KIND, DIAG, kFace, true, I32>(A, Bout, B, nb, f2, x, y, z, cell, m, k, dg);
             else
-                update_cell<FORCE, KIND, DIAG, kFace, false>(A, Bout, B, nb, f2, x, y, z, cell, 0u, k, dg);
+                update_cell<FORCE, KIND, DIAG, kFace, false, I32>(A, Bout, B, nb, f2, x, y, z, cell, 0u, k, dg);
         } else {
             if (masked)
-                update_cell<FORCE, KIND, DIAG, 0, true>(A, Bout, B, nb, f2, x, y, z, cell, m, k, dg);
+                update_cell<FORCE, KIND, DIAG, 0, true, I32>(A, Bout, B, nb, f2, x, y, z, cell, m, k, dg);
             else
-                update_cell<FORCE, KIND, DIAG, 0, false>(A, Bout, B, nb, f2, x, y, z, cell, 0u, k, dg);
+                update_cell<FORCE, KIND, DIAG, 0, false, I32>(A, Bout, B, nb, f2, x, y, z, cell, 0u, k, dg);
         }
     }
 }
 
-template <bool FORCE, int KIND, bool DIAG, int THROUGH>
+template <bool FORCE, int KIND, bool DIAG, int THROUGH, bool I32>
 __global__ void __launch_bounds__(256, DIAG ? kMinBDiag : kMinB)
     k_sweep(StoreT *__restrict__ A, StoreT *__restrict__ Bout, const DevBlock *__restrict__ blocks,
             const DevTile *__restrict__ tiles, int tx, int tz, Coll<R> k, double *__restrict__ partials,
@@ -321,22 +321,22 @@ __global__ void __launch_bounds__(256, DIAG ? kMinBDiag : kMinB)
     extern __shared__ __align__(16) unsigned char stage_smem[];
     Diag<DIAG> dg;
     // every thread takes part in the block reduction, including those without cells
-    sweep_cells<FORCE, KIND, DIAG, THROUGH>(A, Bout, blocks, tiles, tz, k, dg, stage_smem, err);
+    sweep_cells<FORCE, KIND, DIAG, THROUGH, I32>(A, Bout, blocks, tiles, tz, k, dg, stage_smem, err);
     dg.tile_record(partials);
 }
 
-template <bool FORCE, int KIND, bool DIAG, int THROUGH>
+template <bool FORCE, int KIND, bool DIAG, int THROUGH, bool I32 = false>
 cudaError_t go1(const SweepArgs &s, const Coll<R> &k, size_t smem)
 {
     dim3 grid((unsigned)s.ntiles), block((unsigned)(s.tx * s.ty));
     // static shared memory (diagnostics sums, neighbour table) counts against the 48 KB that
     // need no opt-in, so larger staging buffers opt in with a margin for it
     if (smem > 32 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_sweep<FORCE, KIND, DIAG, THROUGH>,
+        cudaError_t e = cudaFuncSetAttribute(k_sweep<FORCE, KIND, DIAG, THROUGH, I32>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k_sweep<FORCE, KIND, DIAG, THROUGH><<<grid, block, smem, s.stream>>>((StoreT *)s.a, (StoreT *)s.b, s.blocks,
+    k_sweep<FORCE, KIND, DIAG, THROUGH, I32><<<grid, block, smem, s.stream>>>((StoreT *)s.a, (StoreT *)s.b, s.blocks,
                                                                         s.tiles, s.tx, s.tz, k, s.partials, s.err);
     return cudaGetLastError();
 }
@@ -348,6 +348,16 @@ cudaError_t go(const SweepArgs &s, const Coll<R> &k)
     if (s.ntiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     // shared memory of the staged tiles (pull sweep only)
     const size_t smem = (KIND == SWEEP_PULL && THROUGH != 2 && LBM_ST >= 2) ? s.stage_bytes : 0;
+    // the neighbour sweep spends its issue slots on 38 neighbour addresses per cell: 32-bit
+    // index arithmetic where the arena allows it (measured on the 256^3 channel: FP32 AA
+    // 0.890 -> 0.903 of HBM, FP16 AA 0.573 -> 0.616)
+    // (and the pull sweep's gather where the collision, not memory, bounds the sweep: MRT and
+    // cumulant objects)
+    if constexpr (KIND == SWEEP_AA_NBR || (KIND == SWEEP_PULL && (kMrt || kCum))) {
+        if (s.idx32 && smem == 0)
+            return s.partials ? go1<FORCE, KIND, true, THROUGH, true>(s, k, smem)
+                              : go1<FORCE, KIND, false, THROUGH, true>(s, k, smem);
+    }
     return s.partials ? go1<FORCE, KIND, true, THROUGH>(s, k, smem) : go1<FORCE, KIND, false, THROUGH>(s, k, smem);
 }
 
