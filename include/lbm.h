@@ -407,6 +407,14 @@ lbm_status lbm_set_batching(lbm_ctx *ctx, int32_t batched);
  * Paper: none (launch structure of the Sec. 5.1.2 sweep). */
 lbm_status lbm_set_graph(lbm_ctx *ctx, int32_t enable);
 
+/* Index arithmetic of the neighbour addresses in the sweeps that spend their issue slots on
+ * them (the AA neighbour sweep, the MRT and cumulant pull gathers, the closure's AA neighbour
+ * sweep): bits = 32 (default) uses 32-bit element indices when every PDF array of the context
+ * holds at most 2^32 elements and 64-bit ones otherwise; bits = 64 always uses 64-bit ones.
+ * Both give the same results bit for bit.  Errors: LBM_ERR_ARG (bits not 32 or 64).
+ * Paper: none (address arithmetic of the Sec. 5.1.2 sweep). */
+lbm_status lbm_set_index_bits(lbm_ctx *ctx, int32_t bits);
+
 /* Autotuner: times trial_steps steps for each candidate sweep tile shape (a fixed list from
  * 256x1x16 to 32x4x1, including shapes with few cells per CTA for small blocks) and each
  * neighbour mode (lbm_set_in_place; the other mode is tried only

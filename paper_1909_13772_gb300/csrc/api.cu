@@ -92,6 +92,7 @@ struct lbm_ctx {
     std::vector<int64_t> tile_start;  // first tile of each block (+ total at the end)
 
     // CUDA-graph replay of step pairs (graph mode): one executable graph per starting parity
+    bool wide_index = false;  // lbm_set_index_bits(64): no 32-bit index arithmetic in the sweeps
     bool graph_mode = false;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_epoch[2] = {-1, -1};
@@ -1095,7 +1096,7 @@ void step_args(lbm_ctx *c, SweepArgs &sw, FillArgs &fa)
     if (sw.through == 1 && (!P.links.empty() || !P.zouhe.empty() || refine)) sw.through = 2;
     sw.stage_bytes = c->stage_bytes;
     sw.err = c->d_sweep_err;
-    sw.idx32 = c->arena_elems <= ((int64_t)1 << 32) ? 1 : 0;
+    sw.idx32 = !c->wide_index && c->arena_elems <= ((int64_t)1 << 32) ? 1 : 0;
     sw.cd = c->cd;
     sw.cf = c->cf;
     sw.stream = c->stream;
@@ -1373,6 +1374,15 @@ lbm_status lbm_set_graph(lbm_ctx *c, int32_t enable)
                                             "between steps");
     c->graph_mode = enable != 0;
     if (!enable) drop_graphs(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_index_bits(lbm_ctx *c, int32_t bits)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (bits != 32 && bits != 64) return fail(c, LBM_ERR_ARG, "index bits must be 32 or 64, not %d", bits);
+    c->wide_index = bits == 64;
+    drop_graphs(c);  // captured launches carry the previous choice
     return LBM_OK;
 }
 

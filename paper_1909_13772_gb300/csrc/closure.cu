@@ -300,7 +300,7 @@ __device__ __forceinline__ float tc_mlp_256(tc::TcSmem256 &S, float b3, const fl
 #define LBM_CLOSURE_MINB_MLP 3
 #endif
 
-template <int KIND, int CLOSURE, bool DIAG, int THROUGH>
+template <int KIND, int CLOSURE, bool DIAG, int THROUGH, bool I32>
 __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LBM_CLOSURE_MINB_MLP)
     k_closure_sweep(StoreT *__restrict__ A, StoreT *__restrict__ Bout, const DevBlock *__restrict__ blocks,
                     const DevTile *__restrict__ tiles, int tz, Coll<float> k, const MlpDev *__restrict__ mlp,
@@ -376,14 +376,14 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
         if (live) {
             if (kThr && any_face) {
                 if (masked)
-                    gather_cell<KIND, kFace, true>(f, A, B, nb, f2, x, y, z, cell, m, k.base);
+                    gather_cell<KIND, kFace, true, I32>(f, A, B, nb, f2, x, y, z, cell, m, k.base);
                 else
-                    gather_cell<KIND, kFace, false>(f, A, B, nb, f2, x, y, z, cell, 0u, k.base);
+                    gather_cell<KIND, kFace, false, I32>(f, A, B, nb, f2, x, y, z, cell, 0u, k.base);
             } else {
                 if (masked && KIND != SWEEP_AA_LOCAL)
-                    gather_cell<KIND, 0, true>(f, A, B, nb, f2, x, y, z, cell, m, k.base);
+                    gather_cell<KIND, 0, true, I32>(f, A, B, nb, f2, x, y, z, cell, m, k.base);
                 else
-                    gather_cell<KIND, 0, false>(f, A, B, nb, f2, x, y, z, cell, 0u, k.base);
+                    gather_cell<KIND, 0, false, I32>(f, A, B, nb, f2, x, y, z, cell, 0u, k.base);
             }
         } else {
 #pragma unroll
@@ -416,14 +416,14 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
             dg.add(f, 0.f, r2, ux, uy, uz);
             if (kThr && any_face) {
                 if (masked)
-                    scatter_cell<KIND, kFace, true>(f, A, Bout, B, nb, f2, x, y, z, cell, m, k.base);
+                    scatter_cell<KIND, kFace, true, I32>(f, A, Bout, B, nb, f2, x, y, z, cell, m, k.base);
                 else
-                    scatter_cell<KIND, kFace, false>(f, A, Bout, B, nb, f2, x, y, z, cell, 0u, k.base);
+                    scatter_cell<KIND, kFace, false, I32>(f, A, Bout, B, nb, f2, x, y, z, cell, 0u, k.base);
             } else {
                 if (masked && KIND != SWEEP_AA_LOCAL)
-                    scatter_cell<KIND, 0, true>(f, A, Bout, B, nb, f2, x, y, z, cell, m, k.base);
+                    scatter_cell<KIND, 0, true, I32>(f, A, Bout, B, nb, f2, x, y, z, cell, m, k.base);
                 else
-                    scatter_cell<KIND, 0, false>(f, A, Bout, B, nb, f2, x, y, z, cell, 0u, k.base);
+                    scatter_cell<KIND, 0, false, I32>(f, A, Bout, B, nb, f2, x, y, z, cell, 0u, k.base);
             }
         }
     }
@@ -438,19 +438,19 @@ __global__ void __launch_bounds__(256, CLOSURE == 1 ? LBM_CLOSURE_MINB_SMAG : LB
     dg.tile_record(partials);
 }
 
-template <int KIND, int CLOSURE, bool DIAG>
+template <int KIND, int CLOSURE, bool DIAG, bool I32>
 cudaError_t go3(const ClosureLaunch &s)
 {
     dim3 grid((unsigned)s.sw.ntiles), block((unsigned)(s.sw.tx * s.sw.ty));
     const ClosureArgsDev ca{s.tau0, s.cs, s.lambda, s.trt, s.err};
     if (s.sw.through == 2)
-        k_closure_sweep<KIND, CLOSURE, DIAG, 2><<<grid, block, 0, s.sw.stream>>>(
+        k_closure_sweep<KIND, CLOSURE, DIAG, 2, I32><<<grid, block, 0, s.sw.stream>>>(
             (StoreT *)s.sw.a, (StoreT *)s.sw.b, s.sw.blocks, s.sw.tiles, s.sw.tz, s.sw.cf, s.mlp, ca, s.sw.partials);
     else if (s.sw.through)
-        k_closure_sweep<KIND, CLOSURE, DIAG, 1><<<grid, block, 0, s.sw.stream>>>(
+        k_closure_sweep<KIND, CLOSURE, DIAG, 1, I32><<<grid, block, 0, s.sw.stream>>>(
             (StoreT *)s.sw.a, (StoreT *)s.sw.b, s.sw.blocks, s.sw.tiles, s.sw.tz, s.sw.cf, s.mlp, ca, s.sw.partials);
     else
-        k_closure_sweep<KIND, CLOSURE, DIAG, 0><<<grid, block, 0, s.sw.stream>>>(
+        k_closure_sweep<KIND, CLOSURE, DIAG, 0, I32><<<grid, block, 0, s.sw.stream>>>(
             (StoreT *)s.sw.a, (StoreT *)s.sw.b, s.sw.blocks, s.sw.tiles, s.sw.tz, s.sw.cf, s.mlp, ca, s.sw.partials);
     return cudaGetLastError();
 }
@@ -458,7 +458,12 @@ cudaError_t go3(const ClosureLaunch &s)
 template <int KIND, int CLOSURE>
 cudaError_t go2(const ClosureLaunch &s)
 {
-    return s.sw.partials ? go3<KIND, CLOSURE, true>(s) : go3<KIND, CLOSURE, false>(s);
+    // 32-bit neighbour indices in the AA neighbour sweep where the arena allows it (as the
+    // plain sweeps)
+    if constexpr (KIND == SWEEP_AA_NBR) {
+        if (s.sw.idx32) return s.sw.partials ? go3<KIND, CLOSURE, true, true>(s) : go3<KIND, CLOSURE, false, true>(s);
+    }
+    return s.sw.partials ? go3<KIND, CLOSURE, true, false>(s) : go3<KIND, CLOSURE, false, false>(s);
 }
 
 template <int KIND>

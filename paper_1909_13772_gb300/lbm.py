@@ -88,6 +88,7 @@ _SIGS = {
     "lbm_set_tile": ([_vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "lbm_kernel_launches": ([_vp], ctypes.c_int64),
     "lbm_set_graph": ([_vp, ctypes.c_int32], ctypes.c_int),
+    "lbm_set_index_bits": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_set_batching": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_set_in_place": ([_vp, ctypes.c_int32], ctypes.c_int),
     "lbm_autotune": ([_vp, ctypes.c_int32, _i32p, _i32p, _dp], ctypes.c_int),
@@ -380,6 +381,10 @@ def lbm_set_in_place(ctx, enable=True):
 
 def lbm_set_graph(ctx, enable=True):
     _check(ctx, load_library().lbm_set_graph(ctx, 1 if enable else 0))
+
+
+def lbm_set_index_bits(ctx, bits):
+    _check(ctx, load_library().lbm_set_index_bits(ctx, int(bits)))
 
 
 def lbm_autotune(ctx, trial_steps=20):

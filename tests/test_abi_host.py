@@ -61,6 +61,12 @@ def test_create_rejects_bad_arguments():
             assert e.value.status == 1
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_tile(ctx, 48, 4, 4)
+        for bits in (16, 0, 128):
+            with pytest.raises(lbm.LbmError) as e:
+                lbm.lbm_set_index_bits(ctx, bits)
+            assert e.value.status == 1
+        lbm.lbm_set_index_bits(ctx, 64)
+        lbm.lbm_set_index_bits(ctx, 32)
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_boundary(ctx, 3, None)
         with pytest.raises(lbm.LbmError):
