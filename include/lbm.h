@@ -284,7 +284,9 @@ lbm_status lbm_set_boundary(lbm_ctx *ctx, int32_t block, const uint8_t *flags, c
  * populations are the equilibrium at (rho, u - F/(2 rho)), so the half-force-corrected
  * velocity equals u; the stored state is their post-collision image, written in the
  * context's current storage layout (two-grid source array or the current AA parity).
- * Non-fluid cells are left untouched.
+ * Non-fluid cells are left untouched.  Page-locked host buffers (cudaHostAlloc, cudaHostRegister,
+ * torch pin_memory) are read by the initialising kernel itself over the host link; other host
+ * memory goes through a device staging copy.  Synchronises the stream.
  * Paper: Eq. 1 (moments of the equilibrium populations), Sec. 4.3 (set-up on the host, copied to
  * the GPU field). */
 lbm_status lbm_init_macroscopic(lbm_ctx *ctx, int32_t block, const double *rho, const double *u);
@@ -298,7 +300,8 @@ lbm_status lbm_init_macroscopic(lbm_ctx *ctx, int32_t block, const double *rho, 
 lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
 
 /* Density rho[N] and velocity u[3N] of one block's stored state (host FP64 buffers).
- * Non-fluid cells give 0.  Synchronises the stream.
+ * Non-fluid cells give 0.  Page-locked host buffers are written by the moment kernel itself over
+ * the host link; other host memory through a device staging copy.  Synchronises the stream.
  * Paper: Eq. 1 (density and velocity moments), Sec. 4.3 (output through the host mirror). */
 lbm_status lbm_get_macroscopic(lbm_ctx *ctx, int32_t block, double *rho, double *u);
 

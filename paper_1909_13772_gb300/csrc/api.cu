@@ -474,6 +474,20 @@ lbm_status ensure_lists(lbm_ctx *c)
     return LBM_OK;
 }
 
+// Device address of a page-locked (cudaHostAlloc'd or cudaHostRegister'ed) host buffer, which
+// kernels can read and write over the host link directly; nullptr for any other pointer
+// (pageable host memory goes through a device staging copy).
+double *device_view(const void *host)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    return static_cast<double *>(at.devicePointer);
+}
+
 lbm_status ensure_scratch(lbm_ctx *c, int64_t doubles)
 {
     if (doubles <= c->scratch_cap) return LBM_OK;
@@ -1051,11 +1065,19 @@ lbm_status lbm_init_macroscopic(lbm_ctx *c, int32_t block, const double *rho, co
     if ((s = ensure_dense(c)) != LBM_OK) return s;
     const BlockLayout &L = c->blocks[block];
     const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
-    if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
-    CK(cudaMemcpyAsync(c->d_scratch, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy rho");
-    CK(cudaMemcpyAsync(c->d_scratch + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy u");
     CellArgs a = cell_args(c, block);
-    a.f64 = c->d_scratch;
+    double *vr = device_view(rho), *vu = device_view(u);
+    if (vr && vu) {
+        // page-locked host buffers: the kernel reads them over the host link itself
+        a.rho = vr;
+        a.u = vu;
+    } else {
+        if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
+        CK(cudaMemcpyAsync(c->d_scratch, rho, N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy rho");
+        CK(cudaMemcpyAsync(c->d_scratch + N, u, 3 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy u");
+        a.rho = c->d_scratch;
+        a.u = c->d_scratch + N;
+    }
     CK(do_cells(c->q, c->storage, CELL_INIT, c->force ? 1 : 0, a), "init kernel");
     c->list_valid = false;  // the dense arrays hold the new state
     c->step_diag_valid = false;
@@ -1480,13 +1502,21 @@ lbm_status lbm_get_macroscopic(lbm_ctx *c, int32_t block, double *rho, double *u
     if ((s = ensure_dense(c)) != LBM_OK) return s;
     const BlockLayout &L = c->blocks[block];
     const int64_t N = (int64_t)L.n[0] * L.n[1] * L.n[2];
-    if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
     CellArgs a = cell_args(c, block);
-    a.rho = c->d_scratch;
-    a.u = c->d_scratch + N;
-    CK(do_cells(c->q, c->storage, CELL_MACRO, 0, a), "macroscopic kernel");
-    CK(cudaMemcpyAsync(rho, c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy rho");
-    CK(cudaMemcpyAsync(u, c->d_scratch + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy u");
+    double *vr = device_view(rho), *vu = device_view(u);
+    if (vr && vu) {
+        // page-locked host buffers: the kernel writes them over the host link itself
+        a.rho = vr;
+        a.u = vu;
+        CK(do_cells(c->q, c->storage, CELL_MACRO, 0, a), "macroscopic kernel");
+    } else {
+        if ((s = ensure_scratch(c, 4 * N)) != LBM_OK) return s;
+        a.rho = c->d_scratch;
+        a.u = c->d_scratch + N;
+        CK(do_cells(c->q, c->storage, CELL_MACRO, 0, a), "macroscopic kernel");
+        CK(cudaMemcpyAsync(rho, c->d_scratch, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy rho");
+        CK(cudaMemcpyAsync(u, c->d_scratch + N, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy u");
+    }
     CK(cudaStreamSynchronize(c->stream), "get_macroscopic");
     return wait_status(c);
 }

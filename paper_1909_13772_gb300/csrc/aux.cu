@@ -264,7 +264,7 @@ __device__ __forceinline__ void init_collide(R (&f)[Q], const Coll<R> &k)
 // (the stored state is post-collision).  Equilibrium: w rho (1 + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u).
 template <bool FORCE>
 __global__ void k_init(StoreT *__restrict__ A, const DevBlock *__restrict__ blocks, int blk, int layout,
-                       const double *__restrict__ in,
+                       const double *__restrict__ rho_in, const double *__restrict__ u_in,
                        const uint32_t *__restrict__ mask, Coll<R> k)
 {
     const DevBlock *Bp = blocks + blk;
@@ -277,8 +277,8 @@ __global__ void k_init(StoreT *__restrict__ A, const DevBlock *__restrict__ bloc
     StoreT *a = A + B.offset;
     const uint32_t m = mask ? mask[cell] : 0u;
     if (m & kMaskSolid) return;  // non-fluid cells hold no state
-    const R rho = R(in[n]);
-    R ux = R(in[N + n]), uy = R(in[2 * N + n]), uz = R(in[3 * N + n]);
+    const R rho = R(rho_in[n]);
+    R ux = R(u_in[n]), uy = R(u_in[N + n]), uz = R(u_in[2 * N + n]);
     if (FORCE) {
         ux -= R(0.5) * k.F[0] / rho;
         uy -= R(0.5) * k.F[1] / rho;
@@ -586,9 +586,9 @@ cudaError_t LBM_CAT(launch_cells_, LBM_Q, LBM_ST)(int op, int force, const CellA
     switch (op) {
         case CELL_INIT:
             if (force)
-                k_init<true><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, k);
+                k_init<true><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.rho, s.u, s.mask, k);
             else
-                k_init<false><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.f64, s.mask, k);
+                k_init<false><<<(unsigned)ctas, threads, 0, s.stream>>>((StoreT *)s.a, s.blocks, s.block, s.layout, s.rho, s.u, s.mask, k);
             break;
         case CELL_GET: {
             // region (the whole block when rn is zero)

@@ -110,8 +110,8 @@ struct CellArgs {
     int block;               // this block's index in it
     DevBlock blk;
     int layout;  // Layout of the stored state
-    double *f64;        // get: out f[Q*N]; set: in; init: rho[N] then u[3N]
-    double *rho, *u;    // macroscopic out
+    double *f64;        // get: out f[Q*N]; set: in
+    double *rho, *u;    // macroscopic out; init: in (rho[N], u[3N])
     const uint32_t *mask;
     int ratio;  // coarse: edge of the coarse cell in interior cells
     int r0[3], rn[3];  // get: box origin and size in interior cells (rn[0] == 0: the whole block)

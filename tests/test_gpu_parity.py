@@ -283,6 +283,48 @@ def test_macroscopic_output_matches_oracle_elementwise(storage, pattern, steps):
     assert np.all(du <= (10 * e + np.abs(wu[:, fluid]) * 19 * e) / wrho[fluid] + 1e-300)
 
 
+@pytest.mark.parametrize("storage,pattern", [(lbm.FP32, lbm.TWO_GRID), (lbm.FP64, lbm.AA), (lbm.FP16_DEV, lbm.TWO_GRID)])
+def test_page_locked_host_buffers_equal_pageable(storage, pattern):
+    """Page-locked host buffers are read (init) and written (macroscopic output) by the kernels
+    directly; pageable ones go through the device staging copy: the same bits either way."""
+    torch = pytest.importorskip("torch")
+    case = _porous_case(storage, pattern)
+    rho, u = inputs.random_state(case.shape, seed=17, rho_amp=0.02, u_amp=0.02)
+    out = []
+    for pinned in (False, True):
+        s = case.make_sim()
+        try:
+            keep = []
+            for b, (o, sz) in enumerate(s.blocks):
+                r = np.ascontiguousarray(rho[o[2]:o[2] + sz[2], o[1]:o[1] + sz[1], o[0]:o[0] + sz[0]])
+                v = np.ascontiguousarray(u[:, o[2]:o[2] + sz[2], o[1]:o[1] + sz[1], o[0]:o[0] + sz[0]])
+                if pinned:
+                    tr, tv = torch.from_numpy(r).pin_memory(), torch.from_numpy(v).pin_memory()
+                    keep += [tr, tv]
+                    r, v = tr.numpy(), tv.numpy()
+                lbm.lbm_init_macroscopic(s.ctx, b, r, v)
+            s.step(4)
+            got = []
+            for b, (o, sz) in enumerate(s.blocks):
+                n = sz[0] * sz[1] * sz[2]
+                if pinned:
+                    tr = torch.empty(n, dtype=torch.float64).pin_memory()
+                    tv = torch.empty(3 * n, dtype=torch.float64).pin_memory()
+                    keep += [tr, tv]
+                    r, v = tr.numpy(), tv.numpy()
+                else:
+                    r, v = np.empty(n), np.empty(3 * n)
+                lbm.lbm_get_macroscopic(s.ctx, b, r, v)
+                got.append((r.copy(), v.copy()))
+            out.append((gather_pdfs(s, case), got))
+        finally:
+            s.close()
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    for (r0, v0), (r1, v1) in zip(out[0][1], out[1][1]):
+        np.testing.assert_array_equal(r0, r1)
+        np.testing.assert_array_equal(v0, v1)
+
+
 def test_macroscopic_output_removes_half_the_force():
     """At rest under a body force the stored post-collision state carries sum c f* = F/2 per
     cell; the output velocity (sum c f* - F/2) / rho is zero there (and F/(2 rho) if the shift
