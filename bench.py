@@ -351,6 +351,35 @@ def variant_error(lbm, variant, steps=ERROR_STEPS):
             "against": "oracle column after %d steps (tests/golden/channel_column_2000.txt)" % steps}
 
 
+def time_diag_sweep(lbm, variant, calls=40):
+    """The sweep that ends every lbm_step call (and every step of the e2e leg) computes the step
+    diagnostics; its mean time over `calls` one-step calls against the plain sweep's mean over
+    one call of `calls` steps, both from the library's event tracing."""
+    import torch
+    from paper_1909_13772_gb300 import inputs
+    storage, pattern, collision = VARIANTS[variant]
+    stream = torch.cuda.Stream()
+    sim = make_sim(lbm, storage, pattern, stream.cuda_stream, None, collision)
+    try:
+        rho, u = inputs.rest(SHAPE)
+        sim.init(0, rho, u)
+        sim.step(4)
+        torch.cuda.synchronize()
+        lbm.lbm_enable_timing(sim.ctx, True)
+        for _ in range(calls):
+            lbm.lbm_step(sim.ctx, 1)
+        torch.cuda.synchronize()
+        d = lbm.lbm_read_timing(sim.ctx)
+        lbm.lbm_step(sim.ctx, calls)  # calls - 1 plain sweeps and one with diagnostics
+        torch.cuda.synchronize()
+        p = lbm.lbm_read_timing(sim.ctx)
+    finally:
+        sim.close()
+    diag = d["sweep"][0] / d["sweep"][1]
+    plain = (p["sweep"][0] - diag) / (p["sweep"][1] - 1)
+    return {"diag_ms": round(diag, 4), "plain_ms": round(plain, 4), "ratio": round(diag / plain, 3), "calls": calls}
+
+
 def time_e2e(lbm, variant, steps, world):
     """Same metric through the C ABI with host buffers: host->device upload of the initial
     macroscopic fields, K x (lbm_step + read-back of the step's diagnostics -- mass, momentum,
@@ -507,6 +536,7 @@ def run_ours(args):
                 k = max(10, min(args.steps, 200 if v.startswith("fp64") else args.steps))
                 variants[v] = time_variant(lbm, v, k, args.warmup, world)
             variants[v]["error"] = variant_error(lbm, v)
+    diag_sweep = time_diag_sweep(lbm, head)
     e2e = time_e2e(lbm, head, args.steps, world)
     cpu = cpu_baseline() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     peak, peak_kind = measured_peaks()
@@ -541,6 +571,7 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "diagnostics_sweep": diag_sweep,
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],
         "timing": {"repeats": res["repeats"], "value_from": "median of the repeats of the K-step timed region "

@@ -38,6 +38,7 @@ def test_headline_line_has_the_contract_keys(monkeypatch, capsys):
     pytest.importorskip("torch")
     monkeypatch.setattr(bench, "time_variant", _fake_variant)
     monkeypatch.setattr(bench, "time_e2e", _fake_e2e)
+    monkeypatch.setattr(bench, "time_diag_sweep", lambda lbm, variant: {"diag_ms": 1.1, "plain_ms": 1.0})
     monkeypatch.setattr(bench, "variant_error", _fake_error)
     monkeypatch.setattr(bench, "measure_workloads", lambda args: {"c1_taylor_green": {"value": 1.0}})
     monkeypatch.setenv("RANK", "0")
@@ -75,6 +76,7 @@ def test_no_workloads_flag(monkeypatch, capsys):
     pytest.importorskip("torch")
     monkeypatch.setattr(bench, "time_variant", _fake_variant)
     monkeypatch.setattr(bench, "time_e2e", _fake_e2e)
+    monkeypatch.setattr(bench, "time_diag_sweep", lambda lbm, variant: {"diag_ms": 1.1, "plain_ms": 1.0})
     monkeypatch.setattr(bench, "variant_error", _fake_error)
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
