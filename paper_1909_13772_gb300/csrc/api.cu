@@ -116,6 +116,7 @@ struct lbm_ctx {
             int wait_err[2];
         } slot[LBM_DIAG_SLOTS];
     } *h_io = nullptr;
+    HostIO *h_io_dev = nullptr;  // its device address (kernels write the pipelined slots directly)
     cudaEvent_t slot_done[LBM_DIAG_SLOTS] = {};      // recorded after each slot's copies
     int64_t slot_ticket[LBM_DIAG_SLOTS] = {-1, -1, -1, -1};  // untaken ticket per slot (-1: free)
     int64_t next_ticket = 0;
@@ -275,6 +276,7 @@ lbm_status ensure_arena(lbm_ctx *c)
     CK(cudaMalloc((void **)&c->d_sweep_err, sizeof(int)), "cudaMalloc(sweep status)");
     CK(cudaMemsetAsync(c->d_sweep_err, 0, sizeof(int), c->stream), "clear sweep status");
     CK(cudaMallocHost((void **)&c->h_io, sizeof(lbm_ctx::HostIO)), "cudaMallocHost(status)");
+    CK(cudaHostGetDevicePointer((void **)&c->h_io_dev, c->h_io, 0), "device address of the host landing zone");
     c->dev_ready = true;
     return LBM_OK;
 }
@@ -1737,17 +1739,21 @@ lbm_status lbm_step_diagnostics_post(lbm_ctx *c, int64_t *ticket)
     lbm_ctx::HostIO::Slot &h = c->h_io->slot[k];
     std::fill(h.diag, h.diag + 8, 0.0);
     h.wait_err[0] = h.wait_err[1] = 0;
+    const int *tc_err = (c->d_tc_err && c->closure == CLOSURE_MLP) ? c->d_tc_err : nullptr;
     if (diag_records(c) > 0) {
-        CK(launch_reduce_final(c->d_step_partials, diag_records(c), c->d_out, c->stream), "diagnostics kernel");
-        CK(cudaMemcpyAsync(h.diag, c->d_out, 8 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
-           "copy diagnostics");
+        // the final sum writes the record and the wait-status flags into the slot itself
+        lbm_ctx::HostIO::Slot *hd = &c->h_io_dev->slot[k];
+        CK(launch_reduce_final_slot(c->d_step_partials, diag_records(c), c->d_out, hd->diag, hd->wait_err,
+                                    c->d_sweep_err, tc_err, c->stream),
+           "diagnostics kernel");
+    } else {
+        if (c->d_sweep_err)
+            CK(cudaMemcpyAsync(&h.wait_err[0], c->d_sweep_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+               "read wait status");
+        if (tc_err)
+            CK(cudaMemcpyAsync(&h.wait_err[1], tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
+               "read network status");
     }
-    if (c->d_sweep_err)
-        CK(cudaMemcpyAsync(&h.wait_err[0], c->d_sweep_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
-           "read wait status");
-    if (c->d_tc_err && c->closure == CLOSURE_MLP)
-        CK(cudaMemcpyAsync(&h.wait_err[1], c->d_tc_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream),
-           "read network status");
     CK(cudaEventRecord(c->slot_done[k], c->stream), "cudaEventRecord");
     // the ticket names its slot: ticket % LBM_DIAG_SLOTS == k
     int64_t t = c->next_ticket;

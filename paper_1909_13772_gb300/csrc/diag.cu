@@ -20,31 +20,47 @@ __device__ __forceinline__ double dmax(double v)
     return v;
 }
 
-// Fixed-order sum of n records into out[8] by the calling CTA.
+// Fixed-order sum of n records into out[8] by the calling CTA (at most 256 threads): each
+// thread sums its records, then warp 0 alone sums the threads' sums (lane j takes threads j,
+// j + 32, ...) and shuffles.  The FP64 pipe of this GPU retires 2 lanes per clock per SM, so
+// warp-wide FP64 shuffles in every warp would cost more than the sums themselves.
 __device__ __forceinline__ void final_sum(const double *__restrict__ partials, int64_t n, double *__restrict__ out)
 {
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     for (int64_t p = threadIdx.x; p < n; p += blockDim.x)
         for (int c = 0; c < 8; ++c) acc[c] = c == 5 ? fmax(acc[c], partials[p * 8 + c]) : acc[c] + partials[p * 8 + c];
-    __shared__ double sh[8][8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double sh[8][256];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const double v = c == 5 ? dmax(acc[c]) : dsum(acc[c]);
-        if (lane == 0) sh[warp][c] = v;
-    }
+    for (int c = 0; c < 8; ++c) sh[c][threadIdx.x] = acc[c];
     __syncthreads();
-    if (threadIdx.x < 8) {
-        const int c = threadIdx.x;
-        double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v = c == 5 ? fmax(v, sh[w][c]) : v + sh[w][c];
-        out[c] = v;
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, nt = (int)blockDim.x;
+        for (int c = 0; c < 8; ++c) {
+            double v = 0.0;
+            for (int j = lane; j < nt; j += 32) v = c == 5 ? fmax(v, sh[c][j]) : v + sh[c][j];
+            v = c == 5 ? dmax(v) : dsum(v);
+            if (lane == 0) out[c] = v;
+        }
     }
 }
 
 __global__ void __launch_bounds__(256) k_diag_final(const double *__restrict__ partials, int64_t n, double *__restrict__ out)
 {
     final_sum(partials, n, out);
+}
+
+// The same sum written straight into a page-locked host slot (its device address), with the
+// bounded-wait status flags beside it, so that reading a step's record needs no copy.
+__global__ void __launch_bounds__(256) k_diag_final_slot(const double *__restrict__ partials, int64_t n,
+                                                         double *__restrict__ slot, int *__restrict__ slot_err,
+                                                         const int *__restrict__ err0, const int *__restrict__ err1)
+{
+    __shared__ double res[8];
+    final_sum(partials, n, res);
+    __syncthreads();
+    if (threadIdx.x < 8) slot[threadIdx.x] = res[threadIdx.x];
+    if (threadIdx.x == 8) slot_err[0] = err0 ? *(const volatile int *)err0 : 0;
+    if (threadIdx.x == 9) slot_err[1] = err1 ? *(const volatile int *)err1 : 0;
 }
 
 // Per block: CTA b sums the records of tiles start[b] .. start[b+1] - 1 into out[8 b ..].
@@ -82,6 +98,23 @@ cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_diag_final<<<1, 256, 0, s>>>(out + 8, chunks, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_final_slot(const double *partials, int64_t n, double *scratch, double *slot, int *slot_err,
+                                     const int *err0, const int *err1, cudaStream_t s)
+{
+    // the partition of launch_reduce_final: the same result bits
+    if (n <= kChunk) {
+        k_diag_final_slot<<<1, 256, 0, s>>>(partials, n, slot, slot_err, err0, err1);
+        return cudaGetLastError();
+    }
+    const int64_t chunks = (n + kChunk - 1) / kChunk;
+    if (chunks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    k_diag_chunks<<<(unsigned)chunks, 256, 0, s>>>(partials, n, scratch + 8);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_diag_final_slot<<<1, 256, 0, s>>>(scratch + 8, chunks, slot, slot_err, err0, err1);
     return cudaGetLastError();
 }
 

@@ -150,6 +150,10 @@ cudaError_t launch_reduce_final(const double *partials, int64_t n, double *out, 
 // One thread waits `polls` polls on an mbarrier that never completes and sets *err = 2.
 cudaError_t launch_wait_selfcheck(int *err, uint32_t polls, cudaStream_t s);
 int64_t reduce_final_scratch(int64_t n);
+// The same sum written to slot[0..7] (device address of page-locked host memory), with *err0
+// and *err1 (device flags, either may be null: 0) copied to slot_err[0..1]; scratch as out above.
+cudaError_t launch_reduce_final_slot(const double *partials, int64_t n, double *scratch, double *slot, int *slot_err,
+                                     const int *err0, const int *err1, cudaStream_t s);
 // Per-block second pass: block b sums the records of tiles start[b] .. start[b+1] - 1 (tiles
 // are stored block by block) into out[8 b .. 8 b + 7].
 cudaError_t launch_block_final(const double *partials, const int64_t *start, int64_t nblocks, double *out,
