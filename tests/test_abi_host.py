@@ -67,6 +67,16 @@ def test_create_rejects_bad_arguments():
             assert e.value.status == 1
         lbm.lbm_set_index_bits(ctx, 64)
         lbm.lbm_set_index_bits(ctx, 32)
+        # pipelined diagnostics: nothing to post before a step, no ticket to take
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step_diagnostics_post(ctx)
+        assert e.value.status == 2
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step_diagnostics_take(ctx, 5)
+        assert e.value.status == 2
+        with pytest.raises(lbm.LbmError) as e:
+            lbm.lbm_step_diagnostics_take(ctx, -1)
+        assert e.value.status == 1
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_boundary(ctx, 3, None)
         with pytest.raises(lbm.LbmError):
