@@ -335,8 +335,11 @@ lbm_status lbm_reduce(lbm_ctx *ctx, lbm_diagnostics *out);
  * per-thread and per-CTA sums in the sweep's arithmetic type (FP64 for FP64 storage; FP32 for
  * FP32 and 16-bit storage, with the mass an exact float-float sum of the stored values per cell
  * and float-float across cells, momentum and energy compensated per thread), FP64 across CTAs,
- * fixed order.  FP32 bounds against the FP64 pass (u = 2^-24): mass (Q^2 + 6 Q) u^2 relative,
- * momentum 20 u mass + 9 u sum |rho u|.  Cheap enough to read after every step; lbm_reduce is
+ * fixed order.  FP32 bounds against the FP64 pass (u = 2^-24): mass (Q + n + 3)^2 u^2 relative,
+ * n the cells one thread sweeps (the tile's z extent, twice that in the paired 16-bit tiles),
+ * for states whose rest population is at least every other population (each cell's sum is a
+ * Fast2Sum chain started there; the deviation storages start it at rho0); momentum
+ * 20 u mass + 9 u sum |rho u|.  Cheap enough to read after every step; lbm_reduce is
  * the full-FP64 pass over the stored values.  Synchronises the stream.
  * Errors: LBM_ERR_STATE when the state was set (init, set_pdfs) after the last step.
  * Paper: Eq. 1 (moments), summed over the domain inside the Sec. 5.1.2 sweep; no counterpart in

@@ -56,7 +56,10 @@ __device__ __forceinline__ T wmax(T v)
 //   populations, which is at least every other population: w_0 >= 6 w_i), the error terms in
 //   FP32; the cells of a thread by TwoSum (Knuth: b = t - s, e = (s - (t - b)) + (x - b), exact
 //   whatever the magnitudes -- consecutive cell masses straddle powers of two).  A cell
-//   contributes at most Q^2 u^2 rho of error (u = 2^-24), 1.3e-12 relative.
+//   contributes at most Q^2 u^2 rho of error (u = 2^-24).  The thread adds each cell's error
+//   terms and its TwoSum error to its low part in FP32: with n cells those 2n additions round
+//   by at most u/2 of a low part below (k + Q) u/2 of the running mass at cell k, at most
+//   (2 Q n + n^2) u^2 of the thread's mass in all.
 //   Momentum and kinetic energy come from the collision's moments and are accumulated per
 //   thread with Kahan's compensated sum (error at most 2u of the sum of magnitudes, whatever
 //   the number of cells).  With FP64 arithmetic the sums are plain FP64.  A cell counts as
@@ -66,8 +69,9 @@ __device__ __forceinline__ T wmax(T v)
 // cells per thread cost more than the rest of the diagnostics.  Mass: the threads' float-float
 // pairs are added pairwise (butterfly over the warp, then the warps in order), high parts by
 // TwoSum, low parts in FP32 -- 12 additions on every path, each rounding the low part by at
-// most u/2 of the low parts' magnitudes (<= Q u of the mass), so the record adds at most
-// 6 Q u^2 relative to the per-cell Q^2 u^2.  Momentum and energy: each thread's Kahan pair
+// most u/2 of the low parts' magnitudes (<= (Q + n) u/2 of the mass), 3 (Q + n) u^2 more: the
+// record's mass is within (Q + n + 3)^2 u^2 of the exact sum of the stored values (2.4e-12
+// for D3Q19 at n = 4).  Momentum and energy: each thread's Kahan pair
 // s - c rounded once (u of the magnitudes), then the same 12 plain FP32 additions (6 u);
 // counts are integers below 2^24, exact; the maximum exact.  Then FP64.
 // The running sums of a thread live in shared memory, column threadIdx.x of a [13][256]

@@ -426,9 +426,10 @@ def test_bound_torch_buffer_and_stream():
 
 # Bounds of the fused step diagnostics against the FP64 pass over the stored state (lbm_reduce).
 # Mass: with FP32 arithmetic each cell's stored values are summed exactly as a float-float pair
-# (error terms in FP32: at most Q^2 u^2 rho per cell, u = 2^-24, 1.3e-12 relative); the CTA adds
-# the threads' pairs with the low parts in FP32, 12 additions deep, each rounding by u/2 of the
-# low parts (<= Q u of the mass): 6 Q u^2 more; both sides' FP64 sums add < 1e-13.  Momentum: the
+# (error terms in FP32: at most Q^2 u^2 rho per cell, u = 2^-24); a thread's n cells add up to
+# (2 Q n + n^2) u^2 in its FP32 low part; the CTA adds the threads' pairs with the low parts in
+# FP32, 12 additions deep (3 (Q + n) u^2): within (Q + n + 3)^2 u^2 in all, n = 4 cells per
+# thread in the default 256 x 1 x 4 tiles; both sides' FP64 sums add < 1e-13.  Momentum: the
 # collision's FP32 moment rho u of a cell (a sum of 19 values, then the half-force term) against
 # the FP64 moment of the stored values (rounded once more): at most 20 u sum_i f_i = 20 u rho per
 # cell; per thread Kahan's compensation (2u of the magnitudes sum |rho u| <= mass max|u|), the
@@ -436,7 +437,7 @@ def test_bound_torch_buffer_and_stream():
 # 29 u mass.  Kinetic energy: the velocities differ by at most 24 u per cell, so
 # |d sum rho u^2 / 2| <= 24 u sum rho |u| <= 24 u sqrt(2 mass KE) (Cauchy-Schwarz), plus 24 u KE
 # for rho and 9 u KE for the sums; max |u|: 24 u.
-DIAG_MASS_TOL = {lbm.FP64: 1e-13, lbm.FP32: (19 * 19 + 6 * 19) * 2.0 ** -48 + 1e-13}
+DIAG_MASS_TOL = {lbm.FP64: 1e-13, lbm.FP32: (19 + 4 + 3) ** 2 * 2.0 ** -48 + 1e-13}
 U32 = 2.0 ** -24
 
 
@@ -481,7 +482,8 @@ def test_step_diagnostics_mass_16bit_storage(storage, pattern):
     s.step(5)
     fused, full = s.step_diagnostics(), s.reduce()
     s.close()
-    assert abs(fused["mass"] / full["mass"] - 1) < DIAG_MASS_TOL[lbm.FP32]
+    # staged 16-bit tiles: 8 z steps of two cells per thread, n = 16
+    assert abs(fused["mass"] / full["mass"] - 1) < (19 + 16 + 3) ** 2 * 2.0 ** -48 + 1e-13
     assert fused["fluid_cells"] == full["fluid_cells"] and fused["nonfinite"] == 0
 
 
