@@ -473,8 +473,9 @@ def test_step_diagnostics_match_full_reduction(storage, pattern):
 @pytest.mark.parametrize("pattern", [lbm.TWO_GRID, lbm.AA])
 def test_step_diagnostics_mass_16bit_storage(storage, pattern):
     """16-bit deviation storage: the fused mass is the exact sum of rho0 + the stored (rounded)
-    deviations, so it matches the FP64 pass over the stored field to the same bound as FP32;
-    the 256-wide periodic box takes the staged (bulk-copy) two-grid path."""
+    deviations, so it matches the FP64 pass over the stored field within the bound stated for
+    FP32 arithmetic, (Q + n + 3)^2 u^2 with n the cells a thread sweeps; the 256-wide periodic
+    box takes the staged (bulk-copy) two-grid path."""
     case = Case(shape=(256, 12, 10), storage=storage, pattern=pattern, omega=1.3, force=(1e-5, 2e-6, 0.0))
     rho, u = inputs.random_state(case.shape, seed=15, rho_amp=0.02, u_amp=0.03)
     s = case.make_sim()
@@ -482,7 +483,7 @@ def test_step_diagnostics_mass_16bit_storage(storage, pattern):
     s.step(5)
     fused, full = s.step_diagnostics(), s.reduce()
     s.close()
-    # staged 16-bit tiles: 8 z steps of two cells per thread, n = 16
+    # staged 16-bit tiles: 8 z steps of two cells per thread, n = 16 (AA: n = 4)
     assert abs(fused["mass"] / full["mass"] - 1) < (19 + 16 + 3) ** 2 * 2.0 ** -48 + 1e-13
     assert fused["fluid_cells"] == full["fluid_cells"] and fused["nonfinite"] == 0
 
